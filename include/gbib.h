@@ -1,0 +1,199 @@
+/*
+ * gbib.h -- C ABI of the GB300-native multidirect-forcing immersed-boundary
+ * library (Zeng et al., "IAMReX", arXiv 2408.14140).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  * Grid (ib_grid): n[0] x n[1] x n[2] cells of uniform spacing h, first
+ *    cell centre at origin + h/2 on every axis, periodic with period n[a]*h.
+ *    This is the cell-centred "finest level" of Sec. 3.1 (semi-staggered grid:
+ *    velocity, force and PVF at cell centres, level set at nodes).
+ *    Each n[a] must be >= 12; prec is IB_F64 or IB_F32 and fixes the element
+ *    type of every Eulerian field argument (u, f).
+ *  * Eulerian fields are structure-of-arrays u[3][n2][n1][n0] (x fastest),
+ *    contiguous, 16-byte aligned.
+ *  * Lagrangian vectors are [count][3] row-major FP64, 8-byte aligned.
+ *  * Every pointer passed to a compute call is a DEVICE pointer on the
+ *    context's device, owned by the caller; the library never frees or keeps
+ *    it after the work queued on `stream` completes.  `stream` is a
+ *    cudaStream_t (NULL = legacy default stream).
+ *  * Calls are asynchronous on `stream`.  Their return value reports argument
+ *    and launch errors synchronously; errors found on the device (non-finite
+ *    input, a wait that gave up, a bin overflow) are latched in the context
+ *    and returned by ib_ctx_status().
+ *  * Work scratch lives in the context's workspace, allocated by
+ *    ib_ctx_create()/ib_ctx_reserve(); calls never allocate.  A call whose
+ *    scratch does not fit returns IB_ERR_OOM and ib_last_error() states the
+ *    bytes needed.  Calls on one context must not overlap on the GPU (they
+ *    share its workspace): use one context per concurrent stream.
+ *  * Results are deterministic: the same inputs give bitwise identical
+ *    outputs run to run (fixed summation orders, no floating-point atomics).
+ */
+#ifndef GBIB_H
+#define GBIB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(GBIB_BUILD) && defined(__GNUC__)
+#define GBIB_API __attribute__((visibility("default")))
+#else
+#define GBIB_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define IB_OK 0
+#define IB_ERR_INVALID (-1)      /* bad argument (null pointer, size, value)  */
+#define IB_ERR_OOM (-2)          /* workspace too small / allocation failed   */
+#define IB_ERR_CUDA (-3)         /* a CUDA runtime call failed                */
+#define IB_ERR_TIMEOUT (-4)      /* a bounded device-side wait gave up        */
+#define IB_ERR_NONFINITE (-5)    /* NaN/Inf in a particle or marker input     */
+#define IB_ERR_UNSUPPORTED (-6)  /* valid but outside this build's limits     */
+
+/* ---- enumerations ------------------------------------------------------ */
+typedef enum { IB_F64 = 0, IB_F32 = 1 } ib_prec;
+/* Regularised delta kernels (Sec. 3.1 Step 2: "three-point or four-point").
+ * ROMA3: Roma, Peskin & Berger (1999); PESKIN4: Peskin (2002).            */
+typedef enum { IB_DELTA_ROMA3 = 0, IB_DELTA_PESKIN4 = 1 } ib_delta;
+/* Particle order of Algorithm 1 (Sec. 3.1: "each particle goes into 1 to
+ * Ns loop sequentially").  SEQUENTIAL: particle p starts from the field left
+ * by particles 0..p-1.  SIMULTANEOUS: one Ns loop over all markers.        */
+typedef enum { IB_ORDER_SEQUENTIAL = 0, IB_ORDER_SIMULTANEOUS = 1 } ib_order;
+
+/* ---- problem description ----------------------------------------------- */
+typedef struct {
+    int n[3];          /* cells per axis (each >= 12)                       */
+    double h;          /* cell size (> 0)                                   */
+    double origin[3];  /* corner of cell (0,0,0)                            */
+    int prec;          /* ib_prec of every Eulerian field argument          */
+} ib_grid;
+
+/* P rigid spheres (Sec. 3.2).  Xr, Ur, Wr are [P][3]; radius, rho_p are [P];
+ * marker_offset is [P+1] (CSR: markers of particle p are
+ * marker_offset[p] .. marker_offset[p+1]-1, increasing, marker_offset[0]=0). */
+typedef struct {
+    int P;
+    double *Xr;        /* centroid X_r                                      */
+    double *Ur;        /* centroid velocity U_r                             */
+    double *Wr;        /* angular velocity W_r                              */
+    const double *radius;
+    const double *rho_p;
+    const int *marker_offset;
+} ib_particles;
+
+/* Surface markers (Sec. 3.1 Step 2, markers on the surface only).
+ * R[M][3] = X_l - X_r, the marker's offset from its particle's centroid
+ * (Eq. pr1); dV[M] = the marker's volume weight Delta V_l (Algorithm 1).    */
+typedef struct {
+    int M;
+    const double *R;
+    const double *dV;
+} ib_markers;
+
+/* Physical constants of Eqs. (particle1), (particle2), (DKT_model). */
+typedef struct {
+    double rho_f;      /* fluid density                                     */
+    double g[3];       /* gravitational acceleration                        */
+    double g_coll;     /* ||g|| of Eq. (DKT_model)                          */
+    double eps_c;      /* stiffness parameter epsilon_c (paper: 1e-4)       */
+    double d_c;        /* collision range d_c (paper: finest grid spacing)  */
+} ib_phys;
+
+typedef struct ib_ctx ib_ctx;
+
+/* ---- context ----------------------------------------------------------- */
+/* Create a context on the current CUDA device with a device workspace of
+ * `workspace_bytes` (0 selects 64 MiB).  Returns IB_OK, IB_ERR_INVALID
+ * (ctx NULL) or IB_ERR_OOM / IB_ERR_CUDA.                                 */
+GBIB_API int ib_ctx_create(ib_ctx **ctx, size_t workspace_bytes);
+/* Grow the workspace to at least `bytes` (synchronises the device).       */
+GBIB_API int ib_ctx_reserve(ib_ctx *ctx, size_t bytes);
+/* Free the context and its workspace (synchronises the device).           */
+GBIB_API int ib_ctx_destroy(ib_ctx *ctx);
+/* Synchronise `stream`, then return and clear the first device-side error
+ * latched by work queued since the last call (IB_OK when none).           */
+GBIB_API int ib_ctx_status(ib_ctx *ctx, void *stream);
+/* Human-readable message of the last failing call on this host thread.    */
+GBIB_API const char *ib_last_error(void);
+/* Workspace bytes the last call that returned IB_ERR_OOM on this host
+ * thread needed (0 if none); pass it to ib_ctx_reserve() and retry.       */
+GBIB_API size_t ib_workspace_needed(void);
+/* Number of streaming multiprocessors of the context's device.            */
+GBIB_API int ib_ctx_sm_count(const ib_ctx *ctx);
+
+/* ---- velocity interpolation J: Eq. (u), Eq. (vi), Algorithm 1 -----------
+ * U[l] = sum_ijk u(x_ijk) delta_h(x_ijk - X[l]) h^3 for l < M, where
+ * delta_h(x) = h^-3 prod_a phi(x_a / h) (Sec. 2).  X[M][3] are absolute
+ * positions (any value; the grid is periodic).  u is [3][n2][n1][n0] in the
+ * grid precision; U[M][3] is FP64 and overwritten.  M = 0 is a no-op.      */
+GBIB_API int ib_interpolate(ib_ctx *ctx, const ib_grid *grid, const void *u, int M,
+                   const double *X, int delta, double *U, void *stream);
+
+/* ---- force spreading S: Eq. (f), Eq. (fs), Algorithm 1 ------------------
+ * f(x_ijk) += sum_l F[l] delta_h(x_ijk - X[l]) dV[l] for every cell.  f is
+ * ACCUMULATED (zero it first for a plain spread), grid precision.  The sum
+ * per cell is a deterministic gather over markers binned by cell tile.     */
+GBIB_API int ib_spread(ib_ctx *ctx, const ib_grid *grid, int M, const double *X,
+              const double *F, const double *dV, int delta, void *f,
+              void *stream);
+
+/* ---- Algorithm 1, multidirect forcing over all particles ---------------
+ * u (in/out, grid precision) holds u~*,n+1 on entry and u*,n+1 on exit.
+ * Marker positions X_l = X_r + R_l and desired velocities
+ * U^d_l = U_r + W_r x R_l (Eq. pr1) are formed from `parts` and `marks`.
+ * Starting from F^0 = 0, each of the Ns passes interpolates U^{m-1}, sets
+ * F^m = F^{m-1} + (U^d - U^{m-1})/dt, spreads it and corrects
+ * u(m) = u(0) + dt f^m (Algorithm 1).  F_out[M][3] (FP64) receives F^Ns of
+ * every marker; f_out (nullable, grid precision) is ACCUMULATED with the
+ * Eulerian force dt^-1 (u_exit - u_entry) contributed by every particle.
+ * Sphere markers must lie within a box smaller than the grid.  Ns >= 1,
+ * dt > 0 finite.                                                          */
+GBIB_API int ib_multidirect_forcing(ib_ctx *ctx, const ib_grid *grid, void *u,
+                           const ib_particles *parts, const ib_markers *marks,
+                           int Ns, double dt, int delta, int order,
+                           double *F_out, void *f_out, void *stream);
+
+/* ---- particle volume integrals through the PVF (Sec. 4.1, Eq. level-set
+ * function, Eq. Heaviside; the flow-unsteadiness terms of Eqs. particle1/2):
+ *   Iu[p]   = sum_c alpha_c u_c h^3
+ *   Irxu[p] = sum_c alpha_c (x_c - X_r) x u_c h^3
+ *   vol[p]  = sum_c alpha_c h^3
+ * alpha_c = sum_m -phi_m H(-phi_m) / sum_m |phi_m| over the 8 cell corners,
+ * phi = |x - X_r| / radius - 1 (nearest periodic image).  Outputs FP64,
+ * overwritten; any of Iu, Irxu, vol may be NULL.                          */
+GBIB_API int particle_volume_integrals(ib_ctx *ctx, const ib_grid *grid, const void *u,
+                              const ib_particles *parts, double *Iu,
+                              double *Irxu, double *vol, void *stream);
+
+/* ---- marker force and torque (Eqs. particle1, particle2, first terms) ---
+ * F_ib[p] = -rho_f sum_l F[l] dV[l],  T_ib[p] = -rho_f sum_l R[l] x F[l] dV[l]
+ * over the markers of particle p; FP64, overwritten.                      */
+GBIB_API int particle_force_torque(ib_ctx *ctx, const ib_particles *parts,
+                          const ib_markers *marks, const double *F,
+                          double rho_f, double *F_ib, double *T_ib,
+                          void *stream);
+
+/* ---- collision + Newton-Euler + centroid update ------------------------
+ * F_c,i = sum_j F_c,ij of Eq. (DKT_model) with delta_ij = X_j - X_i (nearest
+ * image), D_c = R_i + R_j + d_c, mass (m_i + m_j)/2, evaluated at X^n; then
+ *   U^{n+1} = U^n + dt/(rho_p V_p) [F_ib + rho_f (Iu_new - Iu_old)/dt
+ *                                   + (rho_p - rho_f) V_p g + F_c]
+ *   W^{n+1} = W^n + dt/I_p [T_ib + rho_f (Irxu_new - Irxu_old)/dt]
+ *   X^{n+1} = X^n + dt/2 (U^{n+1} + U^n)                        (Eq. pr2)
+ * V_p = 4/3 pi R^3, I_p = 2/5 rho_p V_p R^2.  Ur, Wr, Xr of `parts` are
+ * updated in place; Fc_out[P][3] (nullable) receives F_c.                  */
+GBIB_API int particle_collide_update(ib_ctx *ctx, ib_particles *parts,
+                            const ib_grid *grid, const ib_phys *phys,
+                            double dt, const double *F_ib, const double *T_ib,
+                            const double *Iu_new, const double *Iu_old,
+                            const double *Irxu_new, const double *Irxu_old,
+                            double *Fc_out, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GBIB_H */

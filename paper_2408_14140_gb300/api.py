@@ -1,0 +1,349 @@
+"""ctypes binding of ``libgbib.so`` (C ABI in ``include/gbib.h``).
+
+Argument marshalling only: PyTorch tensors supply device memory and the
+current CUDA stream; every step of the method runs in the library's CUDA
+kernels.  There is no CPU fallback -- loading fails loudly when the library
+is missing.
+
+Entry points mirror the C ABI names:
+  ib_interpolate, ib_spread, ib_multidirect_forcing,
+  particle_volume_integrals, particle_force_torque, particle_collide_update
+as methods of :class:`Context`.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libgbib.so")
+
+IB_OK = 0
+IB_ERR_INVALID = -1
+IB_ERR_OOM = -2
+IB_ERR_CUDA = -3
+IB_ERR_TIMEOUT = -4
+IB_ERR_NONFINITE = -5
+IB_ERR_UNSUPPORTED = -6
+
+IB_F64 = 0
+IB_F32 = 1
+ROMA3 = 0
+PESKIN4 = 1
+SEQUENTIAL = 0
+SIMULTANEOUS = 1
+
+EXPORTS = ["ib_ctx_create", "ib_ctx_reserve", "ib_ctx_destroy", "ib_ctx_status",
+           "ib_last_error", "ib_workspace_needed", "ib_ctx_sm_count",
+           "ib_interpolate", "ib_spread", "ib_multidirect_forcing",
+           "particle_volume_integrals", "particle_force_torque",
+           "particle_collide_update"]
+
+
+class IBError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("gbib error %d: %s" % (code, msg))
+        self.code = code
+
+
+class Grid(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int * 3), ("h", ctypes.c_double),
+                ("origin", ctypes.c_double * 3), ("prec", ctypes.c_int)]
+
+
+class Particles(ctypes.Structure):
+    _fields_ = [("P", ctypes.c_int), ("Xr", ctypes.c_void_p), ("Ur", ctypes.c_void_p),
+                ("Wr", ctypes.c_void_p), ("radius", ctypes.c_void_p),
+                ("rho_p", ctypes.c_void_p), ("marker_offset", ctypes.c_void_p)]
+
+
+class Markers(ctypes.Structure):
+    _fields_ = [("M", ctypes.c_int), ("R", ctypes.c_void_p), ("dV", ctypes.c_void_p)]
+
+
+class Phys(ctypes.Structure):
+    _fields_ = [("rho_f", ctypes.c_double), ("g", ctypes.c_double * 3),
+                ("g_coll", ctypes.c_double), ("eps_c", ctypes.c_double),
+                ("d_c", ctypes.c_double)]
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load the CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError("libgbib.so is not built (%s); run __graft_entry__.build()" % path)
+    lib = ctypes.CDLL(path)
+    i, p, d, sz = ctypes.c_int, ctypes.c_void_p, ctypes.c_double, ctypes.c_size_t
+    sig = {
+        "ib_ctx_create": (i, [ctypes.POINTER(p), sz]),
+        "ib_ctx_reserve": (i, [p, sz]),
+        "ib_ctx_destroy": (i, [p]),
+        "ib_ctx_status": (i, [p, p]),
+        "ib_last_error": (ctypes.c_char_p, []),
+        "ib_workspace_needed": (sz, []),
+        "ib_ctx_sm_count": (i, [p]),
+        "ib_interpolate": (i, [p, p, p, i, p, i, p, p]),
+        "ib_spread": (i, [p, p, i, p, p, p, i, p, p]),
+        "ib_multidirect_forcing": (i, [p, p, p, p, p, i, d, i, i, p, p, p]),
+        "particle_volume_integrals": (i, [p, p, p, p, p, p, p, p]),
+        "particle_force_torque": (i, [p, p, p, p, d, p, p, p]),
+        "particle_collide_update": (i, [p, p, p, p, d, p, p, p, p, p, p, p, p]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _need(t, name, dtype, shape=None):
+    if not isinstance(t, torch.Tensor):
+        raise TypeError("%s must be a torch.Tensor" % name)
+    if not t.is_cuda:
+        raise ValueError("%s must be a CUDA tensor" % name)
+    if t.dtype != dtype:
+        raise TypeError("%s must be %s, got %s" % (name, dtype, t.dtype))
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError("%s must have shape %s, got %s" % (name, tuple(shape), tuple(t.shape)))
+    return t
+
+
+def field_dtype(prec):
+    return torch.float64 if prec == IB_F64 else torch.float32
+
+
+def make_grid(n, h, origin=(0.0, 0.0, 0.0), prec=IB_F64) -> Grid:
+    g = Grid()
+    for a in range(3):
+        g.n[a] = int(n[a])
+        g.origin[a] = float(origin[a])
+    g.h = float(h)
+    g.prec = int(prec)
+    return g
+
+
+class Context:
+    """Owns one ``ib_ctx`` (device workspace + error latch)."""
+
+    def __init__(self, workspace_bytes: int = 0):
+        self.lib = load()
+        h = ctypes.c_void_p()
+        self._check(self.lib.ib_ctx_create(ctypes.byref(h), int(workspace_bytes)))
+        self.handle = h
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.ib_ctx_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc):
+        if rc != IB_OK:
+            raise IBError(rc, self.lib.ib_last_error().decode())
+
+    def _call(self, fn, *args):
+        rc = fn(*args)
+        if rc == IB_ERR_OOM:
+            need = self.lib.ib_workspace_needed()
+            if need:
+                self._check(self.lib.ib_ctx_reserve(self.handle, int(need * 5 // 4) + (1 << 20)))
+                rc = fn(*args)
+        self._check(rc)
+
+    @property
+    def sm_count(self):
+        return self.lib.ib_ctx_sm_count(self.handle)
+
+    def reserve(self, nbytes: int):
+        self._check(self.lib.ib_ctx_reserve(self.handle, int(nbytes)))
+
+    def status(self, stream=None):
+        """Synchronise the stream and raise the first device-side error."""
+        self._check(self.lib.ib_ctx_status(self.handle, _stream(stream)))
+
+    # -- operators -------------------------------------------------------
+    @staticmethod
+    def _grid_of(u, n, h, origin):
+        prec = IB_F64 if u.dtype == torch.float64 else IB_F32
+        return make_grid(n, h, origin, prec)
+
+    def ib_interpolate(self, u, X, h, origin=(0.0, 0.0, 0.0), delta=ROMA3, U=None, stream=None):
+        """U[M,3] (float64) = J u at positions X[M,3]; u is [3, n2, n1, n0]."""
+        if u.dtype not in (torch.float64, torch.float32):
+            raise TypeError("u must be float64 or float32")
+        n = (u.shape[3], u.shape[2], u.shape[1])
+        _need(u, "u", u.dtype, (3, n[2], n[1], n[0]))
+        M = X.shape[0]
+        _need(X, "X", torch.float64, (M, 3))
+        if U is None:
+            U = torch.empty((M, 3), dtype=torch.float64, device=X.device)
+        _need(U, "U", torch.float64, (M, 3))
+        g = self._grid_of(u, n, h, origin)
+        self._call(self.lib.ib_interpolate, self.handle, ctypes.byref(g), _ptr(u), M, _ptr(X),
+                   int(delta), _ptr(U), _stream(stream))
+        return U
+
+    def ib_spread(self, f, X, F, dV, h, origin=(0.0, 0.0, 0.0), delta=ROMA3, stream=None):
+        """f += S F (deterministic gather); f is [3, n2, n1, n0]."""
+        n = (f.shape[3], f.shape[2], f.shape[1])
+        _need(f, "f", f.dtype, (3, n[2], n[1], n[0]))
+        M = X.shape[0]
+        _need(X, "X", torch.float64, (M, 3))
+        _need(F, "F", torch.float64, (M, 3))
+        _need(dV, "dV", torch.float64, (M,))
+        g = self._grid_of(f, n, h, origin)
+        self._call(self.lib.ib_spread, self.handle, ctypes.byref(g), M, _ptr(X), _ptr(F), _ptr(dV),
+                   int(delta), _ptr(f), _stream(stream))
+        return f
+
+    @staticmethod
+    def particles_struct(Xr, Ur, Wr, radius, rho_p, moff):
+        P = Xr.shape[0]
+        for t, nm in ((Xr, "Xr"), (Ur, "Ur"), (Wr, "Wr")):
+            _need(t, nm, torch.float64, (P, 3))
+        _need(radius, "radius", torch.float64, (P,))
+        _need(rho_p, "rho_p", torch.float64, (P,))
+        _need(moff, "marker_offset", torch.int32, (P + 1,))
+        s = Particles()
+        s.P = P
+        s.Xr, s.Ur, s.Wr = Xr.data_ptr(), Ur.data_ptr(), Wr.data_ptr()
+        s.radius, s.rho_p, s.marker_offset = radius.data_ptr(), rho_p.data_ptr(), moff.data_ptr()
+        return s
+
+    @staticmethod
+    def markers_struct(R, dV):
+        M = R.shape[0]
+        _need(R, "R", torch.float64, (M, 3))
+        _need(dV, "dV", torch.float64, (M,))
+        s = Markers()
+        s.M = M
+        s.R, s.dV = R.data_ptr(), dV.data_ptr()
+        return s
+
+    def ib_multidirect_forcing(self, u, h, parts, marks, Ns, dt, origin=(0.0, 0.0, 0.0),
+                               delta=ROMA3, order=SEQUENTIAL, F_out=None, f_out=None,
+                               stream=None):
+        """Algorithm 1 in place on u; returns F_out[M,3] (float64).
+
+        ``parts`` = dict(Xr, Ur, Wr, radius, rho_p, moff); ``marks`` = dict(R, dV).
+        """
+        n = (u.shape[3], u.shape[2], u.shape[1])
+        _need(u, "u", u.dtype, (3, n[2], n[1], n[0]))
+        ps = self.particles_struct(parts["Xr"], parts["Ur"], parts["Wr"], parts["radius"],
+                                   parts["rho_p"], parts["moff"])
+        ms = self.markers_struct(marks["R"], marks["dV"])
+        if F_out is None:
+            F_out = torch.empty((ms.M, 3), dtype=torch.float64, device=u.device)
+        _need(F_out, "F_out", torch.float64, (ms.M, 3))
+        if f_out is not None:
+            _need(f_out, "f_out", u.dtype, tuple(u.shape))
+        g = self._grid_of(u, n, h, origin)
+        self._call(self.lib.ib_multidirect_forcing, self.handle, ctypes.byref(g), _ptr(u),
+                   ctypes.byref(ps), ctypes.byref(ms), int(Ns), float(dt), int(delta), int(order),
+                   _ptr(F_out), _ptr(f_out), _stream(stream))
+        return F_out
+
+    def particle_volume_integrals(self, u, h, parts, origin=(0.0, 0.0, 0.0), out=None, stream=None):
+        """(Iu[P,3], Irxu[P,3], vol[P]) through the PVF of each sphere."""
+        n = (u.shape[3], u.shape[2], u.shape[1])
+        _need(u, "u", u.dtype, (3, n[2], n[1], n[0]))
+        ps = self.particles_struct(parts["Xr"], parts["Ur"], parts["Wr"], parts["radius"],
+                                   parts["rho_p"], parts["moff"])
+        P = ps.P
+        if out is None:
+            out = (torch.empty((P, 3), dtype=torch.float64, device=u.device),
+                   torch.empty((P, 3), dtype=torch.float64, device=u.device),
+                   torch.empty((P,), dtype=torch.float64, device=u.device))
+        Iu, Irxu, vol = out
+        _need(Iu, "Iu", torch.float64, (P, 3))
+        _need(Irxu, "Irxu", torch.float64, (P, 3))
+        _need(vol, "vol", torch.float64, (P,))
+        g = self._grid_of(u, n, h, origin)
+        self._call(self.lib.particle_volume_integrals, self.handle, ctypes.byref(g), _ptr(u),
+                   ctypes.byref(ps), _ptr(Iu), _ptr(Irxu), _ptr(vol), _stream(stream))
+        return Iu, Irxu, vol
+
+    def particle_force_torque(self, parts, marks, F, rho_f, out=None, stream=None):
+        """(F_ib[P,3], T_ib[P,3]) = (-rho_f sum F dV, -rho_f sum R x F dV)."""
+        ps = self.particles_struct(parts["Xr"], parts["Ur"], parts["Wr"], parts["radius"],
+                                   parts["rho_p"], parts["moff"])
+        ms = self.markers_struct(marks["R"], marks["dV"])
+        _need(F, "F", torch.float64, (ms.M, 3))
+        P = ps.P
+        if out is None:
+            out = (torch.empty((P, 3), dtype=torch.float64, device=F.device),
+                   torch.empty((P, 3), dtype=torch.float64, device=F.device))
+        Fib, Tib = out
+        _need(Fib, "F_ib", torch.float64, (P, 3))
+        _need(Tib, "T_ib", torch.float64, (P, 3))
+        self._call(self.lib.particle_force_torque, self.handle, ctypes.byref(ps), ctypes.byref(ms),
+                   _ptr(F), float(rho_f), _ptr(Fib), _ptr(Tib), _stream(stream))
+        return Fib, Tib
+
+    def particle_collide_update(self, parts, n, h, phys, dt, F_ib, T_ib, Iu_new, Iu_old,
+                                Irxu_new, Irxu_old, Fc_out=None, origin=(0.0, 0.0, 0.0),
+                                stream=None):
+        """Collision + Newton-Euler + centroid update, in place on parts['Xr','Ur','Wr'].
+
+        ``phys`` = (rho_f, gx, gy, gz, g_coll, eps_c, d_c).
+        """
+        ps = self.particles_struct(parts["Xr"], parts["Ur"], parts["Wr"], parts["radius"],
+                                   parts["rho_p"], parts["moff"])
+        P = ps.P
+        for t, nm in ((F_ib, "F_ib"), (T_ib, "T_ib"), (Iu_new, "Iu_new"), (Iu_old, "Iu_old"),
+                      (Irxu_new, "Irxu_new"), (Irxu_old, "Irxu_old")):
+            _need(t, nm, torch.float64, (P, 3))
+        if Fc_out is not None:
+            _need(Fc_out, "Fc_out", torch.float64, (P, 3))
+        ph = Phys()
+        ph.rho_f = float(phys[0])
+        for a in range(3):
+            ph.g[a] = float(phys[1 + a])
+        ph.g_coll, ph.eps_c, ph.d_c = float(phys[4]), float(phys[5]), float(phys[6])
+        g = make_grid(n, h, origin, IB_F64)
+        self._call(self.lib.particle_collide_update, self.handle, ctypes.byref(ps), ctypes.byref(g),
+                   ctypes.byref(ph), float(dt), _ptr(F_ib), _ptr(T_ib), _ptr(Iu_new), _ptr(Iu_old),
+                   _ptr(Irxu_new), _ptr(Irxu_old), _ptr(Fc_out), _stream(stream))
+        return Fc_out
+
+
+def device_case(case, prec=IB_F64, device="cuda"):
+    """Copy a :class:`synth.Case` to the device: returns (u, parts, marks).
+
+    ``u`` has the field dtype of ``prec``; particle and marker arrays are
+    float64 (offsets int32), as the C ABI expects.
+    """
+    dt = field_dtype(prec)
+
+    def t(a, dtype=torch.float64):
+        return torch.as_tensor(a).to(device=device, dtype=dtype).contiguous()
+
+    u = t(case.u, dt)
+    parts = dict(Xr=t(case.Xr), Ur=t(case.Ur), Wr=t(case.Wr), radius=t(case.radius),
+                 rho_p=t(case.rho_p), moff=t(case.moff, torch.int32))
+    marks = dict(R=t(case.R), dV=t(case.dV))
+    return u, parts, marks

@@ -1,0 +1,223 @@
+// Context, workspace, error reporting and the exclusive scan used by the
+// binning stages.
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include "gbib_internal.cuh"
+
+namespace gbib {
+
+static thread_local char g_last_error[512] = "";
+static thread_local size_t g_ws_need = 0;
+
+int oom_error(size_t need, size_t have) {
+    g_ws_need = need;
+    return set_error(IB_ERR_OOM, "workspace too small: need %zu bytes (have %zu); call ib_ctx_reserve",
+                     need, have);
+}
+
+int set_error(int code, const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_last_error, sizeof(g_last_error), fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+int check_launch(const char *what) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess)
+        return set_error(IB_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+    return IB_OK;
+}
+
+int validate_grid(const ib_grid *g, int need_prec) {
+    if (!g) return set_error(IB_ERR_INVALID, "grid is NULL");
+    for (int a = 0; a < 3; ++a)
+        if (g->n[a] < 12 || g->n[a] >= (1 << 21))
+            return set_error(IB_ERR_INVALID, "grid n[%d]=%d outside [12, 2^21)", a, g->n[a]);
+    if (!(g->h > 0.0) || !isfinite(g->h))
+        return set_error(IB_ERR_INVALID, "grid h must be finite and > 0");
+    for (int a = 0; a < 3; ++a)
+        if (!isfinite(g->origin[a])) return set_error(IB_ERR_INVALID, "grid origin not finite");
+    if (need_prec && g->prec != IB_F64 && g->prec != IB_F32)
+        return set_error(IB_ERR_INVALID, "grid prec must be IB_F64 or IB_F32");
+    long long cells = (long long)g->n[0] * g->n[1] * g->n[2];
+    if (cells > (1LL << 40)) return set_error(IB_ERR_INVALID, "grid too large");
+    return IB_OK;
+}
+
+DevGrid make_dev_grid(const ib_grid *g) {
+    DevGrid d;
+    for (int a = 0; a < 3; ++a) {
+        d.n[a] = g->n[a];
+        d.org[a] = g->origin[a];
+    }
+    d.h = g->h;
+    d.inv_h = 1.0 / g->h;
+    d.inv_h3 = 1.0 / (g->h * g->h * g->h);
+    return d;
+}
+
+// ---- exclusive scan ------------------------------------------------------
+// Three stages: per-block totals, a scan of the totals in one block, then a
+// per-block scan that adds the block's offset.  1024 elements per block.
+constexpr int kScanBlock = 1024;
+
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *total) {
+    __shared__ uint32_t warp_sums[32];
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    uint32_t x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_sums[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        int nw = blockDim.x >> 5;
+        uint32_t s = lane < nw ? warp_sums[lane] : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s += y;
+        }
+        warp_sums[lane] = s;
+    }
+    __syncthreads();
+    uint32_t base = wid ? warp_sums[wid - 1] : 0;
+    if (total) *total = warp_sums[(blockDim.x >> 5) - 1];
+    uint32_t r = base + x - v;
+    __syncthreads();
+    return r;
+}
+
+__global__ void k_scan_totals(const uint32_t *in, int n, uint32_t *totals) {
+    int i = blockIdx.x * kScanBlock + threadIdx.x;
+    uint32_t v = i < n ? in[i] : 0;
+    uint32_t tot;
+    block_exclusive_scan(v, &tot);
+    if (threadIdx.x == 0) totals[blockIdx.x] = tot;
+}
+
+__global__ void k_scan_top(uint32_t *totals, int nb) {
+    // nb <= kScanBlock * kScanBlock: each thread folds a strided chunk.
+    __shared__ uint32_t carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int base = 0; base < nb; base += kScanBlock) {
+        int i = base + threadIdx.x;
+        uint32_t v = i < nb ? totals[i] : 0;
+        uint32_t tot;
+        uint32_t ex = block_exclusive_scan(v, &tot);
+        if (i < nb) totals[i] = carry + ex;
+        __syncthreads();
+        if (threadIdx.x == 0) carry += tot;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) totals[nb] = carry;
+}
+
+__global__ void k_scan_apply(const uint32_t *in, uint32_t *out, int n, const uint32_t *totals) {
+    int i = blockIdx.x * kScanBlock + threadIdx.x;
+    uint32_t v = i < n ? in[i] : 0;
+    uint32_t ex = block_exclusive_scan(v, nullptr);
+    if (i < n) out[i] = totals[blockIdx.x] + ex;
+    if (blockIdx.x == 0 && threadIdx.x == 0) out[n] = totals[gridDim.x];
+}
+
+size_t scan_workspace(int n) { return (size_t)(n + kScanBlock - 1) / kScanBlock + 2; }
+
+void exclusive_scan(const uint32_t *in, uint32_t *out, int n, uint32_t *scratch,
+                    cudaStream_t s) {
+    int nb = (n + kScanBlock - 1) / kScanBlock;
+    if (nb == 0) nb = 1;
+    k_scan_totals<<<nb, kScanBlock, 0, s>>>(in, n, scratch);
+    k_scan_top<<<1, kScanBlock, 0, s>>>(scratch, nb);
+    k_scan_apply<<<nb, kScanBlock, 0, s>>>(in, out, n, scratch);
+}
+
+}  // namespace gbib
+
+using namespace gbib;
+
+extern "C" {
+
+const char *ib_last_error(void) { return g_last_error; }
+
+size_t ib_workspace_needed(void) { return g_ws_need; }
+
+int ib_ctx_create(ib_ctx **ctx, size_t workspace_bytes) {
+    if (!ctx) return set_error(IB_ERR_INVALID, "ctx out-pointer is NULL");
+    *ctx = nullptr;
+    ib_ctx *c = new ib_ctx();
+    if (cudaGetDevice(&c->device) != cudaSuccess) {
+        delete c;
+        return set_error(IB_ERR_CUDA, "no CUDA device");
+    }
+    cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->device);
+    if (workspace_bytes == 0) workspace_bytes = (size_t)64 << 20;
+    c->ws_bytes = workspace_bytes;
+    if (cudaMalloc(&c->ws, workspace_bytes) != cudaSuccess) {
+        cudaGetLastError();
+        delete c;
+        return set_error(IB_ERR_OOM, "workspace of %zu bytes: cudaMalloc failed", workspace_bytes);
+    }
+    if (cudaMalloc(&c->status, sizeof(DevStatus)) != cudaSuccess ||
+        cudaMemset(c->status, 0, sizeof(DevStatus)) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(c->ws);
+        delete c;
+        return set_error(IB_ERR_CUDA, "status latch allocation failed");
+    }
+    *ctx = c;
+    return IB_OK;
+}
+
+int ib_ctx_reserve(ib_ctx *c, size_t bytes) {
+    if (!c) return set_error(IB_ERR_INVALID, "ctx is NULL");
+    if (bytes <= c->ws_bytes) return IB_OK;
+    if (cudaDeviceSynchronize() != cudaSuccess)
+        return set_error(IB_ERR_CUDA, "reserve: %s", cudaGetErrorString(cudaGetLastError()));
+    void *p = nullptr;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(IB_ERR_OOM, "reserve: cudaMalloc(%zu) failed", bytes);
+    }
+    cudaFree(c->ws);
+    c->ws = p;
+    c->ws_bytes = bytes;
+    return IB_OK;
+}
+
+int ib_ctx_destroy(ib_ctx *c) {
+    if (!c) return IB_OK;
+    cudaDeviceSynchronize();
+    cudaFree(c->ws);
+    cudaFree(c->status);
+    delete c;
+    return IB_OK;
+}
+
+int ib_ctx_status(ib_ctx *c, void *stream) {
+    if (!c) return set_error(IB_ERR_INVALID, "ctx is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (cudaStreamSynchronize(s) != cudaSuccess)
+        return set_error(IB_ERR_CUDA, "status: %s", cudaGetErrorString(cudaGetLastError()));
+    DevStatus h;
+    if (cudaMemcpy(&h, c->status, sizeof(h), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return set_error(IB_ERR_CUDA, "status copy failed");
+    if (h.code != 0) {
+        cudaMemset(c->status, 0, sizeof(DevStatus));
+        const char *what = h.code == IB_ERR_TIMEOUT      ? "a device-side wait gave up"
+                           : h.code == IB_ERR_NONFINITE  ? "non-finite particle or marker input"
+                           : h.code == IB_ERR_UNSUPPORTED ? "a bin exceeded its capacity"
+                                                          : "device error";
+        return set_error(h.code, "device status %d (%s), detail %d", h.code, what, h.detail);
+    }
+    return IB_OK;
+}
+
+int ib_ctx_sm_count(const ib_ctx *c) { return c ? c->sm_count : 0; }
+
+}  // extern "C"

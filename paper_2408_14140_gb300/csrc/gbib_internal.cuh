@@ -1,0 +1,149 @@
+// Internal declarations of the GB300 multidirect-forcing IB library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "gbib.h"
+
+namespace gbib {
+
+// Cells per axis of one spreading tile (the unit owned by one CTA in the
+// deterministic gather).  512 cells = one thread per cell.
+constexpr int kTile = 8;
+constexpr int kTileCells = kTile * kTile * kTile;
+// Anchors (first stencil cell) that can touch a tile lie in
+// [lo - 3, lo + kTile - 1]; rel = wrap(anchor - lo + 3) is in [0, kRow).
+constexpr int kRow = kTile + 3;
+constexpr int kRows = kRow * kRow;
+// Largest candidate list one tile may gather from.
+constexpr int kMaxCand = 4096;
+// Bounded spin of device-side waits (iterations of ~100 ns sleeps).
+constexpr long long kSpinLimit = 20LL * 1000 * 1000;
+
+struct DevGrid {
+    int n[3];
+    double h, inv_h, inv_h3;
+    double org[3];
+};
+
+// Device-side error latch: first code wins.
+struct DevStatus {
+    int code;
+    int detail;
+};
+
+__device__ __forceinline__ void raise_status(DevStatus *st, int code, int detail) {
+    if (atomicCAS(&st->code, 0, code) == 0) st->detail = detail;
+}
+
+__host__ __device__ __forceinline__ int wrap_int(long long j, int n) {
+    long long m = j % n;
+    return (int)(m < 0 ? m + n : m);
+}
+
+// Add k (0 <= k < n) to a wrapped index without a modulo.
+__device__ __forceinline__ int wrap_add(int j, int k, int n) {
+    int v = j + k;
+    return v >= n ? v - n : v;
+}
+
+// (c - j) mod n for c, j in [0, n).
+__device__ __forceinline__ int wrap_diff(int c, int j, int n) {
+    int d = c - j;
+    return d < 0 ? d + n : d;
+}
+
+// Packed wrapped anchor: 21 bits per axis.
+__host__ __device__ __forceinline__ uint64_t pack_anchor(int x, int y, int z) {
+    return (uint64_t)x | ((uint64_t)y << 21) | ((uint64_t)z << 42);
+}
+__device__ __forceinline__ int anchor_x(uint64_t a) { return (int)(a & 0x1FFFFF); }
+__device__ __forceinline__ int anchor_y(uint64_t a) { return (int)((a >> 21) & 0x1FFFFF); }
+__device__ __forceinline__ int anchor_z(uint64_t a) { return (int)(a >> 42); }
+
+template <int KER> struct Kernel;
+template <> struct Kernel<IB_DELTA_ROMA3> { static constexpr int W = 3; };
+template <> struct Kernel<IB_DELTA_PESKIN4> { static constexpr int W = 4; };
+
+// One axis of the regularised delta kernel.  s is the position in units of
+// h measured from the first cell centre; returns the first stencil cell
+// (unwrapped) and the kernel weights of the W cells from there.  All
+// stencil weights share one square root: for the three-point kernel with
+// r = s - round(s) they are ((2 - 3r - q)/6, (1 + q)/3, (2 + 3r - q)/6),
+// q = sqrt(1 - 3 r^2); for the four-point kernel with r = s - floor(s)
+// they are ((3 - 2r - q)/8, (3 - 2r + q)/8, (1 + 2r + q)/8, (1 + 2r - q)/8),
+// q = sqrt(1 + 4r - 4r^2).  These are the piecewise kernels of Roma et al.
+// (1999) and Peskin (2002) evaluated at the W offsets of the stencil.
+template <int KER, typename T>
+__device__ __forceinline__ long long axis_weights(double s, T w[4]) {
+    if (KER == IB_DELTA_ROMA3) {
+        double b = floor(s + 0.5);
+        T r = (T)(s - b);
+        T q = sqrt(T(1) - T(3) * r * r);
+        w[0] = (T(2) - T(3) * r - q) * T(1.0 / 6.0);
+        w[1] = (T(1) + q) * T(1.0 / 3.0);
+        w[2] = (T(2) + T(3) * r - q) * T(1.0 / 6.0);
+        w[3] = T(0);
+        return (long long)b - 1;
+    } else {
+        double b = floor(s);
+        T r = (T)(s - b);
+        T q = sqrt(T(1) + T(4) * r - T(4) * r * r);
+        w[0] = (T(3) - T(2) * r - q) * T(0.125);
+        w[1] = (T(3) - T(2) * r + q) * T(0.125);
+        w[2] = (T(1) + T(2) * r + q) * T(0.125);
+        w[3] = (T(1) + T(2) * r - q) * T(0.125);
+        return (long long)b - 1;
+    }
+}
+
+__device__ __forceinline__ bool finite3(const double *v) {
+    return isfinite(v[0]) && isfinite(v[1]) && isfinite(v[2]);
+}
+
+}  // namespace gbib
+
+// ---- host side ------------------------------------------------------------
+struct ib_ctx {
+    int device;
+    int sm_count;
+    void *ws;            // device workspace
+    size_t ws_bytes;
+    gbib::DevStatus *status;  // device error latch
+};
+
+namespace gbib {
+
+// Bump allocator over the context workspace (256-byte aligned chunks).
+struct Arena {
+    char *base;
+    size_t cap, used;
+    explicit Arena(ib_ctx *c) : base((char *)c->ws), cap(c->ws_bytes), used(0) {}
+    template <typename T> T *take(size_t count) {
+        size_t bytes = ((count * sizeof(T)) + 255) & ~(size_t)255;
+        if (used + bytes > cap) {
+            used += bytes;  // keep counting so the caller can report the need
+            return nullptr;
+        }
+        T *p = (T *)(base + used);
+        used += bytes;
+        return p;
+    }
+    bool ok() const { return used <= cap; }
+};
+
+int set_error(int code, const char *fmt, ...);
+// Record an out-of-workspace failure of `need` bytes and return IB_ERR_OOM.
+int oom_error(size_t need, size_t have);
+int check_launch(const char *what);
+int validate_grid(const ib_grid *g, int need_prec);
+DevGrid make_dev_grid(const ib_grid *g);
+
+// Exclusive scan of n uint32 counts into out[0..n] (out[n] = total).
+// Needs scan_workspace(n) uint32 of scratch.
+size_t scan_workspace(int n);
+void exclusive_scan(const uint32_t *in, uint32_t *out, int n, uint32_t *scratch,
+                    cudaStream_t s);
+
+}  // namespace gbib

@@ -1,0 +1,1007 @@
+// Velocity interpolation, force spreading and Algorithm 1 (multidirect
+// forcing) of arXiv 2408.14140, Sec. 3.1 Step 2.
+//
+// Data path on the device
+// -----------------------
+//  1. Marker preparation: position X_l = X_r + R_l, desired velocity
+//     U^d_l = U_r + W_r x R_l (Eq. pr1), the first stencil cell ("anchor",
+//     wrapped) and the per-axis kernel weights, computed once per call.
+//  2. Binning: every marker is listed in each spreading tile (8^3 cells) its
+//     stencil touches.  Tiles are global grid tiles (simultaneous order and
+//     ib_spread) or tiles of each particle's own bounding box (sequential
+//     order).  Each tile's list is sorted by (anchor row, marker index) once,
+//     which fixes the summation order of every cell: spreading is a
+//     deterministic gather over marker bins, with no floating-point atomics.
+//  3. Passes: one persistent cooperative kernel runs, per wavefront of
+//     non-conflicting particles and per forcing pass m, an interpolation
+//     phase over markers (U, F += (U^d - U)/dt) and a gather phase over tiles
+//     (u += S (U^d - U) dV / h^3, the increment of Algorithm 1's correction),
+//     separated by grid-wide barriers with bounded waits.
+//
+// The correction is applied incrementally, u(m) = u(m-1) + dt S(F^m - F^{m-1}),
+// which equals the paper's u(m) = u(0) + dt S F^m in exact arithmetic and
+// needs no copy of u(0).
+#include <float.h>
+
+#include "gbib_internal.cuh"
+
+namespace gbib {
+
+constexpr int kBlock = 512;          // threads per CTA (one per tile cell)
+constexpr int kLocalTiles = 8;       // local tiles per axis of a particle box
+constexpr int kLocalSlots = kLocalTiles * kLocalTiles * kLocalTiles;
+constexpr int kMaxBox = kLocalTiles * kTile;  // 64 cells
+
+// Per-marker state kept in the workspace for one call.
+template <typename T>
+struct MarkerState {
+    uint64_t *anchor;  // [M] wrapped first stencil cell
+    T *wts;            // [M][12] per-axis weights (x 0..3, y 4..7, z 8..11)
+    T *A;              // [M][4] spread source of the current pass
+    double *Ud;        // [M][3] desired velocity
+};
+
+// Slot (spreading tile) records.
+struct Slots {
+    uint32_t *count;   // [ndense] candidates per dense slot
+    uint32_t *start;   // [ndense+1] exclusive scan of count
+    uint32_t *cursor;  // [ndense] fill cursors
+    uint32_t *flag_scan;  // [ndense+1] compact index of non-empty slots
+    uint32_t *dense_of;   // [ncompact_max] dense id of each compact slot
+    uint32_t *cand;    // [total candidates] marker ids, sorted per slot
+    uint16_t *rows;    // [ncompact_max][kRows+1] row starts, relative
+    int4 *geo_lo;      // [ncompact_max] tile first cell (wrapped), w = level
+    int4 *geo_dim;     // [ncompact_max] tile dims, w = candidate count
+};
+
+// ---------------------------------------------------------------------------
+// interpolation of one marker from precomputed weights
+// ---------------------------------------------------------------------------
+// Loads of data that other CTAs of a persistent kernel write between grid
+// barriers go through L2 (ld.global.cg): L1 is not coherent across SMs.
+template <bool COH, typename T>
+__device__ __forceinline__ T ld(const T *p) {
+    if (COH) return __ldcg(p);
+    return __ldg(p);
+}
+
+template <typename T, int KW, bool COH = false>
+__device__ __forceinline__ void interp_marker(const T *__restrict__ u, const DevGrid &g,
+                                              long long N, uint64_t anc,
+                                              const T *__restrict__ w, T out[3]) {
+    int ix[KW], iy[KW], iz[KW];
+    int ax = anchor_x(anc), ay = anchor_y(anc), az = anchor_z(anc);
+#pragma unroll
+    for (int k = 0; k < KW; ++k) {
+        ix[k] = wrap_add(ax, k, g.n[0]);
+        iy[k] = wrap_add(ay, k, g.n[1]);
+        iz[k] = wrap_add(az, k, g.n[2]);
+    }
+    T a0 = 0, a1 = 0, a2 = 0;
+#pragma unroll
+    for (int kz = 0; kz < KW; ++kz) {
+#pragma unroll
+        for (int ky = 0; ky < KW; ++ky) {
+            long long row = ((long long)iz[kz] * g.n[1] + iy[ky]) * g.n[0];
+            T wyz = w[8 + kz] * w[4 + ky];
+#pragma unroll
+            for (int kx = 0; kx < KW; ++kx) {
+                long long c = row + ix[kx];
+                T wt = wyz * w[kx];
+                a0 += wt * ld<COH>(u + c);
+                a1 += wt * ld<COH>(u + N + c);
+                a2 += wt * ld<COH>(u + 2 * N + c);
+            }
+        }
+    }
+    out[0] = a0;
+    out[1] = a1;
+    out[2] = a2;
+}
+
+template <typename T, int KER>
+__device__ __forceinline__ uint64_t marker_weights(const DevGrid &g, const double X[3],
+                                                   T w[12], long long first[3]) {
+    int a[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        double s = (X[d] - g.org[d]) * g.inv_h - 0.5;
+        first[d] = axis_weights<KER, T>(s, w + 4 * d);
+        a[d] = wrap_int(first[d], g.n[d]);
+    }
+    return pack_anchor(a[0], a[1], a[2]);
+}
+
+// ---------------------------------------------------------------------------
+// ib_interpolate
+// ---------------------------------------------------------------------------
+template <typename T, int KER>
+__global__ void __launch_bounds__(256) k_interpolate(DevGrid g, const T *__restrict__ u, int M,
+                                                     const double *__restrict__ X,
+                                                     double *__restrict__ U, DevStatus *st) {
+    constexpr int KW = Kernel<KER>::W;
+    long long N = (long long)g.n[0] * g.n[1] * g.n[2];
+    for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < M; l += gridDim.x * blockDim.x) {
+        double x[3] = {X[3 * l], X[3 * l + 1], X[3 * l + 2]};
+        if (!finite3(x)) {
+            raise_status(st, IB_ERR_NONFINITE, l);
+            U[3 * l] = U[3 * l + 1] = U[3 * l + 2] = 0.0;
+            continue;
+        }
+        T w[12];
+        long long first[3];
+        uint64_t anc = marker_weights<T, KER>(g, x, w, first);
+        T o[3];
+        interp_marker<T, KW>(u, g, N, anc, w, o);
+        U[3 * l] = (double)o[0];
+        U[3 * l + 1] = (double)o[1];
+        U[3 * l + 2] = (double)o[2];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// marker preparation
+// ---------------------------------------------------------------------------
+// Standalone spreading: positions X given, source A = F dV / h^3.
+template <typename T, int KER>
+__global__ void k_prep_spread(DevGrid g, int M, const double *__restrict__ X,
+                              const double *__restrict__ F, const double *__restrict__ dV,
+                              MarkerState<T> ms, DevStatus *st) {
+    for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < M; l += gridDim.x * blockDim.x) {
+        double x[3] = {X[3 * l], X[3 * l + 1], X[3 * l + 2]};
+        double f[3] = {F[3 * l], F[3 * l + 1], F[3 * l + 2]};
+        double dv = dV[l];
+        bool ok = finite3(x) && finite3(f) && isfinite(dv);
+        if (!ok) {
+            raise_status(st, IB_ERR_NONFINITE, l);
+            x[0] = g.org[0];
+            x[1] = g.org[1];
+            x[2] = g.org[2];
+            f[0] = f[1] = f[2] = 0.0;
+            dv = 0.0;
+        }
+        T w[12];
+        long long first[3];
+        ms.anchor[l] = marker_weights<T, KER>(g, x, w, first);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) ms.wts[12 * l + k] = w[k];
+        double q = dv * g.inv_h3;
+        ms.A[4 * l + 0] = (T)(f[0] * q);
+        ms.A[4 * l + 1] = (T)(f[1] * q);
+        ms.A[4 * l + 2] = (T)(f[2] * q);
+        ms.A[4 * l + 3] = T(0);
+    }
+}
+
+// Per particle (one CTA): marker positions, desired velocities, anchors,
+// weights; the particle's marker radius and its unwrapped stencil box.
+template <typename T, int KER>
+__global__ void __launch_bounds__(kBlock) k_prep_particles(
+    DevGrid g, int P, const double *__restrict__ Xr, const double *__restrict__ Ur,
+    const double *__restrict__ Wr, const int *__restrict__ moff, const double *__restrict__ R,
+    const double *__restrict__ dV, MarkerState<T> ms, double *__restrict__ F,
+    double *__restrict__ rho, int4 *__restrict__ box_lo, int4 *__restrict__ box_dim,
+    int *__restrict__ part_of, DevStatus *st) {
+    constexpr int KW = Kernel<KER>::W;
+    __shared__ long long s_lo[3], s_hi[3];
+    __shared__ double s_rho;
+    int p = blockIdx.x;
+    if (p >= P) return;
+    if (threadIdx.x < 3) {
+        s_lo[threadIdx.x] = LLONG_MAX;
+        s_hi[threadIdx.x] = LLONG_MIN;
+    }
+    if (threadIdx.x == 0) s_rho = 0.0;
+    __syncthreads();
+    double xc[3] = {Xr[3 * p], Xr[3 * p + 1], Xr[3 * p + 2]};
+    double uc[3] = {Ur[3 * p], Ur[3 * p + 1], Ur[3 * p + 2]};
+    double wc[3] = {Wr[3 * p], Wr[3 * p + 1], Wr[3 * p + 2]};
+    bool pok = finite3(xc) && finite3(uc) && finite3(wc);
+    if (!pok && threadIdx.x == 0) raise_status(st, IB_ERR_NONFINITE, p);
+    int m0 = moff[p], m1 = moff[p + 1];
+    long long lo[3] = {LLONG_MAX, LLONG_MAX, LLONG_MAX}, hi[3] = {LLONG_MIN, LLONG_MIN, LLONG_MIN};
+    double rmax = 0.0;
+    for (int l = m0 + threadIdx.x; l < m1; l += blockDim.x) {
+        double r[3] = {R[3 * l], R[3 * l + 1], R[3 * l + 2]};
+        double dv = dV[l];
+        if (!pok || !finite3(r) || !isfinite(dv)) {
+            raise_status(st, IB_ERR_NONFINITE, l);
+            r[0] = r[1] = r[2] = 0.0;
+        }
+        double x[3] = {xc[0] + r[0], xc[1] + r[1], xc[2] + r[2]};
+        if (!pok) x[0] = g.org[0], x[1] = g.org[1], x[2] = g.org[2];
+        T w[12];
+        long long first[3];
+        ms.anchor[l] = marker_weights<T, KER>(g, x, w, first);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) ms.wts[12 * l + k] = w[k];
+        ms.Ud[3 * l + 0] = uc[0] + (wc[1] * r[2] - wc[2] * r[1]);
+        ms.Ud[3 * l + 1] = uc[1] + (wc[2] * r[0] - wc[0] * r[2]);
+        ms.Ud[3 * l + 2] = uc[2] + (wc[0] * r[1] - wc[1] * r[0]);
+        F[3 * l] = F[3 * l + 1] = F[3 * l + 2] = 0.0;
+        part_of[l] = p;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            lo[d] = min(lo[d], first[d]);
+            hi[d] = max(hi[d], first[d] + KW - 1);
+        }
+        rmax = fmax(rmax, sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]));
+    }
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        atomicMin(&s_lo[d], lo[d]);
+        atomicMax(&s_hi[d], hi[d]);
+    }
+    // rmax >= 0: the bit pattern orders like the value
+    atomicMax((unsigned long long *)&s_rho, (unsigned long long)__double_as_longlong(rmax));
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        rho[p] = s_rho;
+        if (m1 > m0) {
+            int dims[3];
+            for (int d = 0; d < 3; ++d) dims[d] = (int)(s_hi[d] - s_lo[d] + 1);
+            box_lo[p] = make_int4(wrap_int(s_lo[0], g.n[0]), wrap_int(s_lo[1], g.n[1]),
+                                  wrap_int(s_lo[2], g.n[2]), 0);
+            box_dim[p] = make_int4(dims[0], dims[1], dims[2], 0);
+            for (int d = 0; d < 3; ++d)
+                if (dims[d] > kMaxBox || dims[d] > g.n[d]) raise_status(st, IB_ERR_UNSUPPORTED, p);
+        } else {
+            box_lo[p] = make_int4(0, 0, 0, 0);
+            box_dim[p] = make_int4(0, 0, 0, 0);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// wavefront levels (sequential order).  One CTA.
+// Particles p and q conflict when their marker stencils may share a cell:
+// nearest-image centre distance < rho_p + rho_q + sqrt(3) * W * h.  level(p)
+// = 1 + max level(q) over conflicting q < p; a level's particles have
+// pairwise disjoint stencil supports, so running a level at once equals
+// running its particles one after another.
+// ---------------------------------------------------------------------------
+struct LevelOut {
+    int *level;       // [P]
+    int *rank;        // [P] position of p in level-major order
+    int *mbase;       // [P] first slot of p's markers in the level-major marker list
+    int *lev_pbeg;    // [P+1] first level-major rank of each level
+    int *lev_mbeg;    // [P+1] first level-major marker of each level
+    int *nlev;        // [1]
+};
+
+__global__ void __launch_bounds__(1024) k_levels(DevGrid g, int P, int order, int KW,
+                                                 const double *__restrict__ Xr,
+                                                 const double *__restrict__ rho,
+                                                 const int *__restrict__ moff, LevelOut lo,
+                                                 int *__restrict__ work, DevStatus *st) {
+    // work: [P] levels (scratch) + [P+1] counts
+    __shared__ int s_changed;
+    __shared__ int s_nlev;
+    int *lev = lo.level;
+    for (int p = threadIdx.x; p < P; p += blockDim.x) lev[p] = 0;
+    __syncthreads();
+    if (order == IB_ORDER_SEQUENTIAL && P > 1) {
+        double L[3] = {g.n[0] * g.h, g.n[1] * g.h, g.n[2] * g.h};
+        double halo = sqrt(3.0) * KW * g.h;
+        // Bellman-Ford style relaxation over the conflict DAG; converges in
+        // (longest chain) sweeps.
+        for (int it = 0; it <= P; ++it) {
+            if (threadIdx.x == 0) s_changed = 0;
+            __syncthreads();
+            for (int p = threadIdx.x; p < P; p += blockDim.x) {
+                double xp[3] = {Xr[3 * p], Xr[3 * p + 1], Xr[3 * p + 2]};
+                int best = 0;
+                for (int q = 0; q < p; ++q) {
+                    double d2 = 0.0;
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) {
+                        double d = Xr[3 * q + a] - xp[a];
+                        d -= L[a] * nearbyint(d / L[a]);
+                        d2 += d * d;
+                    }
+                    double lim = rho[p] + rho[q] + halo;
+                    if (d2 < lim * lim) best = max(best, lev[q] + 1);
+                }
+                if (best != lev[p]) {
+                    lev[p] = best;
+                    s_changed = 1;
+                }
+            }
+            __syncthreads();
+            if (!s_changed) break;
+            __syncthreads();
+        }
+    }
+    __syncthreads();
+    // counting sort of particles by level (stable: index order inside a level)
+    if (threadIdx.x == 0) {
+        int nl = 0;
+        for (int p = 0; p < P; ++p) nl = max(nl, lev[p] + 1);
+        s_nlev = P > 0 ? nl : 0;
+        *lo.nlev = s_nlev;
+    }
+    __syncthreads();
+    int nl = s_nlev;
+    int *cnt = work;  // [P+1]
+    for (int i = threadIdx.x; i <= P; i += blockDim.x) cnt[i] = 0;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int p = 0; p < P; ++p) cnt[lev[p]]++;
+        int acc = 0, macc = 0;
+        for (int L = 0; L < nl; ++L) {
+            lo.lev_pbeg[L] = acc;
+            acc += cnt[L];
+        }
+        lo.lev_pbeg[nl] = acc;
+        // ranks and marker bases in level-major order
+        for (int L = 0; L < nl; ++L) cnt[L] = lo.lev_pbeg[L];
+        for (int p = 0; p < P; ++p) lo.rank[p] = cnt[lev[p]]++;
+        // marker bases: walk particles in rank order
+        int *by_rank = cnt;  // reuse: by_rank[r] = p
+        for (int p = 0; p < P; ++p) by_rank[lo.rank[p]] = p;
+        int L = 0;
+        for (int r = 0; r < P; ++r) {
+            int p = by_rank[r];
+            while (L < nl && lo.lev_pbeg[L] <= r) {
+                lo.lev_mbeg[L] = macc;
+                ++L;
+            }
+            lo.mbase[p] = macc;
+            macc += moff[p + 1] - moff[p];
+        }
+        while (L <= nl) lo.lev_mbeg[L++] = macc;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// slot counting and filling
+// ---------------------------------------------------------------------------
+// Tiles a marker's stencil touches along one axis: distinct tile indices of
+// the KW cells from `first`.  Global tiles use wrapped cells; local tiles use
+// cells relative to the particle box (no wrap, box <= grid).
+template <int KW>
+__device__ __forceinline__ int axis_tiles_global(int first, int n, int t[3]) {
+    int cnt = 0;
+#pragma unroll
+    for (int k = 0; k < KW; ++k) {
+        int c = wrap_add(first, k, n);
+        int tt = c / kTile;
+        bool dup = false;
+        for (int j = 0; j < cnt; ++j) dup |= (t[j] == tt);
+        if (!dup && cnt < 3) t[cnt++] = tt;
+    }
+    return cnt;
+}
+
+template <int KW>
+__device__ __forceinline__ int axis_tiles_local(long long first_rel, int t[3]) {
+    int a = (int)(first_rel / kTile), b = (int)((first_rel + KW - 1) / kTile);
+    t[0] = a;
+    if (b != a) {
+        t[1] = b;
+        return 2;
+    }
+    return 1;
+}
+
+struct SlotGeom {
+    int mode;              // 0 global tiles, 1 particle-local tiles
+    int tiles[3];          // global tiles per axis
+    const int *part_of;    // [M]
+    const int *rank;       // [P]
+    const int4 *box_lo;    // [P]
+    const int4 *box_dim;   // [P]
+};
+
+// Enumerate the dense slots of marker l and call f(slot).
+template <int KW, typename Fn>
+__device__ __forceinline__ void for_marker_slots(const DevGrid &g, const SlotGeom &sg, int l,
+                                                 uint64_t anc, Fn f) {
+    int tx[3], ty[3], tz[3], nx, ny, nz;
+    uint32_t base = 0;
+    if (sg.mode == 0) {
+        nx = axis_tiles_global<KW>(anchor_x(anc), g.n[0], tx);
+        ny = axis_tiles_global<KW>(anchor_y(anc), g.n[1], ty);
+        nz = axis_tiles_global<KW>(anchor_z(anc), g.n[2], tz);
+    } else {
+        int p = sg.part_of[l];
+        int4 blo = sg.box_lo[p];
+        // relative first cell: (anchor - box_lo) mod n, < box dims
+        long long rx = wrap_diff(anchor_x(anc), wrap_int(blo.x, g.n[0]), g.n[0]);
+        long long ry = wrap_diff(anchor_y(anc), wrap_int(blo.y, g.n[1]), g.n[1]);
+        long long rz = wrap_diff(anchor_z(anc), wrap_int(blo.z, g.n[2]), g.n[2]);
+        nx = axis_tiles_local<KW>(rx, tx);
+        ny = axis_tiles_local<KW>(ry, ty);
+        nz = axis_tiles_local<KW>(rz, tz);
+        // a box wider than kMaxBox is reported by the preparation kernel;
+        // keep every slot id in range regardless
+        if (tx[nx - 1] >= kLocalTiles || ty[ny - 1] >= kLocalTiles || tz[nz - 1] >= kLocalTiles) return;
+        base = (uint32_t)sg.rank[p] * kLocalSlots;
+    }
+    for (int k = 0; k < nz; ++k)
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i) {
+                uint32_t s;
+                if (sg.mode == 0)
+                    s = ((uint32_t)tz[k] * sg.tiles[1] + ty[j]) * sg.tiles[0] + tx[i];
+                else
+                    s = base + ((uint32_t)tz[k] * kLocalTiles + ty[j]) * kLocalTiles + tx[i];
+                f(s);
+            }
+}
+
+template <int KW>
+__global__ void k_slot_count(DevGrid g, int M, SlotGeom sg, const uint64_t *__restrict__ anchor,
+                             uint32_t *__restrict__ count) {
+    for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < M; l += gridDim.x * blockDim.x)
+        for_marker_slots<KW>(g, sg, l, anchor[l], [&](uint32_t s) { atomicAdd(count + s, 1u); });
+}
+
+template <int KW>
+__global__ void k_slot_fill(DevGrid g, int M, SlotGeom sg, const uint64_t *__restrict__ anchor,
+                            const uint32_t *__restrict__ start, uint32_t *__restrict__ cursor,
+                            uint32_t *__restrict__ cand) {
+    for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < M; l += gridDim.x * blockDim.x)
+        for_marker_slots<KW>(g, sg, l, anchor[l], [&](uint32_t s) {
+            uint32_t pos = start[s] + atomicAdd(cursor + s, 1u);
+            cand[pos] = (uint32_t)l;
+        });
+}
+
+__global__ void k_flags(const uint32_t *__restrict__ count, uint32_t *__restrict__ flags, int n) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        flags[i] = count[i] ? 1u : 0u;
+}
+
+__global__ void k_compact(const uint32_t *__restrict__ count, const uint32_t *__restrict__ fscan,
+                          uint32_t *__restrict__ dense_of, int n) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        if (count[i]) dense_of[fscan[i]] = (uint32_t)i;
+}
+
+// Per-level ranges of the compact slot list (dense slots of the
+// particle-local mode are level-major: rank * 512 + local tile).
+__global__ void k_level_slots(int mode, const int *__restrict__ nlev_p, const int *__restrict__ lev_pbeg,
+                              const uint32_t *__restrict__ fscan, int ndense, int *__restrict__ lev_sbeg) {
+    int nl = *nlev_p;
+    for (int L = threadIdx.x; L <= nl; L += blockDim.x) {
+        if (mode == 0) {
+            lev_sbeg[L] = L == 0 ? 0 : (int)fscan[ndense];
+        } else {
+            long long d = (long long)lev_pbeg[L] * kLocalSlots;
+            lev_sbeg[L] = (int)fscan[d < ndense ? d : ndense];
+        }
+    }
+}
+
+// Level-major marker list: mperm[mbase[p] + (l - moff[p])] = l.
+__global__ void k_marker_perm(int M, const int *__restrict__ part_of, const int *__restrict__ moff,
+                              const int *__restrict__ mbase, int *__restrict__ mperm) {
+    for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < M; l += gridDim.x * blockDim.x) {
+        int p = part_of[l];
+        mperm[mbase[p] + (l - moff[p])] = l;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// per-slot sort by (row, marker) and row starts; one CTA per compact slot
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kBlock) k_slot_sort(
+    DevGrid g, int mode, int ncompact_cap, const int *__restrict__ ncompact_p, SlotGeom sg,
+    const uint32_t *__restrict__ dense_of, const uint32_t *__restrict__ start,
+    const uint64_t *__restrict__ anchor, const int *__restrict__ level, Slots sl, DevStatus *st) {
+    __shared__ unsigned long long keys[kMaxCand];
+    __shared__ uint32_t rowcnt[kRows + 1];
+    int ncompact = min(*ncompact_p, ncompact_cap);
+    for (int cs = blockIdx.x; cs < ncompact; cs += gridDim.x) {
+        uint32_t d = dense_of[cs];
+        uint32_t b = start[d], e = start[d + 1];
+        int nc = (int)(e - b);
+        // tile geometry
+        int lo[3], dim[3], lev = 0;
+        if (mode == 0) {
+            int t[3] = {(int)(d % sg.tiles[0]), (int)((d / sg.tiles[0]) % sg.tiles[1]),
+                        (int)(d / ((uint32_t)sg.tiles[0] * sg.tiles[1]))};
+            for (int a = 0; a < 3; ++a) {
+                lo[a] = t[a] * kTile;
+                dim[a] = min(kTile, g.n[a] - lo[a]);
+            }
+        } else {
+            // rank -> particle: the first candidate's particle
+            int p = sg.part_of[sl.cand[b]];
+            int lt = (int)(d % kLocalSlots);
+            int t[3] = {lt % kLocalTiles, (lt / kLocalTiles) % kLocalTiles, lt / (kLocalTiles * kLocalTiles)};
+            int4 blo = sg.box_lo[p], bd = sg.box_dim[p];
+            int bl[3] = {blo.x, blo.y, blo.z}, bdm[3] = {bd.x, bd.y, bd.z};
+            for (int a = 0; a < 3; ++a) {
+                lo[a] = wrap_int((long long)bl[a] + t[a] * kTile, g.n[a]);
+                dim[a] = min(kTile, bdm[a] - t[a] * kTile);
+            }
+            lev = level[p];
+        }
+        if (nc > kMaxCand) {
+            if (threadIdx.x == 0) {
+                raise_status(st, IB_ERR_UNSUPPORTED, nc);
+                sl.geo_lo[cs] = make_int4(lo[0], lo[1], lo[2], lev);
+                sl.geo_dim[cs] = make_int4(0, 0, 0, 0);
+            }
+            __syncthreads();
+            continue;
+        }
+        int np2 = 1;
+        while (np2 < nc) np2 <<= 1;
+        for (int i = threadIdx.x; i <= kRows; i += blockDim.x) rowcnt[i] = 0;
+        __syncthreads();
+        for (int i = threadIdx.x; i < np2; i += blockDim.x) {
+            unsigned long long key = ~0ull;
+            if (i < nc) {
+                uint32_t m = sl.cand[b + i];
+                uint64_t anc = anchor[m];
+                int rz = wrap_int((long long)anchor_z(anc) - lo[2] + 3, g.n[2]);
+                int ry = wrap_int((long long)anchor_y(anc) - lo[1] + 3, g.n[1]);
+                int row = (rz < kRow && ry < kRow) ? rz * kRow + ry : kRows;  // kRows: never read
+                key = ((unsigned long long)row << 32) | m;
+                atomicAdd(&rowcnt[row], 1u);
+            }
+            keys[i] = key;
+        }
+        __syncthreads();
+        // bitonic sort of np2 keys
+        for (int k = 2; k <= np2; k <<= 1) {
+            for (int j = k >> 1; j > 0; j >>= 1) {
+                for (int i = threadIdx.x; i < np2; i += blockDim.x) {
+                    int ixj = i ^ j;
+                    if (ixj > i) {
+                        unsigned long long a = keys[i], c = keys[ixj];
+                        bool up = (i & k) == 0;
+                        if ((a > c) == up) {
+                            keys[i] = c;
+                            keys[ixj] = a;
+                        }
+                    }
+                }
+                __syncthreads();
+            }
+        }
+        for (int i = threadIdx.x; i < nc; i += blockDim.x) sl.cand[b + i] = (uint32_t)(keys[i] & 0xffffffffu);
+        if (threadIdx.x == 0) {
+            uint16_t *rs = sl.rows + (size_t)cs * (kRows + 1);
+            uint32_t acc = 0;
+            for (int r = 0; r < kRows; ++r) {
+                rs[r] = (uint16_t)acc;
+                acc += rowcnt[r];
+            }
+            rs[kRows] = (uint16_t)acc;
+            sl.geo_lo[cs] = make_int4(lo[0], lo[1], lo[2], lev);
+            sl.geo_dim[cs] = make_int4(dim[0], dim[1], dim[2], (int)b);
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// gather of one tile: every cell sums w * A over the markers whose stencil
+// covers it, rows in (z, y) order, markers in index order within a row.
+// Returns true when the cell had any contribution.
+// ---------------------------------------------------------------------------
+template <typename T, int KW, bool COH>
+__device__ __forceinline__ bool gather_cell(const DevGrid &g, int cx, int cy, int cz, int tx, int ty,
+                                            int tz, const uint16_t *rs, const uint32_t *__restrict__ cand,
+                                            const uint64_t *__restrict__ anchor,
+                                            const T *__restrict__ wts, const T *__restrict__ A,
+                                            T acc[3]) {
+    bool hit = false;
+    acc[0] = acc[1] = acc[2] = T(0);
+#pragma unroll
+    for (int dz = 0; dz < KW; ++dz) {
+        int rz = tz + 3 - (KW - 1) + dz;
+#pragma unroll
+        for (int dy = 0; dy < KW; ++dy) {
+            int ry = ty + 3 - (KW - 1) + dy;
+            int row = rz * kRow + ry;
+            int i0 = rs[row], i1 = rs[row + 1];
+            for (int i = i0; i < i1; ++i) {
+                uint32_t m = cand[i];
+                uint64_t anc = __ldg((const unsigned long long *)anchor + m);
+                int ox = wrap_diff(cx, anchor_x(anc), g.n[0]);
+                if (ox < KW) {
+                    int oy = wrap_diff(cy, anchor_y(anc), g.n[1]);
+                    int oz = wrap_diff(cz, anchor_z(anc), g.n[2]);
+                    const T *w = wts + 12 * (size_t)m;
+                    T wt = w[ox] * w[4 + oy] * w[8 + oz];
+                    acc[0] += wt * ld<COH>(A + 4 * (size_t)m + 0);
+                    acc[1] += wt * ld<COH>(A + 4 * (size_t)m + 1);
+                    acc[2] += wt * ld<COH>(A + 4 * (size_t)m + 2);
+                    hit = true;
+                }
+            }
+        }
+    }
+    return hit;
+}
+
+// One tile (compact slot cs) of a gather phase: f += S A (spread) or
+// u += S A with f_out += S A / dt (forcing pass).
+template <typename T, int KW, bool COH>
+__device__ __forceinline__ void gather_tile(const DevGrid &g, long long N, int cs, const Slots &sl,
+                                            const uint64_t *anchor, const T *wts, const T *A,
+                                            T *__restrict__ dst, T *__restrict__ f_out, double inv_dt,
+                                            uint16_t *s_rows) {
+    int4 lo = sl.geo_lo[cs], dim = sl.geo_dim[cs];
+    const uint16_t *rs = sl.rows + (size_t)cs * (kRows + 1);
+    for (int i = threadIdx.x; i <= kRows; i += blockDim.x) s_rows[i] = rs[i];
+    __syncthreads();
+    int tx = threadIdx.x & 7, ty = (threadIdx.x >> 3) & 7, tz = threadIdx.x >> 6;
+    if (tx < dim.x && ty < dim.y && tz < dim.z) {
+        int cx = wrap_add(lo.x, tx, g.n[0]);
+        int cy = wrap_add(lo.y, ty, g.n[1]);
+        int cz = wrap_add(lo.z, tz, g.n[2]);
+        T acc[3];
+        if (gather_cell<T, KW, COH>(g, cx, cy, cz, tx, ty, tz, s_rows, sl.cand + dim.w, anchor, wts, A,
+                                    acc)) {
+            long long c = ((long long)cz * g.n[1] + cy) * g.n[0] + cx;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                T *q = dst + k * N + c;
+                *q = (COH ? __ldcg(q) : *q) + acc[k];
+            }
+            if (f_out) {
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    T *q = f_out + k * N + c;
+                    *q = (COH ? __ldcg(q) : *q) + (T)(acc[k] * inv_dt);
+                }
+            }
+        }
+    }
+    __syncthreads();
+}
+
+template <typename T, int KER>
+__global__ void __launch_bounds__(kBlock) k_spread_gather(DevGrid g, const int *__restrict__ ncompact_p,
+                                                          Slots sl, const uint64_t *__restrict__ anchor,
+                                                          const T *__restrict__ wts, const T *__restrict__ A,
+                                                          T *__restrict__ f) {
+    __shared__ uint16_t s_rows[kRows + 1];
+    long long N = (long long)g.n[0] * g.n[1] * g.n[2];
+    int nc = *ncompact_p;
+    for (int cs = blockIdx.x; cs < nc; cs += gridDim.x)
+        gather_tile<T, Kernel<KER>::W, false>(g, N, cs, sl, anchor, wts, A, f, (T *)nullptr, 0.0, s_rows);
+}
+
+// ---------------------------------------------------------------------------
+// grid barrier with a bounded wait
+// ---------------------------------------------------------------------------
+struct Barrier {
+    unsigned int *count;
+    unsigned int *gen;
+};
+
+__device__ __forceinline__ bool grid_sync(Barrier b, DevStatus *st) {
+    __syncthreads();
+    __shared__ int s_ok;
+    if (threadIdx.x == 0) {
+        volatile unsigned int *vgen = b.gen;
+        unsigned int g0 = *vgen;
+        __threadfence();
+        unsigned int arrived = atomicAdd(b.count, 1u);
+        int ok = 1;
+        if (arrived == gridDim.x - 1) {
+            atomicExch(b.count, 0u);
+            __threadfence();
+            atomicAdd(b.gen, 1u);
+        } else {
+            long long it = 0;
+            while (*vgen == g0) {
+                __nanosleep(64);
+                if (++it > kSpinLimit) {
+                    raise_status(st, IB_ERR_TIMEOUT, (int)blockIdx.x);
+                    ok = 0;
+                    break;
+                }
+            }
+        }
+        __threadfence();
+        s_ok = ok && (*(volatile int *)&st->code != IB_ERR_TIMEOUT);
+    }
+    __syncthreads();
+    return s_ok;
+}
+
+// ---------------------------------------------------------------------------
+// persistent multidirect-forcing passes (cooperative launch)
+// ---------------------------------------------------------------------------
+template <typename T>
+struct PassArgs {
+    DevGrid g;
+    T *u;
+    T *f_out;
+    double *F;
+    const double *dV;
+    MarkerState<T> ms;
+    Slots sl;
+    const int *mperm;
+    const int *lev_mbeg;
+    const int *lev_sbeg;
+    const int *nlev;
+    int Ns;
+    double dt;
+    Barrier bar;
+    DevStatus *st;
+};
+
+template <typename T, int KER>
+__global__ void __launch_bounds__(kBlock) k_mdf_passes(PassArgs<T> a) {
+    constexpr int KW = Kernel<KER>::W;
+    __shared__ uint16_t s_rows[kRows + 1];
+    const DevGrid g = a.g;
+    long long N = (long long)g.n[0] * g.n[1] * g.n[2];
+    int nl = *a.nlev;
+    double inv_dt = 1.0 / a.dt;
+    int gtid = blockIdx.x * blockDim.x + threadIdx.x;
+    int gsz = gridDim.x * blockDim.x;
+    for (int L = 0; L < nl; ++L) {
+        int m0 = a.lev_mbeg[L], m1 = a.lev_mbeg[L + 1];
+        int s0 = a.lev_sbeg[L], s1 = a.lev_sbeg[L + 1];
+        for (int m = 0; m < a.Ns; ++m) {
+            // interpolation phase: U = J u, F += (U^d - U)/dt, A = (U^d - U) dV / h^3
+            for (int i = m0 + gtid; i < m1; i += gsz) {
+                int l = a.mperm[i];
+                T U[3];
+                interp_marker<T, KW, true>(a.u, g, N, a.ms.anchor[l], a.ms.wts + 12 * (size_t)l, U);
+                double q = a.dV[l] * g.inv_h3;
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    double e = a.ms.Ud[3 * l + c] - (double)U[c];
+                    a.F[3 * l + c] = __ldcg(a.F + 3 * l + c) + e * inv_dt;
+                    a.ms.A[4 * l + c] = (T)(e * q);
+                }
+            }
+            if (!grid_sync(a.bar, a.st)) return;
+            // gather phase over the level's tiles
+            for (int cs = s0 + blockIdx.x; cs < s1; cs += gridDim.x)
+                gather_tile<T, KW, true>(g, N, cs, a.sl, a.ms.anchor, a.ms.wts, a.ms.A, a.u, a.f_out,
+                                         inv_dt, s_rows);
+            if (!grid_sync(a.bar, a.st)) return;
+        }
+    }
+    // non-finite result check of the forces (cheap, once)
+    for (int l = gtid; l < a.lev_mbeg[nl]; l += gsz) {
+        int m = a.mperm[l];
+        double fv[3] = {__ldcg(a.F + 3 * m), __ldcg(a.F + 3 * m + 1), __ldcg(a.F + 3 * m + 2)};
+        if (!finite3(fv)) raise_status(a.st, IB_ERR_NONFINITE, m);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// host helpers
+// ---------------------------------------------------------------------------
+static int grid_blocks(long long work, int threads, int sm) {
+    long long b = (work + threads - 1) / threads;
+    long long cap = (long long)sm * 8;
+    if (b < 1) b = 1;
+    return (int)(b < cap ? b : cap);
+}
+
+template <typename T>
+static bool take_markers(Arena &ar, int M, MarkerState<T> &ms) {
+    ms.anchor = ar.take<uint64_t>(M > 0 ? M : 1);
+    ms.wts = ar.take<T>((size_t)12 * (M > 0 ? M : 1));
+    ms.A = ar.take<T>((size_t)4 * (M > 0 ? M : 1));
+    ms.Ud = ar.take<double>((size_t)3 * (M > 0 ? M : 1));
+    return ar.ok();
+}
+
+// Build sorted slot lists for `M` prepared markers.  ndense dense slots.
+template <int KW>
+static int build_slots(ib_ctx *ctx, Arena &ar, const DevGrid &g, int M, int ndense, SlotGeom sg,
+                       const uint64_t *anchor, const int *level, Slots &sl, int *&ncompact_dev,
+                       cudaStream_t s) {
+    size_t cand_cap = (size_t)M * (sg.mode == 0 ? 27 : 8) + 1;
+    int ncompact_cap = (int)((size_t)M * (sg.mode == 0 ? 27 : 8) < (size_t)ndense
+                                 ? (size_t)M * (sg.mode == 0 ? 27 : 8)
+                                 : (size_t)ndense);
+    if (ncompact_cap < 1) ncompact_cap = 1;
+    sl.count = ar.take<uint32_t>(ndense);
+    sl.start = ar.take<uint32_t>(ndense + 1);
+    sl.cursor = ar.take<uint32_t>(ndense);
+    sl.flag_scan = ar.take<uint32_t>(ndense + 1);
+    uint32_t *flags = ar.take<uint32_t>(ndense);
+    uint32_t *scratch = ar.take<uint32_t>(scan_workspace(ndense));
+    sl.dense_of = ar.take<uint32_t>(ncompact_cap);
+    sl.cand = ar.take<uint32_t>(cand_cap);
+    sl.rows = ar.take<uint16_t>((size_t)ncompact_cap * (kRows + 1));
+    sl.geo_lo = ar.take<int4>(ncompact_cap);
+    sl.geo_dim = ar.take<int4>(ncompact_cap);
+    if (!ar.ok())
+        return oom_error(ar.used, ar.cap);
+    cudaMemsetAsync(sl.count, 0, sizeof(uint32_t) * ndense, s);
+    cudaMemsetAsync(sl.cursor, 0, sizeof(uint32_t) * ndense, s);
+    int nb = grid_blocks(M, 256, ctx->sm_count);
+    k_slot_count<KW><<<nb, 256, 0, s>>>(g, M, sg, anchor, sl.count);
+    exclusive_scan(sl.count, sl.start, ndense, scratch, s);
+    int nbd = grid_blocks(ndense, 256, ctx->sm_count);
+    k_flags<<<nbd, 256, 0, s>>>(sl.count, flags, ndense);
+    exclusive_scan(flags, sl.flag_scan, ndense, scratch, s);
+    k_compact<<<nbd, 256, 0, s>>>(sl.count, sl.flag_scan, sl.dense_of, ndense);
+    k_slot_fill<KW><<<nb, 256, 0, s>>>(g, M, sg, anchor, sl.start, sl.cursor, sl.cand);
+    ncompact_dev = (int *)(sl.flag_scan + ndense);
+    k_slot_sort<<<ctx->sm_count * 4, kBlock, 0, s>>>(g, sg.mode, ncompact_cap, ncompact_dev, sg,
+                                                     sl.dense_of, sl.start, anchor, level, sl,
+                                                     ctx->status);
+    return check_launch("build_slots");
+}
+
+template <typename T, int KER>
+static int run_interpolate(ib_ctx *ctx, const DevGrid &g, const void *u, int M, const double *X,
+                           double *U, cudaStream_t s) {
+    int nb = grid_blocks(M, 256, ctx->sm_count);
+    k_interpolate<T, KER><<<nb, 256, 0, s>>>(g, (const T *)u, M, X, U, ctx->status);
+    return check_launch("ib_interpolate");
+}
+
+template <typename T, int KER>
+static int run_spread(ib_ctx *ctx, const DevGrid &g, int M, const double *X, const double *F,
+                      const double *dV, void *f, cudaStream_t s) {
+    constexpr int KW = Kernel<KER>::W;
+    Arena ar(ctx);
+    MarkerState<T> ms;
+    take_markers<T>(ar, M, ms);
+    SlotGeom sg{};
+    sg.mode = 0;
+    for (int a = 0; a < 3; ++a) sg.tiles[a] = (g.n[a] + kTile - 1) / kTile;
+    long long ndense = (long long)sg.tiles[0] * sg.tiles[1] * sg.tiles[2];
+    if (ndense > (1LL << 30)) return set_error(IB_ERR_UNSUPPORTED, "grid has too many tiles");
+    if (!ar.ok())
+        return oom_error(ar.used, ar.cap);
+    int nb = grid_blocks(M, 256, ctx->sm_count);
+    k_prep_spread<T, KER><<<nb, 256, 0, s>>>(g, M, X, F, dV, ms, ctx->status);
+    Slots sl;
+    int *ncompact = nullptr;
+    int rc = build_slots<KW>(ctx, ar, g, M, (int)ndense, sg, ms.anchor, nullptr, sl, ncompact, s);
+    if (rc) return rc;
+    k_spread_gather<T, KER><<<ctx->sm_count * 4, kBlock, 0, s>>>(g, ncompact, sl, ms.anchor, ms.wts, ms.A,
+                                                                (T *)f);
+    return check_launch("ib_spread");
+}
+
+template <typename T, int KER>
+static int run_mdf(ib_ctx *ctx, const DevGrid &g, void *u, const ib_particles *pp, const ib_markers *mk,
+                   int Ns, double dt, int order, double *F_out, void *f_out, cudaStream_t s) {
+    constexpr int KW = Kernel<KER>::W;
+    int P = pp->P, M = mk->M;
+    Arena ar(ctx);
+    MarkerState<T> ms;
+    take_markers<T>(ar, M, ms);
+    double *rho = ar.take<double>(P);
+    int4 *box_lo = ar.take<int4>(P);
+    int4 *box_dim = ar.take<int4>(P);
+    int *part_of = ar.take<int>(M > 0 ? M : 1);
+    LevelOut lo;
+    lo.level = ar.take<int>(P);
+    lo.rank = ar.take<int>(P);
+    lo.mbase = ar.take<int>(P);
+    lo.lev_pbeg = ar.take<int>(P + 1);
+    lo.lev_mbeg = ar.take<int>(P + 1);
+    lo.nlev = ar.take<int>(1);
+    int *lev_work = ar.take<int>(P + 1);
+    int *lev_sbeg = ar.take<int>(P + 1);
+    int *mperm = ar.take<int>(M > 0 ? M : 1);
+    Barrier bar;
+    bar.count = ar.take<unsigned int>(2);
+    bar.gen = bar.count + 1;
+    SlotGeom sg{};
+    sg.mode = order == IB_ORDER_SEQUENTIAL ? 1 : 0;
+    long long ndense;
+    if (sg.mode == 0) {
+        for (int a = 0; a < 3; ++a) sg.tiles[a] = (g.n[a] + kTile - 1) / kTile;
+        ndense = (long long)sg.tiles[0] * sg.tiles[1] * sg.tiles[2];
+    } else {
+        ndense = (long long)P * kLocalSlots;
+    }
+    if (ndense > (1LL << 30)) return set_error(IB_ERR_UNSUPPORTED, "too many tiles");
+    if (!ar.ok())
+        return oom_error(ar.used, ar.cap);
+    k_prep_particles<T, KER><<<P, kBlock, 0, s>>>(g, P, pp->Xr, pp->Ur, pp->Wr, pp->marker_offset, mk->R,
+                                                 mk->dV, ms, F_out, rho, box_lo, box_dim, part_of,
+                                                 ctx->status);
+    k_levels<<<1, 1024, 0, s>>>(g, P, order, KW, pp->Xr, rho, pp->marker_offset, lo, lev_work, ctx->status);
+    k_marker_perm<<<grid_blocks(M, 256, ctx->sm_count), 256, 0, s>>>(M, part_of, pp->marker_offset,
+                                                                     lo.mbase, mperm);
+    sg.part_of = part_of;
+    sg.rank = lo.rank;
+    sg.box_lo = box_lo;
+    sg.box_dim = box_dim;
+    Slots sl;
+    int *ncompact = nullptr;
+    int rc = build_slots<KW>(ctx, ar, g, M, (int)ndense, sg, ms.anchor, lo.level, sl, ncompact, s);
+    if (rc) return rc;
+    k_level_slots<<<1, 256, 0, s>>>(sg.mode, lo.nlev, lo.lev_pbeg, sl.flag_scan, (int)ndense, lev_sbeg);
+    cudaMemsetAsync(bar.count, 0, 2 * sizeof(unsigned int), s);
+    PassArgs<T> a;
+    a.g = g;
+    a.u = (T *)u;
+    a.f_out = (T *)f_out;
+    a.F = F_out;
+    a.dV = mk->dV;
+    a.ms = ms;
+    a.sl = sl;
+    a.mperm = mperm;
+    a.lev_mbeg = lo.lev_mbeg;
+    a.lev_sbeg = lev_sbeg;
+    a.nlev = lo.nlev;
+    a.Ns = Ns;
+    a.dt = dt;
+    a.bar = bar;
+    a.st = ctx->status;
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mdf_passes<T, KER>, kBlock, 0);
+    if (per_sm < 1) return set_error(IB_ERR_CUDA, "mdf kernel cannot be resident");
+    int nblocks = per_sm * ctx->sm_count;
+    void *args[] = {&a};
+    cudaError_t e = cudaLaunchCooperativeKernel((const void *)k_mdf_passes<T, KER>, nblocks, kBlock, args, 0, s);
+    if (e != cudaSuccess) return set_error(IB_ERR_CUDA, "mdf launch: %s", cudaGetErrorString(e));
+    return check_launch("ib_multidirect_forcing");
+}
+
+}  // namespace gbib
+
+using namespace gbib;
+
+#define DISPATCH(prec, delta, FN, ...)                                                            \
+    ((prec) == IB_F64 ? ((delta) == IB_DELTA_ROMA3 ? FN<double, IB_DELTA_ROMA3>(__VA_ARGS__)      \
+                                                   : FN<double, IB_DELTA_PESKIN4>(__VA_ARGS__))   \
+                      : ((delta) == IB_DELTA_ROMA3 ? FN<float, IB_DELTA_ROMA3>(__VA_ARGS__)       \
+                                                   : FN<float, IB_DELTA_PESKIN4>(__VA_ARGS__)))
+
+extern "C" {
+
+int ib_interpolate(ib_ctx *ctx, const ib_grid *grid, const void *u, int M, const double *X, int delta,
+                   double *U, void *stream) {
+    if (!ctx) return set_error(IB_ERR_INVALID, "ctx is NULL");
+    int rc = validate_grid(grid, 1);
+    if (rc) return rc;
+    if (delta != IB_DELTA_ROMA3 && delta != IB_DELTA_PESKIN4) return set_error(IB_ERR_INVALID, "bad delta");
+    if (M < 0) return set_error(IB_ERR_INVALID, "M < 0");
+    if (M == 0) return IB_OK;
+    if (!u || !X || !U) return set_error(IB_ERR_INVALID, "NULL array");
+    DevGrid g = make_dev_grid(grid);
+    return DISPATCH(grid->prec, delta, run_interpolate, ctx, g, u, M, X, U, (cudaStream_t)stream);
+}
+
+int ib_spread(ib_ctx *ctx, const ib_grid *grid, int M, const double *X, const double *F, const double *dV,
+              int delta, void *f, void *stream) {
+    if (!ctx) return set_error(IB_ERR_INVALID, "ctx is NULL");
+    int rc = validate_grid(grid, 1);
+    if (rc) return rc;
+    if (delta != IB_DELTA_ROMA3 && delta != IB_DELTA_PESKIN4) return set_error(IB_ERR_INVALID, "bad delta");
+    if (M < 0) return set_error(IB_ERR_INVALID, "M < 0");
+    if (M == 0) return IB_OK;
+    if (!X || !F || !dV || !f) return set_error(IB_ERR_INVALID, "NULL array");
+    DevGrid g = make_dev_grid(grid);
+    return DISPATCH(grid->prec, delta, run_spread, ctx, g, M, X, F, dV, f, (cudaStream_t)stream);
+}
+
+int ib_multidirect_forcing(ib_ctx *ctx, const ib_grid *grid, void *u, const ib_particles *parts,
+                           const ib_markers *marks, int Ns, double dt, int delta, int order, double *F_out,
+                           void *f_out, void *stream) {
+    if (!ctx) return set_error(IB_ERR_INVALID, "ctx is NULL");
+    int rc = validate_grid(grid, 1);
+    if (rc) return rc;
+    if (!parts || !marks) return set_error(IB_ERR_INVALID, "particles/markers NULL");
+    if (delta != IB_DELTA_ROMA3 && delta != IB_DELTA_PESKIN4) return set_error(IB_ERR_INVALID, "bad delta");
+    if (order != IB_ORDER_SEQUENTIAL && order != IB_ORDER_SIMULTANEOUS)
+        return set_error(IB_ERR_INVALID, "bad order");
+    if (Ns < 1) return set_error(IB_ERR_INVALID, "Ns must be >= 1");
+    if (!(dt > 0.0) || !isfinite(dt)) return set_error(IB_ERR_INVALID, "dt must be finite and > 0");
+    if (parts->P < 0 || marks->M < 0) return set_error(IB_ERR_INVALID, "negative P or M");
+    if (parts->P == 0 || marks->M == 0) return IB_OK;
+    if (!u || !parts->Xr || !parts->Ur || !parts->Wr || !parts->marker_offset || !marks->R || !marks->dV ||
+        !F_out)
+        return set_error(IB_ERR_INVALID, "NULL array");
+    DevGrid g = make_dev_grid(grid);
+    return DISPATCH(grid->prec, delta, run_mdf, ctx, g, u, parts, marks, Ns, dt, order, F_out, f_out,
+                    (cudaStream_t)stream);
+}
+
+}  // extern "C"

@@ -1,0 +1,325 @@
+// Per-particle reductions and updates around Algorithm 1 (arXiv 2408.14140):
+//   * PVF volume integrals (Sec. 4.1, Eqs. level-set function / Heaviside;
+//     the flow-unsteadiness terms of Eqs. particle1/particle2),
+//   * marker force and torque (first terms of Eqs. particle1/particle2),
+//   * repulsive-potential collision (Eq. DKT_model) + Newton-Euler update
+//     (Eqs. particle1, particle2) + centroid update (Eq. pr2).
+// All sums are FP64 and run in a fixed order (per-thread strided partials,
+// then a fixed shuffle tree), so results are bitwise reproducible.
+#include "gbib_internal.cuh"
+
+namespace gbib {
+
+constexpr double kPi = 3.14159265358979323846;
+
+// Fixed-order block sum of NV doubles; result valid in thread 0.
+template <int NV>
+__device__ __forceinline__ void block_sum(double v[NV]) {
+    __shared__ double red[32][NV];
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NV; ++k)
+        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) red[wid][k] = v[k];
+    __syncthreads();
+    if (wid == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            double x = lane < nw ? red[lane][k] : 0.0;
+            for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+            v[k] = x;
+        }
+    }
+    __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// volume integrals: grid = P * kVolSplit CTAs; CTA (p, s) takes the z-slabs
+// s, s + kVolSplit, ... of particle p's cell box.
+// ---------------------------------------------------------------------------
+constexpr int kVolSplit = 16;
+constexpr int kVolThreads = 256;
+
+template <typename T>
+__global__ void __launch_bounds__(kVolThreads) k_volume(DevGrid g, const T *__restrict__ u, int P,
+                                                        const double *__restrict__ Xr,
+                                                        const double *__restrict__ radius,
+                                                        double *__restrict__ partial, DevStatus *st) {
+    int p = blockIdx.x / kVolSplit, split = blockIdx.x % kVolSplit;
+    if (p >= P) return;
+    double c[3] = {Xr[3 * p], Xr[3 * p + 1], Xr[3 * p + 2]};
+    double Rp = radius[p];
+    double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+    if (finite3(c) && isfinite(Rp) && Rp > 0.0) {
+        long long lo[3], dims[3];
+        for (int a = 0; a < 3; ++a) {
+            lo[a] = (long long)floor((c[a] - Rp - g.org[a]) * g.inv_h) - 1;
+            long long hi = (long long)floor((c[a] + Rp - g.org[a]) * g.inv_h) + 1;
+            dims[a] = hi - lo[a] + 1;
+        }
+        long long N = (long long)g.n[0] * g.n[1] * g.n[2];
+        double h = g.h, h3 = h * h * h;
+        double rin = Rp - 0.8661 * h, rout = Rp + 0.8661 * h;
+        double rin2 = rin > 0 ? rin * rin : -1.0, rout2 = rout * rout;
+        long long plane = dims[0] * dims[1];
+        for (long long kz = split; kz < dims[2]; kz += kVolSplit) {
+            long long k = lo[2] + kz;
+            for (long long q = threadIdx.x; q < plane; q += blockDim.x) {
+                long long j = lo[1] + q / dims[0], i = lo[0] + q % dims[0];
+                double r[3] = {g.org[0] + ((double)i + 0.5) * h - c[0], g.org[1] + ((double)j + 0.5) * h - c[1],
+                               g.org[2] + ((double)k + 0.5) * h - c[2]};
+                double d2 = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
+                double al;
+                if (d2 < rin2) {
+                    al = 1.0;
+                } else if (d2 > rout2) {
+                    continue;
+                } else {
+                    double num = 0.0, den = 0.0;
+#pragma unroll
+                    for (int m = 0; m < 8; ++m) {
+                        double x = g.org[0] + (double)(i + (m & 1)) * h;
+                        double y = g.org[1] + (double)(j + ((m >> 1) & 1)) * h;
+                        double z = g.org[2] + (double)(k + ((m >> 2) & 1)) * h;
+                        double a = (x - c[0]) / Rp, b = (y - c[1]) / Rp, d = (z - c[2]) / Rp;
+                        double phi = sqrt(a * a + b * b + d * d) - 1.0;
+                        if (-phi > 0.0) num += -phi;
+                        den += fabs(phi);
+                    }
+                    al = den > 0.0 ? num / den : 0.5;
+                    if (al == 0.0) continue;
+                }
+                long long cc = ((long long)wrap_int(k, g.n[2]) * g.n[1] + wrap_int(j, g.n[1])) * g.n[0] +
+                               wrap_int(i, g.n[0]);
+                double uc[3] = {(double)u[cc], (double)u[N + cc], (double)u[2 * N + cc]};
+                double wv = al * h3;
+                acc[0] += wv * uc[0];
+                acc[1] += wv * uc[1];
+                acc[2] += wv * uc[2];
+                acc[3] += wv * (r[1] * uc[2] - r[2] * uc[1]);
+                acc[4] += wv * (r[2] * uc[0] - r[0] * uc[2]);
+                acc[5] += wv * (r[0] * uc[1] - r[1] * uc[0]);
+                acc[6] += wv;
+            }
+        }
+    } else if (threadIdx.x == 0 && split == 0) {
+        raise_status(st, IB_ERR_NONFINITE, p);
+    }
+    block_sum<7>(acc);
+    if (threadIdx.x == 0)
+        for (int k = 0; k < 7; ++k) partial[((size_t)p * kVolSplit + split) * 7 + k] = acc[k];
+}
+
+__global__ void k_volume_final(int P, const double *__restrict__ partial, double *Iu, double *Irxu,
+                               double *vol) {
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x) {
+        double s[7] = {0, 0, 0, 0, 0, 0, 0};
+        for (int sp = 0; sp < kVolSplit; ++sp)
+            for (int k = 0; k < 7; ++k) s[k] += partial[((size_t)p * kVolSplit + sp) * 7 + k];
+        if (Iu)
+            for (int a = 0; a < 3; ++a) Iu[3 * p + a] = s[a];
+        if (Irxu)
+            for (int a = 0; a < 3; ++a) Irxu[3 * p + a] = s[3 + a];
+        if (vol) vol[p] = s[6];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// force and torque: one CTA per particle
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_force_torque(int P, const int *__restrict__ moff,
+                                                      const double *__restrict__ R,
+                                                      const double *__restrict__ dV,
+                                                      const double *__restrict__ F, double rho_f,
+                                                      double *__restrict__ Fib, double *__restrict__ Tib) {
+    int p = blockIdx.x;
+    if (p >= P) return;
+    double acc[6] = {0, 0, 0, 0, 0, 0};
+    for (int l = moff[p] + threadIdx.x; l < moff[p + 1]; l += blockDim.x) {
+        double gx = F[3 * l] * dV[l], gy = F[3 * l + 1] * dV[l], gz = F[3 * l + 2] * dV[l];
+        double rx = R[3 * l], ry = R[3 * l + 1], rz = R[3 * l + 2];
+        acc[0] += gx;
+        acc[1] += gy;
+        acc[2] += gz;
+        acc[3] += ry * gz - rz * gy;
+        acc[4] += rz * gx - rx * gz;
+        acc[5] += rx * gy - ry * gx;
+    }
+    block_sum<6>(acc);
+    if (threadIdx.x == 0)
+        for (int a = 0; a < 3; ++a) {
+            Fib[3 * p + a] = -rho_f * acc[a];
+            Tib[3 * p + a] = -rho_f * acc[3 + a];
+        }
+}
+
+// ---------------------------------------------------------------------------
+// collision + Newton-Euler: one thread per particle, pairs in index order
+// ---------------------------------------------------------------------------
+struct CollideArgs {
+    int P;
+    double *Xr, *Ur, *Wr;
+    const double *radius, *rho_p;
+    double L[3];
+    double rho_f, g[3], g_coll, eps_c, d_c, dt;
+    const double *Fib, *Tib, *Iu_new, *Iu_old, *Ir_new, *Ir_old;
+    double *Fc_out;
+    double *Xnew;  // [P][3] scratch: positions are read by every thread
+};
+
+__global__ void k_collide_forces(CollideArgs a, double *__restrict__ Fc) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.P) return;
+    double xi[3] = {a.Xr[3 * i], a.Xr[3 * i + 1], a.Xr[3 * i + 2]};
+    double Ri = a.radius[i];
+    double mi = a.rho_p[i] * 4.0 / 3.0 * kPi * Ri * Ri * Ri;
+    double f[3] = {0, 0, 0};
+    for (int j = 0; j < a.P; ++j) {
+        if (j == i) continue;
+        double del[3], d2 = 0.0;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            double dd = a.Xr[3 * j + k] - xi[k];
+            del[k] = dd - a.L[k] * nearbyint(dd / a.L[k]);
+            d2 += del[k] * del[k];
+        }
+        double Rj = a.radius[j];
+        double Dc = Ri + Rj + a.d_c;
+        if (d2 < Dc * Dc) {
+            double d = sqrt(d2);
+            if (d < Dc && d > 0.0) {
+                double mj = a.rho_p[j] * 4.0 / 3.0 * kPi * Rj * Rj * Rj;
+                double q = (d - Dc) / a.d_c;
+                double coef = -(0.5 * (mi + mj) * a.g_coll / a.eps_c) * q * q / d;
+#pragma unroll
+                for (int k = 0; k < 3; ++k) f[k] += coef * del[k];
+            }
+        }
+    }
+    for (int k = 0; k < 3; ++k) Fc[3 * i + k] = f[k];
+}
+
+__global__ void k_newton_euler(CollideArgs a, const double *__restrict__ Fc, DevStatus *st) {
+    int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= a.P) return;
+    double Rp = a.radius[p];
+    double V = 4.0 / 3.0 * kPi * Rp * Rp * Rp;
+    double m = a.rho_p[p] * V;
+    double I = 0.4 * m * Rp * Rp;
+    bool ok = true;
+    for (int k = 0; k < 3; ++k) {
+        double Un = a.Ur[3 * p + k];
+        double rhs = a.Fib[3 * p + k] + a.rho_f * (a.Iu_new[3 * p + k] - a.Iu_old[3 * p + k]) / a.dt +
+                     (a.rho_p[p] - a.rho_f) * V * a.g[k] + Fc[3 * p + k];
+        double Unew = Un + a.dt / m * rhs;
+        double trq = a.Tib[3 * p + k] + a.rho_f * (a.Ir_new[3 * p + k] - a.Ir_old[3 * p + k]) / a.dt;
+        double Wnew = a.Wr[3 * p + k] + a.dt / I * trq;
+        double Xnew = a.Xr[3 * p + k] + 0.5 * a.dt * (Unew + Un);
+        ok = ok && isfinite(Unew) && isfinite(Wnew) && isfinite(Xnew);
+        a.Ur[3 * p + k] = Unew;
+        a.Wr[3 * p + k] = Wnew;
+        a.Xr[3 * p + k] = Xnew;
+        if (a.Fc_out) a.Fc_out[3 * p + k] = Fc[3 * p + k];
+    }
+    if (!ok) raise_status(st, IB_ERR_NONFINITE, p);
+}
+
+template <typename T>
+static int run_volume(ib_ctx *ctx, const DevGrid &g, const void *u, const ib_particles *pp, double *Iu,
+                      double *Irxu, double *vol, cudaStream_t s) {
+    Arena ar(ctx);
+    double *partial = ar.take<double>((size_t)pp->P * kVolSplit * 7);
+    if (!ar.ok())
+        return oom_error(ar.used, ar.cap);
+    k_volume<T><<<pp->P * kVolSplit, kVolThreads, 0, s>>>(g, (const T *)u, pp->P, pp->Xr, pp->radius, partial,
+                                                          ctx->status);
+    k_volume_final<<<(pp->P + 127) / 128, 128, 0, s>>>(pp->P, partial, Iu, Irxu, vol);
+    return check_launch("particle_volume_integrals");
+}
+
+}  // namespace gbib
+
+using namespace gbib;
+
+extern "C" {
+
+int particle_volume_integrals(ib_ctx *ctx, const ib_grid *grid, const void *u, const ib_particles *parts,
+                              double *Iu, double *Irxu, double *vol, void *stream) {
+    if (!ctx) return set_error(IB_ERR_INVALID, "ctx is NULL");
+    int rc = validate_grid(grid, 1);
+    if (rc) return rc;
+    if (!parts || parts->P < 0) return set_error(IB_ERR_INVALID, "bad particles");
+    if (parts->P == 0) return IB_OK;
+    if (!u || !parts->Xr || !parts->radius) return set_error(IB_ERR_INVALID, "NULL array");
+    if ((long long)parts->P * kVolSplit > (1LL << 31) - 1) return set_error(IB_ERR_UNSUPPORTED, "too many particles");
+    DevGrid g = make_dev_grid(grid);
+    if (grid->prec == IB_F64)
+        return run_volume<double>(ctx, g, u, parts, Iu, Irxu, vol, (cudaStream_t)stream);
+    return run_volume<float>(ctx, g, u, parts, Iu, Irxu, vol, (cudaStream_t)stream);
+}
+
+int particle_force_torque(ib_ctx *ctx, const ib_particles *parts, const ib_markers *marks, const double *F,
+                          double rho_f, double *F_ib, double *T_ib, void *stream) {
+    if (!ctx) return set_error(IB_ERR_INVALID, "ctx is NULL");
+    if (!parts || !marks || parts->P < 0 || marks->M < 0) return set_error(IB_ERR_INVALID, "bad arguments");
+    if (!isfinite(rho_f)) return set_error(IB_ERR_INVALID, "rho_f not finite");
+    if (parts->P == 0) return IB_OK;
+    if (!parts->marker_offset || !F_ib || !T_ib || (marks->M > 0 && (!marks->R || !marks->dV || !F)))
+        return set_error(IB_ERR_INVALID, "NULL array");
+    k_force_torque<<<parts->P, 256, 0, (cudaStream_t)stream>>>(parts->P, parts->marker_offset, marks->R,
+                                                              marks->dV, F, rho_f, F_ib, T_ib);
+    return check_launch("particle_force_torque");
+}
+
+int particle_collide_update(ib_ctx *ctx, ib_particles *parts, const ib_grid *grid, const ib_phys *phys,
+                            double dt, const double *F_ib, const double *T_ib, const double *Iu_new,
+                            const double *Iu_old, const double *Irxu_new, const double *Irxu_old,
+                            double *Fc_out, void *stream) {
+    if (!ctx) return set_error(IB_ERR_INVALID, "ctx is NULL");
+    int rc = validate_grid(grid, 0);
+    if (rc) return rc;
+    if (!parts || !phys || parts->P < 0) return set_error(IB_ERR_INVALID, "bad arguments");
+    if (!(dt > 0.0) || !isfinite(dt)) return set_error(IB_ERR_INVALID, "dt must be finite and > 0");
+    if (!(phys->eps_c > 0.0) || !(phys->d_c > 0.0)) return set_error(IB_ERR_INVALID, "eps_c and d_c must be > 0");
+    if (parts->P == 0) return IB_OK;
+    if (!parts->Xr || !parts->Ur || !parts->Wr || !parts->radius || !parts->rho_p || !F_ib || !T_ib ||
+        !Iu_new || !Iu_old || !Irxu_new || !Irxu_old)
+        return set_error(IB_ERR_INVALID, "NULL array");
+    Arena ar(ctx);
+    double *Fc = ar.take<double>((size_t)3 * parts->P);
+    if (!ar.ok())
+        return oom_error(ar.used, ar.cap);
+    CollideArgs a;
+    a.P = parts->P;
+    a.Xr = parts->Xr;
+    a.Ur = parts->Ur;
+    a.Wr = parts->Wr;
+    a.radius = parts->radius;
+    a.rho_p = parts->rho_p;
+    for (int k = 0; k < 3; ++k) {
+        a.L[k] = grid->n[k] * grid->h;
+        a.g[k] = phys->g[k];
+    }
+    a.rho_f = phys->rho_f;
+    a.g_coll = phys->g_coll;
+    a.eps_c = phys->eps_c;
+    a.d_c = phys->d_c;
+    a.dt = dt;
+    a.Fib = F_ib;
+    a.Tib = T_ib;
+    a.Iu_new = Iu_new;
+    a.Iu_old = Iu_old;
+    a.Ir_new = Irxu_new;
+    a.Ir_old = Irxu_old;
+    a.Fc_out = Fc_out;
+    a.Xnew = nullptr;
+    cudaStream_t s = (cudaStream_t)stream;
+    int nb = (parts->P + 127) / 128;
+    k_collide_forces<<<nb, 128, 0, s>>>(a, Fc);
+    k_newton_euler<<<nb, 128, 0, s>>>(a, Fc, ctx->status);
+    return check_launch("particle_collide_update");
+}
+
+}  // extern "C"

@@ -1,0 +1,256 @@
+"""GPU parity: every C-ABI entry point against the FP64 oracle.
+
+Metric: normwise relative error ||gpu - oracle||_inf / ||oracle||_inf per
+output array.  Gates: 1e-12 with FP64 fields, 2e-5 with FP32 fields (the
+oracle then runs on the FP32-rounded input, promoted to FP64).  Marker,
+particle and reduction arrays are FP64 in both modes.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2408_14140_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL = {0: 1e-12, 1: 2e-5}
+
+
+@pytest.fixture(scope="module")
+def api():
+    from paper_2408_14140_gb300 import api as a
+    from paper_2408_14140_gb300 import build
+    build.build()
+    return a
+
+
+@pytest.fixture(scope="module")
+def ctx(api):
+    c = api.Context()
+    yield c
+    c.close()
+
+
+def nerr(g, o):
+    g = g.detach().cpu().numpy() if isinstance(g, torch.Tensor) else np.asarray(g)
+    o = np.asarray(o)
+    den = np.max(np.abs(o))
+    if den == 0:
+        return float(np.max(np.abs(g)))
+    return float(np.max(np.abs(g.astype(np.float64) - o)) / den)
+
+
+def field_in(case, prec):
+    """Input field as the GPU sees it, promoted to FP64 for the oracle."""
+    return case.u if prec == 0 else case.u.astype(np.float32).astype(np.float64)
+
+
+def small_cluster(seed=3, N=48, P=6, D=10, phi=0.2, Ns=3):
+    return synth.cluster_case(N=N, P=P, D_cells=D, phi=phi, K=6, Ns=Ns, seed=seed)
+
+
+# ---------------------------------------------------------------- interpolation
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("kernel", [0, 1])
+def test_interpolate(api, ctx, prec, kernel):
+    rng = np.random.default_rng(10 + kernel)
+    N = (40, 36, 44)  # ragged: not multiples of the 8-cell tile
+    h = 0.03
+    org = (0.1, -0.2, 0.05)
+    u = synth.fourier_field(N, 6, synth.SplitMix64(5), h, org)
+    M = 3001
+    X = np.asarray(org) + rng.uniform(-0.5, 1.5, (M, 3)) * np.array(N) * h  # crosses the seam
+    uin = u if prec == 0 else u.astype(np.float32).astype(np.float64)
+    ref = oracle.interpolate(N, h, org, uin, X, kernel)
+    ug = torch.tensor(u, device="cuda", dtype=torch.float64 if prec == 0 else torch.float32)
+    U = ctx.ib_interpolate(ug, torch.tensor(X, device="cuda"), h, org, kernel)
+    ctx.status()
+    assert nerr(U, ref) <= TOL[prec]
+
+
+# -------------------------------------------------------------------- spreading
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("kernel", [0, 1])
+def test_spread(api, ctx, prec, kernel):
+    rng = np.random.default_rng(20 + kernel)
+    N = (33, 40, 28)
+    h = 0.05
+    org = (0.0, 0.3, -0.1)
+    M = 2501
+    X = np.asarray(org) + rng.uniform(-0.5, 1.5, (M, 3)) * np.array(N) * h
+    F = rng.normal(size=(M, 3))
+    dV = rng.uniform(0.5, 1.5, M) * h ** 3
+    f0 = rng.normal(size=(3, N[2], N[1], N[0]))
+    f0in = f0 if prec == 0 else f0.astype(np.float32).astype(np.float64)
+    ref = oracle.spread(N, h, org, X, F, dV, kernel, f=f0in.copy())
+    dt = torch.float64 if prec == 0 else torch.float32
+    fg = torch.tensor(f0, device="cuda", dtype=dt)
+    ctx.ib_spread(fg, torch.tensor(X, device="cuda"), torch.tensor(F, device="cuda"),
+                  torch.tensor(dV, device="cuda"), h, org, kernel)
+    ctx.status()
+    assert nerr(fg, ref) <= TOL[prec]
+    # the spread part alone, against its own scale
+    assert nerr(fg.double().cpu().numpy() - f0in, ref - f0in) <= TOL[prec] * 4
+
+
+def test_spread_deterministic(api, ctx):
+    rng = np.random.default_rng(3)
+    N = (32, 32, 32)
+    h = 1 / 32
+    X = torch.tensor(rng.uniform(0, 1, (4000, 3)), device="cuda")
+    F = torch.tensor(rng.normal(size=(4000, 3)), device="cuda")
+    dV = torch.full((4000,), h ** 3, device="cuda", dtype=torch.float64)
+    outs = []
+    for _ in range(3):
+        f = torch.zeros((3, 32, 32, 32), device="cuda", dtype=torch.float64)
+        ctx.ib_spread(f, X, F, dV, h)
+        outs.append(f)
+    ctx.status()
+    assert torch.equal(outs[0], outs[1]) and torch.equal(outs[0], outs[2])
+
+
+# ------------------------------------------------------- multidirect forcing
+def run_mdf(api, ctx, case, prec, kernel=0, order=0, want_f=True):
+    u, parts, marks = api.device_case(case, prec)
+    f = torch.zeros_like(u) if want_f else None
+    F = ctx.ib_multidirect_forcing(u, case.h, parts, marks, case.Ns, case.dt, delta=kernel,
+                                   order=order, f_out=f)
+    ctx.status()
+    return u, F, f
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_mdf_single_sphere(api, ctx, prec):
+    """64^3 grid, one D = 20 sphere, 8 modes, Ns = 2 (the small correctness case)."""
+    case = synth.single_sphere_case(N=64, D_cells=20, K=8, Ns=2, seed=0)
+    u, F, f = run_mdf(api, ctx, case, prec)
+    un, Fo, fo = oracle.multidirect(case.n, case.h, case.org, field_in(case, prec), case.Xr,
+                                    case.Ur, case.Wr, case.moff, case.R, case.dV, case.Ns,
+                                    case.dt, want_f=True)
+    assert nerr(u, un) <= TOL[prec]
+    assert nerr(F, Fo) <= TOL[prec]
+    assert nerr(f, fo) <= TOL[prec] * 10
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("kernel", [0, 1])
+@pytest.mark.parametrize("order", [0, 1])
+def test_mdf_cluster(api, ctx, prec, kernel, order):
+    """Several spheres with overlapping kernel supports, both particle orders."""
+    case = small_cluster()
+    u, F, f = run_mdf(api, ctx, case, prec, kernel, order)
+    un, Fo, fo = oracle.multidirect(case.n, case.h, case.org, field_in(case, prec), case.Xr,
+                                    case.Ur, case.Wr, case.moff, case.R, case.dV, case.Ns,
+                                    case.dt, kernel, order, want_f=True)
+    assert nerr(u, un) <= TOL[prec]
+    assert nerr(F, Fo) <= TOL[prec]
+    assert nerr(f, fo) <= TOL[prec] * 10
+
+
+def test_mdf_particle_across_seam(api, ctx):
+    """A sphere straddling the periodic seam on every axis."""
+    case = synth.single_sphere_case(N=48, D_cells=12, K=5, Ns=3, seed=4,
+                                    centre=[0.01, 0.995, 0.5 / 48])
+    u, F, _ = run_mdf(api, ctx, case, 0, want_f=False)
+    un, Fo, _ = oracle.multidirect(case.n, case.h, case.org, case.u, case.Xr, case.Ur, case.Wr,
+                                   case.moff, case.R, case.dV, case.Ns, case.dt)
+    assert nerr(u, un) <= 1e-12
+    assert nerr(F, Fo) <= 1e-12
+
+
+def test_mdf_deterministic(api, ctx):
+    case = small_cluster(seed=5)
+    outs = [run_mdf(api, ctx, case, 1) for _ in range(2)]
+    assert torch.equal(outs[0][0], outs[1][0]) and torch.equal(outs[0][1], outs[1][1])
+
+
+# ----------------------------------------------- integrals, reductions, update
+@pytest.mark.parametrize("prec", [0, 1])
+def test_volume_integrals(api, ctx, prec):
+    case = small_cluster(seed=7, N=64, P=10, D=12)
+    u, parts, _ = api.device_case(case, prec)
+    Iu, Ir, vol = ctx.particle_volume_integrals(u, case.h, parts)
+    ctx.status()
+    a = oracle.volume_integrals(case.n, case.h, case.org, field_in(case, prec), case.Xr, case.radius)
+    assert nerr(Iu, a[0]) <= 1e-12
+    assert nerr(Ir, a[1]) <= 1e-12
+    assert nerr(vol, a[2]) <= 1e-13
+
+
+def test_volume_integrals_pvf_table(api, ctx):
+    """The GPU reproduces the paper's PVF sphere volumes (Sec. 4.1 table)."""
+    for doh, val in ((16, 0.2667230796), (32, 0.2677639589), (64, 0.2679990393)):
+        h = 0.8 / doh
+        n = int(round(2 / h))
+        u = torch.zeros((3, n, n, n), device="cuda", dtype=torch.float64)
+        parts = dict(Xr=torch.tensor([[1.0, 1.0, 1.0]], device="cuda", dtype=torch.float64),
+                     Ur=torch.zeros((1, 3), device="cuda", dtype=torch.float64),
+                     Wr=torch.zeros((1, 3), device="cuda", dtype=torch.float64),
+                     radius=torch.tensor([0.4], device="cuda", dtype=torch.float64),
+                     rho_p=torch.ones(1, device="cuda", dtype=torch.float64),
+                     moff=torch.zeros(2, device="cuda", dtype=torch.int32))
+        _, _, vol = ctx.particle_volume_integrals(u, h, parts)
+        assert abs(float(vol[0]) - val) <= 5e-11
+
+
+def test_force_torque(api, ctx):
+    case = small_cluster(seed=8)
+    _, parts, marks = api.device_case(case, 0)
+    rng = np.random.default_rng(1)
+    F = rng.normal(size=(case.M, 3)) * 100
+    Fib, Tib = ctx.particle_force_torque(parts, marks, torch.tensor(F, device="cuda"), 1.3)
+    ctx.status()
+    fo, to = oracle.force_torque(case.moff, case.R, case.dV, F, 1.3)
+    assert nerr(Fib, fo) <= 1e-12
+    assert nerr(Tib, to) <= 1e-12
+
+
+def test_collide_update(api, ctx):
+    case = synth.cluster_case(N=96, P=24, D_cells=10, phi=0.25, K=2, Ns=3, seed=2,
+                              min_gap_cells=0.1)
+    _, parts, _ = api.device_case(case, 0)
+    rng = np.random.default_rng(2)
+    arrs = [rng.normal(size=(case.P, 3)) * s for s in (1e-3, 1e-6, 1e-5, 1e-5, 1e-7, 1e-7)]
+    Fc = torch.zeros((case.P, 3), device="cuda", dtype=torch.float64)
+    ctx.particle_collide_update(parts, case.n, case.h, case.phys(), case.dt,
+                                *[torch.tensor(a, device="cuda") for a in arrs], Fc_out=Fc)
+    ctx.status()
+    X, U, W, Fco = oracle.collide_update(case.Xr, case.Ur, case.Wr, case.radius, case.rho_p,
+                                         case.n, case.h, case.phys(), case.dt, *arrs)
+    assert np.any(Fco != 0)
+    assert nerr(Fc, Fco) <= 1e-12
+    assert nerr(parts["Xr"], X) <= 1e-12
+    assert nerr(parts["Ur"], U) <= 1e-12
+    assert nerr(parts["Wr"], W) <= 1e-12
+
+
+# ------------------------------------------------------------------ edge cases
+def test_empty_inputs_are_noops(api, ctx):
+    u = torch.randn((3, 16, 16, 16), device="cuda", dtype=torch.float64)
+    u0 = u.clone()
+    U = ctx.ib_interpolate(u, torch.zeros((0, 3), device="cuda", dtype=torch.float64), 1 / 16)
+    assert U.shape == (0, 3)
+    ctx.ib_spread(u, torch.zeros((0, 3), device="cuda", dtype=torch.float64),
+                  torch.zeros((0, 3), device="cuda", dtype=torch.float64),
+                  torch.zeros((0,), device="cuda", dtype=torch.float64), 1 / 16)
+    ctx.status()
+    assert torch.equal(u, u0)
+
+
+def test_invalid_arguments_raise(api, ctx):
+    u = torch.zeros((3, 8, 8, 8), device="cuda", dtype=torch.float64)  # n < 12
+    with pytest.raises(api.IBError) as e:
+        ctx.ib_interpolate(u, torch.zeros((4, 3), device="cuda", dtype=torch.float64), 1 / 8)
+    assert e.value.code == api.IB_ERR_INVALID
+
+
+def test_nonfinite_marker_is_reported(api, ctx):
+    u = torch.zeros((3, 16, 16, 16), device="cuda", dtype=torch.float64)
+    X = torch.full((5, 3), 0.5, device="cuda", dtype=torch.float64)
+    X[2, 1] = float("nan")
+    ctx.ib_interpolate(u, X, 1 / 16)
+    with pytest.raises(api.IBError) as e:
+        ctx.status()
+    assert e.value.code == api.IB_ERR_NONFINITE
+    ctx.status()  # latch cleared
