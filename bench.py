@@ -1,0 +1,491 @@
+#!/usr/bin/env python
+"""Benchmark of the multidirect-forcing IB hot path on one GB300 per rank.
+
+Workload (synthetic, shaped like the paper's particle clusters): 64
+monodisperse spheres of D = 24 cells (1810 Fibonacci markers each) placed
+without overlap in a centred cluster box at volume fraction 0.2 of a 256^3
+periodic grid; 32-mode Fourier velocity field; Ns = 5 forcing passes;
+dt = 1e-3; the paper's three-point kernel; sequential particle order.
+
+One step = every row of the hot path:
+  particle_volume_integrals(u)  (I^n)
+  -> ib_multidirect_forcing      (Algorithm 1, Ns passes)
+  -> particle_force_torque       (F_ib, T_ib)
+  -> particle_volume_integrals(u) (I^{n+1})
+  -> particle_collide_update     (collision + Newton-Euler + centroid)
+
+Metric: marker updates per second = M * Ns * steps / time (a marker update
+is one marker through one interpolate + force + spread pass).  The default
+line is the FP32-field form (interpolation and spreading in FP32, forces,
+reductions, integrals and updates in FP64); the plain FP64 form is reported
+beside it under "fp64".  Between timed steps L2 is flushed by writing a
+512 MiB buffer (outside the timed events).
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gbib|reference]
+For N > 1 (torchrun) every rank runs an independent replica of the workload
+(different seed); value = all ranks' marker updates / max rank time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "IB marker interp+spread updates/s"
+WORKLOAD = dict(N=256, P=64, D=24.0, phi=0.2, K=32, Ns=5, dt=1e-3)
+WORKLOAD_NAME = "cluster-256^3-64xD24-phi0.2-Ns5"
+PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM = 6800.0
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def make_case(seed):
+    from paper_2408_14140_gb300 import synth
+    w = WORKLOAD
+    return synth.cluster_case(N=w["N"], P=w["P"], D_cells=w["D"], phi=w["phi"], K=w["K"],
+                              Ns=w["Ns"], dt=w["dt"], seed=seed, build_field=False)
+
+
+def band_cells(case, kernel_width=3):
+    """Unique cells in the markers' kernel supports (the algorithmic band)."""
+    X = case.R + np.repeat(case.Xr, np.diff(case.moff), axis=0)
+    s = (X - np.asarray(case.org)) / case.h - 0.5
+    first = np.floor(s + 0.5).astype(np.int64) - 1
+    n = np.asarray(case.n, dtype=np.int64)
+    cells = []
+    for dz in range(kernel_width):
+        for dy in range(kernel_width):
+            for dx in range(kernel_width):
+                c = (first + np.array([dx, dy, dz])) % n
+                cells.append((c[:, 2] * n[1] + c[:, 1]) * n[0] + c[:, 0])
+    return int(np.unique(np.concatenate(cells)).size)
+
+
+def interior_cells(case):
+    """Cells a volume integral reads (alpha > 0 or the box walk): sum of
+    (4/3) pi (R + sqrt(3) h / 2)^3 / h^3 per particle, an algorithmic bound."""
+    r = case.radius / case.h + 0.8661
+    return float(np.sum(4.0 / 3.0 * np.pi * r ** 3))
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def peaks():
+    try:
+        with open(PEAKS_PATH) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM, "fallback"
+
+
+# --------------------------------------------------------------------------
+# GPU arm
+# --------------------------------------------------------------------------
+class Runner:
+    """Device state of one workload replica and the hot-path step."""
+
+    def __init__(self, case, prec, device):
+        import torch
+        from paper_2408_14140_gb300 import api, synth
+        self.torch, self.api = torch, api
+        self.case = case
+        self.prec = prec
+        self.dev = device
+        self.ctx = api.Context()
+        dt = api.field_dtype(prec)
+        self.u = synth.fourier_eval_torch(case.n, case.meta["modes"], case.h, case.org,
+                                          device=device).to(dt).contiguous()
+        _, self.parts, self.marks = self._small(case)
+        P, M = case.P, case.M
+        z = lambda *s: torch.zeros(s, dtype=torch.float64, device=device)  # noqa: E731
+        self.F = z(M, 3)
+        self.I0 = (z(P, 3), z(P, 3), z(P))
+        self.I1 = (z(P, 3), z(P, 3), z(P))
+        self.Fib, self.Tib, self.Fc = z(P, 3), z(P, 3), z(P, 3)
+
+    def _small(self, case):
+        torch = self.torch
+
+        def t(a, dtype=torch.float64):
+            return torch.as_tensor(np.asarray(a)).to(device=self.dev, dtype=dtype).contiguous()
+
+        parts = dict(Xr=t(case.Xr), Ur=t(case.Ur), Wr=t(case.Wr), radius=t(case.radius),
+                     rho_p=t(case.rho_p), moff=t(case.moff, torch.int32))
+        marks = dict(R=t(case.R), dV=t(case.dV))
+        return None, parts, marks
+
+    def step(self):
+        c, ctx = self.case, self.ctx
+        ctx.particle_volume_integrals(self.u, c.h, self.parts, out=self.I0)
+        ctx.ib_multidirect_forcing(self.u, c.h, self.parts, self.marks, c.Ns, c.dt, F_out=self.F)
+        ctx.particle_force_torque(self.parts, self.marks, self.F, c.rho_f, out=(self.Fib, self.Tib))
+        ctx.particle_volume_integrals(self.u, c.h, self.parts, out=self.I1)
+        ctx.particle_collide_update(self.parts, c.n, c.h, c.phys(), c.dt, self.Fib, self.Tib,
+                                    self.I1[0], self.I0[0], self.I1[1], self.I0[1], Fc_out=self.Fc)
+
+
+def launches_per_step():
+    # volume: 2 kernels x 2 calls; mdf: prep 1 + levels 1 + perm 1 + count 1 + 2 scans x 3
+    # + flags 1 + compact 1 + fill 1 + sort 1 + level_slots 1 + passes 1; force 1; collide 2
+    return 4 + (1 + 1 + 1 + 1 + 6 + 1 + 1 + 1 + 1 + 1 + 1) + 1 + 2
+
+
+def time_steps(runner, steps, warmup, flush, use_graph):
+    torch = runner.torch
+    stream = torch.cuda.current_stream()
+    graph = None
+    if use_graph:
+        try:
+            g = torch.cuda.CUDAGraph()
+            s = torch.cuda.Stream()
+            s.wait_stream(stream)
+            with torch.cuda.stream(s):
+                runner.step()  # warm allocations on the capture stream
+            stream.wait_stream(s)
+            torch.cuda.synchronize()
+            with torch.cuda.graph(g):
+                runner.step()
+            graph = g
+        except Exception as e:  # capture unsupported: fall back to eager launches
+            print("# graph capture failed, eager launches: %s" % e, file=sys.stderr)
+            graph = None
+            torch.cuda.synchronize()
+    run = graph.replay if graph is not None else runner.step
+    for _ in range(warmup):
+        run()
+    torch.cuda.synchronize()
+    runner.ctx.status()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    for a, b in ev:
+        flush.fill_(1.0)
+        a.record(stream)
+        run()
+        b.record(stream)
+    torch.cuda.synchronize()
+    runner.ctx.status()
+    ms = [a.elapsed_time(b) for a, b in ev]
+    return ms, graph is not None
+
+
+def kernel_timing(runner, steps, flush):
+    """Per-phase device time of the library's kernels (CUDA events recorded by
+    the library on the launching stream) over `steps` eager steps."""
+    torch = runner.torch
+    ctx = runner.ctx
+    for ph in runner.api.PHASES:
+        ctx.read_timing(ph)
+    ctx.set_timing(True)
+    for _ in range(steps):
+        flush.fill_(1.0)
+        runner.step()
+    torch.cuda.synchronize()
+    ctx.set_timing(False)
+    out = {}
+    for ph in runner.api.PHASES:
+        ms, n = ctx.read_timing(ph)
+        if n:
+            out[ph] = (ms, n)
+    return out
+
+
+def e2e_steps(runner, steps):
+    """Same step through the public API with host buffers: H2D copy of the
+    step's inputs from pinned memory, the step, D2H read of its results."""
+    torch = runner.torch
+    dev_in = [runner.u, runner.parts["Xr"], runner.parts["Ur"], runner.parts["Wr"],
+              runner.parts["radius"], runner.parts["rho_p"], runner.parts["moff"],
+              runner.marks["R"], runner.marks["dV"]]
+    host_in = [t.detach().cpu().pin_memory() for t in dev_in]
+    dev_out = [runner.u, runner.parts["Xr"], runner.parts["Ur"], runner.parts["Wr"], runner.F]
+    host_out = [torch.empty(t.shape, dtype=t.dtype, pin_memory=True) for t in dev_out]
+    bi = sum(t.numel() * t.element_size() for t in host_in)
+    bo = sum(t.numel() * t.element_size() for t in host_out)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        for d, h in zip(dev_in, host_in):
+            d.copy_(h, non_blocking=True)
+        runner.step()
+        for d, h in zip(dev_out, host_out):
+            h.copy_(d, non_blocking=True)
+        torch.cuda.synchronize()
+    dt = (time.perf_counter() - t0) / steps
+    runner.ctx.status()
+    return dt, bi, bo
+
+
+def cpu_baseline(case_np, min_seconds=10.0, max_steps=6):
+    """The oracle as it stands, one full hot-path step of the same workload at
+    a time on the host cores, repeated until >= min_seconds."""
+    import oracle
+    c = case_np
+    oracle.build()
+    steps = 0
+    u = c.u.copy()
+    Xr, Ur, Wr = c.Xr.copy(), c.Ur.copy(), c.Wr.copy()
+    t0 = time.perf_counter()
+    while True:
+        a0 = oracle.volume_integrals(c.n, c.h, c.org, u, Xr, c.radius)
+        u, F, _ = oracle.multidirect(c.n, c.h, c.org, u, Xr, Ur, Wr, c.moff, c.R, c.dV, c.Ns, c.dt)
+        fo, to = oracle.force_torque(c.moff, c.R, c.dV, F, c.rho_f)
+        a1 = oracle.volume_integrals(c.n, c.h, c.org, u, Xr, c.radius)
+        Xr, Ur, Wr, _ = oracle.collide_update(Xr, Ur, Wr, c.radius, c.rho_p, c.n, c.h, c.phys(),
+                                              c.dt, fo, to, a1[0], a0[0], a1[1], a0[1])
+        steps += 1
+        el = time.perf_counter() - t0
+        if el >= min_seconds or steps >= max_steps:
+            break
+    return el / steps, steps, oracle.num_threads()
+
+
+def run_gpu(args):
+    import torch
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    device = torch.device("cuda", torch.cuda.current_device())
+    from paper_2408_14140_gb300 import api, build
+
+    if rank == 0 or not os.path.exists(build.LIB):
+        build.build()
+    if world > 1:
+        dist.barrier()
+    case = make_case(seed=rank)
+    M, Ns = case.M, case.Ns
+    flush = torch.empty(512 << 20 >> 2, dtype=torch.float32, device=device)
+
+    results = {}
+    for prec in (api.IB_F32, api.IB_F64):
+        r = Runner(case, prec, device)
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        clk = ClockSampler(local) if prec == api.IB_F32 else None
+        if clk:
+            clk.start()
+        ms, graphed = time_steps(r, args.steps, args.warmup, flush, not args.no_graph)
+        clocks = clk.stop() if clk else None
+        t_rank = sum(ms) / 1000.0
+        if world > 1:
+            tt = torch.tensor([t_rank], device=device, dtype=torch.float64)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            t_rank = float(tt.item())
+        kt = kernel_timing(r, max(3, min(args.steps, 10)), flush)
+        e2e = e2e_steps(r, max(2, min(args.steps, 5))) if not args.no_e2e else None
+        results[prec] = dict(ms=ms, t=t_rank, graphed=graphed, clocks=clocks, kt=kt, e2e=e2e,
+                             runner=r)
+        del r
+
+    # algorithmic traffic of the dominant kernel (the persistent Ns-pass kernel)
+    B = band_cells(case)
+    out = {}
+    for prec, res in results.items():
+        s = 8 if prec == api.IB_F64 else 4
+        alg_mdf = 6 * s * B + (24 + 8 + 24) * M
+        ms_pass, n_pass = res["kt"].get("mdf_passes", (float("nan"), 1))
+        dur = ms_pass / n_pass / 1000.0
+        step_s = res["t"] / args.steps
+        out[prec] = dict(step_s=step_s, value=world * M * Ns / step_s,
+                         alg_mdf=alg_mdf, mdf_dur=dur,
+                         phases={k: round(v[0] / v[1] * 1000.0, 2) for k, v in res["kt"].items()},
+                         e2e=res["e2e"], graphed=res["graphed"], clocks=res["clocks"])
+    if rank != 0:
+        if world > 1:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+    hbm, hbm_src = peaks()
+    f32 = out[api.IB_F32]
+    f64 = out[api.IB_F64]
+    achieved = f32["alg_mdf"] / f32["mdf_dur"] / 1e9
+    line = {
+        "metric": METRIC,
+        "value": f32["value"],
+        "unit": "marker-updates/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": f32["step_s"] * 1000.0,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32 fields, f64 forces/reductions",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD_NAME, "grid": [256, 256, 256], "particles": case.P,
+                   "markers": M, "Ns": Ns, "kernel": "roma3", "order": "sequential",
+                   "band_cells": B, "parallelism": "replicas" if world > 1 else "single-gpu",
+                   "l2": "flushed (512 MiB write) between timed steps",
+                   "launch": "cuda-graph replay" if f32["graphed"] else "eager"},
+        "e2e": None,
+        "gpu_launches": args.steps * launches_per_step(),
+        "roofline": {"bound": "hbm", "kernel": "k_mdf_passes",
+                     "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": achieved / hbm, "peak_source": hbm_src,
+                     "algorithmic_bytes": f32["alg_mdf"], "duration_us": f32["mdf_dur"] * 1e6,
+                     "traffic": None},
+        "phases_us": f32["phases"],
+        "clocks": f32["clocks"],
+        "fp64": {"value": f64["value"], "ms_per_step": f64["step_s"] * 1000.0,
+                 "phases_us": f64["phases"],
+                 "mdf_achieved_gbs": f64["alg_mdf"] / f64["mdf_dur"] / 1e9},
+    }
+    if f32["e2e"]:
+        dt, bi, bo = f32["e2e"]
+        line["e2e"] = {"value": world * M * Ns / dt, "unit": "marker-updates/s",
+                       "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo}
+    if f64["e2e"]:
+        dt, bi, bo = f64["e2e"]
+        line["fp64"]["e2e"] = {"value": world * M * Ns / dt, "h2d_bytes_per_step": bi,
+                               "d2h_bytes_per_step": bo}
+    if world == 1 and not args.no_cpu_baseline:
+        from paper_2408_14140_gb300 import synth
+        case.u = synth.fourier_eval_torch(case.n, case.meta["modes"], case.h, case.org,
+                                          device=device).cpu().numpy()
+        t_cpu, n_cpu, thr = cpu_baseline(case)
+        line["cpu_baseline"] = {"value": M * Ns / t_cpu, "unit": "marker-updates/s",
+                                "cores": thr, "kind": "oracle",
+                                "sample": "%d full FP64 step(s) of the same workload" % n_cpu}
+    print(json.dumps(line))
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def run_reference(args):
+    """The FP64 oracle timed on the host cores on this workload (the reference
+    arm for a paper with no published implementation)."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    from paper_2408_14140_gb300 import synth
+    import oracle
+    case = make_case(seed=0)
+    case.u = synth.fourier_eval(case.n, case.meta["modes"], case.h, case.org)
+    oracle.build()
+    c = case
+    u = c.u.copy()
+    Xr, Ur, Wr = c.Xr.copy(), c.Ur.copy(), c.Wr.copy()
+
+    def step():
+        nonlocal u, Xr, Ur, Wr
+        a0 = oracle.volume_integrals(c.n, c.h, c.org, u, Xr, c.radius)
+        u, F, _ = oracle.multidirect(c.n, c.h, c.org, u, Xr, Ur, Wr, c.moff, c.R, c.dV, c.Ns, c.dt)
+        fo, to = oracle.force_torque(c.moff, c.R, c.dV, F, c.rho_f)
+        a1 = oracle.volume_integrals(c.n, c.h, c.org, u, Xr, c.radius)
+        Xr, Ur, Wr, _ = oracle.collide_update(Xr, Ur, Wr, c.radius, c.rho_p, c.n, c.h, c.phys(),
+                                              c.dt, fo, to, a1[0], a0[0], a1[1], a0[1])
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = (time.perf_counter() - t0) / args.steps
+    v = c.M * c.Ns / dt
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "marker-updates/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": dt * 1000.0, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD_NAME, "grid": [256, 256, 256], "particles": c.P,
+                       "markers": c.M, "Ns": c.Ns},
+            "cpu_baseline": {"value": v, "unit": "marker-updates/s", "cores": oracle.num_threads(),
+                             "kind": "oracle",
+                             "sample": "%d full FP64 steps of the same workload" % args.steps},
+            "e2e": {"value": v, "unit": "marker-updates/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gbib", choices=["gbib", "reference"])
+    ap.add_argument("--no-graph", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

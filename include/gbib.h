@@ -125,6 +125,24 @@ GBIB_API size_t ib_workspace_needed(void);
 /* Number of streaming multiprocessors of the context's device.            */
 GBIB_API int ib_ctx_sm_count(const ib_ctx *ctx);
 
+/* ---- optional device timing of the library's own kernels ---------------
+ * When enabled, every call records a CUDA event pair on its stream around
+ * each phase below.  ib_ctx_read_timing() waits for the recorded events,
+ * returns the summed device time (ms) and the number of launches of one
+ * phase since the last read, and resets that phase.  Timing adds two event
+ * records per phase and must stay off while a stream is being captured.  */
+#define IB_PHASE_MDF_PREP 0    /* marker preparation, levels, tile binning  */
+#define IB_PHASE_MDF_PASSES 1  /* the persistent Ns-pass kernel            */
+#define IB_PHASE_SPREAD 2      /* ib_spread (binning + gather)              */
+#define IB_PHASE_INTERP 3      /* ib_interpolate                            */
+#define IB_PHASE_VOLUME 4      /* particle_volume_integrals                 */
+#define IB_PHASE_FORCE 5       /* particle_force_torque                     */
+#define IB_PHASE_COLLIDE 6     /* particle_collide_update                   */
+#define IB_PHASE_COUNT 7
+GBIB_API int ib_ctx_set_timing(ib_ctx *ctx, int enable);
+GBIB_API int ib_ctx_read_timing(ib_ctx *ctx, int phase, double *ms_total,
+                                int *launches);
+
 /* ---- velocity interpolation J: Eq. (u), Eq. (vi), Algorithm 1 -----------
  * U[l] = sum_ijk u(x_ijk) delta_h(x_ijk - X[l]) h^3 for l < M, where
  * delta_h(x) = h^-3 prod_a phi(x_a / h) (Sec. 2).  X[M][3] are absolute

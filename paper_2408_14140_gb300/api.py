@@ -35,8 +35,12 @@ PESKIN4 = 1
 SEQUENTIAL = 0
 SIMULTANEOUS = 1
 
+PHASES = {"mdf_prep": 0, "mdf_passes": 1, "spread": 2, "interp": 3, "volume": 4,
+          "force": 5, "collide": 6}
+
 EXPORTS = ["ib_ctx_create", "ib_ctx_reserve", "ib_ctx_destroy", "ib_ctx_status",
            "ib_last_error", "ib_workspace_needed", "ib_ctx_sm_count",
+           "ib_ctx_set_timing", "ib_ctx_read_timing",
            "ib_interpolate", "ib_spread", "ib_multidirect_forcing",
            "particle_volume_integrals", "particle_force_torque",
            "particle_collide_update"]
@@ -89,6 +93,8 @@ def load(path: str = LIB_PATH):
         "ib_last_error": (ctypes.c_char_p, []),
         "ib_workspace_needed": (sz, []),
         "ib_ctx_sm_count": (i, [p]),
+        "ib_ctx_set_timing": (i, [p, i]),
+        "ib_ctx_read_timing": (i, [p, i, ctypes.POINTER(d), ctypes.POINTER(i)]),
         "ib_interpolate": (i, [p, p, p, i, p, i, p, p]),
         "ib_spread": (i, [p, p, i, p, p, p, i, p, p]),
         "ib_multidirect_forcing": (i, [p, p, p, p, p, i, d, i, i, p, p, p]),
@@ -180,6 +186,18 @@ class Context:
 
     def reserve(self, nbytes: int):
         self._check(self.lib.ib_ctx_reserve(self.handle, int(nbytes)))
+
+    def set_timing(self, enable: bool):
+        """Record CUDA events around the library's kernels (see gbib.h)."""
+        self._check(self.lib.ib_ctx_set_timing(self.handle, 1 if enable else 0))
+
+    def read_timing(self, phase: str):
+        """(total ms, launches) of one phase since the last read; resets it."""
+        ms = ctypes.c_double()
+        n = ctypes.c_int()
+        self._check(self.lib.ib_ctx_read_timing(self.handle, PHASES[phase], ctypes.byref(ms),
+                                                ctypes.byref(n)))
+        return ms.value, n.value
 
     def status(self, stream=None):
         """Synchronise the stream and raise the first device-side error."""

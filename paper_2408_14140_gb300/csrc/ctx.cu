@@ -126,6 +126,39 @@ __global__ void k_scan_apply(const uint32_t *in, uint32_t *out, int n, const uin
     if (blockIdx.x == 0 && threadIdx.x == 0) out[n] = totals[gridDim.x];
 }
 
+static cudaEvent_t take_event(ib_ctx *c) {
+    if (!c->pool.empty()) {
+        cudaEvent_t e = c->pool.back();
+        c->pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return e;
+}
+
+PhaseTimer::PhaseTimer(ib_ctx *c, int ph, cudaStream_t st) : ctx(c), phase(ph), s(st) {
+    if (!ctx || !ctx->timing) return;
+    a = take_event(ctx);
+    b = take_event(ctx);
+    if (a && b) cudaEventRecord(a, s);
+}
+
+void PhaseTimer::stop() {
+    if (!ctx) return;
+    if (ctx->timing && a && b) {
+        cudaEventRecord(b, s);
+        ctx->pending[phase].push_back({a, b});
+    } else {
+        if (a) ctx->pool.push_back(a);
+        if (b) ctx->pool.push_back(b);
+    }
+    ctx = nullptr;
+}
+
 size_t scan_workspace(int n) { return (size_t)(n + kScanBlock - 1) / kScanBlock + 2; }
 
 void exclusive_scan(const uint32_t *in, uint32_t *out, int n, uint32_t *scratch,
@@ -190,9 +223,42 @@ int ib_ctx_reserve(ib_ctx *c, size_t bytes) {
     return IB_OK;
 }
 
+int ib_ctx_set_timing(ib_ctx *c, int enable) {
+    if (!c) return set_error(IB_ERR_INVALID, "ctx is NULL");
+    c->timing = enable ? 1 : 0;
+    return IB_OK;
+}
+
+int ib_ctx_read_timing(ib_ctx *c, int phase, double *ms_total, int *launches) {
+    if (!c) return set_error(IB_ERR_INVALID, "ctx is NULL");
+    if (phase < 0 || phase >= IB_PHASE_COUNT) return set_error(IB_ERR_INVALID, "bad phase");
+    double tot = 0.0;
+    int n = 0;
+    for (auto &pr : c->pending[phase]) {
+        if (cudaEventSynchronize(pr.second) != cudaSuccess)
+            return set_error(IB_ERR_CUDA, "timing: %s", cudaGetErrorString(cudaGetLastError()));
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, pr.first, pr.second);
+        tot += ms;
+        ++n;
+        c->pool.push_back(pr.first);
+        c->pool.push_back(pr.second);
+    }
+    c->pending[phase].clear();
+    if (ms_total) *ms_total = tot;
+    if (launches) *launches = n;
+    return IB_OK;
+}
+
 int ib_ctx_destroy(ib_ctx *c) {
     if (!c) return IB_OK;
     cudaDeviceSynchronize();
+    for (auto &v : c->pending)
+        for (auto &pr : v) {
+            cudaEventDestroy(pr.first);
+            cudaEventDestroy(pr.second);
+        }
+    for (auto e : c->pool) cudaEventDestroy(e);
     cudaFree(c->ws);
     cudaFree(c->status);
     delete c;

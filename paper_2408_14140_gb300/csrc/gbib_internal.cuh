@@ -105,12 +105,18 @@ __device__ __forceinline__ bool finite3(const double *v) {
 }  // namespace gbib
 
 // ---- host side ------------------------------------------------------------
+#include <utility>
+#include <vector>
+
 struct ib_ctx {
     int device;
     int sm_count;
     void *ws;            // device workspace
     size_t ws_bytes;
     gbib::DevStatus *status;  // device error latch
+    int timing;          // record phase events
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending[IB_PHASE_COUNT];
+    std::vector<cudaEvent_t> pool;
 };
 
 namespace gbib {
@@ -139,6 +145,17 @@ int oom_error(size_t need, size_t have);
 int check_launch(const char *what);
 int validate_grid(const ib_grid *g, int need_prec);
 DevGrid make_dev_grid(const ib_grid *g);
+
+// Records a CUDA event pair around a scope when the context times phases.
+struct PhaseTimer {
+    ib_ctx *ctx;
+    int phase;
+    cudaStream_t s;
+    cudaEvent_t a = nullptr, b = nullptr;
+    PhaseTimer(ib_ctx *c, int ph, cudaStream_t st);
+    void stop();
+    ~PhaseTimer() { stop(); }
+};
 
 // Exclusive scan of n uint32 counts into out[0..n] (out[n] = total).
 // Needs scan_workspace(n) uint32 of scratch.

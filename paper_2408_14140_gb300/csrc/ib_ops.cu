@@ -836,6 +836,7 @@ template <typename T, int KER>
 static int run_interpolate(ib_ctx *ctx, const DevGrid &g, const void *u, int M, const double *X,
                            double *U, cudaStream_t s) {
     int nb = grid_blocks(M, 256, ctx->sm_count);
+    PhaseTimer tm(ctx, IB_PHASE_INTERP, s);
     k_interpolate<T, KER><<<nb, 256, 0, s>>>(g, (const T *)u, M, X, U, ctx->status);
     return check_launch("ib_interpolate");
 }
@@ -855,6 +856,7 @@ static int run_spread(ib_ctx *ctx, const DevGrid &g, int M, const double *X, con
     if (!ar.ok())
         return oom_error(ar.used, ar.cap);
     int nb = grid_blocks(M, 256, ctx->sm_count);
+    PhaseTimer tm(ctx, IB_PHASE_SPREAD, s);
     k_prep_spread<T, KER><<<nb, 256, 0, s>>>(g, M, X, F, dV, ms, ctx->status);
     Slots sl;
     int *ncompact = nullptr;
@@ -902,6 +904,7 @@ static int run_mdf(ib_ctx *ctx, const DevGrid &g, void *u, const ib_particles *p
     if (ndense > (1LL << 30)) return set_error(IB_ERR_UNSUPPORTED, "too many tiles");
     if (!ar.ok())
         return oom_error(ar.used, ar.cap);
+    PhaseTimer tprep(ctx, IB_PHASE_MDF_PREP, s);
     k_prep_particles<T, KER><<<P, kBlock, 0, s>>>(g, P, pp->Xr, pp->Ur, pp->Wr, pp->marker_offset, mk->R,
                                                  mk->dV, ms, F_out, rho, box_lo, box_dim, part_of,
                                                  ctx->status);
@@ -918,6 +921,7 @@ static int run_mdf(ib_ctx *ctx, const DevGrid &g, void *u, const ib_particles *p
     if (rc) return rc;
     k_level_slots<<<1, 256, 0, s>>>(sg.mode, lo.nlev, lo.lev_pbeg, sl.flag_scan, (int)ndense, lev_sbeg);
     cudaMemsetAsync(bar.count, 0, 2 * sizeof(unsigned int), s);
+    tprep.stop();
     PassArgs<T> a;
     a.g = g;
     a.u = (T *)u;
@@ -939,6 +943,7 @@ static int run_mdf(ib_ctx *ctx, const DevGrid &g, void *u, const ib_particles *p
     if (per_sm < 1) return set_error(IB_ERR_CUDA, "mdf kernel cannot be resident");
     int nblocks = per_sm * ctx->sm_count;
     void *args[] = {&a};
+    PhaseTimer tpass(ctx, IB_PHASE_MDF_PASSES, s);
     cudaError_t e = cudaLaunchCooperativeKernel((const void *)k_mdf_passes<T, KER>, nblocks, kBlock, args, 0, s);
     if (e != cudaSuccess) return set_error(IB_ERR_CUDA, "mdf launch: %s", cudaGetErrorString(e));
     return check_launch("ib_multidirect_forcing");

@@ -233,6 +233,7 @@ static int run_volume(ib_ctx *ctx, const DevGrid &g, const void *u, const ib_par
     double *partial = ar.take<double>((size_t)pp->P * kVolSplit * 7);
     if (!ar.ok())
         return oom_error(ar.used, ar.cap);
+    PhaseTimer tm(ctx, IB_PHASE_VOLUME, s);
     k_volume<T><<<pp->P * kVolSplit, kVolThreads, 0, s>>>(g, (const T *)u, pp->P, pp->Xr, pp->radius, partial,
                                                           ctx->status);
     k_volume_final<<<(pp->P + 127) / 128, 128, 0, s>>>(pp->P, partial, Iu, Irxu, vol);
@@ -268,6 +269,7 @@ int particle_force_torque(ib_ctx *ctx, const ib_particles *parts, const ib_marke
     if (parts->P == 0) return IB_OK;
     if (!parts->marker_offset || !F_ib || !T_ib || (marks->M > 0 && (!marks->R || !marks->dV || !F)))
         return set_error(IB_ERR_INVALID, "NULL array");
+    PhaseTimer tm(ctx, IB_PHASE_FORCE, (cudaStream_t)stream);
     k_force_torque<<<parts->P, 256, 0, (cudaStream_t)stream>>>(parts->P, parts->marker_offset, marks->R,
                                                               marks->dV, F, rho_f, F_ib, T_ib);
     return check_launch("particle_force_torque");
@@ -317,6 +319,7 @@ int particle_collide_update(ib_ctx *ctx, ib_particles *parts, const ib_grid *gri
     a.Xnew = nullptr;
     cudaStream_t s = (cudaStream_t)stream;
     int nb = (parts->P + 127) / 128;
+    PhaseTimer tm(ctx, IB_PHASE_COLLIDE, s);
     k_collide_forces<<<nb, 128, 0, s>>>(a, Fc);
     k_newton_euler<<<nb, 128, 0, s>>>(a, Fc, ctx->status);
     return check_launch("particle_collide_update");

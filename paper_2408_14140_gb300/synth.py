@@ -96,13 +96,8 @@ def sphere_markers(radius: float, h: float):
 # fields
 # --------------------------------------------------------------------------
 
-def fourier_field(n, K: int, rng: SplitMix64, h: float | None = None,
-                  org=(0.0, 0.0, 0.0), dtype=np.float64) -> np.ndarray:
-    """u[3, n2, n1, n0] = sum of K random Fourier modes at cell centres."""
-    n = [int(v) for v in n]
-    if h is None:
-        h = 1.0 / n[0]
-    L = [n[a] * h for a in range(3)]
+def fourier_modes(K: int, rng: SplitMix64):
+    """K random modes (a_k[3], n_k[3] integers, theta_k) in draw order."""
     modes = []
     for _ in range(K):
         a = rng.normals(3)
@@ -112,6 +107,13 @@ def fourier_field(n, K: int, rng: SplitMix64, h: float | None = None,
                 break
         th = 2.0 * math.pi * rng.uniform()
         modes.append((a, kv, th))
+    return modes
+
+
+def fourier_eval(n, modes, h, org=(0.0, 0.0, 0.0), dtype=np.float64) -> np.ndarray:
+    """u[3, n2, n1, n0] = sum_k a_k cos(2 pi n_k . x / L + theta_k) at cell centres."""
+    n = [int(v) for v in n]
+    L = [n[a] * h for a in range(3)]
     xs = [org[a] + (np.arange(n[a]) + 0.5) * h for a in range(3)]
     u = np.zeros((3, n[2], n[1], n[0]), dtype=np.float64)
     for a, kv, th in modes:
@@ -124,6 +126,35 @@ def fourier_field(n, K: int, rng: SplitMix64, h: float | None = None,
             for c in range(3):
                 u[c, k0:k0 + 32] += a[c] * blk
     return u.astype(dtype, copy=False)
+
+
+def fourier_eval_torch(n, modes, h, org=(0.0, 0.0, 0.0), device="cuda", dtype=None):
+    """Same field as :func:`fourier_eval`, evaluated with torch on ``device``
+    (FP64 arithmetic, then cast) -- used for grids too large to build on the
+    host quickly."""
+    import torch
+    n = [int(v) for v in n]
+    L = [n[a] * h for a in range(3)]
+    xs = [org[a] + (torch.arange(n[a], device=device, dtype=torch.float64) + 0.5) * h
+          for a in range(3)]
+    u = torch.zeros((3, n[2], n[1], n[0]), device=device, dtype=torch.float64)
+    for a, kv, th in modes:
+        ex = torch.exp(1j * 2.0 * math.pi * kv[0] * xs[0] / L[0])
+        ey = torch.exp(1j * 2.0 * math.pi * kv[1] * xs[1] / L[1])
+        ez = torch.exp(1j * (2.0 * math.pi * kv[2] * xs[2] / L[2] + th))
+        blk = (ez[:, None, None] * ey[None, :, None] * ex[None, None, :]).real
+        for c in range(3):
+            u[c] += float(a[c]) * blk
+        del blk
+    return u if dtype is None else u.to(dtype)
+
+
+def fourier_field(n, K: int, rng: SplitMix64, h: float | None = None,
+                  org=(0.0, 0.0, 0.0), dtype=np.float64) -> np.ndarray:
+    """u[3, n2, n1, n0] = sum of K random Fourier modes at cell centres."""
+    if h is None:
+        h = 1.0 / int(n[0])
+    return fourier_eval(n, fourier_modes(K, rng), h, org, dtype)
 
 
 def taylor_green_field(n, U0: float = 1.0, h: float | None = None,
@@ -244,7 +275,7 @@ def single_sphere_case(N: int = 64, D_cells: float = 20.0, K: int = 8,
 
 def cluster_case(N: int, P: int, D_cells: float, phi: float, K: int, Ns: int,
                  dt: float = 1e-3, seed: int = 0, min_gap_cells: float = 0.0,
-                 u_dtype=np.float64) -> Case:
+                 u_dtype=np.float64, build_field: bool = True) -> Case:
     """P monodisperse spheres placed by RSA inside a centred cubic cluster box
     whose side makes their volume fraction ``phi`` (the 256^3 / 64 x D24 and
     384^3 / 512 x D16 cases)."""
@@ -256,11 +287,13 @@ def cluster_case(N: int, P: int, D_cells: float, phi: float, K: int, Ns: int,
         raise ValueError("cluster box does not fit the grid")
     lo = 0.5 * (N - side)
     cent = rsa_place(P, D_cells, [lo] * 3, [lo + side] * 3, min_gap_cells, rng)
-    u = fourier_field((N, N, N), K, rng, h)
-    case = _assemble((N, N, N), h, u.astype(u_dtype, copy=False), cent * h,
+    modes = fourier_modes(K, rng)
+    u = fourier_eval((N, N, N), modes, h).astype(u_dtype, copy=False) if build_field else None
+    case = _assemble((N, N, N), h, u, cent * h,
                      [0.5 * D_cells * h] * P, rng, Ns, dt,
                      meta={"workload": "cluster", "N": N, "P": P,
-                           "D": D_cells, "phi": phi, "box_side": side})
+                           "D": D_cells, "phi": phi, "box_side": side,
+                           "modes": modes})
     return case
 
 
