@@ -49,6 +49,7 @@ struct Slots {
     uint32_t *flag_scan;  // [ndense+1] compact index of non-empty slots
     uint32_t *dense_of;   // [ncompact_max] dense id of each compact slot
     uint32_t *cand;    // [total candidates] marker ids, sorted per slot
+    int8_t *relx;      // [total candidates] first stencil x - tile lo x, in [-3, 7]
     uint16_t *rows;    // [ncompact_max][kRows+1] row starts, relative
     int4 *geo_lo;      // [ncompact_max] tile first cell (wrapped), w = level
     int4 *geo_dim;     // [ncompact_max] tile dims, w = candidate count
@@ -269,88 +270,96 @@ struct LevelOut {
     int *nlev;        // [1]
 };
 
-__global__ void __launch_bounds__(1024) k_levels(DevGrid g, int P, int order, int KW,
-                                                 const double *__restrict__ Xr,
-                                                 const double *__restrict__ rho,
-                                                 const int *__restrict__ moff, LevelOut lo,
-                                                 int *__restrict__ work, DevStatus *st) {
-    // work: [P] levels (scratch) + [P+1] counts
-    __shared__ int s_changed;
-    __shared__ int s_nlev;
+constexpr int kMaxNbr = 48;
+
+// Conflict lists: for every p, the q < p whose stencils may share a cell
+// (count -1 = more than kMaxNbr, scanned again when levels are assigned).
+__global__ void k_conflicts(DevGrid g, int P, int KW, const double *__restrict__ Xr,
+                            const double *__restrict__ rho, int *__restrict__ nbr_cnt,
+                            int *__restrict__ nbr) {
+    const double L[3] = {g.n[0] * g.h, g.n[1] * g.h, g.n[2] * g.h};
+    const double iL[3] = {1.0 / L[0], 1.0 / L[1], 1.0 / L[2]};
+    const double halo = 1.7320508075688772 * KW * g.h;
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x) {
+        const double xp[3] = {Xr[3 * p], Xr[3 * p + 1], Xr[3 * p + 2]};
+        int cnt = 0;
+        for (int q = 0; q < p; ++q) {
+            double d2 = 0.0;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                double d = Xr[3 * q + a] - xp[a];
+                d -= L[a] * rint(d * iL[a]);
+                d2 += d * d;
+            }
+            const double lim = rho[p] + rho[q] + halo;
+            if (d2 < lim * lim) {
+                if (cnt < kMaxNbr) nbr[(size_t)p * kMaxNbr + cnt] = q;
+                ++cnt;
+            }
+        }
+        nbr_cnt[p] = cnt <= kMaxNbr ? cnt : -1;
+    }
+}
+
+// Levels by one sequential sweep (level(p) needs only q < p), then the
+// counting sort of particles by level and the level-major marker offsets.
+__global__ void __launch_bounds__(32) k_levels(DevGrid g, int P, int order, int KW,
+                                               const double *__restrict__ Xr,
+                                               const double *__restrict__ rho,
+                                               const int *__restrict__ moff,
+                                               const int *__restrict__ nbr_cnt,
+                                               const int *__restrict__ nbr, LevelOut lo,
+                                               int *__restrict__ work) {
+    if (threadIdx.x != 0) return;
     int *lev = lo.level;
-    for (int p = threadIdx.x; p < P; p += blockDim.x) lev[p] = 0;
-    __syncthreads();
-    if (order == IB_ORDER_SEQUENTIAL && P > 1) {
-        double L[3] = {g.n[0] * g.h, g.n[1] * g.h, g.n[2] * g.h};
-        double halo = sqrt(3.0) * KW * g.h;
-        // Bellman-Ford style relaxation over the conflict DAG; converges in
-        // (longest chain) sweeps.
-        for (int it = 0; it <= P; ++it) {
-            if (threadIdx.x == 0) s_changed = 0;
-            __syncthreads();
-            for (int p = threadIdx.x; p < P; p += blockDim.x) {
-                double xp[3] = {Xr[3 * p], Xr[3 * p + 1], Xr[3 * p + 2]};
-                int best = 0;
+    int nl = 0;
+    const double L[3] = {g.n[0] * g.h, g.n[1] * g.h, g.n[2] * g.h};
+    const double iL[3] = {1.0 / L[0], 1.0 / L[1], 1.0 / L[2]};
+    const double halo = 1.7320508075688772 * KW * g.h;
+    for (int p = 0; p < P; ++p) {
+        int best = 0;
+        if (order == IB_ORDER_SEQUENTIAL) {
+            int c = nbr_cnt[p];
+            if (c >= 0) {
+                for (int k = 0; k < c; ++k) best = max(best, lev[nbr[(size_t)p * kMaxNbr + k]] + 1);
+            } else {
                 for (int q = 0; q < p; ++q) {
                     double d2 = 0.0;
-#pragma unroll
                     for (int a = 0; a < 3; ++a) {
-                        double d = Xr[3 * q + a] - xp[a];
-                        d -= L[a] * nearbyint(d / L[a]);
+                        double d = Xr[3 * q + a] - Xr[3 * p + a];
+                        d -= L[a] * rint(d * iL[a]);
                         d2 += d * d;
                     }
-                    double lim = rho[p] + rho[q] + halo;
+                    const double lim = rho[p] + rho[q] + halo;
                     if (d2 < lim * lim) best = max(best, lev[q] + 1);
                 }
-                if (best != lev[p]) {
-                    lev[p] = best;
-                    s_changed = 1;
-                }
             }
-            __syncthreads();
-            if (!s_changed) break;
-            __syncthreads();
         }
+        lev[p] = best;
+        nl = max(nl, best + 1);
     }
-    __syncthreads();
-    // counting sort of particles by level (stable: index order inside a level)
-    if (threadIdx.x == 0) {
-        int nl = 0;
-        for (int p = 0; p < P; ++p) nl = max(nl, lev[p] + 1);
-        s_nlev = P > 0 ? nl : 0;
-        *lo.nlev = s_nlev;
-    }
-    __syncthreads();
-    int nl = s_nlev;
+    *lo.nlev = nl;
     int *cnt = work;  // [P+1]
-    for (int i = threadIdx.x; i <= P; i += blockDim.x) cnt[i] = 0;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        for (int p = 0; p < P; ++p) cnt[lev[p]]++;
-        int acc = 0, macc = 0;
-        for (int L = 0; L < nl; ++L) {
-            lo.lev_pbeg[L] = acc;
-            acc += cnt[L];
-        }
-        lo.lev_pbeg[nl] = acc;
-        // ranks and marker bases in level-major order
-        for (int L = 0; L < nl; ++L) cnt[L] = lo.lev_pbeg[L];
-        for (int p = 0; p < P; ++p) lo.rank[p] = cnt[lev[p]]++;
-        // marker bases: walk particles in rank order
-        int *by_rank = cnt;  // reuse: by_rank[r] = p
-        for (int p = 0; p < P; ++p) by_rank[lo.rank[p]] = p;
-        int L = 0;
-        for (int r = 0; r < P; ++r) {
-            int p = by_rank[r];
-            while (L < nl && lo.lev_pbeg[L] <= r) {
-                lo.lev_mbeg[L] = macc;
-                ++L;
-            }
-            lo.mbase[p] = macc;
-            macc += moff[p + 1] - moff[p];
-        }
-        while (L <= nl) lo.lev_mbeg[L++] = macc;
+    for (int i = 0; i <= P; ++i) cnt[i] = 0;
+    for (int p = 0; p < P; ++p) cnt[lev[p]]++;
+    int acc = 0;
+    for (int l = 0; l < nl; ++l) {
+        lo.lev_pbeg[l] = acc;
+        acc += cnt[l];
     }
+    lo.lev_pbeg[nl] = acc;
+    for (int l = 0; l < nl; ++l) cnt[l] = lo.lev_pbeg[l];
+    for (int p = 0; p < P; ++p) lo.rank[p] = cnt[lev[p]]++;
+    int *by_rank = cnt;
+    for (int p = 0; p < P; ++p) by_rank[lo.rank[p]] = p;
+    int l = 0, macc = 0;
+    for (int r = 0; r < P; ++r) {
+        const int p = by_rank[r];
+        while (l < nl && lo.lev_pbeg[l] <= r) lo.lev_mbeg[l++] = macc;
+        lo.mbase[p] = macc;
+        macc += moff[p + 1] - moff[p];
+    }
+    while (l <= nl) lo.lev_mbeg[l++] = macc;
 }
 
 // ---------------------------------------------------------------------------
@@ -520,10 +529,13 @@ __global__ void __launch_bounds__(kBlock) k_slot_sort(
             lev = level[p];
         }
         if (nc > kMaxCand) {
+            // report, and leave an empty tile (no rows, no cells)
+            uint16_t *rs = sl.rows + (size_t)cs * (kRows + 1);
+            for (int r = threadIdx.x; r <= kRows; r += blockDim.x) rs[r] = 0;
             if (threadIdx.x == 0) {
                 raise_status(st, IB_ERR_UNSUPPORTED, nc);
                 sl.geo_lo[cs] = make_int4(lo[0], lo[1], lo[2], lev);
-                sl.geo_dim[cs] = make_int4(0, 0, 0, 0);
+                sl.geo_dim[cs] = make_int4(0, 0, 0, (int)b);
             }
             __syncthreads();
             continue;
@@ -563,7 +575,11 @@ __global__ void __launch_bounds__(kBlock) k_slot_sort(
                 __syncthreads();
             }
         }
-        for (int i = threadIdx.x; i < nc; i += blockDim.x) sl.cand[b + i] = (uint32_t)(keys[i] & 0xffffffffu);
+        for (int i = threadIdx.x; i < nc; i += blockDim.x) {
+            uint32_t m = (uint32_t)(keys[i] & 0xffffffffu);
+            sl.cand[b + i] = m;
+            sl.relx[b + i] = (int8_t)(wrap_int((long long)anchor_x(anchor[m]) - lo[0] + 3, g.n[0]) - 3);
+        }
         if (threadIdx.x == 0) {
             uint16_t *rs = sl.rows + (size_t)cs * (kRows + 1);
             uint32_t acc = 0;
@@ -582,36 +598,65 @@ __global__ void __launch_bounds__(kBlock) k_slot_sort(
 // ---------------------------------------------------------------------------
 // gather of one tile: every cell sums w * A over the markers whose stencil
 // covers it, rows in (z, y) order, markers in index order within a row.
-// Returns true when the cell had any contribution.
+// The tile's candidates (their per-axis weights, spread source and x offset)
+// are first staged in shared memory with independent loads; the per-cell
+// sums then read shared memory only.  Tiles with more than Stage<T>::N
+// candidates read the same values from global memory instead.
 // ---------------------------------------------------------------------------
-template <typename T, int KW, bool COH>
-__device__ __forceinline__ bool gather_cell(const DevGrid &g, int cx, int cy, int cz, int tx, int ty,
-                                            int tz, const uint16_t *rs, const uint32_t *__restrict__ cand,
-                                            const uint64_t *__restrict__ anchor,
-                                            const T *__restrict__ wts, const T *__restrict__ A,
-                                            T acc[3]) {
+template <typename T> struct Stage;
+template <> struct Stage<float> { static constexpr int N = 1024; };
+template <> struct Stage<double> { static constexpr int N = 512; };
+
+template <typename T>
+constexpr size_t stage_bytes() {
+    return (size_t)Stage<T>::N * (12 + 4) * sizeof(T) + (size_t)Stage<T>::N + 2 * (kRows + 1);
+}
+
+template <typename T>
+struct StageSmem {
+    T *w;          // [N][12]
+    T *A;          // [N][4]
+    int8_t *relx;  // [N]
+    uint16_t *rows;
+    __device__ explicit StageSmem(unsigned char *base) {
+        w = (T *)base;
+        A = w + (size_t)Stage<T>::N * 12;
+        relx = (int8_t *)(A + (size_t)Stage<T>::N * 4);
+        rows = (uint16_t *)(relx + Stage<T>::N);
+    }
+};
+
+template <typename T, int KW, bool STAGED, bool COH>
+__device__ __forceinline__ bool gather_cell(int tx, int ty, int tz, const uint16_t *rs,
+                                            const int8_t *relx, const uint32_t *cand, const T *w_src,
+                                            const T *A_src, T acc[3]) {
     bool hit = false;
     acc[0] = acc[1] = acc[2] = T(0);
 #pragma unroll
     for (int dz = 0; dz < KW; ++dz) {
-        int rz = tz + 3 - (KW - 1) + dz;
+        const int rz = tz + 3 - (KW - 1) + dz, oz = KW - 1 - dz;
 #pragma unroll
         for (int dy = 0; dy < KW; ++dy) {
-            int ry = ty + 3 - (KW - 1) + dy;
-            int row = rz * kRow + ry;
-            int i0 = rs[row], i1 = rs[row + 1];
+            const int ry = ty + 3 - (KW - 1) + dy, oy = KW - 1 - dy;
+            const int row = rz * kRow + ry;
+            const int i0 = rs[row], i1 = rs[row + 1];
             for (int i = i0; i < i1; ++i) {
-                uint32_t m = cand[i];
-                uint64_t anc = __ldg((const unsigned long long *)anchor + m);
-                int ox = wrap_diff(cx, anchor_x(anc), g.n[0]);
-                if (ox < KW) {
-                    int oy = wrap_diff(cy, anchor_y(anc), g.n[1]);
-                    int oz = wrap_diff(cz, anchor_z(anc), g.n[2]);
-                    const T *w = wts + 12 * (size_t)m;
-                    T wt = w[ox] * w[4 + oy] * w[8 + oz];
-                    acc[0] += wt * ld<COH>(A + 4 * (size_t)m + 0);
-                    acc[1] += wt * ld<COH>(A + 4 * (size_t)m + 1);
-                    acc[2] += wt * ld<COH>(A + 4 * (size_t)m + 2);
+                const int ox = tx - (int)relx[i];
+                if ((unsigned)ox < (unsigned)KW) {
+                    const size_t k = STAGED ? (size_t)i : (size_t)cand[i];
+                    const T *w = w_src + 12 * k;
+                    const T *A = A_src + 4 * k;
+                    T wt, a0, a1, a2;
+                    if (STAGED) {
+                        wt = w[ox] * w[4 + oy] * w[8 + oz];
+                        a0 = A[0], a1 = A[1], a2 = A[2];
+                    } else {
+                        wt = __ldg(w + ox) * __ldg(w + 4 + oy) * __ldg(w + 8 + oz);
+                        a0 = ld<COH>(A), a1 = ld<COH>(A + 1), a2 = ld<COH>(A + 2);
+                    }
+                    acc[0] += wt * a0;
+                    acc[1] += wt * a1;
+                    acc[2] += wt * a2;
                     hit = true;
                 }
             }
@@ -620,26 +665,46 @@ __device__ __forceinline__ bool gather_cell(const DevGrid &g, int cx, int cy, in
     return hit;
 }
 
-// One tile (compact slot cs) of a gather phase: f += S A (spread) or
-// u += S A with f_out += S A / dt (forcing pass).
+// One tile (compact slot cs) of a gather phase: dst += S A, and, when f_out
+// is given (forcing pass), f_out += S A / dt.
 template <typename T, int KW, bool COH>
 __device__ __forceinline__ void gather_tile(const DevGrid &g, long long N, int cs, const Slots &sl,
-                                            const uint64_t *anchor, const T *wts, const T *A,
+                                            const T *__restrict__ wts, const T *A,
                                             T *__restrict__ dst, T *__restrict__ f_out, double inv_dt,
-                                            uint16_t *s_rows) {
-    int4 lo = sl.geo_lo[cs], dim = sl.geo_dim[cs];
+                                            StageSmem<T> &sm) {
+    const int4 lo = sl.geo_lo[cs], dim = sl.geo_dim[cs];
     const uint16_t *rs = sl.rows + (size_t)cs * (kRows + 1);
-    for (int i = threadIdx.x; i <= kRows; i += blockDim.x) s_rows[i] = rs[i];
+    for (int i = threadIdx.x; i <= kRows; i += blockDim.x) sm.rows[i] = rs[i];
     __syncthreads();
-    int tx = threadIdx.x & 7, ty = (threadIdx.x >> 3) & 7, tz = threadIdx.x >> 6;
+    const int nc = sm.rows[kRows];
+    const uint32_t *cand = sl.cand + dim.w;
+    const int8_t *relx = sl.relx + dim.w;
+    const bool staged = nc <= Stage<T>::N;
+    if (staged) {
+        for (int i = threadIdx.x; i < nc; i += blockDim.x) {
+            const uint32_t m = cand[i];
+            const T *wm = wts + 12 * (size_t)m;
+#pragma unroll
+            for (int k = 0; k < 3; ++k)
+#pragma unroll
+                for (int j = 0; j < KW; ++j) sm.w[12 * i + 4 * k + j] = __ldg(wm + 4 * k + j);
+#pragma unroll
+            for (int k = 0; k < 3; ++k) sm.A[4 * i + k] = ld<COH>(A + 4 * (size_t)m + k);
+            sm.relx[i] = relx[i];
+        }
+        __syncthreads();
+    }
+    const int tx = threadIdx.x & 7, ty = (threadIdx.x >> 3) & 7, tz = threadIdx.x >> 6;
     if (tx < dim.x && ty < dim.y && tz < dim.z) {
-        int cx = wrap_add(lo.x, tx, g.n[0]);
-        int cy = wrap_add(lo.y, ty, g.n[1]);
-        int cz = wrap_add(lo.z, tz, g.n[2]);
         T acc[3];
-        if (gather_cell<T, KW, COH>(g, cx, cy, cz, tx, ty, tz, s_rows, sl.cand + dim.w, anchor, wts, A,
-                                    acc)) {
-            long long c = ((long long)cz * g.n[1] + cy) * g.n[0] + cx;
+        const bool hit = staged
+                             ? gather_cell<T, KW, true, COH>(tx, ty, tz, sm.rows, sm.relx, cand, sm.w, sm.A, acc)
+                             : gather_cell<T, KW, false, COH>(tx, ty, tz, sm.rows, relx, cand, wts, A, acc);
+        if (hit) {
+            const int cx = wrap_add(lo.x, tx, g.n[0]);
+            const int cy = wrap_add(lo.y, ty, g.n[1]);
+            const int cz = wrap_add(lo.z, tz, g.n[2]);
+            const long long c = ((long long)cz * g.n[1] + cy) * g.n[0] + cx;
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
                 T *q = dst + k * N + c;
@@ -659,14 +724,14 @@ __device__ __forceinline__ void gather_tile(const DevGrid &g, long long N, int c
 
 template <typename T, int KER>
 __global__ void __launch_bounds__(kBlock) k_spread_gather(DevGrid g, const int *__restrict__ ncompact_p,
-                                                          Slots sl, const uint64_t *__restrict__ anchor,
-                                                          const T *__restrict__ wts, const T *__restrict__ A,
-                                                          T *__restrict__ f) {
-    __shared__ uint16_t s_rows[kRows + 1];
+                                                          Slots sl, const T *__restrict__ wts,
+                                                          const T *__restrict__ A, T *__restrict__ f) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    StageSmem<T> sm(smem_raw);
     long long N = (long long)g.n[0] * g.n[1] * g.n[2];
     int nc = *ncompact_p;
     for (int cs = blockIdx.x; cs < nc; cs += gridDim.x)
-        gather_tile<T, Kernel<KER>::W, false>(g, N, cs, sl, anchor, wts, A, f, (T *)nullptr, 0.0, s_rows);
+        gather_tile<T, Kernel<KER>::W, false>(g, N, cs, sl, wts, A, f, (T *)nullptr, 0.0, sm);
 }
 
 // ---------------------------------------------------------------------------
@@ -733,7 +798,8 @@ struct PassArgs {
 template <typename T, int KER>
 __global__ void __launch_bounds__(kBlock) k_mdf_passes(PassArgs<T> a) {
     constexpr int KW = Kernel<KER>::W;
-    __shared__ uint16_t s_rows[kRows + 1];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    StageSmem<T> sm(smem_raw);
     const DevGrid g = a.g;
     long long N = (long long)g.n[0] * g.n[1] * g.n[2];
     int nl = *a.nlev;
@@ -760,8 +826,7 @@ __global__ void __launch_bounds__(kBlock) k_mdf_passes(PassArgs<T> a) {
             if (!grid_sync(a.bar, a.st)) return;
             // gather phase over the level's tiles
             for (int cs = s0 + blockIdx.x; cs < s1; cs += gridDim.x)
-                gather_tile<T, KW, true>(g, N, cs, a.sl, a.ms.anchor, a.ms.wts, a.ms.A, a.u, a.f_out,
-                                         inv_dt, s_rows);
+                gather_tile<T, KW, true>(g, N, cs, a.sl, a.ms.wts, a.ms.A, a.u, a.f_out, inv_dt, sm);
             if (!grid_sync(a.bar, a.st)) return;
         }
     }
@@ -810,6 +875,7 @@ static int build_slots(ib_ctx *ctx, Arena &ar, const DevGrid &g, int M, int nden
     uint32_t *scratch = ar.take<uint32_t>(scan_workspace(ndense));
     sl.dense_of = ar.take<uint32_t>(ncompact_cap);
     sl.cand = ar.take<uint32_t>(cand_cap);
+    sl.relx = ar.take<int8_t>(cand_cap);
     sl.rows = ar.take<uint16_t>((size_t)ncompact_cap * (kRows + 1));
     sl.geo_lo = ar.take<int4>(ncompact_cap);
     sl.geo_dim = ar.take<int4>(ncompact_cap);
@@ -862,8 +928,10 @@ static int run_spread(ib_ctx *ctx, const DevGrid &g, int M, const double *X, con
     int *ncompact = nullptr;
     int rc = build_slots<KW>(ctx, ar, g, M, (int)ndense, sg, ms.anchor, nullptr, sl, ncompact, s);
     if (rc) return rc;
-    k_spread_gather<T, KER><<<ctx->sm_count * 4, kBlock, 0, s>>>(g, ncompact, sl, ms.anchor, ms.wts, ms.A,
-                                                                (T *)f);
+    cudaFuncSetAttribute(k_spread_gather<T, KER>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)stage_bytes<T>());
+    k_spread_gather<T, KER><<<ctx->sm_count * 2, kBlock, stage_bytes<T>(), s>>>(g, ncompact, sl, ms.wts, ms.A,
+                                                                               (T *)f);
     return check_launch("ib_spread");
 }
 
@@ -887,6 +955,8 @@ static int run_mdf(ib_ctx *ctx, const DevGrid &g, void *u, const ib_particles *p
     lo.lev_mbeg = ar.take<int>(P + 1);
     lo.nlev = ar.take<int>(1);
     int *lev_work = ar.take<int>(P + 1);
+    int *nbr_cnt = ar.take<int>(P);
+    int *nbr = ar.take<int>((size_t)P * kMaxNbr);
     int *lev_sbeg = ar.take<int>(P + 1);
     int *mperm = ar.take<int>(M > 0 ? M : 1);
     Barrier bar;
@@ -908,7 +978,9 @@ static int run_mdf(ib_ctx *ctx, const DevGrid &g, void *u, const ib_particles *p
     k_prep_particles<T, KER><<<P, kBlock, 0, s>>>(g, P, pp->Xr, pp->Ur, pp->Wr, pp->marker_offset, mk->R,
                                                  mk->dV, ms, F_out, rho, box_lo, box_dim, part_of,
                                                  ctx->status);
-    k_levels<<<1, 1024, 0, s>>>(g, P, order, KW, pp->Xr, rho, pp->marker_offset, lo, lev_work, ctx->status);
+    if (order == IB_ORDER_SEQUENTIAL)
+        k_conflicts<<<grid_blocks(P, 128, ctx->sm_count), 128, 0, s>>>(g, P, KW, pp->Xr, rho, nbr_cnt, nbr);
+    k_levels<<<1, 32, 0, s>>>(g, P, order, KW, pp->Xr, rho, pp->marker_offset, nbr_cnt, nbr, lo, lev_work);
     k_marker_perm<<<grid_blocks(M, 256, ctx->sm_count), 256, 0, s>>>(M, part_of, pp->marker_offset,
                                                                      lo.mbase, mperm);
     sg.part_of = part_of;
@@ -939,12 +1011,15 @@ static int run_mdf(ib_ctx *ctx, const DevGrid &g, void *u, const ib_particles *p
     a.bar = bar;
     a.st = ctx->status;
     int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mdf_passes<T, KER>, kBlock, 0);
+    const size_t smem = stage_bytes<T>();
+    cudaFuncSetAttribute(k_mdf_passes<T, KER>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mdf_passes<T, KER>, kBlock, smem);
     if (per_sm < 1) return set_error(IB_ERR_CUDA, "mdf kernel cannot be resident");
     int nblocks = per_sm * ctx->sm_count;
     void *args[] = {&a};
     PhaseTimer tpass(ctx, IB_PHASE_MDF_PASSES, s);
-    cudaError_t e = cudaLaunchCooperativeKernel((const void *)k_mdf_passes<T, KER>, nblocks, kBlock, args, 0, s);
+    cudaError_t e =
+        cudaLaunchCooperativeKernel((const void *)k_mdf_passes<T, KER>, nblocks, kBlock, args, smem, s);
     if (e != cudaSuccess) return set_error(IB_ERR_CUDA, "mdf launch: %s", cudaGetErrorString(e));
     return check_launch("ib_multidirect_forcing");
 }

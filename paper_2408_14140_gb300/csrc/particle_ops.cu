@@ -62,6 +62,7 @@ __global__ void __launch_bounds__(kVolThreads) k_volume(DevGrid g, const T *__re
         long long N = (long long)g.n[0] * g.n[1] * g.n[2];
         double h = g.h, h3 = h * h * h;
         double rin = Rp - 0.8661 * h, rout = Rp + 0.8661 * h;
+        double iR = 1.0 / Rp;
         double rin2 = rin > 0 ? rin * rin : -1.0, rout2 = rout * rout;
         long long plane = dims[0] * dims[1];
         for (long long kz = split; kz < dims[2]; kz += kVolSplit) {
@@ -77,14 +78,21 @@ __global__ void __launch_bounds__(kVolThreads) k_volume(DevGrid g, const T *__re
                 } else if (d2 > rout2) {
                     continue;
                 } else {
+                    // corner offsets in units of R along each axis (nodes at org + i h)
+                    double ax[2], ay[2], az[2];
+#pragma unroll
+                    for (int e = 0; e < 2; ++e) {
+                        ax[e] = (g.org[0] + (double)(i + e) * h - c[0]) * iR;
+                        ay[e] = (g.org[1] + (double)(j + e) * h - c[1]) * iR;
+                        az[e] = (g.org[2] + (double)(k + e) * h - c[2]) * iR;
+                        ax[e] *= ax[e];
+                        ay[e] *= ay[e];
+                        az[e] *= az[e];
+                    }
                     double num = 0.0, den = 0.0;
 #pragma unroll
                     for (int m = 0; m < 8; ++m) {
-                        double x = g.org[0] + (double)(i + (m & 1)) * h;
-                        double y = g.org[1] + (double)(j + ((m >> 1) & 1)) * h;
-                        double z = g.org[2] + (double)(k + ((m >> 2) & 1)) * h;
-                        double a = (x - c[0]) / Rp, b = (y - c[1]) / Rp, d = (z - c[2]) / Rp;
-                        double phi = sqrt(a * a + b * b + d * d) - 1.0;
+                        double phi = sqrt(ax[m & 1] + ay[(m >> 1) & 1] + az[(m >> 2) & 1]) - 1.0;
                         if (-phi > 0.0) num += -phi;
                         den += fabs(phi);
                     }
@@ -169,36 +177,44 @@ struct CollideArgs {
     double *Xnew;  // [P][3] scratch: positions are read by every thread
 };
 
+// One warp per particle i; lane k takes j = k, k + 32, ...; the lane partial
+// sums are combined by a fixed shuffle tree (deterministic).
 __global__ void k_collide_forces(CollideArgs a, double *__restrict__ Fc) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (i >= a.P) return;
-    double xi[3] = {a.Xr[3 * i], a.Xr[3 * i + 1], a.Xr[3 * i + 2]};
-    double Ri = a.radius[i];
-    double mi = a.rho_p[i] * 4.0 / 3.0 * kPi * Ri * Ri * Ri;
+    const double iL[3] = {1.0 / a.L[0], 1.0 / a.L[1], 1.0 / a.L[2]};
+    const double xi[3] = {a.Xr[3 * i], a.Xr[3 * i + 1], a.Xr[3 * i + 2]};
+    const double Ri = a.radius[i];
+    const double mi = a.rho_p[i] * 4.0 / 3.0 * kPi * Ri * Ri * Ri;
+    const double idc = 1.0 / a.d_c;
+    const double gscale = 0.5 * a.g_coll / a.eps_c;
     double f[3] = {0, 0, 0};
-    for (int j = 0; j < a.P; ++j) {
+    for (int j = lane; j < a.P; j += 32) {
         if (j == i) continue;
         double del[3], d2 = 0.0;
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            double dd = a.Xr[3 * j + k] - xi[k];
-            del[k] = dd - a.L[k] * nearbyint(dd / a.L[k]);
+            const double dd = a.Xr[3 * j + k] - xi[k];
+            del[k] = dd - a.L[k] * rint(dd * iL[k]);
             d2 += del[k] * del[k];
         }
-        double Rj = a.radius[j];
-        double Dc = Ri + Rj + a.d_c;
-        if (d2 < Dc * Dc) {
-            double d = sqrt(d2);
-            if (d < Dc && d > 0.0) {
-                double mj = a.rho_p[j] * 4.0 / 3.0 * kPi * Rj * Rj * Rj;
-                double q = (d - Dc) / a.d_c;
-                double coef = -(0.5 * (mi + mj) * a.g_coll / a.eps_c) * q * q / d;
+        const double Rj = a.radius[j];
+        const double Dc = Ri + Rj + a.d_c;
+        if (d2 < Dc * Dc && d2 > 0.0) {
+            const double d = sqrt(d2);
+            const double mj = a.rho_p[j] * 4.0 / 3.0 * kPi * Rj * Rj * Rj;
+            const double q = (d - Dc) * idc;
+            const double coef = -((mi + mj) * gscale) * q * q / d;
 #pragma unroll
-                for (int k = 0; k < 3; ++k) f[k] += coef * del[k];
-            }
+            for (int k = 0; k < 3; ++k) f[k] += coef * del[k];
         }
     }
-    for (int k = 0; k < 3; ++k) Fc[3 * i + k] = f[k];
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+        for (int o = 16; o > 0; o >>= 1) f[k] += __shfl_down_sync(0xffffffffu, f[k], o);
+    if (lane == 0)
+        for (int k = 0; k < 3; ++k) Fc[3 * i + k] = f[k];
 }
 
 __global__ void k_newton_euler(CollideArgs a, const double *__restrict__ Fc, DevStatus *st) {
@@ -320,7 +336,7 @@ int particle_collide_update(ib_ctx *ctx, ib_particles *parts, const ib_grid *gri
     cudaStream_t s = (cudaStream_t)stream;
     int nb = (parts->P + 127) / 128;
     PhaseTimer tm(ctx, IB_PHASE_COLLIDE, s);
-    k_collide_forces<<<nb, 128, 0, s>>>(a, Fc);
+    k_collide_forces<<<(parts->P + 3) / 4, 128, 0, s>>>(a, Fc);
     k_newton_euler<<<nb, 128, 0, s>>>(a, Fc, ctx->status);
     return check_launch("particle_collide_update");
 }
