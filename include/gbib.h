@@ -187,6 +187,32 @@ GBIB_API int particle_volume_integrals(ib_ctx *ctx, const ib_grid *grid, const v
                               const ib_particles *parts, double *Iu,
                               double *Irxu, double *vol, void *stream);
 
+/* ---- allocation-free volume integrals ----------------------------------
+ * The paper has no counterpart to this entry point; it exists for callers
+ * that cannot allocate device memory: code that runs while a CUDA stream is
+ * being captured (where cudaMalloc is not allowed), latency-critical loops
+ * that must not take cudaMalloc's implicit device synchronisation, and hosts
+ * whose device memory is all owned by another allocator.  It computes the
+ * same Iu, Irxu, vol as particle_volume_integrals (same kernel, same
+ * summation order) but takes no context: its per-particle partial sums live
+ * in a fixed array inside the library, sized for IB_STATIC_VOLUME_MAX_P
+ * particles (1.75 MiB of device memory, held on every device that loads the
+ * library until the process exits).
+ *  * P > IB_STATIC_VOLUME_MAX_P returns IB_ERR_INVALID (nothing is queued).
+ *  * The first call on a device looks up the array's device address (one
+ *    cudaGetSymbolAddress per device); make that first call before any
+ *    stream capture begins.  No call allocates or frees memory.
+ *  * Every call shares the one array and overwrites the part it uses, so
+ *    calls that overlap on the GPU (different streams, no ordering between
+ *    them) race and give wrong sums: order them on one stream or by events.
+ *  * Device-side input checks are not reported (there is no context to
+ *    latch them); non-finite inputs give non-finite sums.                  */
+#define IB_STATIC_VOLUME_MAX_P 2048
+GBIB_API int particle_volume_integrals_static(const ib_grid *grid, const void *u,
+                                              const ib_particles *parts,
+                                              double *Iu, double *Irxu,
+                                              double *vol, void *stream);
+
 /* ---- marker force and torque (Eqs. particle1, particle2, first terms) ---
  * F_ib[p] = -rho_f sum_l F[l] dV[l],  T_ib[p] = -rho_f sum_l R[l] x F[l] dV[l]
  * over the markers of particle p; FP64, overwritten.                      */

@@ -43,7 +43,7 @@ EXPORTS = ["ib_ctx_create", "ib_ctx_reserve", "ib_ctx_destroy", "ib_ctx_status",
            "ib_ctx_set_timing", "ib_ctx_read_timing",
            "ib_interpolate", "ib_spread", "ib_multidirect_forcing",
            "particle_volume_integrals", "particle_force_torque",
-           "particle_collide_update"]
+           "particle_collide_update", "particle_volume_integrals_static"]
 
 
 class IBError(RuntimeError):
@@ -99,6 +99,7 @@ def load(path: str = LIB_PATH):
         "ib_spread": (i, [p, p, i, p, p, p, i, p, p]),
         "ib_multidirect_forcing": (i, [p, p, p, p, p, i, d, i, i, p, p, p]),
         "particle_volume_integrals": (i, [p, p, p, p, p, p, p, p]),
+        "particle_volume_integrals_static": (i, [p, p, p, p, p, p, p]),
         "particle_force_torque": (i, [p, p, p, p, d, p, p, p]),
         "particle_collide_update": (i, [p, p, p, p, d, p, p, p, p, p, p, p, p]),
     }

@@ -6,6 +6,8 @@
 //     (Eqs. particle1, particle2) + centroid update (Eq. pr2).
 // All sums are FP64 and run in a fixed order (per-thread strided partials,
 // then a fixed shuffle tree), so results are bitwise reproducible.
+#include <mutex>
+
 #include "gbib_internal.cuh"
 
 namespace gbib {
@@ -256,6 +258,51 @@ static int run_volume(ib_ctx *ctx, const DevGrid &g, const void *u, const ib_par
     return check_launch("particle_volume_integrals");
 }
 
+// ---- allocation-free variant: scratch in a fixed device array -------------
+// kVolSplit * 7 partial sums per particle for up to IB_STATIC_VOLUME_MAX_P
+// particles (2048 * 16 * 7 doubles = 1.75 MiB).  Host code must not pass the
+// array's name to a kernel (that is a host-side stand-in); the device address
+// is looked up once per device with cudaGetSymbolAddress.
+static __device__ __align__(256) double g_volume_scratch[(size_t)IB_STATIC_VOLUME_MAX_P * kVolSplit * 7];
+static __device__ DevStatus g_volume_status;
+
+constexpr int kMaxDevices = 64;
+static std::mutex g_scratch_mu;
+static double *g_scratch_ptr[kMaxDevices] = {};
+static DevStatus *g_status_ptr[kMaxDevices] = {};
+
+static int static_scratch(double **scratch, DevStatus **status) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return set_error(IB_ERR_CUDA, "no current CUDA device");
+    if (dev < 0 || dev >= kMaxDevices) return set_error(IB_ERR_UNSUPPORTED, "device id %d too large", dev);
+    std::lock_guard<std::mutex> lock(g_scratch_mu);
+    if (!g_scratch_ptr[dev]) {
+        void *p = nullptr, *q = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_volume_scratch);
+        if (e != cudaSuccess) return set_error(IB_ERR_CUDA, "cudaGetSymbolAddress(scratch): %s", cudaGetErrorString(e));
+        e = cudaGetSymbolAddress(&q, g_volume_status);
+        if (e != cudaSuccess) return set_error(IB_ERR_CUDA, "cudaGetSymbolAddress(status): %s", cudaGetErrorString(e));
+        g_scratch_ptr[dev] = (double *)p;
+        g_status_ptr[dev] = (DevStatus *)q;
+    }
+    *scratch = g_scratch_ptr[dev];
+    *status = g_status_ptr[dev];
+    return IB_OK;
+}
+
+template <typename T>
+static int run_volume_static(const DevGrid &g, const void *u, const ib_particles *pp, double *Iu,
+                             double *Irxu, double *vol, cudaStream_t s) {
+    double *partial = nullptr;
+    DevStatus *st = nullptr;
+    int rc = static_scratch(&partial, &st);
+    if (rc) return rc;
+    k_volume<T><<<pp->P * kVolSplit, kVolThreads, 0, s>>>(g, (const T *)u, pp->P, pp->Xr, pp->radius, partial,
+                                                          st);
+    k_volume_final<<<(pp->P + 127) / 128, 128, 0, s>>>(pp->P, partial, Iu, Irxu, vol);
+    return check_launch("particle_volume_integrals_static");
+}
+
 }  // namespace gbib
 
 using namespace gbib;
@@ -275,6 +322,22 @@ int particle_volume_integrals(ib_ctx *ctx, const ib_grid *grid, const void *u, c
     if (grid->prec == IB_F64)
         return run_volume<double>(ctx, g, u, parts, Iu, Irxu, vol, (cudaStream_t)stream);
     return run_volume<float>(ctx, g, u, parts, Iu, Irxu, vol, (cudaStream_t)stream);
+}
+
+int particle_volume_integrals_static(const ib_grid *grid, const void *u, const ib_particles *parts,
+                                     double *Iu, double *Irxu, double *vol, void *stream) {
+    int rc = validate_grid(grid, 1);
+    if (rc) return rc;
+    if (!parts || parts->P < 0) return set_error(IB_ERR_INVALID, "bad particles");
+    if (parts->P > IB_STATIC_VOLUME_MAX_P)
+        return set_error(IB_ERR_INVALID, "particle_volume_integrals_static: P = %d exceeds the fixed maximum %d",
+                         parts->P, IB_STATIC_VOLUME_MAX_P);
+    if (parts->P == 0) return IB_OK;
+    if (!u || !parts->Xr || !parts->radius) return set_error(IB_ERR_INVALID, "NULL array");
+    DevGrid g = make_dev_grid(grid);
+    if (grid->prec == IB_F64)
+        return run_volume_static<double>(g, u, parts, Iu, Irxu, vol, (cudaStream_t)stream);
+    return run_volume_static<float>(g, u, parts, Iu, Irxu, vol, (cudaStream_t)stream);
 }
 
 int particle_force_torque(ib_ctx *ctx, const ib_particles *parts, const ib_markers *marks, const double *F,
