@@ -52,7 +52,7 @@ extern "C" {
 #define IB_ERR_CUDA (-3)         /* a CUDA runtime call failed                */
 #define IB_ERR_TIMEOUT (-4)      /* a bounded device-side wait gave up        */
 #define IB_ERR_NONFINITE (-5)    /* NaN/Inf in a particle or marker input     */
-#define IB_ERR_UNSUPPORTED (-6)  /* valid but outside this build's limits     */
+#define IB_ERR_UNSUPPORTED (-6)  /* valid but beyond the library's limits      */
 
 /* ---- enumerations ------------------------------------------------------ */
 typedef enum { IB_F64 = 0, IB_F32 = 1 } ib_prec;

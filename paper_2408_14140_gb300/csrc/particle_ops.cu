@@ -6,6 +6,7 @@
 //     (Eqs. particle1, particle2) + centroid update (Eq. pr2).
 // All sums are FP64 and run in a fixed order (per-thread strided partials,
 // then a fixed shuffle tree), so results are bitwise reproducible.
+#include <climits>
 #include <mutex>
 
 #include "gbib_internal.cuh"
@@ -38,101 +39,140 @@ __device__ __forceinline__ void block_sum(double v[NV]) {
 }
 
 // ---------------------------------------------------------------------------
-// volume integrals: grid = P * kVolSplit CTAs; CTA (p, s) takes the z-slabs
-// s, s + kVolSplit, ... of particle p's cell box.
+// volume integrals.  Grid = P * kVolSplit CTAs; CTA (p, s) walks a slab of
+// cell planes of particle p's box.  Per plane it evaluates the level set
+// phi = |x - X_r|/R - 1 once per node (only for nodes within 1.75 h of the
+// surface: the corners of every cell whose centre lies within 0.8661 h of the
+// surface), keeps two node planes in shared memory, and then visits, row by
+// row, only the cells whose centre lies within R + 0.8661 h.  Cells whose
+// centre lies deeper than R - 0.8661 h have all corners inside (alpha = 1);
+// the others form alpha from their eight corner values.  The last CTA of a
+// particle (completion counter) adds the kVolSplit partial sums in slab order.
 // ---------------------------------------------------------------------------
 constexpr int kVolSplit = 16;
-constexpr int kVolThreads = 256;
+constexpr int kVolThreads = 256;   // 8 warps; warp w takes rows w, w + 8, ...
+constexpr int kVolMaxBox = 64;     // cells per axis of one particle's box
+constexpr size_t kVolSmem = 2 * (kVolMaxBox + 1) * (kVolMaxBox + 1) * sizeof(double);
 
 template <typename T>
 __global__ void __launch_bounds__(kVolThreads) k_volume(DevGrid g, const T *__restrict__ u, int P,
                                                         const double *__restrict__ Xr,
                                                         const double *__restrict__ radius,
-                                                        double *__restrict__ partial, DevStatus *st) {
-    int p = blockIdx.x / kVolSplit, split = blockIdx.x % kVolSplit;
+                                                        double *__restrict__ partial,
+                                                        unsigned int *__restrict__ done, double *Iu,
+                                                        double *Irxu, double *vol, DevStatus *st) {
+    extern __shared__ double s_phi[];  // two node planes
+    __shared__ int s_last;
+    const int p = blockIdx.x / kVolSplit, split = blockIdx.x % kVolSplit;
     if (p >= P) return;
-    double c[3] = {Xr[3 * p], Xr[3 * p + 1], Xr[3 * p + 2]};
-    double Rp = radius[p];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const double c[3] = {Xr[3 * p], Xr[3 * p + 1], Xr[3 * p + 2]};
+    const double Rp = radius[p];
     double acc[7] = {0, 0, 0, 0, 0, 0, 0};
-    if (finite3(c) && isfinite(Rp) && Rp > 0.0) {
-        long long lo[3], dims[3];
+    bool ok = finite3(c) && isfinite(Rp) && Rp > 0.0;
+    if (!ok && threadIdx.x == 0 && split == 0) raise_status(st, IB_ERR_NONFINITE, p);
+    int lo[3] = {0, 0, 0}, dims[3] = {0, 0, 0};
+    if (ok) {
         for (int a = 0; a < 3; ++a) {
-            lo[a] = (long long)floor((c[a] - Rp - g.org[a]) * g.inv_h) - 1;
-            long long hi = (long long)floor((c[a] + Rp - g.org[a]) * g.inv_h) + 1;
-            dims[a] = hi - lo[a] + 1;
+            long long l = (long long)floor((c[a] - Rp - g.org[a]) * g.inv_h) - 1;
+            long long hgh = (long long)floor((c[a] + Rp - g.org[a]) * g.inv_h) + 1;
+            lo[a] = (int)l;
+            dims[a] = (int)(hgh - l + 1);
+            if (dims[a] > kVolMaxBox || dims[a] > g.n[a] || l < INT_MIN / 2 || l > INT_MAX / 2) ok = false;
         }
-        long long N = (long long)g.n[0] * g.n[1] * g.n[2];
-        double h = g.h, h3 = h * h * h;
-        double rin = Rp - 0.8661 * h, rout = Rp + 0.8661 * h;
-        double iR = 1.0 / Rp;
-        double rin2 = rin > 0 ? rin * rin : -1.0, rout2 = rout * rout;
-        long long plane = dims[0] * dims[1];
-        for (long long kz = split; kz < dims[2]; kz += kVolSplit) {
-            long long k = lo[2] + kz;
-            for (long long q = threadIdx.x; q < plane; q += blockDim.x) {
-                long long j = lo[1] + q / dims[0], i = lo[0] + q % dims[0];
-                double r[3] = {g.org[0] + ((double)i + 0.5) * h - c[0], g.org[1] + ((double)j + 0.5) * h - c[1],
-                               g.org[2] + ((double)k + 0.5) * h - c[2]};
-                double d2 = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
-                double al;
-                if (d2 < rin2) {
-                    al = 1.0;
-                } else if (d2 > rout2) {
-                    continue;
-                } else {
-                    // corner offsets in units of R along each axis (nodes at org + i h)
-                    double ax[2], ay[2], az[2];
-#pragma unroll
-                    for (int e = 0; e < 2; ++e) {
-                        ax[e] = (g.org[0] + (double)(i + e) * h - c[0]) * iR;
-                        ay[e] = (g.org[1] + (double)(j + e) * h - c[1]) * iR;
-                        az[e] = (g.org[2] + (double)(k + e) * h - c[2]) * iR;
-                        ax[e] *= ax[e];
-                        ay[e] *= ay[e];
-                        az[e] *= az[e];
-                    }
-                    double num = 0.0, den = 0.0;
-#pragma unroll
-                    for (int m = 0; m < 8; ++m) {
-                        double phi = sqrt(ax[m & 1] + ay[(m >> 1) & 1] + az[(m >> 2) & 1]) - 1.0;
-                        if (-phi > 0.0) num += -phi;
-                        den += fabs(phi);
-                    }
-                    al = den > 0.0 ? num / den : 0.5;
-                    if (al == 0.0) continue;
-                }
-                long long cc = ((long long)wrap_int(k, g.n[2]) * g.n[1] + wrap_int(j, g.n[1])) * g.n[0] +
-                               wrap_int(i, g.n[0]);
-                double uc[3] = {(double)u[cc], (double)u[N + cc], (double)u[2 * N + cc]};
-                double wv = al * h3;
-                acc[0] += wv * uc[0];
-                acc[1] += wv * uc[1];
-                acc[2] += wv * uc[2];
-                acc[3] += wv * (r[1] * uc[2] - r[2] * uc[1]);
-                acc[4] += wv * (r[2] * uc[0] - r[0] * uc[2]);
-                acc[5] += wv * (r[0] * uc[1] - r[1] * uc[0]);
-                acc[6] += wv;
+        if (!ok && threadIdx.x == 0 && split == 0) raise_status(st, IB_ERR_UNSUPPORTED, p);
+    }
+    const int t = (dims[2] + kVolSplit - 1) / kVolSplit;
+    const int z0 = split * t, z1 = min(dims[2], z0 + t);
+    if (ok && z0 < z1) {
+        const long long N = (long long)g.n[0] * g.n[1] * g.n[2];
+        const double h = g.h, iR = 1.0 / Rp;
+        const double rin = Rp - 0.8661 * h, rout = Rp + 0.8661 * h;
+        const double rin2 = rin > 0 ? rin * rin : -1.0, rout2 = rout * rout;
+        const double sl = fmax(0.0, Rp - 1.75 * h), sh = Rp + 1.75 * h;
+        const double sl2 = sl * sl, sh2 = sh * sh;
+        const int nx = dims[0] + 1, plane = nx * (dims[1] + 1);
+        const int lo0w = wrap_int(lo[0], g.n[0]);
+        auto node_plane = [&](int kn, double *buf) {
+            const double z = g.org[2] + (double)(lo[2] + kn) * h - c[2];
+            for (int q = threadIdx.x; q < plane; q += blockDim.x) {
+                const int j = q / nx, i = q - j * nx;
+                const double x = g.org[0] + (double)(lo[0] + i) * h - c[0];
+                const double y = g.org[1] + (double)(lo[1] + j) * h - c[1];
+                const double d2 = x * x + y * y + z * z;
+                buf[q] = (d2 > sl2 && d2 < sh2) ? sqrt(d2) * iR - 1.0 : 0.0;
             }
+        };
+        node_plane(z0, s_phi + (z0 & 1) * plane);
+        for (int kz = z0; kz < z1; ++kz) {
+            node_plane(kz + 1, s_phi + ((kz + 1) & 1) * plane);
+            __syncthreads();
+            const double *b0 = s_phi + (kz & 1) * plane, *b1 = s_phi + ((kz + 1) & 1) * plane;
+            const int k = lo[2] + kz;
+            const double rz = g.org[2] + ((double)k + 0.5) * h - c[2];
+            const int kw = wrap_int(k, g.n[2]);
+            for (int j = warp; j < dims[1]; j += kVolThreads / 32) {
+                const double ry = g.org[1] + ((double)(lo[1] + j) + 0.5) * h - c[1];
+                const double w2 = rout2 - ry * ry - rz * rz;
+                if (w2 < 0.0) continue;
+                const double half = sqrt(w2);
+                const int ia = max(0, (int)floor((c[0] - half - g.org[0]) * g.inv_h - 0.5) - lo[0]);
+                const int ib = min(dims[0] - 1, (int)ceil((c[0] + half - g.org[0]) * g.inv_h - 0.5) - lo[0]);
+                const long long rowbase = ((long long)kw * g.n[1] + wrap_int(lo[1] + j, g.n[1])) * g.n[0];
+                for (int i = ia + lane; i <= ib; i += 32) {
+                    const double rx = g.org[0] + ((double)(lo[0] + i) + 0.5) * h - c[0];
+                    const double d2 = rx * rx + ry * ry + rz * rz;
+                    if (d2 > rout2) continue;
+                    double al = 1.0;
+                    if (!(d2 < rin2)) {
+                        const int q = j * nx + i;
+                        const double ph[8] = {b0[q], b0[q + 1], b0[q + nx], b0[q + nx + 1],
+                                              b1[q], b1[q + 1], b1[q + nx], b1[q + nx + 1]};
+                        double num = 0.0, den = 0.0;
+#pragma unroll
+                        for (int m = 0; m < 8; ++m) {
+                            if (-ph[m] > 0.0) num += -ph[m];
+                            den += fabs(ph[m]);
+                        }
+                        al = den > 0.0 ? num / den : 0.5;
+                        if (al == 0.0) continue;
+                    }
+                    const long long cc = rowbase + wrap_add(lo0w, i, g.n[0]);
+                    const double u0 = (double)u[cc], u1 = (double)u[N + cc], u2 = (double)u[2 * N + cc];
+                    acc[0] += al * u0;
+                    acc[1] += al * u1;
+                    acc[2] += al * u2;
+                    acc[3] += al * (ry * u2 - rz * u1);
+                    acc[4] += al * (rz * u0 - rx * u2);
+                    acc[5] += al * (rx * u1 - ry * u0);
+                    acc[6] += al;
+                }
+            }
+            __syncthreads();
         }
-    } else if (threadIdx.x == 0 && split == 0) {
-        raise_status(st, IB_ERR_NONFINITE, p);
+        const double h3 = h * h * h;
+#pragma unroll
+        for (int k = 0; k < 7; ++k) acc[k] *= h3;
     }
     block_sum<7>(acc);
-    if (threadIdx.x == 0)
-        for (int k = 0; k < 7; ++k) partial[((size_t)p * kVolSplit + split) * 7 + k] = acc[k];
-}
-
-__global__ void k_volume_final(int P, const double *__restrict__ partial, double *Iu, double *Irxu,
-                               double *vol) {
-    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x) {
-        double s[7] = {0, 0, 0, 0, 0, 0, 0};
+    if (threadIdx.x == 0) {
+        double *dst = partial + ((size_t)p * kVolSplit + split) * 7;
+        for (int k = 0; k < 7; ++k) dst[k] = acc[k];
+        __threadfence();
+        s_last = atomicAdd(done + p, 1u) == kVolSplit - 1;
+    }
+    __syncthreads();
+    if (s_last && threadIdx.x == 0) {
+        __threadfence();
+        double sum[7] = {0, 0, 0, 0, 0, 0, 0};
         for (int sp = 0; sp < kVolSplit; ++sp)
-            for (int k = 0; k < 7; ++k) s[k] += partial[((size_t)p * kVolSplit + sp) * 7 + k];
+            for (int k = 0; k < 7; ++k) sum[k] += __ldcg(partial + ((size_t)p * kVolSplit + sp) * 7 + k);
         if (Iu)
-            for (int a = 0; a < 3; ++a) Iu[3 * p + a] = s[a];
+            for (int a = 0; a < 3; ++a) Iu[3 * p + a] = sum[a];
         if (Irxu)
-            for (int a = 0; a < 3; ++a) Irxu[3 * p + a] = s[3 + a];
-        if (vol) vol[p] = s[6];
+            for (int a = 0; a < 3; ++a) Irxu[3 * p + a] = sum[3 + a];
+        if (vol) vol[p] = sum[6];
+        done[p] = 0;  // ready for the next call
     }
 }
 
@@ -249,12 +289,14 @@ static int run_volume(ib_ctx *ctx, const DevGrid &g, const void *u, const ib_par
                       double *Irxu, double *vol, cudaStream_t s) {
     Arena ar(ctx);
     double *partial = ar.take<double>((size_t)pp->P * kVolSplit * 7);
+    unsigned int *done = ar.take<unsigned int>(pp->P);
     if (!ar.ok())
         return oom_error(ar.used, ar.cap);
     PhaseTimer tm(ctx, IB_PHASE_VOLUME, s);
-    k_volume<T><<<pp->P * kVolSplit, kVolThreads, 0, s>>>(g, (const T *)u, pp->P, pp->Xr, pp->radius, partial,
-                                                          ctx->status);
-    k_volume_final<<<(pp->P + 127) / 128, 128, 0, s>>>(pp->P, partial, Iu, Irxu, vol);
+    cudaMemsetAsync(done, 0, sizeof(unsigned int) * pp->P, s);
+    cudaFuncSetAttribute(k_volume<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kVolSmem);
+    k_volume<T><<<pp->P * kVolSplit, kVolThreads, kVolSmem, s>>>(g, (const T *)u, pp->P, pp->Xr, pp->radius,
+                                                                 partial, done, Iu, Irxu, vol, ctx->status);
     return check_launch("particle_volume_integrals");
 }
 
@@ -265,28 +307,39 @@ static int run_volume(ib_ctx *ctx, const DevGrid &g, const void *u, const ib_par
 // is looked up once per device with cudaGetSymbolAddress.
 static __device__ __align__(256) double g_volume_scratch[(size_t)IB_STATIC_VOLUME_MAX_P * kVolSplit * 7];
 static __device__ DevStatus g_volume_status;
+// completion counters of the final reduction; zero at load, reset by each call
+static __device__ unsigned int g_volume_done[IB_STATIC_VOLUME_MAX_P];
 
 constexpr int kMaxDevices = 64;
 static std::mutex g_scratch_mu;
 static double *g_scratch_ptr[kMaxDevices] = {};
 static DevStatus *g_status_ptr[kMaxDevices] = {};
+static unsigned int *g_done_ptr[kMaxDevices] = {};
 
-static int static_scratch(double **scratch, DevStatus **status) {
+static int static_scratch(double **scratch, DevStatus **status, unsigned int **done) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return set_error(IB_ERR_CUDA, "no current CUDA device");
     if (dev < 0 || dev >= kMaxDevices) return set_error(IB_ERR_UNSUPPORTED, "device id %d too large", dev);
     std::lock_guard<std::mutex> lock(g_scratch_mu);
     if (!g_scratch_ptr[dev]) {
-        void *p = nullptr, *q = nullptr;
+        void *p = nullptr, *q = nullptr, *r = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_volume_scratch);
         if (e != cudaSuccess) return set_error(IB_ERR_CUDA, "cudaGetSymbolAddress(scratch): %s", cudaGetErrorString(e));
         e = cudaGetSymbolAddress(&q, g_volume_status);
         if (e != cudaSuccess) return set_error(IB_ERR_CUDA, "cudaGetSymbolAddress(status): %s", cudaGetErrorString(e));
+        e = cudaGetSymbolAddress(&r, g_volume_done);
+        if (e != cudaSuccess) return set_error(IB_ERR_CUDA, "cudaGetSymbolAddress(done): %s", cudaGetErrorString(e));
+        e = cudaFuncSetAttribute(k_volume<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kVolSmem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_volume<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kVolSmem);
+        if (e != cudaSuccess) return set_error(IB_ERR_CUDA, "volume kernel attribute: %s", cudaGetErrorString(e));
         g_scratch_ptr[dev] = (double *)p;
         g_status_ptr[dev] = (DevStatus *)q;
+        g_done_ptr[dev] = (unsigned int *)r;
     }
     *scratch = g_scratch_ptr[dev];
     *status = g_status_ptr[dev];
+    *done = g_done_ptr[dev];
     return IB_OK;
 }
 
@@ -295,11 +348,11 @@ static int run_volume_static(const DevGrid &g, const void *u, const ib_particles
                              double *Irxu, double *vol, cudaStream_t s) {
     double *partial = nullptr;
     DevStatus *st = nullptr;
-    int rc = static_scratch(&partial, &st);
+    unsigned int *done = nullptr;
+    int rc = static_scratch(&partial, &st, &done);
     if (rc) return rc;
-    k_volume<T><<<pp->P * kVolSplit, kVolThreads, 0, s>>>(g, (const T *)u, pp->P, pp->Xr, pp->radius, partial,
-                                                          st);
-    k_volume_final<<<(pp->P + 127) / 128, 128, 0, s>>>(pp->P, partial, Iu, Irxu, vol);
+    k_volume<T><<<pp->P * kVolSplit, kVolThreads, kVolSmem, s>>>(g, (const T *)u, pp->P, pp->Xr, pp->radius,
+                                                                 partial, done, Iu, Irxu, vol, st);
     return check_launch("particle_volume_integrals_static");
 }
 
