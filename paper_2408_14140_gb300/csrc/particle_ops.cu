@@ -78,7 +78,7 @@ __global__ void __launch_bounds__(kVolThreads) k_volume(DevGrid g, const T *__re
             long long hgh = (long long)floor((c[a] + Rp - g.org[a]) * g.inv_h) + 1;
             lo[a] = (int)l;
             dims[a] = (int)(hgh - l + 1);
-            if (dims[a] > kVolMaxBox || dims[a] > g.n[a] || l < INT_MIN / 2 || l > INT_MAX / 2) ok = false;
+            if (dims[a] > g.n[a] || l < INT_MIN / 2 || l > INT_MAX / 2) ok = false;
         }
         if (!ok && threadIdx.x == 0 && split == 0) raise_status(st, IB_ERR_UNSUPPORTED, p);
     }
@@ -92,8 +92,12 @@ __global__ void __launch_bounds__(kVolThreads) k_volume(DevGrid g, const T *__re
         const double sl = fmax(0.0, Rp - 1.75 * h), sh = Rp + 1.75 * h;
         const double sl2 = sl * sl, sh2 = sh * sh;
         const int nx = dims[0] + 1, plane = nx * (dims[1] + 1);
+        // boxes wider than kVolMaxBox evaluate the corners of each boundary
+        // cell directly instead of sharing node values through shared memory
+        const bool shared_nodes = dims[0] <= kVolMaxBox && dims[1] <= kVolMaxBox;
         const int lo0w = wrap_int(lo[0], g.n[0]);
         auto node_plane = [&](int kn, double *buf) {
+            if (!shared_nodes) return;
             const double z = g.org[2] + (double)(lo[2] + kn) * h - c[2];
             for (int q = threadIdx.x; q < plane; q += blockDim.x) {
                 const int j = q / nx, i = q - j * nx;
@@ -125,9 +129,20 @@ __global__ void __launch_bounds__(kVolThreads) k_volume(DevGrid g, const T *__re
                     if (d2 > rout2) continue;
                     double al = 1.0;
                     if (!(d2 < rin2)) {
-                        const int q = j * nx + i;
-                        const double ph[8] = {b0[q], b0[q + 1], b0[q + nx], b0[q + nx + 1],
-                                              b1[q], b1[q + 1], b1[q + nx], b1[q + nx + 1]};
+                        double ph[8];
+                        if (shared_nodes) {
+                            const int q = j * nx + i;
+                            ph[0] = b0[q], ph[1] = b0[q + 1], ph[2] = b0[q + nx], ph[3] = b0[q + nx + 1];
+                            ph[4] = b1[q], ph[5] = b1[q + 1], ph[6] = b1[q + nx], ph[7] = b1[q + nx + 1];
+                        } else {
+#pragma unroll
+                            for (int m = 0; m < 8; ++m) {
+                                const double x = g.org[0] + (double)(lo[0] + i + (m & 1)) * h - c[0];
+                                const double y = g.org[1] + (double)(lo[1] + j + ((m >> 1) & 1)) * h - c[1];
+                                const double z = g.org[2] + (double)(k + ((m >> 2) & 1)) * h - c[2];
+                                ph[m] = sqrt(x * x + y * y + z * z) * iR - 1.0;
+                            }
+                        }
                         double num = 0.0, den = 0.0;
 #pragma unroll
                         for (int m = 0; m < 8; ++m) {
