@@ -196,7 +196,7 @@ GBIB_API int particle_volume_integrals(ib_ctx *ctx, const ib_grid *grid, const v
  * same Iu, Irxu, vol as particle_volume_integrals (same kernel, same
  * summation order) but takes no context: its per-particle partial sums live
  * in a fixed array inside the library, sized for IB_STATIC_VOLUME_MAX_P
- * particles (1.75 MiB of device memory, held on every device that loads the
+ * particles (896 KiB of device memory, held on every device that loads the
  * library until the process exits).
  *  * P > IB_STATIC_VOLUME_MAX_P returns IB_ERR_INVALID (nothing is queued).
  *  * The first call on a device looks up the array's device address (one

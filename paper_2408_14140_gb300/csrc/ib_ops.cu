@@ -626,6 +626,38 @@ struct StageSmem {
     }
 };
 
+// Per-wavefront staging of the tiles one CTA owns in the persistent kernel:
+// their row tables, candidate ids, x offsets and weights are loaded once per
+// wavefront and reused by all Ns passes; each pass then reloads only the
+// candidates' spread sources.  Wavefronts whose tiles do not fit fall back to
+// per-tile staging.
+template <typename T> struct LvlStage;
+template <> struct LvlStage<float> { static constexpr int REC = 1536; };
+template <> struct LvlStage<double> { static constexpr int REC = 768; };
+constexpr int kMaxMyTiles = 24;
+
+template <typename T>
+constexpr size_t lvl_stage_bytes() {
+    return (size_t)LvlStage<T>::REC * (12 + 4) * sizeof(T) + (size_t)LvlStage<T>::REC * 5 +
+           (size_t)kMaxMyTiles * (kRows + 1) * 2;
+}
+
+template <typename T>
+struct LvlSmem {
+    T *w;           // [REC][12]
+    T *A;           // [REC][4]
+    uint32_t *ids;  // [REC]
+    int8_t *relx;   // [REC]
+    uint16_t *rows; // [kMaxMyTiles][kRows+1]
+    __device__ explicit LvlSmem(unsigned char *base) {
+        w = (T *)base;
+        A = w + (size_t)LvlStage<T>::REC * 12;
+        ids = (uint32_t *)(A + (size_t)LvlStage<T>::REC * 4);
+        relx = (int8_t *)(ids + LvlStage<T>::REC);
+        rows = (uint16_t *)(relx + LvlStage<T>::REC);
+    }
+};
+
 template <typename T, int KW, bool STAGED, bool COH>
 __device__ __forceinline__ bool gather_cell(int tx, int ty, int tz, const uint16_t *rs,
                                             const int8_t *relx, const uint32_t *cand, const T *w_src,
@@ -796,7 +828,7 @@ struct PassArgs {
 };
 
 template <typename T, int KER>
-__global__ void __launch_bounds__(kBlock) k_mdf_passes(PassArgs<T> a) {
+__global__ void __launch_bounds__(kBlock, 2) k_mdf_passes(PassArgs<T> a) {
     constexpr int KW = Kernel<KER>::W;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     StageSmem<T> sm(smem_raw);
@@ -806,9 +838,52 @@ __global__ void __launch_bounds__(kBlock) k_mdf_passes(PassArgs<T> a) {
     double inv_dt = 1.0 / a.dt;
     int gtid = blockIdx.x * blockDim.x + threadIdx.x;
     int gsz = gridDim.x * blockDim.x;
+    LvlSmem<T> lv(smem_raw);
+    __shared__ int s_nmine, s_total, s_staged;
+    __shared__ int s_off[kMaxMyTiles + 1];
+    __shared__ int4 s_lo[kMaxMyTiles], s_dim[kMaxMyTiles];
+    const int tx = threadIdx.x & 7, ty = (threadIdx.x >> 3) & 7, tz = threadIdx.x >> 6;
     for (int L = 0; L < nl; ++L) {
         int m0 = a.lev_mbeg[L], m1 = a.lev_mbeg[L + 1];
         int s0 = a.lev_sbeg[L], s1 = a.lev_sbeg[L + 1];
+        // stage this CTA's tiles of the wavefront (tiles s0 + blockIdx.x + k gridDim.x)
+        if (threadIdx.x == 0) {
+            int nmine = s1 > s0 + (int)blockIdx.x ? (s1 - s0 - (int)blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
+            int tot = 0, ok = nmine <= kMaxMyTiles;
+            for (int k = 0; ok && k < nmine; ++k) {
+                const int cs = s0 + blockIdx.x + k * gridDim.x;
+                s_off[k] = tot;
+                s_lo[k] = a.sl.geo_lo[cs];
+                s_dim[k] = a.sl.geo_dim[cs];
+                tot += a.sl.rows[(size_t)cs * (kRows + 1) + kRows];
+            }
+            s_off[ok ? nmine : 0] = tot;
+            s_nmine = nmine;
+            s_total = tot;
+            s_staged = ok && tot <= LvlStage<T>::REC;
+        }
+        __syncthreads();
+        const bool staged = s_staged;
+        const int nmine = s_nmine;
+        if (staged) {
+            for (int k = 0; k < nmine; ++k) {
+                const int cs = s0 + blockIdx.x + k * gridDim.x;
+                const uint16_t *rs = a.sl.rows + (size_t)cs * (kRows + 1);
+                for (int i = threadIdx.x; i <= kRows; i += blockDim.x) lv.rows[k * (kRows + 1) + i] = rs[i];
+                const int b = s_dim[k].w, off = s_off[k], nc = s_off[k + 1] - off;
+                for (int i = threadIdx.x; i < nc; i += blockDim.x) {
+                    const uint32_t mk = a.sl.cand[b + i];
+                    lv.ids[off + i] = mk;
+                    lv.relx[off + i] = a.sl.relx[b + i];
+                    const T *wm = a.ms.wts + 12 * (size_t)mk;
+#pragma unroll
+                    for (int q = 0; q < 3; ++q)
+#pragma unroll
+                        for (int j = 0; j < KW; ++j) lv.w[12 * (off + i) + 4 * q + j] = __ldg(wm + 4 * q + j);
+                }
+            }
+            __syncthreads();
+        }
         for (int m = 0; m < a.Ns; ++m) {
             // interpolation phase: U = J u, F += (U^d - U)/dt, A = (U^d - U) dV / h^3
             for (int i = m0 + gtid; i < m1; i += gsz) {
@@ -825,8 +900,62 @@ __global__ void __launch_bounds__(kBlock) k_mdf_passes(PassArgs<T> a) {
             }
             if (!grid_sync(a.bar, a.st)) return;
             // gather phase over the level's tiles
-            for (int cs = s0 + blockIdx.x; cs < s1; cs += gridDim.x)
-                gather_tile<T, KW, true>(g, N, cs, a.sl, a.ms.wts, a.ms.A, a.u, a.f_out, inv_dt, sm);
+            if (staged) {
+                const int tot = s_total;
+                for (int i = threadIdx.x; i < tot; i += blockDim.x) {
+                    const T *src = a.ms.A + 4 * (size_t)lv.ids[i];
+                    lv.A[4 * i + 0] = __ldcg(src + 0);
+                    lv.A[4 * i + 1] = __ldcg(src + 1);
+                    lv.A[4 * i + 2] = __ldcg(src + 2);
+                }
+                __syncthreads();
+                // software pipeline over the CTA's tiles: the u loads of tile k
+                // are in flight while tile k + 1 is summed
+                T pacc[3], pu[3], pf[3];
+                long long pc = -1;
+                for (int k = 0; k <= nmine; ++k) {
+                    T acc[3];
+                    long long c = -1;
+                    T uo[3], fo[3];
+                    if (k < nmine) {
+                        const int4 dim = s_dim[k];
+                        const int off = s_off[k];
+                        if (tx < dim.x && ty < dim.y && tz < dim.z &&
+                            gather_cell<T, KW, true, true>(tx, ty, tz, lv.rows + k * (kRows + 1), lv.relx + off,
+                                                           nullptr, lv.w + 12 * (size_t)off, lv.A + 4 * (size_t)off,
+                                                           acc)) {
+                            const int4 lo = s_lo[k];
+                            c = ((long long)wrap_add(lo.z, tz, g.n[2]) * g.n[1] + wrap_add(lo.y, ty, g.n[1])) *
+                                    g.n[0] +
+                                wrap_add(lo.x, tx, g.n[0]);
+#pragma unroll
+                            for (int q = 0; q < 3; ++q) uo[q] = __ldcg(a.u + q * N + c);
+                            if (a.f_out)
+#pragma unroll
+                                for (int q = 0; q < 3; ++q) fo[q] = __ldcg(a.f_out + q * N + c);
+                        }
+                    }
+                    if (pc >= 0) {
+#pragma unroll
+                        for (int q = 0; q < 3; ++q) a.u[q * N + pc] = pu[q] + pacc[q];
+                        if (a.f_out)
+#pragma unroll
+                            for (int q = 0; q < 3; ++q) a.f_out[q * N + pc] = pf[q] + (T)(pacc[q] * inv_dt);
+                    }
+                    pc = c;
+                    if (c >= 0) {
+#pragma unroll
+                        for (int q = 0; q < 3; ++q) {
+                            pacc[q] = acc[q];
+                            pu[q] = uo[q];
+                            pf[q] = a.f_out ? fo[q] : T(0);
+                        }
+                    }
+                }
+            } else {
+                for (int cs = s0 + blockIdx.x; cs < s1; cs += gridDim.x)
+                    gather_tile<T, KW, true>(g, N, cs, a.sl, a.ms.wts, a.ms.A, a.u, a.f_out, inv_dt, sm);
+            }
             if (!grid_sync(a.bar, a.st)) return;
         }
     }
@@ -1011,7 +1140,7 @@ static int run_mdf(ib_ctx *ctx, const DevGrid &g, void *u, const ib_particles *p
     a.bar = bar;
     a.st = ctx->status;
     int per_sm = 0;
-    const size_t smem = stage_bytes<T>();
+    const size_t smem = stage_bytes<T>() > lvl_stage_bytes<T>() ? stage_bytes<T>() : lvl_stage_bytes<T>();
     cudaFuncSetAttribute(k_mdf_passes<T, KER>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mdf_passes<T, KER>, kBlock, smem);
     if (per_sm < 1) return set_error(IB_ERR_CUDA, "mdf kernel cannot be resident");

@@ -49,11 +49,18 @@ __device__ __forceinline__ void block_sum(double v[NV]) {
 // the others form alpha from their eight corner values.  The last CTA of a
 // particle (completion counter) adds the kVolSplit partial sums in slab order.
 // ---------------------------------------------------------------------------
-constexpr int kVolSplit = 16;
+constexpr int kVolSplit = 8;
 constexpr int kVolThreads = 256;   // 8 warps; warp w takes rows w, w + 8, ...
-constexpr int kVolMaxBox = 64;     // cells per axis of one particle's box
-constexpr size_t kVolSmem = 2 * (kVolMaxBox + 1) * (kVolMaxBox + 1) * sizeof(double);
+constexpr int kVolMaxBox = 64;     // cells per axis of one particle's box (shared-node path)
+constexpr int kVolAx = kVolMaxBox + 1;
+// two node planes + per-axis tables (node squares, cell offsets, cell squares)
+constexpr size_t kVolSmem = (2 * kVolAx * kVolAx + 9 * kVolAx) * sizeof(double);
 
+// Most of this kernel's cost is GB300's low FP64 rate, so FP64 work is
+// kept per node and per row where possible: squared node and cell-centre
+// offsets along each axis are tabulated once per CTA; a node plane computes
+// phi only inside the surface shell, whose x-range per node row is known in
+// closed form; a cell row visits only cells within R + 0.8661 h.
 template <typename T>
 __global__ void __launch_bounds__(kVolThreads) k_volume(DevGrid g, const T *__restrict__ u, int P,
                                                         const double *__restrict__ Xr,
@@ -61,7 +68,7 @@ __global__ void __launch_bounds__(kVolThreads) k_volume(DevGrid g, const T *__re
                                                         double *__restrict__ partial,
                                                         unsigned int *__restrict__ done, double *Iu,
                                                         double *Irxu, double *vol, DevStatus *st) {
-    extern __shared__ double s_phi[];  // two node planes
+    extern __shared__ double s_vol[];
     __shared__ int s_last;
     const int p = blockIdx.x / kVolSplit, split = blockIdx.x % kVolSplit;
     if (p >= P) return;
@@ -91,46 +98,72 @@ __global__ void __launch_bounds__(kVolThreads) k_volume(DevGrid g, const T *__re
         const double rin2 = rin > 0 ? rin * rin : -1.0, rout2 = rout * rout;
         const double sl = fmax(0.0, Rp - 1.75 * h), sh = Rp + 1.75 * h;
         const double sl2 = sl * sl, sh2 = sh * sh;
+        const bool tab = dims[0] <= kVolMaxBox && dims[1] <= kVolMaxBox && dims[2] <= kVolMaxBox;
         const int nx = dims[0] + 1, plane = nx * (dims[1] + 1);
-        // boxes wider than kVolMaxBox evaluate the corners of each boundary
-        // cell directly instead of sharing node values through shared memory
-        const bool shared_nodes = dims[0] <= kVolMaxBox && dims[1] <= kVolMaxBox;
-        const int lo0w = wrap_int(lo[0], g.n[0]);
+        double *phi2 = s_vol;                    // [2][plane]
+        double *tb = s_vol + 2 * kVolAx * kVolAx;  // [9][kVolAx]
+        // tb[a*kVolAx + i]: node offset^2 along axis a; tb[(3+a)*..]: cell-centre offset;
+        // tb[(6+a)*..]: cell-centre offset^2
+        if (tab) {
+            for (int a = 0; a < 3; ++a)
+                for (int i = threadIdx.x; i <= dims[a]; i += blockDim.x) {
+                    const double xn = g.org[a] + (double)(lo[a] + i) * h - c[a];
+                    const double xc = g.org[a] + ((double)(lo[a] + i) + 0.5) * h - c[a];
+                    tb[a * kVolAx + i] = xn * xn;
+                    tb[(3 + a) * kVolAx + i] = xc;
+                    tb[(6 + a) * kVolAx + i] = xc * xc;
+                }
+            __syncthreads();
+        }
+        auto cell_off = [&](int a, int i) -> double {
+            return tab ? tb[(3 + a) * kVolAx + i] : g.org[a] + ((double)(lo[a] + i) + 0.5) * h - c[a];
+        };
+        auto cell_sq = [&](int a, int i) -> double {
+            if (tab) return tb[(6 + a) * kVolAx + i];
+            const double x = cell_off(a, i);
+            return x * x;
+        };
         auto node_plane = [&](int kn, double *buf) {
-            if (!shared_nodes) return;
-            const double z = g.org[2] + (double)(lo[2] + kn) * h - c[2];
-            for (int q = threadIdx.x; q < plane; q += blockDim.x) {
-                const int j = q / nx, i = q - j * nx;
-                const double x = g.org[0] + (double)(lo[0] + i) * h - c[0];
-                const double y = g.org[1] + (double)(lo[1] + j) * h - c[1];
-                const double d2 = x * x + y * y + z * z;
-                buf[q] = (d2 > sl2 && d2 < sh2) ? sqrt(d2) * iR - 1.0 : 0.0;
+            if (!tab) return;
+            const double zz = tb[2 * kVolAx + kn];
+            for (int j = warp; j <= dims[1]; j += kVolThreads / 32) {
+                const double dyz = tb[kVolAx + j] + zz;
+                if (dyz >= sh2) continue;
+                // shell nodes of this row: sl2 < x^2 + dyz < sh2
+                const double xo = sqrt(sh2 - dyz);
+                const int i_lo = max(0, (int)floor((c[0] - xo - g.org[0]) * g.inv_h) - lo[0] - 1);
+                const int i_hi = min(dims[0], (int)ceil((c[0] + xo - g.org[0]) * g.inv_h) - lo[0] + 1);
+                for (int i = i_lo + lane; i <= i_hi; i += 32) {
+                    const double d2 = tb[i] + dyz;
+                    if (d2 >= sl2 && d2 < sh2) buf[j * nx + i] = sqrt(d2) * iR - 1.0;
+                }
             }
         };
-        node_plane(z0, s_phi + (z0 & 1) * plane);
+        const int lo0w = wrap_int(lo[0], g.n[0]);
+        node_plane(z0, phi2 + (z0 & 1) * plane);
         for (int kz = z0; kz < z1; ++kz) {
-            node_plane(kz + 1, s_phi + ((kz + 1) & 1) * plane);
+            node_plane(kz + 1, phi2 + ((kz + 1) & 1) * plane);
             __syncthreads();
-            const double *b0 = s_phi + (kz & 1) * plane, *b1 = s_phi + ((kz + 1) & 1) * plane;
+            const double *b0 = phi2 + (kz & 1) * plane, *b1 = phi2 + ((kz + 1) & 1) * plane;
             const int k = lo[2] + kz;
-            const double rz = g.org[2] + ((double)k + 0.5) * h - c[2];
+            const double rz = cell_off(2, kz), rz2 = cell_sq(2, kz);
             const int kw = wrap_int(k, g.n[2]);
             for (int j = warp; j < dims[1]; j += kVolThreads / 32) {
-                const double ry = g.org[1] + ((double)(lo[1] + j) + 0.5) * h - c[1];
-                const double w2 = rout2 - ry * ry - rz * rz;
+                const double ry = cell_off(1, j);
+                const double ryz2 = cell_sq(1, j) + rz2;
+                const double w2 = rout2 - ryz2;
                 if (w2 < 0.0) continue;
                 const double half = sqrt(w2);
                 const int ia = max(0, (int)floor((c[0] - half - g.org[0]) * g.inv_h - 0.5) - lo[0]);
                 const int ib = min(dims[0] - 1, (int)ceil((c[0] + half - g.org[0]) * g.inv_h - 0.5) - lo[0]);
                 const long long rowbase = ((long long)kw * g.n[1] + wrap_int(lo[1] + j, g.n[1])) * g.n[0];
                 for (int i = ia + lane; i <= ib; i += 32) {
-                    const double rx = g.org[0] + ((double)(lo[0] + i) + 0.5) * h - c[0];
-                    const double d2 = rx * rx + ry * ry + rz * rz;
+                    const double d2 = cell_sq(0, i) + ryz2;
                     if (d2 > rout2) continue;
                     double al = 1.0;
                     if (!(d2 < rin2)) {
                         double ph[8];
-                        if (shared_nodes) {
+                        if (tab) {
                             const int q = j * nx + i;
                             ph[0] = b0[q], ph[1] = b0[q + 1], ph[2] = b0[q + nx], ph[3] = b0[q + nx + 1];
                             ph[4] = b1[q], ph[5] = b1[q + 1], ph[6] = b1[q + nx], ph[7] = b1[q + nx + 1];
@@ -152,6 +185,7 @@ __global__ void __launch_bounds__(kVolThreads) k_volume(DevGrid g, const T *__re
                         al = den > 0.0 ? num / den : 0.5;
                         if (al == 0.0) continue;
                     }
+                    const double rx = cell_off(0, i);
                     const long long cc = rowbase + wrap_add(lo0w, i, g.n[0]);
                     const double u0 = (double)u[cc], u1 = (double)u[N + cc], u2 = (double)u[2 * N + cc];
                     acc[0] += al * u0;
@@ -317,7 +351,7 @@ static int run_volume(ib_ctx *ctx, const DevGrid &g, const void *u, const ib_par
 
 // ---- allocation-free variant: scratch in a fixed device array -------------
 // kVolSplit * 7 partial sums per particle for up to IB_STATIC_VOLUME_MAX_P
-// particles (2048 * 16 * 7 doubles = 1.75 MiB).  Host code must not pass the
+// particles (2048 * 8 * 7 doubles = 896 KiB).  Host code must not pass the
 // array's name to a kernel (that is a host-side stand-in); the device address
 // is looked up once per device with cudaGetSymbolAddress.
 static __device__ __align__(256) double g_volume_scratch[(size_t)IB_STATIC_VOLUME_MAX_P * kVolSplit * 7];
