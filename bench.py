@@ -211,9 +211,12 @@ class Runner:
 
 
 def launches_per_step():
-    # volume: 2 kernels x 2 calls; mdf: prep 1 + levels 1 + perm 1 + count 1 + 2 scans x 3
-    # + flags 1 + compact 1 + fill 1 + sort 1 + level_slots 1 + passes 1; force 1; collide 2
-    return 4 + (1 + 1 + 1 + 1 + 6 + 1 + 1 + 1 + 1 + 1 + 1) + 1 + 2
+    """Library kernels per step on this workload (P * 512 = 32768 dense tiles,
+    so each scan is one kernel): volume 1 x 2 calls; multidirect forcing:
+    prep, conflicts, levels, marker order, tile count, scan, flags, scan,
+    compact, fill, sort, level ranges, passes (13); force/torque 1;
+    collision + Newton-Euler 2."""
+    return 2 + 13 + 1 + 2
 
 
 def time_steps(runner, steps, warmup, flush, use_graph):

@@ -159,10 +159,36 @@ void PhaseTimer::stop() {
     ctx = nullptr;
 }
 
+// Small arrays: one CTA, each thread scans kScanItems consecutive elements.
+constexpr int kScanItems = 32;
+
+__global__ void __launch_bounds__(kScanBlock) k_scan_single(const uint32_t *in, uint32_t *out, int n) {
+    const int base = threadIdx.x * kScanItems;
+    uint32_t v[kScanItems];
+    uint32_t sum = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        v[k] = base + k < n ? in[base + k] : 0u;
+        sum += v[k];
+    }
+    uint32_t tot;
+    uint32_t run = block_exclusive_scan(sum, &tot);
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        if (base + k < n) out[base + k] = run;
+        run += v[k];
+    }
+    if (threadIdx.x == 0) out[n] = tot;
+}
+
 size_t scan_workspace(int n) { return (size_t)(n + kScanBlock - 1) / kScanBlock + 2; }
 
 void exclusive_scan(const uint32_t *in, uint32_t *out, int n, uint32_t *scratch,
                     cudaStream_t s) {
+    if (n <= kScanBlock * kScanItems) {
+        k_scan_single<<<1, kScanBlock, 0, s>>>(in, out, n);
+        return;
+    }
     int nb = (n + kScanBlock - 1) / kScanBlock;
     if (nb == 0) nb = 1;
     k_scan_totals<<<nb, kScanBlock, 0, s>>>(in, n, scratch);

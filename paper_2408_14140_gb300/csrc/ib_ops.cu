@@ -226,7 +226,7 @@ __global__ void __launch_bounds__(kBlock) k_prep_particles(
             lo[d] = min(lo[d], first[d]);
             hi[d] = max(hi[d], first[d] + KW - 1);
         }
-        rmax = fmax(rmax, sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]));
+        rmax = fmax(rmax, r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);  // squared; root taken once below
     }
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
@@ -237,7 +237,7 @@ __global__ void __launch_bounds__(kBlock) k_prep_particles(
     atomicMax((unsigned long long *)&s_rho, (unsigned long long)__double_as_longlong(rmax));
     __syncthreads();
     if (threadIdx.x == 0) {
-        rho[p] = s_rho;
+        rho[p] = sqrt(s_rho);
         if (m1 > m0) {
             int dims[3];
             for (int d = 0; d < 3; ++d) dims[d] = (int)(s_hi[d] - s_lo[d] + 1);
@@ -274,24 +274,28 @@ constexpr int kMaxNbr = 48;
 
 // Conflict lists: for every p, the q < p whose stencils may share a cell
 // (count -1 = more than kMaxNbr, scanned again when levels are assigned).
+// The test runs in FP32 against a limit widened by h/16, far above FP32
+// rounding of unit-scale positions, so no true conflict is ever missed (an
+// extra conflict only serialises two particles).
 __global__ void k_conflicts(DevGrid g, int P, int KW, const double *__restrict__ Xr,
                             const double *__restrict__ rho, int *__restrict__ nbr_cnt,
                             int *__restrict__ nbr) {
-    const double L[3] = {g.n[0] * g.h, g.n[1] * g.h, g.n[2] * g.h};
-    const double iL[3] = {1.0 / L[0], 1.0 / L[1], 1.0 / L[2]};
-    const double halo = 1.7320508075688772 * KW * g.h;
+    const float L[3] = {(float)(g.n[0] * g.h), (float)(g.n[1] * g.h), (float)(g.n[2] * g.h)};
+    const float iL[3] = {1.0f / L[0], 1.0f / L[1], 1.0f / L[2]};
+    const float halo = (float)(1.7320508075688772 * KW * g.h + 0.0625 * g.h);
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x) {
-        const double xp[3] = {Xr[3 * p], Xr[3 * p + 1], Xr[3 * p + 2]};
+        const float xp[3] = {(float)Xr[3 * p], (float)Xr[3 * p + 1], (float)Xr[3 * p + 2]};
+        const float rp = (float)rho[p] + halo;
         int cnt = 0;
         for (int q = 0; q < p; ++q) {
-            double d2 = 0.0;
+            float d2 = 0.0f;
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
-                double d = Xr[3 * q + a] - xp[a];
-                d -= L[a] * rint(d * iL[a]);
+                float d = (float)Xr[3 * q + a] - xp[a];
+                d -= L[a] * rintf(d * iL[a]);
                 d2 += d * d;
             }
-            const double lim = rho[p] + rho[q] + halo;
+            const float lim = rp + (float)rho[q];
             if (d2 < lim * lim) {
                 if (cnt < kMaxNbr) nbr[(size_t)p * kMaxNbr + cnt] = q;
                 ++cnt;
@@ -303,15 +307,33 @@ __global__ void k_conflicts(DevGrid g, int P, int KW, const double *__restrict__
 
 // Levels by one sequential sweep (level(p) needs only q < p), then the
 // counting sort of particles by level and the level-major marker offsets.
-__global__ void __launch_bounds__(32) k_levels(DevGrid g, int P, int order, int KW,
-                                               const double *__restrict__ Xr,
-                                               const double *__restrict__ rho,
-                                               const int *__restrict__ moff,
-                                               const int *__restrict__ nbr_cnt,
-                                               const int *__restrict__ nbr, LevelOut lo,
-                                               int *__restrict__ work) {
+// The conflict lists and levels are first copied into shared memory when
+// they fit (kLevSmemP particles), so the sweep's dependent reads are on-chip.
+constexpr int kLevSmemP = 1024;
+constexpr size_t kLevSmem = (size_t)kLevSmemP * (4 + 2 + 2 * kMaxNbr);
+
+__global__ void __launch_bounds__(1024) k_levels(DevGrid g, int P, int order, int KW,
+                                                 const double *__restrict__ Xr,
+                                                 const double *__restrict__ rho,
+                                                 const int *__restrict__ moff,
+                                                 const int *__restrict__ nbr_cnt,
+                                                 const int *__restrict__ nbr, LevelOut lo,
+                                                 int *__restrict__ work) {
+    extern __shared__ __align__(16) unsigned char lsm[];
+    const bool onchip = P <= kLevSmemP && order == IB_ORDER_SEQUENTIAL;
+    int *s_lev = (int *)lsm;
+    short *s_cnt = (short *)(s_lev + kLevSmemP);
+    unsigned short *s_nbr = (unsigned short *)(s_cnt + kLevSmemP);
+    if (onchip) {
+        for (int p = threadIdx.x; p < P; p += blockDim.x) {
+            const int c = nbr_cnt[p];
+            s_cnt[p] = (short)c;
+            for (int k = 0; k < c; ++k) s_nbr[p * kMaxNbr + k] = (unsigned short)nbr[(size_t)p * kMaxNbr + k];
+        }
+        __syncthreads();
+    }
     if (threadIdx.x != 0) return;
-    int *lev = lo.level;
+    int *lev = onchip ? s_lev : lo.level;
     int nl = 0;
     const double L[3] = {g.n[0] * g.h, g.n[1] * g.h, g.n[2] * g.h};
     const double iL[3] = {1.0 / L[0], 1.0 / L[1], 1.0 / L[2]};
@@ -319,18 +341,19 @@ __global__ void __launch_bounds__(32) k_levels(DevGrid g, int P, int order, int 
     for (int p = 0; p < P; ++p) {
         int best = 0;
         if (order == IB_ORDER_SEQUENTIAL) {
-            int c = nbr_cnt[p];
+            const int c = onchip ? s_cnt[p] : nbr_cnt[p];
             if (c >= 0) {
-                for (int k = 0; k < c; ++k) best = max(best, lev[nbr[(size_t)p * kMaxNbr + k]] + 1);
+                for (int k = 0; k < c; ++k)
+                    best = max(best, lev[onchip ? s_nbr[p * kMaxNbr + k] : nbr[(size_t)p * kMaxNbr + k]] + 1);
             } else {
                 for (int q = 0; q < p; ++q) {
-                    double d2 = 0.0;
+                    float d2 = 0.0f;
                     for (int a = 0; a < 3; ++a) {
-                        double d = Xr[3 * q + a] - Xr[3 * p + a];
-                        d -= L[a] * rint(d * iL[a]);
+                        float d = (float)Xr[3 * q + a] - (float)Xr[3 * p + a];
+                        d -= (float)L[a] * rintf(d * (float)iL[a]);
                         d2 += d * d;
                     }
-                    const double lim = rho[p] + rho[q] + halo;
+                    const float lim = (float)(rho[p] + rho[q] + halo + 0.0625 * g.h);
                     if (d2 < lim * lim) best = max(best, lev[q] + 1);
                 }
             }
@@ -338,6 +361,8 @@ __global__ void __launch_bounds__(32) k_levels(DevGrid g, int P, int order, int 
         lev[p] = best;
         nl = max(nl, best + 1);
     }
+    if (onchip)
+        for (int p = 0; p < P; ++p) lo.level[p] = lev[p];
     *lo.nlev = nl;
     int *cnt = work;  // [P+1]
     for (int i = 0; i <= P; ++i) cnt[i] = 0;
@@ -493,41 +518,119 @@ __global__ void k_marker_perm(int M, const int *__restrict__ part_of, const int 
 }
 
 // ---------------------------------------------------------------------------
-// per-slot sort by (row, marker) and row starts; one CTA per compact slot
+// per-slot sort by (row, marker) and row starts.  Tiles with at most
+// kWarpSort candidates are sorted by one warp each (bitonic network in a
+// warp-private shared-memory region); larger tiles by a whole CTA.
 // ---------------------------------------------------------------------------
+constexpr int kWarpSort = 256;
+
+__device__ __forceinline__ void slot_geometry(const DevGrid &g, int mode, const SlotGeom &sg, const Slots &sl,
+                                              const int *level, uint32_t d, uint32_t b, int lo[3], int dim[3],
+                                              int &lev) {
+    lev = 0;
+    if (mode == 0) {
+        const int t[3] = {(int)(d % sg.tiles[0]), (int)((d / sg.tiles[0]) % sg.tiles[1]),
+                          (int)(d / ((uint32_t)sg.tiles[0] * sg.tiles[1]))};
+        for (int a = 0; a < 3; ++a) {
+            lo[a] = t[a] * kTile;
+            dim[a] = min(kTile, g.n[a] - lo[a]);
+        }
+    } else {
+        const int p = sg.part_of[sl.cand[b]];  // every candidate of a local tile has the same particle
+        const int lt = (int)(d % kLocalSlots);
+        const int t[3] = {lt % kLocalTiles, (lt / kLocalTiles) % kLocalTiles, lt / (kLocalTiles * kLocalTiles)};
+        const int4 blo = sg.box_lo[p], bd = sg.box_dim[p];
+        const int bl[3] = {blo.x, blo.y, blo.z}, bdm[3] = {bd.x, bd.y, bd.z};
+        for (int a = 0; a < 3; ++a) {
+            lo[a] = wrap_int((long long)bl[a] + t[a] * kTile, g.n[a]);
+            dim[a] = min(kTile, bdm[a] - t[a] * kTile);
+        }
+        lev = level[p];
+    }
+}
+
+__device__ __forceinline__ unsigned long long slot_key(const DevGrid &g, const uint64_t *anchor, uint32_t m,
+                                                       const int lo[3]) {
+    const uint64_t anc = anchor[m];
+    const int rz = wrap_int((long long)anchor_z(anc) - lo[2] + 3, g.n[2]);
+    const int ry = wrap_int((long long)anchor_y(anc) - lo[1] + 3, g.n[1]);
+    const int row = (rz < kRow && ry < kRow) ? rz * kRow + ry : kRows;  // kRows: never read
+    return ((unsigned long long)row << 32) | m;
+}
+
+// Writes the sorted candidates, their x offsets and the row starts of slot cs
+// from keys[0..nc) (sorted); `lane`/`nl` split the work over nl threads.
+__device__ __forceinline__ void slot_emit(const DevGrid &g, const uint64_t *anchor, const unsigned long long *keys,
+                                          int nc, uint32_t b, int cs, const int lo[3], const Slots &sl, int lane,
+                                          int nl) {
+    for (int i = lane; i < nc; i += nl) {
+        const uint32_t m = (uint32_t)(keys[i] & 0xffffffffu);
+        sl.cand[b + i] = m;
+        sl.relx[b + i] = (int8_t)(wrap_int((long long)anchor_x(anchor[m]) - lo[0] + 3, g.n[0]) - 3);
+    }
+    uint16_t *rs = sl.rows + (size_t)cs * (kRows + 1);
+    for (int r = lane; r <= kRows; r += nl) {
+        // first index whose row >= r
+        int a = 0, e = nc;
+        while (a < e) {
+            const int mid = (a + e) >> 1;
+            if ((int)(keys[mid] >> 32) < r) a = mid + 1;
+            else e = mid;
+        }
+        rs[r] = (uint16_t)a;
+    }
+}
+
 __global__ void __launch_bounds__(kBlock) k_slot_sort(
     DevGrid g, int mode, int ncompact_cap, const int *__restrict__ ncompact_p, SlotGeom sg,
     const uint32_t *__restrict__ dense_of, const uint32_t *__restrict__ start,
     const uint64_t *__restrict__ anchor, const int *__restrict__ level, Slots sl, DevStatus *st) {
-    __shared__ unsigned long long keys[kMaxCand];
-    __shared__ uint32_t rowcnt[kRows + 1];
-    int ncompact = min(*ncompact_p, ncompact_cap);
-    for (int cs = blockIdx.x; cs < ncompact; cs += gridDim.x) {
-        uint32_t d = dense_of[cs];
-        uint32_t b = start[d], e = start[d + 1];
-        int nc = (int)(e - b);
-        // tile geometry
-        int lo[3], dim[3], lev = 0;
-        if (mode == 0) {
-            int t[3] = {(int)(d % sg.tiles[0]), (int)((d / sg.tiles[0]) % sg.tiles[1]),
-                        (int)(d / ((uint32_t)sg.tiles[0] * sg.tiles[1]))};
-            for (int a = 0; a < 3; ++a) {
-                lo[a] = t[a] * kTile;
-                dim[a] = min(kTile, g.n[a] - lo[a]);
+    __shared__ unsigned long long keys[kMaxCand];  // also kBlock/32 warp regions of kWarpSort
+    const int ncompact = min(*ncompact_p, ncompact_cap);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    // ---- phase 1: one warp per small tile
+    unsigned long long *wk = keys + warp * kWarpSort;
+    for (int cs = blockIdx.x * nwarp + warp; cs < ncompact; cs += gridDim.x * nwarp) {
+        const uint32_t d = dense_of[cs];
+        const uint32_t b = start[d];
+        const int nc = (int)(start[d + 1] - b);
+        if (nc > kWarpSort) continue;
+        int lo[3], dim[3], lev;
+        slot_geometry(g, mode, sg, sl, level, d, b, lo, dim, lev);
+        int np2 = 1;
+        while (np2 < nc) np2 <<= 1;
+        for (int i = lane; i < np2; i += 32) wk[i] = i < nc ? slot_key(g, anchor, sl.cand[b + i], lo) : ~0ull;
+        __syncwarp();
+        for (int k = 2; k <= np2; k <<= 1)
+            for (int j = k >> 1; j > 0; j >>= 1) {
+                for (int i = lane; i < np2; i += 32) {
+                    const int ixj = i ^ j;
+                    if (ixj > i) {
+                        const unsigned long long x = wk[i], y = wk[ixj];
+                        if ((x > y) == ((i & k) == 0)) {
+                            wk[i] = y;
+                            wk[ixj] = x;
+                        }
+                    }
+                }
+                __syncwarp();
             }
-        } else {
-            // rank -> particle: the first candidate's particle
-            int p = sg.part_of[sl.cand[b]];
-            int lt = (int)(d % kLocalSlots);
-            int t[3] = {lt % kLocalTiles, (lt / kLocalTiles) % kLocalTiles, lt / (kLocalTiles * kLocalTiles)};
-            int4 blo = sg.box_lo[p], bd = sg.box_dim[p];
-            int bl[3] = {blo.x, blo.y, blo.z}, bdm[3] = {bd.x, bd.y, bd.z};
-            for (int a = 0; a < 3; ++a) {
-                lo[a] = wrap_int((long long)bl[a] + t[a] * kTile, g.n[a]);
-                dim[a] = min(kTile, bdm[a] - t[a] * kTile);
-            }
-            lev = level[p];
+        slot_emit(g, anchor, wk, nc, b, cs, lo, sl, lane, 32);
+        if (lane == 0) {
+            sl.geo_lo[cs] = make_int4(lo[0], lo[1], lo[2], lev);
+            sl.geo_dim[cs] = make_int4(dim[0], dim[1], dim[2], (int)b);
         }
+        __syncwarp();
+    }
+    __syncthreads();
+    // ---- phase 2: one CTA per large tile
+    for (int cs = blockIdx.x; cs < ncompact; cs += gridDim.x) {
+        const uint32_t d = dense_of[cs];
+        const uint32_t b = start[d];
+        const int nc = (int)(start[d + 1] - b);
+        if (nc <= kWarpSort) continue;
+        int lo[3], dim[3], lev;
+        slot_geometry(g, mode, sg, sl, level, d, b, lo, dim, lev);
         if (nc > kMaxCand) {
             // report, and leave an empty tile (no rows, no cells)
             uint16_t *rs = sl.rows + (size_t)cs * (kRows + 1);
@@ -542,52 +645,25 @@ __global__ void __launch_bounds__(kBlock) k_slot_sort(
         }
         int np2 = 1;
         while (np2 < nc) np2 <<= 1;
-        for (int i = threadIdx.x; i <= kRows; i += blockDim.x) rowcnt[i] = 0;
+        for (int i = threadIdx.x; i < np2; i += blockDim.x)
+            keys[i] = i < nc ? slot_key(g, anchor, sl.cand[b + i], lo) : ~0ull;
         __syncthreads();
-        for (int i = threadIdx.x; i < np2; i += blockDim.x) {
-            unsigned long long key = ~0ull;
-            if (i < nc) {
-                uint32_t m = sl.cand[b + i];
-                uint64_t anc = anchor[m];
-                int rz = wrap_int((long long)anchor_z(anc) - lo[2] + 3, g.n[2]);
-                int ry = wrap_int((long long)anchor_y(anc) - lo[1] + 3, g.n[1]);
-                int row = (rz < kRow && ry < kRow) ? rz * kRow + ry : kRows;  // kRows: never read
-                key = ((unsigned long long)row << 32) | m;
-                atomicAdd(&rowcnt[row], 1u);
-            }
-            keys[i] = key;
-        }
-        __syncthreads();
-        // bitonic sort of np2 keys
-        for (int k = 2; k <= np2; k <<= 1) {
+        for (int k = 2; k <= np2; k <<= 1)
             for (int j = k >> 1; j > 0; j >>= 1) {
                 for (int i = threadIdx.x; i < np2; i += blockDim.x) {
-                    int ixj = i ^ j;
+                    const int ixj = i ^ j;
                     if (ixj > i) {
-                        unsigned long long a = keys[i], c = keys[ixj];
-                        bool up = (i & k) == 0;
-                        if ((a > c) == up) {
-                            keys[i] = c;
-                            keys[ixj] = a;
+                        const unsigned long long x = keys[i], y = keys[ixj];
+                        if ((x > y) == ((i & k) == 0)) {
+                            keys[i] = y;
+                            keys[ixj] = x;
                         }
                     }
                 }
                 __syncthreads();
             }
-        }
-        for (int i = threadIdx.x; i < nc; i += blockDim.x) {
-            uint32_t m = (uint32_t)(keys[i] & 0xffffffffu);
-            sl.cand[b + i] = m;
-            sl.relx[b + i] = (int8_t)(wrap_int((long long)anchor_x(anchor[m]) - lo[0] + 3, g.n[0]) - 3);
-        }
+        slot_emit(g, anchor, keys, nc, b, cs, lo, sl, threadIdx.x, blockDim.x);
         if (threadIdx.x == 0) {
-            uint16_t *rs = sl.rows + (size_t)cs * (kRows + 1);
-            uint32_t acc = 0;
-            for (int r = 0; r < kRows; ++r) {
-                rs[r] = (uint16_t)acc;
-                acc += rowcnt[r];
-            }
-            rs[kRows] = (uint16_t)acc;
             sl.geo_lo[cs] = make_int4(lo[0], lo[1], lo[2], lev);
             sl.geo_dim[cs] = make_int4(dim[0], dim[1], dim[2], (int)b);
         }
@@ -774,24 +850,34 @@ struct Barrier {
     unsigned int *gen;
 };
 
+__device__ __forceinline__ unsigned int ld_acquire(const unsigned int *p) {
+    unsigned int v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Sense-free generation barrier over all CTAs of a cooperative launch.  The
+// waiting thread polls the generation word without sleeping (a sleep's wake-up
+// latency dominated the phases) and gives up after kSpinCycles SM cycles,
+// raising IB_ERR_TIMEOUT; every CTA then returns.
+constexpr long long kSpinCycles = 4LL * 1000 * 1000 * 1000;  // ~2 s at 2 GHz
+
 __device__ __forceinline__ bool grid_sync(Barrier b, DevStatus *st) {
     __syncthreads();
     __shared__ int s_ok;
     if (threadIdx.x == 0) {
-        volatile unsigned int *vgen = b.gen;
-        unsigned int g0 = *vgen;
+        const unsigned int g0 = ld_acquire(b.gen);
         __threadfence();
-        unsigned int arrived = atomicAdd(b.count, 1u);
+        const unsigned int arrived = atomicAdd(b.count, 1u);
         int ok = 1;
         if (arrived == gridDim.x - 1) {
             atomicExch(b.count, 0u);
             __threadfence();
             atomicAdd(b.gen, 1u);
         } else {
-            long long it = 0;
-            while (*vgen == g0) {
-                __nanosleep(64);
-                if (++it > kSpinLimit) {
+            const long long t0 = clock64();
+            while (ld_acquire(b.gen) == g0) {
+                if (clock64() - t0 > kSpinCycles) {
                     raise_status(st, IB_ERR_TIMEOUT, (int)blockIdx.x);
                     ok = 0;
                     break;
@@ -1109,7 +1195,8 @@ static int run_mdf(ib_ctx *ctx, const DevGrid &g, void *u, const ib_particles *p
                                                  ctx->status);
     if (order == IB_ORDER_SEQUENTIAL)
         k_conflicts<<<grid_blocks(P, 128, ctx->sm_count), 128, 0, s>>>(g, P, KW, pp->Xr, rho, nbr_cnt, nbr);
-    k_levels<<<1, 32, 0, s>>>(g, P, order, KW, pp->Xr, rho, pp->marker_offset, nbr_cnt, nbr, lo, lev_work);
+    cudaFuncSetAttribute(k_levels, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLevSmem);
+    k_levels<<<1, 1024, kLevSmem, s>>>(g, P, order, KW, pp->Xr, rho, pp->marker_offset, nbr_cnt, nbr, lo, lev_work);
     k_marker_perm<<<grid_blocks(M, 256, ctx->sm_count), 256, 0, s>>>(M, part_of, pp->marker_offset,
                                                                      lo.mbase, mperm);
     sg.part_of = part_of;
