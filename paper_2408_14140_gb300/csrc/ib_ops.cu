@@ -58,11 +58,16 @@ struct Slots {
 // ---------------------------------------------------------------------------
 // interpolation of one marker from precomputed weights
 // ---------------------------------------------------------------------------
-// Loads of data that other CTAs of a persistent kernel write between grid
-// barriers go through L2 (ld.global.cg): L1 is not coherent across SMs.
+// Loads of data that other CTAs of the persistent kernel write between grid
+// barriers (COH) are ordinary weak loads: the barrier is a GPU-scope
+// release/acquire pattern, so by the PTX memory model every write before it
+// is visible to every load after it.  (The read-only path, ld.global.nc, is
+// not coherent with writes made during the kernel and is used only for data
+// that no kernel writes meanwhile.)  ld.global.cg forms are avoided here:
+// they were issued one at a time, serialising ~80 L2 round trips per marker.
 template <bool COH, typename T>
 __device__ __forceinline__ T ld(const T *p) {
-    if (COH) return __ldcg(p);
+    if (COH) return *p;
     return __ldg(p);
 }
 
@@ -816,13 +821,13 @@ __device__ __forceinline__ void gather_tile(const DevGrid &g, long long N, int c
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
                 T *q = dst + k * N + c;
-                *q = (COH ? __ldcg(q) : *q) + acc[k];
+                *q += acc[k];
             }
             if (f_out) {
 #pragma unroll
                 for (int k = 0; k < 3; ++k) {
                     T *q = f_out + k * N + c;
-                    *q = (COH ? __ldcg(q) : *q) + (T)(acc[k] * inv_dt);
+                    *q += (T)(acc[k] * inv_dt);
                 }
             }
         }
@@ -980,7 +985,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_mdf_passes(PassArgs<T> a) {
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
                     double e = a.ms.Ud[3 * l + c] - (double)U[c];
-                    a.F[3 * l + c] = __ldcg(a.F + 3 * l + c) + e * inv_dt;
+                    a.F[3 * l + c] += e * inv_dt;
                     a.ms.A[4 * l + c] = (T)(e * q);
                 }
             }
@@ -990,9 +995,9 @@ __global__ void __launch_bounds__(kBlock, 2) k_mdf_passes(PassArgs<T> a) {
                 const int tot = s_total;
                 for (int i = threadIdx.x; i < tot; i += blockDim.x) {
                     const T *src = a.ms.A + 4 * (size_t)lv.ids[i];
-                    lv.A[4 * i + 0] = __ldcg(src + 0);
-                    lv.A[4 * i + 1] = __ldcg(src + 1);
-                    lv.A[4 * i + 2] = __ldcg(src + 2);
+                    lv.A[4 * i + 0] = src[0];
+                    lv.A[4 * i + 1] = src[1];
+                    lv.A[4 * i + 2] = src[2];
                 }
                 __syncthreads();
                 // software pipeline over the CTA's tiles: the u loads of tile k
@@ -1015,10 +1020,10 @@ __global__ void __launch_bounds__(kBlock, 2) k_mdf_passes(PassArgs<T> a) {
                                     g.n[0] +
                                 wrap_add(lo.x, tx, g.n[0]);
 #pragma unroll
-                            for (int q = 0; q < 3; ++q) uo[q] = __ldcg(a.u + q * N + c);
+                            for (int q = 0; q < 3; ++q) uo[q] = a.u[q * N + c];
                             if (a.f_out)
 #pragma unroll
-                                for (int q = 0; q < 3; ++q) fo[q] = __ldcg(a.f_out + q * N + c);
+                                for (int q = 0; q < 3; ++q) fo[q] = a.f_out[q * N + c];
                         }
                     }
                     if (pc >= 0) {
@@ -1048,7 +1053,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_mdf_passes(PassArgs<T> a) {
     // non-finite result check of the forces (cheap, once)
     for (int l = gtid; l < a.lev_mbeg[nl]; l += gsz) {
         int m = a.mperm[l];
-        double fv[3] = {__ldcg(a.F + 3 * m), __ldcg(a.F + 3 * m + 1), __ldcg(a.F + 3 * m + 2)};
+        double fv[3] = {a.F[3 * m], a.F[3 * m + 1], a.F[3 * m + 2]};
         if (!finite3(fv)) raise_status(a.st, IB_ERR_NONFINITE, m);
     }
 }

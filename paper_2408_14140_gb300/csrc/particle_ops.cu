@@ -204,18 +204,24 @@ __global__ void __launch_bounds__(kVolThreads) k_volume(DevGrid g, const T *__re
         for (int k = 0; k < 7; ++k) acc[k] *= h3;
     }
     block_sum<7>(acc);
+    __shared__ double s_part[kVolSplit * 7];
     if (threadIdx.x == 0) {
         double *dst = partial + ((size_t)p * kVolSplit + split) * 7;
         for (int k = 0; k < 7; ++k) dst[k] = acc[k];
-        __threadfence();
+        __threadfence();  // release: partials before the count
         s_last = atomicAdd(done + p, 1u) == kVolSplit - 1;
+        __threadfence();  // acquire: the count before the other partials
     }
     __syncthreads();
+    if (s_last) {
+        // the last CTA of the particle adds the partials in slab order
+        for (int i = threadIdx.x; i < kVolSplit * 7; i += blockDim.x) s_part[i] = partial[(size_t)p * kVolSplit * 7 + i];
+        __syncthreads();
+    }
     if (s_last && threadIdx.x == 0) {
-        __threadfence();
         double sum[7] = {0, 0, 0, 0, 0, 0, 0};
         for (int sp = 0; sp < kVolSplit; ++sp)
-            for (int k = 0; k < 7; ++k) sum[k] += __ldcg(partial + ((size_t)p * kVolSplit + sp) * 7 + k);
+            for (int k = 0; k < 7; ++k) sum[k] += s_part[sp * 7 + k];
         if (Iu)
             for (int a = 0; a < 3; ++a) Iu[3 * p + a] = sum[a];
         if (Irxu)
