@@ -513,12 +513,54 @@ __global__ void k_level_slots(int mode, const int *__restrict__ nlev_p, const in
     }
 }
 
-// Level-major marker list: mperm[mbase[p] + (l - moff[p])] = l.
-__global__ void k_marker_perm(int M, const int *__restrict__ part_of, const int *__restrict__ moff,
-                              const int *__restrict__ mbase, int *__restrict__ mperm) {
-    for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < M; l += gridDim.x * blockDim.x) {
-        int p = part_of[l];
-        mperm[mbase[p] + (l - moff[p])] = l;
+// Level-major marker list.  Inside each particle the markers are listed in
+// spatial order of their anchors (z, y, x of the first stencil cell), so the
+// warps of the interpolation phase read neighbouring cells; the order has no
+// effect on results (every marker is interpolated independently).  One CTA
+// per particle sorts up to kMaxCand (anchor key, marker) pairs; larger
+// particles keep index order.
+__global__ void __launch_bounds__(kBlock) k_marker_order(int P, const int *__restrict__ moff,
+                                                         const int *__restrict__ mbase,
+                                                         const uint64_t *__restrict__ anchor,
+                                                         int *__restrict__ mperm) {
+    __shared__ unsigned long long keys[kMaxCand];
+    for (int p = blockIdx.x; p < P; p += gridDim.x) {
+        const int m0 = moff[p], n = moff[p + 1] - m0, base = mbase[p];
+        if (n > kMaxCand) {
+            for (int i = threadIdx.x; i < n; i += blockDim.x) mperm[base + i] = m0 + i;
+            continue;
+        }
+        int np2 = 1;
+        while (np2 < n) np2 <<= 1;
+        for (int i = threadIdx.x; i < np2; i += blockDim.x) {
+            if (i < n) {
+                const uint64_t a = anchor[m0 + i];
+                // z, y, x of the anchor, 10 bits each (wrapped cells modulo 1024 still sort locally)
+                const unsigned long long key = ((unsigned long long)(anchor_z(a) & 1023) << 20) |
+                                               ((unsigned long long)(anchor_y(a) & 1023) << 10) |
+                                               (unsigned long long)(anchor_x(a) & 1023);
+                keys[i] = (key << 32) | (unsigned)i;
+            } else {
+                keys[i] = ~0ull;
+            }
+        }
+        __syncthreads();
+        for (int k = 2; k <= np2; k <<= 1)
+            for (int j = k >> 1; j > 0; j >>= 1) {
+                for (int i = threadIdx.x; i < np2; i += blockDim.x) {
+                    const int ixj = i ^ j;
+                    if (ixj > i) {
+                        const unsigned long long x = keys[i], y = keys[ixj];
+                        if ((x > y) == ((i & k) == 0)) {
+                            keys[i] = y;
+                            keys[ixj] = x;
+                        }
+                    }
+                }
+                __syncthreads();
+            }
+        for (int i = threadIdx.x; i < n; i += blockDim.x) mperm[base + i] = m0 + (int)(keys[i] & 0xffffffffu);
+        __syncthreads();
     }
 }
 
@@ -919,7 +961,7 @@ struct PassArgs {
 };
 
 template <typename T, int KER>
-__global__ void __launch_bounds__(kBlock, 2) k_mdf_passes(PassArgs<T> a) {
+__global__ void __launch_bounds__(kBlock, 1) k_mdf_passes(PassArgs<T> a) {
     constexpr int KW = Kernel<KER>::W;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     StageSmem<T> sm(smem_raw);
@@ -1000,47 +1042,54 @@ __global__ void __launch_bounds__(kBlock, 2) k_mdf_passes(PassArgs<T> a) {
                     lv.A[4 * i + 2] = src[2];
                 }
                 __syncthreads();
-                // software pipeline over the CTA's tiles: the u loads of tile k
-                // are in flight while tile k + 1 is summed
-                T pacc[3], pu[3], pf[3];
-                long long pc = -1;
-                for (int k = 0; k <= nmine; ++k) {
-                    T acc[3];
-                    long long c = -1;
-                    T uo[3], fo[3];
-                    if (k < nmine) {
-                        const int4 dim = s_dim[k];
-                        const int off = s_off[k];
-                        if (tx < dim.x && ty < dim.y && tz < dim.z &&
-                            gather_cell<T, KW, true, true>(tx, ty, tz, lv.rows + k * (kRows + 1), lv.relx + off,
-                                                           nullptr, lv.w + 12 * (size_t)off, lv.A + 4 * (size_t)off,
-                                                           acc)) {
-                            const int4 lo = s_lo[k];
-                            c = ((long long)wrap_add(lo.z, tz, g.n[2]) * g.n[1] + wrap_add(lo.y, ty, g.n[1])) *
-                                    g.n[0] +
-                                wrap_add(lo.x, tx, g.n[0]);
+                // tiles in chunks of kChunk: first every cell sum of the chunk,
+                // then all the chunk's u (and f) loads, then all the stores, so
+                // the loads of different tiles are in flight together
+                constexpr int kChunk = sizeof(T) == 4 ? 8 : 4;
+                for (int k0 = 0; k0 < nmine; k0 += kChunk) {
+                    T acc[kChunk][3];
+                    long long cell[kChunk];
 #pragma unroll
-                            for (int q = 0; q < 3; ++q) uo[q] = a.u[q * N + c];
-                            if (a.f_out)
-#pragma unroll
-                                for (int q = 0; q < 3; ++q) fo[q] = a.f_out[q * N + c];
+                    for (int j = 0; j < kChunk; ++j) {
+                        cell[j] = -1;
+                        const int k = k0 + j;
+                        if (k < nmine) {
+                            const int4 dim = s_dim[k];
+                            const int off = s_off[k];
+                            if (tx < dim.x && ty < dim.y && tz < dim.z &&
+                                gather_cell<T, KW, true, true>(tx, ty, tz, lv.rows + k * (kRows + 1), lv.relx + off,
+                                                               nullptr, lv.w + 12 * (size_t)off,
+                                                               lv.A + 4 * (size_t)off, acc[j])) {
+                                const int4 lo = s_lo[k];
+                                cell[j] = ((long long)wrap_add(lo.z, tz, g.n[2]) * g.n[1] +
+                                           wrap_add(lo.y, ty, g.n[1])) * g.n[0] +
+                                          wrap_add(lo.x, tx, g.n[0]);
+                            }
                         }
                     }
-                    if (pc >= 0) {
+                    T uo[kChunk][3];
 #pragma unroll
-                        for (int q = 0; q < 3; ++q) a.u[q * N + pc] = pu[q] + pacc[q];
-                        if (a.f_out)
+                    for (int j = 0; j < kChunk; ++j)
+                        if (cell[j] >= 0)
 #pragma unroll
-                            for (int q = 0; q < 3; ++q) a.f_out[q * N + pc] = pf[q] + (T)(pacc[q] * inv_dt);
-                    }
-                    pc = c;
-                    if (c >= 0) {
+                            for (int q = 0; q < 3; ++q) uo[j][q] = a.u[q * N + cell[j]];
 #pragma unroll
-                        for (int q = 0; q < 3; ++q) {
-                            pacc[q] = acc[q];
-                            pu[q] = uo[q];
-                            pf[q] = a.f_out ? fo[q] : T(0);
-                        }
+                    for (int j = 0; j < kChunk; ++j)
+                        if (cell[j] >= 0)
+#pragma unroll
+                            for (int q = 0; q < 3; ++q) a.u[q * N + cell[j]] = uo[j][q] + acc[j][q];
+                    if (a.f_out) {
+#pragma unroll
+                        for (int j = 0; j < kChunk; ++j)
+                            if (cell[j] >= 0)
+#pragma unroll
+                                for (int q = 0; q < 3; ++q) uo[j][q] = a.f_out[q * N + cell[j]];
+#pragma unroll
+                        for (int j = 0; j < kChunk; ++j)
+                            if (cell[j] >= 0)
+#pragma unroll
+                                for (int q = 0; q < 3; ++q)
+                                    a.f_out[q * N + cell[j]] = uo[j][q] + (T)(acc[j][q] * inv_dt);
                     }
                 }
             } else {
@@ -1202,8 +1251,8 @@ static int run_mdf(ib_ctx *ctx, const DevGrid &g, void *u, const ib_particles *p
         k_conflicts<<<grid_blocks(P, 128, ctx->sm_count), 128, 0, s>>>(g, P, KW, pp->Xr, rho, nbr_cnt, nbr);
     cudaFuncSetAttribute(k_levels, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLevSmem);
     k_levels<<<1, 1024, kLevSmem, s>>>(g, P, order, KW, pp->Xr, rho, pp->marker_offset, nbr_cnt, nbr, lo, lev_work);
-    k_marker_perm<<<grid_blocks(M, 256, ctx->sm_count), 256, 0, s>>>(M, part_of, pp->marker_offset,
-                                                                     lo.mbase, mperm);
+    k_marker_order<<<P < ctx->sm_count * 2 ? P : ctx->sm_count * 2, kBlock, 0, s>>>(P, pp->marker_offset, lo.mbase,
+                                                                                    ms.anchor, mperm);
     sg.part_of = part_of;
     sg.rank = lo.rank;
     sg.box_lo = box_lo;
