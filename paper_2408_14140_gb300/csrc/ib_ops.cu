@@ -754,15 +754,18 @@ struct StageSmem {
 // wavefront and reused by all Ns passes; each pass then reloads only the
 // candidates' spread sources.  Wavefronts whose tiles do not fit fall back to
 // per-tile staging.
+// Within a wavefront every band cell is written by exactly one tile, so the
+// u values of a CTA's tiles (up to UT tiles) also stay in shared memory for
+// all passes: a pass adds its sums there and stores them, loading nothing.
 template <typename T> struct LvlStage;
-template <> struct LvlStage<float> { static constexpr int REC = 1536; };
-template <> struct LvlStage<double> { static constexpr int REC = 768; };
+template <> struct LvlStage<float> { static constexpr int REC = 1536, UT = 12; };
+template <> struct LvlStage<double> { static constexpr int REC = 640, UT = 9; };
 constexpr int kMaxMyTiles = 24;
 
 template <typename T>
 constexpr size_t lvl_stage_bytes() {
     return (size_t)LvlStage<T>::REC * (12 + 4) * sizeof(T) + (size_t)LvlStage<T>::REC * 5 +
-           (size_t)kMaxMyTiles * (kRows + 1) * 2;
+           (size_t)kMaxMyTiles * (kRows + 1) * 2 + (size_t)LvlStage<T>::UT * 3 * kTileCells * sizeof(T);
 }
 
 template <typename T>
@@ -772,8 +775,10 @@ struct LvlSmem {
     uint32_t *ids;  // [REC]
     int8_t *relx;   // [REC]
     uint16_t *rows; // [kMaxMyTiles][kRows+1]
+    T *u;           // [UT][3][kTileCells]
     __device__ explicit LvlSmem(unsigned char *base) {
-        w = (T *)base;
+        u = (T *)base;  // first: keeps T alignment
+        w = u + (size_t)LvlStage<T>::UT * 3 * kTileCells;
         A = w + (size_t)LvlStage<T>::REC * 12;
         ids = (uint32_t *)(A + (size_t)LvlStage<T>::REC * 4);
         relx = (int8_t *)(ids + LvlStage<T>::REC);
@@ -993,7 +998,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_mdf_passes(PassArgs<T> a) {
             s_off[ok ? nmine : 0] = tot;
             s_nmine = nmine;
             s_total = tot;
-            s_staged = ok && tot <= LvlStage<T>::REC;
+            s_staged = ok && tot <= LvlStage<T>::REC && nmine <= LvlStage<T>::UT;
         }
         __syncthreads();
         const bool staged = s_staged;
@@ -1004,6 +1009,16 @@ __global__ void __launch_bounds__(kBlock, 1) k_mdf_passes(PassArgs<T> a) {
                 const uint16_t *rs = a.sl.rows + (size_t)cs * (kRows + 1);
                 for (int i = threadIdx.x; i <= kRows; i += blockDim.x) lv.rows[k * (kRows + 1) + i] = rs[i];
                 const int b = s_dim[k].w, off = s_off[k], nc = s_off[k + 1] - off;
+                {
+                    // the tile's u values (every cell of the tile; only band cells are written)
+                    const int4 lo = s_lo[k], dim = s_dim[k];
+                    if (tx < dim.x && ty < dim.y && tz < dim.z) {
+                        const long long c = ((long long)wrap_add(lo.z, tz, g.n[2]) * g.n[1] +
+                                             wrap_add(lo.y, ty, g.n[1])) * g.n[0] + wrap_add(lo.x, tx, g.n[0]);
+#pragma unroll
+                        for (int q = 0; q < 3; ++q) lv.u[(k * 3 + q) * kTileCells + threadIdx.x] = a.u[q * N + c];
+                    }
+                }
                 for (int i = threadIdx.x; i < nc; i += blockDim.x) {
                     const uint32_t mk = a.sl.cand[b + i];
                     lv.ids[off + i] = mk;
@@ -1042,54 +1057,27 @@ __global__ void __launch_bounds__(kBlock, 1) k_mdf_passes(PassArgs<T> a) {
                     lv.A[4 * i + 2] = src[2];
                 }
                 __syncthreads();
-                // tiles in chunks of kChunk: first every cell sum of the chunk,
-                // then all the chunk's u (and f) loads, then all the stores, so
-                // the loads of different tiles are in flight together
-                constexpr int kChunk = sizeof(T) == 4 ? 8 : 4;
-                for (int k0 = 0; k0 < nmine; k0 += kChunk) {
-                    T acc[kChunk][3];
-                    long long cell[kChunk];
+#pragma unroll 1
+                for (int k = 0; k < nmine; ++k) {
+                    const int4 dim = s_dim[k];
+                    const int off = s_off[k];
+                    T acc[3];
+                    if (tx < dim.x && ty < dim.y && tz < dim.z &&
+                        gather_cell<T, KW, true, true>(tx, ty, tz, lv.rows + k * (kRows + 1), lv.relx + off,
+                                                       nullptr, lv.w + 12 * (size_t)off, lv.A + 4 * (size_t)off,
+                                                       acc)) {
+                        const int4 lo = s_lo[k];
+                        const long long c = ((long long)wrap_add(lo.z, tz, g.n[2]) * g.n[1] +
+                                             wrap_add(lo.y, ty, g.n[1])) * g.n[0] + wrap_add(lo.x, tx, g.n[0]);
 #pragma unroll
-                    for (int j = 0; j < kChunk; ++j) {
-                        cell[j] = -1;
-                        const int k = k0 + j;
-                        if (k < nmine) {
-                            const int4 dim = s_dim[k];
-                            const int off = s_off[k];
-                            if (tx < dim.x && ty < dim.y && tz < dim.z &&
-                                gather_cell<T, KW, true, true>(tx, ty, tz, lv.rows + k * (kRows + 1), lv.relx + off,
-                                                               nullptr, lv.w + 12 * (size_t)off,
-                                                               lv.A + 4 * (size_t)off, acc[j])) {
-                                const int4 lo = s_lo[k];
-                                cell[j] = ((long long)wrap_add(lo.z, tz, g.n[2]) * g.n[1] +
-                                           wrap_add(lo.y, ty, g.n[1])) * g.n[0] +
-                                          wrap_add(lo.x, tx, g.n[0]);
-                            }
+                        for (int q = 0; q < 3; ++q) {
+                            T *su = lv.u + (k * 3 + q) * kTileCells + threadIdx.x;
+                            *su += acc[q];
+                            a.u[q * N + c] = *su;
                         }
-                    }
-                    T uo[kChunk][3];
+                        if (a.f_out)
 #pragma unroll
-                    for (int j = 0; j < kChunk; ++j)
-                        if (cell[j] >= 0)
-#pragma unroll
-                            for (int q = 0; q < 3; ++q) uo[j][q] = a.u[q * N + cell[j]];
-#pragma unroll
-                    for (int j = 0; j < kChunk; ++j)
-                        if (cell[j] >= 0)
-#pragma unroll
-                            for (int q = 0; q < 3; ++q) a.u[q * N + cell[j]] = uo[j][q] + acc[j][q];
-                    if (a.f_out) {
-#pragma unroll
-                        for (int j = 0; j < kChunk; ++j)
-                            if (cell[j] >= 0)
-#pragma unroll
-                                for (int q = 0; q < 3; ++q) uo[j][q] = a.f_out[q * N + cell[j]];
-#pragma unroll
-                        for (int j = 0; j < kChunk; ++j)
-                            if (cell[j] >= 0)
-#pragma unroll
-                                for (int q = 0; q < 3; ++q)
-                                    a.f_out[q * N + cell[j]] = uo[j][q] + (T)(acc[j][q] * inv_dt);
+                            for (int q = 0; q < 3; ++q) a.f_out[q * N + c] += (T)(acc[q] * inv_dt);
                     }
                 }
             } else {
