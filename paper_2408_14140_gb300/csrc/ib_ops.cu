@@ -31,6 +31,13 @@ constexpr int kBlock = 512;          // threads per CTA (one per tile cell)
 constexpr int kLocalTiles = 8;       // local tiles per axis of a particle box
 constexpr int kLocalSlots = kLocalTiles * kLocalTiles * kLocalTiles;
 constexpr int kMaxBox = kLocalTiles * kTile;  // 64 cells
+// A tile's candidates are sorted by (anchor row, x offset, marker).  Bin
+// (row, v), v = x offset + 3 in [0, 10], holds the markers whose first stencil
+// cell is at row `row` and x offset v - 3 from the tile; kBins[row * 12 + v]
+// is the bin's first candidate and [row * 12 + 11] the row's end, so a cell
+// reads exactly the KW^3 bins of its stencil.
+constexpr int kBinsPerRow = 12;
+constexpr int kBins = kRows * kBinsPerRow + 1;
 
 // Per-marker state kept in the workspace for one call.
 template <typename T>
@@ -49,8 +56,7 @@ struct Slots {
     uint32_t *flag_scan;  // [ndense+1] compact index of non-empty slots
     uint32_t *dense_of;   // [ncompact_max] dense id of each compact slot
     uint32_t *cand;    // [total candidates] marker ids, sorted per slot
-    int8_t *relx;      // [total candidates] first stencil x - tile lo x, in [-3, 7]
-    uint16_t *rows;    // [ncompact_max][kRows+1] row starts, relative
+    uint16_t *bins;    // [ncompact_max][kBins] bin starts, relative (see kBins)
     int4 *geo_lo;      // [ncompact_max] tile first cell (wrapped), w = level
     int4 *geo_dim;     // [ncompact_max] tile dims, w = candidate count
 };
@@ -601,8 +607,10 @@ __device__ __forceinline__ unsigned long long slot_key(const DevGrid &g, const u
     const uint64_t anc = anchor[m];
     const int rz = wrap_int((long long)anchor_z(anc) - lo[2] + 3, g.n[2]);
     const int ry = wrap_int((long long)anchor_y(anc) - lo[1] + 3, g.n[1]);
-    const int row = (rz < kRow && ry < kRow) ? rz * kRow + ry : kRows;  // kRows: never read
-    return ((unsigned long long)row << 32) | m;
+    const int v = wrap_int((long long)anchor_x(anc) - lo[0] + 3, g.n[0]);
+    const int bin = (rz < kRow && ry < kRow && v < kRow) ? (rz * kRow + ry) * kBinsPerRow + v
+                                                         : kBins - 1;  // never read
+    return ((unsigned long long)bin << 32) | m;
 }
 
 // Writes the sorted candidates, their x offsets and the row starts of slot cs
@@ -610,21 +618,17 @@ __device__ __forceinline__ unsigned long long slot_key(const DevGrid &g, const u
 __device__ __forceinline__ void slot_emit(const DevGrid &g, const uint64_t *anchor, const unsigned long long *keys,
                                           int nc, uint32_t b, int cs, const int lo[3], const Slots &sl, int lane,
                                           int nl) {
-    for (int i = lane; i < nc; i += nl) {
-        const uint32_t m = (uint32_t)(keys[i] & 0xffffffffu);
-        sl.cand[b + i] = m;
-        sl.relx[b + i] = (int8_t)(wrap_int((long long)anchor_x(anchor[m]) - lo[0] + 3, g.n[0]) - 3);
-    }
-    uint16_t *rs = sl.rows + (size_t)cs * (kRows + 1);
-    for (int r = lane; r <= kRows; r += nl) {
-        // first index whose row >= r
+    for (int i = lane; i < nc; i += nl) sl.cand[b + i] = (uint32_t)(keys[i] & 0xffffffffu);
+    uint16_t *bs = sl.bins + (size_t)cs * kBins;
+    for (int r = lane; r < kBins; r += nl) {
+        // first index whose bin >= r
         int a = 0, e = nc;
         while (a < e) {
             const int mid = (a + e) >> 1;
             if ((int)(keys[mid] >> 32) < r) a = mid + 1;
             else e = mid;
         }
-        rs[r] = (uint16_t)a;
+        bs[r] = (uint16_t)(r == kBins - 1 ? nc : a);
     }
 }
 
@@ -679,9 +683,9 @@ __global__ void __launch_bounds__(kBlock) k_slot_sort(
         int lo[3], dim[3], lev;
         slot_geometry(g, mode, sg, sl, level, d, b, lo, dim, lev);
         if (nc > kMaxCand) {
-            // report, and leave an empty tile (no rows, no cells)
-            uint16_t *rs = sl.rows + (size_t)cs * (kRows + 1);
-            for (int r = threadIdx.x; r <= kRows; r += blockDim.x) rs[r] = 0;
+            // report, and leave an empty tile (no bins, no cells)
+            uint16_t *bs = sl.bins + (size_t)cs * kBins;
+            for (int r = threadIdx.x; r < kBins; r += blockDim.x) bs[r] = 0;
             if (threadIdx.x == 0) {
                 raise_status(st, IB_ERR_UNSUPPORTED, nc);
                 sl.geo_lo[cs] = make_int4(lo[0], lo[1], lo[2], lev);
@@ -732,20 +736,18 @@ template <> struct Stage<double> { static constexpr int N = 512; };
 
 template <typename T>
 constexpr size_t stage_bytes() {
-    return (size_t)Stage<T>::N * (12 + 4) * sizeof(T) + (size_t)Stage<T>::N + 2 * (kRows + 1);
+    return (size_t)Stage<T>::N * (12 + 4) * sizeof(T) + 2 * (size_t)kBins;
 }
 
 template <typename T>
 struct StageSmem {
     T *w;          // [N][12]
     T *A;          // [N][4]
-    int8_t *relx;  // [N]
-    uint16_t *rows;
+    uint16_t *bins;
     __device__ explicit StageSmem(unsigned char *base) {
         w = (T *)base;
         A = w + (size_t)Stage<T>::N * 12;
-        relx = (int8_t *)(A + (size_t)Stage<T>::N * 4);
-        rows = (uint16_t *)(relx + Stage<T>::N);
+        bins = (uint16_t *)(A + (size_t)Stage<T>::N * 4);
     }
 };
 
@@ -759,13 +761,13 @@ struct StageSmem {
 // all passes: a pass adds its sums there and stores them, loading nothing.
 template <typename T> struct LvlStage;
 template <> struct LvlStage<float> { static constexpr int REC = 1536, UT = 12; };
-template <> struct LvlStage<double> { static constexpr int REC = 640, UT = 9; };
-constexpr int kMaxMyTiles = 24;
+template <> struct LvlStage<double> { static constexpr int REC = 576, UT = 9; };
+constexpr int kMaxMyTiles = 12;  // >= every UT
 
 template <typename T>
 constexpr size_t lvl_stage_bytes() {
-    return (size_t)LvlStage<T>::REC * (12 + 4) * sizeof(T) + (size_t)LvlStage<T>::REC * 5 +
-           (size_t)kMaxMyTiles * (kRows + 1) * 2 + (size_t)LvlStage<T>::UT * 3 * kTileCells * sizeof(T);
+    return (size_t)LvlStage<T>::REC * (12 + 4) * sizeof(T) + (size_t)LvlStage<T>::REC * 4 +
+           (size_t)LvlStage<T>::UT * kBins * 2 + (size_t)LvlStage<T>::UT * 3 * kTileCells * sizeof(T);
 }
 
 template <typename T>
@@ -773,23 +775,20 @@ struct LvlSmem {
     T *w;           // [REC][12]
     T *A;           // [REC][4]
     uint32_t *ids;  // [REC]
-    int8_t *relx;   // [REC]
-    uint16_t *rows; // [kMaxMyTiles][kRows+1]
+    uint16_t *bins; // [UT][kBins]
     T *u;           // [UT][3][kTileCells]
     __device__ explicit LvlSmem(unsigned char *base) {
         u = (T *)base;  // first: keeps T alignment
         w = u + (size_t)LvlStage<T>::UT * 3 * kTileCells;
         A = w + (size_t)LvlStage<T>::REC * 12;
         ids = (uint32_t *)(A + (size_t)LvlStage<T>::REC * 4);
-        relx = (int8_t *)(ids + LvlStage<T>::REC);
-        rows = (uint16_t *)(relx + LvlStage<T>::REC);
+        bins = (uint16_t *)(ids + LvlStage<T>::REC);
     }
 };
 
 template <typename T, int KW, bool STAGED, bool COH>
-__device__ __forceinline__ bool gather_cell(int tx, int ty, int tz, const uint16_t *rs,
-                                            const int8_t *relx, const uint32_t *cand, const T *w_src,
-                                            const T *A_src, T acc[3]) {
+__device__ __forceinline__ bool gather_cell(int tx, int ty, int tz, const uint16_t *bins, const uint32_t *cand,
+                                            const T *w_src, const T *A_src, T acc[3]) {
     bool hit = false;
     acc[0] = acc[1] = acc[2] = T(0);
 #pragma unroll
@@ -798,11 +797,14 @@ __device__ __forceinline__ bool gather_cell(int tx, int ty, int tz, const uint16
 #pragma unroll
         for (int dy = 0; dy < KW; ++dy) {
             const int ry = ty + 3 - (KW - 1) + dy, oy = KW - 1 - dy;
-            const int row = rz * kRow + ry;
-            const int i0 = rs[row], i1 = rs[row + 1];
-            for (int i = i0; i < i1; ++i) {
-                const int ox = tx - (int)relx[i];
-                if ((unsigned)ox < (unsigned)KW) {
+            const uint16_t *rb = bins + (rz * kRow + ry) * kBinsPerRow + tx + 3 - (KW - 1);
+            int e[KW + 1];
+#pragma unroll
+            for (int dx = 0; dx <= KW; ++dx) e[dx] = rb[dx];
+#pragma unroll
+            for (int dx = 0; dx < KW; ++dx) {
+                const int ox = KW - 1 - dx;
+                for (int i = e[dx]; i < e[dx + 1]; ++i) {
                     const size_t k = STAGED ? (size_t)i : (size_t)cand[i];
                     const T *w = w_src + 12 * k;
                     const T *A = A_src + 4 * k;
@@ -833,12 +835,11 @@ __device__ __forceinline__ void gather_tile(const DevGrid &g, long long N, int c
                                             T *__restrict__ dst, T *__restrict__ f_out, double inv_dt,
                                             StageSmem<T> &sm) {
     const int4 lo = sl.geo_lo[cs], dim = sl.geo_dim[cs];
-    const uint16_t *rs = sl.rows + (size_t)cs * (kRows + 1);
-    for (int i = threadIdx.x; i <= kRows; i += blockDim.x) sm.rows[i] = rs[i];
+    const uint16_t *bs = sl.bins + (size_t)cs * kBins;
+    for (int i = threadIdx.x; i < kBins; i += blockDim.x) sm.bins[i] = bs[i];
     __syncthreads();
-    const int nc = sm.rows[kRows];
+    const int nc = sm.bins[kBins - 1];
     const uint32_t *cand = sl.cand + dim.w;
-    const int8_t *relx = sl.relx + dim.w;
     const bool staged = nc <= Stage<T>::N;
     if (staged) {
         for (int i = threadIdx.x; i < nc; i += blockDim.x) {
@@ -850,7 +851,6 @@ __device__ __forceinline__ void gather_tile(const DevGrid &g, long long N, int c
                 for (int j = 0; j < KW; ++j) sm.w[12 * i + 4 * k + j] = __ldg(wm + 4 * k + j);
 #pragma unroll
             for (int k = 0; k < 3; ++k) sm.A[4 * i + k] = ld<COH>(A + 4 * (size_t)m + k);
-            sm.relx[i] = relx[i];
         }
         __syncthreads();
     }
@@ -858,8 +858,8 @@ __device__ __forceinline__ void gather_tile(const DevGrid &g, long long N, int c
     if (tx < dim.x && ty < dim.y && tz < dim.z) {
         T acc[3];
         const bool hit = staged
-                             ? gather_cell<T, KW, true, COH>(tx, ty, tz, sm.rows, sm.relx, cand, sm.w, sm.A, acc)
-                             : gather_cell<T, KW, false, COH>(tx, ty, tz, sm.rows, relx, cand, wts, A, acc);
+                             ? gather_cell<T, KW, true, COH>(tx, ty, tz, sm.bins, cand, sm.w, sm.A, acc)
+                             : gather_cell<T, KW, false, COH>(tx, ty, tz, sm.bins, cand, wts, A, acc);
         if (hit) {
             const int cx = wrap_add(lo.x, tx, g.n[0]);
             const int cy = wrap_add(lo.y, ty, g.n[1]);
@@ -993,7 +993,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_mdf_passes(PassArgs<T> a) {
                 s_off[k] = tot;
                 s_lo[k] = a.sl.geo_lo[cs];
                 s_dim[k] = a.sl.geo_dim[cs];
-                tot += a.sl.rows[(size_t)cs * (kRows + 1) + kRows];
+                tot += a.sl.bins[(size_t)cs * kBins + kBins - 1];
             }
             s_off[ok ? nmine : 0] = tot;
             s_nmine = nmine;
@@ -1006,8 +1006,8 @@ __global__ void __launch_bounds__(kBlock, 1) k_mdf_passes(PassArgs<T> a) {
         if (staged) {
             for (int k = 0; k < nmine; ++k) {
                 const int cs = s0 + blockIdx.x + k * gridDim.x;
-                const uint16_t *rs = a.sl.rows + (size_t)cs * (kRows + 1);
-                for (int i = threadIdx.x; i <= kRows; i += blockDim.x) lv.rows[k * (kRows + 1) + i] = rs[i];
+                const uint16_t *bs = a.sl.bins + (size_t)cs * kBins;
+                for (int i = threadIdx.x; i < kBins; i += blockDim.x) lv.bins[k * kBins + i] = bs[i];
                 const int b = s_dim[k].w, off = s_off[k], nc = s_off[k + 1] - off;
                 {
                     // the tile's u values (every cell of the tile; only band cells are written)
@@ -1022,7 +1022,6 @@ __global__ void __launch_bounds__(kBlock, 1) k_mdf_passes(PassArgs<T> a) {
                 for (int i = threadIdx.x; i < nc; i += blockDim.x) {
                     const uint32_t mk = a.sl.cand[b + i];
                     lv.ids[off + i] = mk;
-                    lv.relx[off + i] = a.sl.relx[b + i];
                     const T *wm = a.ms.wts + 12 * (size_t)mk;
 #pragma unroll
                     for (int q = 0; q < 3; ++q)
@@ -1063,9 +1062,8 @@ __global__ void __launch_bounds__(kBlock, 1) k_mdf_passes(PassArgs<T> a) {
                     const int off = s_off[k];
                     T acc[3];
                     if (tx < dim.x && ty < dim.y && tz < dim.z &&
-                        gather_cell<T, KW, true, true>(tx, ty, tz, lv.rows + k * (kRows + 1), lv.relx + off,
-                                                       nullptr, lv.w + 12 * (size_t)off, lv.A + 4 * (size_t)off,
-                                                       acc)) {
+                        gather_cell<T, KW, true, true>(tx, ty, tz, lv.bins + k * kBins, nullptr,
+                                                       lv.w + 12 * (size_t)off, lv.A + 4 * (size_t)off, acc)) {
                         const int4 lo = s_lo[k];
                         const long long c = ((long long)wrap_add(lo.z, tz, g.n[2]) * g.n[1] +
                                              wrap_add(lo.y, ty, g.n[1])) * g.n[0] + wrap_add(lo.x, tx, g.n[0]);
@@ -1132,8 +1130,7 @@ static int build_slots(ib_ctx *ctx, Arena &ar, const DevGrid &g, int M, int nden
     uint32_t *scratch = ar.take<uint32_t>(scan_workspace(ndense));
     sl.dense_of = ar.take<uint32_t>(ncompact_cap);
     sl.cand = ar.take<uint32_t>(cand_cap);
-    sl.relx = ar.take<int8_t>(cand_cap);
-    sl.rows = ar.take<uint16_t>((size_t)ncompact_cap * (kRows + 1));
+    sl.bins = ar.take<uint16_t>((size_t)ncompact_cap * kBins);
     sl.geo_lo = ar.take<int4>(ncompact_cap);
     sl.geo_dim = ar.take<int4>(ncompact_cap);
     if (!ar.ok())
