@@ -90,7 +90,7 @@ __device__ __forceinline__ void interp_marker(const T *__restrict__ u, const Dev
         iz[k] = wrap_add(az, k, g.n[2]);
     }
     T a0 = 0, a1 = 0, a2 = 0;
-#pragma unroll
+#pragma unroll 1
     for (int kz = 0; kz < KW; ++kz) {
 #pragma unroll
         for (int ky = 0; ky < KW; ++ky) {
@@ -791,10 +791,10 @@ __device__ __forceinline__ bool gather_cell(int tx, int ty, int tz, const uint16
                                             const T *w_src, const T *A_src, T acc[3]) {
     bool hit = false;
     acc[0] = acc[1] = acc[2] = T(0);
-#pragma unroll
+#pragma unroll 1
     for (int dz = 0; dz < KW; ++dz) {
         const int rz = tz + 3 - (KW - 1) + dz, oz = KW - 1 - dz;
-#pragma unroll
+#pragma unroll 1
         for (int dy = 0; dy < KW; ++dy) {
             const int ry = ty + 3 - (KW - 1) + dy, oy = KW - 1 - dy;
             const uint16_t *rb = bins + (rz * kRow + ry) * kBinsPerRow + tx + 3 - (KW - 1);
@@ -880,6 +880,17 @@ __device__ __forceinline__ void gather_tile(const DevGrid &g, long long N, int c
         }
     }
     __syncthreads();
+}
+
+// Out-of-line copy of gather_tile for the persistent kernel's fallback path
+// (wavefronts whose tiles do not fit the per-CTA staging), so that its code
+// stays out of the hot loop.
+template <typename T, int KW>
+__device__ __noinline__ void gather_tile_fallback(const DevGrid g, long long N, int cs, const Slots sl,
+                                                  const T *wts, const T *A, T *dst, T *f_out, double inv_dt,
+                                                  unsigned char *smem) {
+    StageSmem<T> sm(smem);
+    gather_tile<T, KW, true>(g, N, cs, sl, wts, A, dst, f_out, inv_dt, sm);
 }
 
 template <typename T, int KER>
@@ -1080,7 +1091,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_mdf_passes(PassArgs<T> a) {
                 }
             } else {
                 for (int cs = s0 + blockIdx.x; cs < s1; cs += gridDim.x)
-                    gather_tile<T, KW, true>(g, N, cs, a.sl, a.ms.wts, a.ms.A, a.u, a.f_out, inv_dt, sm);
+                    gather_tile_fallback<T, KW>(g, N, cs, a.sl, a.ms.wts, a.ms.A, a.u, a.f_out, inv_dt, smem_raw);
             }
             if (!grid_sync(a.bar, a.st)) return;
         }
