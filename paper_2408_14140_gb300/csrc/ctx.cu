@@ -229,6 +229,15 @@ int ib_ctx_create(ib_ctx **ctx, size_t workspace_bytes) {
         delete c;
         return set_error(IB_ERR_CUDA, "status latch allocation failed");
     }
+    if (cudaHostAlloc((void **)&c->h_nlev, sizeof(int), cudaHostAllocDefault) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->nlev_ev, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(c->status);
+        cudaFree(c->ws);
+        delete c;
+        return set_error(IB_ERR_CUDA, "context host word / event creation failed");
+    }
+    *c->h_nlev = 0;
     *ctx = c;
     return IB_OK;
 }
@@ -285,6 +294,8 @@ int ib_ctx_destroy(ib_ctx *c) {
             cudaEventDestroy(pr.second);
         }
     for (auto e : c->pool) cudaEventDestroy(e);
+    cudaEventDestroy(c->nlev_ev);
+    cudaFreeHost(c->h_nlev);
     cudaFree(c->ws);
     cudaFree(c->status);
     delete c;

@@ -117,6 +117,13 @@ struct ib_ctx {
     int timing;          // record phase events
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending[IB_PHASE_COUNT];
     std::vector<cudaEvent_t> pool;
+    // wavefront count of the last multidirect-forcing call (read back
+    // asynchronously): how many wavefronts the next call enqueues as separate
+    // kernels before the persistent kernel takes the rest
+    int *h_nlev;         // pinned host word
+    cudaEvent_t nlev_ev;
+    int nlev_pending;
+    int nlev_hint;
 };
 
 namespace gbib {
