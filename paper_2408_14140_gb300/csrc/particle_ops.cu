@@ -50,17 +50,50 @@ __device__ __forceinline__ void block_sum(double v[NV]) {
 // particle (completion counter) adds the kVolSplit partial sums in slab order.
 // ---------------------------------------------------------------------------
 constexpr int kVolSplit = 8;
-constexpr int kVolThreads = 256;   // 8 warps; warp w takes rows w, w + 8, ...
-constexpr int kVolMaxBox = 64;     // cells per axis of one particle's box (shared-node path)
+constexpr int kVolThreads = 256;   // 8 warps
+constexpr int kVolMaxBox = 64;     // cells per axis of one particle's box (tabulated path)
 constexpr int kVolAx = kVolMaxBox + 1;
 // two node planes + per-axis tables (node squares, cell offsets, cell squares)
 constexpr size_t kVolSmem = (2 * kVolAx * kVolAx + 9 * kVolAx) * sizeof(double);
 
-// Most of this kernel's cost is GB300's low FP64 rate, so FP64 work is
-// kept per node and per row where possible: squared node and cell-centre
-// offsets along each axis are tabulated once per CTA; a node plane computes
-// phi only inside the surface shell, whose x-range per node row is known in
-// closed form; a cell row visits only cells within R + 0.8661 h.
+// Exclusive scan of cnt[0..n) into pre[0..n] by warp 0 (n may exceed 32).
+__device__ __forceinline__ void warp0_scan(const int *cnt, int *pre, int n) {
+    if (threadIdx.x >= 32) return;
+    const int lane = threadIdx.x;
+    int carry = 0;
+    for (int base = 0; base < n; base += 32) {
+        const int v = base + lane < n ? cnt[base + lane] : 0;
+        int x = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (base + lane < n) pre[base + lane] = carry + x - v;
+        carry += __shfl_sync(0xffffffffu, x, 31);
+    }
+    if (lane == 0) pre[n] = carry;
+}
+
+// Row of flat index t: largest r with pre[r] <= t (pre ascending, pre[0] = 0).
+__device__ __forceinline__ int find_row(const int *pre, int nrows, int t) {
+    int a = 0, b = nrows - 1;
+    while (a < b) {
+        const int mid = (a + b + 1) >> 1;
+        if (pre[mid] <= t) a = mid;
+        else b = mid - 1;
+    }
+    return a;
+}
+
+// Most of this kernel's cost is GB300's low FP64 rate, and FP64 pipe time is
+// charged per warp instruction whatever the number of active lanes.  So each
+// plane is walked as flat lists that keep warps full and uniform:
+//   * shell nodes (|x - X_r| within 1.75 h of the surface): phi in FP64;
+//   * interior cells (centre deeper than R - 0.8661 h, shrunk by one cell,
+//     all corners inside: alpha = 1): plain sums;
+//   * boundary cells (the rest within R + 0.8661 h): alpha from the corners.
+// Per-row index ranges come from FP32 square roots widened by a cell; every
+// node and boundary cell is still tested exactly in FP64.
 template <typename T>
 __global__ void __launch_bounds__(kVolThreads) k_volume(DevGrid g, const T *__restrict__ u, int P,
                                                         const double *__restrict__ Xr,
@@ -70,9 +103,13 @@ __global__ void __launch_bounds__(kVolThreads) k_volume(DevGrid g, const T *__re
                                                         double *Irxu, double *vol, DevStatus *st) {
     extern __shared__ double s_vol[];
     __shared__ int s_last;
+    // per-row work lists (rows <= kVolAx)
+    __shared__ int r_na[kVolAx], r_nb[kVolAx], r_nc[2][kVolAx], r_ca[kVolAx], r_cb[kVolAx];
+    __shared__ int r_ia[kVolAx], r_ib[kVolAx], r_ic[kVolAx];
+    __shared__ int p_node[kVolAx + 1], p_int[kVolAx + 1], p_bnd[kVolAx + 1];
+    __shared__ int c_node[kVolAx], c_int[kVolAx], c_bnd[kVolAx];
     const int p = blockIdx.x / kVolSplit, split = blockIdx.x % kVolSplit;
     if (p >= P) return;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const double c[3] = {Xr[3 * p], Xr[3 * p + 1], Xr[3 * p + 2]};
     const double Rp = radius[p];
     double acc[7] = {0, 0, 0, 0, 0, 0, 0};
@@ -98,13 +135,12 @@ __global__ void __launch_bounds__(kVolThreads) k_volume(DevGrid g, const T *__re
         const double rin2 = rin > 0 ? rin * rin : -1.0, rout2 = rout * rout;
         const double sl = fmax(0.0, Rp - 1.75 * h), sh = Rp + 1.75 * h;
         const double sl2 = sl * sl, sh2 = sh * sh;
+        const int lo0w = wrap_int(lo[0], g.n[0]);
         const bool tab = dims[0] <= kVolMaxBox && dims[1] <= kVolMaxBox && dims[2] <= kVolMaxBox;
-        const int nx = dims[0] + 1, plane = nx * (dims[1] + 1);
-        double *phi2 = s_vol;                    // [2][plane]
-        double *tb = s_vol + 2 * kVolAx * kVolAx;  // [9][kVolAx]
-        // tb[a*kVolAx + i]: node offset^2 along axis a; tb[(3+a)*..]: cell-centre offset;
-        // tb[(6+a)*..]: cell-centre offset^2
         if (tab) {
+            const int nx = dims[0] + 1, plane = nx * (dims[1] + 1);
+            double *phi2 = s_vol;
+            double *tb = s_vol + 2 * kVolAx * kVolAx;
             for (int a = 0; a < 3; ++a)
                 for (int i = threadIdx.x; i <= dims[a]; i += blockDim.x) {
                     const double xn = g.org[a] + (double)(lo[a] + i) * h - c[a];
@@ -114,68 +150,122 @@ __global__ void __launch_bounds__(kVolThreads) k_volume(DevGrid g, const T *__re
                     tb[(6 + a) * kVolAx + i] = xc * xc;
                 }
             __syncthreads();
-        }
-        auto cell_off = [&](int a, int i) -> double {
-            return tab ? tb[(3 + a) * kVolAx + i] : g.org[a] + ((double)(lo[a] + i) + 0.5) * h - c[a];
-        };
-        auto cell_sq = [&](int a, int i) -> double {
-            if (tab) return tb[(6 + a) * kVolAx + i];
-            const double x = cell_off(a, i);
-            return x * x;
-        };
-        auto node_plane = [&](int kn, double *buf) {
-            if (!tab) return;
-            const double zz = tb[2 * kVolAx + kn];
-            for (int j = warp; j <= dims[1]; j += kVolThreads / 32) {
-                const double dyz = tb[kVolAx + j] + zz;
-                if (dyz >= sh2) continue;
-                // shell nodes of this row: sl2 < x^2 + dyz < sh2
-                const double xo = sqrt(sh2 - dyz);
-                const int i_lo = max(0, (int)floor((c[0] - xo - g.org[0]) * g.inv_h) - lo[0] - 1);
-                const int i_hi = min(dims[0], (int)ceil((c[0] + xo - g.org[0]) * g.inv_h) - lo[0] + 1);
-                for (int i = i_lo + lane; i <= i_hi; i += 32) {
-                    const double d2 = tb[i] + dyz;
+            const float fih = (float)g.inv_h;
+            // index range [first, last] of positions x_i = base + i h (i in [0, n)) with
+            // |x_i| <= w, widened by one on each side; empty when first > last
+            auto range = [&](double base, float w, int n, int &first, int &last) {
+                first = max(0, (int)floorf((float)(-w - base) * fih) - 1);
+                last = min(n - 1, (int)ceilf((float)(w - base) * fih) + 1);
+            };
+            auto node_plane = [&](int kn, double *buf) {
+                const double zz = tb[2 * kVolAx + kn];
+                const int rows = dims[1] + 1;
+                const double xb = g.org[0] + (double)lo[0] * h - c[0];  // x of node 0
+                for (int j = threadIdx.x; j < rows; j += blockDim.x) {
+                    const double dyz = tb[kVolAx + j] + zz;
+                    int a0 = 0, n0 = 0, a1 = 0, n1 = 0;
+                    if (dyz < sh2) {
+                        const float xo = sqrtf((float)(sh2 - dyz));
+                        const float xi = sl2 > dyz ? sqrtf((float)(sl2 - dyz)) : -1.0f;
+                        int f, l;
+                        range(xb, xo, nx, f, l);
+                        if (xi > 2.0f * (float)h) {
+                            // two intervals: left [f, f2], right [l2, l]
+                            int f2, l2;
+                            range(xb, xi, nx, f2, l2);  // widened inner range
+                            const int li = f2 + 2, ri = l2 - 2;  // shrink back: inner exclusion
+                            a0 = f;
+                            n0 = max(0, min(l, li) - f + 1);
+                            a1 = max(ri, f);
+                            n1 = ri > f && l >= a1 ? l - a1 + 1 : 0;
+                            if (li >= ri) {  // exclusion vanished: one interval
+                                n0 = l - f + 1;
+                                n1 = 0;
+                            }
+                        } else {
+                            a0 = f;
+                            n0 = max(0, l - f + 1);
+                        }
+                    }
+                    r_na[j] = a0, r_nc[0][j] = n0, r_nb[j] = a1, r_nc[1][j] = n1;
+                    c_node[j] = n0 + n1;
+                }
+                __syncthreads();
+                warp0_scan(c_node, p_node, rows);
+                __syncthreads();
+                const int tot = p_node[rows];
+                for (int q = threadIdx.x; q < tot; q += blockDim.x) {
+                    const int j = find_row(p_node, rows, q);
+                    const int k = q - p_node[j];
+                    const int i = k < r_nc[0][j] ? r_na[j] + k : r_nb[j] + (k - r_nc[0][j]);
+                    const double d2 = tb[i] + tb[kVolAx + j] + zz;
                     if (d2 >= sl2 && d2 < sh2) buf[j * nx + i] = sqrt(d2) * iR - 1.0;
                 }
-            }
-        };
-        const int lo0w = wrap_int(lo[0], g.n[0]);
-        node_plane(z0, phi2 + (z0 & 1) * plane);
-        for (int kz = z0; kz < z1; ++kz) {
-            node_plane(kz + 1, phi2 + ((kz + 1) & 1) * plane);
-            __syncthreads();
-            const double *b0 = phi2 + (kz & 1) * plane, *b1 = phi2 + ((kz + 1) & 1) * plane;
-            const int k = lo[2] + kz;
-            const double rz = cell_off(2, kz), rz2 = cell_sq(2, kz);
-            const int kw = wrap_int(k, g.n[2]);
-            for (int j = warp; j < dims[1]; j += kVolThreads / 32) {
-                const double ry = cell_off(1, j);
-                const double ryz2 = cell_sq(1, j) + rz2;
-                const double w2 = rout2 - ryz2;
-                if (w2 < 0.0) continue;
-                const double half = sqrt(w2);
-                const int ia = max(0, (int)floor((c[0] - half - g.org[0]) * g.inv_h - 0.5) - lo[0]);
-                const int ib = min(dims[0] - 1, (int)ceil((c[0] + half - g.org[0]) * g.inv_h - 0.5) - lo[0]);
-                const long long rowbase = ((long long)kw * g.n[1] + wrap_int(lo[1] + j, g.n[1])) * g.n[0];
-                for (int i = ia + lane; i <= ib; i += 32) {
-                    const double d2 = cell_sq(0, i) + ryz2;
+            };
+            node_plane(z0, phi2 + (z0 & 1) * plane);
+            for (int kz = z0; kz < z1; ++kz) {
+                node_plane(kz + 1, phi2 + ((kz + 1) & 1) * plane);
+                // cell rows of plane kz: interior range and the boundary ranges around it
+                const double rz = tb[5 * kVolAx + kz], rz2 = tb[8 * kVolAx + kz];
+                const double xcb = g.org[0] + ((double)lo[0] + 0.5) * h - c[0];  // x of cell 0
+                for (int j = threadIdx.x; j < dims[1]; j += blockDim.x) {
+                    const double ryz2 = tb[7 * kVolAx + j] + rz2;
+                    int ia = 0, ib = -1, ja = 0, jb = -1;
+                    if (ryz2 <= rout2) {
+                        range(xcb, sqrtf((float)(rout2 - ryz2)), dims[0], ia, ib);
+                        if (ryz2 < rin2) {
+                            range(xcb, sqrtf((float)(rin2 - ryz2)), dims[0], ja, jb);
+                            ja += 2;  // undo the widening and shrink one more cell: all surely inside
+                            jb -= 2;
+                        }
+                    }
+                    if (jb < ja) {
+                        ja = ib + 1;  // no interior: one boundary interval [ia, ib]
+                        jb = ib;
+                    }
+                    r_ia[j] = ia;
+                    r_ib[j] = ib;
+                    r_ic[j] = ja;  // interior [ja, jb] with jb stored implicitly by count
+                    c_int[j] = jb >= ja ? jb - ja + 1 : 0;
+                    r_ca[j] = max(0, min(ja - 1, ib) - ia + 1);   // left boundary [ia, ja-1]
+                    r_cb[j] = jb >= ja ? max(0, ib - jb) : 0;      // right boundary [jb+1, ib]
+                    c_bnd[j] = r_ca[j] + r_cb[j];
+                }
+                __syncthreads();
+                warp0_scan(c_int, p_int, dims[1]);
+                warp0_scan(c_bnd, p_bnd, dims[1]);
+                __syncthreads();
+                const double *b0 = phi2 + (kz & 1) * plane, *b1 = phi2 + ((kz + 1) & 1) * plane;
+                const long long plane_off = (long long)wrap_int(lo[2] + kz, g.n[2]) * g.n[1];
+                // interior cells: alpha = 1
+                const int nint = p_int[dims[1]];
+                for (int q = threadIdx.x; q < nint; q += blockDim.x) {
+                    const int j = find_row(p_int, dims[1], q);
+                    const int i = r_ic[j] + (q - p_int[j]);
+                    const double rx = tb[3 * kVolAx + i], ry = tb[4 * kVolAx + j];
+                    const long long cc = (plane_off + wrap_int(lo[1] + j, g.n[1])) * g.n[0] + wrap_add(lo0w, i, g.n[0]);
+                    const double u0 = (double)u[cc], u1 = (double)u[N + cc], u2 = (double)u[2 * N + cc];
+                    acc[0] += u0;
+                    acc[1] += u1;
+                    acc[2] += u2;
+                    acc[3] += ry * u2 - rz * u1;
+                    acc[4] += rz * u0 - rx * u2;
+                    acc[5] += rx * u1 - ry * u0;
+                    acc[6] += 1.0;
+                }
+                // boundary cells: alpha from the corners
+                const int nbnd = p_bnd[dims[1]];
+                for (int q = threadIdx.x; q < nbnd; q += blockDim.x) {
+                    const int j = find_row(p_bnd, dims[1], q);
+                    const int k = q - p_bnd[j];
+                    const int i = k < r_ca[j] ? r_ia[j] + k : r_ic[j] + c_int[j] + (k - r_ca[j]);
+                    const double d2 = tb[6 * kVolAx + i] + tb[7 * kVolAx + j] + rz2;
                     if (d2 > rout2) continue;
                     double al = 1.0;
                     if (!(d2 < rin2)) {
-                        double ph[8];
-                        if (tab) {
-                            const int q = j * nx + i;
-                            ph[0] = b0[q], ph[1] = b0[q + 1], ph[2] = b0[q + nx], ph[3] = b0[q + nx + 1];
-                            ph[4] = b1[q], ph[5] = b1[q + 1], ph[6] = b1[q + nx], ph[7] = b1[q + nx + 1];
-                        } else {
-#pragma unroll
-                            for (int m = 0; m < 8; ++m) {
-                                const double x = g.org[0] + (double)(lo[0] + i + (m & 1)) * h - c[0];
-                                const double y = g.org[1] + (double)(lo[1] + j + ((m >> 1) & 1)) * h - c[1];
-                                const double z = g.org[2] + (double)(k + ((m >> 2) & 1)) * h - c[2];
-                                ph[m] = sqrt(x * x + y * y + z * z) * iR - 1.0;
-                            }
-                        }
+                        const int qn = j * nx + i;
+                        const double ph[8] = {b0[qn], b0[qn + 1], b0[qn + nx], b0[qn + nx + 1],
+                                              b1[qn], b1[qn + 1], b1[qn + nx], b1[qn + nx + 1]};
                         double num = 0.0, den = 0.0;
 #pragma unroll
                         for (int m = 0; m < 8; ++m) {
@@ -185,8 +275,47 @@ __global__ void __launch_bounds__(kVolThreads) k_volume(DevGrid g, const T *__re
                         al = den > 0.0 ? num / den : 0.5;
                         if (al == 0.0) continue;
                     }
-                    const double rx = cell_off(0, i);
-                    const long long cc = rowbase + wrap_add(lo0w, i, g.n[0]);
+                    const double rx = tb[3 * kVolAx + i], ry = tb[4 * kVolAx + j];
+                    const long long cc = (plane_off + wrap_int(lo[1] + j, g.n[1])) * g.n[0] + wrap_add(lo0w, i, g.n[0]);
+                    const double u0 = (double)u[cc], u1 = (double)u[N + cc], u2 = (double)u[2 * N + cc];
+                    acc[0] += al * u0;
+                    acc[1] += al * u1;
+                    acc[2] += al * u2;
+                    acc[3] += al * (ry * u2 - rz * u1);
+                    acc[4] += al * (rz * u0 - rx * u2);
+                    acc[5] += al * (rx * u1 - ry * u0);
+                    acc[6] += al;
+                }
+                __syncthreads();
+            }
+        } else {
+            // boxes wider than kVolMaxBox: every cell of the slab, corners evaluated directly
+            for (int kz = z0; kz < z1; ++kz) {
+                const int k = lo[2] + kz;
+                const double rz = g.org[2] + ((double)k + 0.5) * h - c[2];
+                const long long plane_off = (long long)wrap_int(k, g.n[2]) * g.n[1];
+                for (int q = threadIdx.x; q < dims[0] * dims[1]; q += blockDim.x) {
+                    const int j = q / dims[0], i = q - j * dims[0];
+                    const double rx = g.org[0] + ((double)(lo[0] + i) + 0.5) * h - c[0];
+                    const double ry = g.org[1] + ((double)(lo[1] + j) + 0.5) * h - c[1];
+                    const double d2 = rx * rx + ry * ry + rz * rz;
+                    if (d2 > rout2) continue;
+                    double al = 1.0;
+                    if (!(d2 < rin2)) {
+                        double num = 0.0, den = 0.0;
+#pragma unroll
+                        for (int m = 0; m < 8; ++m) {
+                            const double x = g.org[0] + (double)(lo[0] + i + (m & 1)) * h - c[0];
+                            const double y = g.org[1] + (double)(lo[1] + j + ((m >> 1) & 1)) * h - c[1];
+                            const double z = g.org[2] + (double)(k + ((m >> 2) & 1)) * h - c[2];
+                            const double ph = sqrt(x * x + y * y + z * z) * iR - 1.0;
+                            if (-ph > 0.0) num += -ph;
+                            den += fabs(ph);
+                        }
+                        al = den > 0.0 ? num / den : 0.5;
+                        if (al == 0.0) continue;
+                    }
+                    const long long cc = (plane_off + wrap_int(lo[1] + j, g.n[1])) * g.n[0] + wrap_add(lo0w, i, g.n[0]);
                     const double u0 = (double)u[cc], u1 = (double)u[N + cc], u2 = (double)u[2 * N + cc];
                     acc[0] += al * u0;
                     acc[1] += al * u1;
@@ -197,7 +326,6 @@ __global__ void __launch_bounds__(kVolThreads) k_volume(DevGrid g, const T *__re
                     acc[6] += al;
                 }
             }
-            __syncthreads();
         }
         const double h3 = h * h * h;
 #pragma unroll
