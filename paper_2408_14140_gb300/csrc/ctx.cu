@@ -229,13 +229,12 @@ int ib_ctx_create(ib_ctx **ctx, size_t workspace_bytes) {
         delete c;
         return set_error(IB_ERR_CUDA, "status latch allocation failed");
     }
-    if (cudaHostAlloc((void **)&c->h_nlev, sizeof(int), cudaHostAllocDefault) != cudaSuccess ||
-        cudaEventCreateWithFlags(&c->nlev_ev, cudaEventDisableTiming) != cudaSuccess) {
+    if (cudaHostAlloc((void **)&c->h_nlev, sizeof(int), cudaHostAllocDefault) != cudaSuccess) {
         cudaGetLastError();
         cudaFree(c->status);
         cudaFree(c->ws);
         delete c;
-        return set_error(IB_ERR_CUDA, "context host word / event creation failed");
+        return set_error(IB_ERR_CUDA, "context host word allocation failed");
     }
     *c->h_nlev = 0;
     *ctx = c;
@@ -294,7 +293,6 @@ int ib_ctx_destroy(ib_ctx *c) {
             cudaEventDestroy(pr.second);
         }
     for (auto e : c->pool) cudaEventDestroy(e);
-    cudaEventDestroy(c->nlev_ev);
     cudaFreeHost(c->h_nlev);
     cudaFree(c->ws);
     cudaFree(c->status);

@@ -121,8 +121,6 @@ struct ib_ctx {
     // asynchronously): how many wavefronts the next call enqueues as separate
     // kernels before the persistent kernel takes the rest
     int *h_nlev;         // pinned host word
-    cudaEvent_t nlev_ev;
-    int nlev_pending;
     int nlev_hint;
 };
 

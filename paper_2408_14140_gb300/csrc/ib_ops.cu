@@ -1370,14 +1370,11 @@ static int run_mdf(ib_ctx *ctx, const DevGrid &g, void *u, const ib_particles *p
     a.dt = dt;
     a.bar = bar;
     a.st = ctx->status;
-    // wavefronts enqueued as separate kernels: the count of the last call
-    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
-    cudaStreamIsCapturing(s, &cap);
-    if (cap == cudaStreamCaptureStatusNone && ctx->nlev_pending && cudaEventQuery(ctx->nlev_ev) == cudaSuccess) {
-        ctx->nlev_hint = *ctx->h_nlev;
-        ctx->nlev_pending = 0;
-    }
-    cudaGetLastError();  // a not-ready query is not an error
+    // wavefronts enqueued as separate kernels: the count the last call on this
+    // context copied to a pinned host word (read without synchronising: an
+    // aligned 4-byte word is either the old or the new count; a short count
+    // only leaves more wavefronts to the persistent kernel)
+    ctx->nlev_hint = *(volatile int *)ctx->h_nlev;
     const int Lenq = ctx->nlev_hint < P ? ctx->nlev_hint : P;
     a.L0 = Lenq;
     // one timed phase: the wavefront kernels and the persistent remainder
@@ -1403,11 +1400,7 @@ static int run_mdf(ib_ctx *ctx, const DevGrid &g, void *u, const ib_particles *p
         cudaLaunchCooperativeKernel((const void *)k_mdf_passes<T, KER>, nblocks, kBlock, args, smem, s);
     if (e != cudaSuccess) return set_error(IB_ERR_CUDA, "mdf launch: %s", cudaGetErrorString(e));
     tpass.stop();
-    if (cap == cudaStreamCaptureStatusNone) {
-        cudaMemcpyAsync(ctx->h_nlev, lo.nlev, sizeof(int), cudaMemcpyDeviceToHost, s);
-        cudaEventRecord(ctx->nlev_ev, s);
-        ctx->nlev_pending = 1;
-    }
+    cudaMemcpyAsync(ctx->h_nlev, lo.nlev, sizeof(int), cudaMemcpyDeviceToHost, s);
     return check_launch("ib_multidirect_forcing");
 }
 
