@@ -78,9 +78,9 @@ def band_cells(case, kernel_width=3):
     return int(np.unique(np.concatenate(cells)).size)
 
 
-def wavefront_levels(case, kernel_width=3):
-    """Number of wavefronts of the sequential particle order (same conflict
-    test as the library: centre distance < rho_p + rho_q + sqrt(3) W h)."""
+def wavefront_levels(case, kernel_width=3, return_levels=False):
+    """Wavefronts of the sequential particle order (same conflict test as the
+    library: centre distance < rho_p + rho_q + sqrt(3) W h + h/16)."""
     P = case.P
     rho = np.array([np.max(np.linalg.norm(case.R[case.moff[p]:case.moff[p + 1]], axis=1))
                     for p in range(P)])
@@ -89,9 +89,44 @@ def wavefront_levels(case, kernel_width=3):
     for p in range(P):
         d = case.Xr[:p] - case.Xr[p]
         d -= L * np.rint(d / L)
-        conf = np.sqrt(np.sum(d * d, axis=1)) < rho[:p] + rho[p] + np.sqrt(3) * kernel_width * case.h
+        conf = np.sqrt(np.sum(d * d, axis=1)) < (rho[:p] + rho[p] + np.sqrt(3) * kernel_width * case.h
+                                                  + case.h / 16)
         lev[p] = 1 + (lev[:p][conf].max() if conf.any() else -1)
+    if return_levels:
+        return lev
     return int(lev.max() + 1) if P else 0
+
+
+def level_band_cells(case, kernel_width=3):
+    """(band cells, markers) of every wavefront: the cells a wavefront's gather
+    kernel must read and write once per pass, and the markers it spreads."""
+    lev = wavefront_levels(case, kernel_width, return_levels=True)
+    out = []
+    for L in range(int(lev.max()) + 1 if case.P else 0):
+        ps = np.nonzero(lev == L)[0]
+        sub = case.__class__(**{**case.__dict__})
+        idx = np.concatenate([np.arange(case.moff[p], case.moff[p + 1]) for p in ps])
+        sub.Xr = case.Xr[ps]
+        sub.R = case.R[idx]
+        sub.moff = np.concatenate([[0], np.cumsum(np.diff(case.moff)[ps])])
+        out.append((band_cells(sub, kernel_width), int(idx.size)))
+    return out
+
+
+def recorded_traffic(kernel):
+    """DRAM bytes per launch of `kernel` recorded under profiles/ by an ncu
+    capture, or None when the kernel source changed since (hash mismatch)."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "traffic_%s.txt" % kernel)
+    src = os.path.join(ROOT, "paper_2408_14140_gb300", "csrc", "ib_ops.cu")
+    try:
+        rec = dict(line.split(":", 1) for line in open(path) if ":" in line)
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+        if rec.get("source_sha256", "").strip() != sha:
+            return None
+        return float(rec["bytes_per_launch"])
+    except Exception:
+        return None
 
 
 def interior_cells(case):
@@ -117,7 +152,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
-                 "--format=csv,noheader,nounits", "-lms", "100"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.th = threading.Thread(target=self._read, daemon=True)
             self.th.start()
@@ -210,13 +245,14 @@ class Runner:
                                     self.I1[0], self.I0[0], self.I1[1], self.I0[1], Fc_out=self.Fc)
 
 
-def launches_per_step():
+def launches_per_step(Ns, levels):
     """Library kernels per step on this workload (P * 512 = 32768 dense tiles,
     so each scan is one kernel): volume 1 x 2 calls; multidirect forcing:
     prep, conflicts, levels, marker order, tile count, scan, flags, scan,
-    compact, fill, sort, level ranges, passes (13); force/torque 1;
-    collision + Newton-Euler 2."""
-    return 2 + 13 + 1 + 2
+    compact, fill, sort, level ranges (12), one interpolation and one gather
+    kernel per wavefront and pass, the persistent remainder kernel (1);
+    force/torque 1; collision + Newton-Euler 2."""
+    return 2 + 12 + 2 * Ns * levels + 1 + 1 + 2
 
 
 def time_steps(runner, steps, warmup, flush, use_graph):
@@ -369,17 +405,23 @@ def run_gpu(args):
                              runner=r)
         del r
 
-    # algorithmic traffic of the dominant kernel (the persistent Ns-pass kernel)
+    # algorithmic traffic: the whole Ns-pass phase, and per launch of the
+    # dominant kernel (the per-wavefront gather: read + write u on the
+    # wavefront's band, read the markers' sources)
     B = band_cells(case)
+    lb = level_band_cells(case)
+    nlev = len(lb)
     out = {}
     for prec, res in results.items():
         s = 8 if prec == api.IB_F64 else 4
         alg_mdf = 6 * s * B + (24 + 8 + 24) * M
         ms_pass, n_pass = res["kt"].get("mdf_passes", (float("nan"), 1))
         dur = ms_pass / n_pass / 1000.0
+        ms_g, n_g = res["kt"].get("mdf_gather", (float("nan"), 1))
+        alg_g = sum(6 * s * bl + 3 * s * ml for bl, ml in lb) / max(1, nlev)
         step_s = res["t"] / args.steps
         out[prec] = dict(step_s=step_s, value=world * M * Ns / step_s,
-                         alg_mdf=alg_mdf, mdf_dur=dur,
+                         alg_mdf=alg_mdf, mdf_dur=dur, alg_g=alg_g, g_dur=ms_g / n_g / 1000.0,
                          phases={k: round(v[0] / v[1] * 1000.0, 2) for k, v in res["kt"].items()},
                          e2e=res["e2e"], graphed=res["graphed"], clocks=res["clocks"])
     if rank != 0:
@@ -390,7 +432,8 @@ def run_gpu(args):
     hbm, hbm_src = peaks()
     f32 = out.get(api.IB_F32, out.get(api.IB_F64))
     f64 = out.get(api.IB_F64, f32)
-    achieved = f32["alg_mdf"] / f32["mdf_dur"] / 1e9
+    achieved = f32["alg_g"] / f32["g_dur"] / 1e9
+    traffic = recorded_traffic("k_gather_level")
     line = {
         "metric": METRIC,
         "value": f32["value"],
@@ -406,17 +449,19 @@ def run_gpu(args):
         "data": "synthetic",
         "config": {"workload": WORKLOAD_NAME, "grid": [256, 256, 256], "particles": case.P,
                    "markers": M, "Ns": Ns, "kernel": "roma3", "order": "sequential",
-                   "band_cells": B, "levels": wavefront_levels(case),
+                   "band_cells": B, "levels": nlev,
                    "parallelism": "replicas" if world > 1 else "single-gpu",
                    "l2": "flushed (512 MiB write) between timed steps",
                    "launch": "cuda-graph replay" if f32["graphed"] else "eager"},
         "e2e": None,
-        "gpu_launches": args.steps * launches_per_step(),
-        "roofline": {"bound": "hbm", "kernel": "k_mdf_passes",
+        "gpu_launches": args.steps * launches_per_step(Ns, nlev),
+        "roofline": {"bound": "hbm", "kernel": "k_gather_level",
                      "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "peak_source": hbm_src,
-                     "algorithmic_bytes": f32["alg_mdf"], "duration_us": f32["mdf_dur"] * 1e6,
-                     "traffic": None},
+                     "algorithmic_bytes_per_launch": f32["alg_g"],
+                     "duration_us": f32["g_dur"] * 1e6, "traffic": traffic},
+        "pass_phase": {"algorithmic_bytes": f32["alg_mdf"], "duration_us": f32["mdf_dur"] * 1e6,
+                       "achieved_gbs": f32["alg_mdf"] / f32["mdf_dur"] / 1e9},
         "phases_us": f32["phases"],
         "clocks": f32["clocks"],
         "fp64": {"value": f64["value"], "ms_per_step": f64["step_s"] * 1000.0,
@@ -493,7 +538,7 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gbib", choices=["gbib", "reference"])
     ap.add_argument("--no-graph", action="store_true")

@@ -138,7 +138,9 @@ GBIB_API int ib_ctx_sm_count(const ib_ctx *ctx);
 #define IB_PHASE_VOLUME 4      /* particle_volume_integrals                 */
 #define IB_PHASE_FORCE 5       /* particle_force_torque                     */
 #define IB_PHASE_COLLIDE 6     /* particle_collide_update                   */
-#define IB_PHASE_COUNT 7
+#define IB_PHASE_MDF_INTERP 7  /* each wavefront-pass interpolation kernel  */
+#define IB_PHASE_MDF_GATHER 8  /* each wavefront-pass gather kernel         */
+#define IB_PHASE_COUNT 9
 GBIB_API int ib_ctx_set_timing(ib_ctx *ctx, int enable);
 GBIB_API int ib_ctx_read_timing(ib_ctx *ctx, int phase, double *ms_total,
                                 int *launches);

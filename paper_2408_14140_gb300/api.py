@@ -36,7 +36,7 @@ SEQUENTIAL = 0
 SIMULTANEOUS = 1
 
 PHASES = {"mdf_prep": 0, "mdf_passes": 1, "spread": 2, "interp": 3, "volume": 4,
-          "force": 5, "collide": 6}
+          "force": 5, "collide": 6, "mdf_interp": 7, "mdf_gather": 8}
 
 EXPORTS = ["ib_ctx_create", "ib_ctx_reserve", "ib_ctx_destroy", "ib_ctx_status",
            "ib_last_error", "ib_workspace_needed", "ib_ctx_sm_count",

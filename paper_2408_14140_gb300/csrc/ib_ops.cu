@@ -1385,7 +1385,11 @@ static int run_mdf(ib_ctx *ctx, const DevGrid &g, void *u, const ib_particles *p
         cudaFuncSetAttribute(k_gather_level<T, KER>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsm);
         for (int L = 0; L < Lenq; ++L)
             for (int m = 0; m < Ns; ++m) {
-                k_interp_level<T, KER><<<gi, 256, 0, s>>>(a, L);
+                {
+                    PhaseTimer ti(ctx, IB_PHASE_MDF_INTERP, s);
+                    k_interp_level<T, KER><<<gi, 256, 0, s>>>(a, L);
+                }
+                PhaseTimer tg(ctx, IB_PHASE_MDF_GATHER, s);
                 k_gather_level<T, KER><<<ctx->sm_count * 6, 256, gsm, s>>>(a, L);
             }
     }
