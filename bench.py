@@ -49,6 +49,22 @@ PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM = 6800.0
 
 
+def max_over_ranks(t, device=None):
+    """Largest per-rank time: the job's time when every rank runs a replica."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(t)
+    tt = torch.tensor([float(t)], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def job_value(markers_per_rank, Ns, world, t_job):
+    """Whole-job marker updates per second over all replicas."""
+    return world * markers_per_rank * Ns / t_job
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -394,11 +410,7 @@ def run_gpu(args):
             clk.start()
         ms, graphed = time_steps(r, args.steps, args.warmup, flush, not args.no_graph)
         clocks = clk.stop() if clk else None
-        t_rank = sum(ms) / 1000.0
-        if world > 1:
-            tt = torch.tensor([t_rank], device=device, dtype=torch.float64)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            t_rank = float(tt.item())
+        t_rank = max_over_ranks(sum(ms) / 1000.0, device)
         kt = kernel_timing(r, max(3, min(args.steps, 10)), flush)
         e2e = e2e_steps(r, max(2, min(args.steps, 5))) if not args.no_e2e else None
         results[prec] = dict(ms=ms, t=t_rank, graphed=graphed, clocks=clocks, kt=kt, e2e=e2e,
@@ -420,7 +432,7 @@ def run_gpu(args):
         ms_g, n_g = res["kt"].get("mdf_gather", (float("nan"), 1))
         alg_g = sum(6 * s * bl + 3 * s * ml for bl, ml in lb) / max(1, nlev)
         step_s = res["t"] / args.steps
-        out[prec] = dict(step_s=step_s, value=world * M * Ns / step_s,
+        out[prec] = dict(step_s=step_s, value=job_value(M, Ns, world, step_s),
                          alg_mdf=alg_mdf, mdf_dur=dur, alg_g=alg_g, g_dur=ms_g / n_g / 1000.0,
                          phases={k: round(v[0] / v[1] * 1000.0, 2) for k, v in res["kt"].items()},
                          e2e=res["e2e"], graphed=res["graphed"], clocks=res["clocks"])
