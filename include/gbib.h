@@ -189,6 +189,50 @@ GBIB_API int particle_volume_integrals(ib_ctx *ctx, const ib_grid *grid, const v
                               const ib_particles *parts, double *Iu,
                               double *Irxu, double *vol, void *stream);
 
+/* ---- batches of independent cases (continuous batching, serving) -------
+ * A batch runs many independent periodic cases -- each with its own grid
+ * size, field and particles -- through the same kernel launches.  The
+ * particles of all cases sit in one flat ib_particles (marker_offset global
+ * over the flat marker arrays); case c owns particles p_begin .. p_end-1 and
+ * their markers.  Cases must partition [0, P) in order: cases[0].p_begin = 0,
+ * cases[c+1].p_begin = cases[c].p_end, cases[n-1].p_end = P (a case may have
+ * no particles).  Every case's grid must have the same prec.  Particles of
+ * different cases never interact.  Each batch entry point computes, for every
+ * case, exactly what the single-case entry point of the same name computes
+ * (bitwise: the same kernels and summation orders).
+ * The case table is copied to the workspace from pageable host memory on
+ * `stream`, so batch calls cannot be captured into a CUDA graph (single-case
+ * calls can).  Errors as for the single-case entry points, plus
+ * IB_ERR_INVALID for ranges that do not partition [0, P) or mixed precisions
+ * (the message names the case).                                            */
+typedef struct {
+    ib_grid grid;   /* the case's grid                                      */
+    void *u;        /* the case's field [3][n2][n1][n0] (in/out where written) */
+    void *f_out;    /* nullable: the case's accumulated Eulerian force        */
+    int p_begin;    /* first particle of the case                           */
+    int p_end;      /* one past its last particle                           */
+} ib_case;
+
+/* Algorithm 1 over every case (see ib_multidirect_forcing). */
+GBIB_API int ib_batch_multidirect_forcing(ib_ctx *ctx, int ncases, const ib_case *cases,
+                                          const ib_particles *parts,
+                                          const ib_markers *marks, int Ns, double dt,
+                                          int delta, int order, double *F_out,
+                                          void *stream);
+/* PVF volume integrals of every particle in its case's field. */
+GBIB_API int ib_batch_volume_integrals(ib_ctx *ctx, int ncases, const ib_case *cases,
+                                       const ib_particles *parts, double *Iu,
+                                       double *Irxu, double *vol, void *stream);
+/* Collision (pairs within a case, the case's periodic box) + Newton-Euler. */
+GBIB_API int ib_batch_collide_update(ib_ctx *ctx, int ncases, const ib_case *cases,
+                                     ib_particles *parts, const ib_phys *phys,
+                                     double dt, const double *F_ib,
+                                     const double *T_ib, const double *Iu_new,
+                                     const double *Iu_old, const double *Irxu_new,
+                                     const double *Irxu_old, double *Fc_out,
+                                     void *stream);
+/* (particle_force_torque works on any flat particle set, batched or not.) */
+
 /* ---- allocation-free volume integrals ----------------------------------
  * The paper has no counterpart to this entry point; it exists for callers
  * that cannot allocate device memory: code that runs while a CUDA stream is

@@ -7,8 +7,10 @@ is missing.
 
 Entry points mirror the C ABI names:
   ib_interpolate, ib_spread, ib_multidirect_forcing,
-  particle_volume_integrals, particle_force_torque, particle_collide_update
-as methods of :class:`Context`.
+  particle_volume_integrals, particle_force_torque, particle_collide_update,
+  ib_batch_multidirect_forcing, ib_batch_volume_integrals, ib_batch_collide_update
+as methods of :class:`Context`.  :func:`pack_batch` lays several cases'
+particles and markers out as one flat set for the batch entry points.
 """
 from __future__ import annotations
 
@@ -43,7 +45,8 @@ EXPORTS = ["ib_ctx_create", "ib_ctx_reserve", "ib_ctx_destroy", "ib_ctx_status",
            "ib_ctx_set_timing", "ib_ctx_read_timing",
            "ib_interpolate", "ib_spread", "ib_multidirect_forcing",
            "particle_volume_integrals", "particle_force_torque",
-           "particle_collide_update", "particle_volume_integrals_static"]
+           "particle_collide_update", "particle_volume_integrals_static",
+           "ib_batch_multidirect_forcing", "ib_batch_volume_integrals", "ib_batch_collide_update"]
 
 
 class IBError(RuntimeError):
@@ -65,6 +68,11 @@ class Particles(ctypes.Structure):
 
 class Markers(ctypes.Structure):
     _fields_ = [("M", ctypes.c_int), ("R", ctypes.c_void_p), ("dV", ctypes.c_void_p)]
+
+
+class Case(ctypes.Structure):
+    _fields_ = [("grid", Grid), ("u", ctypes.c_void_p), ("f_out", ctypes.c_void_p),
+                ("p_begin", ctypes.c_int), ("p_end", ctypes.c_int)]
 
 
 class Phys(ctypes.Structure):
@@ -102,6 +110,9 @@ def load(path: str = LIB_PATH):
         "particle_volume_integrals_static": (i, [p, p, p, p, p, p, p]),
         "particle_force_torque": (i, [p, p, p, p, d, p, p, p]),
         "particle_collide_update": (i, [p, p, p, p, d, p, p, p, p, p, p, p, p]),
+        "ib_batch_multidirect_forcing": (i, [p, i, p, p, p, i, d, i, i, p, p]),
+        "ib_batch_volume_integrals": (i, [p, i, p, p, p, p, p, p]),
+        "ib_batch_collide_update": (i, [p, i, p, p, p, d, p, p, p, p, p, p, p, p]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -338,16 +349,135 @@ class Context:
             _need(t, nm, torch.float64, (P, 3))
         if Fc_out is not None:
             _need(Fc_out, "Fc_out", torch.float64, (P, 3))
-        ph = Phys()
-        ph.rho_f = float(phys[0])
-        for a in range(3):
-            ph.g[a] = float(phys[1 + a])
-        ph.g_coll, ph.eps_c, ph.d_c = float(phys[4]), float(phys[5]), float(phys[6])
+        ph = _phys_struct(phys)
         g = make_grid(n, h, origin, IB_F64)
         self._call(self.lib.particle_collide_update, self.handle, ctypes.byref(ps), ctypes.byref(g),
                    ctypes.byref(ph), float(dt), _ptr(F_ib), _ptr(T_ib), _ptr(Iu_new), _ptr(Iu_old),
                    _ptr(Irxu_new), _ptr(Irxu_old), _ptr(Fc_out), _stream(stream))
         return Fc_out
+
+    def ib_batch_multidirect_forcing(self, fields, hs, parts, marks, ranges, Ns, dt, origins=None,
+                                     delta=ROMA3, order=SEQUENTIAL, F_out=None, f_outs=None,
+                                     stream=None):
+        """Algorithm 1 on every case of a batch, in place on ``fields``.
+
+        ``parts``/``marks`` are the flat particle and marker sets of the
+        batch (see :func:`pack_batch`); ``ranges[c]`` = (p_begin, p_end).
+        Returns F_out[M,3] over the flat markers.
+        """
+        cases = case_array(fields, hs, ranges, origins, f_outs)
+        ps = self.particles_struct(parts["Xr"], parts["Ur"], parts["Wr"], parts["radius"],
+                                   parts["rho_p"], parts["moff"])
+        ms = self.markers_struct(marks["R"], marks["dV"])
+        if F_out is None:
+            F_out = torch.empty((ms.M, 3), dtype=torch.float64, device=parts["Xr"].device)
+        _need(F_out, "F_out", torch.float64, (ms.M, 3))
+        self._call(self.lib.ib_batch_multidirect_forcing, self.handle, len(cases), cases,
+                   ctypes.byref(ps), ctypes.byref(ms), int(Ns), float(dt), int(delta), int(order),
+                   _ptr(F_out), _stream(stream))
+        return F_out
+
+    def ib_batch_volume_integrals(self, fields, hs, parts, ranges, origins=None, out=None,
+                                  stream=None):
+        """(Iu, Irxu, vol) of every particle of a batch in its case's field."""
+        cases = case_array(fields, hs, ranges, origins)
+        ps = self.particles_struct(parts["Xr"], parts["Ur"], parts["Wr"], parts["radius"],
+                                   parts["rho_p"], parts["moff"])
+        P = ps.P
+        dev = parts["Xr"].device
+        if out is None:
+            out = (torch.empty((P, 3), dtype=torch.float64, device=dev),
+                   torch.empty((P, 3), dtype=torch.float64, device=dev),
+                   torch.empty((P,), dtype=torch.float64, device=dev))
+        Iu, Irxu, vol = out
+        _need(Iu, "Iu", torch.float64, (P, 3))
+        _need(Irxu, "Irxu", torch.float64, (P, 3))
+        _need(vol, "vol", torch.float64, (P,))
+        self._call(self.lib.ib_batch_volume_integrals, self.handle, len(cases), cases, ctypes.byref(ps),
+                   _ptr(Iu), _ptr(Irxu), _ptr(vol), _stream(stream))
+        return Iu, Irxu, vol
+
+    def ib_batch_collide_update(self, parts, shapes, hs, ranges, phys, dt, F_ib, T_ib, Iu_new,
+                                Iu_old, Irxu_new, Irxu_old, Fc_out=None, origins=None, stream=None):
+        """Collision within each case + Newton-Euler, in place on the flat set.
+
+        ``shapes[c]`` = (n0, n1, n2) of case c's periodic box.
+        """
+        cases = case_array(None, hs, ranges, origins, shapes=shapes)
+        ps = self.particles_struct(parts["Xr"], parts["Ur"], parts["Wr"], parts["radius"],
+                                   parts["rho_p"], parts["moff"])
+        P = ps.P
+        for t, nm in ((F_ib, "F_ib"), (T_ib, "T_ib"), (Iu_new, "Iu_new"), (Iu_old, "Iu_old"),
+                      (Irxu_new, "Irxu_new"), (Irxu_old, "Irxu_old")):
+            _need(t, nm, torch.float64, (P, 3))
+        if Fc_out is not None:
+            _need(Fc_out, "Fc_out", torch.float64, (P, 3))
+        ph = _phys_struct(phys)
+        self._call(self.lib.ib_batch_collide_update, self.handle, len(cases), cases, ctypes.byref(ps),
+                   ctypes.byref(ph), float(dt), _ptr(F_ib), _ptr(T_ib), _ptr(Iu_new), _ptr(Iu_old),
+                   _ptr(Irxu_new), _ptr(Irxu_old), _ptr(Fc_out), _stream(stream))
+        return Fc_out
+
+
+def _phys_struct(phys):
+    ph = Phys()
+    ph.rho_f = float(phys[0])
+    for a in range(3):
+        ph.g[a] = float(phys[1 + a])
+    ph.g_coll, ph.eps_c, ph.d_c = float(phys[4]), float(phys[5]), float(phys[6])
+    return ph
+
+
+def case_array(fields, hs, ranges, origins=None, f_outs=None, shapes=None):
+    """ctypes ``ib_case[]`` of a batch.
+
+    ``fields[c]`` is case c's field [3, n2, n1, n0] (or None with ``shapes[c]``
+    = (n0, n1, n2) where no field is read), ``hs[c]`` its spacing and
+    ``ranges[c]`` = (p_begin, p_end) its particles in the flat set.
+    """
+    nc = len(ranges)
+    arr = (Case * nc)()
+    for c in range(nc):
+        u = fields[c] if fields is not None else None
+        if u is not None:
+            n = (u.shape[3], u.shape[2], u.shape[1])
+            _need(u, "fields[%d]" % c, u.dtype, (3, n[2], n[1], n[0]))
+            prec = IB_F64 if u.dtype == torch.float64 else IB_F32
+        else:
+            n, prec = shapes[c], IB_F64
+        f = f_outs[c] if f_outs is not None else None
+        if f is not None:
+            _need(f, "f_outs[%d]" % c, u.dtype, tuple(u.shape))
+        arr[c].grid = make_grid(n, hs[c], origins[c] if origins is not None else (0.0, 0.0, 0.0), prec)
+        arr[c].u = u.data_ptr() if u is not None else None
+        arr[c].f_out = f.data_ptr() if f is not None else None
+        arr[c].p_begin, arr[c].p_end = int(ranges[c][0]), int(ranges[c][1])
+    return arr
+
+
+def pack_batch(parts_list, marks_list):
+    """Concatenate per-case particle/marker dicts into one flat set.
+
+    Returns (parts, marks, ranges, mranges): marker offsets are shifted to
+    index the flat marker arrays; ``ranges[c]`` / ``mranges[c]`` are case c's
+    particle and marker index ranges.
+    """
+    keys = ("Xr", "Ur", "Wr", "radius", "rho_p")
+    parts = {k: torch.cat([p[k] for p in parts_list]).contiguous() for k in keys}
+    offs, ranges, mranges = [], [], []
+    pb = mb = 0
+    for p, m in zip(parts_list, marks_list):
+        P, M = p["Xr"].shape[0], m["R"].shape[0]
+        offs.append(p["moff"][:P] + mb)
+        ranges.append((pb, pb + P))
+        mranges.append((mb, mb + M))
+        pb += P
+        mb += M
+    dev = parts_list[0]["Xr"].device
+    offs.append(torch.tensor([mb], dtype=torch.int32, device=dev))
+    parts["moff"] = torch.cat(offs).to(torch.int32).contiguous()
+    marks = {k: torch.cat([m[k] for m in marks_list]).contiguous() for k in ("R", "dV")}
+    return parts, marks, ranges, mranges
 
 
 def device_case(case, prec=IB_F64, device="cuda"):

@@ -60,6 +60,66 @@ DevGrid make_dev_grid(const ib_grid *g) {
     return d;
 }
 
+DevCase make_dev_case(const ib_grid *g, void *u, void *f, int p0, int p1) {
+    DevCase c;
+    c.g = make_dev_grid(g);
+    c.u = u;
+    c.f = f;
+    c.p0 = p0;
+    c.p1 = p1;
+    for (int a = 0; a < 3; ++a) c.tiles[a] = (g->n[a] + kTile - 1) / kTile;
+    c.tile_off = 0;
+    return c;
+}
+
+CaseTab single_case(const ib_grid *g, void *u, void *f, int P) {
+    CaseTab ct;
+    ct.arr = nullptr;
+    ct.pcase = nullptr;
+    ct.ncases = 1;
+    ct.one = make_dev_case(g, u, f, 0, P);
+    ct.ntiles = (long long)ct.one.tiles[0] * ct.one.tiles[1] * ct.one.tiles[2];
+    return ct;
+}
+
+__global__ void k_case_of_particle(const DevCase *cases, int ncases, int *pcase) {
+    for (int c = blockIdx.x; c < ncases; c += gridDim.x)
+        for (int p = cases[c].p0 + threadIdx.x; p < cases[c].p1; p += blockDim.x) pcase[p] = c;
+}
+
+int build_case_table(ib_ctx *ctx, Arena &ar, int ncases, const ib_case *cases, int P, int need_prec,
+                     CaseTab &ct, cudaStream_t s) {
+    if (ncases < 1 || !cases) return set_error(IB_ERR_INVALID, "batch needs ncases >= 1 and a case array");
+    int prec = cases[0].grid.prec;
+    std::vector<DevCase> h(ncases);
+    unsigned long long toff = 0;
+    for (int c = 0; c < ncases; ++c) {
+        int rc = validate_grid(&cases[c].grid, need_prec);
+        if (rc) return set_error(rc, "case %d: %s", c, ib_last_error());
+        if (need_prec && cases[c].grid.prec != prec) return set_error(IB_ERR_INVALID, "case %d: mixed precisions", c);
+        const int expect = c == 0 ? 0 : cases[c - 1].p_end;
+        if (cases[c].p_begin != expect || cases[c].p_end < cases[c].p_begin)
+            return set_error(IB_ERR_INVALID, "case %d: particle ranges must partition [0, P) in order", c);
+        h[c] = make_dev_case(&cases[c].grid, cases[c].u, cases[c].f_out, cases[c].p_begin, cases[c].p_end);
+        h[c].tile_off = (unsigned int)toff;
+        toff += (unsigned long long)h[c].tiles[0] * h[c].tiles[1] * h[c].tiles[2];
+        if (toff > (1ull << 30)) return set_error(IB_ERR_UNSUPPORTED, "batch has too many grid tiles");
+    }
+    if (cases[ncases - 1].p_end != P) return set_error(IB_ERR_INVALID, "case ranges must end at P = %d", P);
+    DevCase *d = ar.take<DevCase>(ncases);
+    int *pcase = ar.take<int>(P > 0 ? P : 1);
+    if (!ar.ok()) return oom_error(ar.used, ar.cap);
+    if (cudaMemcpyAsync(d, h.data(), sizeof(DevCase) * ncases, cudaMemcpyHostToDevice, s) != cudaSuccess)
+        return set_error(IB_ERR_CUDA, "case table upload: %s", cudaGetErrorString(cudaGetLastError()));
+    k_case_of_particle<<<ncases < 1024 ? ncases : 1024, 128, 0, s>>>(d, ncases, pcase);
+    ct.arr = d;
+    ct.pcase = pcase;
+    ct.ncases = ncases;
+    ct.ntiles = (long long)toff;
+    ct.one = h[0];
+    return check_launch("case table");
+}
+
 // ---- exclusive scan ------------------------------------------------------
 // Three stages: per-block totals, a scan of the totals in one block, then a
 // per-block scan that adds the block's offset.  1024 elements per block.

@@ -27,6 +27,30 @@ struct DevGrid {
     double org[3];
 };
 
+// One case of a batch on the device: its grid, its fields and its particle
+// range in the batch's flat particle arrays.
+struct DevCase {
+    DevGrid g;
+    void *u;                // field of the case
+    void *f;                // accumulated force field of the case (nullable)
+    int p0, p1;             // particles [p0, p1)
+    int tiles[3];           // 8^3 grid tiles per axis (global-tile binning)
+    unsigned int tile_off;  // first global-tile slot of the case
+};
+
+// Case table of a call: a device array of cases, or one case passed by value
+// (single-case entry points, which stay capturable into CUDA graphs).
+struct CaseTab {
+    const DevCase *arr;  // nullptr: every particle belongs to `one`
+    const int *pcase;    // [P] case of each particle (with arr)
+    int ncases;
+    long long ntiles;    // global 8^3 tiles over all cases
+    DevCase one;
+    __device__ __forceinline__ int case_of(int p) const { return arr ? pcase[p] : 0; }
+    __device__ __forceinline__ const DevCase &get(int c) const { return arr ? arr[c] : one; }
+    __device__ __forceinline__ const DevCase &of_particle(int p) const { return arr ? arr[pcase[p]] : one; }
+};
+
 // Device-side error latch: first code wins.
 struct DevStatus {
     int code;
@@ -150,6 +174,14 @@ int oom_error(size_t need, size_t have);
 int check_launch(const char *what);
 int validate_grid(const ib_grid *g, int need_prec);
 DevGrid make_dev_grid(const ib_grid *g);
+DevCase make_dev_case(const ib_grid *g, void *u, void *f, int p0, int p1);
+// Case table of one case passed by value (no device memory, capturable).
+CaseTab single_case(const ib_grid *g, void *u, void *f, int P);
+// Case table in the workspace for `ncases` host cases, uploaded on stream `s`
+// (a pageable copy: not capturable into a CUDA graph).  Returns an error status
+// when the cases are invalid or the workspace is short.
+int build_case_table(ib_ctx *ctx, struct Arena &ar, int ncases, const ib_case *cases, int P, int need_prec,
+                     CaseTab &ct, cudaStream_t s);
 
 // Records a CUDA event pair around a scope when the context times phases.
 struct PhaseTimer {

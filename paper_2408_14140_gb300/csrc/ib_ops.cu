@@ -58,7 +58,8 @@ struct Slots {
     uint32_t *cand;    // [total candidates] marker ids, sorted per slot
     uint16_t *bins;    // [ncompact_max][kBins] bin starts, relative (see kBins)
     int4 *geo_lo;      // [ncompact_max] tile first cell (wrapped), w = level
-    int4 *geo_dim;     // [ncompact_max] tile dims, w = candidate count
+    int4 *geo_dim;     // [ncompact_max] tile dims, w = first candidate
+    int *geo_case;     // [ncompact_max] case of the tile
 };
 
 // ---------------------------------------------------------------------------
@@ -189,7 +190,7 @@ __global__ void k_prep_spread(DevGrid g, int M, const double *__restrict__ X,
 // weights; the particle's marker radius and its unwrapped stencil box.
 template <typename T, int KER>
 __global__ void __launch_bounds__(kBlock) k_prep_particles(
-    DevGrid g, int P, const double *__restrict__ Xr, const double *__restrict__ Ur,
+    CaseTab ct, int P, const double *__restrict__ Xr, const double *__restrict__ Ur,
     const double *__restrict__ Wr, const int *__restrict__ moff, const double *__restrict__ R,
     const double *__restrict__ dV, MarkerState<T> ms, double *__restrict__ F,
     double *__restrict__ rho, int4 *__restrict__ box_lo, int4 *__restrict__ box_dim,
@@ -199,6 +200,7 @@ __global__ void __launch_bounds__(kBlock) k_prep_particles(
     __shared__ double s_rho;
     int p = blockIdx.x;
     if (p >= P) return;
+    const DevGrid g = ct.of_particle(p).g;
     if (threadIdx.x < 3) {
         s_lo[threadIdx.x] = LLONG_MAX;
         s_hi[threadIdx.x] = LLONG_MIN;
@@ -288,17 +290,19 @@ constexpr int kMaxNbr = 48;
 // The test runs in FP32 against a limit widened by h/16, far above FP32
 // rounding of unit-scale positions, so no true conflict is ever missed (an
 // extra conflict only serialises two particles).
-__global__ void k_conflicts(DevGrid g, int P, int KW, const double *__restrict__ Xr,
+__global__ void k_conflicts(CaseTab ct, int P, int KW, const double *__restrict__ Xr,
                             const double *__restrict__ rho, int *__restrict__ nbr_cnt,
                             int *__restrict__ nbr) {
-    const float L[3] = {(float)(g.n[0] * g.h), (float)(g.n[1] * g.h), (float)(g.n[2] * g.h)};
-    const float iL[3] = {1.0f / L[0], 1.0f / L[1], 1.0f / L[2]};
-    const float halo = (float)(1.7320508075688772 * KW * g.h + 0.0625 * g.h);
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x) {
+        const DevCase &cd = ct.of_particle(p);
+        const DevGrid &g = cd.g;
+        const float L[3] = {(float)(g.n[0] * g.h), (float)(g.n[1] * g.h), (float)(g.n[2] * g.h)};
+        const float iL[3] = {1.0f / L[0], 1.0f / L[1], 1.0f / L[2]};
+        const float halo = (float)(1.7320508075688772 * KW * g.h + 0.0625 * g.h);
         const float xp[3] = {(float)Xr[3 * p], (float)Xr[3 * p + 1], (float)Xr[3 * p + 2]};
         const float rp = (float)rho[p] + halo;
         int cnt = 0;
-        for (int q = 0; q < p; ++q) {
+        for (int q = cd.p0; q < p; ++q) {  // particles of other cases never conflict
             float d2 = 0.0f;
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
@@ -323,7 +327,7 @@ __global__ void k_conflicts(DevGrid g, int P, int KW, const double *__restrict__
 constexpr int kLevSmemP = 1024;
 constexpr size_t kLevSmem = (size_t)kLevSmemP * (4 + 2 + 2 * kMaxNbr);
 
-__global__ void __launch_bounds__(1024) k_levels(DevGrid g, int P, int order, int KW,
+__global__ void __launch_bounds__(1024) k_levels(CaseTab ct, int P, int order, int KW,
                                                  const double *__restrict__ Xr,
                                                  const double *__restrict__ rho,
                                                  const int *__restrict__ moff,
@@ -346,9 +350,6 @@ __global__ void __launch_bounds__(1024) k_levels(DevGrid g, int P, int order, in
     if (threadIdx.x != 0) return;
     int *lev = onchip ? s_lev : lo.level;
     int nl = 0;
-    const double L[3] = {g.n[0] * g.h, g.n[1] * g.h, g.n[2] * g.h};
-    const double iL[3] = {1.0 / L[0], 1.0 / L[1], 1.0 / L[2]};
-    const double halo = 1.7320508075688772 * KW * g.h;
     for (int p = 0; p < P; ++p) {
         int best = 0;
         if (order == IB_ORDER_SEQUENTIAL) {
@@ -357,7 +358,12 @@ __global__ void __launch_bounds__(1024) k_levels(DevGrid g, int P, int order, in
                 for (int k = 0; k < c; ++k)
                     best = max(best, lev[onchip ? s_nbr[p * kMaxNbr + k] : nbr[(size_t)p * kMaxNbr + k]] + 1);
             } else {
-                for (int q = 0; q < p; ++q) {
+                const DevCase &cd = ct.of_particle(p);
+                const DevGrid &g = cd.g;
+                const double L[3] = {g.n[0] * g.h, g.n[1] * g.h, g.n[2] * g.h};
+                const double iL[3] = {1.0 / L[0], 1.0 / L[1], 1.0 / L[2]};
+                const double halo = 1.7320508075688772 * KW * g.h;
+                for (int q = cd.p0; q < p; ++q) {
                     float d2 = 0.0f;
                     for (int a = 0; a < 3; ++a) {
                         float d = (float)Xr[3 * q + a] - (float)Xr[3 * p + a];
@@ -430,9 +436,8 @@ __device__ __forceinline__ int axis_tiles_local(long long first_rel, int t[3]) {
 }
 
 struct SlotGeom {
-    int mode;              // 0 global tiles, 1 particle-local tiles
-    int tiles[3];          // global tiles per axis
-    const int *part_of;    // [M]
+    int mode;              // 0 global tiles (per case), 1 particle-local tiles
+    const int *part_of;    // [M], nullptr: every marker in case 0
     const int *rank;       // [P]
     const int4 *box_lo;    // [P]
     const int4 *box_dim;   // [P]
@@ -440,10 +445,12 @@ struct SlotGeom {
 
 // Enumerate the dense slots of marker l and call f(slot).
 template <int KW, typename Fn>
-__device__ __forceinline__ void for_marker_slots(const DevGrid &g, const SlotGeom &sg, int l,
+__device__ __forceinline__ void for_marker_slots(const CaseTab &ct, const SlotGeom &sg, int l,
                                                  uint64_t anc, Fn f) {
     int tx[3], ty[3], tz[3], nx, ny, nz;
     uint32_t base = 0;
+    const DevCase &cd = ct.get(sg.part_of ? ct.case_of(sg.part_of[l]) : 0);
+    const DevGrid &g = cd.g;
     if (sg.mode == 0) {
         nx = axis_tiles_global<KW>(anchor_x(anc), g.n[0], tx);
         ny = axis_tiles_global<KW>(anchor_y(anc), g.n[1], ty);
@@ -468,7 +475,7 @@ __device__ __forceinline__ void for_marker_slots(const DevGrid &g, const SlotGeo
             for (int i = 0; i < nx; ++i) {
                 uint32_t s;
                 if (sg.mode == 0)
-                    s = ((uint32_t)tz[k] * sg.tiles[1] + ty[j]) * sg.tiles[0] + tx[i];
+                    s = cd.tile_off + ((uint32_t)tz[k] * cd.tiles[1] + ty[j]) * cd.tiles[0] + tx[i];
                 else
                     s = base + ((uint32_t)tz[k] * kLocalTiles + ty[j]) * kLocalTiles + tx[i];
                 f(s);
@@ -476,18 +483,18 @@ __device__ __forceinline__ void for_marker_slots(const DevGrid &g, const SlotGeo
 }
 
 template <int KW>
-__global__ void k_slot_count(DevGrid g, int M, SlotGeom sg, const uint64_t *__restrict__ anchor,
+__global__ void k_slot_count(CaseTab ct, int M, SlotGeom sg, const uint64_t *__restrict__ anchor,
                              uint32_t *__restrict__ count) {
     for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < M; l += gridDim.x * blockDim.x)
-        for_marker_slots<KW>(g, sg, l, anchor[l], [&](uint32_t s) { atomicAdd(count + s, 1u); });
+        for_marker_slots<KW>(ct, sg, l, anchor[l], [&](uint32_t s) { atomicAdd(count + s, 1u); });
 }
 
 template <int KW>
-__global__ void k_slot_fill(DevGrid g, int M, SlotGeom sg, const uint64_t *__restrict__ anchor,
+__global__ void k_slot_fill(CaseTab ct, int M, SlotGeom sg, const uint64_t *__restrict__ anchor,
                             const uint32_t *__restrict__ start, uint32_t *__restrict__ cursor,
                             uint32_t *__restrict__ cand) {
     for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < M; l += gridDim.x * blockDim.x)
-        for_marker_slots<KW>(g, sg, l, anchor[l], [&](uint32_t s) {
+        for_marker_slots<KW>(ct, sg, l, anchor[l], [&](uint32_t s) {
             uint32_t pos = start[s] + atomicAdd(cursor + s, 1u);
             cand[pos] = (uint32_t)l;
         });
@@ -577,19 +584,37 @@ __global__ void __launch_bounds__(kBlock) k_marker_order(int P, const int *__res
 // ---------------------------------------------------------------------------
 constexpr int kWarpSort = 256;
 
-__device__ __forceinline__ void slot_geometry(const DevGrid &g, int mode, const SlotGeom &sg, const Slots &sl,
-                                              const int *level, uint32_t d, uint32_t b, int lo[3], int dim[3],
-                                              int &lev) {
+// Case of dense global-tile slot d: the last case whose tile_off <= d.
+__device__ __forceinline__ int case_of_tile(const CaseTab &ct, uint32_t d) {
+    if (!ct.arr) return 0;
+    int a = 0, b = ct.ncases - 1;
+    while (a < b) {
+        const int mid = (a + b + 1) >> 1;
+        if (ct.arr[mid].tile_off <= d) a = mid;
+        else b = mid - 1;
+    }
+    return a;
+}
+
+__device__ __forceinline__ int slot_geometry(const CaseTab &ct, int mode, const SlotGeom &sg, const Slots &sl,
+                                             const int *level, uint32_t d, uint32_t b, int lo[3], int dim[3],
+                                             int &lev) {
     lev = 0;
     if (mode == 0) {
-        const int t[3] = {(int)(d % sg.tiles[0]), (int)((d / sg.tiles[0]) % sg.tiles[1]),
-                          (int)(d / ((uint32_t)sg.tiles[0] * sg.tiles[1]))};
+        const int c = case_of_tile(ct, d);
+        const DevCase &cd = ct.get(c);
+        const DevGrid &g = cd.g;
+        d -= cd.tile_off;
+        const int t[3] = {(int)(d % cd.tiles[0]), (int)((d / cd.tiles[0]) % cd.tiles[1]),
+                          (int)(d / ((uint32_t)cd.tiles[0] * cd.tiles[1]))};
         for (int a = 0; a < 3; ++a) {
             lo[a] = t[a] * kTile;
             dim[a] = min(kTile, g.n[a] - lo[a]);
         }
+        return c;
     } else {
         const int p = sg.part_of[sl.cand[b]];  // every candidate of a local tile has the same particle
+        const DevGrid &g = ct.of_particle(p).g;
         const int lt = (int)(d % kLocalSlots);
         const int t[3] = {lt % kLocalTiles, (lt / kLocalTiles) % kLocalTiles, lt / (kLocalTiles * kLocalTiles)};
         const int4 blo = sg.box_lo[p], bd = sg.box_dim[p];
@@ -599,6 +624,7 @@ __device__ __forceinline__ void slot_geometry(const DevGrid &g, int mode, const 
             dim[a] = min(kTile, bdm[a] - t[a] * kTile);
         }
         lev = level[p];
+        return ct.case_of(p);
     }
 }
 
@@ -633,7 +659,7 @@ __device__ __forceinline__ void slot_emit(const DevGrid &g, const uint64_t *anch
 }
 
 __global__ void __launch_bounds__(kBlock) k_slot_sort(
-    DevGrid g, int mode, int ncompact_cap, const int *__restrict__ ncompact_p, SlotGeom sg,
+    CaseTab ct, int mode, int ncompact_cap, const int *__restrict__ ncompact_p, SlotGeom sg,
     const uint32_t *__restrict__ dense_of, const uint32_t *__restrict__ start,
     const uint64_t *__restrict__ anchor, const int *__restrict__ level, Slots sl, DevStatus *st) {
     __shared__ unsigned long long keys[kMaxCand];  // also kBlock/32 warp regions of kWarpSort
@@ -647,7 +673,8 @@ __global__ void __launch_bounds__(kBlock) k_slot_sort(
         const int nc = (int)(start[d + 1] - b);
         if (nc > kWarpSort) continue;
         int lo[3], dim[3], lev;
-        slot_geometry(g, mode, sg, sl, level, d, b, lo, dim, lev);
+        const int cse = slot_geometry(ct, mode, sg, sl, level, d, b, lo, dim, lev);
+        const DevGrid &g = ct.get(cse).g;
         int np2 = 1;
         while (np2 < nc) np2 <<= 1;
         for (int i = lane; i < np2; i += 32) wk[i] = i < nc ? slot_key(g, anchor, sl.cand[b + i], lo) : ~0ull;
@@ -670,6 +697,7 @@ __global__ void __launch_bounds__(kBlock) k_slot_sort(
         if (lane == 0) {
             sl.geo_lo[cs] = make_int4(lo[0], lo[1], lo[2], lev);
             sl.geo_dim[cs] = make_int4(dim[0], dim[1], dim[2], (int)b);
+            sl.geo_case[cs] = cse;
         }
         __syncwarp();
     }
@@ -681,7 +709,8 @@ __global__ void __launch_bounds__(kBlock) k_slot_sort(
         const int nc = (int)(start[d + 1] - b);
         if (nc <= kWarpSort) continue;
         int lo[3], dim[3], lev;
-        slot_geometry(g, mode, sg, sl, level, d, b, lo, dim, lev);
+        const int cse = slot_geometry(ct, mode, sg, sl, level, d, b, lo, dim, lev);
+        const DevGrid &g = ct.get(cse).g;
         if (nc > kMaxCand) {
             // report, and leave an empty tile (no bins, no cells)
             uint16_t *bs = sl.bins + (size_t)cs * kBins;
@@ -690,6 +719,7 @@ __global__ void __launch_bounds__(kBlock) k_slot_sort(
                 raise_status(st, IB_ERR_UNSUPPORTED, nc);
                 sl.geo_lo[cs] = make_int4(lo[0], lo[1], lo[2], lev);
                 sl.geo_dim[cs] = make_int4(0, 0, 0, (int)b);
+                sl.geo_case[cs] = cse;
             }
             __syncthreads();
             continue;
@@ -717,6 +747,7 @@ __global__ void __launch_bounds__(kBlock) k_slot_sort(
         if (threadIdx.x == 0) {
             sl.geo_lo[cs] = make_int4(lo[0], lo[1], lo[2], lev);
             sl.geo_dim[cs] = make_int4(dim[0], dim[1], dim[2], (int)b);
+            sl.geo_case[cs] = cse;
         }
         __syncthreads();
     }
@@ -827,13 +858,17 @@ __device__ __forceinline__ bool gather_cell(int tx, int ty, int tz, const uint16
     return hit;
 }
 
-// One tile (compact slot cs) of a gather phase: dst += S A, and, when f_out
-// is given (forcing pass), f_out += S A / dt.
+// One tile (compact slot cs) of a gather phase into the tile's case: u += S A,
+// and, when the case has a force field (forcing pass), f += S A / dt.
 template <typename T, int KW, bool COH>
-__device__ __forceinline__ void gather_tile(const DevGrid &g, long long N, int cs, const Slots &sl,
-                                            const T *__restrict__ wts, const T *A,
-                                            T *__restrict__ dst, T *__restrict__ f_out, double inv_dt,
+__device__ __forceinline__ void gather_tile(const CaseTab &ct, int cs, const Slots &sl,
+                                            const T *__restrict__ wts, const T *A, double inv_dt,
                                             StageSmem<T> &sm) {
+    const DevCase &cd = ct.get(sl.geo_case[cs]);
+    const DevGrid g = cd.g;
+    const long long N = (long long)g.n[0] * g.n[1] * g.n[2];
+    T *__restrict__ dst = (T *)cd.u;
+    T *__restrict__ f_out = (T *)cd.f;
     const int4 lo = sl.geo_lo[cs], dim = sl.geo_dim[cs];
     const uint16_t *bs = sl.bins + (size_t)cs * kBins;
     for (int i = threadIdx.x; i < kBins; i += blockDim.x) sm.bins[i] = bs[i];
@@ -886,23 +921,22 @@ __device__ __forceinline__ void gather_tile(const DevGrid &g, long long N, int c
 // (wavefronts whose tiles do not fit the per-CTA staging), so that its code
 // stays out of the hot loop.
 template <typename T, int KW>
-__device__ __noinline__ void gather_tile_fallback(const DevGrid g, long long N, int cs, const Slots sl,
-                                                  const T *wts, const T *A, T *dst, T *f_out, double inv_dt,
-                                                  unsigned char *smem) {
+__device__ __noinline__ void gather_tile_fallback(const CaseTab ct, int cs, const Slots sl, const T *wts,
+                                                  const T *A, double inv_dt, unsigned char *smem) {
     StageSmem<T> sm(smem);
-    gather_tile<T, KW, true>(g, N, cs, sl, wts, A, dst, f_out, inv_dt, sm);
+    gather_tile<T, KW, true>(ct, cs, sl, wts, A, inv_dt, sm);
 }
 
+// Spreading: the case's u slot holds the field spread into, its f slot is null.
 template <typename T, int KER>
-__global__ void __launch_bounds__(kBlock) k_spread_gather(DevGrid g, const int *__restrict__ ncompact_p,
+__global__ void __launch_bounds__(kBlock) k_spread_gather(CaseTab ct, const int *__restrict__ ncompact_p,
                                                           Slots sl, const T *__restrict__ wts,
-                                                          const T *__restrict__ A, T *__restrict__ f) {
+                                                          const T *__restrict__ A) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     StageSmem<T> sm(smem_raw);
-    long long N = (long long)g.n[0] * g.n[1] * g.n[2];
     int nc = *ncompact_p;
     for (int cs = blockIdx.x; cs < nc; cs += gridDim.x)
-        gather_tile<T, Kernel<KER>::W, false>(g, N, cs, sl, wts, A, f, (T *)nullptr, 0.0, sm);
+        gather_tile<T, Kernel<KER>::W, false>(ct, cs, sl, wts, A, 0.0, sm);
 }
 
 // ---------------------------------------------------------------------------
@@ -959,9 +993,8 @@ __device__ __forceinline__ bool grid_sync(Barrier b, DevStatus *st) {
 // ---------------------------------------------------------------------------
 template <typename T>
 struct PassArgs {
-    DevGrid g;
-    T *u;
-    T *f_out;
+    CaseTab ct;        // cases: grid, u, accumulated force field (nullable)
+    const int *part_of;  // [M] particle of each marker
     double *F;
     const double *dV;
     MarkerState<T> ms;
@@ -986,14 +1019,15 @@ template <typename T, int KER>
 __global__ void __launch_bounds__(256) k_interp_level(PassArgs<T> a, int L) {
     constexpr int KW = Kernel<KER>::W;
     if (L >= *a.nlev) return;
-    const DevGrid g = a.g;
-    const long long N = (long long)g.n[0] * g.n[1] * g.n[2];
     const double inv_dt = 1.0 / a.dt;
     const int m0 = a.lev_mbeg[L], m1 = a.lev_mbeg[L + 1];
     for (int i = m0 + blockIdx.x * blockDim.x + threadIdx.x; i < m1; i += gridDim.x * blockDim.x) {
         const int l = a.mperm[i];
+        const DevCase &cd = a.ct.of_particle(a.part_of[l]);
+        const DevGrid g = cd.g;
+        const long long N = (long long)g.n[0] * g.n[1] * g.n[2];
         T U[3];
-        interp_marker<T, KW, false>(a.u, g, N, a.ms.anchor[l], a.ms.wts + 12 * (size_t)l, U);
+        interp_marker<T, KW, false>((const T *)cd.u, g, N, a.ms.anchor[l], a.ms.wts + 12 * (size_t)l, U);
         const double q = a.dV[l] * g.inv_h3;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
@@ -1021,12 +1055,15 @@ __global__ void __launch_bounds__(256) k_gather_level(PassArgs<T> a, int L) {
     T *sw = (T *)smem_raw;                          // [N][12]
     T *sA = sw + (size_t)TileStage<T>::N * 12;      // [N][4]
     uint16_t *sb = (uint16_t *)(sA + (size_t)TileStage<T>::N * 4);
-    const DevGrid g = a.g;
-    const long long N = (long long)g.n[0] * g.n[1] * g.n[2];
     const double inv_dt = 1.0 / a.dt;
     const int s0 = a.lev_sbeg[L], s1 = a.lev_sbeg[L + 1];
     const int tx = threadIdx.x & 7, ty = (threadIdx.x >> 3) & 7, tz0 = threadIdx.x >> 6;
     for (int cs = s0 + blockIdx.x; cs < s1; cs += gridDim.x) {
+        const DevCase &cd = a.ct.get(a.sl.geo_case[cs]);
+        const DevGrid g = cd.g;
+        const long long N = (long long)g.n[0] * g.n[1] * g.n[2];
+        T *const u = (T *)cd.u;
+        T *const f_out = (T *)cd.f;
         const int4 lo = a.sl.geo_lo[cs], dim = a.sl.geo_dim[cs];
         const uint16_t *bs = a.sl.bins + (size_t)cs * kBins;
         for (int i = threadIdx.x; i < kBins; i += blockDim.x) sb[i] = bs[i];
@@ -1059,10 +1096,10 @@ __global__ void __launch_bounds__(256) k_gather_level(PassArgs<T> a, int L) {
                     const long long c = ((long long)wrap_add(lo.z, tz, g.n[2]) * g.n[1] +
                                          wrap_add(lo.y, ty, g.n[1])) * g.n[0] + wrap_add(lo.x, tx, g.n[0]);
 #pragma unroll
-                    for (int q = 0; q < 3; ++q) a.u[q * N + c] += acc[q];
-                    if (a.f_out)
+                    for (int q = 0; q < 3; ++q) u[q * N + c] += acc[q];
+                    if (f_out)
 #pragma unroll
-                        for (int q = 0; q < 3; ++q) a.f_out[q * N + c] += (T)(acc[q] * inv_dt);
+                        for (int q = 0; q < 3; ++q) f_out[q * N + c] += (T)(acc[q] * inv_dt);
                 }
             }
         }
@@ -1075,8 +1112,6 @@ __global__ void __launch_bounds__(kBlock, 1) k_mdf_passes(PassArgs<T> a) {
     constexpr int KW = Kernel<KER>::W;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     StageSmem<T> sm(smem_raw);
-    const DevGrid g = a.g;
-    long long N = (long long)g.n[0] * g.n[1] * g.n[2];
     const int nl = *a.nlev;
     double inv_dt = 1.0 / a.dt;
     int gtid = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1085,6 +1120,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_mdf_passes(PassArgs<T> a) {
     __shared__ int s_nmine, s_total, s_staged;
     __shared__ int s_off[kMaxMyTiles + 1];
     __shared__ int4 s_lo[kMaxMyTiles], s_dim[kMaxMyTiles];
+    __shared__ int s_case[kMaxMyTiles];
     const int tx = threadIdx.x & 7, ty = (threadIdx.x >> 3) & 7, tz = threadIdx.x >> 6;
     for (int L = a.L0; L < nl; ++L) {
         int m0 = a.lev_mbeg[L], m1 = a.lev_mbeg[L + 1];
@@ -1098,6 +1134,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_mdf_passes(PassArgs<T> a) {
                 s_off[k] = tot;
                 s_lo[k] = a.sl.geo_lo[cs];
                 s_dim[k] = a.sl.geo_dim[cs];
+                s_case[k] = a.sl.geo_case[cs];
                 tot += a.sl.bins[(size_t)cs * kBins + kBins - 1];
             }
             s_off[ok ? nmine : 0] = tot;
@@ -1118,10 +1155,14 @@ __global__ void __launch_bounds__(kBlock, 1) k_mdf_passes(PassArgs<T> a) {
                     // the tile's u values (every cell of the tile; only band cells are written)
                     const int4 lo = s_lo[k], dim = s_dim[k];
                     if (tx < dim.x && ty < dim.y && tz < dim.z) {
+                        const DevCase &cd = a.ct.get(s_case[k]);
+                        const DevGrid &g = cd.g;
+                        const long long N = (long long)g.n[0] * g.n[1] * g.n[2];
                         const long long c = ((long long)wrap_add(lo.z, tz, g.n[2]) * g.n[1] +
                                              wrap_add(lo.y, ty, g.n[1])) * g.n[0] + wrap_add(lo.x, tx, g.n[0]);
 #pragma unroll
-                        for (int q = 0; q < 3; ++q) lv.u[(k * 3 + q) * kTileCells + threadIdx.x] = a.u[q * N + c];
+                        for (int q = 0; q < 3; ++q)
+                            lv.u[(k * 3 + q) * kTileCells + threadIdx.x] = ((const T *)cd.u)[q * N + c];
                     }
                 }
                 for (int i = threadIdx.x; i < nc; i += blockDim.x) {
@@ -1140,8 +1181,11 @@ __global__ void __launch_bounds__(kBlock, 1) k_mdf_passes(PassArgs<T> a) {
             // interpolation phase: U = J u, F += (U^d - U)/dt, A = (U^d - U) dV / h^3
             for (int i = m0 + gtid; i < m1; i += gsz) {
                 int l = a.mperm[i];
+                const DevCase &cd = a.ct.of_particle(a.part_of[l]);
+                const DevGrid &g = cd.g;
+                const long long N = (long long)g.n[0] * g.n[1] * g.n[2];
                 T U[3];
-                interp_marker<T, KW, true>(a.u, g, N, a.ms.anchor[l], a.ms.wts + 12 * (size_t)l, U);
+                interp_marker<T, KW, true>((const T *)cd.u, g, N, a.ms.anchor[l], a.ms.wts + 12 * (size_t)l, U);
                 double q = a.dV[l] * g.inv_h3;
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
@@ -1170,22 +1214,27 @@ __global__ void __launch_bounds__(kBlock, 1) k_mdf_passes(PassArgs<T> a) {
                         gather_cell<T, KW, true, true>(tx, ty, tz, lv.bins + k * kBins, nullptr,
                                                        lv.w + 12 * (size_t)off, lv.A + 4 * (size_t)off, acc)) {
                         const int4 lo = s_lo[k];
+                        const DevCase &cd = a.ct.get(s_case[k]);
+                        const DevGrid &g = cd.g;
+                        const long long N = (long long)g.n[0] * g.n[1] * g.n[2];
                         const long long c = ((long long)wrap_add(lo.z, tz, g.n[2]) * g.n[1] +
                                              wrap_add(lo.y, ty, g.n[1])) * g.n[0] + wrap_add(lo.x, tx, g.n[0]);
+                        T *const u = (T *)cd.u;
+                        T *const f_out = (T *)cd.f;
 #pragma unroll
                         for (int q = 0; q < 3; ++q) {
                             T *su = lv.u + (k * 3 + q) * kTileCells + threadIdx.x;
                             *su += acc[q];
-                            a.u[q * N + c] = *su;
+                            u[q * N + c] = *su;
                         }
-                        if (a.f_out)
+                        if (f_out)
 #pragma unroll
-                            for (int q = 0; q < 3; ++q) a.f_out[q * N + c] += (T)(acc[q] * inv_dt);
+                            for (int q = 0; q < 3; ++q) f_out[q * N + c] += (T)(acc[q] * inv_dt);
                     }
                 }
             } else {
                 for (int cs = s0 + blockIdx.x; cs < s1; cs += gridDim.x)
-                    gather_tile_fallback<T, KW>(g, N, cs, a.sl, a.ms.wts, a.ms.A, a.u, a.f_out, inv_dt, smem_raw);
+                    gather_tile_fallback<T, KW>(a.ct, cs, a.sl, a.ms.wts, a.ms.A, inv_dt, smem_raw);
             }
             if (!grid_sync(a.bar, a.st)) return;
         }
@@ -1219,7 +1268,7 @@ static bool take_markers(Arena &ar, int M, MarkerState<T> &ms) {
 
 // Build sorted slot lists for `M` prepared markers.  ndense dense slots.
 template <int KW>
-static int build_slots(ib_ctx *ctx, Arena &ar, const DevGrid &g, int M, int ndense, SlotGeom sg,
+static int build_slots(ib_ctx *ctx, Arena &ar, const CaseTab &ct, int M, int ndense, SlotGeom sg,
                        const uint64_t *anchor, const int *level, Slots &sl, int *&ncompact_dev,
                        cudaStream_t s) {
     size_t cand_cap = (size_t)M * (sg.mode == 0 ? 27 : 8) + 1;
@@ -1238,20 +1287,21 @@ static int build_slots(ib_ctx *ctx, Arena &ar, const DevGrid &g, int M, int nden
     sl.bins = ar.take<uint16_t>((size_t)ncompact_cap * kBins);
     sl.geo_lo = ar.take<int4>(ncompact_cap);
     sl.geo_dim = ar.take<int4>(ncompact_cap);
+    sl.geo_case = ar.take<int>(ncompact_cap);
     if (!ar.ok())
         return oom_error(ar.used, ar.cap);
     cudaMemsetAsync(sl.count, 0, sizeof(uint32_t) * ndense, s);
     cudaMemsetAsync(sl.cursor, 0, sizeof(uint32_t) * ndense, s);
     int nb = grid_blocks(M, 256, ctx->sm_count);
-    k_slot_count<KW><<<nb, 256, 0, s>>>(g, M, sg, anchor, sl.count);
+    k_slot_count<KW><<<nb, 256, 0, s>>>(ct, M, sg, anchor, sl.count);
     exclusive_scan(sl.count, sl.start, ndense, scratch, s);
     int nbd = grid_blocks(ndense, 256, ctx->sm_count);
     k_flags<<<nbd, 256, 0, s>>>(sl.count, flags, ndense);
     exclusive_scan(flags, sl.flag_scan, ndense, scratch, s);
     k_compact<<<nbd, 256, 0, s>>>(sl.count, sl.flag_scan, sl.dense_of, ndense);
-    k_slot_fill<KW><<<nb, 256, 0, s>>>(g, M, sg, anchor, sl.start, sl.cursor, sl.cand);
+    k_slot_fill<KW><<<nb, 256, 0, s>>>(ct, M, sg, anchor, sl.start, sl.cursor, sl.cand);
     ncompact_dev = (int *)(sl.flag_scan + ndense);
-    k_slot_sort<<<ctx->sm_count * 4, kBlock, 0, s>>>(g, sg.mode, ncompact_cap, ncompact_dev, sg,
+    k_slot_sort<<<ctx->sm_count * 4, kBlock, 0, s>>>(ct, sg.mode, ncompact_cap, ncompact_dev, sg,
                                                      sl.dense_of, sl.start, anchor, level, sl,
                                                      ctx->status);
     return check_launch("build_slots");
@@ -1267,16 +1317,17 @@ static int run_interpolate(ib_ctx *ctx, const DevGrid &g, const void *u, int M, 
 }
 
 template <typename T, int KER>
-static int run_spread(ib_ctx *ctx, const DevGrid &g, int M, const double *X, const double *F,
+static int run_spread(ib_ctx *ctx, const ib_grid *grid, int M, const double *X, const double *F,
                       const double *dV, void *f, cudaStream_t s) {
     constexpr int KW = Kernel<KER>::W;
     Arena ar(ctx);
     MarkerState<T> ms;
     take_markers<T>(ar, M, ms);
+    const CaseTab ct = single_case(grid, f, nullptr, 0);  // spread into the case's u slot
+    const DevGrid &g = ct.one.g;
     SlotGeom sg{};
     sg.mode = 0;
-    for (int a = 0; a < 3; ++a) sg.tiles[a] = (g.n[a] + kTile - 1) / kTile;
-    long long ndense = (long long)sg.tiles[0] * sg.tiles[1] * sg.tiles[2];
+    const long long ndense = ct.ntiles;
     if (ndense > (1LL << 30)) return set_error(IB_ERR_UNSUPPORTED, "grid has too many tiles");
     if (!ar.ok())
         return oom_error(ar.used, ar.cap);
@@ -1285,21 +1336,19 @@ static int run_spread(ib_ctx *ctx, const DevGrid &g, int M, const double *X, con
     k_prep_spread<T, KER><<<nb, 256, 0, s>>>(g, M, X, F, dV, ms, ctx->status);
     Slots sl;
     int *ncompact = nullptr;
-    int rc = build_slots<KW>(ctx, ar, g, M, (int)ndense, sg, ms.anchor, nullptr, sl, ncompact, s);
+    int rc = build_slots<KW>(ctx, ar, ct, M, (int)ndense, sg, ms.anchor, nullptr, sl, ncompact, s);
     if (rc) return rc;
     cudaFuncSetAttribute(k_spread_gather<T, KER>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)stage_bytes<T>());
-    k_spread_gather<T, KER><<<ctx->sm_count * 2, kBlock, stage_bytes<T>(), s>>>(g, ncompact, sl, ms.wts, ms.A,
-                                                                               (T *)f);
+    k_spread_gather<T, KER><<<ctx->sm_count * 2, kBlock, stage_bytes<T>(), s>>>(ct, ncompact, sl, ms.wts, ms.A);
     return check_launch("ib_spread");
 }
 
 template <typename T, int KER>
-static int run_mdf(ib_ctx *ctx, const DevGrid &g, void *u, const ib_particles *pp, const ib_markers *mk,
-                   int Ns, double dt, int order, double *F_out, void *f_out, cudaStream_t s) {
+static int run_mdf(ib_ctx *ctx, Arena &ar, const CaseTab &ct, const ib_particles *pp, const ib_markers *mk,
+                   int Ns, double dt, int order, double *F_out, cudaStream_t s) {
     constexpr int KW = Kernel<KER>::W;
     int P = pp->P, M = mk->M;
-    Arena ar(ctx);
     MarkerState<T> ms;
     take_markers<T>(ar, M, ms);
     double *rho = ar.take<double>(P);
@@ -1323,24 +1372,18 @@ static int run_mdf(ib_ctx *ctx, const DevGrid &g, void *u, const ib_particles *p
     bar.gen = bar.count + 1;
     SlotGeom sg{};
     sg.mode = order == IB_ORDER_SEQUENTIAL ? 1 : 0;
-    long long ndense;
-    if (sg.mode == 0) {
-        for (int a = 0; a < 3; ++a) sg.tiles[a] = (g.n[a] + kTile - 1) / kTile;
-        ndense = (long long)sg.tiles[0] * sg.tiles[1] * sg.tiles[2];
-    } else {
-        ndense = (long long)P * kLocalSlots;
-    }
+    const long long ndense = sg.mode == 0 ? ct.ntiles : (long long)P * kLocalSlots;
     if (ndense > (1LL << 30)) return set_error(IB_ERR_UNSUPPORTED, "too many tiles");
     if (!ar.ok())
         return oom_error(ar.used, ar.cap);
     PhaseTimer tprep(ctx, IB_PHASE_MDF_PREP, s);
-    k_prep_particles<T, KER><<<P, kBlock, 0, s>>>(g, P, pp->Xr, pp->Ur, pp->Wr, pp->marker_offset, mk->R,
+    k_prep_particles<T, KER><<<P, kBlock, 0, s>>>(ct, P, pp->Xr, pp->Ur, pp->Wr, pp->marker_offset, mk->R,
                                                  mk->dV, ms, F_out, rho, box_lo, box_dim, part_of,
                                                  ctx->status);
     if (order == IB_ORDER_SEQUENTIAL)
-        k_conflicts<<<grid_blocks(P, 128, ctx->sm_count), 128, 0, s>>>(g, P, KW, pp->Xr, rho, nbr_cnt, nbr);
+        k_conflicts<<<grid_blocks(P, 128, ctx->sm_count), 128, 0, s>>>(ct, P, KW, pp->Xr, rho, nbr_cnt, nbr);
     cudaFuncSetAttribute(k_levels, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLevSmem);
-    k_levels<<<1, 1024, kLevSmem, s>>>(g, P, order, KW, pp->Xr, rho, pp->marker_offset, nbr_cnt, nbr, lo, lev_work);
+    k_levels<<<1, 1024, kLevSmem, s>>>(ct, P, order, KW, pp->Xr, rho, pp->marker_offset, nbr_cnt, nbr, lo, lev_work);
     k_marker_order<<<P < ctx->sm_count * 2 ? P : ctx->sm_count * 2, kBlock, 0, s>>>(P, pp->marker_offset, lo.mbase,
                                                                                     ms.anchor, mperm);
     sg.part_of = part_of;
@@ -1349,15 +1392,14 @@ static int run_mdf(ib_ctx *ctx, const DevGrid &g, void *u, const ib_particles *p
     sg.box_dim = box_dim;
     Slots sl;
     int *ncompact = nullptr;
-    int rc = build_slots<KW>(ctx, ar, g, M, (int)ndense, sg, ms.anchor, lo.level, sl, ncompact, s);
+    int rc = build_slots<KW>(ctx, ar, ct, M, (int)ndense, sg, ms.anchor, lo.level, sl, ncompact, s);
     if (rc) return rc;
     k_level_slots<<<1, 256, 0, s>>>(sg.mode, lo.nlev, lo.lev_pbeg, sl.flag_scan, (int)ndense, lev_sbeg);
     cudaMemsetAsync(bar.count, 0, 2 * sizeof(unsigned int), s);
     tprep.stop();
     PassArgs<T> a;
-    a.g = g;
-    a.u = (T *)u;
-    a.f_out = (T *)f_out;
+    a.ct = ct;
+    a.part_of = part_of;
     a.F = F_out;
     a.dV = mk->dV;
     a.ms = ms;
@@ -1442,16 +1484,13 @@ int ib_spread(ib_ctx *ctx, const ib_grid *grid, int M, const double *X, const do
     if (M < 0) return set_error(IB_ERR_INVALID, "M < 0");
     if (M == 0) return IB_OK;
     if (!X || !F || !dV || !f) return set_error(IB_ERR_INVALID, "NULL array");
-    DevGrid g = make_dev_grid(grid);
-    return DISPATCH(grid->prec, delta, run_spread, ctx, g, M, X, F, dV, f, (cudaStream_t)stream);
+    return DISPATCH(grid->prec, delta, run_spread, ctx, grid, M, X, F, dV, f, (cudaStream_t)stream);
 }
 
-int ib_multidirect_forcing(ib_ctx *ctx, const ib_grid *grid, void *u, const ib_particles *parts,
-                           const ib_markers *marks, int Ns, double dt, int delta, int order, double *F_out,
-                           void *f_out, void *stream) {
+// Arguments shared by the single-case and batch forms; 1 = nothing to do.
+static int check_mdf_args(ib_ctx *ctx, const ib_particles *parts, const ib_markers *marks, int Ns, double dt,
+                          int delta, int order, const double *F_out) {
     if (!ctx) return set_error(IB_ERR_INVALID, "ctx is NULL");
-    int rc = validate_grid(grid, 1);
-    if (rc) return rc;
     if (!parts || !marks) return set_error(IB_ERR_INVALID, "particles/markers NULL");
     if (delta != IB_DELTA_ROMA3 && delta != IB_DELTA_PESKIN4) return set_error(IB_ERR_INVALID, "bad delta");
     if (order != IB_ORDER_SEQUENTIAL && order != IB_ORDER_SIMULTANEOUS)
@@ -1459,12 +1498,38 @@ int ib_multidirect_forcing(ib_ctx *ctx, const ib_grid *grid, void *u, const ib_p
     if (Ns < 1) return set_error(IB_ERR_INVALID, "Ns must be >= 1");
     if (!(dt > 0.0) || !isfinite(dt)) return set_error(IB_ERR_INVALID, "dt must be finite and > 0");
     if (parts->P < 0 || marks->M < 0) return set_error(IB_ERR_INVALID, "negative P or M");
-    if (parts->P == 0 || marks->M == 0) return IB_OK;
-    if (!u || !parts->Xr || !parts->Ur || !parts->Wr || !parts->marker_offset || !marks->R || !marks->dV ||
-        !F_out)
+    if (parts->P == 0 || marks->M == 0) return 1;
+    if (!parts->Xr || !parts->Ur || !parts->Wr || !parts->marker_offset || !marks->R || !marks->dV || !F_out)
         return set_error(IB_ERR_INVALID, "NULL array");
-    DevGrid g = make_dev_grid(grid);
-    return DISPATCH(grid->prec, delta, run_mdf, ctx, g, u, parts, marks, Ns, dt, order, F_out, f_out,
+    return IB_OK;
+}
+
+int ib_multidirect_forcing(ib_ctx *ctx, const ib_grid *grid, void *u, const ib_particles *parts,
+                           const ib_markers *marks, int Ns, double dt, int delta, int order, double *F_out,
+                           void *f_out, void *stream) {
+    int rc = check_mdf_args(ctx, parts, marks, Ns, dt, delta, order, F_out);
+    if (rc) return rc == 1 ? IB_OK : rc;
+    rc = validate_grid(grid, 1);
+    if (rc) return rc;
+    if (!u) return set_error(IB_ERR_INVALID, "NULL array");
+    const CaseTab ct = single_case(grid, u, f_out, parts->P);
+    Arena ar(ctx);
+    return DISPATCH(grid->prec, delta, run_mdf, ctx, ar, ct, parts, marks, Ns, dt, order, F_out,
+                    (cudaStream_t)stream);
+}
+
+int ib_batch_multidirect_forcing(ib_ctx *ctx, int ncases, const ib_case *cases, const ib_particles *parts,
+                                 const ib_markers *marks, int Ns, double dt, int delta, int order, double *F_out,
+                                 void *stream) {
+    int rc = check_mdf_args(ctx, parts, marks, Ns, dt, delta, order, F_out);
+    if (rc) return rc == 1 ? IB_OK : rc;
+    for (int c = 0; c < ncases && cases; ++c)
+        if (!cases[c].u) return set_error(IB_ERR_INVALID, "case %d: NULL field", c);
+    Arena ar(ctx);
+    CaseTab ct;
+    rc = build_case_table(ctx, ar, ncases, cases, parts->P, 1, ct, (cudaStream_t)stream);
+    if (rc) return rc;
+    return DISPATCH(cases[0].grid.prec, delta, run_mdf, ctx, ar, ct, parts, marks, Ns, dt, order, F_out,
                     (cudaStream_t)stream);
 }
 

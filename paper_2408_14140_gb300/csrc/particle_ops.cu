@@ -95,7 +95,7 @@ __device__ __forceinline__ int find_row(const int *pre, int nrows, int t) {
 // Per-row index ranges come from FP32 square roots widened by a cell; every
 // node and boundary cell is still tested exactly in FP64.
 template <typename T>
-__global__ void __launch_bounds__(kVolThreads) k_volume(DevGrid g, const T *__restrict__ u, int P,
+__global__ void __launch_bounds__(kVolThreads) k_volume(CaseTab ct, int P,
                                                         const double *__restrict__ Xr,
                                                         const double *__restrict__ radius,
                                                         double *__restrict__ partial,
@@ -110,6 +110,9 @@ __global__ void __launch_bounds__(kVolThreads) k_volume(DevGrid g, const T *__re
     __shared__ int c_node[kVolAx], c_int[kVolAx], c_bnd[kVolAx];
     const int p = blockIdx.x / kVolSplit, split = blockIdx.x % kVolSplit;
     if (p >= P) return;
+    const DevCase &cd = ct.of_particle(p);
+    const DevGrid g = cd.g;
+    const T *__restrict__ u = (const T *)cd.u;
     const double c[3] = {Xr[3 * p], Xr[3 * p + 1], Xr[3 * p + 2]};
     const double Rp = radius[p];
     double acc[7] = {0, 0, 0, 0, 0, 0, 0};
@@ -393,9 +396,9 @@ __global__ void __launch_bounds__(256) k_force_torque(int P, const int *__restri
 // ---------------------------------------------------------------------------
 struct CollideArgs {
     int P;
+    CaseTab ct;  // pairs are taken within a case, in the case's periodic box
     double *Xr, *Ur, *Wr;
     const double *radius, *rho_p;
-    double L[3];
     double rho_f, g[3], g_coll, eps_c, d_c, dt;
     const double *Fib, *Tib, *Iu_new, *Iu_old, *Ir_new, *Ir_old;
     double *Fc_out;
@@ -408,20 +411,22 @@ __global__ void k_collide_forces(CollideArgs a, double *__restrict__ Fc) {
     const int lane = threadIdx.x & 31;
     const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (i >= a.P) return;
-    const double iL[3] = {1.0 / a.L[0], 1.0 / a.L[1], 1.0 / a.L[2]};
+    const DevCase &cd = a.ct.of_particle(i);
+    const double L[3] = {cd.g.n[0] * cd.g.h, cd.g.n[1] * cd.g.h, cd.g.n[2] * cd.g.h};
+    const double iL[3] = {1.0 / L[0], 1.0 / L[1], 1.0 / L[2]};
     const double xi[3] = {a.Xr[3 * i], a.Xr[3 * i + 1], a.Xr[3 * i + 2]};
     const double Ri = a.radius[i];
     const double mi = a.rho_p[i] * 4.0 / 3.0 * kPi * Ri * Ri * Ri;
     const double idc = 1.0 / a.d_c;
     const double gscale = 0.5 * a.g_coll / a.eps_c;
     double f[3] = {0, 0, 0};
-    for (int j = lane; j < a.P; j += 32) {
+    for (int j = cd.p0 + lane; j < cd.p1; j += 32) {
         if (j == i) continue;
         double del[3], d2 = 0.0;
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
             const double dd = a.Xr[3 * j + k] - xi[k];
-            del[k] = dd - a.L[k] * rint(dd * iL[k]);
+            del[k] = dd - L[k] * rint(dd * iL[k]);
             d2 += del[k] * del[k];
         }
         const double Rj = a.radius[j];
@@ -468,9 +473,8 @@ __global__ void k_newton_euler(CollideArgs a, const double *__restrict__ Fc, Dev
 }
 
 template <typename T>
-static int run_volume(ib_ctx *ctx, const DevGrid &g, const void *u, const ib_particles *pp, double *Iu,
+static int run_volume(ib_ctx *ctx, Arena &ar, const CaseTab &ct, const ib_particles *pp, double *Iu,
                       double *Irxu, double *vol, cudaStream_t s) {
-    Arena ar(ctx);
     double *partial = ar.take<double>((size_t)pp->P * kVolSplit * 7);
     unsigned int *done = ar.take<unsigned int>(pp->P);
     if (!ar.ok())
@@ -478,8 +482,8 @@ static int run_volume(ib_ctx *ctx, const DevGrid &g, const void *u, const ib_par
     PhaseTimer tm(ctx, IB_PHASE_VOLUME, s);
     cudaMemsetAsync(done, 0, sizeof(unsigned int) * pp->P, s);
     cudaFuncSetAttribute(k_volume<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kVolSmem);
-    k_volume<T><<<pp->P * kVolSplit, kVolThreads, kVolSmem, s>>>(g, (const T *)u, pp->P, pp->Xr, pp->radius,
-                                                                 partial, done, Iu, Irxu, vol, ctx->status);
+    k_volume<T><<<pp->P * kVolSplit, kVolThreads, kVolSmem, s>>>(ct, pp->P, pp->Xr, pp->radius, partial, done,
+                                                                 Iu, Irxu, vol, ctx->status);
     return check_launch("particle_volume_integrals");
 }
 
@@ -527,15 +531,15 @@ static int static_scratch(double **scratch, DevStatus **status, unsigned int **d
 }
 
 template <typename T>
-static int run_volume_static(const DevGrid &g, const void *u, const ib_particles *pp, double *Iu,
+static int run_volume_static(const CaseTab &ct, const ib_particles *pp, double *Iu,
                              double *Irxu, double *vol, cudaStream_t s) {
     double *partial = nullptr;
     DevStatus *st = nullptr;
     unsigned int *done = nullptr;
     int rc = static_scratch(&partial, &st, &done);
     if (rc) return rc;
-    k_volume<T><<<pp->P * kVolSplit, kVolThreads, kVolSmem, s>>>(g, (const T *)u, pp->P, pp->Xr, pp->radius,
-                                                                 partial, done, Iu, Irxu, vol, st);
+    k_volume<T><<<pp->P * kVolSplit, kVolThreads, kVolSmem, s>>>(ct, pp->P, pp->Xr, pp->radius, partial, done,
+                                                                 Iu, Irxu, vol, st);
     return check_launch("particle_volume_integrals_static");
 }
 
@@ -554,10 +558,29 @@ int particle_volume_integrals(ib_ctx *ctx, const ib_grid *grid, const void *u, c
     if (parts->P == 0) return IB_OK;
     if (!u || !parts->Xr || !parts->radius) return set_error(IB_ERR_INVALID, "NULL array");
     if ((long long)parts->P * kVolSplit > (1LL << 31) - 1) return set_error(IB_ERR_UNSUPPORTED, "too many particles");
-    DevGrid g = make_dev_grid(grid);
+    const CaseTab ct = single_case(grid, (void *)u, nullptr, parts->P);
+    Arena ar(ctx);
     if (grid->prec == IB_F64)
-        return run_volume<double>(ctx, g, u, parts, Iu, Irxu, vol, (cudaStream_t)stream);
-    return run_volume<float>(ctx, g, u, parts, Iu, Irxu, vol, (cudaStream_t)stream);
+        return run_volume<double>(ctx, ar, ct, parts, Iu, Irxu, vol, (cudaStream_t)stream);
+    return run_volume<float>(ctx, ar, ct, parts, Iu, Irxu, vol, (cudaStream_t)stream);
+}
+
+int ib_batch_volume_integrals(ib_ctx *ctx, int ncases, const ib_case *cases, const ib_particles *parts,
+                              double *Iu, double *Irxu, double *vol, void *stream) {
+    if (!ctx) return set_error(IB_ERR_INVALID, "ctx is NULL");
+    if (!parts || parts->P < 0) return set_error(IB_ERR_INVALID, "bad particles");
+    if (parts->P == 0) return IB_OK;
+    if (!parts->Xr || !parts->radius || !Iu || !Irxu || !vol) return set_error(IB_ERR_INVALID, "NULL array");
+    for (int c = 0; c < ncases && cases; ++c)
+        if (!cases[c].u) return set_error(IB_ERR_INVALID, "case %d: NULL field", c);
+    if ((long long)parts->P * kVolSplit > (1LL << 31) - 1) return set_error(IB_ERR_UNSUPPORTED, "too many particles");
+    Arena ar(ctx);
+    CaseTab ct;
+    int rc = build_case_table(ctx, ar, ncases, cases, parts->P, 1, ct, (cudaStream_t)stream);
+    if (rc) return rc;
+    if (cases[0].grid.prec == IB_F64)
+        return run_volume<double>(ctx, ar, ct, parts, Iu, Irxu, vol, (cudaStream_t)stream);
+    return run_volume<float>(ctx, ar, ct, parts, Iu, Irxu, vol, (cudaStream_t)stream);
 }
 
 int particle_volume_integrals_static(const ib_grid *grid, const void *u, const ib_particles *parts,
@@ -570,10 +593,10 @@ int particle_volume_integrals_static(const ib_grid *grid, const void *u, const i
                          parts->P, IB_STATIC_VOLUME_MAX_P);
     if (parts->P == 0) return IB_OK;
     if (!u || !parts->Xr || !parts->radius) return set_error(IB_ERR_INVALID, "NULL array");
-    DevGrid g = make_dev_grid(grid);
+    const CaseTab ct = single_case(grid, (void *)u, nullptr, parts->P);
     if (grid->prec == IB_F64)
-        return run_volume_static<double>(g, u, parts, Iu, Irxu, vol, (cudaStream_t)stream);
-    return run_volume_static<float>(g, u, parts, Iu, Irxu, vol, (cudaStream_t)stream);
+        return run_volume_static<double>(ct, parts, Iu, Irxu, vol, (cudaStream_t)stream);
+    return run_volume_static<float>(ct, parts, Iu, Irxu, vol, (cudaStream_t)stream);
 }
 
 int particle_force_torque(ib_ctx *ctx, const ib_particles *parts, const ib_markers *marks, const double *F,
@@ -590,35 +613,37 @@ int particle_force_torque(ib_ctx *ctx, const ib_particles *parts, const ib_marke
     return check_launch("particle_force_torque");
 }
 
-int particle_collide_update(ib_ctx *ctx, ib_particles *parts, const ib_grid *grid, const ib_phys *phys,
-                            double dt, const double *F_ib, const double *T_ib, const double *Iu_new,
-                            const double *Iu_old, const double *Irxu_new, const double *Irxu_old,
-                            double *Fc_out, void *stream) {
+// Arguments shared by the single-case and batch forms; 1 = nothing to do.
+static int check_collide_args(ib_ctx *ctx, const ib_particles *parts, const ib_phys *phys, double dt,
+                              const double *F_ib, const double *T_ib, const double *Iu_new, const double *Iu_old,
+                              const double *Irxu_new, const double *Irxu_old) {
     if (!ctx) return set_error(IB_ERR_INVALID, "ctx is NULL");
-    int rc = validate_grid(grid, 0);
-    if (rc) return rc;
     if (!parts || !phys || parts->P < 0) return set_error(IB_ERR_INVALID, "bad arguments");
     if (!(dt > 0.0) || !isfinite(dt)) return set_error(IB_ERR_INVALID, "dt must be finite and > 0");
     if (!(phys->eps_c > 0.0) || !(phys->d_c > 0.0)) return set_error(IB_ERR_INVALID, "eps_c and d_c must be > 0");
-    if (parts->P == 0) return IB_OK;
+    if (parts->P == 0) return 1;
     if (!parts->Xr || !parts->Ur || !parts->Wr || !parts->radius || !parts->rho_p || !F_ib || !T_ib ||
         !Iu_new || !Iu_old || !Irxu_new || !Irxu_old)
         return set_error(IB_ERR_INVALID, "NULL array");
-    Arena ar(ctx);
+    return IB_OK;
+}
+
+static int run_collide(ib_ctx *ctx, Arena &ar, const CaseTab &ct, ib_particles *parts, const ib_phys *phys,
+                       double dt, const double *F_ib, const double *T_ib, const double *Iu_new,
+                       const double *Iu_old, const double *Irxu_new, const double *Irxu_old, double *Fc_out,
+                       cudaStream_t s) {
     double *Fc = ar.take<double>((size_t)3 * parts->P);
     if (!ar.ok())
         return oom_error(ar.used, ar.cap);
     CollideArgs a;
     a.P = parts->P;
+    a.ct = ct;
     a.Xr = parts->Xr;
     a.Ur = parts->Ur;
     a.Wr = parts->Wr;
     a.radius = parts->radius;
     a.rho_p = parts->rho_p;
-    for (int k = 0; k < 3; ++k) {
-        a.L[k] = grid->n[k] * grid->h;
-        a.g[k] = phys->g[k];
-    }
+    for (int k = 0; k < 3; ++k) a.g[k] = phys->g[k];
     a.rho_f = phys->rho_f;
     a.g_coll = phys->g_coll;
     a.eps_c = phys->eps_c;
@@ -632,12 +657,39 @@ int particle_collide_update(ib_ctx *ctx, ib_particles *parts, const ib_grid *gri
     a.Ir_old = Irxu_old;
     a.Fc_out = Fc_out;
     a.Xnew = nullptr;
-    cudaStream_t s = (cudaStream_t)stream;
     int nb = (parts->P + 127) / 128;
     PhaseTimer tm(ctx, IB_PHASE_COLLIDE, s);
     k_collide_forces<<<(parts->P + 3) / 4, 128, 0, s>>>(a, Fc);
     k_newton_euler<<<nb, 128, 0, s>>>(a, Fc, ctx->status);
     return check_launch("particle_collide_update");
+}
+
+int particle_collide_update(ib_ctx *ctx, ib_particles *parts, const ib_grid *grid, const ib_phys *phys,
+                            double dt, const double *F_ib, const double *T_ib, const double *Iu_new,
+                            const double *Iu_old, const double *Irxu_new, const double *Irxu_old,
+                            double *Fc_out, void *stream) {
+    int rc = check_collide_args(ctx, parts, phys, dt, F_ib, T_ib, Iu_new, Iu_old, Irxu_new, Irxu_old);
+    if (rc) return rc == 1 ? IB_OK : rc;
+    rc = validate_grid(grid, 0);
+    if (rc) return rc;
+    const CaseTab ct = single_case(grid, nullptr, nullptr, parts->P);
+    Arena ar(ctx);
+    return run_collide(ctx, ar, ct, parts, phys, dt, F_ib, T_ib, Iu_new, Iu_old, Irxu_new, Irxu_old, Fc_out,
+                       (cudaStream_t)stream);
+}
+
+int ib_batch_collide_update(ib_ctx *ctx, int ncases, const ib_case *cases, ib_particles *parts,
+                            const ib_phys *phys, double dt, const double *F_ib, const double *T_ib,
+                            const double *Iu_new, const double *Iu_old, const double *Irxu_new,
+                            const double *Irxu_old, double *Fc_out, void *stream) {
+    int rc = check_collide_args(ctx, parts, phys, dt, F_ib, T_ib, Iu_new, Iu_old, Irxu_new, Irxu_old);
+    if (rc) return rc == 1 ? IB_OK : rc;
+    Arena ar(ctx);
+    CaseTab ct;
+    rc = build_case_table(ctx, ar, ncases, cases, parts->P, 0, ct, (cudaStream_t)stream);
+    if (rc) return rc;
+    return run_collide(ctx, ar, ct, parts, phys, dt, F_ib, T_ib, Iu_new, Iu_old, Irxu_new, Irxu_old, Fc_out,
+                       (cudaStream_t)stream);
 }
 
 }  // extern "C"
