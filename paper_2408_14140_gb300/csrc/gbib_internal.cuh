@@ -47,8 +47,10 @@ struct CaseTab {
     long long ntiles;    // global 8^3 tiles over all cases
     DevCase one;
     __device__ __forceinline__ int case_of(int p) const { return arr ? pcase[p] : 0; }
-    __device__ __forceinline__ const DevCase &get(int c) const { return arr ? arr[c] : one; }
-    __device__ __forceinline__ const DevCase &of_particle(int p) const { return arr ? arr[pcase[p]] : one; }
+    // by value: a reference could point at either the kernel parameter or
+    // global memory, which forces the parameter into local memory
+    __device__ __forceinline__ DevCase get(int c) const { return arr ? arr[c] : one; }
+    __device__ __forceinline__ DevCase of_particle(int p) const { return arr ? arr[pcase[p]] : one; }
 };
 
 // Device-side error latch: first code wins.

@@ -1048,7 +1048,7 @@ constexpr size_t tile_stage_bytes() {
 }
 
 template <typename T, int KER>
-__global__ void __launch_bounds__(256) k_gather_level(PassArgs<T> a, int L) {
+__global__ void __launch_bounds__(256, 5) k_gather_level(PassArgs<T> a, int L) {
     constexpr int KW = Kernel<KER>::W;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     if (L >= *a.nlev) return;
@@ -1425,6 +1425,10 @@ static int run_mdf(ib_ctx *ctx, Arena &ar, const CaseTab &ct, const ib_particles
         const int gi = grid_blocks(M, 256, ctx->sm_count);
         const size_t gsm = tile_stage_bytes<T>();
         cudaFuncSetAttribute(k_gather_level<T, KER>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsm);
+        // one resident wave of gather CTAs (grid-stride over the wavefront's tiles)
+        int gper = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&gper, k_gather_level<T, KER>, 256, gsm);
+        const int gg = ctx->sm_count * (gper > 0 ? gper : 1);
         for (int L = 0; L < Lenq; ++L)
             for (int m = 0; m < Ns; ++m) {
                 {
@@ -1432,7 +1436,7 @@ static int run_mdf(ib_ctx *ctx, Arena &ar, const CaseTab &ct, const ib_particles
                     k_interp_level<T, KER><<<gi, 256, 0, s>>>(a, L);
                 }
                 PhaseTimer tg(ctx, IB_PHASE_MDF_GATHER, s);
-                k_gather_level<T, KER><<<ctx->sm_count * 6, 256, gsm, s>>>(a, L);
+                k_gather_level<T, KER><<<gg, 256, gsm, s>>>(a, L);
             }
     }
     int per_sm = 0;
