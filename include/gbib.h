@@ -132,7 +132,7 @@ GBIB_API int ib_ctx_sm_count(const ib_ctx *ctx);
  * phase since the last read, and resets that phase.  Timing adds two event
  * records per phase and must stay off while a stream is being captured.  */
 #define IB_PHASE_MDF_PREP 0    /* marker preparation, levels, tile binning  */
-#define IB_PHASE_MDF_PASSES 1  /* the persistent Ns-pass kernel            */
+#define IB_PHASE_MDF_PASSES 1  /* all Ns passes (resident or wavefront form) */
 #define IB_PHASE_SPREAD 2      /* ib_spread (binning + gather)              */
 #define IB_PHASE_INTERP 3      /* ib_interpolate                            */
 #define IB_PHASE_VOLUME 4      /* particle_volume_integrals                 */
@@ -144,6 +144,22 @@ GBIB_API int ib_ctx_sm_count(const ib_ctx *ctx);
 GBIB_API int ib_ctx_set_timing(ib_ctx *ctx, int enable);
 GBIB_API int ib_ctx_read_timing(ib_ctx *ctx, int phase, double *ms_total,
                                 int *launches);
+
+/* ---- kernels of the sequential-order passes ----------------------------
+ * Both forms compute bitwise the same result (same summation orders).
+ * RESIDENT (the default, AUTO): one thread-block cluster per particle keeps
+ *   the particle's band in shared memory for all Ns passes; particles start
+ *   as soon as the earlier particles they conflict with are stored.
+ * WAVEFRONT: per wavefront of non-conflicting particles and per pass, an
+ *   interpolation kernel and a gather kernel through global memory (a
+ *   persistent cooperative kernel takes the wavefronts beyond the count the
+ *   previous call on the context saw).
+ * The simultaneous order always runs the wavefront form (one wavefront).
+ * Returns IB_ERR_INVALID for any other value.                             */
+#define IB_PASSES_AUTO 0
+#define IB_PASSES_WAVEFRONT 1
+#define IB_PASSES_RESIDENT 2
+GBIB_API int ib_ctx_set_pass_kernels(ib_ctx *ctx, int which);
 
 /* ---- velocity interpolation J: Eq. (u), Eq. (vi), Algorithm 1 -----------
  * U[l] = sum_ijk u(x_ijk) delta_h(x_ijk - X[l]) h^3 for l < M, where

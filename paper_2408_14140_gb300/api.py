@@ -36,13 +36,14 @@ ROMA3 = 0
 PESKIN4 = 1
 SEQUENTIAL = 0
 SIMULTANEOUS = 1
+PASSES = {"auto": 0, "wavefront": 1, "resident": 2}
 
 PHASES = {"mdf_prep": 0, "mdf_passes": 1, "spread": 2, "interp": 3, "volume": 4,
           "force": 5, "collide": 6, "mdf_interp": 7, "mdf_gather": 8}
 
 EXPORTS = ["ib_ctx_create", "ib_ctx_reserve", "ib_ctx_destroy", "ib_ctx_status",
            "ib_last_error", "ib_workspace_needed", "ib_ctx_sm_count",
-           "ib_ctx_set_timing", "ib_ctx_read_timing",
+           "ib_ctx_set_timing", "ib_ctx_read_timing", "ib_ctx_set_pass_kernels",
            "ib_interpolate", "ib_spread", "ib_multidirect_forcing",
            "particle_volume_integrals", "particle_force_torque",
            "particle_collide_update", "particle_volume_integrals_static",
@@ -103,6 +104,7 @@ def load(path: str = LIB_PATH):
         "ib_ctx_sm_count": (i, [p]),
         "ib_ctx_set_timing": (i, [p, i]),
         "ib_ctx_read_timing": (i, [p, i, ctypes.POINTER(d), ctypes.POINTER(i)]),
+        "ib_ctx_set_pass_kernels": (i, [p, i]),
         "ib_interpolate": (i, [p, p, p, i, p, i, p, p]),
         "ib_spread": (i, [p, p, i, p, p, p, i, p, p]),
         "ib_multidirect_forcing": (i, [p, p, p, p, p, i, d, i, i, p, p, p]),
@@ -202,6 +204,11 @@ class Context:
     def set_timing(self, enable: bool):
         """Record CUDA events around the library's kernels (see gbib.h)."""
         self._check(self.lib.ib_ctx_set_timing(self.handle, 1 if enable else 0))
+
+    def set_pass_kernels(self, which: str):
+        """Kernels of the sequential-order passes: "auto", "wavefront" or
+        "resident" (see gbib.h; every choice gives bitwise the same result)."""
+        self._check(self.lib.ib_ctx_set_pass_kernels(self.handle, PASSES[which]))
 
     def read_timing(self, phase: str):
         """(total ms, launches) of one phase since the last read; resets it."""

@@ -297,6 +297,7 @@ int ib_ctx_create(ib_ctx **ctx, size_t workspace_bytes) {
         return set_error(IB_ERR_CUDA, "context host word allocation failed");
     }
     *c->h_nlev = 0;
+    c->pass_kernels = IB_PASSES_AUTO;
     *ctx = c;
     return IB_OK;
 }
@@ -320,6 +321,14 @@ int ib_ctx_reserve(ib_ctx *c, size_t bytes) {
 int ib_ctx_set_timing(ib_ctx *c, int enable) {
     if (!c) return set_error(IB_ERR_INVALID, "ctx is NULL");
     c->timing = enable ? 1 : 0;
+    return IB_OK;
+}
+
+int ib_ctx_set_pass_kernels(ib_ctx *c, int which) {
+    if (!c) return set_error(IB_ERR_INVALID, "ctx is NULL");
+    if (which != IB_PASSES_AUTO && which != IB_PASSES_WAVEFRONT && which != IB_PASSES_RESIDENT)
+        return set_error(IB_ERR_INVALID, "bad pass-kernel choice %d", which);
+    c->pass_kernels = which;
     return IB_OK;
 }
 

@@ -148,6 +148,7 @@ struct ib_ctx {
     // kernels before the persistent kernel takes the rest
     int *h_nlev;         // pinned host word
     int nlev_hint;
+    int pass_kernels;    // IB_PASSES_* of the sequential order
 };
 
 namespace gbib {

@@ -1,0 +1,180 @@
+// Device-side pieces shared by the forcing kernels of arXiv 2408.14140,
+// Sec. 3.1 Step 2 (Algorithm 1): per-marker state, spreading-tile records,
+// one marker's interpolation and one cell's deterministic gather.
+#pragma once
+
+#include "gbib_internal.cuh"
+
+namespace gbib {
+
+constexpr int kBlock = 512;          // threads per CTA (one per tile cell)
+constexpr int kLocalTiles = 8;       // local tiles per axis of a particle box
+constexpr int kLocalSlots = kLocalTiles * kLocalTiles * kLocalTiles;
+constexpr int kMaxBox = kLocalTiles * kTile;  // 64 cells
+// A tile's candidates are sorted by (anchor row, x offset, marker).  Bin
+// (row, v), v = x offset + 3 in [0, 10], holds the markers whose first stencil
+// cell is at row `row` and x offset v - 3 from the tile; kBins[row * 12 + v]
+// is the bin's first candidate and [row * 12 + 11] the row's end, so a cell
+// reads exactly the KW^3 bins of its stencil.
+constexpr int kBinsPerRow = 12;
+// Conflict-list entries kept per particle (more: the list is marked full).
+constexpr int kMaxNbr = 48;
+// Bounded device-side waits give up after this many SM cycles (~2 s).
+constexpr long long kSpinCycles = 4LL * 1000 * 1000 * 1000;  // ~2 s at 2 GHz
+
+__device__ __forceinline__ unsigned int ld_acquire(const unsigned int *p) {
+    unsigned int v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+constexpr int kBins = kRows * kBinsPerRow + 1;
+
+// Per-marker state kept in the workspace for one call.
+template <typename T>
+struct MarkerState {
+    uint64_t *anchor;  // [M] wrapped first stencil cell
+    T *wts;            // [M][12] per-axis weights (x 0..3, y 4..7, z 8..11)
+    T *A;              // [M][4] spread source of the current pass
+    double *Ud;        // [M][3] desired velocity
+};
+
+// Slot (spreading tile) records.
+struct Slots {
+    uint32_t *count;   // [ndense] candidates per dense slot
+    uint32_t *start;   // [ndense+1] exclusive scan of count
+    uint32_t *cursor;  // [ndense] fill cursors
+    uint32_t *flag_scan;  // [ndense+1] compact index of non-empty slots
+    uint32_t *dense_of;   // [ncompact_max] dense id of each compact slot
+    uint32_t *cand;    // [total candidates] marker ids, sorted per slot
+    uint16_t *bins;    // [ncompact_max][kBins] bin starts, relative (see kBins)
+    int4 *geo_lo;      // [ncompact_max] tile first cell (wrapped), w = level
+    int4 *geo_dim;     // [ncompact_max] tile dims, w = first candidate
+    int *geo_case;     // [ncompact_max] case of the tile
+};
+
+// ---------------------------------------------------------------------------
+// interpolation of one marker from precomputed weights
+// ---------------------------------------------------------------------------
+// Loads of data that other CTAs of the persistent kernel write between grid
+// barriers (COH) are ordinary weak loads: the barrier is a GPU-scope
+// release/acquire pattern, so by the PTX memory model every write before it
+// is visible to every load after it.  (The read-only path, ld.global.nc, is
+// not coherent with writes made during the kernel and is used only for data
+// that no kernel writes meanwhile.)  ld.global.cg forms are avoided here:
+// they were issued one at a time, serialising ~80 L2 round trips per marker.
+template <bool COH, typename T>
+__device__ __forceinline__ T ld(const T *p) {
+    if (COH) return *p;
+    return __ldg(p);
+}
+
+template <typename T, int KW, bool COH = false>
+__device__ __forceinline__ void interp_marker(const T *__restrict__ u, const DevGrid &g,
+                                              long long N, uint64_t anc,
+                                              const T *__restrict__ w, T out[3]) {
+    int ix[KW], iy[KW], iz[KW];
+    int ax = anchor_x(anc), ay = anchor_y(anc), az = anchor_z(anc);
+#pragma unroll
+    for (int k = 0; k < KW; ++k) {
+        ix[k] = wrap_add(ax, k, g.n[0]);
+        iy[k] = wrap_add(ay, k, g.n[1]);
+        iz[k] = wrap_add(az, k, g.n[2]);
+    }
+    T a0 = 0, a1 = 0, a2 = 0;
+#pragma unroll 1
+    for (int kz = 0; kz < KW; ++kz) {
+#pragma unroll
+        for (int ky = 0; ky < KW; ++ky) {
+            long long row = ((long long)iz[kz] * g.n[1] + iy[ky]) * g.n[0];
+            T wyz = w[8 + kz] * w[4 + ky];
+#pragma unroll
+            for (int kx = 0; kx < KW; ++kx) {
+                long long c = row + ix[kx];
+                T wt = wyz * w[kx];
+                a0 += wt * ld<COH>(u + c);
+                a1 += wt * ld<COH>(u + N + c);
+                a2 += wt * ld<COH>(u + 2 * N + c);
+            }
+        }
+    }
+    out[0] = a0;
+    out[1] = a1;
+    out[2] = a2;
+}
+
+template <typename T, int KW, bool STAGED, bool COH>
+__device__ __forceinline__ bool gather_cell(int tx, int ty, int tz, const uint16_t *bins, const uint32_t *cand,
+                                            const T *w_src, const T *A_src, T acc[3]) {
+    bool hit = false;
+    acc[0] = acc[1] = acc[2] = T(0);
+#pragma unroll 1
+    for (int dz = 0; dz < KW; ++dz) {
+        const int rz = tz + 3 - (KW - 1) + dz, oz = KW - 1 - dz;
+#pragma unroll 1
+        for (int dy = 0; dy < KW; ++dy) {
+            const int ry = ty + 3 - (KW - 1) + dy, oy = KW - 1 - dy;
+            const uint16_t *rb = bins + (rz * kRow + ry) * kBinsPerRow + tx + 3 - (KW - 1);
+            int e[KW + 1];
+#pragma unroll
+            for (int dx = 0; dx <= KW; ++dx) e[dx] = rb[dx];
+#pragma unroll
+            for (int dx = 0; dx < KW; ++dx) {
+                const int ox = KW - 1 - dx;
+                for (int i = e[dx]; i < e[dx + 1]; ++i) {
+                    const size_t k = STAGED ? (size_t)i : (size_t)cand[i];
+                    const T *w = w_src + 12 * k;
+                    const T *A = A_src + 4 * k;
+                    T wt, a0, a1, a2;
+                    if (STAGED) {
+                        wt = w[ox] * w[4 + oy] * w[8 + oz];
+                        a0 = A[0], a1 = A[1], a2 = A[2];
+                    } else {
+                        wt = __ldg(w + ox) * __ldg(w + 4 + oy) * __ldg(w + 8 + oz);
+                        a0 = ld<COH>(A), a1 = ld<COH>(A + 1), a2 = ld<COH>(A + 2);
+                    }
+                    acc[0] += wt * a0;
+                    acc[1] += wt * a1;
+                    acc[2] += wt * a2;
+                    hit = true;
+                }
+            }
+        }
+    }
+    return hit;
+}
+
+}  // namespace gbib
+
+namespace gbib {
+
+// Arguments of the particle-resident pass kernel (sequential order): the
+// outputs of the preparation kernels plus the scheduling words.
+template <typename T>
+struct ResidentArgs {
+    CaseTab ct;
+    double *F;              // [M][3] marker forces (zeroed by the preparation)
+    const double *dV;       // [M]
+    MarkerState<T> ms;
+    Slots sl;               // particle-local tiles, compact and sorted
+    const int *mperm;       // markers level-major, spatially sorted per particle
+    const int *mbase;       // [P] first position of a particle's markers in mperm
+    const int *moff;        // [P+1]
+    const int *by_rank;     // [P] particle of each rank (level-major order)
+    const int *rank;        // [P]
+    const int *level;       // [P]
+    const int4 *box_lo;     // [P] first cell of the particle's stencil box
+    const int *nbr_cnt;     // [P] conflicts with q < p (-1: list full)
+    const int *nbr;         // [P][kMaxNbr]
+    unsigned int *done;     // [P] CTAs that finished each particle (zeroed)
+    unsigned int *ticket;   // next rank to take (zeroed)
+    int P, Ns;
+    double dt;
+    DevStatus *st;
+};
+
+// Enqueues the particle-resident passes on `s` (mdf_resident.cu).
+template <typename T, int KER>
+int launch_mdf_resident(ib_ctx *ctx, const ResidentArgs<T> &a, cudaStream_t s);
+
+}  // namespace gbib

@@ -23,94 +23,9 @@
 // needs no copy of u(0).
 #include <float.h>
 
-#include "gbib_internal.cuh"
+#include "ib_device.cuh"
 
 namespace gbib {
-
-constexpr int kBlock = 512;          // threads per CTA (one per tile cell)
-constexpr int kLocalTiles = 8;       // local tiles per axis of a particle box
-constexpr int kLocalSlots = kLocalTiles * kLocalTiles * kLocalTiles;
-constexpr int kMaxBox = kLocalTiles * kTile;  // 64 cells
-// A tile's candidates are sorted by (anchor row, x offset, marker).  Bin
-// (row, v), v = x offset + 3 in [0, 10], holds the markers whose first stencil
-// cell is at row `row` and x offset v - 3 from the tile; kBins[row * 12 + v]
-// is the bin's first candidate and [row * 12 + 11] the row's end, so a cell
-// reads exactly the KW^3 bins of its stencil.
-constexpr int kBinsPerRow = 12;
-constexpr int kBins = kRows * kBinsPerRow + 1;
-
-// Per-marker state kept in the workspace for one call.
-template <typename T>
-struct MarkerState {
-    uint64_t *anchor;  // [M] wrapped first stencil cell
-    T *wts;            // [M][12] per-axis weights (x 0..3, y 4..7, z 8..11)
-    T *A;              // [M][4] spread source of the current pass
-    double *Ud;        // [M][3] desired velocity
-};
-
-// Slot (spreading tile) records.
-struct Slots {
-    uint32_t *count;   // [ndense] candidates per dense slot
-    uint32_t *start;   // [ndense+1] exclusive scan of count
-    uint32_t *cursor;  // [ndense] fill cursors
-    uint32_t *flag_scan;  // [ndense+1] compact index of non-empty slots
-    uint32_t *dense_of;   // [ncompact_max] dense id of each compact slot
-    uint32_t *cand;    // [total candidates] marker ids, sorted per slot
-    uint16_t *bins;    // [ncompact_max][kBins] bin starts, relative (see kBins)
-    int4 *geo_lo;      // [ncompact_max] tile first cell (wrapped), w = level
-    int4 *geo_dim;     // [ncompact_max] tile dims, w = first candidate
-    int *geo_case;     // [ncompact_max] case of the tile
-};
-
-// ---------------------------------------------------------------------------
-// interpolation of one marker from precomputed weights
-// ---------------------------------------------------------------------------
-// Loads of data that other CTAs of the persistent kernel write between grid
-// barriers (COH) are ordinary weak loads: the barrier is a GPU-scope
-// release/acquire pattern, so by the PTX memory model every write before it
-// is visible to every load after it.  (The read-only path, ld.global.nc, is
-// not coherent with writes made during the kernel and is used only for data
-// that no kernel writes meanwhile.)  ld.global.cg forms are avoided here:
-// they were issued one at a time, serialising ~80 L2 round trips per marker.
-template <bool COH, typename T>
-__device__ __forceinline__ T ld(const T *p) {
-    if (COH) return *p;
-    return __ldg(p);
-}
-
-template <typename T, int KW, bool COH = false>
-__device__ __forceinline__ void interp_marker(const T *__restrict__ u, const DevGrid &g,
-                                              long long N, uint64_t anc,
-                                              const T *__restrict__ w, T out[3]) {
-    int ix[KW], iy[KW], iz[KW];
-    int ax = anchor_x(anc), ay = anchor_y(anc), az = anchor_z(anc);
-#pragma unroll
-    for (int k = 0; k < KW; ++k) {
-        ix[k] = wrap_add(ax, k, g.n[0]);
-        iy[k] = wrap_add(ay, k, g.n[1]);
-        iz[k] = wrap_add(az, k, g.n[2]);
-    }
-    T a0 = 0, a1 = 0, a2 = 0;
-#pragma unroll 1
-    for (int kz = 0; kz < KW; ++kz) {
-#pragma unroll
-        for (int ky = 0; ky < KW; ++ky) {
-            long long row = ((long long)iz[kz] * g.n[1] + iy[ky]) * g.n[0];
-            T wyz = w[8 + kz] * w[4 + ky];
-#pragma unroll
-            for (int kx = 0; kx < KW; ++kx) {
-                long long c = row + ix[kx];
-                T wt = wyz * w[kx];
-                a0 += wt * ld<COH>(u + c);
-                a1 += wt * ld<COH>(u + N + c);
-                a2 += wt * ld<COH>(u + 2 * N + c);
-            }
-        }
-    }
-    out[0] = a0;
-    out[1] = a1;
-    out[2] = a2;
-}
 
 template <typename T, int KER>
 __device__ __forceinline__ uint64_t marker_weights(const DevGrid &g, const double X[3],
@@ -283,7 +198,6 @@ struct LevelOut {
     int *nlev;        // [1]
 };
 
-constexpr int kMaxNbr = 48;
 
 // Conflict lists: for every p, the q < p whose stencils may share a cell
 // (count -1 = more than kMaxNbr, scanned again when levels are assigned).
@@ -817,47 +731,6 @@ struct LvlSmem {
     }
 };
 
-template <typename T, int KW, bool STAGED, bool COH>
-__device__ __forceinline__ bool gather_cell(int tx, int ty, int tz, const uint16_t *bins, const uint32_t *cand,
-                                            const T *w_src, const T *A_src, T acc[3]) {
-    bool hit = false;
-    acc[0] = acc[1] = acc[2] = T(0);
-#pragma unroll 1
-    for (int dz = 0; dz < KW; ++dz) {
-        const int rz = tz + 3 - (KW - 1) + dz, oz = KW - 1 - dz;
-#pragma unroll 1
-        for (int dy = 0; dy < KW; ++dy) {
-            const int ry = ty + 3 - (KW - 1) + dy, oy = KW - 1 - dy;
-            const uint16_t *rb = bins + (rz * kRow + ry) * kBinsPerRow + tx + 3 - (KW - 1);
-            int e[KW + 1];
-#pragma unroll
-            for (int dx = 0; dx <= KW; ++dx) e[dx] = rb[dx];
-#pragma unroll
-            for (int dx = 0; dx < KW; ++dx) {
-                const int ox = KW - 1 - dx;
-                for (int i = e[dx]; i < e[dx + 1]; ++i) {
-                    const size_t k = STAGED ? (size_t)i : (size_t)cand[i];
-                    const T *w = w_src + 12 * k;
-                    const T *A = A_src + 4 * k;
-                    T wt, a0, a1, a2;
-                    if (STAGED) {
-                        wt = w[ox] * w[4 + oy] * w[8 + oz];
-                        a0 = A[0], a1 = A[1], a2 = A[2];
-                    } else {
-                        wt = __ldg(w + ox) * __ldg(w + 4 + oy) * __ldg(w + 8 + oz);
-                        a0 = ld<COH>(A), a1 = ld<COH>(A + 1), a2 = ld<COH>(A + 2);
-                    }
-                    acc[0] += wt * a0;
-                    acc[1] += wt * a1;
-                    acc[2] += wt * a2;
-                    hit = true;
-                }
-            }
-        }
-    }
-    return hit;
-}
-
 // One tile (compact slot cs) of a gather phase into the tile's case: u += S A,
 // and, when the case has a force field (forcing pass), f += S A / dt.
 template <typename T, int KW, bool COH>
@@ -947,17 +820,11 @@ struct Barrier {
     unsigned int *gen;
 };
 
-__device__ __forceinline__ unsigned int ld_acquire(const unsigned int *p) {
-    unsigned int v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
 
 // Sense-free generation barrier over all CTAs of a cooperative launch.  The
 // waiting thread polls the generation word without sleeping (a sleep's wake-up
 // latency dominated the phases) and gives up after kSpinCycles SM cycles,
 // raising IB_ERR_TIMEOUT; every CTA then returns.
-constexpr long long kSpinCycles = 4LL * 1000 * 1000 * 1000;  // ~2 s at 2 GHz
 
 __device__ __forceinline__ bool grid_sync(Barrier b, DevStatus *st) {
     __syncthreads();
@@ -1367,6 +1234,7 @@ static int run_mdf(ib_ctx *ctx, Arena &ar, const CaseTab &ct, const ib_particles
     int *nbr = ar.take<int>((size_t)P * kMaxNbr);
     int *lev_sbeg = ar.take<int>(P + 1);
     int *mperm = ar.take<int>(M > 0 ? M : 1);
+    unsigned int *sched = ar.take<unsigned int>(P + 1);  // done counters + ticket
     Barrier bar;
     bar.count = ar.take<unsigned int>(2);
     bar.gen = bar.count + 1;
@@ -1394,6 +1262,37 @@ static int run_mdf(ib_ctx *ctx, Arena &ar, const CaseTab &ct, const ib_particles
     int *ncompact = nullptr;
     int rc = build_slots<KW>(ctx, ar, ct, M, (int)ndense, sg, ms.anchor, lo.level, sl, ncompact, s);
     if (rc) return rc;
+    if (order == IB_ORDER_SEQUENTIAL && ctx->pass_kernels != IB_PASSES_WAVEFRONT) {
+        // particle-resident passes: one cluster per particle, scheduled by rank
+        ResidentArgs<T> ra;
+        ra.ct = ct;
+        ra.F = F_out;
+        ra.dV = mk->dV;
+        ra.ms = ms;
+        ra.sl = sl;
+        ra.mperm = mperm;
+        ra.mbase = lo.mbase;
+        ra.moff = pp->marker_offset;
+        ra.by_rank = lev_work;  // k_levels leaves the particle of each rank there
+        ra.rank = lo.rank;
+        ra.level = lo.level;
+        ra.box_lo = box_lo;
+        ra.nbr_cnt = nbr_cnt;
+        ra.nbr = nbr;
+        ra.done = sched;
+        ra.ticket = sched + P;
+        ra.P = P;
+        ra.Ns = Ns;
+        ra.dt = dt;
+        ra.st = ctx->status;
+        cudaMemsetAsync(sched, 0, sizeof(unsigned int) * (P + 1), s);
+        tprep.stop();
+        PhaseTimer tpass(ctx, IB_PHASE_MDF_PASSES, s);
+        rc = launch_mdf_resident<T, KER>(ctx, ra, s);
+        if (rc) return rc;
+        tpass.stop();
+        return check_launch("ib_multidirect_forcing");
+    }
     k_level_slots<<<1, 256, 0, s>>>(sg.mode, lo.nlev, lo.lev_pbeg, sl.flag_scan, (int)ndense, lev_sbeg);
     cudaMemsetAsync(bar.count, 0, 2 * sizeof(unsigned int), s);
     tprep.stop();

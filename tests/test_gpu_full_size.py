@@ -2,9 +2,10 @@
 
 * The benchmark's workload (256^3 periodic grid, 64 spheres of D = 24 cells,
   115,840 markers, Ns = 5, sequential order) in FP64 and FP32 fields, through
-  each way the library can run the forcing passes: the first call on a context
-  (persistent kernel), a later call (per-wavefront kernels), and a CUDA-graph
-  replay of the later form -- the form bench.py times.
+  each way the library can run the forcing passes: the particle-resident
+  kernel eagerly and as a CUDA-graph replay (the form bench.py times), and
+  the wavefront form's first call on a context (persistent kernel), a later
+  call (per-wavefront kernels) and a CUDA-graph replay of the later call.
 * The dense 384^3 case (512 spheres of D = 16 at volume fraction 0.3, Ns = 3,
   FP32 fields) with active collisions, through a whole hot-path step.
 
@@ -63,38 +64,43 @@ def test_mdf_bench_workload_all_paths(api, cluster256, prec):
                                       prec)
     F = torch.zeros((case.M, 3), dtype=torch.float64, device="cuda")
     results = []
-    # 1) first call on the context: every wavefront in the persistent kernel
     u = u0.clone()
-    ctx.ib_multidirect_forcing(u, case.h, parts, marks, case.Ns, case.dt, F_out=F)
-    ctx.status()
-    results.append(("persistent", u.clone(), F.clone()))
-    # 2) later call: the wavefronts as separate kernels
-    u.copy_(u0)
-    ctx.ib_multidirect_forcing(u, case.h, parts, marks, case.Ns, case.dt, F_out=F)
-    ctx.status()
-    results.append(("wavefront kernels", u.clone(), F.clone()))
-    # 3) CUDA-graph replay of the later form
-    g = torch.cuda.CUDAGraph()
-    s = torch.cuda.Stream()
-    s.wait_stream(torch.cuda.current_stream())
-    with torch.cuda.stream(s):
+
+    def call(name):
         u.copy_(u0)
         ctx.ib_multidirect_forcing(u, case.h, parts, marks, case.Ns, case.dt, F_out=F)
-    torch.cuda.current_stream().wait_stream(s)
-    torch.cuda.synchronize()
-    with torch.cuda.graph(g):
-        ctx.ib_multidirect_forcing(u, case.h, parts, marks, case.Ns, case.dt, F_out=F)
-    u.copy_(u0)
-    g.replay()
-    torch.cuda.synchronize()
-    ctx.status()
-    results.append(("graph replay", u.clone(), F.clone()))
+        ctx.status()
+        results.append((name, u.clone(), F.clone()))
+
+    def graph_replay(name):
+        g = torch.cuda.CUDAGraph()
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            u.copy_(u0)
+            ctx.ib_multidirect_forcing(u, case.h, parts, marks, case.Ns, case.dt, F_out=F)
+        torch.cuda.current_stream().wait_stream(s)
+        torch.cuda.synchronize()
+        with torch.cuda.graph(g):
+            ctx.ib_multidirect_forcing(u, case.h, parts, marks, case.Ns, case.dt, F_out=F)
+        u.copy_(u0)
+        g.replay()
+        torch.cuda.synchronize()
+        ctx.status()
+        results.append((name, u.clone(), F.clone()))
+
+    call("resident")
+    graph_replay("resident, graph replay")
+    ctx.set_pass_kernels("wavefront")
+    call("persistent")          # first wavefront-form call: all wavefronts in the persistent kernel
+    call("wavefront kernels")   # later call: the wavefronts as separate kernels
+    graph_replay("wavefront kernels, graph replay")
     for name, ug, Fg in results:
         assert nerr(ug, un) <= TOL[prec], name
         assert nerr(Fg, Fo) <= TOL[prec], name
-    # all three paths agree bitwise
-    assert torch.equal(results[0][1], results[1][1]) and torch.equal(results[1][1], results[2][1])
-    assert torch.equal(results[0][2], results[1][2]) and torch.equal(results[1][2], results[2][2])
+    # every path agrees bitwise
+    for name, ug, Fg in results[1:]:
+        assert torch.equal(ug, results[0][1]) and torch.equal(Fg, results[0][2]), name
     ctx.close()
 
 
