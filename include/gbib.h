@@ -147,13 +147,13 @@ GBIB_API int ib_ctx_read_timing(ib_ctx *ctx, int phase, double *ms_total,
 
 /* ---- kernels of the sequential-order passes ----------------------------
  * Both forms compute bitwise the same result (same summation orders).
- * RESIDENT (the default, AUTO): one thread-block cluster per particle keeps
- *   the particle's band in shared memory for all Ns passes; particles start
- *   as soon as the earlier particles they conflict with are stored.
- * WAVEFRONT: per wavefront of non-conflicting particles and per pass, an
- *   interpolation kernel and a gather kernel through global memory (a
- *   persistent cooperative kernel takes the wavefronts beyond the count the
- *   previous call on the context saw).
+ * WAVEFRONT (the default, AUTO): per wavefront of non-conflicting particles
+ *   and per pass, an interpolation kernel and a gather kernel through global
+ *   memory (a persistent cooperative kernel takes the wavefronts beyond the
+ *   count the previous call on the context saw).
+ * RESIDENT: one thread-block cluster per particle keeps the particle's band
+ *   tiles in shared memory for all Ns passes; particles start as soon as the
+ *   earlier particles they conflict with are stored.
  * The simultaneous order always runs the wavefront form (one wavefront).
  * Returns IB_ERR_INVALID for any other value.                             */
 #define IB_PASSES_AUTO 0

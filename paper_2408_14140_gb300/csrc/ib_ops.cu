@@ -1262,7 +1262,7 @@ static int run_mdf(ib_ctx *ctx, Arena &ar, const CaseTab &ct, const ib_particles
     int *ncompact = nullptr;
     int rc = build_slots<KW>(ctx, ar, ct, M, (int)ndense, sg, ms.anchor, lo.level, sl, ncompact, s);
     if (rc) return rc;
-    if (order == IB_ORDER_SEQUENTIAL && ctx->pass_kernels != IB_PASSES_WAVEFRONT) {
+    if (order == IB_ORDER_SEQUENTIAL && ctx->pass_kernels == IB_PASSES_RESIDENT) {
         // particle-resident passes: one cluster per particle, scheduled by rank
         ResidentArgs<T> ra;
         ra.ct = ct;

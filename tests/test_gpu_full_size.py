@@ -3,9 +3,10 @@
 * The benchmark's workload (256^3 periodic grid, 64 spheres of D = 24 cells,
   115,840 markers, Ns = 5, sequential order) in FP64 and FP32 fields, through
   each way the library can run the forcing passes: the particle-resident
-  kernel eagerly and as a CUDA-graph replay (the form bench.py times), and
-  the wavefront form's first call on a context (persistent kernel), a later
-  call (per-wavefront kernels) and a CUDA-graph replay of the later call.
+  kernel eagerly and as a CUDA-graph replay, and the wavefront form's first
+  call on a context (persistent kernel), a later call (per-wavefront
+  kernels) and a CUDA-graph replay of the later call (the form bench.py
+  times).
 * The dense 384^3 case (512 spheres of D = 16 at volume fraction 0.3, Ns = 3,
   FP32 fields) with active collisions, through a whole hot-path step.
 
@@ -89,6 +90,7 @@ def test_mdf_bench_workload_all_paths(api, cluster256, prec):
         ctx.status()
         results.append((name, u.clone(), F.clone()))
 
+    ctx.set_pass_kernels("resident")
     call("resident")
     graph_replay("resident, graph replay")
     ctx.set_pass_kernels("wavefront")

@@ -1,7 +1,7 @@
 """The two forms of the sequential-order passes give bitwise the same result.
 
 The particle-resident kernel (one thread-block cluster per particle, band in
-shared memory; the default) and the wavefront kernels (per wavefront and
+shared memory) and the wavefront kernels (per wavefront and
 pass through global memory) sum every cell and marker in the same order, so
 u, F and f agree bit for bit; both stay within the oracle's gates.  Cases
 cover the resident fast path, the slow path of particles too large for the
@@ -77,7 +77,8 @@ def test_resident_equals_wavefront_and_oracle(api, name, prec, kernel):
     case = CASES[name]()
     u0 = torch.tensor(case.u, device="cuda", dtype=api.field_dtype(prec))
     ctx = api.Context()
-    res = [run(api, ctx, case, prec, kernel, u0) for _ in range(2)]  # default: resident
+    ctx.set_pass_kernels("resident")
+    res = [run(api, ctx, case, prec, kernel, u0) for _ in range(2)]
     ctx.set_pass_kernels("wavefront")
     wav = [run(api, ctx, case, prec, kernel, u0) for _ in range(2)]  # persistent, then per wavefront
     ctx.set_pass_kernels("resident")
