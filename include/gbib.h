@@ -216,9 +216,10 @@ GBIB_API int particle_volume_integrals(ib_ctx *ctx, const ib_grid *grid, const v
  * different cases never interact.  Each batch entry point computes, for every
  * case, exactly what the single-case entry point of the same name computes
  * (bitwise: the same kernels and summation orders).
- * The case table is copied to the workspace from pageable host memory on
- * `stream`, so batch calls cannot be captured into a CUDA graph (single-case
- * calls can).  Errors as for the single-case entry points, plus
+ * The case table is copied to the workspace through a small ring of pinned
+ * host buffers owned by the context (asynchronous on `stream`; a buffer is
+ * reused once the copy that read it has run), so batch calls must not be
+ * captured into a CUDA graph (single-case calls can).  Errors as for the single-case entry points, plus
  * IB_ERR_INVALID for ranges that do not partition [0, P) or mixed precisions
  * (the message names the case).                                            */
 typedef struct {
@@ -239,7 +240,9 @@ GBIB_API int ib_batch_multidirect_forcing(ib_ctx *ctx, int ncases, const ib_case
 GBIB_API int ib_batch_volume_integrals(ib_ctx *ctx, int ncases, const ib_case *cases,
                                        const ib_particles *parts, double *Iu,
                                        double *Irxu, double *vol, void *stream);
-/* Collision (pairs within a case, the case's periodic box) + Newton-Euler. */
+/* Collision (pairs within a case, the case's periodic box) + Newton-Euler.
+ * phys[ncases]: the physical parameters of each case (the contact distance
+ * d_c is usually the case's own h).                                       */
 GBIB_API int ib_batch_collide_update(ib_ctx *ctx, int ncases, const ib_case *cases,
                                      ib_particles *parts, const ib_phys *phys,
                                      double dt, const double *F_ib,

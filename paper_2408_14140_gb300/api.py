@@ -186,12 +186,18 @@ class Context:
             raise IBError(rc, self.lib.ib_last_error().decode())
 
     def _call(self, fn, *args):
+        """Call an entry point; on IB_ERR_OOM grow the workspace to what the
+        call reported and retry (a call can stop at an earlier allocation, so
+        the need may grow over a few retries)."""
         rc = fn(*args)
-        if rc == IB_ERR_OOM:
+        for _ in range(4):
+            if rc != IB_ERR_OOM:
+                break
             need = self.lib.ib_workspace_needed()
-            if need:
-                self._check(self.lib.ib_ctx_reserve(self.handle, int(need * 5 // 4) + (1 << 20)))
-                rc = fn(*args)
+            if not need:
+                break
+            self._check(self.lib.ib_ctx_reserve(self.handle, int(need * 5 // 4) + (1 << 20)))
+            rc = fn(*args)
         self._check(rc)
 
     @property
@@ -408,7 +414,8 @@ class Context:
                                 Iu_old, Irxu_new, Irxu_old, Fc_out=None, origins=None, stream=None):
         """Collision within each case + Newton-Euler, in place on the flat set.
 
-        ``shapes[c]`` = (n0, n1, n2) of case c's periodic box.
+        ``shapes[c]`` = (n0, n1, n2) of case c's periodic box; ``phys`` is one
+        (rho_f, gx, gy, gz, g_coll, eps_c, d_c) per case, or one for all.
         """
         cases = case_array(None, hs, ranges, origins, shapes=shapes)
         ps = self.particles_struct(parts["Xr"], parts["Ur"], parts["Wr"], parts["radius"],
@@ -419,9 +426,11 @@ class Context:
             _need(t, nm, torch.float64, (P, 3))
         if Fc_out is not None:
             _need(Fc_out, "Fc_out", torch.float64, (P, 3))
-        ph = _phys_struct(phys)
+        per_case = phys if len(phys) == len(cases) and not isinstance(phys[0], (int, float)) else \
+            [phys] * len(cases)
+        ph = (Phys * len(cases))(*[_phys_struct(x) for x in per_case])
         self._call(self.lib.ib_batch_collide_update, self.handle, len(cases), cases, ctypes.byref(ps),
-                   ctypes.byref(ph), float(dt), _ptr(F_ib), _ptr(T_ib), _ptr(Iu_new), _ptr(Iu_old),
+                   ph, float(dt), _ptr(F_ib), _ptr(T_ib), _ptr(Iu_new), _ptr(Iu_old),
                    _ptr(Irxu_new), _ptr(Irxu_old), _ptr(Fc_out), _stream(stream))
         return Fc_out
 

@@ -69,6 +69,7 @@ DevCase make_dev_case(const ib_grid *g, void *u, void *f, int p0, int p1) {
     c.p1 = p1;
     for (int a = 0; a < 3; ++a) c.tiles[a] = (g->n[a] + kTile - 1) / kTile;
     c.tile_off = 0;
+    c.phys = ib_phys{};
     return c;
 }
 
@@ -88,7 +89,7 @@ __global__ void k_case_of_particle(const DevCase *cases, int ncases, int *pcase)
 }
 
 int build_case_table(ib_ctx *ctx, Arena &ar, int ncases, const ib_case *cases, int P, int need_prec,
-                     CaseTab &ct, cudaStream_t s) {
+                     CaseTab &ct, cudaStream_t s, const ib_phys *phys) {
     if (ncases < 1 || !cases) return set_error(IB_ERR_INVALID, "batch needs ncases >= 1 and a case array");
     int prec = cases[0].grid.prec;
     std::vector<DevCase> h(ncases);
@@ -101,6 +102,7 @@ int build_case_table(ib_ctx *ctx, Arena &ar, int ncases, const ib_case *cases, i
         if (cases[c].p_begin != expect || cases[c].p_end < cases[c].p_begin)
             return set_error(IB_ERR_INVALID, "case %d: particle ranges must partition [0, P) in order", c);
         h[c] = make_dev_case(&cases[c].grid, cases[c].u, cases[c].f_out, cases[c].p_begin, cases[c].p_end);
+        if (phys) h[c].phys = phys[c];
         h[c].tile_off = (unsigned int)toff;
         toff += (unsigned long long)h[c].tiles[0] * h[c].tiles[1] * h[c].tiles[2];
         if (toff > (1ull << 30)) return set_error(IB_ERR_UNSUPPORTED, "batch has too many grid tiles");
@@ -109,8 +111,25 @@ int build_case_table(ib_ctx *ctx, Arena &ar, int ncases, const ib_case *cases, i
     DevCase *d = ar.take<DevCase>(ncases);
     int *pcase = ar.take<int>(P > 0 ? P : 1);
     if (!ar.ok()) return oom_error(ar.used, ar.cap);
-    if (cudaMemcpyAsync(d, h.data(), sizeof(DevCase) * ncases, cudaMemcpyHostToDevice, s) != cudaSuccess)
+    // stage through a pinned slot so that the upload stays asynchronous
+    const size_t bytes = sizeof(DevCase) * ncases;
+    const int k = ctx->stage_next;
+    ctx->stage_next = (k + 1) % ib_ctx::kStageSlots;
+    if (ctx->stage_ev[k]) cudaEventSynchronize(ctx->stage_ev[k]);
+    else if (cudaEventCreateWithFlags(&ctx->stage_ev[k], cudaEventDisableTiming) != cudaSuccess)
+        return set_error(IB_ERR_CUDA, "case table event: %s", cudaGetErrorString(cudaGetLastError()));
+    if (ctx->stage_cap[k] < bytes) {
+        if (ctx->stage_ptr[k]) cudaFreeHost(ctx->stage_ptr[k]);
+        ctx->stage_ptr[k] = nullptr;
+        ctx->stage_cap[k] = 0;
+        if (cudaHostAlloc(&ctx->stage_ptr[k], bytes, cudaHostAllocDefault) != cudaSuccess)
+            return set_error(IB_ERR_CUDA, "case table staging: %s", cudaGetErrorString(cudaGetLastError()));
+        ctx->stage_cap[k] = bytes;
+    }
+    memcpy(ctx->stage_ptr[k], h.data(), bytes);
+    if (cudaMemcpyAsync(d, ctx->stage_ptr[k], bytes, cudaMemcpyHostToDevice, s) != cudaSuccess)
         return set_error(IB_ERR_CUDA, "case table upload: %s", cudaGetErrorString(cudaGetLastError()));
+    cudaEventRecord(ctx->stage_ev[k], s);
     k_case_of_particle<<<ncases < 1024 ? ncases : 1024, 128, 0, s>>>(d, ncases, pcase);
     ct.arr = d;
     ct.pcase = pcase;
@@ -298,6 +317,12 @@ int ib_ctx_create(ib_ctx **ctx, size_t workspace_bytes) {
     }
     *c->h_nlev = 0;
     c->pass_kernels = IB_PASSES_AUTO;
+    for (int k = 0; k < ib_ctx::kStageSlots; ++k) {
+        c->stage_ptr[k] = nullptr;
+        c->stage_cap[k] = 0;
+        c->stage_ev[k] = nullptr;
+    }
+    c->stage_next = 0;
     *ctx = c;
     return IB_OK;
 }
@@ -363,6 +388,10 @@ int ib_ctx_destroy(ib_ctx *c) {
         }
     for (auto e : c->pool) cudaEventDestroy(e);
     cudaFreeHost(c->h_nlev);
+    for (int k = 0; k < ib_ctx::kStageSlots; ++k) {
+        if (c->stage_ptr[k]) cudaFreeHost(c->stage_ptr[k]);
+        if (c->stage_ev[k]) cudaEventDestroy(c->stage_ev[k]);
+    }
     cudaFree(c->ws);
     cudaFree(c->status);
     delete c;

@@ -36,6 +36,7 @@ struct DevCase {
     int p0, p1;             // particles [p0, p1)
     int tiles[3];           // 8^3 grid tiles per axis (global-tile binning)
     unsigned int tile_off;  // first global-tile slot of the case
+    ib_phys phys;           // physical parameters (collision update only)
 };
 
 // Case table of a call: a device array of cases, or one case passed by value
@@ -149,6 +150,13 @@ struct ib_ctx {
     int *h_nlev;         // pinned host word
     int nlev_hint;
     int pass_kernels;    // IB_PASSES_* of the sequential order
+    // pinned staging ring for the case tables of batch calls: a slot is
+    // reused only after the copy that last read it has run (its event)
+    static constexpr int kStageSlots = 4;
+    void *stage_ptr[kStageSlots];
+    size_t stage_cap[kStageSlots];
+    cudaEvent_t stage_ev[kStageSlots];
+    int stage_next;
 };
 
 namespace gbib {
@@ -184,7 +192,7 @@ CaseTab single_case(const ib_grid *g, void *u, void *f, int P);
 // (a pageable copy: not capturable into a CUDA graph).  Returns an error status
 // when the cases are invalid or the workspace is short.
 int build_case_table(ib_ctx *ctx, struct Arena &ar, int ncases, const ib_case *cases, int P, int need_prec,
-                     CaseTab &ct, cudaStream_t s);
+                     CaseTab &ct, cudaStream_t s, const ib_phys *phys = nullptr);
 
 // Records a CUDA event pair around a scope when the context times phases.
 struct PhaseTimer {

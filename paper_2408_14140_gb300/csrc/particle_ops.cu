@@ -399,7 +399,7 @@ struct CollideArgs {
     CaseTab ct;  // pairs are taken within a case, in the case's periodic box
     double *Xr, *Ur, *Wr;
     const double *radius, *rho_p;
-    double rho_f, g[3], g_coll, eps_c, d_c, dt;
+    double dt;
     const double *Fib, *Tib, *Iu_new, *Iu_old, *Ir_new, *Ir_old;
     double *Fc_out;
     double *Xnew;  // [P][3] scratch: positions are read by every thread
@@ -412,13 +412,14 @@ __global__ void k_collide_forces(CollideArgs a, double *__restrict__ Fc) {
     const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (i >= a.P) return;
     const DevCase &cd = a.ct.of_particle(i);
+    const ib_phys &ph = cd.phys;
     const double L[3] = {cd.g.n[0] * cd.g.h, cd.g.n[1] * cd.g.h, cd.g.n[2] * cd.g.h};
     const double iL[3] = {1.0 / L[0], 1.0 / L[1], 1.0 / L[2]};
     const double xi[3] = {a.Xr[3 * i], a.Xr[3 * i + 1], a.Xr[3 * i + 2]};
     const double Ri = a.radius[i];
     const double mi = a.rho_p[i] * 4.0 / 3.0 * kPi * Ri * Ri * Ri;
-    const double idc = 1.0 / a.d_c;
-    const double gscale = 0.5 * a.g_coll / a.eps_c;
+    const double idc = 1.0 / ph.d_c;
+    const double gscale = 0.5 * ph.g_coll / ph.eps_c;
     double f[3] = {0, 0, 0};
     for (int j = cd.p0 + lane; j < cd.p1; j += 32) {
         if (j == i) continue;
@@ -430,7 +431,7 @@ __global__ void k_collide_forces(CollideArgs a, double *__restrict__ Fc) {
             d2 += del[k] * del[k];
         }
         const double Rj = a.radius[j];
-        const double Dc = Ri + Rj + a.d_c;
+        const double Dc = Ri + Rj + ph.d_c;
         if (d2 < Dc * Dc && d2 > 0.0) {
             const double d = sqrt(d2);
             const double mj = a.rho_p[j] * 4.0 / 3.0 * kPi * Rj * Rj * Rj;
@@ -450,6 +451,8 @@ __global__ void k_collide_forces(CollideArgs a, double *__restrict__ Fc) {
 __global__ void k_newton_euler(CollideArgs a, const double *__restrict__ Fc, DevStatus *st) {
     int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= a.P) return;
+    const DevCase &cd = a.ct.of_particle(p);
+    const ib_phys &ph = cd.phys;
     double Rp = a.radius[p];
     double V = 4.0 / 3.0 * kPi * Rp * Rp * Rp;
     double m = a.rho_p[p] * V;
@@ -457,10 +460,10 @@ __global__ void k_newton_euler(CollideArgs a, const double *__restrict__ Fc, Dev
     bool ok = true;
     for (int k = 0; k < 3; ++k) {
         double Un = a.Ur[3 * p + k];
-        double rhs = a.Fib[3 * p + k] + a.rho_f * (a.Iu_new[3 * p + k] - a.Iu_old[3 * p + k]) / a.dt +
-                     (a.rho_p[p] - a.rho_f) * V * a.g[k] + Fc[3 * p + k];
+        double rhs = a.Fib[3 * p + k] + ph.rho_f * (a.Iu_new[3 * p + k] - a.Iu_old[3 * p + k]) / a.dt +
+                     (a.rho_p[p] - ph.rho_f) * V * ph.g[k] + Fc[3 * p + k];
         double Unew = Un + a.dt / m * rhs;
-        double trq = a.Tib[3 * p + k] + a.rho_f * (a.Ir_new[3 * p + k] - a.Ir_old[3 * p + k]) / a.dt;
+        double trq = a.Tib[3 * p + k] + ph.rho_f * (a.Ir_new[3 * p + k] - a.Ir_old[3 * p + k]) / a.dt;
         double Wnew = a.Wr[3 * p + k] + a.dt / I * trq;
         double Xnew = a.Xr[3 * p + k] + 0.5 * a.dt * (Unew + Un);
         ok = ok && isfinite(Unew) && isfinite(Wnew) && isfinite(Xnew);
@@ -628,7 +631,7 @@ static int check_collide_args(ib_ctx *ctx, const ib_particles *parts, const ib_p
     return IB_OK;
 }
 
-static int run_collide(ib_ctx *ctx, Arena &ar, const CaseTab &ct, ib_particles *parts, const ib_phys *phys,
+static int run_collide(ib_ctx *ctx, Arena &ar, const CaseTab &ct, ib_particles *parts,
                        double dt, const double *F_ib, const double *T_ib, const double *Iu_new,
                        const double *Iu_old, const double *Irxu_new, const double *Irxu_old, double *Fc_out,
                        cudaStream_t s) {
@@ -643,11 +646,6 @@ static int run_collide(ib_ctx *ctx, Arena &ar, const CaseTab &ct, ib_particles *
     a.Wr = parts->Wr;
     a.radius = parts->radius;
     a.rho_p = parts->rho_p;
-    for (int k = 0; k < 3; ++k) a.g[k] = phys->g[k];
-    a.rho_f = phys->rho_f;
-    a.g_coll = phys->g_coll;
-    a.eps_c = phys->eps_c;
-    a.d_c = phys->d_c;
     a.dt = dt;
     a.Fib = F_ib;
     a.Tib = T_ib;
@@ -672,9 +670,10 @@ int particle_collide_update(ib_ctx *ctx, ib_particles *parts, const ib_grid *gri
     if (rc) return rc == 1 ? IB_OK : rc;
     rc = validate_grid(grid, 0);
     if (rc) return rc;
-    const CaseTab ct = single_case(grid, nullptr, nullptr, parts->P);
+    CaseTab ct = single_case(grid, nullptr, nullptr, parts->P);
+    ct.one.phys = *phys;
     Arena ar(ctx);
-    return run_collide(ctx, ar, ct, parts, phys, dt, F_ib, T_ib, Iu_new, Iu_old, Irxu_new, Irxu_old, Fc_out,
+    return run_collide(ctx, ar, ct, parts, dt, F_ib, T_ib, Iu_new, Iu_old, Irxu_new, Irxu_old, Fc_out,
                        (cudaStream_t)stream);
 }
 
@@ -686,9 +685,12 @@ int ib_batch_collide_update(ib_ctx *ctx, int ncases, const ib_case *cases, ib_pa
     if (rc) return rc == 1 ? IB_OK : rc;
     Arena ar(ctx);
     CaseTab ct;
-    rc = build_case_table(ctx, ar, ncases, cases, parts->P, 0, ct, (cudaStream_t)stream);
+    for (int c = 0; c < ncases && cases; ++c)
+        if (!(phys[c].eps_c > 0.0) || !(phys[c].d_c > 0.0))
+            return set_error(IB_ERR_INVALID, "case %d: eps_c and d_c must be > 0", c);
+    rc = build_case_table(ctx, ar, ncases, cases, parts->P, 0, ct, (cudaStream_t)stream, phys);
     if (rc) return rc;
-    return run_collide(ctx, ar, ct, parts, phys, dt, F_ib, T_ib, Iu_new, Iu_old, Irxu_new, Irxu_old, Fc_out,
+    return run_collide(ctx, ar, ct, parts, dt, F_ib, T_ib, Iu_new, Iu_old, Irxu_new, Irxu_old, Fc_out,
                        (cudaStream_t)stream);
 }
 

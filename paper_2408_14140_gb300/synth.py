@@ -302,7 +302,10 @@ def random_case(N: int, P: int, D_lo: float, D_hi: float, K: int, Ns: int,
                 min_gap_cells: float = 0.25, max_tries: int = 200) -> Case:
     """Polydisperse case: P spheres, D ~ U[D_lo, D_hi] cells, placed without
     overlap anywhere in the periodic box (redraw D, then the count, on
-    failure).  Used by the batched and served workloads."""
+    failure).  Used by the batched and served workloads.  ``field_kind``:
+    "fourier" (K modes, built on the host), "fourier-modes" (the same modes
+    drawn, kept in ``meta["modes"]`` for evaluation on the device, no host
+    field), "tgv" (Taylor-Green vortex) or "none"."""
     h = 1.0 / N
     for _ in range(max_tries):
         D = D_lo + (D_hi - D_lo) * rng.uniforms(P)
@@ -311,16 +314,12 @@ def random_case(N: int, P: int, D_lo: float, D_hi: float, K: int, Ns: int,
         cent = np.zeros((P, 3))
         ok = True
         for p in range(P):
+            lim = 0.5 * (D[p] + D[:p]) + min_gap_cells
             for _t in range(5000):
                 c = rng.uniforms(3) * N
-                good = True
-                for q in range(p):
-                    d = c - cent[q]
-                    d -= N * np.round(d / N)
-                    if np.sqrt(np.sum(d * d)) < 0.5 * (D[p] + D[q]) + min_gap_cells:
-                        good = False
-                        break
-                if good:
+                d = c - cent[:p]
+                d -= N * np.round(d / N)
+                if p == 0 or np.all(np.sqrt(np.sum(d * d, axis=1)) >= lim):
                     cent[p] = c
                     break
             else:
@@ -331,9 +330,47 @@ def random_case(N: int, P: int, D_lo: float, D_hi: float, K: int, Ns: int,
         P = max(1, P - 1)
     else:
         raise RuntimeError("random_case: placement failed")
+    meta = {"workload": "random", "N": N, "P": P}
+    u = None
     if field_kind == "tgv":
         u = taylor_green_field((N, N, N), 1.0, h)
-    else:
+    elif field_kind == "fourier":
         u = fourier_field((N, N, N), K, rng, h)
-    return _assemble((N, N, N), h, u, cent * h, 0.5 * D * h, rng, Ns, dt,
-                     meta={"workload": "random", "N": N, "P": P})
+    elif field_kind == "fourier-modes":
+        meta["modes"] = fourier_modes(K, rng)
+    elif field_kind != "none":
+        raise ValueError("field_kind: " + field_kind)
+    return _assemble((N, N, N), h, u, cent * h, 0.5 * D * h, rng, Ns, dt, meta=meta)
+
+
+def taylor_green_torch(n, U0: float = 1.0, h: float | None = None, device="cuda", dtype=None):
+    """:func:`taylor_green_field` evaluated with torch on ``device``."""
+    import torch
+    n = [int(v) for v in n]
+    if h is None:
+        h = 1.0 / n[0]
+    xs = [(torch.arange(n[a], device=device, dtype=torch.float64) + 0.5) * h for a in range(3)]
+    tp = 2.0 * math.pi
+    sx, cx = torch.sin(tp * xs[0]), torch.cos(tp * xs[0])
+    sy, cy = torch.sin(tp * xs[1]), torch.cos(tp * xs[1])
+    cz = torch.cos(tp * xs[2])
+    u = torch.zeros((3, n[2], n[1], n[0]), device=device, dtype=torch.float64)
+    u[0] = U0 * cz[:, None, None] * cy[None, :, None] * sx[None, None, :]
+    u[1] = -U0 * cz[:, None, None] * sy[None, :, None] * cx[None, None, :]
+    return u if dtype is None else u.to(dtype)
+
+
+def batched_cases(ncases: int = 256, seed: int = 0, grids=(32, 48, 64, 96, 128), P_max: int = 8,
+                  D_lo: float = 8.0, D_hi: float = 24.0, K: int = 8, Ns: int = 3,
+                  dt: float = 1e-3):
+    """Independent periodic cases of the batched workload: grids drawn
+    uniformly from ``grids`` (cubic), 1..P_max spheres each with D uniform in
+    [D_lo, D_hi] cells, K Fourier modes per case (kept in meta["modes"]; the
+    fields are evaluated on the device)."""
+    rng = SplitMix64(seed)
+    out = []
+    for _ in range(ncases):
+        N = int(grids[rng.randint(0, len(grids) - 1)])
+        P = rng.randint(1, P_max)
+        out.append(random_case(N, P, D_lo, D_hi, K, Ns, rng, dt, field_kind="fourier-modes"))
+    return out

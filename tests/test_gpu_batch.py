@@ -121,7 +121,9 @@ def test_batch_volume_and_collide_equal_each_case_alone(api, prec):
     Fib, Tib = (torch.randn((P, 3), generator=g, dtype=torch.float64).cuda() for _ in range(2))
     I0 = tuple(t.clone() for t in Ib[:2])
     I1 = tuple(t * 1.01 for t in Ib[:2])
-    phys = cases[0].phys()
+    # per-case physics: d_c is each case's own h (the particle-free case too)
+    phys = [c.phys() for c in cases]
+    phys.insert(2, cases[0].phys()[:6] + (1.0 / 40,))
     pb = {k: v.clone() for k, v in parts.items()}
     Fcb = torch.zeros((P, 3), dtype=torch.float64, device="cuda")
     ctx.ib_batch_collide_update(pb, shapes, hs, ranges, phys, cases[0].dt, Fib, Tib, I1[0], I0[0], I1[1],
@@ -135,7 +137,7 @@ def test_batch_volume_and_collide_equal_each_case_alone(api, prec):
             assert torch.equal(a, b[p0:p1])
         pa = {kk: v.clone() for kk, v in parts_l[k].items()}
         Fca = torch.zeros((p1 - p0, 3), dtype=torch.float64, device="cuda")
-        ctx.particle_collide_update(pa, c.n, c.h, phys, c.dt, Fib[p0:p1].contiguous(),
+        ctx.particle_collide_update(pa, c.n, c.h, c.phys(), c.dt, Fib[p0:p1].contiguous(),
                                     Tib[p0:p1].contiguous(), I1[0][p0:p1].contiguous(),
                                     I0[0][p0:p1].contiguous(), I1[1][p0:p1].contiguous(),
                                     I0[1][p0:p1].contiguous(), Fc_out=Fca)
