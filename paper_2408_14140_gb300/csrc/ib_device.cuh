@@ -51,6 +51,14 @@ struct Slots {
     int4 *geo_lo;      // [ncompact_max] tile first cell (wrapped), w = level
     int4 *geo_dim;     // [ncompact_max] tile dims, w = first candidate
     int *geo_case;     // [ncompact_max] case of the tile
+    // per-cell gather lists (built once per call, see k_tile_pairs): for
+    // tile cs with first candidate b, band[KW^3 b + q] = {cell | count << 16,
+    // first pair} for its q-th band cell (cells in index order), and
+    // pairs[KW^3 b + k] = candidate | ox << 16 | oy << 18 | oz << 20, each
+    // cell's pairs in ascending candidate order (the gather order).
+    int2 *band;
+    uint32_t *pairs;
+    int *nband;        // [ncompact_max] band cells of the tile
 };
 
 // ---------------------------------------------------------------------------

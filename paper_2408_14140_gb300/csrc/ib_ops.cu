@@ -668,6 +668,109 @@ __global__ void __launch_bounds__(kBlock) k_slot_sort(
 }
 
 // ---------------------------------------------------------------------------
+// per-cell gather lists.  One CTA of 8 warps per compact tile (grid-stride).
+// A cell's contributions are the candidates whose stencil covers it.  The
+// bin walk of gather_cell visits a tile's bins in ascending (anchor z, y, x)
+// order and a bin's candidates in index order -- in ascending candidate
+// index, the order the tile's candidates are sorted in -- so listing every
+// cell's candidates in ascending index reproduces its summation order.
+// Warp w owns cell plane z = w, each lane two cells of it; a warp walks, in
+// order, only the candidates whose anchor plane can reach its plane (a
+// contiguous range: candidates are sorted by anchor plane first), once to
+// count and once to fill.  No atomics: each cell has one owner.
+// ---------------------------------------------------------------------------
+constexpr int kPairThreads = 256;
+
+template <int KW>
+__global__ void __launch_bounds__(kPairThreads) k_tile_pairs(CaseTab ct, int ncompact_cap,
+                                                             const int *__restrict__ ncompact_p, Slots sl,
+                                                             const uint64_t *__restrict__ anchor) {
+    __shared__ unsigned int s_anc[kMaxCand];  // (x + 3) | (y + 3) << 4 | (z + 3) << 8 relative to the tile
+    __shared__ int s_wp[kPairThreads / 32], s_wb[kPairThreads / 32];
+    const int ncompact = min(*ncompact_p, ncompact_cap);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int cx = lane & 7, cy0 = lane >> 3, cy1 = cy0 + 4;  // this lane's cells (cx, cy0|cy1, warp)
+    for (int cs = blockIdx.x; cs < ncompact; cs += gridDim.x) {
+        const int4 lo = sl.geo_lo[cs], dim = sl.geo_dim[cs];
+        const DevGrid g = ct.get(sl.geo_case[cs]).g;
+        const int b = dim.w;
+        const int nc = min((int)sl.bins[(size_t)cs * kBins + kBins - 1], kMaxCand);
+        int2 *band = sl.band + (size_t)KW * KW * KW * b;
+        uint32_t *pairs = sl.pairs + (size_t)KW * KW * KW * b;
+        for (int i = tid; i < nc; i += blockDim.x) {
+            const uint64_t an = anchor[sl.cand[b + i]];
+            int d[3] = {anchor_x(an) - lo.x + 3, anchor_y(an) - lo.y + 3, anchor_z(an) - lo.z + 3};
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                if (d[q] < 0) d[q] += g.n[q];
+                if (d[q] >= g.n[q]) d[q] -= g.n[q];
+                d[q] = min(d[q], 15);  // a candidate's anchor lies within [-3, 8) of the tile
+            }
+            s_anc[i] = (unsigned)d[0] | ((unsigned)d[1] << 4) | ((unsigned)d[2] << 8);
+        }
+        __syncthreads();
+        // candidates whose anchor plane (z + 3 stored) lies in [warp + 4 - KW, warp + 3]
+        auto lower = [&](int key) {  // first candidate with stored z >= key
+            int a = 0, e = nc;
+            while (a < e) {
+                const int mid = (a + e) >> 1;
+                if ((int)(s_anc[mid] >> 8) < key) a = mid + 1;
+                else e = mid;
+            }
+            return a;
+        };
+        const bool live = warp < dim.z;
+        const int i0 = live ? lower(warp + 4 - KW) : 0, i1 = live ? lower(warp + 4) : 0;
+        const bool in0 = live && cx < dim.x && cy0 < dim.y, in1 = live && cx < dim.x && cy1 < dim.y;
+        auto covers = [&](unsigned pk, int cy, int &o) {  // o = ox | oy << 2 | oz << 4
+            const int ox = cx - ((int)(pk & 15) - 3), oy = cy - ((int)((pk >> 4) & 15) - 3);
+            const int oz = warp - ((int)(pk >> 8) - 3);
+            o = ox | (oy << 2) | (oz << 4);
+            return (unsigned)ox < (unsigned)KW && (unsigned)oy < (unsigned)KW && (unsigned)oz < (unsigned)KW;
+        };
+        int n0 = 0, n1 = 0, o;
+        for (int i = i0; i < i1; ++i) {
+            const unsigned pk = s_anc[i];
+            n0 += in0 && covers(pk, cy0, o);
+            n1 += in1 && covers(pk, cy1, o);
+        }
+        // block scan of (pairs, band cells) in cell index order; cell index =
+        // (z * 8 + y) * 8 + x, so order by (warp, y, x): lanes 0..31 hold
+        // y = 0..3 (cell 0) and y = 4..7 (cell 1) -- scan cell 0 of all lanes,
+        // then cell 1 of all lanes
+        int p0 = n0, b0 = n0 > 0, p1 = n1, b1 = n1 > 0;
+        for (int o2 = 1; o2 < 32; o2 <<= 1) {
+            const int a0 = __shfl_up_sync(0xffffffffu, p0, o2), a1 = __shfl_up_sync(0xffffffffu, b0, o2);
+            const int a2 = __shfl_up_sync(0xffffffffu, p1, o2), a3 = __shfl_up_sync(0xffffffffu, b1, o2);
+            if (lane >= o2) p0 += a0, b0 += a1, p1 += a2, b1 += a3;
+        }
+        const int t0p = __shfl_sync(0xffffffffu, p0, 31), t0b = __shfl_sync(0xffffffffu, b0, 31);
+        const int t1p = __shfl_sync(0xffffffffu, p1, 31), t1b = __shfl_sync(0xffffffffu, b1, 31);
+        if (lane == 0) s_wp[warp] = t0p + t1p, s_wb[warp] = t0b + t1b;
+        __syncthreads();
+        int wp = 0, wb = 0;
+        for (int w = 0; w < warp; ++w) wp += s_wp[w], wb += s_wb[w];
+        const int e0p = wp + p0 - n0, e0b = wb + b0 - (n0 > 0);
+        const int e1p = wp + t0p + p1 - n1, e1b = wb + t0b + b1 - (n1 > 0);
+        if (n0 > 0) band[e0b] = make_int2(((warp * kTile + cy0) * kTile + cx) | (n0 << 16), e0p);
+        if (n1 > 0) band[e1b] = make_int2(((warp * kTile + cy1) * kTile + cx) | (n1 << 16), e1p);
+        if (tid == blockDim.x - 1) {
+            int tb = 0;
+            for (int w = 0; w < kPairThreads / 32; ++w) tb += s_wb[w];
+            sl.nband[cs] = tb;
+        }
+        // fill, in candidate order
+        int q0 = e0p, q1 = e1p;
+        for (int i = i0; i < i1; ++i) {
+            const unsigned pk = s_anc[i];
+            if (in0 && covers(pk, cy0, o)) pairs[q0++] = (uint32_t)i | ((uint32_t)o << 16);
+            if (in1 && covers(pk, cy1, o)) pairs[q1++] = (uint32_t)i | ((uint32_t)o << 16);
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
 // gather of one tile: every cell sums w * A over the markers whose stencil
 // covers it, rows in (z, y) order, markers in index order within a row.
 // The tile's candidates (their per-axis weights, spread source and x offset)
@@ -911,20 +1014,24 @@ template <> struct TileStage<double> { static constexpr int N = 192; };
 
 template <typename T>
 constexpr size_t tile_stage_bytes() {
-    return (size_t)TileStage<T>::N * 16 * sizeof(T) + 2 * (size_t)kBins;
+    return (size_t)TileStage<T>::N * 16 * sizeof(T);
 }
 
+// The wavefront gather, one CTA per tile (grid-stride), many CTAs per SM.
+// The tile's candidate weights and sources are staged in shared memory, and
+// each thread takes band cells of the tile and adds its cell's pairs in list
+// order (ascending candidate = the bin order of gather_cell, so the sums are
+// bitwise those of the bin walk).  Cells outside the band cost nothing.
 template <typename T, int KER>
 __global__ void __launch_bounds__(256, 5) k_gather_level(PassArgs<T> a, int L) {
     constexpr int KW = Kernel<KER>::W;
+    constexpr int KW3 = KW * KW * KW;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     if (L >= *a.nlev) return;
     T *sw = (T *)smem_raw;                          // [N][12]
     T *sA = sw + (size_t)TileStage<T>::N * 12;      // [N][4]
-    uint16_t *sb = (uint16_t *)(sA + (size_t)TileStage<T>::N * 4);
     const double inv_dt = 1.0 / a.dt;
     const int s0 = a.lev_sbeg[L], s1 = a.lev_sbeg[L + 1];
-    const int tx = threadIdx.x & 7, ty = (threadIdx.x >> 3) & 7, tz0 = threadIdx.x >> 6;
     for (int cs = s0 + blockIdx.x; cs < s1; cs += gridDim.x) {
         const DevCase &cd = a.ct.get(a.sl.geo_case[cs]);
         const DevGrid g = cd.g;
@@ -932,11 +1039,11 @@ __global__ void __launch_bounds__(256, 5) k_gather_level(PassArgs<T> a, int L) {
         T *const u = (T *)cd.u;
         T *const f_out = (T *)cd.f;
         const int4 lo = a.sl.geo_lo[cs], dim = a.sl.geo_dim[cs];
-        const uint16_t *bs = a.sl.bins + (size_t)cs * kBins;
-        for (int i = threadIdx.x; i < kBins; i += blockDim.x) sb[i] = bs[i];
-        __syncthreads();
-        const int nc = sb[kBins - 1];
+        const int nc = a.sl.bins[(size_t)cs * kBins + kBins - 1];
+        const int nb = a.sl.nband[cs];
         const uint32_t *cand = a.sl.cand + dim.w;
+        const int2 *band = a.sl.band + (size_t)KW3 * dim.w;
+        const uint32_t *pairs = a.sl.pairs + (size_t)KW3 * dim.w;
         const bool staged = nc <= TileStage<T>::N;
         if (staged) {
             for (int i = threadIdx.x; i < nc; i += blockDim.x) {
@@ -951,23 +1058,41 @@ __global__ void __launch_bounds__(256, 5) k_gather_level(PassArgs<T> a, int L) {
             }
             __syncthreads();
         }
-#pragma unroll
-        for (int half = 0; half < 2; ++half) {
-            const int tz = tz0 + 4 * half;
-            if (tx < dim.x && ty < dim.y && tz < dim.z) {
-                T acc[3];
-                const bool hit = staged ? gather_cell<T, KW, true, false>(tx, ty, tz, sb, cand, sw, sA, acc)
-                                        : gather_cell<T, KW, false, false>(tx, ty, tz, sb, cand, a.ms.wts,
-                                                                           a.ms.A, acc);
-                if (hit) {
-                    const long long c = ((long long)wrap_add(lo.z, tz, g.n[2]) * g.n[1] +
-                                         wrap_add(lo.y, ty, g.n[1])) * g.n[0] + wrap_add(lo.x, tx, g.n[0]);
-#pragma unroll
-                    for (int q = 0; q < 3; ++q) u[q * N + c] += acc[q];
-                    if (f_out)
-#pragma unroll
-                        for (int q = 0; q < 3; ++q) f_out[q * N + c] += (T)(acc[q] * inv_dt);
+        for (int q = threadIdx.x; q < nb; q += blockDim.x) {
+            const int2 e = band[q];
+            const int cell = e.x & 0xffff, cnt = e.x >> 16;
+            const uint32_t *pr = pairs + e.y;
+            T acc0 = 0, acc1 = 0, acc2 = 0;
+            for (int k = 0; k < cnt; ++k) {
+                const uint32_t pk = pr[k];
+                const int i = pk & 0xffff, ox = (pk >> 16) & 3, oy = (pk >> 18) & 3, oz = (pk >> 20) & 3;
+                T wt, a0, a1, a2;
+                if (staged) {
+                    const T *w = sw + 12 * i;
+                    const T *A = sA + 4 * i;
+                    wt = w[ox] * w[4 + oy] * w[8 + oz];
+                    a0 = A[0], a1 = A[1], a2 = A[2];
+                } else {
+                    const size_t m = cand[i];
+                    const T *w = a.ms.wts + 12 * m;
+                    const T *A = a.ms.A + 4 * m;
+                    wt = __ldg(w + ox) * __ldg(w + 4 + oy) * __ldg(w + 8 + oz);
+                    a0 = __ldg(A), a1 = __ldg(A + 1), a2 = __ldg(A + 2);
                 }
+                acc0 += wt * a0;
+                acc1 += wt * a1;
+                acc2 += wt * a2;
+            }
+            const int tx = cell & 7, ty = (cell >> 3) & 7, tz = cell >> 6;
+            const long long c = ((long long)wrap_add(lo.z, tz, g.n[2]) * g.n[1] +
+                                 wrap_add(lo.y, ty, g.n[1])) * g.n[0] + wrap_add(lo.x, tx, g.n[0]);
+            u[c] += acc0;
+            u[N + c] += acc1;
+            u[2 * N + c] += acc2;
+            if (f_out) {
+                f_out[c] += (T)(acc0 * inv_dt);
+                f_out[N + c] += (T)(acc1 * inv_dt);
+                f_out[2 * N + c] += (T)(acc2 * inv_dt);
             }
         }
         __syncthreads();
@@ -1137,7 +1262,7 @@ static bool take_markers(Arena &ar, int M, MarkerState<T> &ms) {
 template <int KW>
 static int build_slots(ib_ctx *ctx, Arena &ar, const CaseTab &ct, int M, int ndense, SlotGeom sg,
                        const uint64_t *anchor, const int *level, Slots &sl, int *&ncompact_dev,
-                       cudaStream_t s) {
+                       cudaStream_t s, bool with_pairs = false) {
     size_t cand_cap = (size_t)M * (sg.mode == 0 ? 27 : 8) + 1;
     int ncompact_cap = (int)((size_t)M * (sg.mode == 0 ? 27 : 8) < (size_t)ndense
                                  ? (size_t)M * (sg.mode == 0 ? 27 : 8)
@@ -1155,6 +1280,16 @@ static int build_slots(ib_ctx *ctx, Arena &ar, const CaseTab &ct, int M, int nde
     sl.geo_lo = ar.take<int4>(ncompact_cap);
     sl.geo_dim = ar.take<int4>(ncompact_cap);
     sl.geo_case = ar.take<int>(ncompact_cap);
+    constexpr int KW3 = KW * KW * KW;
+    if (with_pairs) {
+        sl.band = ar.take<int2>((size_t)KW3 * cand_cap);
+        sl.pairs = ar.take<uint32_t>((size_t)KW3 * cand_cap);
+        sl.nband = ar.take<int>(ncompact_cap);
+    } else {
+        sl.band = nullptr;
+        sl.pairs = nullptr;
+        sl.nband = nullptr;
+    }
     if (!ar.ok())
         return oom_error(ar.used, ar.cap);
     cudaMemsetAsync(sl.count, 0, sizeof(uint32_t) * ndense, s);
@@ -1171,6 +1306,8 @@ static int build_slots(ib_ctx *ctx, Arena &ar, const CaseTab &ct, int M, int nde
     k_slot_sort<<<ctx->sm_count * 4, kBlock, 0, s>>>(ct, sg.mode, ncompact_cap, ncompact_dev, sg,
                                                      sl.dense_of, sl.start, anchor, level, sl,
                                                      ctx->status);
+    if (with_pairs)
+        k_tile_pairs<KW><<<ctx->sm_count * 8, kPairThreads, 0, s>>>(ct, ncompact_cap, ncompact_dev, sl, anchor);
     return check_launch("build_slots");
 }
 
@@ -1260,7 +1397,7 @@ static int run_mdf(ib_ctx *ctx, Arena &ar, const CaseTab &ct, const ib_particles
     sg.box_dim = box_dim;
     Slots sl;
     int *ncompact = nullptr;
-    int rc = build_slots<KW>(ctx, ar, ct, M, (int)ndense, sg, ms.anchor, lo.level, sl, ncompact, s);
+    int rc = build_slots<KW>(ctx, ar, ct, M, (int)ndense, sg, ms.anchor, lo.level, sl, ncompact, s, true);
     if (rc) return rc;
     if (order == IB_ORDER_SEQUENTIAL && ctx->pass_kernels == IB_PASSES_RESIDENT) {
         // particle-resident passes: one cluster per particle, scheduled by rank
