@@ -674,29 +674,33 @@ __global__ void __launch_bounds__(kBlock) k_slot_sort(
 // order and a bin's candidates in index order -- in ascending candidate
 // index, the order the tile's candidates are sorted in -- so listing every
 // cell's candidates in ascending index reproduces its summation order.
-// Warp w owns cell plane z = w, each lane two cells of it; a warp walks, in
-// order, only the candidates whose anchor plane can reach its plane (a
-// contiguous range: candidates are sorted by anchor plane first), once to
-// count and once to fill.  No atomics: each cell has one owner.
+// The (candidate, stencil cell) pairs are enumerated candidate-major and
+// scattered by a stable counting sort on the cell: each warp counts its
+// contiguous segment of the enumeration, a scan over (cell, warp) gives every
+// warp its base in every cell's list, and each warp then places its pairs in
+// enumeration order (lanes with the same cell ranked by lane).
 // ---------------------------------------------------------------------------
 constexpr int kPairThreads = 256;
+constexpr int kPairWarps = kPairThreads / 32;
 
 template <int KW>
 __global__ void __launch_bounds__(kPairThreads) k_tile_pairs(CaseTab ct, int ncompact_cap,
                                                              const int *__restrict__ ncompact_p, Slots sl,
                                                              const uint64_t *__restrict__ anchor) {
-    __shared__ unsigned int s_anc[kMaxCand];  // (x + 3) | (y + 3) << 4 | (z + 3) << 8 relative to the tile
-    __shared__ int s_wp[kPairThreads / 32], s_wb[kPairThreads / 32];
+    constexpr int KW3 = KW * KW * KW;
+    __shared__ unsigned int s_anc[kMaxCand];                // (x + 3) | (y + 3) << 4 | (z + 3) << 8
+    __shared__ unsigned int s_cnt[kPairWarps][kTileCells];  // counts, then list cursors
+    __shared__ int s_wp[kPairWarps], s_wb[kPairWarps];
     const int ncompact = min(*ncompact_p, ncompact_cap);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int cx = lane & 7, cy0 = lane >> 3, cy1 = cy0 + 4;  // this lane's cells (cx, cy0|cy1, warp)
+    const unsigned lt_mask = (1u << lane) - 1u;
     for (int cs = blockIdx.x; cs < ncompact; cs += gridDim.x) {
         const int4 lo = sl.geo_lo[cs], dim = sl.geo_dim[cs];
         const DevGrid g = ct.get(sl.geo_case[cs]).g;
         const int b = dim.w;
         const int nc = min((int)sl.bins[(size_t)cs * kBins + kBins - 1], kMaxCand);
-        int2 *band = sl.band + (size_t)KW * KW * KW * b;
-        uint32_t *pairs = sl.pairs + (size_t)KW * KW * KW * b;
+        int2 *band = sl.band + (size_t)KW3 * b;
+        uint32_t *pairs = sl.pairs + (size_t)KW3 * b;
         for (int i = tid; i < nc; i += blockDim.x) {
             const uint64_t an = anchor[sl.cand[b + i]];
             int d[3] = {anchor_x(an) - lo.x + 3, anchor_y(an) - lo.y + 3, anchor_z(an) - lo.z + 3};
@@ -708,63 +712,71 @@ __global__ void __launch_bounds__(kPairThreads) k_tile_pairs(CaseTab ct, int nco
             }
             s_anc[i] = (unsigned)d[0] | ((unsigned)d[1] << 4) | ((unsigned)d[2] << 8);
         }
+        for (int c = tid; c < kPairWarps * kTileCells; c += blockDim.x) (&s_cnt[0][0])[c] = 0;
         __syncthreads();
-        // candidates whose anchor plane (z + 3 stored) lies in [warp + 4 - KW, warp + 3]
-        auto lower = [&](int key) {  // first candidate with stored z >= key
-            int a = 0, e = nc;
-            while (a < e) {
-                const int mid = (a + e) >> 1;
-                if ((int)(s_anc[mid] >> 8) < key) a = mid + 1;
-                else e = mid;
-            }
-            return a;
-        };
-        const bool live = warp < dim.z;
-        const int i0 = live ? lower(warp + 4 - KW) : 0, i1 = live ? lower(warp + 4) : 0;
-        const bool in0 = live && cx < dim.x && cy0 < dim.y, in1 = live && cx < dim.x && cy1 < dim.y;
-        auto covers = [&](unsigned pk, int cy, int &o) {  // o = ox | oy << 2 | oz << 4
-            const int ox = cx - ((int)(pk & 15) - 3), oy = cy - ((int)((pk >> 4) & 15) - 3);
-            const int oz = warp - ((int)(pk >> 8) - 3);
-            o = ox | (oy << 2) | (oz << 4);
-            return (unsigned)ox < (unsigned)KW && (unsigned)oy < (unsigned)KW && (unsigned)oz < (unsigned)KW;
-        };
-        int n0 = 0, n1 = 0, o;
-        for (int i = i0; i < i1; ++i) {
+        // pair e = i * KW3 + k: candidate i, stencil offset k; cell or -1
+        auto cell_of = [&](int e, unsigned &code) {
+            const int i = e / KW3, k = e - i * KW3;
+            const int ox = k % KW, oy = (k / KW) % KW, oz = k / (KW * KW);
             const unsigned pk = s_anc[i];
-            n0 += in0 && covers(pk, cy0, o);
-            n1 += in1 && covers(pk, cy1, o);
+            const int x = (int)(pk & 15) - 3 + ox, y = (int)((pk >> 4) & 15) - 3 + oy, z = (int)(pk >> 8) - 3 + oz;
+            code = (unsigned)i | ((unsigned)(ox | (oy << 2) | (oz << 4)) << 16);
+            return (x >= 0 && x < dim.x && y >= 0 && y < dim.y && z >= 0 && z < dim.z) ? (z * kTile + y) * kTile + x
+                                                                                      : -1;
+        };
+        const int ne = nc * KW3;
+        const int seg = (ne + kPairWarps - 1) / kPairWarps;
+        const int e0 = min(ne, warp * seg), e1 = min(ne, e0 + seg);
+        for (int e = e0 + lane; e < e1; e += 32) {
+            unsigned code;
+            const int c = cell_of(e, code);
+            if (c >= 0) atomicAdd(&s_cnt[warp][c], 1u);
         }
-        // block scan of (pairs, band cells) in cell index order; cell index =
-        // (z * 8 + y) * 8 + x, so order by (warp, y, x): lanes 0..31 hold
-        // y = 0..3 (cell 0) and y = 4..7 (cell 1) -- scan cell 0 of all lanes,
-        // then cell 1 of all lanes
-        int p0 = n0, b0 = n0 > 0, p1 = n1, b1 = n1 > 0;
-        for (int o2 = 1; o2 < 32; o2 <<= 1) {
-            const int a0 = __shfl_up_sync(0xffffffffu, p0, o2), a1 = __shfl_up_sync(0xffffffffu, b0, o2);
-            const int a2 = __shfl_up_sync(0xffffffffu, p1, o2), a3 = __shfl_up_sync(0xffffffffu, b1, o2);
-            if (lane >= o2) p0 += a0, b0 += a1, p1 += a2, b1 += a3;
+        __syncthreads();
+        // (cell, warp) scan: thread t owns cells 2t and 2t + 1
+        int tot[2], pre[2][kPairWarps];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            int acc = 0;
+#pragma unroll
+            for (int w = 0; w < kPairWarps; ++w) {
+                pre[h][w] = acc;
+                acc += (int)s_cnt[w][2 * tid + h];
+            }
+            tot[h] = acc;
         }
-        const int t0p = __shfl_sync(0xffffffffu, p0, 31), t0b = __shfl_sync(0xffffffffu, b0, 31);
-        const int t1p = __shfl_sync(0xffffffffu, p1, 31), t1b = __shfl_sync(0xffffffffu, b1, 31);
-        if (lane == 0) s_wp[warp] = t0p + t1p, s_wb[warp] = t0b + t1b;
+        int pv = tot[0] + tot[1], bv = (tot[0] > 0) + (tot[1] > 0);
+        for (int o = 1; o < 32; o <<= 1) {
+            const int yp = __shfl_up_sync(0xffffffffu, pv, o), yb = __shfl_up_sync(0xffffffffu, bv, o);
+            if (lane >= o) pv += yp, bv += yb;
+        }
+        if (lane == 31) s_wp[warp] = pv, s_wb[warp] = bv;
         __syncthreads();
         int wp = 0, wb = 0;
         for (int w = 0; w < warp; ++w) wp += s_wp[w], wb += s_wb[w];
-        const int e0p = wp + p0 - n0, e0b = wb + b0 - (n0 > 0);
-        const int e1p = wp + t0p + p1 - n1, e1b = wb + t0b + b1 - (n1 > 0);
-        if (n0 > 0) band[e0b] = make_int2(((warp * kTile + cy0) * kTile + cx) | (n0 << 16), e0p);
-        if (n1 > 0) band[e1b] = make_int2(((warp * kTile + cy1) * kTile + cx) | (n1 << 16), e1p);
-        if (tid == blockDim.x - 1) {
-            int tb = 0;
-            for (int w = 0; w < kPairThreads / 32; ++w) tb += s_wb[w];
-            sl.nband[cs] = tb;
-        }
-        // fill, in candidate order
-        int q0 = e0p, q1 = e1p;
-        for (int i = i0; i < i1; ++i) {
-            const unsigned pk = s_anc[i];
-            if (in0 && covers(pk, cy0, o)) pairs[q0++] = (uint32_t)i | ((uint32_t)o << 16);
-            if (in1 && covers(pk, cy1, o)) pairs[q1++] = (uint32_t)i | ((uint32_t)o << 16);
+        const int cp0 = wp + pv - (tot[0] + tot[1]), cb0 = wb + bv - ((tot[0] > 0) + (tot[1] > 0));
+        const int cbase[2] = {cp0, cp0 + tot[0]};
+        if (tot[0] > 0) band[cb0] = make_int2((2 * tid) | (tot[0] << 16), cbase[0]);
+        if (tot[1] > 0) band[cb0 + (tot[0] > 0)] = make_int2((2 * tid + 1) | (tot[1] << 16), cbase[1]);
+        if (tid == blockDim.x - 1) sl.nband[cs] = cb0 + (tot[0] > 0) + (tot[1] > 0);
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+#pragma unroll
+            for (int w = 0; w < kPairWarps; ++w) s_cnt[w][2 * tid + h] = (unsigned)(cbase[h] + pre[h][w]);
+        __syncthreads();
+        // stable placement of this warp's segment
+        for (int eb = e0; eb < e1; eb += 32) {
+            const int e = eb + lane;
+            unsigned code = 0;
+            const int c = e < e1 ? cell_of(e, code) : -1;
+            const unsigned peers = __match_any_sync(0xffffffffu, c);
+            if (c >= 0) {
+                const unsigned base = s_cnt[warp][c];
+                pairs[base + __popc(peers & lt_mask)] = code;
+            }
+            __syncwarp();
+            if (c >= 0 && (peers & lt_mask) == 0) s_cnt[warp][c] += __popc(peers);
+            __syncwarp();
         }
         __syncthreads();
     }
