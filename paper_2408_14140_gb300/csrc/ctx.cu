@@ -238,8 +238,10 @@ void PhaseTimer::stop() {
     ctx = nullptr;
 }
 
-// Small arrays: one CTA, each thread scans kScanItems consecutive elements.
-constexpr int kScanItems = 32;
+// Small arrays: one CTA, each thread scans kScanItems consecutive elements
+// (few, so that a warp's loads stay within a few cache lines; larger arrays
+// take the three-kernel path, whose loads are fully coalesced).
+constexpr int kScanItems = 4;
 
 __global__ void __launch_bounds__(kScanBlock) k_scan_single(const uint32_t *in, uint32_t *out, int n) {
     const int base = threadIdx.x * kScanItems;

@@ -234,12 +234,51 @@ __global__ void k_conflicts(CaseTab ct, int P, int KW, const double *__restrict_
     }
 }
 
-// Levels by one sequential sweep (level(p) needs only q < p), then the
-// counting sort of particles by level and the level-major marker offsets.
-// The conflict lists and levels are first copied into shared memory when
-// they fit (kLevSmemP particles), so the sweep's dependent reads are on-chip.
-constexpr int kLevSmemP = 1024;
-constexpr size_t kLevSmem = (size_t)kLevSmemP * (4 + 2 + 2 * kMaxNbr);
+// Levels by a sweep over each case's particles in index order (level(p)
+// needs only the q < p of its own case; cases are independent and swept in
+// parallel, one thread each), then a parallel counting sort of the particles
+// by level and the level-major marker offsets.  The sweep's dependent reads
+// stay on chip: levels in shared memory (up to kLevOnchipP particles) and the
+// conflict lists too when they fit (kLevNbrP).  The order of particles inside
+// a level is the order their atomic increments land in; it does not affect
+// any result (a level's particles have disjoint stencil supports).
+constexpr int kLevOnchipP = 8192;
+constexpr int kLevNbrP = 1024;
+constexpr size_t kLevSmem = (size_t)kLevOnchipP * 4 + (size_t)kLevNbrP * (2 + 2 * kMaxNbr);
+
+// Exclusive scan of f(0..n-1) by one CTA (chunks of blockDim.x), calling
+// out(i, prefix) for every i and returning the total (all threads).
+template <typename F, typename O>
+__device__ __forceinline__ int block_scan_chunked(int n, F f, O out) {
+    __shared__ int s_w[32];
+    __shared__ int s_carry;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (threadIdx.x == 0) s_carry = 0;
+    __syncthreads();
+    for (int base = 0; base < n; base += blockDim.x) {
+        const int i = base + threadIdx.x;
+        const int v = i < n ? f(i) : 0;
+        int x = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) s_w[warp] = x;
+        __syncthreads();
+        int wpre = 0;
+        for (int w = 0; w < warp; ++w) wpre += s_w[w];
+        const int carry = s_carry;
+        if (i < n) out(i, carry + wpre + x - v);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int t = 0;
+            for (int w = 0; w < nw; ++w) t += s_w[w];
+            s_carry = carry + t;
+        }
+        __syncthreads();
+    }
+    return s_carry;
+}
 
 __global__ void __launch_bounds__(1024) k_levels(CaseTab ct, int P, int order, int KW,
                                                  const double *__restrict__ Xr,
@@ -247,75 +286,96 @@ __global__ void __launch_bounds__(1024) k_levels(CaseTab ct, int P, int order, i
                                                  const int *__restrict__ moff,
                                                  const int *__restrict__ nbr_cnt,
                                                  const int *__restrict__ nbr, LevelOut lo,
-                                                 int *__restrict__ work) {
+                                                 int *__restrict__ by_rank, int *__restrict__ lev_cur) {
     extern __shared__ __align__(16) unsigned char lsm[];
-    const bool onchip = P <= kLevSmemP && order == IB_ORDER_SEQUENTIAL;
-    int *s_lev = (int *)lsm;
-    short *s_cnt = (short *)(s_lev + kLevSmemP);
-    unsigned short *s_nbr = (unsigned short *)(s_cnt + kLevSmemP);
-    if (onchip) {
+    __shared__ int s_nl;
+    const bool lev_on = P <= kLevOnchipP;
+    const bool nbr_on = P <= kLevNbrP && order == IB_ORDER_SEQUENTIAL;
+    int *lev = lev_on ? (int *)lsm : lo.level;
+    short *s_cnt = (short *)(lsm + (size_t)kLevOnchipP * 4);
+    unsigned short *s_nbr = (unsigned short *)(s_cnt + kLevNbrP);
+    if (threadIdx.x == 0) s_nl = 0;
+    for (int i = threadIdx.x; i <= P; i += blockDim.x) {
+        lo.lev_pbeg[i] = 0;
+        lev_cur[i] = 0;
+    }
+    if (nbr_on)
         for (int p = threadIdx.x; p < P; p += blockDim.x) {
             const int c = nbr_cnt[p];
             s_cnt[p] = (short)c;
             for (int k = 0; k < c; ++k) s_nbr[p * kMaxNbr + k] = (unsigned short)nbr[(size_t)p * kMaxNbr + k];
         }
-        __syncthreads();
-    }
-    if (threadIdx.x != 0) return;
-    int *lev = onchip ? s_lev : lo.level;
-    int nl = 0;
-    for (int p = 0; p < P; ++p) {
-        int best = 0;
-        if (order == IB_ORDER_SEQUENTIAL) {
-            const int c = onchip ? s_cnt[p] : nbr_cnt[p];
-            if (c >= 0) {
-                for (int k = 0; k < c; ++k)
-                    best = max(best, lev[onchip ? s_nbr[p * kMaxNbr + k] : nbr[(size_t)p * kMaxNbr + k]] + 1);
-            } else {
-                const DevCase &cd = ct.of_particle(p);
-                const DevGrid &g = cd.g;
-                const double L[3] = {g.n[0] * g.h, g.n[1] * g.h, g.n[2] * g.h};
-                const double iL[3] = {1.0 / L[0], 1.0 / L[1], 1.0 / L[2]};
-                const double halo = 1.7320508075688772 * KW * g.h;
-                for (int q = cd.p0; q < p; ++q) {
-                    float d2 = 0.0f;
-                    for (int a = 0; a < 3; ++a) {
-                        float d = (float)Xr[3 * q + a] - (float)Xr[3 * p + a];
-                        d -= (float)L[a] * rintf(d * (float)iL[a]);
-                        d2 += d * d;
+    __threadfence();  // the zeroed counters reach L2 before the atomics below
+    __syncthreads();
+    // ---- sweep, one thread per case
+    const int ncases = ct.arr ? ct.ncases : 1;
+    int mymax = 0;
+    for (int c = threadIdx.x; c < ncases; c += blockDim.x) {
+        const DevCase cd = ct.get(c);
+        for (int p = cd.p0; p < cd.p1; ++p) {
+            int best = 0;
+            if (order == IB_ORDER_SEQUENTIAL) {
+                const int cn = nbr_on ? s_cnt[p] : nbr_cnt[p];
+                if (cn >= 0) {
+                    for (int k = 0; k < cn; ++k)
+                        best = max(best, lev[nbr_on ? s_nbr[p * kMaxNbr + k] : nbr[(size_t)p * kMaxNbr + k]] + 1);
+                } else {
+                    const DevGrid &g = cd.g;
+                    const double L[3] = {g.n[0] * g.h, g.n[1] * g.h, g.n[2] * g.h};
+                    const double iL[3] = {1.0 / L[0], 1.0 / L[1], 1.0 / L[2]};
+                    const double halo = 1.7320508075688772 * KW * g.h;
+                    for (int q = cd.p0; q < p; ++q) {
+                        float d2 = 0.0f;
+                        for (int a = 0; a < 3; ++a) {
+                            float d = (float)Xr[3 * q + a] - (float)Xr[3 * p + a];
+                            d -= (float)L[a] * rintf(d * (float)iL[a]);
+                            d2 += d * d;
+                        }
+                        const float lim = (float)(rho[p] + rho[q] + halo + 0.0625 * g.h);
+                        if (d2 < lim * lim) best = max(best, lev[q] + 1);
                     }
-                    const float lim = (float)(rho[p] + rho[q] + halo + 0.0625 * g.h);
-                    if (d2 < lim * lim) best = max(best, lev[q] + 1);
                 }
             }
+            lev[p] = best;
+            mymax = max(mymax, best + 1);
         }
-        lev[p] = best;
-        nl = max(nl, best + 1);
     }
-    if (onchip)
-        for (int p = 0; p < P; ++p) lo.level[p] = lev[p];
-    *lo.nlev = nl;
-    int *cnt = work;  // [P+1]
-    for (int i = 0; i <= P; ++i) cnt[i] = 0;
-    for (int p = 0; p < P; ++p) cnt[lev[p]]++;
-    int acc = 0;
-    for (int l = 0; l < nl; ++l) {
-        lo.lev_pbeg[l] = acc;
-        acc += cnt[l];
+    atomicMax(&s_nl, mymax);
+    __syncthreads();
+    const int nl = s_nl;
+    // ---- counting sort by level
+    for (int p = threadIdx.x; p < P; p += blockDim.x) {
+        if (lev_on) lo.level[p] = lev[p];
+        atomicAdd(&lo.lev_pbeg[lev[p]], 1);
     }
-    lo.lev_pbeg[nl] = acc;
-    for (int l = 0; l < nl; ++l) cnt[l] = lo.lev_pbeg[l];
-    for (int p = 0; p < P; ++p) lo.rank[p] = cnt[lev[p]]++;
-    int *by_rank = cnt;
-    for (int p = 0; p < P; ++p) by_rank[lo.rank[p]] = p;
-    int l = 0, macc = 0;
-    for (int r = 0; r < P; ++r) {
-        const int p = by_rank[r];
-        while (l < nl && lo.lev_pbeg[l] <= r) lo.lev_mbeg[l++] = macc;
-        lo.mbase[p] = macc;
-        macc += moff[p + 1] - moff[p];
+    __syncthreads();
+    // counts -> exclusive offsets, in place (read through atomics: written by atomics above)
+    block_scan_chunked(nl, [&](int l) { return atomicAdd(&lo.lev_pbeg[l], 0); },
+                       [&](int l, int pre) { atomicExch(&lev_cur[l], pre); });
+    __syncthreads();
+    // (values shared through L2 are written and read with atomics throughout)
+    for (int l = threadIdx.x; l < nl; l += blockDim.x) atomicExch(&lo.lev_pbeg[l], atomicAdd(&lev_cur[l], 0));
+    if (threadIdx.x == 0) {
+        lo.lev_pbeg[nl] = P;
+        *lo.nlev = nl;
     }
-    while (l <= nl) lo.lev_mbeg[l++] = macc;
+    __syncthreads();
+    for (int p = threadIdx.x; p < P; p += blockDim.x) {
+        const int r = atomicAdd(&lev_cur[lev[p]], 1);
+        lo.rank[p] = r;
+        atomicExch(&by_rank[r], p);
+    }
+    __syncthreads();
+    // ---- level-major marker offsets: exclusive scan of marker counts by rank
+    const int M = block_scan_chunked(
+        P, [&](int r) { const int p = atomicAdd(&by_rank[r], 0); return moff[p + 1] - moff[p]; },
+        [&](int r, int pre) { atomicExch(&lo.mbase[atomicAdd(&by_rank[r], 0)], pre); });
+    __syncthreads();
+    for (int l = threadIdx.x; l < nl; l += blockDim.x) {
+        const int r = atomicAdd(&lo.lev_pbeg[l], 0);
+        lo.lev_mbeg[l] = atomicAdd(&lo.mbase[atomicAdd(&by_rank[r], 0)], 0);
+    }
+    if (threadIdx.x == 0) lo.lev_mbeg[nl] = M;
 }
 
 // ---------------------------------------------------------------------------
@@ -1378,7 +1438,8 @@ static int run_mdf(ib_ctx *ctx, Arena &ar, const CaseTab &ct, const ib_particles
     lo.lev_pbeg = ar.take<int>(P + 1);
     lo.lev_mbeg = ar.take<int>(P + 1);
     lo.nlev = ar.take<int>(1);
-    int *lev_work = ar.take<int>(P + 1);
+    int *lev_work = ar.take<int>(P + 1);  // the particle of each rank
+    int *lev_cur = ar.take<int>(P + 1);
     int *nbr_cnt = ar.take<int>(P);
     int *nbr = ar.take<int>((size_t)P * kMaxNbr);
     int *lev_sbeg = ar.take<int>(P + 1);
@@ -1400,7 +1461,8 @@ static int run_mdf(ib_ctx *ctx, Arena &ar, const CaseTab &ct, const ib_particles
     if (order == IB_ORDER_SEQUENTIAL)
         k_conflicts<<<grid_blocks(P, 128, ctx->sm_count), 128, 0, s>>>(ct, P, KW, pp->Xr, rho, nbr_cnt, nbr);
     cudaFuncSetAttribute(k_levels, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLevSmem);
-    k_levels<<<1, 1024, kLevSmem, s>>>(ct, P, order, KW, pp->Xr, rho, pp->marker_offset, nbr_cnt, nbr, lo, lev_work);
+    k_levels<<<1, 1024, kLevSmem, s>>>(ct, P, order, KW, pp->Xr, rho, pp->marker_offset, nbr_cnt, nbr, lo, lev_work,
+                                       lev_cur);
     k_marker_order<<<P < ctx->sm_count * 2 ? P : ctx->sm_count * 2, kBlock, 0, s>>>(P, pp->marker_offset, lo.mbase,
                                                                                     ms.anchor, mperm);
     sg.part_of = part_of;
