@@ -51,10 +51,32 @@ __device__ __forceinline__ void block_sum(double v[NV]) {
 // ---------------------------------------------------------------------------
 constexpr int kVolSplit = 8;
 constexpr int kVolThreads = 256;   // 8 warps
-constexpr int kVolMaxBox = 64;     // cells per axis of one particle's box (tabulated path)
+constexpr int kVolMaxBox = 40;     // cells per axis of one particle's box (tabulated path)
 constexpr int kVolAx = kVolMaxBox + 1;
-// two node planes + per-axis tables (node squares, cell offsets, cell squares)
-constexpr size_t kVolSmem = (2 * kVolAx * kVolAx + 9 * kVolAx) * sizeof(double);
+// two node planes of (max(-phi, 0), max(phi, 0)) pairs + per-axis tables
+// (node squares, cell offsets, cell squares) + per-row grid offsets
+constexpr size_t kVolSmem = 2 * kVolAx * kVolAx * sizeof(double2) + 9 * kVolAx * sizeof(double) +
+                            kVolAx * sizeof(long long);
+
+// |x| from x^2 to within a few units of FP64 rounding: an FP32 square root
+// refined by one Newton step in FP64 (s = s0 + (x2 - s0^2) / (2 s0), the
+// classical Heron/Newton iteration; the FP32 start has relative error below
+// 2^-22, so one step leaves an error below 2^-44 relative to the FP64 root).
+// Cheaper than a full FP64 square root on parts whose FP64 rate is low.
+__device__ __forceinline__ double norm_from_square(double x2) {
+    const float sf = sqrtf((float)x2);
+    if (!(sf > 0.0f)) return sqrt(x2);  // zero, or an FP32 under/overflow: exact path
+    const double s0 = (double)sf;
+    const double r = fma(-s0, s0, x2);
+    return fma(r, (double)(0.5f / sf), s0);
+}
+
+// 1/x to within a few units of FP64 rounding: an FP32 reciprocal refined by
+// one Newton step (r = r0 + r0 (1 - x r0)), for x in the FP32 normal range.
+__device__ __forceinline__ double recip_refined(double x) {
+    const double r0 = (double)(1.0f / (float)x);
+    return fma(r0, fma(-x, r0, 1.0), r0);
+}
 
 // Exclusive scan of cnt[0..n) into pre[0..n] by warp 0 (n may exceed 32).
 __device__ __forceinline__ void warp0_scan(const int *cnt, int *pre, int n) {
@@ -101,7 +123,7 @@ __global__ void __launch_bounds__(kVolThreads) k_volume(CaseTab ct, int P,
                                                         double *__restrict__ partial,
                                                         unsigned int *__restrict__ done, double *Iu,
                                                         double *Irxu, double *vol, DevStatus *st) {
-    extern __shared__ double s_vol[];
+    extern __shared__ __align__(16) double s_vol[];
     __shared__ int s_last;
     // per-row work lists (rows <= kVolAx)
     __shared__ int r_na[kVolAx], r_nb[kVolAx], r_nc[2][kVolAx], r_ca[kVolAx], r_cb[kVolAx];
@@ -142,8 +164,9 @@ __global__ void __launch_bounds__(kVolThreads) k_volume(CaseTab ct, int P,
         const bool tab = dims[0] <= kVolMaxBox && dims[1] <= kVolMaxBox && dims[2] <= kVolMaxBox;
         if (tab) {
             const int nx = dims[0] + 1, plane = nx * (dims[1] + 1);
-            double *phi2 = s_vol;
-            double *tb = s_vol + 2 * kVolAx * kVolAx;
+            double2 *phi2 = (double2 *)s_vol;  // node planes: (max(-phi, 0), max(phi, 0))
+            double *tb = (double *)(phi2 + 2 * kVolAx * kVolAx);
+            long long *row_off = (long long *)(tb + 9 * kVolAx);
             for (int a = 0; a < 3; ++a)
                 for (int i = threadIdx.x; i <= dims[a]; i += blockDim.x) {
                     const double xn = g.org[a] + (double)(lo[a] + i) * h - c[a];
@@ -152,6 +175,8 @@ __global__ void __launch_bounds__(kVolThreads) k_volume(CaseTab ct, int P,
                     tb[(3 + a) * kVolAx + i] = xc;
                     tb[(6 + a) * kVolAx + i] = xc * xc;
                 }
+            for (int j = threadIdx.x; j < dims[1]; j += blockDim.x)
+                row_off[j] = (long long)wrap_int(lo[1] + j, g.n[1]) * g.n[0];
             __syncthreads();
             const float fih = (float)g.inv_h;
             // index range [first, last] of positions x_i = base + i h (i in [0, n)) with
@@ -160,7 +185,7 @@ __global__ void __launch_bounds__(kVolThreads) k_volume(CaseTab ct, int P,
                 first = max(0, (int)floorf((float)(-w - base) * fih) - 1);
                 last = min(n - 1, (int)ceilf((float)(w - base) * fih) + 1);
             };
-            auto node_plane = [&](int kn, double *buf) {
+            auto node_plane = [&](int kn, double2 *buf) {
                 const double zz = tb[2 * kVolAx + kn];
                 const int rows = dims[1] + 1;
                 const double xb = g.org[0] + (double)lo[0] * h - c[0];  // x of node 0
@@ -201,11 +226,18 @@ __global__ void __launch_bounds__(kVolThreads) k_volume(CaseTab ct, int P,
                     const int j = find_row(p_node, rows, q);
                     const int k = q - p_node[j];
                     const int i = k < r_nc[0][j] ? r_na[j] + k : r_nb[j] + (k - r_nc[0][j]);
-                    const double d2 = tb[i] + tb[kVolAx + j] + zz;
-                    if (d2 >= sl2 && d2 < sh2) buf[j * nx + i] = sqrt(d2) * iR - 1.0;
+                    // every listed node gets its level set value (nodes slightly
+                    // outside the shell too: the values stay exact)
+                    const double ph = fma(norm_from_square(tb[i] + tb[kVolAx + j] + zz), iR, -1.0);
+                    buf[j * nx + i] = make_double2(fmax(-ph, 0.0), fmax(ph, 0.0));
                 }
             };
             node_plane(z0, phi2 + (z0 & 1) * plane);
+            // per-thread sums.  r x u is split so that rz (constant over a cell
+            // plane) multiplies plane sums once per plane:
+            //   (ry w2 - rz w1, rz w0 - rx w2, rx w1 - ry w0), w = alpha u
+            double sA = 0, sB = 0, sC = 0, sD = 0, svol = 0;
+            long long nint_cells = 0;
             for (int kz = z0; kz < z1; ++kz) {
                 node_plane(kz + 1, phi2 + ((kz + 1) & 1) * plane);
                 // cell rows of plane kz: interior range and the boundary ranges around it
@@ -238,59 +270,72 @@ __global__ void __launch_bounds__(kVolThreads) k_volume(CaseTab ct, int P,
                 warp0_scan(c_int, p_int, dims[1]);
                 warp0_scan(c_bnd, p_bnd, dims[1]);
                 __syncthreads();
-                const double *b0 = phi2 + (kz & 1) * plane, *b1 = phi2 + ((kz + 1) & 1) * plane;
-                const long long plane_off = (long long)wrap_int(lo[2] + kz, g.n[2]) * g.n[1];
+                const double2 *b0 = phi2 + (kz & 1) * plane, *b1 = phi2 + ((kz + 1) & 1) * plane;
+                const long long plane_off = (long long)wrap_int(lo[2] + kz, g.n[2]) * g.n[1] * g.n[0];
+                double s0 = 0, s1 = 0, s2 = 0;  // plane sums of alpha u
                 // interior cells: alpha = 1
                 const int nint = p_int[dims[1]];
                 for (int q = threadIdx.x; q < nint; q += blockDim.x) {
                     const int j = find_row(p_int, dims[1], q);
                     const int i = r_ic[j] + (q - p_int[j]);
                     const double rx = tb[3 * kVolAx + i], ry = tb[4 * kVolAx + j];
-                    const long long cc = (plane_off + wrap_int(lo[1] + j, g.n[1])) * g.n[0] + wrap_add(lo0w, i, g.n[0]);
+                    const long long cc = plane_off + row_off[j] + wrap_add(lo0w, i, g.n[0]);
                     const double u0 = (double)u[cc], u1 = (double)u[N + cc], u2 = (double)u[2 * N + cc];
-                    acc[0] += u0;
-                    acc[1] += u1;
-                    acc[2] += u2;
-                    acc[3] += ry * u2 - rz * u1;
-                    acc[4] += rz * u0 - rx * u2;
-                    acc[5] += rx * u1 - ry * u0;
-                    acc[6] += 1.0;
+                    s0 += u0;
+                    s1 += u1;
+                    s2 += u2;
+                    sA = fma(ry, u2, sA);
+                    sB = fma(rx, u2, sB);
+                    sC = fma(rx, u1, sC);
+                    sD = fma(ry, u0, sD);
                 }
-                // boundary cells: alpha from the corners
+                nint_cells += (nint + (int)blockDim.x - 1 - (int)threadIdx.x) / (int)blockDim.x;
+                // boundary cells: alpha = sum of max(-phi, 0) / sum |phi| over the corners
                 const int nbnd = p_bnd[dims[1]];
                 for (int q = threadIdx.x; q < nbnd; q += blockDim.x) {
                     const int j = find_row(p_bnd, dims[1], q);
                     const int k = q - p_bnd[j];
                     const int i = k < r_ca[j] ? r_ia[j] + k : r_ic[j] + c_int[j] + (k - r_ca[j]);
+                    // exact centre test: beyond R + 0.8661 h every corner is outside
+                    // (alpha = 0), within R - 0.8661 h every corner is inside
+                    // (alpha = 1); only cells in between read their corners,
+                    // all of which lie in the evaluated node shell
                     const double d2 = tb[6 * kVolAx + i] + tb[7 * kVolAx + j] + rz2;
                     if (d2 > rout2) continue;
                     double al = 1.0;
                     if (!(d2 < rin2)) {
                         const int qn = j * nx + i;
-                        const double ph[8] = {b0[qn], b0[qn + 1], b0[qn + nx], b0[qn + nx + 1],
-                                              b1[qn], b1[qn + 1], b1[qn + nx], b1[qn + nx + 1]};
-                        double num = 0.0, den = 0.0;
-#pragma unroll
-                        for (int m = 0; m < 8; ++m) {
-                            if (-ph[m] > 0.0) num += -ph[m];
-                            den += fabs(ph[m]);
-                        }
-                        al = den > 0.0 ? num / den : 0.5;
-                        if (al == 0.0) continue;
+                        const double2 c0 = b0[qn], c1 = b0[qn + 1], c2 = b0[qn + nx], c3 = b0[qn + nx + 1];
+                        const double2 c4 = b1[qn], c5 = b1[qn + 1], c6 = b1[qn + nx], c7 = b1[qn + nx + 1];
+                        const double num = ((c0.x + c1.x) + (c2.x + c3.x)) + ((c4.x + c5.x) + (c6.x + c7.x));
+                        const double neg = ((c0.y + c1.y) + (c2.y + c3.y)) + ((c4.y + c5.y) + (c6.y + c7.y));
+                        if (num == 0.0 && neg > 0.0) continue;  // alpha = 0
+                        const double den = num + neg;
+                        al = den == 0.0 ? 0.5 : (neg == 0.0 ? 1.0 : (den > 1e-30 ? num * recip_refined(den) : num / den));
                     }
                     const double rx = tb[3 * kVolAx + i], ry = tb[4 * kVolAx + j];
-                    const long long cc = (plane_off + wrap_int(lo[1] + j, g.n[1])) * g.n[0] + wrap_add(lo0w, i, g.n[0]);
-                    const double u0 = (double)u[cc], u1 = (double)u[N + cc], u2 = (double)u[2 * N + cc];
-                    acc[0] += al * u0;
-                    acc[1] += al * u1;
-                    acc[2] += al * u2;
-                    acc[3] += al * (ry * u2 - rz * u1);
-                    acc[4] += al * (rz * u0 - rx * u2);
-                    acc[5] += al * (rx * u1 - ry * u0);
-                    acc[6] += al;
+                    const long long cc = plane_off + row_off[j] + wrap_add(lo0w, i, g.n[0]);
+                    const double w0 = al * (double)u[cc], w1 = al * (double)u[N + cc], w2 = al * (double)u[2 * N + cc];
+                    s0 += w0;
+                    s1 += w1;
+                    s2 += w2;
+                    sA = fma(ry, w2, sA);
+                    sB = fma(rx, w2, sB);
+                    sC = fma(rx, w1, sC);
+                    sD = fma(ry, w0, sD);
+                    svol += al;
                 }
+                acc[0] += s0;
+                acc[1] += s1;
+                acc[2] += s2;
+                acc[3] = fma(-rz, s1, acc[3]);
+                acc[4] = fma(rz, s0, acc[4]);
                 __syncthreads();
             }
+            acc[3] += sA;
+            acc[4] -= sB;
+            acc[5] += sC - sD;
+            acc[6] += svol + (double)nint_cells;
         } else {
             // boxes wider than kVolMaxBox: every cell of the slab, corners evaluated directly
             for (int kz = z0; kz < z1; ++kz) {
