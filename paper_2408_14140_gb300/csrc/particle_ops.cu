@@ -179,11 +179,20 @@ __global__ void __launch_bounds__(kVolThreads) k_volume(CaseTab ct, int P,
                 row_off[j] = (long long)wrap_int(lo[1] + j, g.n[1]) * g.n[0];
             __syncthreads();
             const float fih = (float)g.inv_h;
-            // index range [first, last] of positions x_i = base + i h (i in [0, n)) with
-            // |x_i| <= w, widened by one on each side; empty when first > last
-            auto range = [&](double base, float w, int n, int &first, int &last) {
-                first = max(0, (int)floorf((float)(-w - base) * fih) - 1);
-                last = min(n - 1, (int)ceilf((float)(w - base) * fih) + 1);
+            // Index ranges of positions x_i = base + i h, i in [0, n), from FP32
+            // bounds with a margin of kEps cells -- far above the FP32 error of
+            // the bounds (< 1e-4 cells on grids up to 1024^3), so that every
+            // exact member is listed (range_out: |x_i| <= w) or every listed
+            // index is an exact member (range_in: |x_i| < w); empty when
+            // first > last.  Exact FP64 tests decide the cells in the margin.
+            constexpr float kEps = 1e-3f;
+            auto range_out = [&](double base, float w, int n, int &first, int &last) {
+                first = max(0, (int)ceilf((-w - (float)base) * fih - kEps));
+                last = min(n - 1, (int)floorf((w - (float)base) * fih + kEps));
+            };
+            auto range_in = [&](double base, float w, int n, int &first, int &last) {
+                first = max(0, (int)floorf((-w - (float)base) * fih + kEps) + 1);
+                last = min(n - 1, (int)ceilf((w - (float)base) * fih - kEps) - 1);
             };
             auto node_plane = [&](int kn, double2 *buf) {
                 const double zz = tb[2 * kVolAx + kn];
@@ -193,23 +202,16 @@ __global__ void __launch_bounds__(kVolThreads) k_volume(CaseTab ct, int P,
                     const double dyz = tb[kVolAx + j] + zz;
                     int a0 = 0, n0 = 0, a1 = 0, n1 = 0;
                     if (dyz < sh2) {
-                        const float xo = sqrtf((float)(sh2 - dyz));
-                        const float xi = sl2 > dyz ? sqrtf((float)(sl2 - dyz)) : -1.0f;
-                        int f, l;
-                        range(xb, xo, nx, f, l);
-                        if (xi > 2.0f * (float)h) {
-                            // two intervals: left [f, f2], right [l2, l]
-                            int f2, l2;
-                            range(xb, xi, nx, f2, l2);  // widened inner range
-                            const int li = f2 + 2, ri = l2 - 2;  // shrink back: inner exclusion
+                        // nodes of the shell sl <= |x| <= sh: the outer range minus
+                        // the nodes surely inside sl
+                        int f, l, fi = 1, li = 0;
+                        range_out(xb, sqrtf((float)(sh2 - dyz)), nx, f, l);
+                        if (sl2 > dyz) range_in(xb, sqrtf((float)(sl2 - dyz)), nx, fi, li);
+                        if (li >= fi && l >= f) {
                             a0 = f;
-                            n0 = max(0, min(l, li) - f + 1);
-                            a1 = max(ri, f);
-                            n1 = ri > f && l >= a1 ? l - a1 + 1 : 0;
-                            if (li >= ri) {  // exclusion vanished: one interval
-                                n0 = l - f + 1;
-                                n1 = 0;
-                            }
+                            n0 = max(0, min(l, fi - 1) - f + 1);
+                            a1 = max(li + 1, f);
+                            n1 = max(0, l - a1 + 1);
                         } else {
                             a0 = f;
                             n0 = max(0, l - f + 1);
@@ -247,12 +249,10 @@ __global__ void __launch_bounds__(kVolThreads) k_volume(CaseTab ct, int P,
                     const double ryz2 = tb[7 * kVolAx + j] + rz2;
                     int ia = 0, ib = -1, ja = 0, jb = -1;
                     if (ryz2 <= rout2) {
-                        range(xcb, sqrtf((float)(rout2 - ryz2)), dims[0], ia, ib);
-                        if (ryz2 < rin2) {
-                            range(xcb, sqrtf((float)(rin2 - ryz2)), dims[0], ja, jb);
-                            ja += 2;  // undo the widening and shrink one more cell: all surely inside
-                            jb -= 2;
-                        }
+                        range_out(xcb, sqrtf((float)(rout2 - ryz2)), dims[0], ia, ib);
+                        if (ryz2 < rin2) range_in(xcb, sqrtf((float)(rin2 - ryz2)), dims[0], ja, jb);
+                        ja = max(ja, ia);  // interior within the outer range
+                        jb = min(jb, ib);
                     }
                     if (jb < ja) {
                         ja = ib + 1;  // no interior: one boundary interval [ia, ib]
