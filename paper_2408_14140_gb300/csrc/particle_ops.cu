@@ -375,11 +375,31 @@ __global__ void __launch_bounds__(kVolThreads) k_volume(CaseTab ct, int P,
                 }
             }
         }
-        const double h3 = h * h * h;
-#pragma unroll
-        for (int k = 0; k < 7; ++k) acc[k] *= h3;
     }
-    block_sum<7>(acc);
+    // fixed-order CTA sum of the 7 partials through shared memory: 7 warps,
+    // one per quantity, each lane adding 8 entries then a shuffle tree (FP64
+    // adds are scarce on this part: a shuffle tree over all 256 threads would
+    // cost more FP64 work than a thin slab's cells)
+    {
+        __shared__ double s_acc[7][kVolThreads];
+#pragma unroll
+        for (int k = 0; k < 7; ++k) s_acc[k][threadIdx.x] = acc[k];
+        __syncthreads();
+        const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5;
+        if (wq < 7) {
+            double x = 0.0;
+#pragma unroll
+            for (int m = 0; m < kVolThreads / 32; ++m) x += s_acc[wq][lane + 32 * m];
+            for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+            if (lane == 0) s_acc[wq][0] = x;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const double h3 = g.h * g.h * g.h;
+#pragma unroll
+            for (int k = 0; k < 7; ++k) acc[k] = s_acc[k][0] * h3;
+        }
+    }
     __shared__ double s_part[kVolSplit * 7];
     if (threadIdx.x == 0) {
         double *dst = partial + ((size_t)p * kVolSplit + split) * 7;
