@@ -221,13 +221,14 @@ def peaks():
 class Runner:
     """Device state of one workload replica and the hot-path step."""
 
-    def __init__(self, case, prec, device):
+    def __init__(self, case, prec, device, delta=0, order=0):
         import torch
         from paper_2408_14140_gb300 import api, synth
         self.torch, self.api = torch, api
         self.case = case
         self.prec = prec
         self.dev = device
+        self.delta, self.order = delta, order
         self.ctx = api.Context()
         dt = api.field_dtype(prec)
         self.u = synth.fourier_eval_torch(case.n, case.meta["modes"], case.h, case.org,
@@ -254,7 +255,8 @@ class Runner:
     def step(self):
         c, ctx = self.case, self.ctx
         ctx.particle_volume_integrals(self.u, c.h, self.parts, out=self.I0)
-        ctx.ib_multidirect_forcing(self.u, c.h, self.parts, self.marks, c.Ns, c.dt, F_out=self.F)
+        ctx.ib_multidirect_forcing(self.u, c.h, self.parts, self.marks, c.Ns, c.dt, F_out=self.F,
+                                   delta=self.delta, order=self.order)
         ctx.particle_force_torque(self.parts, self.marks, self.F, c.rho_f, out=(self.Fib, self.Tib))
         ctx.particle_volume_integrals(self.u, c.h, self.parts, out=self.I1)
         ctx.particle_collide_update(self.parts, c.n, c.h, c.phys(), c.dt, self.Fib, self.Tib,
@@ -263,12 +265,13 @@ class Runner:
 
 def launches_per_step(Ns, levels):
     """Library kernels per step on this workload (P * 512 = 32768 dense tiles,
-    so each scan is one kernel): volume 1 x 2 calls; multidirect forcing:
-    prep, conflicts, levels, marker order, tile count, scan, flags, scan,
-    compact, fill, sort, level ranges (12), one interpolation and one gather
-    kernel per wavefront and pass, the persistent remainder kernel (1);
-    force/torque 1; collision + Newton-Euler 2."""
-    return 2 + 12 + 2 * Ns * levels + 1 + 1 + 2
+    so each scan is three kernels): volume 1 x 2 calls; multidirect forcing:
+    prep, conflicts, levels, marker order, tile count, scan (3), flags, scan
+    (3), compact, fill, sort, per-cell lists, level ranges (17), one
+    interpolation and one gather kernel per wavefront and pass, the
+    persistent remainder kernel (1); force/torque 1; collision +
+    Newton-Euler 2."""
+    return 2 + 17 + 2 * Ns * levels + 1 + 1 + 2
 
 
 def time_steps(runner, steps, warmup, flush, use_graph):
@@ -642,6 +645,21 @@ def run_gpu(args):
         dt, bi, bo = f64["e2e"]
         line["fp64"]["e2e"] = {"value": world * M * Ns / dt, "h2d_bytes_per_step": bi,
                                "d2h_bytes_per_step": bo}
+    if world == 1 and not args.no_variants:
+        # the same workload with the other particle order and the other kernel
+        # (FP32 fields), each a full step timed like the main line
+        line["variants"] = {}
+        for name, delta, order in (("simultaneous_order", 0, 1), ("peskin4_kernel", 1, 0)):
+            rv = Runner(case, api.IB_F32, device, delta=delta, order=order)
+            msv, gv = time_steps(rv, max(3, args.steps // 4), args.warmup, flush, not args.no_graph)
+            ktv = kernel_timing(rv, 3, flush)
+            tv = sum(msv) / 1000.0 / len(msv)
+            line["variants"][name] = {"value": M * Ns / tv, "unit": "marker-updates/s",
+                                      "ms_per_step": tv * 1000.0, "steps": len(msv),
+                                      "launch": "cuda-graph replay" if gv else "eager",
+                                      "phases_us": {k: round(v[0] / v[1] * 1000.0, 2) for k, v in ktv.items()}}
+            rv.ctx.close()
+            del rv
     if world == 1 and not args.no_batched:
         line["batched"] = run_batched(args, device, hbm)
     if world == 1 and not args.no_serve:
@@ -716,6 +734,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--prec", default="both", choices=["both", "f32", "f64"])
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--serve-rate", type=float, default=200.0)
     ap.add_argument("--serve-seconds", type=float, default=2.0)
