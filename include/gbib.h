@@ -154,11 +154,16 @@ GBIB_API int ib_ctx_read_timing(ib_ctx *ctx, int phase, double *ms_total,
  * RESIDENT: one thread-block cluster per particle keeps the particle's band
  *   tiles in shared memory for all Ns passes; particles start as soon as the
  *   earlier particles they conflict with are stored.
+ * GROUPS: a persistent cooperative kernel split into groups of CTAs; a group
+ *   runs all Ns passes of one particle (barriers over the group's CTAs only),
+ *   and particles start as soon as the earlier particles they conflict with
+ *   are done.
  * The simultaneous order always runs the wavefront form (one wavefront).
  * Returns IB_ERR_INVALID for any other value.                             */
 #define IB_PASSES_AUTO 0
 #define IB_PASSES_WAVEFRONT 1
 #define IB_PASSES_RESIDENT 2
+#define IB_PASSES_GROUPS 3
 GBIB_API int ib_ctx_set_pass_kernels(ib_ctx *ctx, int which);
 
 /* ---- velocity interpolation J: Eq. (u), Eq. (vi), Algorithm 1 -----------

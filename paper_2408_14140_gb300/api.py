@@ -36,7 +36,7 @@ ROMA3 = 0
 PESKIN4 = 1
 SEQUENTIAL = 0
 SIMULTANEOUS = 1
-PASSES = {"auto": 0, "wavefront": 1, "resident": 2}
+PASSES = {"auto": 0, "wavefront": 1, "resident": 2, "groups": 3}
 
 PHASES = {"mdf_prep": 0, "mdf_passes": 1, "spread": 2, "interp": 3, "volume": 4,
           "force": 5, "collide": 6, "mdf_interp": 7, "mdf_gather": 8}
@@ -212,8 +212,9 @@ class Context:
         self._check(self.lib.ib_ctx_set_timing(self.handle, 1 if enable else 0))
 
     def set_pass_kernels(self, which: str):
-        """Kernels of the sequential-order passes: "auto", "wavefront" or
-        "resident" (see gbib.h; every choice gives bitwise the same result)."""
+        """Kernels of the sequential-order passes: "auto", "wavefront",
+        "resident" or "groups" (see gbib.h; every choice gives bitwise the
+        same result)."""
         self._check(self.lib.ib_ctx_set_pass_kernels(self.handle, PASSES[which]))
 
     def read_timing(self, phase: str):

@@ -353,7 +353,8 @@ int ib_ctx_set_timing(ib_ctx *c, int enable) {
 
 int ib_ctx_set_pass_kernels(ib_ctx *c, int which) {
     if (!c) return set_error(IB_ERR_INVALID, "ctx is NULL");
-    if (which != IB_PASSES_AUTO && which != IB_PASSES_WAVEFRONT && which != IB_PASSES_RESIDENT)
+    if (which != IB_PASSES_AUTO && which != IB_PASSES_WAVEFRONT && which != IB_PASSES_RESIDENT &&
+        which != IB_PASSES_GROUPS)
         return set_error(IB_ERR_INVALID, "bad pass-kernel choice %d", which);
     c->pass_kernels = which;
     return IB_OK;

@@ -156,6 +156,185 @@ __device__ __forceinline__ bool gather_cell(int tx, int ty, int tz, const uint16
 
 namespace gbib {
 
+// Candidates of one tile staged in shared memory by the list gathers.
+template <typename T> struct TileStage;
+template <> struct TileStage<float> { static constexpr int N = 256; };
+template <> struct TileStage<double> { static constexpr int N = 192; };
+
+template <typename T>
+constexpr size_t tile_stage_bytes() {
+    return (size_t)TileStage<T>::N * 16 * sizeof(T);
+}
+
+// One tile (compact slot cs) of a gather phase over its per-cell lists: the
+// tile's candidate weights and sources are staged in shared memory (sw
+// [N][12], sA [N][4]) when they fit, then each thread takes band cells and
+// adds their pairs in list order (ascending candidate), u += S A and, when the
+// case has a force field, f += S A / dt.  COH: the sources were written during
+// this kernel (plain loads after an acquire) rather than by an earlier one.
+// Ends with a CTA barrier.
+template <typename T, int KW, bool COH>
+__device__ __forceinline__ void gather_tile_lists(const CaseTab &ct, int cs, const Slots &sl, const T *wts,
+                                                  const T *A_src, double inv_dt, T *sw, T *sA) {
+    constexpr int KW3 = KW * KW * KW;
+    const DevCase cd = ct.get(sl.geo_case[cs]);
+    const DevGrid &g = cd.g;
+    const long long N = (long long)g.n[0] * g.n[1] * g.n[2];
+    T *const u = (T *)cd.u;
+    T *const f_out = (T *)cd.f;
+    const int4 lo = sl.geo_lo[cs], dim = sl.geo_dim[cs];
+    const uint32_t d = sl.dense_of[cs];
+    const int nc = (int)(sl.start[d + 1] - sl.start[d]);
+    const int nb = sl.nband[cs];
+    const uint32_t *cand = sl.cand + dim.w;
+    const int2 *band = sl.band + (size_t)KW3 * dim.w;
+    const uint32_t *pairs = sl.pairs + (size_t)KW3 * dim.w;
+    const bool staged = nc <= TileStage<T>::N;
+    if (staged) {
+        for (int i = threadIdx.x; i < nc; i += blockDim.x) {
+            const uint32_t m = cand[i];
+            const T *wm = wts + 12 * (size_t)m;
+#pragma unroll
+            for (int q = 0; q < 3; ++q)
+#pragma unroll
+                for (int j = 0; j < KW; ++j) sw[12 * i + 4 * q + j] = __ldg(wm + 4 * q + j);
+#pragma unroll
+            for (int q = 0; q < 3; ++q) sA[4 * i + q] = ld<COH>(A_src + 4 * (size_t)m + q);
+        }
+        __syncthreads();
+    }
+    for (int q = threadIdx.x; q < nb; q += blockDim.x) {
+        const int2 e = band[q];
+        const int cell = e.x & 0xffff, cnt = e.x >> 16;
+        const uint32_t *pr = pairs + e.y;
+        T acc0 = 0, acc1 = 0, acc2 = 0;
+        for (int k = 0; k < cnt; ++k) {
+            const uint32_t pk = pr[k];
+            const int i = pk & 0xffff, ox = (pk >> 16) & 3, oy = (pk >> 18) & 3, oz = (pk >> 20) & 3;
+            T wt, a0, a1, a2;
+            if (staged) {
+                const T *w = sw + 12 * i;
+                const T *Ai = sA + 4 * i;
+                wt = w[ox] * w[4 + oy] * w[8 + oz];
+                a0 = Ai[0], a1 = Ai[1], a2 = Ai[2];
+            } else {
+                const size_t m = cand[i];
+                const T *w = wts + 12 * m;
+                const T *Ai = A_src + 4 * m;
+                wt = __ldg(w + ox) * __ldg(w + 4 + oy) * __ldg(w + 8 + oz);
+                a0 = ld<COH>(Ai), a1 = ld<COH>(Ai + 1), a2 = ld<COH>(Ai + 2);
+            }
+            acc0 += wt * a0;
+            acc1 += wt * a1;
+            acc2 += wt * a2;
+        }
+        const int tx = cell & 7, ty = (cell >> 3) & 7, tz = cell >> 6;
+        const long long c = ((long long)wrap_add(lo.z, tz, g.n[2]) * g.n[1] + wrap_add(lo.y, ty, g.n[1])) * g.n[0] +
+                            wrap_add(lo.x, tx, g.n[0]);
+        u[c] += acc0;
+        u[N + c] += acc1;
+        u[2 * N + c] += acc2;
+        if (f_out) {
+            f_out[c] += (T)(acc0 * inv_dt);
+            f_out[N + c] += (T)(acc1 * inv_dt);
+            f_out[2 * N + c] += (T)(acc2 * inv_dt);
+        }
+    }
+    __syncthreads();
+}
+
+// Several consecutive tiles [cs0, cs0 + nt) of one case gathered together:
+// the candidates of all of them are staged at once when they fit, and the
+// band cells of all of them form one flat loop (one staging round trip and
+// one barrier for the lot).  Falls back to one tile at a time otherwise.
+// Sums are those of gather_tile_lists.  Ends with a CTA barrier.
+constexpr int kMultiTiles = 8;
+
+template <typename T, int KW, bool COH>
+__device__ __forceinline__ void gather_tiles_lists(const CaseTab &ct, int cs0, int nt, const Slots &sl,
+                                                   const T *wts, const T *A_src, double inv_dt, T *sw, T *sA) {
+    constexpr int KW3 = KW * KW * KW;
+    __shared__ int s_coff[kMultiTiles + 1], s_boff[kMultiTiles + 1];
+    if (nt <= 0) return;
+    if (nt > kMultiTiles) {
+        for (int k = 0; k < nt; ++k) gather_tile_lists<T, KW, COH>(ct, cs0 + k, sl, wts, A_src, inv_dt, sw, sA);
+        return;
+    }
+    if (threadIdx.x == 0) {
+        int co = 0, bo = 0;
+        for (int k = 0; k < nt; ++k) {
+            const uint32_t d = sl.dense_of[cs0 + k];
+            s_coff[k] = co;
+            s_boff[k] = bo;
+            co += (int)(sl.start[d + 1] - sl.start[d]);
+            bo += sl.nband[cs0 + k];
+        }
+        s_coff[nt] = co;
+        s_boff[nt] = bo;
+    }
+    __syncthreads();
+    if (s_coff[nt] > TileStage<T>::N) {
+        for (int k = 0; k < nt; ++k) gather_tile_lists<T, KW, COH>(ct, cs0 + k, sl, wts, A_src, inv_dt, sw, sA);
+        return;
+    }
+    const DevCase cd = ct.get(sl.geo_case[cs0]);
+    const DevGrid &g = cd.g;
+    const long long N = (long long)g.n[0] * g.n[1] * g.n[2];
+    T *const u = (T *)cd.u;
+    T *const f_out = (T *)cd.f;
+    // stage every candidate of the tiles (tile k's at offset s_coff[k])
+    const int ctot = s_coff[nt];
+    for (int j = threadIdx.x; j < ctot; j += blockDim.x) {
+        int k = 0;
+        while (k + 1 < nt && s_coff[k + 1] <= j) ++k;
+        const uint32_t m = sl.cand[sl.geo_dim[cs0 + k].w + (j - s_coff[k])];
+        const T *wm = wts + 12 * (size_t)m;
+#pragma unroll
+        for (int q = 0; q < 3; ++q)
+#pragma unroll
+            for (int jj = 0; jj < KW; ++jj) sw[12 * j + 4 * q + jj] = __ldg(wm + 4 * q + jj);
+#pragma unroll
+        for (int q = 0; q < 3; ++q) sA[4 * j + q] = ld<COH>(A_src + 4 * (size_t)m + q);
+    }
+    __syncthreads();
+    const int btot = s_boff[nt];
+    for (int qq = threadIdx.x; qq < btot; qq += blockDim.x) {
+        int k = 0;
+        while (k + 1 < nt && s_boff[k + 1] <= qq) ++k;
+        const int cs = cs0 + k;
+        const int4 lo = sl.geo_lo[cs];
+        const int b = sl.geo_dim[cs].w;
+        const int2 e = sl.band[(size_t)KW3 * b + (qq - s_boff[k])];
+        const int cell = e.x & 0xffff, cnt = e.x >> 16;
+        const uint32_t *pr = sl.pairs + (size_t)KW3 * b + e.y;
+        const T *swk = sw + 12 * (size_t)s_coff[k];
+        const T *sAk = sA + 4 * (size_t)s_coff[k];
+        T acc0 = 0, acc1 = 0, acc2 = 0;
+        for (int kk = 0; kk < cnt; ++kk) {
+            const uint32_t pk = pr[kk];
+            const int i = pk & 0xffff, ox = (pk >> 16) & 3, oy = (pk >> 18) & 3, oz = (pk >> 20) & 3;
+            const T *w = swk + 12 * i;
+            const T *Ai = sAk + 4 * i;
+            const T wt = w[ox] * w[4 + oy] * w[8 + oz];
+            acc0 += wt * Ai[0];
+            acc1 += wt * Ai[1];
+            acc2 += wt * Ai[2];
+        }
+        const int tx = cell & 7, ty = (cell >> 3) & 7, tz = cell >> 6;
+        const long long c = ((long long)wrap_add(lo.z, tz, g.n[2]) * g.n[1] + wrap_add(lo.y, ty, g.n[1])) * g.n[0] +
+                            wrap_add(lo.x, tx, g.n[0]);
+        u[c] += acc0;
+        u[N + c] += acc1;
+        u[2 * N + c] += acc2;
+        if (f_out) {
+            f_out[c] += (T)(acc0 * inv_dt);
+            f_out[N + c] += (T)(acc1 * inv_dt);
+            f_out[2 * N + c] += (T)(acc2 * inv_dt);
+        }
+    }
+    __syncthreads();
+}
+
 // Arguments of the particle-resident pass kernel (sequential order): the
 // outputs of the preparation kernels plus the scheduling words.
 template <typename T>
@@ -176,6 +355,7 @@ struct ResidentArgs {
     const int *nbr;         // [P][kMaxNbr]
     unsigned int *done;     // [P] CTAs that finished each particle (zeroed)
     unsigned int *ticket;   // next rank to take (zeroed)
+    unsigned int *gwords;   // [4 * groups] group barrier words and ticket slot (zeroed; group form)
     int P, Ns;
     double dt;
     DevStatus *st;
@@ -184,5 +364,12 @@ struct ResidentArgs {
 // Enqueues the particle-resident passes on `s` (mdf_resident.cu).
 template <typename T, int KER>
 int launch_mdf_resident(ib_ctx *ctx, const ResidentArgs<T> &a, cudaStream_t s);
+
+// Enqueues the particle-group passes on `s` (mdf_groups.cu); `gwords` must
+// hold 4 * mdf_groups_count(ctx) words, zeroed.
+template <typename T, int KER>
+int launch_mdf_groups(ib_ctx *ctx, const ResidentArgs<T> &a, cudaStream_t s);
+template <typename T, int KER>
+int mdf_groups_count(ib_ctx *ctx);
 
 }  // namespace gbib

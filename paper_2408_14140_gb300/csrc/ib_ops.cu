@@ -758,7 +758,9 @@ __global__ void __launch_bounds__(kPairThreads) k_tile_pairs(CaseTab ct, int nco
         const int4 lo = sl.geo_lo[cs], dim = sl.geo_dim[cs];
         const DevGrid g = ct.get(sl.geo_case[cs]).g;
         const int b = dim.w;
-        const int nc = min((int)sl.bins[(size_t)cs * kBins + kBins - 1], kMaxCand);
+        const uint32_t dn = sl.dense_of[cs];
+        int nc = (int)(sl.start[dn + 1] - sl.start[dn]);
+        if (nc > kMaxCand) nc = 0;  // left empty by the sort (status raised there)
         int2 *band = sl.band + (size_t)KW3 * b;
         uint32_t *pairs = sl.pairs + (size_t)KW3 * b;
         for (int i = tid; i < nc; i += blockDim.x) {
@@ -1080,95 +1082,18 @@ __global__ void __launch_bounds__(256) k_interp_level(PassArgs<T> a, int L) {
     }
 }
 
-template <typename T> struct TileStage;
-template <> struct TileStage<float> { static constexpr int N = 256; };
-template <> struct TileStage<double> { static constexpr int N = 192; };
-
-template <typename T>
-constexpr size_t tile_stage_bytes() {
-    return (size_t)TileStage<T>::N * 16 * sizeof(T);
-}
-
-// The wavefront gather, one CTA per tile (grid-stride), many CTAs per SM.
-// The tile's candidate weights and sources are staged in shared memory, and
-// each thread takes band cells of the tile and adds its cell's pairs in list
-// order (ascending candidate = the bin order of gather_cell, so the sums are
-// bitwise those of the bin walk).  Cells outside the band cost nothing.
+// The wavefront gather, one CTA per tile (grid-stride), many CTAs per SM,
+// over the tiles' per-cell lists (sums bitwise those of the bin walk).
 template <typename T, int KER>
 __global__ void __launch_bounds__(256, 5) k_gather_level(PassArgs<T> a, int L) {
-    constexpr int KW = Kernel<KER>::W;
-    constexpr int KW3 = KW * KW * KW;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     if (L >= *a.nlev) return;
     T *sw = (T *)smem_raw;                          // [N][12]
     T *sA = sw + (size_t)TileStage<T>::N * 12;      // [N][4]
     const double inv_dt = 1.0 / a.dt;
     const int s0 = a.lev_sbeg[L], s1 = a.lev_sbeg[L + 1];
-    for (int cs = s0 + blockIdx.x; cs < s1; cs += gridDim.x) {
-        const DevCase &cd = a.ct.get(a.sl.geo_case[cs]);
-        const DevGrid g = cd.g;
-        const long long N = (long long)g.n[0] * g.n[1] * g.n[2];
-        T *const u = (T *)cd.u;
-        T *const f_out = (T *)cd.f;
-        const int4 lo = a.sl.geo_lo[cs], dim = a.sl.geo_dim[cs];
-        const int nc = a.sl.bins[(size_t)cs * kBins + kBins - 1];
-        const int nb = a.sl.nband[cs];
-        const uint32_t *cand = a.sl.cand + dim.w;
-        const int2 *band = a.sl.band + (size_t)KW3 * dim.w;
-        const uint32_t *pairs = a.sl.pairs + (size_t)KW3 * dim.w;
-        const bool staged = nc <= TileStage<T>::N;
-        if (staged) {
-            for (int i = threadIdx.x; i < nc; i += blockDim.x) {
-                const uint32_t m = cand[i];
-                const T *wm = a.ms.wts + 12 * (size_t)m;
-#pragma unroll
-                for (int q = 0; q < 3; ++q)
-#pragma unroll
-                    for (int j = 0; j < KW; ++j) sw[12 * i + 4 * q + j] = __ldg(wm + 4 * q + j);
-#pragma unroll
-                for (int q = 0; q < 3; ++q) sA[4 * i + q] = __ldg(a.ms.A + 4 * (size_t)m + q);
-            }
-            __syncthreads();
-        }
-        for (int q = threadIdx.x; q < nb; q += blockDim.x) {
-            const int2 e = band[q];
-            const int cell = e.x & 0xffff, cnt = e.x >> 16;
-            const uint32_t *pr = pairs + e.y;
-            T acc0 = 0, acc1 = 0, acc2 = 0;
-            for (int k = 0; k < cnt; ++k) {
-                const uint32_t pk = pr[k];
-                const int i = pk & 0xffff, ox = (pk >> 16) & 3, oy = (pk >> 18) & 3, oz = (pk >> 20) & 3;
-                T wt, a0, a1, a2;
-                if (staged) {
-                    const T *w = sw + 12 * i;
-                    const T *A = sA + 4 * i;
-                    wt = w[ox] * w[4 + oy] * w[8 + oz];
-                    a0 = A[0], a1 = A[1], a2 = A[2];
-                } else {
-                    const size_t m = cand[i];
-                    const T *w = a.ms.wts + 12 * m;
-                    const T *A = a.ms.A + 4 * m;
-                    wt = __ldg(w + ox) * __ldg(w + 4 + oy) * __ldg(w + 8 + oz);
-                    a0 = __ldg(A), a1 = __ldg(A + 1), a2 = __ldg(A + 2);
-                }
-                acc0 += wt * a0;
-                acc1 += wt * a1;
-                acc2 += wt * a2;
-            }
-            const int tx = cell & 7, ty = (cell >> 3) & 7, tz = cell >> 6;
-            const long long c = ((long long)wrap_add(lo.z, tz, g.n[2]) * g.n[1] +
-                                 wrap_add(lo.y, ty, g.n[1])) * g.n[0] + wrap_add(lo.x, tx, g.n[0]);
-            u[c] += acc0;
-            u[N + c] += acc1;
-            u[2 * N + c] += acc2;
-            if (f_out) {
-                f_out[c] += (T)(acc0 * inv_dt);
-                f_out[N + c] += (T)(acc1 * inv_dt);
-                f_out[2 * N + c] += (T)(acc2 * inv_dt);
-            }
-        }
-        __syncthreads();
-    }
+    for (int cs = s0 + blockIdx.x; cs < s1; cs += gridDim.x)
+        gather_tile_lists<T, Kernel<KER>::W, false>(a.ct, cs, a.sl, a.ms.wts, a.ms.A, inv_dt, sw, sA);
 }
 
 template <typename T, int KER>
@@ -1473,7 +1398,13 @@ static int run_mdf(ib_ctx *ctx, Arena &ar, const CaseTab &ct, const ib_particles
     int *ncompact = nullptr;
     int rc = build_slots<KW>(ctx, ar, ct, M, (int)ndense, sg, ms.anchor, lo.level, sl, ncompact, s, true);
     if (rc) return rc;
-    if (order == IB_ORDER_SEQUENTIAL && ctx->pass_kernels == IB_PASSES_RESIDENT) {
+    if (order == IB_ORDER_SEQUENTIAL &&
+        (ctx->pass_kernels == IB_PASSES_RESIDENT || ctx->pass_kernels == IB_PASSES_GROUPS)) {
+        const bool groups = ctx->pass_kernels == IB_PASSES_GROUPS;
+        const int ngroups = groups ? mdf_groups_count<T, KER>(ctx) : 0;
+        if (groups && ngroups < 1) return set_error(IB_ERR_CUDA, "group kernel: no resident group");
+        unsigned int *gwords = groups ? ar.take<unsigned int>((size_t)4 * ngroups) : nullptr;
+        if (!ar.ok()) return oom_error(ar.used, ar.cap);
         // particle-resident passes: one cluster per particle, scheduled by rank
         ResidentArgs<T> ra;
         ra.ct = ct;
@@ -1492,14 +1423,16 @@ static int run_mdf(ib_ctx *ctx, Arena &ar, const CaseTab &ct, const ib_particles
         ra.nbr = nbr;
         ra.done = sched;
         ra.ticket = sched + P;
+        ra.gwords = gwords;
         ra.P = P;
         ra.Ns = Ns;
         ra.dt = dt;
         ra.st = ctx->status;
         cudaMemsetAsync(sched, 0, sizeof(unsigned int) * (P + 1), s);
+        if (groups) cudaMemsetAsync(gwords, 0, sizeof(unsigned int) * 4 * ngroups, s);
         tprep.stop();
         PhaseTimer tpass(ctx, IB_PHASE_MDF_PASSES, s);
-        rc = launch_mdf_resident<T, KER>(ctx, ra, s);
+        rc = groups ? launch_mdf_groups<T, KER>(ctx, ra, s) : launch_mdf_resident<T, KER>(ctx, ra, s);
         if (rc) return rc;
         tpass.stop();
         return check_launch("ib_multidirect_forcing");

@@ -93,6 +93,9 @@ def test_mdf_bench_workload_all_paths(api, cluster256, prec):
     ctx.set_pass_kernels("resident")
     call("resident")
     graph_replay("resident, graph replay")
+    ctx.set_pass_kernels("groups")
+    call("groups")
+    graph_replay("groups, graph replay")
     ctx.set_pass_kernels("wavefront")
     call("persistent")          # first wavefront-form call: all wavefronts in the persistent kernel
     call("wavefront kernels")   # later call: the wavefronts as separate kernels

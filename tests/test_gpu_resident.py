@@ -1,11 +1,12 @@
-"""The two forms of the sequential-order passes give bitwise the same result.
+"""The forms of the sequential-order passes give bitwise the same result.
 
 The particle-resident kernel (one thread-block cluster per particle, band in
-shared memory) and the wavefront kernels (per wavefront and
-pass through global memory) sum every cell and marker in the same order, so
-u, F and f agree bit for bit; both stay within the oracle's gates.  Cases
-cover the resident fast path, the slow path of particles too large for the
-cluster's shared memory, and conflicts between the two.
+shared memory), the particle-group kernel (a group of CTAs per particle in a
+persistent launch) and the wavefront kernels (per wavefront and pass through
+global memory) sum every cell and marker in the same order, so u, F and f
+agree bit for bit; all stay within the oracle's gates.  Cases cover the
+resident fast path, the slow path of particles too large for the cluster's
+shared memory, and conflicts between the two.
 """
 import numpy as np
 import pytest
@@ -71,17 +72,18 @@ def run(api, ctx, case, prec, kernel, u0):
     return u, F, f
 
 
+@pytest.mark.parametrize("form", ["resident", "groups"])
 @pytest.mark.parametrize("name", list(CASES))
 @pytest.mark.parametrize("prec,kernel", [(0, 0), (1, 0), (0, 1), (1, 1)])
-def test_resident_equals_wavefront_and_oracle(api, name, prec, kernel):
+def test_resident_equals_wavefront_and_oracle(api, form, name, prec, kernel):
     case = CASES[name]()
     u0 = torch.tensor(case.u, device="cuda", dtype=api.field_dtype(prec))
     ctx = api.Context()
-    ctx.set_pass_kernels("resident")
+    ctx.set_pass_kernels(form)
     res = [run(api, ctx, case, prec, kernel, u0) for _ in range(2)]
     ctx.set_pass_kernels("wavefront")
     wav = [run(api, ctx, case, prec, kernel, u0) for _ in range(2)]  # persistent, then per wavefront
-    ctx.set_pass_kernels("resident")
+    ctx.set_pass_kernels(form)
     res.append(run(api, ctx, case, prec, kernel, u0))
     ref = res[0]
     for out in res[1:] + wav:
