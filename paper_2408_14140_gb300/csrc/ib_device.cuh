@@ -244,13 +244,14 @@ __device__ __forceinline__ void gather_tile_lists(const CaseTab &ct, int cs, con
 }
 
 // Several consecutive tiles [cs0, cs0 + nt) of one case gathered together:
-// the candidates of all of them are staged at once when they fit, and the
+// the candidates of all of them are staged at once when they fit (CAP
+// records in sw/sA; single tiles need TileStage<T>::N), and the
 // band cells of all of them form one flat loop (one staging round trip and
 // one barrier for the lot).  Falls back to one tile at a time otherwise.
 // Sums are those of gather_tile_lists.  Ends with a CTA barrier.
 constexpr int kMultiTiles = 8;
 
-template <typename T, int KW, bool COH>
+template <typename T, int KW, bool COH, int CAP>
 __device__ __forceinline__ void gather_tiles_lists(const CaseTab &ct, int cs0, int nt, const Slots &sl,
                                                    const T *wts, const T *A_src, double inv_dt, T *sw, T *sA) {
     constexpr int KW3 = KW * KW * KW;
@@ -273,7 +274,7 @@ __device__ __forceinline__ void gather_tiles_lists(const CaseTab &ct, int cs0, i
         s_boff[nt] = bo;
     }
     __syncthreads();
-    if (s_coff[nt] > TileStage<T>::N) {
+    if (s_coff[nt] > CAP) {
         for (int k = 0; k < nt; ++k) gather_tile_lists<T, KW, COH>(ct, cs0 + k, sl, wts, A_src, inv_dt, sw, sA);
         return;
     }

@@ -11,9 +11,9 @@
 //   * interpolation: each CTA takes a contiguous share of the particle's
 //     markers (U = J u, F += (U^d - U)/dt, A = (U^d - U) dV / h^3);
 //   * a barrier over the group's CTAs;
-//   * gather: each CTA takes a contiguous share of the particle's tiles and
-//     adds their per-cell lists (the same sums, in the same order, as the
-//     wavefront gather);
+//   * gather: each CTA takes a contiguous share of the particle's tiles,
+//     stages all their candidates at once and adds their per-cell lists (the
+//     same sums, in the same order, as the wavefront gather);
 //   * a barrier over the group, then the next pass.
 // A particle first waits (bounded) until every earlier particle it conflicts
 // with has been published by all CTAs of its group.  Every wait is on a lower
@@ -28,6 +28,15 @@ namespace gbib {
 
 constexpr int kGroupCtas = 16;     // CTAs per particle
 constexpr int kGroupThreads = 256;
+// candidate records staged per CTA: all of a CTA's tiles at once (its share
+// of a D = 24 sphere's tiles holds ~250 candidates, unevenly spread)
+template <typename T> struct GroupStage;
+template <> struct GroupStage<float> { static constexpr int N = 1024; };
+template <> struct GroupStage<double> { static constexpr int N = 512; };
+template <typename T>
+constexpr size_t group_stage_bytes() {
+    return (size_t)GroupStage<T>::N * 16 * sizeof(T);
+}
 
 // First of the items [0, n) that member r of C owns (contiguous chunks).
 __device__ __forceinline__ int group_chunk(int r, int n, int C) { return (int)((long long)r * n / C); }
@@ -96,8 +105,8 @@ __global__ void __launch_bounds__(kGroupThreads) k_mdf_groups(ResidentArgs<T> a)
     constexpr int KW = Kernel<KER>::W;
     constexpr unsigned int G = kGroupCtas;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T *sw = (T *)smem_raw;                      // [N][12]
-    T *sA = sw + (size_t)TileStage<T>::N * 12;  // [N][4]
+    T *sw = (T *)smem_raw;                        // [N][12]
+    T *sA = sw + (size_t)GroupStage<T>::N * 12;   // [N][4]
     __shared__ int s_t;
     const int grp = blockIdx.x / G, r = blockIdx.x % G;
     unsigned int *gw = a.gwords + 4 * (size_t)grp;  // count, generation, ticket slot
@@ -139,7 +148,8 @@ __global__ void __launch_bounds__(kGroupThreads) k_mdf_groups(ResidentArgs<T> a)
                 }
             }
             if (!group_sync(gw, gw + 1, G, a.st)) return;
-            gather_tiles_lists<T, KW, true>(a.ct, c0 + k0, k1 - k0, a.sl, a.ms.wts, a.ms.A, inv_dt, sw, sA);
+            gather_tiles_lists<T, KW, true, GroupStage<T>::N>(a.ct, c0 + k0, k1 - k0, a.sl, a.ms.wts, a.ms.A,
+                                                              inv_dt, sw, sA);
             // the last pass needs no group barrier: the particle is published
             // below, and the next ticket's barrier separates the tasks
             if (m + 1 < a.Ns && !group_sync(gw, gw + 1, G, a.st)) return;
@@ -155,7 +165,7 @@ __global__ void __launch_bounds__(kGroupThreads) k_mdf_groups(ResidentArgs<T> a)
 
 template <typename T, int KER>
 static int groups_capacity(ib_ctx *ctx, int *per_sm) {
-    const size_t smem = tile_stage_bytes<T>();
+    const size_t smem = group_stage_bytes<T>();
     void (*kern)(ResidentArgs<T>) = k_mdf_groups<T, KER>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, kern, kGroupThreads, smem);
@@ -183,7 +193,7 @@ int launch_mdf_groups(ib_ctx *ctx, const ResidentArgs<T> &a, cudaStream_t s) {
     const int groups = a.P < groups_max ? a.P : groups_max;
     void *args[] = {(void *)&a};
     cudaError_t e = cudaLaunchCooperativeKernel((const void *)k_mdf_groups<T, KER>, groups * kGroupCtas,
-                                                kGroupThreads, args, tile_stage_bytes<T>(), s);
+                                                kGroupThreads, args, group_stage_bytes<T>(), s);
     if (e != cudaSuccess) return set_error(IB_ERR_CUDA, "group kernel launch: %s", cudaGetErrorString(e));
     return IB_OK;
 }
