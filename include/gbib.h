@@ -166,6 +166,12 @@ GBIB_API int ib_ctx_read_timing(ib_ctx *ctx, int phase, double *ms_total,
 #define IB_PASSES_GROUPS 3
 GBIB_API int ib_ctx_set_pass_kernels(ib_ctx *ctx, int which);
 
+/* ---- CTAs per particle of the volume integrals (tuning knob) -----------
+ * Each particle's box is cut into this many slabs of cell planes, one CTA
+ * each (default 8; 1 <= n <= 32).  Results do not depend on it beyond the
+ * rounding of the partial sums' grouping.  IB_ERR_INVALID outside the range. */
+GBIB_API int ib_ctx_set_volume_split(ib_ctx *ctx, int ctas_per_particle);
+
 /* ---- velocity interpolation J: Eq. (u), Eq. (vi), Algorithm 1 -----------
  * U[l] = sum_ijk u(x_ijk) delta_h(x_ijk - X[l]) h^3 for l < M, where
  * delta_h(x) = h^-3 prod_a phi(x_a / h) (Sec. 2).  X[M][3] are absolute

@@ -43,7 +43,7 @@ PHASES = {"mdf_prep": 0, "mdf_passes": 1, "spread": 2, "interp": 3, "volume": 4,
 
 EXPORTS = ["ib_ctx_create", "ib_ctx_reserve", "ib_ctx_destroy", "ib_ctx_status",
            "ib_last_error", "ib_workspace_needed", "ib_ctx_sm_count",
-           "ib_ctx_set_timing", "ib_ctx_read_timing", "ib_ctx_set_pass_kernels",
+           "ib_ctx_set_timing", "ib_ctx_read_timing", "ib_ctx_set_pass_kernels", "ib_ctx_set_volume_split",
            "ib_interpolate", "ib_spread", "ib_multidirect_forcing",
            "particle_volume_integrals", "particle_force_torque",
            "particle_collide_update", "particle_volume_integrals_static",
@@ -105,6 +105,7 @@ def load(path: str = LIB_PATH):
         "ib_ctx_set_timing": (i, [p, i]),
         "ib_ctx_read_timing": (i, [p, i, ctypes.POINTER(d), ctypes.POINTER(i)]),
         "ib_ctx_set_pass_kernels": (i, [p, i]),
+        "ib_ctx_set_volume_split": (i, [p, i]),
         "ib_interpolate": (i, [p, p, p, i, p, i, p, p]),
         "ib_spread": (i, [p, p, i, p, p, p, i, p, p]),
         "ib_multidirect_forcing": (i, [p, p, p, p, p, i, d, i, i, p, p, p]),
@@ -216,6 +217,10 @@ class Context:
         "resident" or "groups" (see gbib.h; every choice gives bitwise the
         same result)."""
         self._check(self.lib.ib_ctx_set_pass_kernels(self.handle, PASSES[which]))
+
+    def set_volume_split(self, ctas_per_particle: int):
+        """CTAs per particle of the volume integrals (see gbib.h)."""
+        self._check(self.lib.ib_ctx_set_volume_split(self.handle, int(ctas_per_particle)))
 
     def read_timing(self, phase: str):
         """(total ms, launches) of one phase since the last read; resets it."""

@@ -39,7 +39,7 @@ __device__ __forceinline__ void block_sum(double v[NV]) {
 }
 
 // ---------------------------------------------------------------------------
-// volume integrals.  Grid = P * kVolSplit CTAs; CTA (p, s) walks a slab of
+// volume integrals.  Grid = P * nsplit CTAs; CTA (p, s) walks a slab of
 // cell planes of particle p's box.  Per plane it evaluates the level set
 // phi = |x - X_r|/R - 1 once per node (only for nodes within 1.75 h of the
 // surface: the corners of every cell whose centre lies within 0.8661 h of the
@@ -47,9 +47,10 @@ __device__ __forceinline__ void block_sum(double v[NV]) {
 // row, only the cells whose centre lies within R + 0.8661 h.  Cells whose
 // centre lies deeper than R - 0.8661 h have all corners inside (alpha = 1);
 // the others form alpha from their eight corner values.  The last CTA of a
-// particle (completion counter) adds the kVolSplit partial sums in slab order.
+// particle (completion counter) adds the nsplit partial sums in slab order.
 // ---------------------------------------------------------------------------
-constexpr int kVolSplit = 8;
+constexpr int kVolSplit = 8;       // default CTAs per particle (the context may choose another)
+constexpr int kVolMaxSplit = 32;
 constexpr int kVolThreads = 256;   // 8 warps
 constexpr int kVolMaxBox = 40;     // cells per axis of one particle's box (tabulated path)
 constexpr int kVolAx = kVolMaxBox + 1;
@@ -117,7 +118,7 @@ __device__ __forceinline__ int find_row(const int *pre, int nrows, int t) {
 // Per-row index ranges come from FP32 square roots widened by a cell; every
 // node and boundary cell is still tested exactly in FP64.
 template <typename T>
-__global__ void __launch_bounds__(kVolThreads) k_volume(CaseTab ct, int P,
+__global__ void __launch_bounds__(kVolThreads) k_volume(CaseTab ct, int P, int nsplit,
                                                         const double *__restrict__ Xr,
                                                         const double *__restrict__ radius,
                                                         double *__restrict__ partial,
@@ -130,7 +131,7 @@ __global__ void __launch_bounds__(kVolThreads) k_volume(CaseTab ct, int P,
     __shared__ int r_ia[kVolAx], r_ib[kVolAx], r_ic[kVolAx];
     __shared__ int p_node[kVolAx + 1], p_int[kVolAx + 1], p_bnd[kVolAx + 1];
     __shared__ int c_node[kVolAx], c_int[kVolAx], c_bnd[kVolAx];
-    const int p = blockIdx.x / kVolSplit, split = blockIdx.x % kVolSplit;
+    const int p = blockIdx.x / nsplit, split = blockIdx.x % nsplit;
     if (p >= P) return;
     const DevCase &cd = ct.of_particle(p);
     const DevGrid g = cd.g;
@@ -151,7 +152,7 @@ __global__ void __launch_bounds__(kVolThreads) k_volume(CaseTab ct, int P,
         }
         if (!ok && threadIdx.x == 0 && split == 0) raise_status(st, IB_ERR_UNSUPPORTED, p);
     }
-    const int t = (dims[2] + kVolSplit - 1) / kVolSplit;
+    const int t = (dims[2] + nsplit - 1) / nsplit;
     const int z0 = split * t, z1 = min(dims[2], z0 + t);
     if (ok && z0 < z1) {
         const long long N = (long long)g.n[0] * g.n[1] * g.n[2];
@@ -400,23 +401,23 @@ __global__ void __launch_bounds__(kVolThreads) k_volume(CaseTab ct, int P,
             for (int k = 0; k < 7; ++k) acc[k] = s_acc[k][0] * h3;
         }
     }
-    __shared__ double s_part[kVolSplit * 7];
+    __shared__ double s_part[kVolMaxSplit * 7];
     if (threadIdx.x == 0) {
-        double *dst = partial + ((size_t)p * kVolSplit + split) * 7;
+        double *dst = partial + ((size_t)p * nsplit + split) * 7;
         for (int k = 0; k < 7; ++k) dst[k] = acc[k];
         __threadfence();  // release: partials before the count
-        s_last = atomicAdd(done + p, 1u) == kVolSplit - 1;
+        s_last = atomicAdd(done + p, 1u) == (unsigned int)nsplit - 1;
         __threadfence();  // acquire: the count before the other partials
     }
     __syncthreads();
     if (s_last) {
         // the last CTA of the particle adds the partials in slab order
-        for (int i = threadIdx.x; i < kVolSplit * 7; i += blockDim.x) s_part[i] = partial[(size_t)p * kVolSplit * 7 + i];
+        for (int i = threadIdx.x; i < nsplit * 7; i += blockDim.x) s_part[i] = partial[(size_t)p * nsplit * 7 + i];
         __syncthreads();
     }
     if (s_last && threadIdx.x == 0) {
         double sum[7] = {0, 0, 0, 0, 0, 0, 0};
-        for (int sp = 0; sp < kVolSplit; ++sp)
+        for (int sp = 0; sp < nsplit; ++sp)
             for (int k = 0; k < 7; ++k) sum[k] += s_part[sp * 7 + k];
         if (Iu)
             for (int a = 0; a < 3; ++a) Iu[3 * p + a] = sum[a];
@@ -543,15 +544,16 @@ __global__ void k_newton_euler(CollideArgs a, const double *__restrict__ Fc, Dev
 template <typename T>
 static int run_volume(ib_ctx *ctx, Arena &ar, const CaseTab &ct, const ib_particles *pp, double *Iu,
                       double *Irxu, double *vol, cudaStream_t s) {
-    double *partial = ar.take<double>((size_t)pp->P * kVolSplit * 7);
+    const int nsplit = ctx->vol_split;
+    double *partial = ar.take<double>((size_t)pp->P * nsplit * 7);
     unsigned int *done = ar.take<unsigned int>(pp->P);
     if (!ar.ok())
         return oom_error(ar.used, ar.cap);
     PhaseTimer tm(ctx, IB_PHASE_VOLUME, s);
     cudaMemsetAsync(done, 0, sizeof(unsigned int) * pp->P, s);
     cudaFuncSetAttribute(k_volume<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kVolSmem);
-    k_volume<T><<<pp->P * kVolSplit, kVolThreads, kVolSmem, s>>>(ct, pp->P, pp->Xr, pp->radius, partial, done,
-                                                                 Iu, Irxu, vol, ctx->status);
+    k_volume<T><<<pp->P * nsplit, kVolThreads, kVolSmem, s>>>(ct, pp->P, nsplit, pp->Xr, pp->radius, partial,
+                                                               done, Iu, Irxu, vol, ctx->status);
     return check_launch("particle_volume_integrals");
 }
 
@@ -606,8 +608,8 @@ static int run_volume_static(const CaseTab &ct, const ib_particles *pp, double *
     unsigned int *done = nullptr;
     int rc = static_scratch(&partial, &st, &done);
     if (rc) return rc;
-    k_volume<T><<<pp->P * kVolSplit, kVolThreads, kVolSmem, s>>>(ct, pp->P, pp->Xr, pp->radius, partial, done,
-                                                                 Iu, Irxu, vol, st);
+    k_volume<T><<<pp->P * kVolSplit, kVolThreads, kVolSmem, s>>>(ct, pp->P, kVolSplit, pp->Xr, pp->radius,
+                                                                 partial, done, Iu, Irxu, vol, st);
     return check_launch("particle_volume_integrals_static");
 }
 
@@ -625,7 +627,7 @@ int particle_volume_integrals(ib_ctx *ctx, const ib_grid *grid, const void *u, c
     if (!parts || parts->P < 0) return set_error(IB_ERR_INVALID, "bad particles");
     if (parts->P == 0) return IB_OK;
     if (!u || !parts->Xr || !parts->radius) return set_error(IB_ERR_INVALID, "NULL array");
-    if ((long long)parts->P * kVolSplit > (1LL << 31) - 1) return set_error(IB_ERR_UNSUPPORTED, "too many particles");
+    if ((long long)parts->P * kVolMaxSplit > (1LL << 31) - 1) return set_error(IB_ERR_UNSUPPORTED, "too many particles");
     const CaseTab ct = single_case(grid, (void *)u, nullptr, parts->P);
     Arena ar(ctx);
     if (grid->prec == IB_F64)
@@ -641,7 +643,7 @@ int ib_batch_volume_integrals(ib_ctx *ctx, int ncases, const ib_case *cases, con
     if (!parts->Xr || !parts->radius || !Iu || !Irxu || !vol) return set_error(IB_ERR_INVALID, "NULL array");
     for (int c = 0; c < ncases && cases; ++c)
         if (!cases[c].u) return set_error(IB_ERR_INVALID, "case %d: NULL field", c);
-    if ((long long)parts->P * kVolSplit > (1LL << 31) - 1) return set_error(IB_ERR_UNSUPPORTED, "too many particles");
+    if ((long long)parts->P * kVolMaxSplit > (1LL << 31) - 1) return set_error(IB_ERR_UNSUPPORTED, "too many particles");
     Arena ar(ctx);
     CaseTab ct;
     int rc = build_case_table(ctx, ar, ncases, cases, parts->P, 1, ct, (cudaStream_t)stream);

@@ -193,3 +193,38 @@ def test_batch_rejects_bad_ranges_and_mixed_precision(api):
     # nothing was written
     assert torch.equal(u, u2)
     ctx.close()
+
+
+def test_autotune_on_a_batch_keeps_results(api):
+    """The tuner times every launch choice on a real batch step and leaves the
+    fastest set; the forcing results do not depend on the choice."""
+    from paper_2408_14140_gb300 import autotune
+    cases = uneven_cases(71)
+    ctx = api.Context()
+    us, parts_l, marks_l, parts, marks, ranges, mranges, hs = batch_inputs(api, cases, 1)
+    base = [u.clone() for u in us]
+    outs = {}
+
+    def step():
+        for u, b in zip(us, base):
+            u.copy_(b)
+        ctx.ib_batch_volume_integrals(us, hs, parts, ranges)
+        F = ctx.ib_batch_multidirect_forcing(us, hs, parts, marks, ranges, cases[0].Ns, cases[0].dt)
+        outs[autotune_key[0]] = ([u.clone() for u in us], F.clone())
+
+    autotune_key = [None]
+    for form in ("wavefront", "groups"):
+        ctx.set_pass_kernels(form)
+        autotune_key[0] = form
+        step()
+    ctx.status()
+    for a, b in zip(outs["wavefront"][0], outs["groups"][0]):
+        assert torch.equal(a, b)
+    assert torch.equal(outs["wavefront"][1], outs["groups"][1])
+    autotune_key[0] = "tuned"
+    res = autotune.tune([ctx], step, warmup=1, reps=2, steps_per_rep=1)
+    ctx.status()
+    assert res["choice"]["pass_kernels"] in ("wavefront", "groups")
+    assert res["choice"]["volume_split"] in (4, 8, 16)
+    assert len(res["table"]) == 6 and all(ms > 0 for _, ms in res["table"])
+    ctx.close()
