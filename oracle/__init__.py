@@ -67,6 +67,10 @@ def _load():
     lib.or_pvf_ellipsoid_volume.argtypes = [p, d, p, p, p]
     lib.or_volume_integrals.restype = None
     lib.or_volume_integrals.argtypes = [p, d, p, p, i, p, p, p, p, p]
+    lib.or_volume_integrals_ellipsoid.restype = None
+    lib.or_volume_integrals_ellipsoid.argtypes = [p, d, p, p, i, p, p, p, p, p]
+    lib.or_drag_force.restype = None
+    lib.or_drag_force.argtypes = [i, p, p, p, d, d, p]
     lib.or_force_torque.restype = None
     lib.or_force_torque.argtypes = [i, p, p, p, p, d, p, p]
     lib.or_collide_update.restype = None
@@ -187,6 +191,35 @@ def volume_integrals(n, h, org, u, Xr, radius):
                                 _ptr(Xr), _ptr(radius), _ptr(Iu), _ptr(Irxu),
                                 _ptr(vol))
     return Iu, Irxu, vol
+
+
+def volume_integrals_ellipsoid(n, h, org, u, Xr, axes):
+    """(Iu[P,3], Irxu[P,3], vol[P]) of axis-aligned ellipsoids of semi-axes
+    axes[P,3] through their PVF (the sphere is a = b = c = R)."""
+    n, org = _grid(n, org)
+    u = _f64(u)
+    Xr = _f64(Xr).reshape(-1, 3)
+    axes = _f64(axes).reshape(-1, 3)
+    P = Xr.shape[0]
+    Iu = np.zeros((P, 3))
+    Irxu = np.zeros((P, 3))
+    vol = np.zeros(P)
+    _load().or_volume_integrals_ellipsoid(_ptr(n), float(h), _ptr(org), _ptr(u), P,
+                                          _ptr(Xr), _ptr(axes), _ptr(Iu), _ptr(Irxu),
+                                          _ptr(vol))
+    return Iu, Irxu, vol
+
+
+def drag_force(F_ib, Iu_new, Iu_old, rho_f, dt):
+    """F_D[P,3] of Eq. FD: F_ib + rho_f (Iu^{n+1} - Iu^n) / dt."""
+    F_ib = _f64(F_ib).reshape(-1, 3)
+    Iu_new = _f64(Iu_new).reshape(-1, 3)
+    Iu_old = _f64(Iu_old).reshape(-1, 3)
+    P = F_ib.shape[0]
+    FD = np.zeros((P, 3))
+    _load().or_drag_force(P, _ptr(F_ib), _ptr(Iu_new), _ptr(Iu_old), float(rho_f), float(dt),
+                          _ptr(FD))
+    return FD
 
 
 def force_torque(moff, R, dV, F, rho_f):

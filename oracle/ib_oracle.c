@@ -382,67 +382,98 @@ double or_pvf_ellipsoid_volume(const int n[3], double h, const double org[3],
 }
 
 /* ------------------------------------------------------------------------ */
-/* Volume integrals of a sphere through its PVF (Sec. 3.2.2 "flow
+/* Volume integrals of a particle through its PVF (Sec. 3.2.2 "flow
  * unsteadiness" terms, Sec. 4.1):
  *   Iu   = sum_c alpha_c u_c h^3
  *   Irxu = sum_c alpha_c (x_c - X_r) x u_c h^3
  *   vol  = sum_c alpha_c h^3
- * The sphere's level set is phi = |x - X_r| / R - 1, the ellipsoid formula
- * with a = b = c = R.  Cells are visited around the particle centre without
- * wrapping, so x_c - X_r is already the nearest periodic image; only the
- * field index wraps.                                                         */
+ * with alpha from the level set of an axis-aligned ellipsoid of semi-axes
+ * (a, b, c) centred at X_r, Eq. (level-set function of spheroidal
+ * geometries); a sphere is a = b = c = R.  Cells are visited around the
+ * particle centre without wrapping, so x_c - X_r is already the nearest
+ * periodic image; only the field index wraps.                              */
 /* ------------------------------------------------------------------------ */
+static void volume_integrals_one(const int n[3], double h, const double org[3], const double *u,
+                                 const double c[3], const double axes[3], double *Iu, double *Irxu,
+                                 double *vol)
+{
+    long N = (long)n[0] * n[1] * n[2];
+    long lo[3], hi[3];
+    for (int a = 0; a < 3; ++a) {
+        lo[a] = (long)floor((c[a] - axes[a] - org[a]) / h) - 1;
+        hi[a] = (long)floor((c[a] + axes[a] - org[a]) / h) + 1;
+    }
+    double su[3] = {0, 0, 0}, sw[3] = {0, 0, 0}, sv = 0.0;
+    double h3 = h * h * h;
+    for (long k = lo[2]; k <= hi[2]; ++k)
+        for (long j = lo[1]; j <= hi[1]; ++j)
+            for (long i = lo[0]; i <= hi[0]; ++i) {
+                double phi[8];
+                for (int m = 0; m < 8; ++m) {
+                    double x = org[0] + (double)(i + (m & 1)) * h;
+                    double y = org[1] + (double)(j + ((m >> 1) & 1)) * h;
+                    double z = org[2] + (double)(k + ((m >> 2) & 1)) * h;
+                    phi[m] = level_set_ellipsoid(x, y, z, c, axes);
+                }
+                double al = pvf_alpha(phi);
+                if (al == 0.0)
+                    continue;
+                long cc = cell_index(n, i, j, k);
+                double uc[3] = {u[cc], u[N + cc], u[2 * N + cc]};
+                double r[3] = {org[0] + ((double)i + 0.5) * h - c[0],
+                               org[1] + ((double)j + 0.5) * h - c[1],
+                               org[2] + ((double)k + 0.5) * h - c[2]};
+                double wv = al * h3;
+                su[0] += wv * uc[0];
+                su[1] += wv * uc[1];
+                su[2] += wv * uc[2];
+                sw[0] += wv * (r[1] * uc[2] - r[2] * uc[1]);
+                sw[1] += wv * (r[2] * uc[0] - r[0] * uc[2]);
+                sw[2] += wv * (r[0] * uc[1] - r[1] * uc[0]);
+                sv += wv;
+            }
+    for (int a = 0; a < 3; ++a) {
+        Iu[a] = su[a];
+        Irxu[a] = sw[a];
+    }
+    *vol = sv;
+}
+
 void or_volume_integrals(const int n[3], double h, const double org[3],
                          const double *u, int P, const double *Xr,
                          const double *radius, double *Iu, double *Irxu,
                          double *vol)
 {
-    long N = (long)n[0] * n[1] * n[2];
 #pragma omp parallel for schedule(dynamic, 1)
     for (int p = 0; p < P; ++p) {
-        const double *c = Xr + 3 * p;
-        double Rp = radius[p];
-        double axes[3] = {Rp, Rp, Rp};
-        long lo[3], hi[3];
-        for (int a = 0; a < 3; ++a) {
-            lo[a] = (long)floor((c[a] - Rp - org[a]) / h) - 1;
-            hi[a] = (long)floor((c[a] + Rp - org[a]) / h) + 1;
-        }
-        double su[3] = {0, 0, 0}, sw[3] = {0, 0, 0}, sv = 0.0;
-        double h3 = h * h * h;
-        for (long k = lo[2]; k <= hi[2]; ++k)
-            for (long j = lo[1]; j <= hi[1]; ++j)
-                for (long i = lo[0]; i <= hi[0]; ++i) {
-                    double phi[8];
-                    for (int m = 0; m < 8; ++m) {
-                        double x = org[0] + (double)(i + (m & 1)) * h;
-                        double y = org[1] + (double)(j + ((m >> 1) & 1)) * h;
-                        double z = org[2] + (double)(k + ((m >> 2) & 1)) * h;
-                        phi[m] = level_set_ellipsoid(x, y, z, c, axes);
-                    }
-                    double al = pvf_alpha(phi);
-                    if (al == 0.0)
-                        continue;
-                    long cc = cell_index(n, i, j, k);
-                    double uc[3] = {u[cc], u[N + cc], u[2 * N + cc]};
-                    double r[3] = {org[0] + ((double)i + 0.5) * h - c[0],
-                                   org[1] + ((double)j + 0.5) * h - c[1],
-                                   org[2] + ((double)k + 0.5) * h - c[2]};
-                    double wv = al * h3;
-                    su[0] += wv * uc[0];
-                    su[1] += wv * uc[1];
-                    su[2] += wv * uc[2];
-                    sw[0] += wv * (r[1] * uc[2] - r[2] * uc[1]);
-                    sw[1] += wv * (r[2] * uc[0] - r[0] * uc[2]);
-                    sw[2] += wv * (r[0] * uc[1] - r[1] * uc[0]);
-                    sv += wv;
-                }
-        for (int a = 0; a < 3; ++a) {
-            Iu[3 * p + a] = su[a];
-            Irxu[3 * p + a] = sw[a];
-        }
-        vol[p] = sv;
+        double axes[3] = {radius[p], radius[p], radius[p]};
+        volume_integrals_one(n, h, org, u, Xr + 3 * p, axes, Iu + 3 * p, Irxu + 3 * p, vol + p);
     }
+}
+
+/* The same for ellipsoids: axes[P][3] = (a, b, c) of each particle. */
+void or_volume_integrals_ellipsoid(const int n[3], double h, const double org[3],
+                                   const double *u, int P, const double *Xr,
+                                   const double *axes, double *Iu, double *Irxu,
+                                   double *vol)
+{
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int p = 0; p < P; ++p)
+        volume_integrals_one(n, h, org, u, Xr + 3 * p, axes + 3 * p, Iu + 3 * p, Irxu + 3 * p, vol + p);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Drag diagnostic, Eq. (FD): the marker-force sum plus the rate of change of
+ * the velocity integral over the particle volume,
+ *   F_D = -rho_f sum_l F_l dV_l + rho_f d/dt int_Vp u dV
+ *       = F_ib + rho_f (Iu^{n+1} - Iu^n) / dt,
+ * the time derivative taken as the difference of the PVF integrals.        */
+/* ------------------------------------------------------------------------ */
+void or_drag_force(int P, const double *Fib, const double *Iu_new, const double *Iu_old,
+                   double rho_f, double dt, double *FD)
+{
+    for (long q = 0; q < 3L * P; ++q)
+        FD[q] = Fib[q] + rho_f * (Iu_new[q] - Iu_old[q]) / dt;
 }
 
 /* ------------------------------------------------------------------------ */

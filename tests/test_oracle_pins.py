@@ -503,3 +503,67 @@ def test_collision_conserves_momentum():
                                case.n, case.h, case.phys(), 1e-3, *_zeros(case.P))[3]
     assert np.any(Fc != 0)
     assert np.max(np.abs(Fc.sum(axis=0))) < 1e-9 * np.max(np.abs(Fc))
+
+
+# ------------------------------------------- ellipsoid PVF and drag (NEXT-3)
+@pytest.mark.parametrize("shape,doh,val", [r for r in _golden() if r[0] == "ellipsoid" and r[1] <= 32])
+def test_volume_integrals_ellipsoid_table(shape, doh, val):
+    """or_volume_integrals_ellipsoid: the PVF volume of the paper's ellipsoid
+    (Sec. 4.1 ellipsoid table; axes (0.4, 0.6, 0.4), centre (1, 1, 1),
+    domain 2^3) to every printed digit."""
+    h = 0.8 / doh
+    n = [int(round(2.0 / h))] * 3
+    u = np.zeros((3,) + tuple(n))
+    _, _, vol = oracle.volume_integrals_ellipsoid(n, h, (0, 0, 0), u, [[1, 1, 1]], [[0.4, 0.6, 0.4]])
+    tol = 0.5 * 10.0 ** (-(len(val.split(".")[1])))
+    assert abs(vol[0] - float(val)) <= tol
+
+
+def test_volume_integrals_ellipsoid_reduces_to_sphere():
+    """Equal semi-axes give the sphere's integrals."""
+    N = 32
+    h = 1.0 / N
+    rng = synth.SplitMix64(11)
+    u = synth.fourier_field((N,) * 3, 5, rng, h)
+    c = [[0.43, 0.52, 0.61], [0.1, 0.95, 0.5]]
+    a = oracle.volume_integrals((N,) * 3, h, (0, 0, 0), u, c, [0.2, 0.15])
+    b = oracle.volume_integrals_ellipsoid((N,) * 3, h, (0, 0, 0), u, c, [[0.2] * 3, [0.15] * 3])
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)
+
+
+def test_volume_integrals_ellipsoid_closed_forms():
+    """u = const gives Iu = c vol and a zero first moment for a node-centred
+    ellipsoid; solid rotation u = w x r gives Irxu -> I w with the ellipsoid's
+    inertia I = V/5 diag(b^2 + c^2, a^2 + c^2, a^2 + b^2), V = 4/3 pi abc,
+    with second-order convergence."""
+    ax = np.array([0.3, 0.2, 0.25])
+    w = np.array([0.3, -1.2, 0.7])
+    V = 4 / 3 * math.pi * np.prod(ax)
+    inertia = V / 5 * np.array([ax[1] ** 2 + ax[2] ** 2, ax[0] ** 2 + ax[2] ** 2, ax[0] ** 2 + ax[1] ** 2])
+    errs = []
+    for N in (20, 40, 80):
+        h = 1.0 / N
+        c = np.array([0.5, 0.5, 0.5])
+        cst = np.array([1.5, -2.0, 0.25])
+        u = np.broadcast_to(cst[:, None, None, None], (3, N, N, N)).copy()
+        Iu, Irxu, vol = oracle.volume_integrals_ellipsoid((N,) * 3, h, (0, 0, 0), u, [c], [ax])
+        assert np.allclose(Iu[0], cst * vol[0], rtol=1e-11, atol=0)
+        assert np.max(np.abs(Irxu[0])) < 1e-14
+        xs = (np.arange(N) + 0.5) * h - 0.5
+        Z, Y, X = np.meshgrid(xs, xs, xs, indexing="ij")
+        r = np.stack([X, Y, Z])
+        ur = np.stack([w[1] * r[2] - w[2] * r[1], w[2] * r[0] - w[0] * r[2], w[0] * r[1] - w[1] * r[0]])
+        Iu, Irxu, vol = oracle.volume_integrals_ellipsoid((N,) * 3, h, (0, 0, 0), ur, [c], [ax])
+        exact = inertia * w
+        errs.append(max(np.max(np.abs(Irxu[0] - exact)) / np.max(np.abs(exact)), abs(vol[0] - V) / V))
+    assert errs[2] < errs[0] / 8
+
+
+def test_drag_force_definition():
+    """Eq. FD by hand: F_D = F_ib + rho_f (Iu_new - Iu_old) / dt."""
+    Fib = [[1.0, 2.0, 3.0], [-1.0, 0.0, 0.5]]
+    Inew = [[1.0, 1.0, 1.0], [0.0, 2.0, 0.0]]
+    Iold = [[0.0, 0.0, 0.0], [0.0, 1.0, 0.25]]
+    FD = oracle.drag_force(Fib, Inew, Iold, 2.0, 0.5)
+    assert np.array_equal(FD, [[5.0, 6.0, 7.0], [-1.0, 4.0, -0.5]])
