@@ -216,6 +216,28 @@ GBIB_API int particle_volume_integrals(ib_ctx *ctx, const ib_grid *grid, const v
                               const ib_particles *parts, double *Iu,
                               double *Irxu, double *vol, void *stream);
 
+/* ---- PVF volume integrals of ellipsoids: Sec. 4.1, Eq. (level-set
+ * function of spheroidal geometries) -----------------------------------
+ * As particle_volume_integrals, for P axis-aligned ellipsoids centred at
+ * Xr[P][3] with semi-axes axes[P][3] = (a, b, c): phi = sqrt((x/a)^2 +
+ * (y/b)^2 + (z/c)^2) - 1 at the nodes, alpha from the eight corners of each
+ * cell.  A sphere is a = b = c = R.  Outputs Iu[P][3], Irxu[P][3], vol[P]
+ * (FP64, overwritten).  IB_ERR_NONFINITE for a non-finite centre or a
+ * non-positive axis; IB_ERR_UNSUPPORTED when an ellipsoid's box exceeds the
+ * grid.                                                                     */
+GBIB_API int particle_volume_integrals_ellipsoid(ib_ctx *ctx, const ib_grid *grid, const void *u,
+                                                 int P, const double *Xr, const double *axes,
+                                                 double *Iu, double *Irxu, double *vol,
+                                                 void *stream);
+
+/* ---- drag diagnostic: Sec. 4.2, Eq. (FD) ----------------------------------
+ * F_D[P][3] = -rho_f sum_l F_l dV_l + rho_f d/dt int_Vp u dV, with the first
+ * term given as F_ib (particle_force_torque) and the time derivative as
+ * (Iu_new - Iu_old) / dt of the PVF integrals.  FP64, overwritten.          */
+GBIB_API int particle_drag_force(ib_ctx *ctx, int P, const double *F_ib, const double *Iu_new,
+                                 const double *Iu_old, double rho_f, double dt, double *F_D,
+                                 void *stream);
+
 /* ---- batches of independent cases (continuous batching, serving) -------
  * A batch runs many independent periodic cases -- each with its own grid
  * size, field and particles -- through the same kernel launches.  The

@@ -47,7 +47,8 @@ EXPORTS = ["ib_ctx_create", "ib_ctx_reserve", "ib_ctx_destroy", "ib_ctx_status",
            "ib_interpolate", "ib_spread", "ib_multidirect_forcing",
            "particle_volume_integrals", "particle_force_torque",
            "particle_collide_update", "particle_volume_integrals_static",
-           "ib_batch_multidirect_forcing", "ib_batch_volume_integrals", "ib_batch_collide_update"]
+           "ib_batch_multidirect_forcing", "ib_batch_volume_integrals", "ib_batch_collide_update",
+           "particle_volume_integrals_ellipsoid", "particle_drag_force"]
 
 
 class IBError(RuntimeError):
@@ -114,6 +115,8 @@ def load(path: str = LIB_PATH):
         "particle_force_torque": (i, [p, p, p, p, d, p, p, p]),
         "particle_collide_update": (i, [p, p, p, p, d, p, p, p, p, p, p, p, p]),
         "ib_batch_multidirect_forcing": (i, [p, i, p, p, p, i, d, i, i, p, p]),
+        "particle_volume_integrals_ellipsoid": (i, [p, p, p, i, p, p, p, p, p, p]),
+        "particle_drag_force": (i, [p, i, p, p, p, d, d, p, p]),
         "ib_batch_volume_integrals": (i, [p, i, p, p, p, p, p, p]),
         "ib_batch_collide_update": (i, [p, i, p, p, p, d, p, p, p, p, p, p, p, p]),
     }
@@ -335,6 +338,40 @@ class Context:
         self._call(self.lib.particle_volume_integrals, self.handle, ctypes.byref(g), _ptr(u),
                    ctypes.byref(ps), _ptr(Iu), _ptr(Irxu), _ptr(vol), _stream(stream))
         return Iu, Irxu, vol
+
+    def particle_volume_integrals_ellipsoid(self, u, h, Xr, axes, origin=(0.0, 0.0, 0.0), out=None,
+                                            stream=None):
+        """(Iu[P,3], Irxu[P,3], vol[P]) through the PVF of axis-aligned
+        ellipsoids (semi-axes axes[P,3])."""
+        n = (u.shape[3], u.shape[2], u.shape[1])
+        _need(u, "u", u.dtype, (3, n[2], n[1], n[0]))
+        P = Xr.shape[0]
+        _need(Xr, "Xr", torch.float64, (P, 3))
+        _need(axes, "axes", torch.float64, (P, 3))
+        if out is None:
+            out = (torch.empty((P, 3), dtype=torch.float64, device=u.device),
+                   torch.empty((P, 3), dtype=torch.float64, device=u.device),
+                   torch.empty((P,), dtype=torch.float64, device=u.device))
+        Iu, Irxu, vol = out
+        _need(Iu, "Iu", torch.float64, (P, 3))
+        _need(Irxu, "Irxu", torch.float64, (P, 3))
+        _need(vol, "vol", torch.float64, (P,))
+        g = self._grid_of(u, n, h, origin)
+        self._call(self.lib.particle_volume_integrals_ellipsoid, self.handle, ctypes.byref(g), _ptr(u), P,
+                   _ptr(Xr), _ptr(axes), _ptr(Iu), _ptr(Irxu), _ptr(vol), _stream(stream))
+        return Iu, Irxu, vol
+
+    def particle_drag_force(self, F_ib, Iu_new, Iu_old, rho_f, dt, out=None, stream=None):
+        """F_D[P,3] of Eq. FD = F_ib + rho_f (Iu_new - Iu_old) / dt."""
+        P = F_ib.shape[0]
+        for t, nm in ((F_ib, "F_ib"), (Iu_new, "Iu_new"), (Iu_old, "Iu_old")):
+            _need(t, nm, torch.float64, (P, 3))
+        if out is None:
+            out = torch.empty((P, 3), dtype=torch.float64, device=F_ib.device)
+        _need(out, "F_D", torch.float64, (P, 3))
+        self._call(self.lib.particle_drag_force, self.handle, P, _ptr(F_ib), _ptr(Iu_new), _ptr(Iu_old),
+                   float(rho_f), float(dt), _ptr(out), _stream(stream))
+        return out
 
     def particle_force_torque(self, parts, marks, F, rho_f, out=None, stream=None):
         """(F_ib[P,3], T_ib[P,3]) = (-rho_f sum F dV, -rho_f sum R x F dV)."""

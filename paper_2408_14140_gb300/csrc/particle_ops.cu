@@ -108,6 +108,64 @@ __device__ __forceinline__ int find_row(const int *pre, int nrows, int t) {
     return a;
 }
 
+// End of a volume-integral CTA: the fixed-order CTA sum of the 7 partial
+// sums, scaled by h^3, is stored as slab `split` of particle p; the last slab
+// of the particle to finish (completion counter) adds the nsplit slabs in
+// order and writes the particle's integrals.
+__device__ void volume_finish(double acc[7], double h, int p, int split, int nsplit, double *__restrict__ partial,
+                              unsigned int *__restrict__ done, double *Iu, double *Irxu, double *vol) {
+    __shared__ int s_last;
+    // fixed-order CTA sum of the 7 partials through shared memory: 7 warps,
+    // one per quantity, each lane adding 8 entries then a shuffle tree (FP64
+    // adds are scarce on this part: a shuffle tree over all 256 threads would
+    // cost more FP64 work than a thin slab's cells)
+    {
+        __shared__ double s_acc[7][kVolThreads];
+#pragma unroll
+        for (int k = 0; k < 7; ++k) s_acc[k][threadIdx.x] = acc[k];
+        __syncthreads();
+        const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5;
+        if (wq < 7) {
+            double x = 0.0;
+#pragma unroll
+            for (int m = 0; m < kVolThreads / 32; ++m) x += s_acc[wq][lane + 32 * m];
+            for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+            if (lane == 0) s_acc[wq][0] = x;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const double h3 = h * h * h;
+#pragma unroll
+            for (int k = 0; k < 7; ++k) acc[k] = s_acc[k][0] * h3;
+        }
+    }
+    __shared__ double s_part[kVolMaxSplit * 7];
+    if (threadIdx.x == 0) {
+        double *dst = partial + ((size_t)p * nsplit + split) * 7;
+        for (int k = 0; k < 7; ++k) dst[k] = acc[k];
+        __threadfence();  // release: partials before the count
+        s_last = atomicAdd(done + p, 1u) == (unsigned int)nsplit - 1;
+        __threadfence();  // acquire: the count before the other partials
+    }
+    __syncthreads();
+    if (s_last) {
+        // the last CTA of the particle adds the partials in slab order
+        for (int i = threadIdx.x; i < nsplit * 7; i += blockDim.x) s_part[i] = partial[(size_t)p * nsplit * 7 + i];
+        __syncthreads();
+    }
+    if (s_last && threadIdx.x == 0) {
+        double sum[7] = {0, 0, 0, 0, 0, 0, 0};
+        for (int sp = 0; sp < nsplit; ++sp)
+            for (int k = 0; k < 7; ++k) sum[k] += s_part[sp * 7 + k];
+        if (Iu)
+            for (int a = 0; a < 3; ++a) Iu[3 * p + a] = sum[a];
+        if (Irxu)
+            for (int a = 0; a < 3; ++a) Irxu[3 * p + a] = sum[3 + a];
+        if (vol) vol[p] = sum[6];
+        done[p] = 0;  // ready for the next call
+    }
+}
+
 // Most of this kernel's cost is GB300's low FP64 rate, and FP64 pipe time is
 // charged per warp instruction whatever the number of active lanes.  So each
 // plane is walked as flat lists that keep warps full and uniform:
@@ -125,7 +183,6 @@ __global__ void __launch_bounds__(kVolThreads) k_volume(CaseTab ct, int P, int n
                                                         unsigned int *__restrict__ done, double *Iu,
                                                         double *Irxu, double *vol, DevStatus *st) {
     extern __shared__ __align__(16) double s_vol[];
-    __shared__ int s_last;
     // per-row work lists (rows <= kVolAx)
     __shared__ int r_na[kVolAx], r_nb[kVolAx], r_nc[2][kVolAx], r_ca[kVolAx], r_cb[kVolAx];
     __shared__ int r_ia[kVolAx], r_ib[kVolAx], r_ic[kVolAx];
@@ -377,55 +434,129 @@ __global__ void __launch_bounds__(kVolThreads) k_volume(CaseTab ct, int P, int n
             }
         }
     }
-    // fixed-order CTA sum of the 7 partials through shared memory: 7 warps,
-    // one per quantity, each lane adding 8 entries then a shuffle tree (FP64
-    // adds are scarce on this part: a shuffle tree over all 256 threads would
-    // cost more FP64 work than a thin slab's cells)
-    {
-        __shared__ double s_acc[7][kVolThreads];
+    volume_finish(acc, g.h, p, split, nsplit, partial, done, Iu, Irxu, vol);
+}
+
+// ---------------------------------------------------------------------------
+// Volume integrals of axis-aligned ellipsoids (semi-axes a, b, c), through
+// the level set of Eq. (level-set function of spheroidal geometries).  Grid =
+// P * nsplit CTAs, CTA (p, s) walks a slab of cell planes of particle p's
+// box: the level set is evaluated once per node into two rolling node planes
+// in shared memory, and every cell of the plane forms alpha from its eight
+// corners (cells with alpha = 0 are skipped).  Boxes wider than kEllAx - 1
+// cells evaluate the corners per cell.  The same sums as the oracle, grouped
+// per CTA then per slab.
+// ---------------------------------------------------------------------------
+constexpr int kEllAx = 65;
+constexpr size_t kEllSmem = 2 * (size_t)kEllAx * kEllAx * sizeof(double);
+
+__device__ __forceinline__ double pvf_alpha8(const double ph[8]) {
+    double num = 0.0, den = 0.0;
 #pragma unroll
-        for (int k = 0; k < 7; ++k) s_acc[k][threadIdx.x] = acc[k];
-        __syncthreads();
-        const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5;
-        if (wq < 7) {
-            double x = 0.0;
-#pragma unroll
-            for (int m = 0; m < kVolThreads / 32; ++m) x += s_acc[wq][lane + 32 * m];
-            for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
-            if (lane == 0) s_acc[wq][0] = x;
+    for (int m = 0; m < 8; ++m) {
+        num += fmax(-ph[m], 0.0);
+        den += fabs(ph[m]);
+    }
+    return den > 0.0 ? num / den : 0.5;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kVolThreads) k_volume_ellipsoid(CaseTab ct, int P, int nsplit,
+                                                                  const double *__restrict__ Xr,
+                                                                  const double *__restrict__ axes,
+                                                                  double *__restrict__ partial,
+                                                                  unsigned int *__restrict__ done, double *Iu,
+                                                                  double *Irxu, double *vol, DevStatus *st) {
+    extern __shared__ __align__(16) double s_phi[];
+    const int p = blockIdx.x / nsplit, split = blockIdx.x % nsplit;
+    if (p >= P) return;
+    const DevCase cd = ct.of_particle(p);
+    const DevGrid g = cd.g;
+    const T *__restrict__ u = (const T *)cd.u;
+    const double c[3] = {Xr[3 * p], Xr[3 * p + 1], Xr[3 * p + 2]};
+    const double ax[3] = {axes[3 * p], axes[3 * p + 1], axes[3 * p + 2]};
+    double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+    bool ok = finite3(c) && finite3(ax) && ax[0] > 0.0 && ax[1] > 0.0 && ax[2] > 0.0;
+    if (!ok && threadIdx.x == 0 && split == 0) raise_status(st, IB_ERR_NONFINITE, p);
+    int lo[3] = {0, 0, 0}, dims[3] = {0, 0, 0};
+    if (ok) {
+        for (int a = 0; a < 3; ++a) {
+            const long long l = (long long)floor((c[a] - ax[a] - g.org[a]) * g.inv_h) - 1;
+            const long long hg = (long long)floor((c[a] + ax[a] - g.org[a]) * g.inv_h) + 1;
+            lo[a] = (int)l;
+            dims[a] = (int)(hg - l + 1);
+            if (dims[a] > g.n[a] || l < INT_MIN / 2 || l > INT_MAX / 2) ok = false;
         }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            const double h3 = g.h * g.h * g.h;
+        if (!ok && threadIdx.x == 0 && split == 0) raise_status(st, IB_ERR_UNSUPPORTED, p);
+    }
+    const int t = (dims[2] + nsplit - 1) / nsplit;
+    const int z0 = split * t, z1 = min(dims[2], z0 + t);
+    if (ok && z0 < z1) {
+        const long long N = (long long)g.n[0] * g.n[1] * g.n[2];
+        const double h = g.h;
+        const double ia[3] = {1.0 / ax[0], 1.0 / ax[1], 1.0 / ax[2]};
+        auto level = [&](int i, int j, int k) {  // node (lo + (i, j, k)): x_node = org + index h
+            const double x = (g.org[0] + (double)(lo[0] + i) * h - c[0]) * ia[0];
+            const double y = (g.org[1] + (double)(lo[1] + j) * h - c[1]) * ia[1];
+            const double z = (g.org[2] + (double)(lo[2] + k) * h - c[2]) * ia[2];
+            return sqrt(x * x + y * y + z * z) - 1.0;
+        };
+        auto add_cell = [&](int i, int j, int k, double al) {
+            const long long cc = ((long long)wrap_int(lo[2] + k, g.n[2]) * g.n[1] + wrap_int(lo[1] + j, g.n[1])) *
+                                     g.n[0] + wrap_int(lo[0] + i, g.n[0]);
+            const double r[3] = {g.org[0] + ((double)(lo[0] + i) + 0.5) * h - c[0],
+                                 g.org[1] + ((double)(lo[1] + j) + 0.5) * h - c[1],
+                                 g.org[2] + ((double)(lo[2] + k) + 0.5) * h - c[2]};
+            const double u0 = (double)u[cc], u1 = (double)u[N + cc], u2 = (double)u[2 * N + cc];
+            acc[0] += al * u0;
+            acc[1] += al * u1;
+            acc[2] += al * u2;
+            acc[3] += al * (r[1] * u2 - r[2] * u1);
+            acc[4] += al * (r[2] * u0 - r[0] * u2);
+            acc[5] += al * (r[0] * u1 - r[1] * u0);
+            acc[6] += al;
+        };
+        const int nx = dims[0] + 1, ny = dims[1] + 1;
+        if (nx <= kEllAx && ny <= kEllAx) {
+            const int plane = nx * ny;
+            auto node_plane = [&](int kn, double *buf) {
+                for (int q = threadIdx.x; q < plane; q += blockDim.x) buf[q] = level(q % nx, q / nx, kn);
+            };
+            node_plane(z0, s_phi + (z0 & 1) * plane);
+            for (int kz = z0; kz < z1; ++kz) {
+                node_plane(kz + 1, s_phi + ((kz + 1) & 1) * plane);
+                __syncthreads();
+                const double *b0 = s_phi + (kz & 1) * plane, *b1 = s_phi + ((kz + 1) & 1) * plane;
+                for (int q = threadIdx.x; q < dims[0] * dims[1]; q += blockDim.x) {
+                    const int j = q / dims[0], i = q - j * dims[0];
+                    const int qn = j * nx + i;
+                    const double ph[8] = {b0[qn], b0[qn + 1], b0[qn + nx], b0[qn + nx + 1],
+                                          b1[qn], b1[qn + 1], b1[qn + nx], b1[qn + nx + 1]};
+                    const double al = pvf_alpha8(ph);
+                    if (al != 0.0) add_cell(i, j, kz, al);
+                }
+                __syncthreads();
+            }
+        } else {
+            for (int kz = z0; kz < z1; ++kz)
+                for (int q = threadIdx.x; q < dims[0] * dims[1]; q += blockDim.x) {
+                    const int j = q / dims[0], i = q - j * dims[0];
+                    double ph[8];
 #pragma unroll
-            for (int k = 0; k < 7; ++k) acc[k] = s_acc[k][0] * h3;
+                    for (int m = 0; m < 8; ++m) ph[m] = level(i + (m & 1), j + ((m >> 1) & 1), kz + ((m >> 2) & 1));
+                    const double al = pvf_alpha8(ph);
+                    if (al != 0.0) add_cell(i, j, kz, al);
+                }
         }
     }
-    __shared__ double s_part[kVolMaxSplit * 7];
-    if (threadIdx.x == 0) {
-        double *dst = partial + ((size_t)p * nsplit + split) * 7;
-        for (int k = 0; k < 7; ++k) dst[k] = acc[k];
-        __threadfence();  // release: partials before the count
-        s_last = atomicAdd(done + p, 1u) == (unsigned int)nsplit - 1;
-        __threadfence();  // acquire: the count before the other partials
-    }
-    __syncthreads();
-    if (s_last) {
-        // the last CTA of the particle adds the partials in slab order
-        for (int i = threadIdx.x; i < nsplit * 7; i += blockDim.x) s_part[i] = partial[(size_t)p * nsplit * 7 + i];
-        __syncthreads();
-    }
-    if (s_last && threadIdx.x == 0) {
-        double sum[7] = {0, 0, 0, 0, 0, 0, 0};
-        for (int sp = 0; sp < nsplit; ++sp)
-            for (int k = 0; k < 7; ++k) sum[k] += s_part[sp * 7 + k];
-        if (Iu)
-            for (int a = 0; a < 3; ++a) Iu[3 * p + a] = sum[a];
-        if (Irxu)
-            for (int a = 0; a < 3; ++a) Irxu[3 * p + a] = sum[3 + a];
-        if (vol) vol[p] = sum[6];
-        done[p] = 0;  // ready for the next call
-    }
+    volume_finish(acc, g.h, p, split, nsplit, partial, done, Iu, Irxu, vol);
+}
+
+// Drag diagnostic of Eq. FD: F_D = F_ib + rho_f (Iu^{n+1} - Iu^n) / dt.
+__global__ void k_drag(int P, const double *__restrict__ Fib, const double *__restrict__ Iu_new,
+                       const double *__restrict__ Iu_old, double rho_f, double dt, double *__restrict__ FD) {
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < 3 * P; q += gridDim.x * blockDim.x)
+        FD[q] = Fib[q] + rho_f * (Iu_new[q] - Iu_old[q]) / dt;
 }
 
 // ---------------------------------------------------------------------------
@@ -667,6 +798,49 @@ int particle_volume_integrals_static(const ib_grid *grid, const void *u, const i
     if (grid->prec == IB_F64)
         return run_volume_static<double>(ct, parts, Iu, Irxu, vol, (cudaStream_t)stream);
     return run_volume_static<float>(ct, parts, Iu, Irxu, vol, (cudaStream_t)stream);
+}
+
+int particle_volume_integrals_ellipsoid(ib_ctx *ctx, const ib_grid *grid, const void *u, int P, const double *Xr,
+                                        const double *axes, double *Iu, double *Irxu, double *vol, void *stream) {
+    if (!ctx) return set_error(IB_ERR_INVALID, "ctx is NULL");
+    int rc = validate_grid(grid, 1);
+    if (rc) return rc;
+    if (P < 0) return set_error(IB_ERR_INVALID, "P < 0");
+    if (P == 0) return IB_OK;
+    if (!u || !Xr || !axes || !Iu || !Irxu || !vol) return set_error(IB_ERR_INVALID, "NULL array");
+    if ((long long)P * kVolMaxSplit > (1LL << 31) - 1) return set_error(IB_ERR_UNSUPPORTED, "too many particles");
+    const CaseTab ct = single_case(grid, (void *)u, nullptr, P);
+    Arena ar(ctx);
+    const int nsplit = ctx->vol_split;
+    double *partial = ar.take<double>((size_t)P * nsplit * 7);
+    unsigned int *done = ar.take<unsigned int>(P);
+    if (!ar.ok()) return oom_error(ar.used, ar.cap);
+    cudaStream_t s = (cudaStream_t)stream;
+    PhaseTimer tm(ctx, IB_PHASE_VOLUME, s);
+    cudaMemsetAsync(done, 0, sizeof(unsigned int) * P, s);
+    if (grid->prec == IB_F64) {
+        cudaFuncSetAttribute(k_volume_ellipsoid<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kEllSmem);
+        k_volume_ellipsoid<double><<<P * nsplit, kVolThreads, kEllSmem, s>>>(ct, P, nsplit, Xr, axes, partial, done,
+                                                                             Iu, Irxu, vol, ctx->status);
+    } else {
+        cudaFuncSetAttribute(k_volume_ellipsoid<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kEllSmem);
+        k_volume_ellipsoid<float><<<P * nsplit, kVolThreads, kEllSmem, s>>>(ct, P, nsplit, Xr, axes, partial, done,
+                                                                            Iu, Irxu, vol, ctx->status);
+    }
+    return check_launch("particle_volume_integrals_ellipsoid");
+}
+
+int particle_drag_force(ib_ctx *ctx, int P, const double *F_ib, const double *Iu_new, const double *Iu_old,
+                        double rho_f, double dt, double *F_D, void *stream) {
+    if (!ctx) return set_error(IB_ERR_INVALID, "ctx is NULL");
+    if (P < 0) return set_error(IB_ERR_INVALID, "P < 0");
+    if (!(dt > 0.0) || !isfinite(dt) || !isfinite(rho_f)) return set_error(IB_ERR_INVALID, "dt or rho_f invalid");
+    if (P == 0) return IB_OK;
+    if (!F_ib || !Iu_new || !Iu_old || !F_D) return set_error(IB_ERR_INVALID, "NULL array");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int nb = (3 * P + 255) / 256;
+    k_drag<<<nb < 1024 ? nb : 1024, 256, 0, s>>>(P, F_ib, Iu_new, Iu_old, rho_f, dt, F_D);
+    return check_launch("particle_drag_force");
 }
 
 int particle_force_torque(ib_ctx *ctx, const ib_particles *parts, const ib_markers *marks, const double *F,
