@@ -51,11 +51,17 @@ struct Slots {
     int4 *geo_lo;      // [ncompact_max] tile first cell (wrapped), w = level
     int4 *geo_dim;     // [ncompact_max] tile dims, w = first candidate
     int *geo_case;     // [ncompact_max] case of the tile
-    // per-cell gather lists (built once per call, see k_tile_pairs): for
-    // tile cs with first candidate b, band[KW^3 b + q] = {cell | count << 16,
-    // first pair} for its q-th band cell (cells in index order), and
-    // pairs[KW^3 b + k] = candidate | ox << 16 | oy << 18 | oz << 20, each
-    // cell's pairs in ascending candidate order (the gather order).
+    // per-cell gather lists (built once per call, see k_tile_pairs).  A
+    // candidate contributes one pair per stencil cell inside its tile;
+    // poff[i] is the exclusive prefix of those counts over candidate
+    // positions, so tile cs with first candidate b owns pairs
+    // [poff[b], poff[b + nc]) -- KW^3 M in total.  band[poff[b] + q] =
+    // {cell | count << 16, first pair relative to poff[b]} for its q-th band
+    // cell (cells in index order), and pairs[poff[b] + k] = candidate | ox << 16
+    // | oy << 18 | oz << 20, each cell's pairs in ascending candidate order
+    // (the gather order).
+    uint32_t *pcnt;    // [cand_cap] in-tile stencil cells of each candidate
+    uint32_t *poff;    // [cand_cap + 1] exclusive scan of pcnt
     int2 *band;
     uint32_t *pairs;
     int *nband;        // [ncompact_max] band cells of the tile
@@ -176,7 +182,6 @@ constexpr size_t tile_stage_bytes() {
 template <typename T, int KW, bool COH>
 __device__ __forceinline__ void gather_tile_lists(const CaseTab &ct, int cs, const Slots &sl, const T *wts,
                                                   const T *A_src, double inv_dt, T *sw, T *sA) {
-    constexpr int KW3 = KW * KW * KW;
     const DevCase cd = ct.get(sl.geo_case[cs]);
     const DevGrid &g = cd.g;
     const long long N = (long long)g.n[0] * g.n[1] * g.n[2];
@@ -187,8 +192,8 @@ __device__ __forceinline__ void gather_tile_lists(const CaseTab &ct, int cs, con
     const int nc = (int)(sl.start[d + 1] - sl.start[d]);
     const int nb = sl.nband[cs];
     const uint32_t *cand = sl.cand + dim.w;
-    const int2 *band = sl.band + (size_t)KW3 * dim.w;
-    const uint32_t *pairs = sl.pairs + (size_t)KW3 * dim.w;
+    const int2 *band = sl.band + sl.poff[dim.w];
+    const uint32_t *pairs = sl.pairs + sl.poff[dim.w];
     const bool staged = nc <= TileStage<T>::N;
     if (staged) {
         for (int i = threadIdx.x; i < nc; i += blockDim.x) {
@@ -254,7 +259,6 @@ constexpr int kMultiTiles = 8;
 template <typename T, int KW, bool COH, int CAP>
 __device__ __forceinline__ void gather_tiles_lists(const CaseTab &ct, int cs0, int nt, const Slots &sl,
                                                    const T *wts, const T *A_src, double inv_dt, T *sw, T *sA) {
-    constexpr int KW3 = KW * KW * KW;
     __shared__ int s_coff[kMultiTiles + 1], s_boff[kMultiTiles + 1];
     if (nt <= 0) return;
     if (nt > kMultiTiles) {
@@ -305,9 +309,10 @@ __device__ __forceinline__ void gather_tiles_lists(const CaseTab &ct, int cs0, i
         const int cs = cs0 + k;
         const int4 lo = sl.geo_lo[cs];
         const int b = sl.geo_dim[cs].w;
-        const int2 e = sl.band[(size_t)KW3 * b + (qq - s_boff[k])];
+        const size_t pb = sl.poff[b];
+        const int2 e = sl.band[pb + (qq - s_boff[k])];
         const int cell = e.x & 0xffff, cnt = e.x >> 16;
-        const uint32_t *pr = sl.pairs + (size_t)KW3 * b + e.y;
+        const uint32_t *pr = sl.pairs + pb + e.y;
         const T *swk = sw + 12 * (size_t)s_coff[k];
         const T *sAk = sA + 4 * (size_t)s_coff[k];
         T acc0 = 0, acc1 = 0, acc2 = 0;

@@ -385,27 +385,34 @@ __global__ void __launch_bounds__(1024) k_levels(CaseTab ct, int P, int order, i
 // the KW cells from `first`.  Global tiles use wrapped cells; local tiles use
 // cells relative to the particle box (no wrap, box <= grid).
 template <int KW>
-__device__ __forceinline__ int axis_tiles_global(int first, int n, int t[3]) {
+__device__ __forceinline__ int axis_tiles_global(int first, int n, int t[3], int c[3]) {
     int cnt = 0;
 #pragma unroll
     for (int k = 0; k < KW; ++k) {
-        int c = wrap_add(first, k, n);
-        int tt = c / kTile;
-        bool dup = false;
-        for (int j = 0; j < cnt; ++j) dup |= (t[j] == tt);
-        if (!dup && cnt < 3) t[cnt++] = tt;
+        int cc = wrap_add(first, k, n);
+        int tt = cc / kTile;
+        int j = 0;
+        while (j < cnt && t[j] != tt) ++j;
+        if (j < cnt) ++c[j];
+        else if (cnt < 3) {
+            t[cnt] = tt;
+            c[cnt++] = 1;
+        }
     }
     return cnt;
 }
 
 template <int KW>
-__device__ __forceinline__ int axis_tiles_local(long long first_rel, int t[3]) {
+__device__ __forceinline__ int axis_tiles_local(long long first_rel, int t[3], int c[3]) {
     int a = (int)(first_rel / kTile), b = (int)((first_rel + KW - 1) / kTile);
     t[0] = a;
     if (b != a) {
         t[1] = b;
+        c[0] = (int)((long long)(a + 1) * kTile - first_rel);
+        c[1] = KW - c[0];
         return 2;
     }
+    c[0] = KW;
     return 1;
 }
 
@@ -422,13 +429,14 @@ template <int KW, typename Fn>
 __device__ __forceinline__ void for_marker_slots(const CaseTab &ct, const SlotGeom &sg, int l,
                                                  uint64_t anc, Fn f) {
     int tx[3], ty[3], tz[3], nx, ny, nz;
+    int cx[3] = {0, 0, 0}, cy[3] = {0, 0, 0}, cz[3] = {0, 0, 0};  // stencil cells per axis tile
     uint32_t base = 0;
     const DevCase &cd = ct.get(sg.part_of ? ct.case_of(sg.part_of[l]) : 0);
     const DevGrid &g = cd.g;
     if (sg.mode == 0) {
-        nx = axis_tiles_global<KW>(anchor_x(anc), g.n[0], tx);
-        ny = axis_tiles_global<KW>(anchor_y(anc), g.n[1], ty);
-        nz = axis_tiles_global<KW>(anchor_z(anc), g.n[2], tz);
+        nx = axis_tiles_global<KW>(anchor_x(anc), g.n[0], tx, cx);
+        ny = axis_tiles_global<KW>(anchor_y(anc), g.n[1], ty, cy);
+        nz = axis_tiles_global<KW>(anchor_z(anc), g.n[2], tz, cz);
     } else {
         int p = sg.part_of[l];
         int4 blo = sg.box_lo[p];
@@ -436,9 +444,9 @@ __device__ __forceinline__ void for_marker_slots(const CaseTab &ct, const SlotGe
         long long rx = wrap_diff(anchor_x(anc), wrap_int(blo.x, g.n[0]), g.n[0]);
         long long ry = wrap_diff(anchor_y(anc), wrap_int(blo.y, g.n[1]), g.n[1]);
         long long rz = wrap_diff(anchor_z(anc), wrap_int(blo.z, g.n[2]), g.n[2]);
-        nx = axis_tiles_local<KW>(rx, tx);
-        ny = axis_tiles_local<KW>(ry, ty);
-        nz = axis_tiles_local<KW>(rz, tz);
+        nx = axis_tiles_local<KW>(rx, tx, cx);
+        ny = axis_tiles_local<KW>(ry, ty, cy);
+        nz = axis_tiles_local<KW>(rz, tz, cz);
         // a box wider than kMaxBox is reported by the preparation kernel;
         // keep every slot id in range regardless
         if (tx[nx - 1] >= kLocalTiles || ty[ny - 1] >= kLocalTiles || tz[nz - 1] >= kLocalTiles) return;
@@ -452,7 +460,7 @@ __device__ __forceinline__ void for_marker_slots(const CaseTab &ct, const SlotGe
                     s = cd.tile_off + ((uint32_t)tz[k] * cd.tiles[1] + ty[j]) * cd.tiles[0] + tx[i];
                 else
                     s = base + ((uint32_t)tz[k] * kLocalTiles + ty[j]) * kLocalTiles + tx[i];
-                f(s);
+                f(s, (uint32_t)(cx[i] * cy[j] * cz[k]));
             }
 }
 
@@ -460,17 +468,18 @@ template <int KW>
 __global__ void k_slot_count(CaseTab ct, int M, SlotGeom sg, const uint64_t *__restrict__ anchor,
                              uint32_t *__restrict__ count) {
     for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < M; l += gridDim.x * blockDim.x)
-        for_marker_slots<KW>(ct, sg, l, anchor[l], [&](uint32_t s) { atomicAdd(count + s, 1u); });
+        for_marker_slots<KW>(ct, sg, l, anchor[l], [&](uint32_t s, uint32_t) { atomicAdd(count + s, 1u); });
 }
 
 template <int KW>
 __global__ void k_slot_fill(CaseTab ct, int M, SlotGeom sg, const uint64_t *__restrict__ anchor,
                             const uint32_t *__restrict__ start, uint32_t *__restrict__ cursor,
-                            uint32_t *__restrict__ cand) {
+                            uint32_t *__restrict__ cand, uint32_t *__restrict__ pcnt) {
     for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < M; l += gridDim.x * blockDim.x)
-        for_marker_slots<KW>(ct, sg, l, anchor[l], [&](uint32_t s) {
+        for_marker_slots<KW>(ct, sg, l, anchor[l], [&](uint32_t s, uint32_t ncell) {
             uint32_t pos = start[s] + atomicAdd(cursor + s, 1u);
             cand[pos] = (uint32_t)l;
+            if (pcnt) pcnt[pos] = ncell;
         });
 }
 
@@ -619,6 +628,7 @@ __device__ __forceinline__ void slot_emit(const DevGrid &g, const uint64_t *anch
                                           int nc, uint32_t b, int cs, const int lo[3], const Slots &sl, int lane,
                                           int nl) {
     for (int i = lane; i < nc; i += nl) sl.cand[b + i] = (uint32_t)(keys[i] & 0xffffffffu);
+    if (!sl.bins) return;
     uint16_t *bs = sl.bins + (size_t)cs * kBins;
     for (int r = lane; r < kBins; r += nl) {
         // first index whose bin >= r
@@ -687,8 +697,10 @@ __global__ void __launch_bounds__(kBlock) k_slot_sort(
         const DevGrid &g = ct.get(cse).g;
         if (nc > kMaxCand) {
             // report, and leave an empty tile (no bins, no cells)
-            uint16_t *bs = sl.bins + (size_t)cs * kBins;
-            for (int r = threadIdx.x; r < kBins; r += blockDim.x) bs[r] = 0;
+            if (sl.bins) {
+                uint16_t *bs = sl.bins + (size_t)cs * kBins;
+                for (int r = threadIdx.x; r < kBins; r += blockDim.x) bs[r] = 0;
+            }
             if (threadIdx.x == 0) {
                 raise_status(st, IB_ERR_UNSUPPORTED, nc);
                 sl.geo_lo[cs] = make_int4(lo[0], lo[1], lo[2], lev);
@@ -761,8 +773,8 @@ __global__ void __launch_bounds__(kPairThreads) k_tile_pairs(CaseTab ct, int nco
         const uint32_t dn = sl.dense_of[cs];
         int nc = (int)(sl.start[dn + 1] - sl.start[dn]);
         if (nc > kMaxCand) nc = 0;  // left empty by the sort (status raised there)
-        int2 *band = sl.band + (size_t)KW3 * b;
-        uint32_t *pairs = sl.pairs + (size_t)KW3 * b;
+        int2 *band = sl.band + sl.poff[b];
+        uint32_t *pairs = sl.pairs + sl.poff[b];
         for (int i = tid; i < nc; i += blockDim.x) {
             const uint64_t an = anchor[sl.cand[b + i]];
             int d[3] = {anchor_x(an) - lo.x + 3, anchor_y(an) - lo.y + 3, anchor_z(an) - lo.z + 3};
@@ -852,141 +864,17 @@ __global__ void __launch_bounds__(kPairThreads) k_tile_pairs(CaseTab ct, int nco
 // sums then read shared memory only.  Tiles with more than Stage<T>::N
 // candidates read the same values from global memory instead.
 // ---------------------------------------------------------------------------
-template <typename T> struct Stage;
-template <> struct Stage<float> { static constexpr int N = 1024; };
-template <> struct Stage<double> { static constexpr int N = 512; };
-
-template <typename T>
-constexpr size_t stage_bytes() {
-    return (size_t)Stage<T>::N * (12 + 4) * sizeof(T) + 2 * (size_t)kBins;
-}
-
-template <typename T>
-struct StageSmem {
-    T *w;          // [N][12]
-    T *A;          // [N][4]
-    uint16_t *bins;
-    __device__ explicit StageSmem(unsigned char *base) {
-        w = (T *)base;
-        A = w + (size_t)Stage<T>::N * 12;
-        bins = (uint16_t *)(A + (size_t)Stage<T>::N * 4);
-    }
-};
-
-// Per-wavefront staging of the tiles one CTA owns in the persistent kernel:
-// their row tables, candidate ids, x offsets and weights are loaded once per
-// wavefront and reused by all Ns passes; each pass then reloads only the
-// candidates' spread sources.  Wavefronts whose tiles do not fit fall back to
-// per-tile staging.
-// Within a wavefront every band cell is written by exactly one tile, so the
-// u values of a CTA's tiles (up to UT tiles) also stay in shared memory for
-// all passes: a pass adds its sums there and stores them, loading nothing.
-template <typename T> struct LvlStage;
-template <> struct LvlStage<float> { static constexpr int REC = 1536, UT = 12; };
-template <> struct LvlStage<double> { static constexpr int REC = 576, UT = 9; };
-constexpr int kMaxMyTiles = 12;  // >= every UT
-
-template <typename T>
-constexpr size_t lvl_stage_bytes() {
-    return (size_t)LvlStage<T>::REC * (12 + 4) * sizeof(T) + (size_t)LvlStage<T>::REC * 4 +
-           (size_t)LvlStage<T>::UT * kBins * 2 + (size_t)LvlStage<T>::UT * 3 * kTileCells * sizeof(T);
-}
-
-template <typename T>
-struct LvlSmem {
-    T *w;           // [REC][12]
-    T *A;           // [REC][4]
-    uint32_t *ids;  // [REC]
-    uint16_t *bins; // [UT][kBins]
-    T *u;           // [UT][3][kTileCells]
-    __device__ explicit LvlSmem(unsigned char *base) {
-        u = (T *)base;  // first: keeps T alignment
-        w = u + (size_t)LvlStage<T>::UT * 3 * kTileCells;
-        A = w + (size_t)LvlStage<T>::REC * 12;
-        ids = (uint32_t *)(A + (size_t)LvlStage<T>::REC * 4);
-        bins = (uint16_t *)(ids + LvlStage<T>::REC);
-    }
-};
-
-// One tile (compact slot cs) of a gather phase into the tile's case: u += S A,
-// and, when the case has a force field (forcing pass), f += S A / dt.
-template <typename T, int KW, bool COH>
-__device__ __forceinline__ void gather_tile(const CaseTab &ct, int cs, const Slots &sl,
-                                            const T *__restrict__ wts, const T *A, double inv_dt,
-                                            StageSmem<T> &sm) {
-    const DevCase &cd = ct.get(sl.geo_case[cs]);
-    const DevGrid g = cd.g;
-    const long long N = (long long)g.n[0] * g.n[1] * g.n[2];
-    T *__restrict__ dst = (T *)cd.u;
-    T *__restrict__ f_out = (T *)cd.f;
-    const int4 lo = sl.geo_lo[cs], dim = sl.geo_dim[cs];
-    const uint16_t *bs = sl.bins + (size_t)cs * kBins;
-    for (int i = threadIdx.x; i < kBins; i += blockDim.x) sm.bins[i] = bs[i];
-    __syncthreads();
-    const int nc = sm.bins[kBins - 1];
-    const uint32_t *cand = sl.cand + dim.w;
-    const bool staged = nc <= Stage<T>::N;
-    if (staged) {
-        for (int i = threadIdx.x; i < nc; i += blockDim.x) {
-            const uint32_t m = cand[i];
-            const T *wm = wts + 12 * (size_t)m;
-#pragma unroll
-            for (int k = 0; k < 3; ++k)
-#pragma unroll
-                for (int j = 0; j < KW; ++j) sm.w[12 * i + 4 * k + j] = __ldg(wm + 4 * k + j);
-#pragma unroll
-            for (int k = 0; k < 3; ++k) sm.A[4 * i + k] = ld<COH>(A + 4 * (size_t)m + k);
-        }
-        __syncthreads();
-    }
-    const int tx = threadIdx.x & 7, ty = (threadIdx.x >> 3) & 7, tz = threadIdx.x >> 6;
-    if (tx < dim.x && ty < dim.y && tz < dim.z) {
-        T acc[3];
-        const bool hit = staged
-                             ? gather_cell<T, KW, true, COH>(tx, ty, tz, sm.bins, cand, sm.w, sm.A, acc)
-                             : gather_cell<T, KW, false, COH>(tx, ty, tz, sm.bins, cand, wts, A, acc);
-        if (hit) {
-            const int cx = wrap_add(lo.x, tx, g.n[0]);
-            const int cy = wrap_add(lo.y, ty, g.n[1]);
-            const int cz = wrap_add(lo.z, tz, g.n[2]);
-            const long long c = ((long long)cz * g.n[1] + cy) * g.n[0] + cx;
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                T *q = dst + k * N + c;
-                *q += acc[k];
-            }
-            if (f_out) {
-#pragma unroll
-                for (int k = 0; k < 3; ++k) {
-                    T *q = f_out + k * N + c;
-                    *q += (T)(acc[k] * inv_dt);
-                }
-            }
-        }
-    }
-    __syncthreads();
-}
-
-// Out-of-line copy of gather_tile for the persistent kernel's fallback path
-// (wavefronts whose tiles do not fit the per-CTA staging), so that its code
-// stays out of the hot loop.
-template <typename T, int KW>
-__device__ __noinline__ void gather_tile_fallback(const CaseTab ct, int cs, const Slots sl, const T *wts,
-                                                  const T *A, double inv_dt, unsigned char *smem) {
-    StageSmem<T> sm(smem);
-    gather_tile<T, KW, true>(ct, cs, sl, wts, A, inv_dt, sm);
-}
-
-// Spreading: the case's u slot holds the field spread into, its f slot is null.
+// Spreading (ib_spread) over the tiles' per-cell lists: the case's u slot
+// holds the field spread into, its f slot is null.
 template <typename T, int KER>
-__global__ void __launch_bounds__(kBlock) k_spread_gather(CaseTab ct, const int *__restrict__ ncompact_p,
-                                                          Slots sl, const T *__restrict__ wts,
-                                                          const T *__restrict__ A) {
+__global__ void __launch_bounds__(256) k_spread_gather(CaseTab ct, const int *__restrict__ ncompact_p, Slots sl,
+                                                       const T *__restrict__ wts, const T *__restrict__ A) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    StageSmem<T> sm(smem_raw);
-    int nc = *ncompact_p;
+    T *sw = (T *)smem_raw;
+    T *sA = sw + (size_t)TileStage<T>::N * 12;
+    const int nc = *ncompact_p;
     for (int cs = blockIdx.x; cs < nc; cs += gridDim.x)
-        gather_tile<T, Kernel<KER>::W, false>(ct, cs, sl, wts, A, 0.0, sm);
+        gather_tile_lists<T, Kernel<KER>::W, false>(ct, cs, sl, wts, A, 0.0, sw, sA);
 }
 
 // ---------------------------------------------------------------------------
@@ -1097,134 +985,39 @@ __global__ void __launch_bounds__(256, 5) k_gather_level(PassArgs<T> a, int L) {
 }
 
 template <typename T, int KER>
-__global__ void __launch_bounds__(kBlock, 1) k_mdf_passes(PassArgs<T> a) {
+__global__ void __launch_bounds__(256) k_mdf_passes(PassArgs<T> a) {
     constexpr int KW = Kernel<KER>::W;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    StageSmem<T> sm(smem_raw);
+    T *sw = (T *)smem_raw;                      // [N][12]
+    T *sA = sw + (size_t)TileStage<T>::N * 12;  // [N][4]
     const int nl = *a.nlev;
-    double inv_dt = 1.0 / a.dt;
-    int gtid = blockIdx.x * blockDim.x + threadIdx.x;
-    int gsz = gridDim.x * blockDim.x;
-    LvlSmem<T> lv(smem_raw);
-    __shared__ int s_nmine, s_total, s_staged;
-    __shared__ int s_off[kMaxMyTiles + 1];
-    __shared__ int4 s_lo[kMaxMyTiles], s_dim[kMaxMyTiles];
-    __shared__ int s_case[kMaxMyTiles];
-    const int tx = threadIdx.x & 7, ty = (threadIdx.x >> 3) & 7, tz = threadIdx.x >> 6;
+    const double inv_dt = 1.0 / a.dt;
+    const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int gsz = gridDim.x * blockDim.x;
     for (int L = a.L0; L < nl; ++L) {
-        int m0 = a.lev_mbeg[L], m1 = a.lev_mbeg[L + 1];
-        int s0 = a.lev_sbeg[L], s1 = a.lev_sbeg[L + 1];
-        // stage this CTA's tiles of the wavefront (tiles s0 + blockIdx.x + k gridDim.x)
-        if (threadIdx.x == 0) {
-            int nmine = s1 > s0 + (int)blockIdx.x ? (s1 - s0 - (int)blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
-            int tot = 0, ok = nmine <= kMaxMyTiles;
-            for (int k = 0; ok && k < nmine; ++k) {
-                const int cs = s0 + blockIdx.x + k * gridDim.x;
-                s_off[k] = tot;
-                s_lo[k] = a.sl.geo_lo[cs];
-                s_dim[k] = a.sl.geo_dim[cs];
-                s_case[k] = a.sl.geo_case[cs];
-                tot += a.sl.bins[(size_t)cs * kBins + kBins - 1];
-            }
-            s_off[ok ? nmine : 0] = tot;
-            s_nmine = nmine;
-            s_total = tot;
-            s_staged = ok && tot <= LvlStage<T>::REC && nmine <= LvlStage<T>::UT;
-        }
-        __syncthreads();
-        const bool staged = s_staged;
-        const int nmine = s_nmine;
-        if (staged) {
-            for (int k = 0; k < nmine; ++k) {
-                const int cs = s0 + blockIdx.x + k * gridDim.x;
-                const uint16_t *bs = a.sl.bins + (size_t)cs * kBins;
-                for (int i = threadIdx.x; i < kBins; i += blockDim.x) lv.bins[k * kBins + i] = bs[i];
-                const int b = s_dim[k].w, off = s_off[k], nc = s_off[k + 1] - off;
-                {
-                    // the tile's u values (every cell of the tile; only band cells are written)
-                    const int4 lo = s_lo[k], dim = s_dim[k];
-                    if (tx < dim.x && ty < dim.y && tz < dim.z) {
-                        const DevCase &cd = a.ct.get(s_case[k]);
-                        const DevGrid &g = cd.g;
-                        const long long N = (long long)g.n[0] * g.n[1] * g.n[2];
-                        const long long c = ((long long)wrap_add(lo.z, tz, g.n[2]) * g.n[1] +
-                                             wrap_add(lo.y, ty, g.n[1])) * g.n[0] + wrap_add(lo.x, tx, g.n[0]);
-#pragma unroll
-                        for (int q = 0; q < 3; ++q)
-                            lv.u[(k * 3 + q) * kTileCells + threadIdx.x] = ((const T *)cd.u)[q * N + c];
-                    }
-                }
-                for (int i = threadIdx.x; i < nc; i += blockDim.x) {
-                    const uint32_t mk = a.sl.cand[b + i];
-                    lv.ids[off + i] = mk;
-                    const T *wm = a.ms.wts + 12 * (size_t)mk;
-#pragma unroll
-                    for (int q = 0; q < 3; ++q)
-#pragma unroll
-                        for (int j = 0; j < KW; ++j) lv.w[12 * (off + i) + 4 * q + j] = __ldg(wm + 4 * q + j);
-                }
-            }
-            __syncthreads();
-        }
+        const int m0 = a.lev_mbeg[L], m1 = a.lev_mbeg[L + 1];
+        const int s0 = a.lev_sbeg[L], s1 = a.lev_sbeg[L + 1];
         for (int m = 0; m < a.Ns; ++m) {
             // interpolation phase: U = J u, F += (U^d - U)/dt, A = (U^d - U) dV / h^3
             for (int i = m0 + gtid; i < m1; i += gsz) {
-                int l = a.mperm[i];
-                const DevCase &cd = a.ct.of_particle(a.part_of[l]);
+                const int l = a.mperm[i];
+                const DevCase cd = a.ct.of_particle(a.part_of[l]);
                 const DevGrid &g = cd.g;
                 const long long N = (long long)g.n[0] * g.n[1] * g.n[2];
                 T U[3];
                 interp_marker<T, KW, true>((const T *)cd.u, g, N, a.ms.anchor[l], a.ms.wts + 12 * (size_t)l, U);
-                double q = a.dV[l] * g.inv_h3;
+                const double q = a.dV[l] * g.inv_h3;
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
-                    double e = a.ms.Ud[3 * l + c] - (double)U[c];
+                    const double e = a.ms.Ud[3 * l + c] - (double)U[c];
                     a.F[3 * l + c] += e * inv_dt;
                     a.ms.A[4 * l + c] = (T)(e * q);
                 }
             }
             if (!grid_sync(a.bar, a.st)) return;
-            // gather phase over the level's tiles
-            if (staged) {
-                const int tot = s_total;
-                for (int i = threadIdx.x; i < tot; i += blockDim.x) {
-                    const T *src = a.ms.A + 4 * (size_t)lv.ids[i];
-                    lv.A[4 * i + 0] = src[0];
-                    lv.A[4 * i + 1] = src[1];
-                    lv.A[4 * i + 2] = src[2];
-                }
-                __syncthreads();
-#pragma unroll 1
-                for (int k = 0; k < nmine; ++k) {
-                    const int4 dim = s_dim[k];
-                    const int off = s_off[k];
-                    T acc[3];
-                    if (tx < dim.x && ty < dim.y && tz < dim.z &&
-                        gather_cell<T, KW, true, true>(tx, ty, tz, lv.bins + k * kBins, nullptr,
-                                                       lv.w + 12 * (size_t)off, lv.A + 4 * (size_t)off, acc)) {
-                        const int4 lo = s_lo[k];
-                        const DevCase &cd = a.ct.get(s_case[k]);
-                        const DevGrid &g = cd.g;
-                        const long long N = (long long)g.n[0] * g.n[1] * g.n[2];
-                        const long long c = ((long long)wrap_add(lo.z, tz, g.n[2]) * g.n[1] +
-                                             wrap_add(lo.y, ty, g.n[1])) * g.n[0] + wrap_add(lo.x, tx, g.n[0]);
-                        T *const u = (T *)cd.u;
-                        T *const f_out = (T *)cd.f;
-#pragma unroll
-                        for (int q = 0; q < 3; ++q) {
-                            T *su = lv.u + (k * 3 + q) * kTileCells + threadIdx.x;
-                            *su += acc[q];
-                            u[q * N + c] = *su;
-                        }
-                        if (f_out)
-#pragma unroll
-                            for (int q = 0; q < 3; ++q) f_out[q * N + c] += (T)(acc[q] * inv_dt);
-                    }
-                }
-            } else {
-                for (int cs = s0 + blockIdx.x; cs < s1; cs += gridDim.x)
-                    gather_tile_fallback<T, KW>(a.ct, cs, a.sl, a.ms.wts, a.ms.A, inv_dt, smem_raw);
-            }
+            // gather phase over the wavefront's tiles (their per-cell lists)
+            for (int cs = s0 + blockIdx.x; cs < s1; cs += gridDim.x)
+                gather_tile_lists<T, KW, true>(a.ct, cs, a.sl, a.ms.wts, a.ms.A, inv_dt, sw, sA);
             if (!grid_sync(a.bar, a.st)) return;
         }
     }
@@ -1259,7 +1052,7 @@ static bool take_markers(Arena &ar, int M, MarkerState<T> &ms) {
 template <int KW>
 static int build_slots(ib_ctx *ctx, Arena &ar, const CaseTab &ct, int M, int ndense, SlotGeom sg,
                        const uint64_t *anchor, const int *level, Slots &sl, int *&ncompact_dev,
-                       cudaStream_t s, bool with_pairs = false) {
+                       cudaStream_t s, bool with_pairs, bool with_bins) {
     size_t cand_cap = (size_t)M * (sg.mode == 0 ? 27 : 8) + 1;
     int ncompact_cap = (int)((size_t)M * (sg.mode == 0 ? 27 : 8) < (size_t)ndense
                                  ? (size_t)M * (sg.mode == 0 ? 27 : 8)
@@ -1271,18 +1064,24 @@ static int build_slots(ib_ctx *ctx, Arena &ar, const CaseTab &ct, int M, int nde
     sl.flag_scan = ar.take<uint32_t>(ndense + 1);
     uint32_t *flags = ar.take<uint32_t>(ndense);
     uint32_t *scratch = ar.take<uint32_t>(scan_workspace(ndense));
+    uint32_t *cscratch = with_pairs ? ar.take<uint32_t>(scan_workspace((int)cand_cap)) : nullptr;
     sl.dense_of = ar.take<uint32_t>(ncompact_cap);
     sl.cand = ar.take<uint32_t>(cand_cap);
-    sl.bins = ar.take<uint16_t>((size_t)ncompact_cap * kBins);
+    // bin tables: only the particle-resident form walks them
+    sl.bins = with_bins ? ar.take<uint16_t>((size_t)ncompact_cap * kBins) : nullptr;
     sl.geo_lo = ar.take<int4>(ncompact_cap);
     sl.geo_dim = ar.take<int4>(ncompact_cap);
     sl.geo_case = ar.take<int>(ncompact_cap);
     constexpr int KW3 = KW * KW * KW;
     if (with_pairs) {
-        sl.band = ar.take<int2>((size_t)KW3 * cand_cap);
-        sl.pairs = ar.take<uint32_t>((size_t)KW3 * cand_cap);
+        // every stencil cell of every marker is one pair: KW^3 M in total
+        sl.pcnt = ar.take<uint32_t>(cand_cap);
+        sl.poff = ar.take<uint32_t>(cand_cap + 1);
+        sl.band = ar.take<int2>((size_t)KW3 * M);
+        sl.pairs = ar.take<uint32_t>((size_t)KW3 * M);
         sl.nband = ar.take<int>(ncompact_cap);
     } else {
+        sl.pcnt = sl.poff = nullptr;
         sl.band = nullptr;
         sl.pairs = nullptr;
         sl.nband = nullptr;
@@ -1298,7 +1097,9 @@ static int build_slots(ib_ctx *ctx, Arena &ar, const CaseTab &ct, int M, int nde
     k_flags<<<nbd, 256, 0, s>>>(sl.count, flags, ndense);
     exclusive_scan(flags, sl.flag_scan, ndense, scratch, s);
     k_compact<<<nbd, 256, 0, s>>>(sl.count, sl.flag_scan, sl.dense_of, ndense);
-    k_slot_fill<KW><<<nb, 256, 0, s>>>(ct, M, sg, anchor, sl.start, sl.cursor, sl.cand);
+    if (with_pairs) cudaMemsetAsync(sl.pcnt, 0, sizeof(uint32_t) * cand_cap, s);
+    k_slot_fill<KW><<<nb, 256, 0, s>>>(ct, M, sg, anchor, sl.start, sl.cursor, sl.cand, sl.pcnt);
+    if (with_pairs) exclusive_scan(sl.pcnt, sl.poff, (int)cand_cap, cscratch, s);
     ncompact_dev = (int *)(sl.flag_scan + ndense);
     k_slot_sort<<<ctx->sm_count * 4, kBlock, 0, s>>>(ct, sg.mode, ncompact_cap, ncompact_dev, sg,
                                                      sl.dense_of, sl.start, anchor, level, sl,
@@ -1337,11 +1138,11 @@ static int run_spread(ib_ctx *ctx, const ib_grid *grid, int M, const double *X, 
     k_prep_spread<T, KER><<<nb, 256, 0, s>>>(g, M, X, F, dV, ms, ctx->status);
     Slots sl;
     int *ncompact = nullptr;
-    int rc = build_slots<KW>(ctx, ar, ct, M, (int)ndense, sg, ms.anchor, nullptr, sl, ncompact, s);
+    int rc = build_slots<KW>(ctx, ar, ct, M, (int)ndense, sg, ms.anchor, nullptr, sl, ncompact, s, true, false);
     if (rc) return rc;
     cudaFuncSetAttribute(k_spread_gather<T, KER>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)stage_bytes<T>());
-    k_spread_gather<T, KER><<<ctx->sm_count * 2, kBlock, stage_bytes<T>(), s>>>(ct, ncompact, sl, ms.wts, ms.A);
+                         (int)tile_stage_bytes<T>());
+    k_spread_gather<T, KER><<<ctx->sm_count * 4, 256, tile_stage_bytes<T>(), s>>>(ct, ncompact, sl, ms.wts, ms.A);
     return check_launch("ib_spread");
 }
 
@@ -1396,7 +1197,8 @@ static int run_mdf(ib_ctx *ctx, Arena &ar, const CaseTab &ct, const ib_particles
     sg.box_dim = box_dim;
     Slots sl;
     int *ncompact = nullptr;
-    int rc = build_slots<KW>(ctx, ar, ct, M, (int)ndense, sg, ms.anchor, lo.level, sl, ncompact, s, true);
+    const bool resident = order == IB_ORDER_SEQUENTIAL && ctx->pass_kernels == IB_PASSES_RESIDENT;
+    int rc = build_slots<KW>(ctx, ar, ct, M, (int)ndense, sg, ms.anchor, lo.level, sl, ncompact, s, true, resident);
     if (rc) return rc;
     if (order == IB_ORDER_SEQUENTIAL &&
         (ctx->pass_kernels == IB_PASSES_RESIDENT || ctx->pass_kernels == IB_PASSES_GROUPS)) {
@@ -1483,14 +1285,14 @@ static int run_mdf(ib_ctx *ctx, Arena &ar, const CaseTab &ct, const ib_particles
             }
     }
     int per_sm = 0;
-    const size_t smem = stage_bytes<T>() > lvl_stage_bytes<T>() ? stage_bytes<T>() : lvl_stage_bytes<T>();
+    const size_t smem = tile_stage_bytes<T>();
     cudaFuncSetAttribute(k_mdf_passes<T, KER>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mdf_passes<T, KER>, kBlock, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mdf_passes<T, KER>, 256, smem);
     if (per_sm < 1) return set_error(IB_ERR_CUDA, "mdf kernel cannot be resident");
     int nblocks = per_sm * ctx->sm_count;
     void *args[] = {&a};
     cudaError_t e =
-        cudaLaunchCooperativeKernel((const void *)k_mdf_passes<T, KER>, nblocks, kBlock, args, smem, s);
+        cudaLaunchCooperativeKernel((const void *)k_mdf_passes<T, KER>, nblocks, 256, args, smem, s);
     if (e != cudaSuccess) return set_error(IB_ERR_CUDA, "mdf launch: %s", cudaGetErrorString(e));
     tpass.stop();
     cudaMemcpyAsync(ctx->h_nlev, lo.nlev, sizeof(int), cudaMemcpyDeviceToHost, s);
