@@ -195,6 +195,25 @@ __device__ __forceinline__ void gather_tile_lists(const CaseTab &ct, int cs, con
     const int2 *band = sl.band + sl.poff[dim.w];
     const uint32_t *pairs = sl.pairs + sl.poff[dim.w];
     const bool staged = nc <= TileStage<T>::N;
+    auto cell_index = [&](int cell) {
+        const int tx = cell & 7, ty = (cell >> 3) & 7, tz = cell >> 6;
+        return ((long long)wrap_add(lo.z, tz, g.n[2]) * g.n[1] + wrap_add(lo.y, ty, g.n[1])) * g.n[0] +
+               wrap_add(lo.x, tx, g.n[0]);
+    };
+    // this thread's first band cell, its list head and its u values are
+    // loaded before the staging barrier (none of them changes meanwhile: a
+    // band cell is updated by its own thread only)
+    const int q0 = threadIdx.x;
+    int2 e0 = make_int2(0, 0);
+    long long c0 = 0;
+    T v0[3] = {T(0), T(0), T(0)};
+    if (q0 < nb) {
+        e0 = band[q0];
+        c0 = cell_index(e0.x & 0xffff);
+        v0[0] = u[c0];
+        v0[1] = u[N + c0];
+        v0[2] = u[2 * N + c0];
+    }
     if (staged) {
         for (int i = threadIdx.x; i < nc; i += blockDim.x) {
             const uint32_t m = cand[i];
@@ -208,9 +227,10 @@ __device__ __forceinline__ void gather_tile_lists(const CaseTab &ct, int cs, con
         }
         __syncthreads();
     }
-    for (int q = threadIdx.x; q < nb; q += blockDim.x) {
-        const int2 e = band[q];
-        const int cell = e.x & 0xffff, cnt = e.x >> 16;
+    for (int q = q0; q < nb; q += blockDim.x) {
+        const bool first = q == q0;
+        const int2 e = first ? e0 : band[q];
+        const int cnt = e.x >> 16;
         const uint32_t *pr = pairs + e.y;
         T acc0 = 0, acc1 = 0, acc2 = 0;
         for (int k = 0; k < cnt; ++k) {
@@ -233,12 +253,11 @@ __device__ __forceinline__ void gather_tile_lists(const CaseTab &ct, int cs, con
             acc1 += wt * a1;
             acc2 += wt * a2;
         }
-        const int tx = cell & 7, ty = (cell >> 3) & 7, tz = cell >> 6;
-        const long long c = ((long long)wrap_add(lo.z, tz, g.n[2]) * g.n[1] + wrap_add(lo.y, ty, g.n[1])) * g.n[0] +
-                            wrap_add(lo.x, tx, g.n[0]);
-        u[c] += acc0;
-        u[N + c] += acc1;
-        u[2 * N + c] += acc2;
+        const long long c = first ? c0 : cell_index(e.x & 0xffff);
+        const T u0 = first ? v0[0] : u[c], u1 = first ? v0[1] : u[N + c], u2 = first ? v0[2] : u[2 * N + c];
+        u[c] = u0 + acc0;
+        u[N + c] = u1 + acc1;
+        u[2 * N + c] = u2 + acc2;
         if (f_out) {
             f_out[c] += (T)(acc0 * inv_dt);
             f_out[N + c] += (T)(acc1 * inv_dt);
