@@ -103,17 +103,29 @@ __global__ void k_prep_spread(DevGrid g, int M, const double *__restrict__ X,
 
 // Per particle (one CTA): marker positions, desired velocities, anchors,
 // weights; the particle's marker radius and its unwrapped stencil box.
+// Scratch of the cross-CTA reductions of k_prep_particles: per particle the
+// stencil box bounds (lo starts at a huge value, hi at a very negative one:
+// memset 0x7f / 0x80 bytes), the squared marker radius (0) and a completion
+// count (0).
+struct PrepScratch {
+    long long *lo, *hi;          // [P][3]
+    unsigned long long *rho2;    // [P] bit pattern of a non-negative double
+    unsigned int *done;          // [P]
+};
+constexpr int kPrepSplit = 4;    // CTAs per particle
+
 template <typename T, int KER>
-__global__ void __launch_bounds__(kBlock) k_prep_particles(
+__global__ void __launch_bounds__(256) k_prep_particles(
     CaseTab ct, int P, const double *__restrict__ Xr, const double *__restrict__ Ur,
     const double *__restrict__ Wr, const int *__restrict__ moff, const double *__restrict__ R,
     const double *__restrict__ dV, MarkerState<T> ms, double *__restrict__ F,
     double *__restrict__ rho, int4 *__restrict__ box_lo, int4 *__restrict__ box_dim,
-    int *__restrict__ part_of, DevStatus *st) {
+    int *__restrict__ part_of, PrepScratch ps, DevStatus *st) {
     constexpr int KW = Kernel<KER>::W;
     __shared__ long long s_lo[3], s_hi[3];
     __shared__ double s_rho;
-    int p = blockIdx.x;
+    __shared__ int s_last;
+    const int p = blockIdx.x / kPrepSplit, part = blockIdx.x % kPrepSplit;
     if (p >= P) return;
     const DevGrid g = ct.of_particle(p).g;
     if (threadIdx.x < 3) {
@@ -126,11 +138,13 @@ __global__ void __launch_bounds__(kBlock) k_prep_particles(
     double uc[3] = {Ur[3 * p], Ur[3 * p + 1], Ur[3 * p + 2]};
     double wc[3] = {Wr[3 * p], Wr[3 * p + 1], Wr[3 * p + 2]};
     bool pok = finite3(xc) && finite3(uc) && finite3(wc);
-    if (!pok && threadIdx.x == 0) raise_status(st, IB_ERR_NONFINITE, p);
-    int m0 = moff[p], m1 = moff[p + 1];
+    if (!pok && threadIdx.x == 0 && part == 0) raise_status(st, IB_ERR_NONFINITE, p);
+    const int m0 = moff[p], m1 = moff[p + 1];
+    const int nm = m1 - m0;
+    const int l0 = m0 + (int)((long long)part * nm / kPrepSplit), l1 = m0 + (int)((long long)(part + 1) * nm / kPrepSplit);
     long long lo[3] = {LLONG_MAX, LLONG_MAX, LLONG_MAX}, hi[3] = {LLONG_MIN, LLONG_MIN, LLONG_MIN};
     double rmax = 0.0;
-    for (int l = m0 + threadIdx.x; l < m1; l += blockDim.x) {
+    for (int l = l0 + threadIdx.x; l < l1; l += blockDim.x) {
         double r[3] = {R[3 * l], R[3 * l + 1], R[3 * l + 2]};
         double dv = dV[l];
         if (!pok || !finite3(r) || !isfinite(dv)) {
@@ -164,13 +178,29 @@ __global__ void __launch_bounds__(kBlock) k_prep_particles(
     // rmax >= 0: the bit pattern orders like the value
     atomicMax((unsigned long long *)&s_rho, (unsigned long long)__double_as_longlong(rmax));
     __syncthreads();
+    // combine the particle's CTAs; the last one to finish writes the results
     if (threadIdx.x == 0) {
-        rho[p] = sqrt(s_rho);
+        for (int d = 0; d < 3; ++d) {
+            atomicMin(&ps.lo[3 * p + d], s_lo[d]);
+            atomicMax(&ps.hi[3 * p + d], s_hi[d]);
+        }
+        atomicMax(&ps.rho2[p], (unsigned long long)__double_as_longlong(s_rho));
+        __threadfence();
+        s_last = atomicAdd(&ps.done[p], 1u) == kPrepSplit - 1;
+        __threadfence();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && s_last) {
+        long long blo[3], bhi[3];
+        for (int d = 0; d < 3; ++d) {
+            blo[d] = atomicAdd((unsigned long long *)&ps.lo[3 * p + d], 0ull);
+            bhi[d] = atomicAdd((unsigned long long *)&ps.hi[3 * p + d], 0ull);
+        }
+        rho[p] = sqrt(__longlong_as_double((long long)atomicAdd(&ps.rho2[p], 0ull)));
         if (m1 > m0) {
             int dims[3];
-            for (int d = 0; d < 3; ++d) dims[d] = (int)(s_hi[d] - s_lo[d] + 1);
-            box_lo[p] = make_int4(wrap_int(s_lo[0], g.n[0]), wrap_int(s_lo[1], g.n[1]),
-                                  wrap_int(s_lo[2], g.n[2]), 0);
+            for (int d = 0; d < 3; ++d) dims[d] = (int)(bhi[d] - blo[d] + 1);
+            box_lo[p] = make_int4(wrap_int(blo[0], g.n[0]), wrap_int(blo[1], g.n[1]), wrap_int(blo[2], g.n[2]), 0);
             box_dim[p] = make_int4(dims[0], dims[1], dims[2], 0);
             for (int d = 0; d < 3; ++d)
                 if (dims[d] > kMaxBox || dims[d] > g.n[d]) raise_status(st, IB_ERR_UNSUPPORTED, p);
@@ -207,8 +237,12 @@ struct LevelOut {
 __global__ void k_conflicts(CaseTab ct, int P, int KW, const double *__restrict__ Xr,
                             const double *__restrict__ rho, int *__restrict__ nbr_cnt,
                             int *__restrict__ nbr) {
-    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x) {
-        const DevCase &cd = ct.of_particle(p);
+    // one warp per particle p; lanes test q = p0 + lane, p0 + 32 + lane, ...
+    // and the hits are appended in ascending q (ballot order)
+    const int lane = threadIdx.x & 31;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    for (int p = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; p < P; p += nw) {
+        const DevCase cd = ct.of_particle(p);
         const DevGrid &g = cd.g;
         const float L[3] = {(float)(g.n[0] * g.h), (float)(g.n[1] * g.h), (float)(g.n[2] * g.h)};
         const float iL[3] = {1.0f / L[0], 1.0f / L[1], 1.0f / L[2]};
@@ -216,21 +250,26 @@ __global__ void k_conflicts(CaseTab ct, int P, int KW, const double *__restrict_
         const float xp[3] = {(float)Xr[3 * p], (float)Xr[3 * p + 1], (float)Xr[3 * p + 2]};
         const float rp = (float)rho[p] + halo;
         int cnt = 0;
-        for (int q = cd.p0; q < p; ++q) {  // particles of other cases never conflict
-            float d2 = 0.0f;
+        for (int q0 = cd.p0; q0 < p; q0 += 32) {  // particles of other cases never conflict
+            const int q = q0 + lane;
+            bool hit = false;
+            if (q < p) {
+                float d2 = 0.0f;
 #pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                float d = (float)Xr[3 * q + a] - xp[a];
-                d -= L[a] * rintf(d * iL[a]);
-                d2 += d * d;
+                for (int a = 0; a < 3; ++a) {
+                    float d = (float)Xr[3 * q + a] - xp[a];
+                    d -= L[a] * rintf(d * iL[a]);
+                    d2 += d * d;
+                }
+                const float lim = rp + (float)rho[q];
+                hit = d2 < lim * lim;
             }
-            const float lim = rp + (float)rho[q];
-            if (d2 < lim * lim) {
-                if (cnt < kMaxNbr) nbr[(size_t)p * kMaxNbr + cnt] = q;
-                ++cnt;
-            }
+            const unsigned b = __ballot_sync(0xffffffffu, hit);
+            const int pos = cnt + __popc(b & ((1u << lane) - 1u));
+            if (hit && pos < kMaxNbr) nbr[(size_t)p * kMaxNbr + pos] = q;
+            cnt += __popc(b);
         }
-        nbr_cnt[p] = cnt <= kMaxNbr ? cnt : -1;
+        if (lane == 0) nbr_cnt[p] = cnt <= kMaxNbr ? cnt : -1;
     }
 }
 
@@ -509,54 +548,15 @@ __global__ void k_level_slots(int mode, const int *__restrict__ nlev_p, const in
     }
 }
 
-// Level-major marker list.  Inside each particle the markers are listed in
-// spatial order of their anchors (z, y, x of the first stencil cell), so the
-// warps of the interpolation phase read neighbouring cells; the order has no
-// effect on results (every marker is interpolated independently).  One CTA
-// per particle sorts up to kMaxCand (anchor key, marker) pairs; larger
-// particles keep index order.
-__global__ void __launch_bounds__(kBlock) k_marker_order(int P, const int *__restrict__ moff,
-                                                         const int *__restrict__ mbase,
-                                                         const uint64_t *__restrict__ anchor,
-                                                         int *__restrict__ mperm) {
-    __shared__ unsigned long long keys[kMaxCand];
+// Level-major marker list: the markers of the particle of rank r follow
+// those of the particles of lower rank, each particle's in index order (the
+// Fibonacci lattice index already walks the sphere band by band in z; a
+// spatial sort of each particle's markers measured slower end to end).
+__global__ void k_marker_order(int P, const int *__restrict__ moff, const int *__restrict__ mbase,
+                               int *__restrict__ mperm) {
     for (int p = blockIdx.x; p < P; p += gridDim.x) {
         const int m0 = moff[p], n = moff[p + 1] - m0, base = mbase[p];
-        if (n > kMaxCand) {
-            for (int i = threadIdx.x; i < n; i += blockDim.x) mperm[base + i] = m0 + i;
-            continue;
-        }
-        int np2 = 1;
-        while (np2 < n) np2 <<= 1;
-        for (int i = threadIdx.x; i < np2; i += blockDim.x) {
-            if (i < n) {
-                const uint64_t a = anchor[m0 + i];
-                // z, y, x of the anchor, 10 bits each (wrapped cells modulo 1024 still sort locally)
-                const unsigned long long key = ((unsigned long long)(anchor_z(a) & 1023) << 20) |
-                                               ((unsigned long long)(anchor_y(a) & 1023) << 10) |
-                                               (unsigned long long)(anchor_x(a) & 1023);
-                keys[i] = (key << 32) | (unsigned)i;
-            } else {
-                keys[i] = ~0ull;
-            }
-        }
-        __syncthreads();
-        for (int k = 2; k <= np2; k <<= 1)
-            for (int j = k >> 1; j > 0; j >>= 1) {
-                for (int i = threadIdx.x; i < np2; i += blockDim.x) {
-                    const int ixj = i ^ j;
-                    if (ixj > i) {
-                        const unsigned long long x = keys[i], y = keys[ixj];
-                        if ((x > y) == ((i & k) == 0)) {
-                            keys[i] = y;
-                            keys[ixj] = x;
-                        }
-                    }
-                }
-                __syncthreads();
-            }
-        for (int i = threadIdx.x; i < n; i += blockDim.x) mperm[base + i] = m0 + (int)(keys[i] & 0xffffffffu);
-        __syncthreads();
+        for (int i = threadIdx.x; i < n; i += blockDim.x) mperm[base + i] = m0 + i;
     }
 }
 
@@ -1157,6 +1157,11 @@ static int run_mdf(ib_ctx *ctx, Arena &ar, const CaseTab &ct, const ib_particles
     int4 *box_lo = ar.take<int4>(P);
     int4 *box_dim = ar.take<int4>(P);
     int *part_of = ar.take<int>(M > 0 ? M : 1);
+    PrepScratch prep_ps;
+    prep_ps.lo = ar.take<long long>((size_t)3 * P);
+    prep_ps.hi = ar.take<long long>((size_t)3 * P);
+    prep_ps.rho2 = ar.take<unsigned long long>(P);
+    prep_ps.done = ar.take<unsigned int>(P);
     LevelOut lo;
     lo.level = ar.take<int>(P);
     lo.rank = ar.take<int>(P);
@@ -1181,16 +1186,20 @@ static int run_mdf(ib_ctx *ctx, Arena &ar, const CaseTab &ct, const ib_particles
     if (!ar.ok())
         return oom_error(ar.used, ar.cap);
     PhaseTimer tprep(ctx, IB_PHASE_MDF_PREP, s);
-    k_prep_particles<T, KER><<<P, kBlock, 0, s>>>(ct, P, pp->Xr, pp->Ur, pp->Wr, pp->marker_offset, mk->R,
-                                                 mk->dV, ms, F_out, rho, box_lo, box_dim, part_of,
+    cudaMemsetAsync(prep_ps.lo, 0x7f, sizeof(long long) * 3 * P, s);
+    cudaMemsetAsync(prep_ps.hi, 0x80, sizeof(long long) * 3 * P, s);
+    cudaMemsetAsync(prep_ps.rho2, 0, sizeof(unsigned long long) * P, s);
+    cudaMemsetAsync(prep_ps.done, 0, sizeof(unsigned int) * P, s);
+    k_prep_particles<T, KER><<<P * kPrepSplit, 256, 0, s>>>(ct, P, pp->Xr, pp->Ur, pp->Wr, pp->marker_offset, mk->R,
+                                                 mk->dV, ms, F_out, rho, box_lo, box_dim, part_of, prep_ps,
                                                  ctx->status);
     if (order == IB_ORDER_SEQUENTIAL)
-        k_conflicts<<<grid_blocks(P, 128, ctx->sm_count), 128, 0, s>>>(ct, P, KW, pp->Xr, rho, nbr_cnt, nbr);
+        k_conflicts<<<grid_blocks(32 * P, 256, ctx->sm_count), 256, 0, s>>>(ct, P, KW, pp->Xr, rho, nbr_cnt, nbr);
     cudaFuncSetAttribute(k_levels, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLevSmem);
     k_levels<<<1, 1024, kLevSmem, s>>>(ct, P, order, KW, pp->Xr, rho, pp->marker_offset, nbr_cnt, nbr, lo, lev_work,
                                        lev_cur);
-    k_marker_order<<<P < ctx->sm_count * 2 ? P : ctx->sm_count * 2, kBlock, 0, s>>>(P, pp->marker_offset, lo.mbase,
-                                                                                    ms.anchor, mperm);
+    k_marker_order<<<P < ctx->sm_count * 4 ? P : ctx->sm_count * 4, 256, 0, s>>>(P, pp->marker_offset, lo.mbase,
+                                                                                 mperm);
     sg.part_of = part_of;
     sg.rank = lo.rank;
     sg.box_lo = box_lo;
