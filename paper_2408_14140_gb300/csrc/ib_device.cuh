@@ -28,6 +28,18 @@ __device__ __forceinline__ unsigned int ld_acquire(const unsigned int *p) {
     return v;
 }
 
+// Programmatic dependent launch (sm_90 and later).  A kernel launched with
+// programmatic stream serialization may start while the kernel before it in
+// the stream still runs.  grid_dep_wait() returns once that predecessor grid
+// has completed and its memory operations are visible to this grid;
+// grid_dep_launch() allows the successor to start once every CTA of this grid
+// has executed it (or exited).  Without the launch attribute both are no-ops.
+// The level kernels call grid_dep_launch() only after grid_dep_wait(), so a
+// grid that starts early has every grid but its predecessor complete: before
+// its wait it may read anything the predecessor does not write.
+__device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void grid_dep_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 constexpr int kBins = kRows * kBinsPerRow + 1;
 
 // Per-marker state kept in the workspace for one call.
@@ -37,6 +49,46 @@ struct MarkerState {
     T *wts;            // [M][12] per-axis weights (x 0..3, y 4..7, z 8..11)
     T *A;              // [M][4] spread source of the current pass
     double *Ud;        // [M][3] desired velocity
+    // FP32 fields only: [M][8] the desired velocity as float pairs, hi
+    // (0..2) + lo (4..6), and dV / h^3 (3)
+    float *Ud32;
+};
+
+// One marker's update in one pass of Algorithm 1, given its interpolated
+// velocity U: with the velocity error e = U^d - U, the force F += e / dt
+// and the spread source A = e dV / h^3 (the field correction is S A).
+// FP64 fields: all in FP64.  FP32 fields: U^d is held as an unevaluated float
+// pair hi + lo and e = (hi - U) + lo is formed in FP32, which is within a unit
+// roundoff of e (the precision of the interpolated U itself); only the force
+// sum stays in FP64.  GB300 runs FP64 at a small fraction of its FP32 rate,
+// so this keeps a pass to six FP64 instructions per marker.
+template <typename T>
+struct PassMarker {
+    T hi[3], lo[3], q;
+    __device__ __forceinline__ void load(const MarkerState<T> &ms, const double *dV, double inv_h3, int l) {
+        if constexpr (sizeof(T) == 8) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) hi[c] = __ldg(ms.Ud + 3 * l + c);
+            q = dV[l] * inv_h3;
+        } else {
+            const float4 a = __ldg((const float4 *)(ms.Ud32 + 8 * (size_t)l));
+            const float4 b = __ldg((const float4 *)(ms.Ud32 + 8 * (size_t)l) + 1);
+            hi[0] = a.x, hi[1] = a.y, hi[2] = a.z, q = a.w;
+            lo[0] = b.x, lo[1] = b.y, lo[2] = b.z;
+        }
+    }
+    // velocity error of component c
+    __device__ __forceinline__ T err(int c, T U) const {
+        if constexpr (sizeof(T) == 8)
+            return hi[c] - U;
+        else
+            return (hi[c] - U) + lo[c];
+    }
+    // F + e / dt (one FP64 fused multiply-add)
+    __device__ __forceinline__ static double force(double F, T e, double inv_dt) {
+        return fma((double)e, inv_dt, F);
+    }
+    __device__ __forceinline__ T source(T e) const { return e * q; }
 };
 
 // Slot (spreading tile) records.
@@ -83,7 +135,9 @@ __device__ __forceinline__ T ld(const T *p) {
     return __ldg(p);
 }
 
-template <typename T, int KW, bool COH = false>
+// ALL: every tap's loads issued at once (the z loop unrolled too); the sums
+// are the same, in the same order.
+template <typename T, int KW, bool COH = false, bool ALL = false>
 __device__ __forceinline__ void interp_marker(const T *__restrict__ u, const DevGrid &g,
                                               long long N, uint64_t anc,
                                               const T *__restrict__ w, T out[3]) {
@@ -96,8 +150,7 @@ __device__ __forceinline__ void interp_marker(const T *__restrict__ u, const Dev
         iz[k] = wrap_add(az, k, g.n[2]);
     }
     T a0 = 0, a1 = 0, a2 = 0;
-#pragma unroll 1
-    for (int kz = 0; kz < KW; ++kz) {
+    auto plane = [&](int kz) {
 #pragma unroll
         for (int ky = 0; ky < KW; ++ky) {
             long long row = ((long long)iz[kz] * g.n[1] + iy[ky]) * g.n[0];
@@ -111,6 +164,13 @@ __device__ __forceinline__ void interp_marker(const T *__restrict__ u, const Dev
                 a2 += wt * ld<COH>(u + 2 * N + c);
             }
         }
+    };
+    if (ALL) {
+#pragma unroll
+        for (int kz = 0; kz < KW; ++kz) plane(kz);
+    } else {
+#pragma unroll 1
+        for (int kz = 0; kz < KW; ++kz) plane(kz);
     }
     out[0] = a0;
     out[1] = a1;
@@ -178,8 +238,12 @@ constexpr size_t tile_stage_bytes() {
 // adds their pairs in list order (ascending candidate), u += S A and, when the
 // case has a force field, f += S A / dt.  COH: the sources were written during
 // this kernel (plain loads after an acquire) rather than by an earlier one.
+// WAIT: the sources are written by the predecessor grid of a programmatic
+// dependent launch; everything else (tile metadata, candidate weights, the
+// first band cell's list head and field values) is read before
+// grid_dep_wait(), the sources after it with plain loads.
 // Ends with a CTA barrier.
-template <typename T, int KW, bool COH>
+template <typename T, int KW, bool COH, bool WAIT = false>
 __device__ __forceinline__ void gather_tile_lists(const CaseTab &ct, int cs, const Slots &sl, const T *wts,
                                                   const T *A_src, double inv_dt, T *sw, T *sA) {
     const DevCase cd = ct.get(sl.geo_case[cs]);
@@ -215,17 +279,27 @@ __device__ __forceinline__ void gather_tile_lists(const CaseTab &ct, int cs, con
         v0[2] = u[2 * N + c0];
     }
     if (staged) {
+        // weights first (written before this phase), then the sources
+        const uint32_t m0 = threadIdx.x < nc ? cand[threadIdx.x] : 0u;
         for (int i = threadIdx.x; i < nc; i += blockDim.x) {
-            const uint32_t m = cand[i];
+            const uint32_t m = i == (int)threadIdx.x ? m0 : cand[i];
             const T *wm = wts + 12 * (size_t)m;
 #pragma unroll
             for (int q = 0; q < 3; ++q)
 #pragma unroll
                 for (int j = 0; j < KW; ++j) sw[12 * i + 4 * q + j] = __ldg(wm + 4 * q + j);
+        }
+        // (no early trigger: the next interpolation starts as the gather's
+        // CTAs exit, onto idle SMs)
+        if (WAIT) grid_dep_wait();
+        for (int i = threadIdx.x; i < nc; i += blockDim.x) {
+            const uint32_t m = i == (int)threadIdx.x ? m0 : cand[i];
 #pragma unroll
-            for (int q = 0; q < 3; ++q) sA[4 * i + q] = ld<COH>(A_src + 4 * (size_t)m + q);
+            for (int q = 0; q < 3; ++q) sA[4 * i + q] = ld<COH || WAIT>(A_src + 4 * (size_t)m + q);
         }
         __syncthreads();
+    } else if (WAIT) {
+        grid_dep_wait();
     }
     for (int q = q0; q < nb; q += blockDim.x) {
         const bool first = q == q0;
@@ -247,7 +321,7 @@ __device__ __forceinline__ void gather_tile_lists(const CaseTab &ct, int cs, con
                 const T *w = wts + 12 * m;
                 const T *Ai = A_src + 4 * m;
                 wt = __ldg(w + ox) * __ldg(w + 4 + oy) * __ldg(w + 8 + oz);
-                a0 = ld<COH>(Ai), a1 = ld<COH>(Ai + 1), a2 = ld<COH>(Ai + 2);
+                a0 = ld<COH || WAIT>(Ai), a1 = ld<COH || WAIT>(Ai + 1), a2 = ld<COH || WAIT>(Ai + 2);
             }
             acc0 += wt * a0;
             acc1 += wt * a1;
@@ -382,7 +456,7 @@ struct ResidentArgs {
     unsigned int *ticket;   // next rank to take (zeroed)
     unsigned int *gwords;   // [4 * groups] group barrier words and ticket slot (zeroed; group form)
     int P, Ns;
-    double dt;
+    double dt, inv_dt;  // inv_dt = 1 / dt, formed on the host
     DevStatus *st;
 };
 

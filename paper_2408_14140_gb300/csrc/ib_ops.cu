@@ -158,9 +158,19 @@ __global__ void __launch_bounds__(256) k_prep_particles(
         ms.anchor[l] = marker_weights<T, KER>(g, x, w, first);
 #pragma unroll
         for (int k = 0; k < 12; ++k) ms.wts[12 * l + k] = w[k];
-        ms.Ud[3 * l + 0] = uc[0] + (wc[1] * r[2] - wc[2] * r[1]);
-        ms.Ud[3 * l + 1] = uc[1] + (wc[2] * r[0] - wc[0] * r[2]);
-        ms.Ud[3 * l + 2] = uc[2] + (wc[0] * r[1] - wc[1] * r[0]);
+        const double ud[3] = {uc[0] + (wc[1] * r[2] - wc[2] * r[1]), uc[1] + (wc[2] * r[0] - wc[0] * r[2]),
+                              uc[2] + (wc[0] * r[1] - wc[1] * r[0])};
+#pragma unroll
+        for (int c = 0; c < 3; ++c) ms.Ud[3 * l + c] = ud[c];
+        if (sizeof(T) == 4) {
+            float4 h, o;
+            h.x = (float)ud[0], h.y = (float)ud[1], h.z = (float)ud[2];
+            h.w = (float)(dv * g.inv_h3);
+            o.x = (float)(ud[0] - (double)h.x), o.y = (float)(ud[1] - (double)h.y);
+            o.z = (float)(ud[2] - (double)h.z), o.w = 0.f;
+            ((float4 *)(ms.Ud32 + 8 * (size_t)l))[0] = h;
+            ((float4 *)(ms.Ud32 + 8 * (size_t)l))[1] = o;
+        }
         F[3 * l] = F[3 * l + 1] = F[3 * l + 2] = 0.0;
         part_of[l] = p;
 #pragma unroll
@@ -923,6 +933,8 @@ __device__ __forceinline__ bool grid_sync(Barrier b, DevStatus *st) {
 // ---------------------------------------------------------------------------
 // persistent multidirect-forcing passes (cooperative launch)
 // ---------------------------------------------------------------------------
+constexpr int kInterpThreads = 256;  // level interpolation CTA
+
 template <typename T>
 struct PassArgs {
     CaseTab ct;        // cases: grid, u, accumulated force field (nullable)
@@ -937,7 +949,7 @@ struct PassArgs {
     const int *nlev;
     int Ns;
     int L0;  // first wavefront the persistent kernel processes
-    double dt;
+    double dt, inv_dt;  // inv_dt = 1 / dt, formed on the host
     Barrier bar;
     DevStatus *st;
 };
@@ -946,26 +958,58 @@ struct PassArgs {
 // one wavefront pass as two ordinary kernels (the form CUDA-graph replay runs
 // back to back): interpolation over the wavefront's markers, then a gather
 // with one CTA per tile (grid-stride), many CTAs per SM hiding latency.
+//
+// Every level kernel but the first of a call is launched as a programmatic
+// dependent of the one before it: it starts while its predecessor finishes,
+// loads what the predecessor does not write (marker weights, anchors, desired
+// velocities, forces; tile lists, candidate weights, the first band cell's
+// field values), then waits for the predecessor and reads what it wrote (the
+// field for an interpolation, the spread sources for a gather).  Every CTA
+// waits before it exits, so a level kernel completes only after its
+// predecessor.
 // ---------------------------------------------------------------------------
 template <typename T, int KER>
-__global__ void __launch_bounds__(256) k_interp_level(PassArgs<T> a, int L) {
+__global__ void __launch_bounds__(kInterpThreads) k_interp_level(PassArgs<T> a, int L) {
     constexpr int KW = Kernel<KER>::W;
-    if (L >= *a.nlev) return;
-    const double inv_dt = 1.0 / a.dt;
-    const int m0 = a.lev_mbeg[L], m1 = a.lev_mbeg[L + 1];
-    for (int i = m0 + blockIdx.x * blockDim.x + threadIdx.x; i < m1; i += gridDim.x * blockDim.x) {
-        const int l = a.mperm[i];
-        const DevCase &cd = a.ct.of_particle(a.part_of[l]);
-        const DevGrid g = cd.g;
+    // all 81 loads of a Roma-kernel marker in flight at once for FP32 fields
+    constexpr bool kAll = KW == 3 && sizeof(T) == 4;
+    const int nl = *a.nlev;
+    const int m0 = L < nl ? a.lev_mbeg[L] : 0, m1 = L < nl ? a.lev_mbeg[L + 1] : 0;
+    const int stride = gridDim.x * blockDim.x;
+    int i = m0 + blockIdx.x * blockDim.x + threadIdx.x;
+    // one marker's data but the field (loaded before the wait for the first)
+    int l = 0;
+    uint64_t anc = 0;
+    T w[12];
+    PassMarker<T> pm;
+    double F[3];
+    auto load = [&]() {
+        l = a.mperm[i];
+        anc = a.ms.anchor[l];
+        if (kAll)
+#pragma unroll
+            for (int k = 0; k < 12; ++k) w[k] = __ldg(a.ms.wts + 12 * (size_t)l + k);
+        pm.load(a.ms, a.dV, a.ct.of_particle(a.part_of[l]).g.inv_h3, l);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) F[c] = a.F[3 * l + c];
+    };
+    if (i < m1) load();
+    grid_dep_wait();
+    grid_dep_launch();
+    for (bool first = true; i < m1; i += stride, first = false) {
+        if (!first) load();
+        const DevCase cd = a.ct.of_particle(a.part_of[l]);
+        const DevGrid &g = cd.g;
         const long long N = (long long)g.n[0] * g.n[1] * g.n[2];
         T U[3];
-        interp_marker<T, KW, false>((const T *)cd.u, g, N, a.ms.anchor[l], a.ms.wts + 12 * (size_t)l, U);
-        const double q = a.dV[l] * g.inv_h3;
+        // the field was written by the predecessor: plain loads
+        // (weights from registers when every tap is unrolled, else from memory)
+        interp_marker<T, KW, true, kAll>((const T *)cd.u, g, N, anc, kAll ? w : a.ms.wts + 12 * (size_t)l, U);
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            const double e = a.ms.Ud[3 * l + c] - (double)U[c];
-            a.F[3 * l + c] += e * inv_dt;
-            a.ms.A[4 * l + c] = (T)(e * q);
+            const T e = pm.err(c, U[c]);
+            a.F[3 * l + c] = PassMarker<T>::force(F[c], e, a.inv_dt);
+            a.ms.A[4 * l + c] = pm.source(e);
         }
     }
 }
@@ -973,15 +1017,20 @@ __global__ void __launch_bounds__(256) k_interp_level(PassArgs<T> a, int L) {
 // The wavefront gather, one CTA per tile (grid-stride), many CTAs per SM,
 // over the tiles' per-cell lists (sums bitwise those of the bin walk).
 template <typename T, int KER>
-__global__ void __launch_bounds__(256, 5) k_gather_level(PassArgs<T> a, int L) {
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 5 : 4) k_gather_level(PassArgs<T> a, int L) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    if (L >= *a.nlev) return;
     T *sw = (T *)smem_raw;                          // [N][12]
     T *sA = sw + (size_t)TileStage<T>::N * 12;      // [N][4]
-    const double inv_dt = 1.0 / a.dt;
-    const int s0 = a.lev_sbeg[L], s1 = a.lev_sbeg[L + 1];
+    const double inv_dt = a.inv_dt;
+    const int nl = *a.nlev;
+    const int s0 = L < nl ? a.lev_sbeg[L] : 0, s1 = L < nl ? a.lev_sbeg[L + 1] : 0;
+    if (s0 + (int)blockIdx.x >= s1) {
+        grid_dep_wait();
+        return;
+    }
+    // (the wait inside returns at once after the first tile)
     for (int cs = s0 + blockIdx.x; cs < s1; cs += gridDim.x)
-        gather_tile_lists<T, Kernel<KER>::W, false>(a.ct, cs, a.sl, a.ms.wts, a.ms.A, inv_dt, sw, sA);
+        gather_tile_lists<T, Kernel<KER>::W, false, true>(a.ct, cs, a.sl, a.ms.wts, a.ms.A, inv_dt, sw, sA);
 }
 
 template <typename T, int KER>
@@ -991,7 +1040,7 @@ __global__ void __launch_bounds__(256) k_mdf_passes(PassArgs<T> a) {
     T *sw = (T *)smem_raw;                      // [N][12]
     T *sA = sw + (size_t)TileStage<T>::N * 12;  // [N][4]
     const int nl = *a.nlev;
-    const double inv_dt = 1.0 / a.dt;
+    const double inv_dt = a.inv_dt;
     const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
     const int gsz = gridDim.x * blockDim.x;
     for (int L = a.L0; L < nl; ++L) {
@@ -1006,12 +1055,13 @@ __global__ void __launch_bounds__(256) k_mdf_passes(PassArgs<T> a) {
                 const long long N = (long long)g.n[0] * g.n[1] * g.n[2];
                 T U[3];
                 interp_marker<T, KW, true>((const T *)cd.u, g, N, a.ms.anchor[l], a.ms.wts + 12 * (size_t)l, U);
-                const double q = a.dV[l] * g.inv_h3;
+                PassMarker<T> pm;
+                pm.load(a.ms, a.dV, g.inv_h3, l);
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
-                    const double e = a.ms.Ud[3 * l + c] - (double)U[c];
-                    a.F[3 * l + c] += e * inv_dt;
-                    a.ms.A[4 * l + c] = (T)(e * q);
+                    const T e = pm.err(c, U[c]);
+                    a.F[3 * l + c] = PassMarker<T>::force(a.F[3 * l + c], e, inv_dt);
+                    a.ms.A[4 * l + c] = pm.source(e);
                 }
             }
             if (!grid_sync(a.bar, a.st)) return;
@@ -1045,6 +1095,7 @@ static bool take_markers(Arena &ar, int M, MarkerState<T> &ms) {
     ms.wts = ar.take<T>((size_t)12 * (M > 0 ? M : 1));
     ms.A = ar.take<T>((size_t)4 * (M > 0 ? M : 1));
     ms.Ud = ar.take<double>((size_t)3 * (M > 0 ? M : 1));
+    ms.Ud32 = sizeof(T) == 4 ? ar.take<float>((size_t)8 * (M > 0 ? M : 1)) : nullptr;
     return ar.ok();
 }
 
@@ -1238,6 +1289,7 @@ static int run_mdf(ib_ctx *ctx, Arena &ar, const CaseTab &ct, const ib_particles
         ra.P = P;
         ra.Ns = Ns;
         ra.dt = dt;
+        ra.inv_dt = 1.0 / dt;
         ra.st = ctx->status;
         cudaMemsetAsync(sched, 0, sizeof(unsigned int) * (P + 1), s);
         if (groups) cudaMemsetAsync(gwords, 0, sizeof(unsigned int) * 4 * ngroups, s);
@@ -1264,6 +1316,7 @@ static int run_mdf(ib_ctx *ctx, Arena &ar, const CaseTab &ct, const ib_particles
     a.nlev = lo.nlev;
     a.Ns = Ns;
     a.dt = dt;
+    a.inv_dt = 1.0 / dt;
     a.bar = bar;
     a.st = ctx->status;
     // wavefronts enqueued as separate kernels: the count the last call on this
@@ -1276,21 +1329,36 @@ static int run_mdf(ib_ctx *ctx, Arena &ar, const CaseTab &ct, const ib_particles
     // one timed phase: the wavefront kernels and the persistent remainder
     PhaseTimer tpass(ctx, IB_PHASE_MDF_PASSES, s);
     {
-        const int gi = grid_blocks(M, 256, ctx->sm_count);
+        const int gi = grid_blocks(M, kInterpThreads, ctx->sm_count);
         const size_t gsm = tile_stage_bytes<T>();
         cudaFuncSetAttribute(k_gather_level<T, KER>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsm);
         // one resident wave of gather CTAs (grid-stride over the wavefront's tiles)
         int gper = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&gper, k_gather_level<T, KER>, 256, gsm);
         const int gg = ctx->sm_count * (gper > 0 ? gper : 1);
+        // every level kernel after the first is a programmatic dependent of
+        // the one before it (see k_interp_level)
+        cudaLaunchAttribute pdl[1];
+        pdl[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        pdl[0].val.programmaticStreamSerializationAllowed = 1;
+        cudaLaunchConfig_t ci = {}, cg = {};
+        ci.gridDim = dim3(gi);
+        ci.blockDim = dim3(kInterpThreads);
+        ci.stream = s;
+        ci.attrs = pdl;
+        cg = ci;
+        cg.gridDim = dim3(gg);
+        cg.dynamicSmemBytes = gsm;
+        cg.numAttrs = 1;
         for (int L = 0; L < Lenq; ++L)
             for (int m = 0; m < Ns; ++m) {
                 {
                     PhaseTimer ti(ctx, IB_PHASE_MDF_INTERP, s);
-                    k_interp_level<T, KER><<<gi, 256, 0, s>>>(a, L);
+                    ci.numAttrs = (L > 0 || m > 0) ? 1 : 0;
+                    cudaLaunchKernelEx(&ci, k_interp_level<T, KER>, a, L);
                 }
                 PhaseTimer tg(ctx, IB_PHASE_MDF_GATHER, s);
-                k_gather_level<T, KER><<<gg, 256, gsm, s>>>(a, L);
+                cudaLaunchKernelEx(&cg, k_gather_level<T, KER>, a, L);
             }
     }
     int per_sm = 0;

@@ -110,7 +110,7 @@ __global__ void __launch_bounds__(kGroupThreads) k_mdf_groups(ResidentArgs<T> a)
     __shared__ int s_t;
     const int grp = blockIdx.x / G, r = blockIdx.x % G;
     unsigned int *gw = a.gwords + 4 * (size_t)grp;  // count, generation, ticket slot
-    const double inv_dt = 1.0 / a.dt;
+    const double inv_dt = a.inv_dt;
     bool go_on = true;  // thread 0: no dependency wait has timed out
     for (;;) {
         // ---- next particle: the group's first CTA takes a ticket for all
@@ -139,12 +139,13 @@ __global__ void __launch_bounds__(kGroupThreads) k_mdf_groups(ResidentArgs<T> a)
                 const int l = a.mperm[i];
                 T U[3];
                 interp_marker<T, KW, true>(u, g, N, a.ms.anchor[l], a.ms.wts + 12 * (size_t)l, U);
-                const double qv = a.dV[l] * g.inv_h3;
+                PassMarker<T> pm;
+                pm.load(a.ms, a.dV, g.inv_h3, l);
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
-                    const double e = a.ms.Ud[3 * l + c] - (double)U[c];
-                    a.F[3 * l + c] += e * inv_dt;
-                    a.ms.A[4 * l + c] = (T)(e * qv);
+                    const T e = pm.err(c, U[c]);
+                    a.F[3 * l + c] = PassMarker<T>::force(a.F[3 * l + c], e, inv_dt);
+                    a.ms.A[4 * l + c] = pm.source(e);
                 }
             }
             if (!group_sync(gw, gw + 1, G, a.st)) return;

@@ -127,7 +127,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_mdf_resident(ResidentArgs<T> a) {
     const int tid = threadIdx.x;
     const int tx = tid & 7, ty = (tid >> 3) & 7, tz = tid >> 6;
     if (tid < C) s_ru[tid] = cl.map_shared_rank(sm.u, tid);
-    const double inv_dt = 1.0 / a.dt;
+    const double inv_dt = a.inv_dt;
     bool go_on = true;  // thread 0: no wait has timed out
     for (;;) {
         // ---- next particle: rank 0 takes a ticket, every CTA reads it
@@ -243,12 +243,13 @@ __global__ void __launch_bounds__(kBlock, 1) k_mdf_resident(ResidentArgs<T> a) {
                     }
                     const T U[3] = {a0, a1, a2};
                     const int l = sm.id[i];
-                    const double qv = a.dV[l] * g.inv_h3;
+                    PassMarker<T> pm;
+                    pm.load(a.ms, a.dV, g.inv_h3, l);
 #pragma unroll
                     for (int c = 0; c < 3; ++c) {
-                        const double e = a.ms.Ud[3 * l + c] - (double)U[c];
-                        if (pk >> 18) a.F[3 * l + c] += e * inv_dt;
-                        sm.A[4 * i + c] = (T)(e * qv);
+                        const T e = pm.err(c, U[c]);
+                        if (pk >> 18) a.F[3 * l + c] = PassMarker<T>::force(a.F[3 * l + c], e, inv_dt);
+                        sm.A[4 * i + c] = pm.source(e);
                     }
                 }
                 cl.sync();  // all reads of u done before any tile is updated
@@ -294,12 +295,13 @@ __global__ void __launch_bounds__(kBlock, 1) k_mdf_resident(ResidentArgs<T> a) {
                     const int l = a.mperm[i];
                     T U[3];
                     interp_marker<T, KW, true>(u, g, N, a.ms.anchor[l], a.ms.wts + 12 * (size_t)l, U);
-                    const double qv = a.dV[l] * g.inv_h3;
+                    PassMarker<T> pm;
+                    pm.load(a.ms, a.dV, g.inv_h3, l);
 #pragma unroll
                     for (int c = 0; c < 3; ++c) {
-                        const double e = a.ms.Ud[3 * l + c] - (double)U[c];
-                        a.F[3 * l + c] += e * inv_dt;
-                        a.ms.A[4 * l + c] = (T)(e * qv);
+                        const T e = pm.err(c, U[c]);
+                        a.F[3 * l + c] = PassMarker<T>::force(a.F[3 * l + c], e, inv_dt);
+                        a.ms.A[4 * l + c] = pm.source(e);
                     }
                 }
                 cluster_gpu_sync(cl, a.ticket);
