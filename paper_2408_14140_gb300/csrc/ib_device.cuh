@@ -34,9 +34,10 @@ __device__ __forceinline__ unsigned int ld_acquire(const unsigned int *p) {
 // has completed and its memory operations are visible to this grid;
 // grid_dep_launch() allows the successor to start once every CTA of this grid
 // has executed it (or exited).  Without the launch attribute both are no-ops.
-// The level kernels call grid_dep_launch() only after grid_dep_wait(), so a
-// grid that starts early has every grid but its predecessor complete: before
-// its wait it may read anything the predecessor does not write.
+// Every CTA of a level kernel waits before it exits and triggers, if at all,
+// only after its wait, so a grid that starts early has every grid but its
+// predecessor complete: before its wait it may read anything the
+// predecessor does not write.
 __device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void grid_dep_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
@@ -238,12 +239,8 @@ constexpr size_t tile_stage_bytes() {
 // adds their pairs in list order (ascending candidate), u += S A and, when the
 // case has a force field, f += S A / dt.  COH: the sources were written during
 // this kernel (plain loads after an acquire) rather than by an earlier one.
-// WAIT: the sources are written by the predecessor grid of a programmatic
-// dependent launch; everything else (tile metadata, candidate weights, the
-// first band cell's list head and field values) is read before
-// grid_dep_wait(), the sources after it with plain loads.
 // Ends with a CTA barrier.
-template <typename T, int KW, bool COH, bool WAIT = false>
+template <typename T, int KW, bool COH>
 __device__ __forceinline__ void gather_tile_lists(const CaseTab &ct, int cs, const Slots &sl, const T *wts,
                                                   const T *A_src, double inv_dt, T *sw, T *sA) {
     const DevCase cd = ct.get(sl.geo_case[cs]);
@@ -267,16 +264,21 @@ __device__ __forceinline__ void gather_tile_lists(const CaseTab &ct, int cs, con
     // this thread's first band cell, its list head and its u values are
     // loaded before the staging barrier (none of them changes meanwhile: a
     // band cell is updated by its own thread only)
+    // (and the first batch of its pairs)
+    constexpr int kPB = 8;  // pairs loaded per batch, all in flight at once
     const int q0 = threadIdx.x;
     int2 e0 = make_int2(0, 0);
     long long c0 = 0;
     T v0[3] = {T(0), T(0), T(0)};
+    uint32_t pb0[kPB];
     if (q0 < nb) {
         e0 = band[q0];
         c0 = cell_index(e0.x & 0xffff);
         v0[0] = u[c0];
         v0[1] = u[N + c0];
         v0[2] = u[2 * N + c0];
+#pragma unroll
+        for (int j = 0; j < kPB; ++j) pb0[j] = j < (e0.x >> 16) ? pairs[e0.y + j] : 0u;
     }
     if (staged) {
         // weights first (written before this phase), then the sources
@@ -289,17 +291,12 @@ __device__ __forceinline__ void gather_tile_lists(const CaseTab &ct, int cs, con
 #pragma unroll
                 for (int j = 0; j < KW; ++j) sw[12 * i + 4 * q + j] = __ldg(wm + 4 * q + j);
         }
-        // (no early trigger: the next interpolation starts as the gather's
-        // CTAs exit, onto idle SMs)
-        if (WAIT) grid_dep_wait();
         for (int i = threadIdx.x; i < nc; i += blockDim.x) {
             const uint32_t m = i == (int)threadIdx.x ? m0 : cand[i];
 #pragma unroll
-            for (int q = 0; q < 3; ++q) sA[4 * i + q] = ld<COH || WAIT>(A_src + 4 * (size_t)m + q);
+            for (int q = 0; q < 3; ++q) sA[4 * i + q] = ld<COH>(A_src + 4 * (size_t)m + q);
         }
         __syncthreads();
-    } else if (WAIT) {
-        grid_dep_wait();
     }
     for (int q = q0; q < nb; q += blockDim.x) {
         const bool first = q == q0;
@@ -307,25 +304,33 @@ __device__ __forceinline__ void gather_tile_lists(const CaseTab &ct, int cs, con
         const int cnt = e.x >> 16;
         const uint32_t *pr = pairs + e.y;
         T acc0 = 0, acc1 = 0, acc2 = 0;
-        for (int k = 0; k < cnt; ++k) {
-            const uint32_t pk = pr[k];
-            const int i = pk & 0xffff, ox = (pk >> 16) & 3, oy = (pk >> 18) & 3, oz = (pk >> 20) & 3;
-            T wt, a0, a1, a2;
-            if (staged) {
-                const T *w = sw + 12 * i;
-                const T *Ai = sA + 4 * i;
-                wt = w[ox] * w[4 + oy] * w[8 + oz];
-                a0 = Ai[0], a1 = Ai[1], a2 = Ai[2];
-            } else {
-                const size_t m = cand[i];
-                const T *w = wts + 12 * m;
-                const T *Ai = A_src + 4 * m;
-                wt = __ldg(w + ox) * __ldg(w + 4 + oy) * __ldg(w + 8 + oz);
-                a0 = ld<COH || WAIT>(Ai), a1 = ld<COH || WAIT>(Ai + 1), a2 = ld<COH || WAIT>(Ai + 2);
+        for (int k0 = 0; k0 < cnt; k0 += kPB) {
+            uint32_t pk[kPB];
+#pragma unroll
+            for (int j = 0; j < kPB; ++j)
+                pk[j] = (first && k0 == 0) ? pb0[j] : (k0 + j < cnt ? pr[k0 + j] : 0u);
+#pragma unroll
+            for (int j = 0; j < kPB; ++j) {
+                if (k0 + j >= cnt) break;
+                const int i = pk[j] & 0xffff, ox = (pk[j] >> 16) & 3, oy = (pk[j] >> 18) & 3,
+                          oz = (pk[j] >> 20) & 3;
+                T wt, a0, a1, a2;
+                if (staged) {
+                    const T *w = sw + 12 * i;
+                    const T *Ai = sA + 4 * i;
+                    wt = w[ox] * w[4 + oy] * w[8 + oz];
+                    a0 = Ai[0], a1 = Ai[1], a2 = Ai[2];
+                } else {
+                    const size_t m = cand[i];
+                    const T *w = wts + 12 * m;
+                    const T *Ai = A_src + 4 * m;
+                    wt = __ldg(w + ox) * __ldg(w + 4 + oy) * __ldg(w + 8 + oz);
+                    a0 = ld<COH>(Ai), a1 = ld<COH>(Ai + 1), a2 = ld<COH>(Ai + 2);
+                }
+                acc0 += wt * a0;
+                acc1 += wt * a1;
+                acc2 += wt * a2;
             }
-            acc0 += wt * a0;
-            acc1 += wt * a1;
-            acc2 += wt * a2;
         }
         const long long c = first ? c0 : cell_index(e.x & 0xffff);
         const T u0 = first ? v0[0] : u[c], u1 = first ? v0[1] : u[N + c], u2 = first ? v0[2] : u[2 * N + c];

@@ -934,6 +934,7 @@ __device__ __forceinline__ bool grid_sync(Barrier b, DevStatus *st) {
 // persistent multidirect-forcing passes (cooperative launch)
 // ---------------------------------------------------------------------------
 constexpr int kInterpThreads = 256;  // level interpolation CTA
+constexpr int kGatherThreads = 256;  // level gather CTA (one tile at a time)
 
 template <typename T>
 struct PassArgs {
@@ -966,7 +967,10 @@ struct PassArgs {
 // field values), then waits for the predecessor and reads what it wrote (the
 // field for an interpolation, the spread sources for a gather).  Every CTA
 // waits before it exits, so a level kernel completes only after its
-// predecessor.
+// predecessor.  An interpolation lets its gather start right after its own
+// wait (the gather's CTAs stage their lists meanwhile); a gather lets the next
+// interpolation start only as its CTAs exit, so that interpolation's CTAs
+// land on idle SMs (measured faster than an early start).
 // ---------------------------------------------------------------------------
 template <typename T, int KER>
 __global__ void __launch_bounds__(kInterpThreads) k_interp_level(PassArgs<T> a, int L) {
@@ -1016,12 +1020,167 @@ __global__ void __launch_bounds__(kInterpThreads) k_interp_level(PassArgs<T> a, 
 
 // The wavefront gather, one CTA per tile (grid-stride), many CTAs per SM,
 // over the tiles' per-cell lists (sums bitwise those of the bin walk).
+//
+// Before the wait (nothing here is written by the interpolation): the tile's
+// candidate weights and its pairs are staged in shared memory, and each
+// thread loads the list heads and field values of its (at most two) band
+// cells.  After the wait only the spread sources are loaded; the sums then
+// run from shared memory and registers.  Each cell's pairs are added in list
+// order, as in gather_tile_lists.
+constexpr int kLevPairs = 3072;  // pairs staged per tile (more: read from memory)
+
+template <typename T>
+constexpr size_t level_stage_bytes() {
+    return tile_stage_bytes<T>() + (size_t)kLevPairs * sizeof(uint32_t);
+}
+
+template <typename T, int KW>
+__device__ __forceinline__ void gather_tile_level(const CaseTab &ct, int cs, const Slots &sl, const T *wts,
+                                                  const T *A_src, double inv_dt, T *sw, T *sA,
+                                                  uint32_t *sp) {
+    const DevCase cd = ct.get(sl.geo_case[cs]);
+    const DevGrid &g = cd.g;
+    const long long N = (long long)g.n[0] * g.n[1] * g.n[2];
+    T *const u = (T *)cd.u;
+    T *const f_out = (T *)cd.f;
+    const int4 lo = sl.geo_lo[cs], dim = sl.geo_dim[cs];
+    const uint32_t d = sl.dense_of[cs];
+    const int nc = (int)(sl.start[d + 1] - sl.start[d]);
+    const int nb = sl.nband[cs];
+    const uint32_t *cand = sl.cand + dim.w;
+    const uint32_t pb = sl.poff[dim.w];
+    const int np = (int)(sl.poff[dim.w + nc] - pb);
+    const int2 *band = sl.band + pb;
+    const uint32_t *pairs = sl.pairs + pb;
+    const bool staged = nc <= TileStage<T>::N, pstaged = np <= kLevPairs;
+    auto cell_index = [&](int cell) {
+        const int tx = cell & 7, ty = (cell >> 3) & 7, tz = cell >> 6;
+        return ((long long)wrap_add(lo.z, tz, g.n[2]) * g.n[1] + wrap_add(lo.y, ty, g.n[1])) * g.n[0] +
+               wrap_add(lo.x, tx, g.n[0]);
+    };
+    // ---- before the wait
+    int2 e[2];
+    long long c[2];
+    T v[2][3];
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+        const int q = threadIdx.x + j * blockDim.x;
+        e[j] = make_int2(0, 0);
+        c[j] = 0;
+        v[j][0] = v[j][1] = v[j][2] = T(0);
+        if (q < nb) {
+            e[j] = band[q];
+            c[j] = cell_index(e[j].x & 0xffff);
+            v[j][0] = u[c[j]];
+            v[j][1] = u[N + c[j]];
+            v[j][2] = u[2 * N + c[j]];
+        }
+    }
+    if (pstaged)
+        for (int k = threadIdx.x; k < np; k += blockDim.x) sp[k] = __ldg(pairs + k);
+    const uint32_t m0 = (staged && (int)threadIdx.x < nc) ? cand[threadIdx.x] : 0u;
+    if (staged)
+        for (int i = threadIdx.x; i < nc; i += blockDim.x) {
+            const uint32_t m = i == (int)threadIdx.x ? m0 : cand[i];
+            const T *wm = wts + 12 * (size_t)m;
+#pragma unroll
+            for (int q = 0; q < 3; ++q)
+#pragma unroll
+                for (int jj = 0; jj < KW; ++jj) sw[12 * i + 4 * q + jj] = __ldg(wm + 4 * q + jj);
+        }
+    // ---- the interpolation's sources
+    grid_dep_wait();
+    if (staged)
+        for (int i = threadIdx.x; i < nc; i += blockDim.x) {
+            const uint32_t m = i == (int)threadIdx.x ? m0 : cand[i];
+#pragma unroll
+            for (int q = 0; q < 3; ++q) sA[4 * i + q] = A_src[4 * (size_t)m + q];
+        }
+    __syncthreads();
+    auto cell_sum = [&](int2 ee, T acc[3]) {
+        const int cnt = ee.x >> 16;
+        acc[0] = acc[1] = acc[2] = T(0);
+        if (staged && pstaged) {
+            // batches of kSB pairs: every shared-memory load of a batch is
+            // issued before its sums, which are added in list order
+            constexpr int kSB = 4;
+            for (int k0 = 0; k0 < cnt; k0 += kSB) {
+                uint32_t pk[kSB];
+#pragma unroll
+                for (int j = 0; j < kSB; ++j) pk[j] = k0 + j < cnt ? sp[ee.y + k0 + j] : 0u;
+                T wt[kSB], a[kSB][3];
+#pragma unroll
+                for (int j = 0; j < kSB; ++j) {
+                    const int i = pk[j] & 0xffff, ox = (pk[j] >> 16) & 3, oy = (pk[j] >> 18) & 3,
+                              oz = (pk[j] >> 20) & 3;
+                    const T *w = sw + 12 * i;
+                    const T *Ai = sA + 4 * i;
+                    wt[j] = w[ox] * w[4 + oy] * w[8 + oz];
+                    a[j][0] = Ai[0], a[j][1] = Ai[1], a[j][2] = Ai[2];
+                }
+#pragma unroll
+                for (int j = 0; j < kSB; ++j)
+                    if (k0 + j < cnt) {
+                        acc[0] += wt[j] * a[j][0];
+                        acc[1] += wt[j] * a[j][1];
+                        acc[2] += wt[j] * a[j][2];
+                    }
+            }
+            return;
+        }
+        for (int k = 0; k < cnt; ++k) {
+            const uint32_t pk = pstaged ? sp[ee.y + k] : __ldg(pairs + ee.y + k);
+            const int i = pk & 0xffff, ox = (pk >> 16) & 3, oy = (pk >> 18) & 3, oz = (pk >> 20) & 3;
+            T wt, a0, a1, a2;
+            if (staged) {
+                const T *w = sw + 12 * i;
+                const T *Ai = sA + 4 * i;
+                wt = w[ox] * w[4 + oy] * w[8 + oz];
+                a0 = Ai[0], a1 = Ai[1], a2 = Ai[2];
+            } else {
+                const size_t m = cand[i];
+                const T *w = wts + 12 * m;
+                const T *Ai = A_src + 4 * m;
+                wt = __ldg(w + ox) * __ldg(w + 4 + oy) * __ldg(w + 8 + oz);
+                a0 = Ai[0], a1 = Ai[1], a2 = Ai[2];
+            }
+            acc[0] += wt * a0;
+            acc[1] += wt * a1;
+            acc[2] += wt * a2;
+        }
+    };
+    auto update = [&](long long cc, const T vv[3], const T acc[3]) {
+#pragma unroll
+        for (int q = 0; q < 3; ++q) u[q * N + cc] = vv[q] + acc[q];
+        if (f_out)
+#pragma unroll
+            for (int q = 0; q < 3; ++q) f_out[q * N + cc] += (T)(acc[q] * inv_dt);
+    };
+#pragma unroll
+    for (int j = 0; j < 2; ++j)
+        if ((int)threadIdx.x + j * (int)blockDim.x < nb) {
+            T acc[3];
+            cell_sum(e[j], acc);
+            update(c[j], v[j], acc);
+        }
+    // cells beyond two per thread (blocks smaller than half a tile)
+    for (int q = threadIdx.x + 2 * blockDim.x; q < nb; q += blockDim.x) {
+        const int2 ee = band[q];
+        const long long cc = cell_index(ee.x & 0xffff);
+        T acc[3];
+        cell_sum(ee, acc);
+        const T vv[3] = {u[cc], u[N + cc], u[2 * N + cc]};
+        update(cc, vv, acc);
+    }
+    __syncthreads();
+}
+
 template <typename T, int KER>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 5 : 4) k_gather_level(PassArgs<T> a, int L) {
+__global__ void __launch_bounds__(kGatherThreads, sizeof(T) == 4 ? 5 : 4) k_gather_level(PassArgs<T> a, int L) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *sw = (T *)smem_raw;                          // [N][12]
     T *sA = sw + (size_t)TileStage<T>::N * 12;      // [N][4]
-    const double inv_dt = a.inv_dt;
+    uint32_t *sp = (uint32_t *)(sA + (size_t)TileStage<T>::N * 4);  // [kLevPairs]
     const int nl = *a.nlev;
     const int s0 = L < nl ? a.lev_sbeg[L] : 0, s1 = L < nl ? a.lev_sbeg[L + 1] : 0;
     if (s0 + (int)blockIdx.x >= s1) {
@@ -1030,7 +1189,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 5 : 4) k_gather_level(Pa
     }
     // (the wait inside returns at once after the first tile)
     for (int cs = s0 + blockIdx.x; cs < s1; cs += gridDim.x)
-        gather_tile_lists<T, Kernel<KER>::W, false, true>(a.ct, cs, a.sl, a.ms.wts, a.ms.A, inv_dt, sw, sA);
+        gather_tile_level<T, Kernel<KER>::W>(a.ct, cs, a.sl, a.ms.wts, a.ms.A, a.inv_dt, sw, sA, sp);
 }
 
 template <typename T, int KER>
@@ -1330,11 +1489,11 @@ static int run_mdf(ib_ctx *ctx, Arena &ar, const CaseTab &ct, const ib_particles
     PhaseTimer tpass(ctx, IB_PHASE_MDF_PASSES, s);
     {
         const int gi = grid_blocks(M, kInterpThreads, ctx->sm_count);
-        const size_t gsm = tile_stage_bytes<T>();
+        const size_t gsm = level_stage_bytes<T>();
         cudaFuncSetAttribute(k_gather_level<T, KER>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsm);
         // one resident wave of gather CTAs (grid-stride over the wavefront's tiles)
         int gper = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&gper, k_gather_level<T, KER>, 256, gsm);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&gper, k_gather_level<T, KER>, kGatherThreads, gsm);
         const int gg = ctx->sm_count * (gper > 0 ? gper : 1);
         // every level kernel after the first is a programmatic dependent of
         // the one before it (see k_interp_level)
@@ -1348,6 +1507,7 @@ static int run_mdf(ib_ctx *ctx, Arena &ar, const CaseTab &ct, const ib_particles
         ci.attrs = pdl;
         cg = ci;
         cg.gridDim = dim3(gg);
+        cg.blockDim = dim3(kGatherThreads);
         cg.dynamicSmemBytes = gsm;
         cg.numAttrs = 1;
         for (int L = 0; L < Lenq; ++L)
