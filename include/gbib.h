@@ -168,8 +168,10 @@ GBIB_API int ib_ctx_set_pass_kernels(ib_ctx *ctx, int which);
 
 /* ---- CTAs per particle of the volume integrals (tuning knob) -----------
  * Each particle's box is cut into this many slabs of cell planes, one CTA
- * each (default 8; 1 <= n <= 32).  Results do not depend on it beyond the
- * rounding of the partial sums' grouping.  IB_ERR_INVALID outside the range. */
+ * each (1 <= n <= 32), or 0 (the default): as many as fill one resident wave
+ * of the device for the call's particle count (at least 1, at most 32).
+ * Results do not depend on it beyond the rounding of the partial sums'
+ * grouping.  IB_ERR_INVALID outside [0, 32].                              */
 GBIB_API int ib_ctx_set_volume_split(ib_ctx *ctx, int ctas_per_particle);
 
 /* ---- velocity interpolation J: Eq. (u), Eq. (vi), Algorithm 1 -----------

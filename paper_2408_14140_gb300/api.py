@@ -222,7 +222,7 @@ class Context:
         self._check(self.lib.ib_ctx_set_pass_kernels(self.handle, PASSES[which]))
 
     def set_volume_split(self, ctas_per_particle: int):
-        """CTAs per particle of the volume integrals (see gbib.h)."""
+        """CTAs per particle of the volume integrals, 0 = automatic (see gbib.h)."""
         self._check(self.lib.ib_ctx_set_volume_split(self.handle, int(ctas_per_particle)))
 
     def read_timing(self, phase: str):

@@ -6,8 +6,8 @@ laid out on the GPU, never the results:
 * the kernels of the sequential-order passes (``wavefront``: one
   interpolation and one gather kernel per wavefront and pass; ``groups``: a
   persistent launch with a CTA group per particle) -- bitwise the same;
-* the CTAs per particle of the volume integrals (slabs of cell planes) --
-  the same sums, grouped differently.
+* the CTAs per particle of the volume integrals (slabs of cell planes; 0:
+  one resident wave) -- the same sums, grouped differently.
 
 :func:`tune` times a caller-supplied step (the call sequence of the
 workload) for every combination on the device -- CUDA events on the current
@@ -22,7 +22,7 @@ import statistics
 
 import torch
 
-SPACE = {"pass_kernels": ("wavefront", "groups"), "volume_split": (4, 8, 16)}
+SPACE = {"pass_kernels": ("wavefront", "groups"), "volume_split": (0, 4, 8, 16)}
 
 
 def apply(ctxs, choice: dict):

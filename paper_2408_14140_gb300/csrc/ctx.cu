@@ -319,7 +319,7 @@ int ib_ctx_create(ib_ctx **ctx, size_t workspace_bytes) {
     }
     *c->h_nlev = 0;
     c->pass_kernels = IB_PASSES_AUTO;
-    c->vol_split = 8;
+    c->vol_split = 0;  // automatic
     for (int k = 0; k < ib_ctx::kStageSlots; ++k) {
         c->stage_ptr[k] = nullptr;
         c->stage_cap[k] = 0;
@@ -363,8 +363,8 @@ int ib_ctx_set_pass_kernels(ib_ctx *c, int which) {
 
 int ib_ctx_set_volume_split(ib_ctx *c, int ctas_per_particle) {
     if (!c) return set_error(IB_ERR_INVALID, "ctx is NULL");
-    if (ctas_per_particle < 1 || ctas_per_particle > 32)
-        return set_error(IB_ERR_INVALID, "volume split %d outside [1, 32]", ctas_per_particle);
+    if (ctas_per_particle < 0 || ctas_per_particle > 32)
+        return set_error(IB_ERR_INVALID, "volume split %d outside [0, 32]", ctas_per_particle);
     c->vol_split = ctas_per_particle;
     return IB_OK;
 }

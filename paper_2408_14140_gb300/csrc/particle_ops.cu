@@ -49,7 +49,7 @@ __device__ __forceinline__ void block_sum(double v[NV]) {
 // the others form alpha from their eight corner values.  The last CTA of a
 // particle (completion counter) adds the nsplit partial sums in slab order.
 // ---------------------------------------------------------------------------
-constexpr int kVolSplit = 8;       // default CTAs per particle (the context may choose another)
+constexpr int kVolSplit = 8;       // CTAs per particle of the allocation-free entry point
 constexpr int kVolMaxSplit = 32;
 constexpr int kVolThreads = 256;   // 8 warps
 constexpr int kVolMaxBox = 40;     // cells per axis of one particle's box (tabulated path)
@@ -57,7 +57,43 @@ constexpr int kVolAx = kVolMaxBox + 1;
 // two node planes of (max(-phi, 0), max(phi, 0)) pairs + per-axis tables
 // (node squares, cell offsets, cell squares) + per-row grid offsets
 constexpr size_t kVolSmem = 2 * kVolAx * kVolAx * sizeof(double2) + 9 * kVolAx * sizeof(double) +
-                            kVolAx * sizeof(long long);
+                            kVolAx * sizeof(long long) + 3 * kVolAx * sizeof(float2);
+
+// Double-float accumulation: a sum kept as the unevaluated pair hi + lo of two
+// floats -- Knuth's TwoSum for the addition error and the fused multiply-add
+// for the exact product error (Dekker 1971) -- about 44 significant bits on
+// the FP32 pipes, which run 64 times faster than FP64 on GB300.  Used for the
+// field sums of FP32 fields; the level set and alpha stay FP64.
+struct DF {
+    float hi, lo;
+};
+__device__ __forceinline__ void df_add2(DF &a, float bh, float bl) {
+    const float s = a.hi + bh;
+    const float bb = s - a.hi;
+    const float e = (a.hi - (s - bb)) + (bh - bb);
+    a.hi = s;
+    a.lo += e + bl;
+}
+// a += (rh + rl) (wh + wl), keeping the product's rounding error and the
+// first-order cross terms
+__device__ __forceinline__ void df_add_prod(DF &a, float rh, float rl, float wh, float wl) {
+    const float pr = rh * wh;
+    const float pe = fmaf(rh, wh, -pr) + fmaf(rh, wl, rl * wh);
+    df_add2(a, pr, pe);
+}
+// hi + lo of every lane added over the warp (fixed shuffle order); result in lane 0
+__device__ __forceinline__ void df_warp_sum(DF &a) {
+    for (int o = 16; o > 0; o >>= 1) {
+        const float bh = __shfl_down_sync(0xffffffffu, a.hi, o), bl = __shfl_down_sync(0xffffffffu, a.lo, o);
+        const float lo = a.lo;
+        a.lo = 0.f;
+        df_add2(a, bh, bl + lo);
+    }
+}
+__device__ __forceinline__ float2 df_split(double x) {
+    const float h = (float)x;
+    return make_float2(h, (float)(x - (double)h));
+}
 
 // |x| from x^2 to within a few units of FP64 rounding: an FP32 square root
 // refined by one Newton step in FP64 (s = s0 + (x2 - s0^2) / (2 s0), the
@@ -112,31 +148,33 @@ __device__ __forceinline__ int find_row(const int *pre, int nrows, int t) {
 // sums, scaled by h^3, is stored as slab `split` of particle p; the last slab
 // of the particle to finish (completion counter) adds the nsplit slabs in
 // order and writes the particle's integrals.
+// s_acc: shared scratch of 7 * kVolThreads doubles (the kernel's dynamic shared
+// memory, free again once the CTA's sums are done).
 __device__ void volume_finish(double acc[7], double h, int p, int split, int nsplit, double *__restrict__ partial,
-                              unsigned int *__restrict__ done, double *Iu, double *Irxu, double *vol) {
+                              unsigned int *__restrict__ done, double *Iu, double *Irxu, double *vol, double *s_acc) {
     __shared__ int s_last;
     // fixed-order CTA sum of the 7 partials through shared memory: 7 warps,
     // one per quantity, each lane adding 8 entries then a shuffle tree (FP64
     // adds are scarce on this part: a shuffle tree over all 256 threads would
     // cost more FP64 work than a thin slab's cells)
     {
-        __shared__ double s_acc[7][kVolThreads];
+        __syncthreads();  // every thread is done with the shared memory reused here
 #pragma unroll
-        for (int k = 0; k < 7; ++k) s_acc[k][threadIdx.x] = acc[k];
+        for (int k = 0; k < 7; ++k) s_acc[k * kVolThreads + threadIdx.x] = acc[k];
         __syncthreads();
         const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5;
         if (wq < 7) {
             double x = 0.0;
 #pragma unroll
-            for (int m = 0; m < kVolThreads / 32; ++m) x += s_acc[wq][lane + 32 * m];
+            for (int m = 0; m < kVolThreads / 32; ++m) x += s_acc[wq * kVolThreads + lane + 32 * m];
             for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
-            if (lane == 0) s_acc[wq][0] = x;
+            if (lane == 0) s_acc[wq * kVolThreads] = x;
         }
         __syncthreads();
         if (threadIdx.x == 0) {
             const double h3 = h * h * h;
 #pragma unroll
-            for (int k = 0; k < 7; ++k) acc[k] = s_acc[k][0] * h3;
+            for (int k = 0; k < 7; ++k) acc[k] = s_acc[k * kVolThreads] * h3;
         }
     }
     __shared__ double s_part[kVolMaxSplit * 7];
@@ -176,7 +214,7 @@ __device__ void volume_finish(double acc[7], double h, int p, int split, int nsp
 // Per-row index ranges come from FP32 square roots widened by a cell; every
 // node and boundary cell is still tested exactly in FP64.
 template <typename T>
-__global__ void __launch_bounds__(kVolThreads) k_volume(CaseTab ct, int P, int nsplit,
+__global__ void __launch_bounds__(kVolThreads, 3) k_volume(CaseTab ct, int P, int nsplit,
                                                         const double *__restrict__ Xr,
                                                         const double *__restrict__ radius,
                                                         double *__restrict__ partial,
@@ -225,6 +263,7 @@ __global__ void __launch_bounds__(kVolThreads) k_volume(CaseTab ct, int P, int n
             double2 *phi2 = (double2 *)s_vol;  // node planes: (max(-phi, 0), max(phi, 0))
             double *tb = (double *)(phi2 + 2 * kVolAx * kVolAx);
             long long *row_off = (long long *)(tb + 9 * kVolAx);
+            float2 *tbf = (float2 *)(row_off + kVolAx);  // cell offsets as float pairs
             for (int a = 0; a < 3; ++a)
                 for (int i = threadIdx.x; i <= dims[a]; i += blockDim.x) {
                     const double xn = g.org[a] + (double)(lo[a] + i) * h - c[a];
@@ -232,6 +271,7 @@ __global__ void __launch_bounds__(kVolThreads) k_volume(CaseTab ct, int P, int n
                     tb[a * kVolAx + i] = xn * xn;
                     tb[(3 + a) * kVolAx + i] = xc;
                     tb[(6 + a) * kVolAx + i] = xc * xc;
+                    if (sizeof(T) == 4) tbf[a * kVolAx + i] = df_split(xc);
                 }
             for (int j = threadIdx.x; j < dims[1]; j += blockDim.x)
                 row_off[j] = (long long)wrap_int(lo[1] + j, g.n[1]) * g.n[0];
@@ -298,6 +338,9 @@ __global__ void __launch_bounds__(kVolThreads) k_volume(CaseTab ct, int P, int n
             //   (ry w2 - rz w1, rz w0 - rx w2, rx w1 - ry w0), w = alpha u
             double sA = 0, sB = 0, sC = 0, sD = 0, svol = 0;
             long long nint_cells = 0;
+            // FP32 fields: double-float sums of w and of ry w2, rz w1, rz w0,
+            // rx w2, rx w1, ry w0 (no FP64 work per cell but alpha's)
+            DF W[3] = {}, Pm[6] = {};
             for (int kz = z0; kz < z1; ++kz) {
                 node_plane(kz + 1, phi2 + ((kz + 1) & 1) * plane);
                 // cell rows of plane kz: interior range and the boundary ranges around it
@@ -329,6 +372,7 @@ __global__ void __launch_bounds__(kVolThreads) k_volume(CaseTab ct, int P, int n
                 warp0_scan(c_bnd, p_bnd, dims[1]);
                 __syncthreads();
                 const double2 *b0 = phi2 + (kz & 1) * plane, *b1 = phi2 + ((kz + 1) & 1) * plane;
+                const float2 fz = sizeof(T) == 4 ? tbf[2 * kVolAx + kz] : make_float2(0.f, 0.f);
                 const long long plane_off = (long long)wrap_int(lo[2] + kz, g.n[2]) * g.n[1] * g.n[0];
                 double s0 = 0, s1 = 0, s2 = 0;  // plane sums of alpha u
                 // interior cells: alpha = 1
@@ -336,8 +380,22 @@ __global__ void __launch_bounds__(kVolThreads) k_volume(CaseTab ct, int P, int n
                 for (int q = threadIdx.x; q < nint; q += blockDim.x) {
                     const int j = find_row(p_int, dims[1], q);
                     const int i = r_ic[j] + (q - p_int[j]);
-                    const double rx = tb[3 * kVolAx + i], ry = tb[4 * kVolAx + j];
                     const long long cc = plane_off + row_off[j] + wrap_add(lo0w, i, g.n[0]);
+                    if constexpr (sizeof(T) == 4) {
+                        const float2 fx = tbf[i], fy = tbf[kVolAx + j];
+                        const float v0 = u[cc], v1 = u[N + cc], v2 = u[2 * N + cc];
+                        df_add2(W[0], v0, 0.f);
+                        df_add2(W[1], v1, 0.f);
+                        df_add2(W[2], v2, 0.f);
+                        df_add_prod(Pm[0], fy.x, fy.y, v2, 0.f);
+                        df_add_prod(Pm[1], fz.x, fz.y, v1, 0.f);
+                        df_add_prod(Pm[2], fz.x, fz.y, v0, 0.f);
+                        df_add_prod(Pm[3], fx.x, fx.y, v2, 0.f);
+                        df_add_prod(Pm[4], fx.x, fx.y, v1, 0.f);
+                        df_add_prod(Pm[5], fy.x, fy.y, v0, 0.f);
+                        continue;
+                    }
+                    const double rx = tb[3 * kVolAx + i], ry = tb[4 * kVolAx + j];
                     const double u0 = (double)u[cc], u1 = (double)u[N + cc], u2 = (double)u[2 * N + cc];
                     s0 += u0;
                     s1 += u1;
@@ -371,8 +429,28 @@ __global__ void __launch_bounds__(kVolThreads) k_volume(CaseTab ct, int P, int n
                         const double den = num + neg;
                         al = den == 0.0 ? 0.5 : (neg == 0.0 ? 1.0 : (den > 1e-30 ? num * recip_refined(den) : num / den));
                     }
-                    const double rx = tb[3 * kVolAx + i], ry = tb[4 * kVolAx + j];
                     const long long cc = plane_off + row_off[j] + wrap_add(lo0w, i, g.n[0]);
+                    if constexpr (sizeof(T) == 4) {
+                        svol += al;
+                        const float2 fx = tbf[i], fy = tbf[kVolAx + j];
+                        const float2 a2 = al == 1.0 ? make_float2(1.f, 0.f) : df_split(al);
+                        const float v[3] = {u[cc], u[N + cc], u[2 * N + cc]};
+                        float wh[3], wl[3];
+#pragma unroll
+                        for (int q = 0; q < 3; ++q) {
+                            wh[q] = a2.x * v[q];
+                            wl[q] = fmaf(a2.x, v[q], -wh[q]) + a2.y * v[q];
+                            df_add2(W[q], wh[q], wl[q]);
+                        }
+                        df_add_prod(Pm[0], fy.x, fy.y, wh[2], wl[2]);
+                        df_add_prod(Pm[1], fz.x, fz.y, wh[1], wl[1]);
+                        df_add_prod(Pm[2], fz.x, fz.y, wh[0], wl[0]);
+                        df_add_prod(Pm[3], fx.x, fx.y, wh[2], wl[2]);
+                        df_add_prod(Pm[4], fx.x, fx.y, wh[1], wl[1]);
+                        df_add_prod(Pm[5], fy.x, fy.y, wh[0], wl[0]);
+                        continue;
+                    }
+                    const double rx = tb[3 * kVolAx + i], ry = tb[4 * kVolAx + j];
                     const double w0 = al * (double)u[cc], w1 = al * (double)u[N + cc], w2 = al * (double)u[2 * N + cc];
                     s0 += w0;
                     s1 += w1;
@@ -383,17 +461,38 @@ __global__ void __launch_bounds__(kVolThreads) k_volume(CaseTab ct, int P, int n
                     sD = fma(ry, w0, sD);
                     svol += al;
                 }
-                acc[0] += s0;
-                acc[1] += s1;
-                acc[2] += s2;
-                acc[3] = fma(-rz, s1, acc[3]);
-                acc[4] = fma(rz, s0, acc[4]);
+                if constexpr (sizeof(T) == 8) {
+                    acc[0] += s0;
+                    acc[1] += s1;
+                    acc[2] += s2;
+                    acc[3] = fma(-rz, s1, acc[3]);
+                    acc[4] = fma(rz, s0, acc[4]);
+                }
                 __syncthreads();
             }
-            acc[3] += sA;
-            acc[4] -= sB;
-            acc[5] += sC - sD;
+            if constexpr (sizeof(T) == 8) {
+                acc[3] += sA;
+                acc[4] -= sB;
+                acc[5] += sC - sD;
+            }
             acc[6] += svol + (double)nint_cells;
+            if constexpr (sizeof(T) == 4) {
+                // warp sums in double-float, then FP64 in lane 0 only
+#pragma unroll
+                for (int q = 0; q < 3; ++q) df_warp_sum(W[q]);
+#pragma unroll
+                for (int q = 0; q < 6; ++q) df_warp_sum(Pm[q]);
+                if ((threadIdx.x & 31) == 0) {
+                    double pm[6];
+#pragma unroll
+                    for (int q = 0; q < 6; ++q) pm[q] = (double)Pm[q].hi + (double)Pm[q].lo;
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) acc[q] = (double)W[q].hi + (double)W[q].lo;
+                    acc[3] = pm[0] - pm[1];
+                    acc[4] = pm[2] - pm[3];
+                    acc[5] = pm[4] - pm[5];
+                }
+            }
         } else {
             // boxes wider than kVolMaxBox: every cell of the slab, corners evaluated directly
             for (int kz = z0; kz < z1; ++kz) {
@@ -434,7 +533,7 @@ __global__ void __launch_bounds__(kVolThreads) k_volume(CaseTab ct, int P, int n
             }
         }
     }
-    volume_finish(acc, g.h, p, split, nsplit, partial, done, Iu, Irxu, vol);
+    volume_finish(acc, g.h, p, split, nsplit, partial, done, Iu, Irxu, vol, s_vol);
 }
 
 // ---------------------------------------------------------------------------
@@ -449,6 +548,8 @@ __global__ void __launch_bounds__(kVolThreads) k_volume(CaseTab ct, int P, int n
 // ---------------------------------------------------------------------------
 constexpr int kEllAx = 65;
 constexpr size_t kEllSmem = 2 * (size_t)kEllAx * kEllAx * sizeof(double);
+static_assert(kEllSmem >= 7 * kVolThreads * sizeof(double) && kVolSmem >= 7 * kVolThreads * sizeof(double),
+              "the CTA sum reuses the dynamic shared memory");
 
 __device__ __forceinline__ double pvf_alpha8(const double ph[8]) {
     double num = 0.0, den = 0.0;
@@ -549,7 +650,7 @@ __global__ void __launch_bounds__(kVolThreads) k_volume_ellipsoid(CaseTab ct, in
                 }
         }
     }
-    volume_finish(acc, g.h, p, split, nsplit, partial, done, Iu, Irxu, vol);
+    volume_finish(acc, g.h, p, split, nsplit, partial, done, Iu, Irxu, vol, s_phi);
 }
 
 // Drag diagnostic of Eq. FD: F_D = F_ib + rho_f (Iu^{n+1} - Iu^n) / dt.
@@ -672,17 +773,28 @@ __global__ void k_newton_euler(CollideArgs a, const double *__restrict__ Fc, Dev
     if (!ok) raise_status(st, IB_ERR_NONFINITE, p);
 }
 
+// CTAs per particle: the context's choice, or (0) as many as fill one resident
+// wave of `kern` for P particles, within [1, kVolMaxSplit].
+static int volume_split(ib_ctx *ctx, const void *kern, size_t smem, int P) {
+    if (ctx->vol_split > 0) return ctx->vol_split;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kVolThreads, smem) != cudaSuccess || per_sm < 1)
+        per_sm = 1;
+    const long long n = (long long)per_sm * ctx->sm_count / (P > 0 ? P : 1);
+    return (int)(n < 1 ? 1 : (n > kVolMaxSplit ? kVolMaxSplit : n));
+}
+
 template <typename T>
 static int run_volume(ib_ctx *ctx, Arena &ar, const CaseTab &ct, const ib_particles *pp, double *Iu,
                       double *Irxu, double *vol, cudaStream_t s) {
-    const int nsplit = ctx->vol_split;
+    cudaFuncSetAttribute(k_volume<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kVolSmem);
+    const int nsplit = volume_split(ctx, (const void *)k_volume<T>, kVolSmem, pp->P);
     double *partial = ar.take<double>((size_t)pp->P * nsplit * 7);
     unsigned int *done = ar.take<unsigned int>(pp->P);
     if (!ar.ok())
         return oom_error(ar.used, ar.cap);
     PhaseTimer tm(ctx, IB_PHASE_VOLUME, s);
     cudaMemsetAsync(done, 0, sizeof(unsigned int) * pp->P, s);
-    cudaFuncSetAttribute(k_volume<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kVolSmem);
     k_volume<T><<<pp->P * nsplit, kVolThreads, kVolSmem, s>>>(ct, pp->P, nsplit, pp->Xr, pp->radius, partial,
                                                                done, Iu, Irxu, vol, ctx->status);
     return check_launch("particle_volume_integrals");
@@ -811,7 +923,9 @@ int particle_volume_integrals_ellipsoid(ib_ctx *ctx, const ib_grid *grid, const 
     if ((long long)P * kVolMaxSplit > (1LL << 31) - 1) return set_error(IB_ERR_UNSUPPORTED, "too many particles");
     const CaseTab ct = single_case(grid, (void *)u, nullptr, P);
     Arena ar(ctx);
-    const int nsplit = ctx->vol_split;
+    const void *ek = grid->prec == IB_F64 ? (const void *)k_volume_ellipsoid<double> : (const void *)k_volume_ellipsoid<float>;
+    cudaFuncSetAttribute(ek, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kEllSmem);
+    const int nsplit = volume_split(ctx, ek, kEllSmem, P);
     double *partial = ar.take<double>((size_t)P * nsplit * 7);
     unsigned int *done = ar.take<unsigned int>(P);
     if (!ar.ok()) return oom_error(ar.used, ar.cap);
