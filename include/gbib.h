@@ -174,6 +174,19 @@ GBIB_API int ib_ctx_set_pass_kernels(ib_ctx *ctx, int which);
  * grouping.  IB_ERR_INVALID outside [0, 32].                              */
 GBIB_API int ib_ctx_set_volume_split(ib_ctx *ctx, int ctas_per_particle);
 
+/* ---- overlap: a dependency before the field is written ------------------
+ * `event` is a cudaEvent_t (or NULL, the default, for none).  Every
+ * multidirect-forcing call on this context (single or batched) makes its
+ * stream wait for the event after its preparation kernels -- which read only
+ * the particles and markers -- and before the first kernel that reads or
+ * writes the field.  A caller can so run work that reads the same field (for
+ * example the volume integrals of the same time step, on another stream and
+ * another context) concurrently with the preparation: record the event after
+ * that work and before the forcing call.  The event is waited on as recorded
+ * when the forcing call is enqueued (also inside CUDA-graph capture, where the
+ * wait becomes a graph dependency).  The context does not own the event.    */
+GBIB_API int ib_ctx_set_field_wait(ib_ctx *ctx, void *event);
+
 /* ---- velocity interpolation J: Eq. (u), Eq. (vi), Algorithm 1 -----------
  * U[l] = sum_ijk u(x_ijk) delta_h(x_ijk - X[l]) h^3 for l < M, where
  * delta_h(x) = h^-3 prod_a phi(x_a / h) (Sec. 2).  X[M][3] are absolute

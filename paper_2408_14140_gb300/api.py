@@ -44,6 +44,7 @@ PHASES = {"mdf_prep": 0, "mdf_passes": 1, "spread": 2, "interp": 3, "volume": 4,
 EXPORTS = ["ib_ctx_create", "ib_ctx_reserve", "ib_ctx_destroy", "ib_ctx_status",
            "ib_last_error", "ib_workspace_needed", "ib_ctx_sm_count",
            "ib_ctx_set_timing", "ib_ctx_read_timing", "ib_ctx_set_pass_kernels", "ib_ctx_set_volume_split",
+           "ib_ctx_set_field_wait",
            "ib_interpolate", "ib_spread", "ib_multidirect_forcing",
            "particle_volume_integrals", "particle_force_torque",
            "particle_collide_update", "particle_volume_integrals_static",
@@ -107,6 +108,7 @@ def load(path: str = LIB_PATH):
         "ib_ctx_read_timing": (i, [p, i, ctypes.POINTER(d), ctypes.POINTER(i)]),
         "ib_ctx_set_pass_kernels": (i, [p, i]),
         "ib_ctx_set_volume_split": (i, [p, i]),
+        "ib_ctx_set_field_wait": (i, [p, p]),
         "ib_interpolate": (i, [p, p, p, i, p, i, p, p]),
         "ib_spread": (i, [p, p, i, p, p, p, i, p, p]),
         "ib_multidirect_forcing": (i, [p, p, p, p, p, i, d, i, i, p, p, p]),
@@ -220,6 +222,14 @@ class Context:
         "resident" or "groups" (see gbib.h; every choice gives bitwise the
         same result)."""
         self._check(self.lib.ib_ctx_set_pass_kernels(self.handle, PASSES[which]))
+
+    def set_field_wait(self, event):
+        """Make the forcing calls on this context wait for a torch.cuda.Event
+        (None clears it) after their preparation, before they touch the field
+        (see gbib.h).  The caller keeps the event alive."""
+        self._field_wait = event
+        handle = None if event is None else ctypes.c_void_p(event.cuda_event)
+        self._check(self.lib.ib_ctx_set_field_wait(self.handle, handle))
 
     def set_volume_split(self, ctas_per_particle: int):
         """CTAs per particle of the volume integrals, 0 = automatic (see gbib.h)."""

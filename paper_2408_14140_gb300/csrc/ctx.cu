@@ -320,6 +320,7 @@ int ib_ctx_create(ib_ctx **ctx, size_t workspace_bytes) {
     *c->h_nlev = 0;
     c->pass_kernels = IB_PASSES_AUTO;
     c->vol_split = 0;  // automatic
+    c->field_wait = nullptr;
     for (int k = 0; k < ib_ctx::kStageSlots; ++k) {
         c->stage_ptr[k] = nullptr;
         c->stage_cap[k] = 0;
@@ -358,6 +359,12 @@ int ib_ctx_set_pass_kernels(ib_ctx *c, int which) {
         which != IB_PASSES_GROUPS)
         return set_error(IB_ERR_INVALID, "bad pass-kernel choice %d", which);
     c->pass_kernels = which;
+    return IB_OK;
+}
+
+int ib_ctx_set_field_wait(ib_ctx *c, void *event) {
+    if (!c) return set_error(IB_ERR_INVALID, "ctx is NULL");
+    c->field_wait = event;
     return IB_OK;
 }
 

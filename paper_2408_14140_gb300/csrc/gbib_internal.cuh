@@ -151,6 +151,7 @@ struct ib_ctx {
     int nlev_hint;
     int pass_kernels;    // IB_PASSES_* of the sequential order
     int vol_split;       // CTAs per particle of the volume integrals (0: one resident wave)
+    void *field_wait;    // cudaEvent_t waited on before the forcing passes (nullable)
     // pinned staging ring for the case tables of batch calls: a slot is
     // reused only after the copy that last read it has run (its event)
     static constexpr int kStageSlots = 4;

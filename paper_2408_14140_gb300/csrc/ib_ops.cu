@@ -1453,6 +1453,7 @@ static int run_mdf(ib_ctx *ctx, Arena &ar, const CaseTab &ct, const ib_particles
         cudaMemsetAsync(sched, 0, sizeof(unsigned int) * (P + 1), s);
         if (groups) cudaMemsetAsync(gwords, 0, sizeof(unsigned int) * 4 * ngroups, s);
         tprep.stop();
+        if (ctx->field_wait) cudaStreamWaitEvent(s, (cudaEvent_t)ctx->field_wait, 0);
         PhaseTimer tpass(ctx, IB_PHASE_MDF_PASSES, s);
         rc = groups ? launch_mdf_groups<T, KER>(ctx, ra, s) : launch_mdf_resident<T, KER>(ctx, ra, s);
         if (rc) return rc;
@@ -1462,6 +1463,8 @@ static int run_mdf(ib_ctx *ctx, Arena &ar, const CaseTab &ct, const ib_particles
     k_level_slots<<<1, 256, 0, s>>>(sg.mode, lo.nlev, lo.lev_pbeg, sl.flag_scan, (int)ndense, lev_sbeg);
     cudaMemsetAsync(bar.count, 0, 2 * sizeof(unsigned int), s);
     tprep.stop();
+    // (the field is first read and written by the pass kernels below)
+    if (ctx->field_wait) cudaStreamWaitEvent(s, (cudaEvent_t)ctx->field_wait, 0);
     PassArgs<T> a;
     a.ct = ct;
     a.part_of = part_of;
