@@ -271,9 +271,13 @@ class Runner:
             self.ev_v.record(self.side)
         ctx.ib_multidirect_forcing(self.u, c.h, self.parts, self.marks, c.Ns, c.dt, F_out=self.F,
                                    delta=self.delta, order=self.order)
-        main.wait_stream(self.side)
+        # the second volume integrals (field after forcing) beside the marker
+        # force and torque sums (forces only)
+        self.side.wait_stream(main)
+        with torch.cuda.stream(self.side):
+            self.ctx_v.particle_volume_integrals(self.u, c.h, self.parts, out=self.I1)
         ctx.particle_force_torque(self.parts, self.marks, self.F, c.rho_f, out=(self.Fib, self.Tib))
-        ctx.particle_volume_integrals(self.u, c.h, self.parts, out=self.I1)
+        main.wait_stream(self.side)
         ctx.particle_collide_update(self.parts, c.n, c.h, c.phys(), c.dt, self.Fib, self.Tib,
                                     self.I1[0], self.I0[0], self.I1[1], self.I0[1], Fc_out=self.Fc)
 
@@ -329,22 +333,26 @@ def time_steps(runner, steps, warmup, flush, use_graph):
 
 def kernel_timing(runner, steps, flush):
     """Per-phase device time of the library's kernels (CUDA events recorded by
-    the library on the launching stream) over `steps` eager steps."""
+    the library on the launching stream) over `steps` eager steps, summed over
+    the runner's contexts (the side-stream context runs the volume integrals)."""
     torch = runner.torch
-    ctx = runner.ctx
-    for ph in runner.api.PHASES:
-        ctx.read_timing(ph)
-    ctx.set_timing(True)
+    ctxs = [runner.ctx] + ([runner.ctx_v] if getattr(runner, "ctx_v", None) is not None else [])
+    for ctx in ctxs:
+        for ph in runner.api.PHASES:
+            ctx.read_timing(ph)
+        ctx.set_timing(True)
     for _ in range(steps):
         flush.fill_(1.0)
         runner.step()
     torch.cuda.synchronize()
-    ctx.set_timing(False)
     out = {}
-    for ph in runner.api.PHASES:
-        ms, n = ctx.read_timing(ph)
-        if n:
-            out[ph] = (ms, n)
+    for ctx in ctxs:
+        ctx.set_timing(False)
+        for ph in runner.api.PHASES:
+            ms, n = ctx.read_timing(ph)
+            if n:
+                m0, n0 = out.get(ph, (0.0, 0))
+                out[ph] = (m0 + ms, n0 + n)
     return out
 
 

@@ -171,7 +171,10 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *t
     return r;
 }
 
+// (the scan kernels are launched as programmatic dependents: they wait for
+// their predecessor before touching memory)
 __global__ void k_scan_totals(const uint32_t *in, int n, uint32_t *totals) {
+    grid_dep_wait();
     int i = blockIdx.x * kScanBlock + threadIdx.x;
     uint32_t v = i < n ? in[i] : 0;
     uint32_t tot;
@@ -182,6 +185,7 @@ __global__ void k_scan_totals(const uint32_t *in, int n, uint32_t *totals) {
 __global__ void k_scan_top(uint32_t *totals, int nb) {
     // nb <= kScanBlock * kScanBlock: each thread folds a strided chunk.
     __shared__ uint32_t carry;
+    grid_dep_wait();
     if (threadIdx.x == 0) carry = 0;
     __syncthreads();
     for (int base = 0; base < nb; base += kScanBlock) {
@@ -198,6 +202,7 @@ __global__ void k_scan_top(uint32_t *totals, int nb) {
 }
 
 __global__ void k_scan_apply(const uint32_t *in, uint32_t *out, int n, const uint32_t *totals) {
+    grid_dep_wait();
     int i = blockIdx.x * kScanBlock + threadIdx.x;
     uint32_t v = i < n ? in[i] : 0;
     uint32_t ex = block_exclusive_scan(v, nullptr);
@@ -244,6 +249,7 @@ void PhaseTimer::stop() {
 constexpr int kScanItems = 4;
 
 __global__ void __launch_bounds__(kScanBlock) k_scan_single(const uint32_t *in, uint32_t *out, int n) {
+    grid_dep_wait();
     const int base = threadIdx.x * kScanItems;
     uint32_t v[kScanItems];
     uint32_t sum = 0;
@@ -267,14 +273,14 @@ size_t scan_workspace(int n) { return (size_t)(n + kScanBlock - 1) / kScanBlock 
 void exclusive_scan(const uint32_t *in, uint32_t *out, int n, uint32_t *scratch,
                     cudaStream_t s) {
     if (n <= kScanBlock * kScanItems) {
-        k_scan_single<<<1, kScanBlock, 0, s>>>(in, out, n);
+        launch_pdl(k_scan_single, dim3(1), dim3(kScanBlock), 0, s, in, out, n);
         return;
     }
     int nb = (n + kScanBlock - 1) / kScanBlock;
     if (nb == 0) nb = 1;
-    k_scan_totals<<<nb, kScanBlock, 0, s>>>(in, n, scratch);
-    k_scan_top<<<1, kScanBlock, 0, s>>>(scratch, nb);
-    k_scan_apply<<<nb, kScanBlock, 0, s>>>(in, out, n, scratch);
+    launch_pdl(k_scan_totals, dim3(nb), dim3(kScanBlock), 0, s, in, n, scratch);
+    launch_pdl(k_scan_top, dim3(1), dim3(kScanBlock), 0, s, scratch, nb);
+    launch_pdl(k_scan_apply, dim3(nb), dim3(kScanBlock), 0, s, in, out, n, (const uint32_t *)scratch);
 }
 
 }  // namespace gbib

@@ -197,6 +197,39 @@ int build_case_table(ib_ctx *ctx, struct Arena &ar, int ncases, const ib_case *c
                      CaseTab &ct, cudaStream_t s, const ib_phys *phys = nullptr);
 
 // Records a CUDA event pair around a scope when the context times phases.
+// Programmatic dependent launch (sm_90 and later).  A kernel launched with
+// programmatic stream serialization may start while the kernel before it in
+// the stream still runs.  grid_dep_wait() returns once that predecessor grid
+// has completed and its memory operations are visible to this grid;
+// grid_dep_launch() allows the successor to start once every CTA of this grid
+// has executed it (or exited).  Without the launch attribute both are no-ops.
+// Every CTA of a kernel launched this way waits before it exits and triggers,
+// if at all, only after its wait, so a grid that starts early has every grid
+// but its predecessor complete: before its wait it may read anything the
+// predecessor does not write.  The preparation kernels of a forcing call wait
+// first thing (their launch and scheduling overlap the predecessor's tail);
+// the level kernels load what they can before waiting.
+__device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void grid_dep_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+// Host side: launch with programmatic stream serialization.  The kernel must
+// call grid_dep_wait() before it touches memory its predecessor may write.
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              Args &&...args) {
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
+}
+
 struct PhaseTimer {
     ib_ctx *ctx;
     int phase;

@@ -28,19 +28,6 @@ __device__ __forceinline__ unsigned int ld_acquire(const unsigned int *p) {
     return v;
 }
 
-// Programmatic dependent launch (sm_90 and later).  A kernel launched with
-// programmatic stream serialization may start while the kernel before it in
-// the stream still runs.  grid_dep_wait() returns once that predecessor grid
-// has completed and its memory operations are visible to this grid;
-// grid_dep_launch() allows the successor to start once every CTA of this grid
-// has executed it (or exited).  Without the launch attribute both are no-ops.
-// Every CTA of a level kernel waits before it exits and triggers, if at all,
-// only after its wait, so a grid that starts early has every grid but its
-// predecessor complete: before its wait it may read anything the
-// predecessor does not write.
-__device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
-__device__ __forceinline__ void grid_dep_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
-
 constexpr int kBins = kRows * kBinsPerRow + 1;
 
 // Per-marker state kept in the workspace for one call.

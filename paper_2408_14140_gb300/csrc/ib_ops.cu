@@ -247,6 +247,7 @@ struct LevelOut {
 __global__ void k_conflicts(CaseTab ct, int P, int KW, const double *__restrict__ Xr,
                             const double *__restrict__ rho, int *__restrict__ nbr_cnt,
                             int *__restrict__ nbr) {
+    grid_dep_wait();
     // one warp per particle p; lanes test q = p0 + lane, p0 + 32 + lane, ...
     // and the hits are appended in ascending q (ballot order)
     const int lane = threadIdx.x & 31;
@@ -336,6 +337,7 @@ __global__ void __launch_bounds__(1024) k_levels(CaseTab ct, int P, int order, i
                                                  const int *__restrict__ nbr_cnt,
                                                  const int *__restrict__ nbr, LevelOut lo,
                                                  int *__restrict__ by_rank, int *__restrict__ lev_cur) {
+    grid_dep_wait();
     extern __shared__ __align__(16) unsigned char lsm[];
     __shared__ int s_nl;
     const bool lev_on = P <= kLevOnchipP;
@@ -516,6 +518,7 @@ __device__ __forceinline__ void for_marker_slots(const CaseTab &ct, const SlotGe
 template <int KW>
 __global__ void k_slot_count(CaseTab ct, int M, SlotGeom sg, const uint64_t *__restrict__ anchor,
                              uint32_t *__restrict__ count) {
+    grid_dep_wait();
     for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < M; l += gridDim.x * blockDim.x)
         for_marker_slots<KW>(ct, sg, l, anchor[l], [&](uint32_t s, uint32_t) { atomicAdd(count + s, 1u); });
 }
@@ -524,6 +527,7 @@ template <int KW>
 __global__ void k_slot_fill(CaseTab ct, int M, SlotGeom sg, const uint64_t *__restrict__ anchor,
                             const uint32_t *__restrict__ start, uint32_t *__restrict__ cursor,
                             uint32_t *__restrict__ cand, uint32_t *__restrict__ pcnt) {
+    grid_dep_wait();
     for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < M; l += gridDim.x * blockDim.x)
         for_marker_slots<KW>(ct, sg, l, anchor[l], [&](uint32_t s, uint32_t ncell) {
             uint32_t pos = start[s] + atomicAdd(cursor + s, 1u);
@@ -533,12 +537,14 @@ __global__ void k_slot_fill(CaseTab ct, int M, SlotGeom sg, const uint64_t *__re
 }
 
 __global__ void k_flags(const uint32_t *__restrict__ count, uint32_t *__restrict__ flags, int n) {
+    grid_dep_wait();
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
         flags[i] = count[i] ? 1u : 0u;
 }
 
 __global__ void k_compact(const uint32_t *__restrict__ count, const uint32_t *__restrict__ fscan,
                           uint32_t *__restrict__ dense_of, int n) {
+    grid_dep_wait();
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
         if (count[i]) dense_of[fscan[i]] = (uint32_t)i;
 }
@@ -547,6 +553,7 @@ __global__ void k_compact(const uint32_t *__restrict__ count, const uint32_t *__
 // particle-local mode are level-major: rank * 512 + local tile).
 __global__ void k_level_slots(int mode, const int *__restrict__ nlev_p, const int *__restrict__ lev_pbeg,
                               const uint32_t *__restrict__ fscan, int ndense, int *__restrict__ lev_sbeg) {
+    grid_dep_wait();
     int nl = *nlev_p;
     for (int L = threadIdx.x; L <= nl; L += blockDim.x) {
         if (mode == 0) {
@@ -564,6 +571,7 @@ __global__ void k_level_slots(int mode, const int *__restrict__ nlev_p, const in
 // spatial sort of each particle's markers measured slower end to end).
 __global__ void k_marker_order(int P, const int *__restrict__ moff, const int *__restrict__ mbase,
                                int *__restrict__ mperm) {
+    grid_dep_wait();
     for (int p = blockIdx.x; p < P; p += gridDim.x) {
         const int m0 = moff[p], n = moff[p + 1] - m0, base = mbase[p];
         for (int i = threadIdx.x; i < n; i += blockDim.x) mperm[base + i] = m0 + i;
@@ -656,6 +664,7 @@ __global__ void __launch_bounds__(kBlock) k_slot_sort(
     CaseTab ct, int mode, int ncompact_cap, const int *__restrict__ ncompact_p, SlotGeom sg,
     const uint32_t *__restrict__ dense_of, const uint32_t *__restrict__ start,
     const uint64_t *__restrict__ anchor, const int *__restrict__ level, Slots sl, DevStatus *st) {
+    grid_dep_wait();
     __shared__ unsigned long long keys[kMaxCand];  // also kBlock/32 warp regions of kWarpSort
     const int ncompact = min(*ncompact_p, ncompact_cap);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
@@ -769,6 +778,7 @@ template <int KW>
 __global__ void __launch_bounds__(kPairThreads) k_tile_pairs(CaseTab ct, int ncompact_cap,
                                                              const int *__restrict__ ncompact_p, Slots sl,
                                                              const uint64_t *__restrict__ anchor) {
+    grid_dep_wait();
     constexpr int KW3 = KW * KW * KW;
     __shared__ unsigned int s_anc[kMaxCand];                // (x + 3) | (y + 3) << 4 | (z + 3) << 8
     __shared__ unsigned int s_cnt[kPairWarps][kTileCells];  // counts, then list cursors
@@ -1258,38 +1268,47 @@ static bool take_markers(Arena &ar, int M, MarkerState<T> &ms) {
     return ar.ok();
 }
 
-// Build sorted slot lists for `M` prepared markers.  ndense dense slots.
+// Slot lists for `M` prepared markers over ndense dense slots, in two steps
+// so that a call issues every memset before its kernel chain (the chain's
+// kernels are programmatic dependents of one another; a memset in between
+// would break it).
+struct SlotScratch {
+    size_t cand_cap;
+    int ncompact_cap;
+    uint32_t *flags, *scratch, *cscratch;
+};
+
+// Workspace of the slot lists, and the zeroing they need.
 template <int KW>
-static int build_slots(ib_ctx *ctx, Arena &ar, const CaseTab &ct, int M, int ndense, SlotGeom sg,
-                       const uint64_t *anchor, const int *level, Slots &sl, int *&ncompact_dev,
-                       cudaStream_t s, bool with_pairs, bool with_bins) {
-    size_t cand_cap = (size_t)M * (sg.mode == 0 ? 27 : 8) + 1;
-    int ncompact_cap = (int)((size_t)M * (sg.mode == 0 ? 27 : 8) < (size_t)ndense
-                                 ? (size_t)M * (sg.mode == 0 ? 27 : 8)
-                                 : (size_t)ndense);
-    if (ncompact_cap < 1) ncompact_cap = 1;
+static int slots_alloc(Arena &ar, int M, int ndense, int mode, Slots &sl, SlotScratch &sc, cudaStream_t s,
+                       bool with_pairs, bool with_bins) {
+    const size_t per = mode == 0 ? 27 : 8;
+    sc.cand_cap = (size_t)M * per + 1;
+    sc.ncompact_cap = (int)((size_t)M * per < (size_t)ndense ? (size_t)M * per : (size_t)ndense);
+    if (sc.ncompact_cap < 1) sc.ncompact_cap = 1;
+    const int ncap = sc.ncompact_cap;
     sl.count = ar.take<uint32_t>(ndense);
     sl.start = ar.take<uint32_t>(ndense + 1);
     sl.cursor = ar.take<uint32_t>(ndense);
     sl.flag_scan = ar.take<uint32_t>(ndense + 1);
-    uint32_t *flags = ar.take<uint32_t>(ndense);
-    uint32_t *scratch = ar.take<uint32_t>(scan_workspace(ndense));
-    uint32_t *cscratch = with_pairs ? ar.take<uint32_t>(scan_workspace((int)cand_cap)) : nullptr;
-    sl.dense_of = ar.take<uint32_t>(ncompact_cap);
-    sl.cand = ar.take<uint32_t>(cand_cap);
+    sc.flags = ar.take<uint32_t>(ndense);
+    sc.scratch = ar.take<uint32_t>(scan_workspace(ndense));
+    sc.cscratch = with_pairs ? ar.take<uint32_t>(scan_workspace((int)sc.cand_cap)) : nullptr;
+    sl.dense_of = ar.take<uint32_t>(ncap);
+    sl.cand = ar.take<uint32_t>(sc.cand_cap);
     // bin tables: only the particle-resident form walks them
-    sl.bins = with_bins ? ar.take<uint16_t>((size_t)ncompact_cap * kBins) : nullptr;
-    sl.geo_lo = ar.take<int4>(ncompact_cap);
-    sl.geo_dim = ar.take<int4>(ncompact_cap);
-    sl.geo_case = ar.take<int>(ncompact_cap);
+    sl.bins = with_bins ? ar.take<uint16_t>((size_t)ncap * kBins) : nullptr;
+    sl.geo_lo = ar.take<int4>(ncap);
+    sl.geo_dim = ar.take<int4>(ncap);
+    sl.geo_case = ar.take<int>(ncap);
     constexpr int KW3 = KW * KW * KW;
     if (with_pairs) {
         // every stencil cell of every marker is one pair: KW^3 M in total
-        sl.pcnt = ar.take<uint32_t>(cand_cap);
-        sl.poff = ar.take<uint32_t>(cand_cap + 1);
+        sl.pcnt = ar.take<uint32_t>(sc.cand_cap);
+        sl.poff = ar.take<uint32_t>(sc.cand_cap + 1);
         sl.band = ar.take<int2>((size_t)KW3 * M);
         sl.pairs = ar.take<uint32_t>((size_t)KW3 * M);
-        sl.nband = ar.take<int>(ncompact_cap);
+        sl.nband = ar.take<int>(ncap);
     } else {
         sl.pcnt = sl.poff = nullptr;
         sl.band = nullptr;
@@ -1300,23 +1319,34 @@ static int build_slots(ib_ctx *ctx, Arena &ar, const CaseTab &ct, int M, int nde
         return oom_error(ar.used, ar.cap);
     cudaMemsetAsync(sl.count, 0, sizeof(uint32_t) * ndense, s);
     cudaMemsetAsync(sl.cursor, 0, sizeof(uint32_t) * ndense, s);
-    int nb = grid_blocks(M, 256, ctx->sm_count);
-    k_slot_count<KW><<<nb, 256, 0, s>>>(ct, M, sg, anchor, sl.count);
-    exclusive_scan(sl.count, sl.start, ndense, scratch, s);
-    int nbd = grid_blocks(ndense, 256, ctx->sm_count);
-    k_flags<<<nbd, 256, 0, s>>>(sl.count, flags, ndense);
-    exclusive_scan(flags, sl.flag_scan, ndense, scratch, s);
-    k_compact<<<nbd, 256, 0, s>>>(sl.count, sl.flag_scan, sl.dense_of, ndense);
-    if (with_pairs) cudaMemsetAsync(sl.pcnt, 0, sizeof(uint32_t) * cand_cap, s);
-    k_slot_fill<KW><<<nb, 256, 0, s>>>(ct, M, sg, anchor, sl.start, sl.cursor, sl.cand, sl.pcnt);
-    if (with_pairs) exclusive_scan(sl.pcnt, sl.poff, (int)cand_cap, cscratch, s);
+    if (with_pairs) cudaMemsetAsync(sl.pcnt, 0, sizeof(uint32_t) * sc.cand_cap, s);
+    return IB_OK;
+}
+
+// The kernel chain: count, scan, compact, fill, scan, sort, per-cell lists.
+template <int KW>
+static int slots_build(ib_ctx *ctx, const CaseTab &ct, int M, int ndense, SlotGeom sg, const uint64_t *anchor,
+                       const int *level, Slots &sl, const SlotScratch &sc, int *&ncompact_dev, cudaStream_t s,
+                       bool with_pairs) {
+    const int nb = grid_blocks(M, 256, ctx->sm_count);
+    launch_pdl(k_slot_count<KW>, dim3(nb), dim3(256), 0, s, ct, M, sg, anchor, sl.count);
+    exclusive_scan(sl.count, sl.start, ndense, sc.scratch, s);
+    const int nbd = grid_blocks(ndense, 256, ctx->sm_count);
+    launch_pdl(k_flags, dim3(nbd), dim3(256), 0, s, (const uint32_t *)sl.count, sc.flags, ndense);
+    exclusive_scan(sc.flags, sl.flag_scan, ndense, sc.scratch, s);
+    launch_pdl(k_compact, dim3(nbd), dim3(256), 0, s, (const uint32_t *)sl.count, (const uint32_t *)sl.flag_scan,
+               sl.dense_of, ndense);
+    launch_pdl(k_slot_fill<KW>, dim3(nb), dim3(256), 0, s, ct, M, sg, anchor, (const uint32_t *)sl.start,
+               sl.cursor, sl.cand, sl.pcnt);
+    if (with_pairs) exclusive_scan(sl.pcnt, sl.poff, (int)sc.cand_cap, sc.cscratch, s);
     ncompact_dev = (int *)(sl.flag_scan + ndense);
-    k_slot_sort<<<ctx->sm_count * 4, kBlock, 0, s>>>(ct, sg.mode, ncompact_cap, ncompact_dev, sg,
-                                                     sl.dense_of, sl.start, anchor, level, sl,
-                                                     ctx->status);
+    launch_pdl(k_slot_sort, dim3(ctx->sm_count * 4), dim3(kBlock), 0, s, ct, sg.mode, sc.ncompact_cap,
+               (const int *)ncompact_dev, sg, (const uint32_t *)sl.dense_of, (const uint32_t *)sl.start, anchor,
+               level, sl, ctx->status);
     if (with_pairs)
-        k_tile_pairs<KW><<<ctx->sm_count * 8, kPairThreads, 0, s>>>(ct, ncompact_cap, ncompact_dev, sl, anchor);
-    return check_launch("build_slots");
+        launch_pdl(k_tile_pairs<KW>, dim3(ctx->sm_count * 8), dim3(kPairThreads), 0, s, ct, sc.ncompact_cap,
+                   (const int *)ncompact_dev, sl, anchor);
+    return check_launch("slot lists");
 }
 
 template <typename T, int KER>
@@ -1344,11 +1374,14 @@ static int run_spread(ib_ctx *ctx, const ib_grid *grid, int M, const double *X, 
     if (!ar.ok())
         return oom_error(ar.used, ar.cap);
     int nb = grid_blocks(M, 256, ctx->sm_count);
+    Slots sl;
+    SlotScratch sc;
+    int *ncompact = nullptr;
+    int rc = slots_alloc<KW>(ar, M, (int)ndense, sg.mode, sl, sc, s, true, false);
+    if (rc) return rc;
     PhaseTimer tm(ctx, IB_PHASE_SPREAD, s);
     k_prep_spread<T, KER><<<nb, 256, 0, s>>>(g, M, X, F, dV, ms, ctx->status);
-    Slots sl;
-    int *ncompact = nullptr;
-    int rc = build_slots<KW>(ctx, ar, ct, M, (int)ndense, sg, ms.anchor, nullptr, sl, ncompact, s, true, false);
+    rc = slots_build<KW>(ctx, ct, M, (int)ndense, sg, ms.anchor, nullptr, sl, sc, ncompact, s, true);
     if (rc) return rc;
     cudaFuncSetAttribute(k_spread_gather<T, KER>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)tile_stage_bytes<T>());
@@ -1395,7 +1428,13 @@ static int run_mdf(ib_ctx *ctx, Arena &ar, const CaseTab &ct, const ib_particles
     if (ndense > (1LL << 30)) return set_error(IB_ERR_UNSUPPORTED, "too many tiles");
     if (!ar.ok())
         return oom_error(ar.used, ar.cap);
+    const bool resident = order == IB_ORDER_SEQUENTIAL && ctx->pass_kernels == IB_PASSES_RESIDENT;
+    Slots sl;
+    SlotScratch sc;
+    int rc = slots_alloc<KW>(ar, M, (int)ndense, sg.mode, sl, sc, s, true, resident);
+    if (rc) return rc;
     PhaseTimer tprep(ctx, IB_PHASE_MDF_PREP, s);
+    cudaMemsetAsync(bar.count, 0, 2 * sizeof(unsigned int), s);
     cudaMemsetAsync(prep_ps.lo, 0x7f, sizeof(long long) * 3 * P, s);
     cudaMemsetAsync(prep_ps.hi, 0x80, sizeof(long long) * 3 * P, s);
     cudaMemsetAsync(prep_ps.rho2, 0, sizeof(unsigned long long) * P, s);
@@ -1404,20 +1443,20 @@ static int run_mdf(ib_ctx *ctx, Arena &ar, const CaseTab &ct, const ib_particles
                                                  mk->dV, ms, F_out, rho, box_lo, box_dim, part_of, prep_ps,
                                                  ctx->status);
     if (order == IB_ORDER_SEQUENTIAL)
-        k_conflicts<<<grid_blocks(32 * P, 256, ctx->sm_count), 256, 0, s>>>(ct, P, KW, pp->Xr, rho, nbr_cnt, nbr);
+        launch_pdl(k_conflicts, dim3(grid_blocks(32 * P, 256, ctx->sm_count)), dim3(256), 0, s, ct, P, KW,
+                   (const double *)pp->Xr, (const double *)rho, nbr_cnt, nbr);
     cudaFuncSetAttribute(k_levels, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLevSmem);
-    k_levels<<<1, 1024, kLevSmem, s>>>(ct, P, order, KW, pp->Xr, rho, pp->marker_offset, nbr_cnt, nbr, lo, lev_work,
-                                       lev_cur);
-    k_marker_order<<<P < ctx->sm_count * 4 ? P : ctx->sm_count * 4, 256, 0, s>>>(P, pp->marker_offset, lo.mbase,
-                                                                                 mperm);
+    launch_pdl(k_levels, dim3(1), dim3(1024), kLevSmem, s, ct, P, order, KW, (const double *)pp->Xr,
+               (const double *)rho, (const int *)pp->marker_offset, (const int *)nbr_cnt, (const int *)nbr, lo,
+               lev_work, lev_cur);
+    launch_pdl(k_marker_order, dim3(P < ctx->sm_count * 4 ? P : ctx->sm_count * 4), dim3(256), 0, s, P,
+               (const int *)pp->marker_offset, (const int *)lo.mbase, mperm);
     sg.part_of = part_of;
     sg.rank = lo.rank;
     sg.box_lo = box_lo;
     sg.box_dim = box_dim;
-    Slots sl;
     int *ncompact = nullptr;
-    const bool resident = order == IB_ORDER_SEQUENTIAL && ctx->pass_kernels == IB_PASSES_RESIDENT;
-    int rc = build_slots<KW>(ctx, ar, ct, M, (int)ndense, sg, ms.anchor, lo.level, sl, ncompact, s, true, resident);
+    rc = slots_build<KW>(ctx, ct, M, (int)ndense, sg, ms.anchor, lo.level, sl, sc, ncompact, s, true);
     if (rc) return rc;
     if (order == IB_ORDER_SEQUENTIAL &&
         (ctx->pass_kernels == IB_PASSES_RESIDENT || ctx->pass_kernels == IB_PASSES_GROUPS)) {
@@ -1460,8 +1499,8 @@ static int run_mdf(ib_ctx *ctx, Arena &ar, const CaseTab &ct, const ib_particles
         tpass.stop();
         return check_launch("ib_multidirect_forcing");
     }
-    k_level_slots<<<1, 256, 0, s>>>(sg.mode, lo.nlev, lo.lev_pbeg, sl.flag_scan, (int)ndense, lev_sbeg);
-    cudaMemsetAsync(bar.count, 0, 2 * sizeof(unsigned int), s);
+    launch_pdl(k_level_slots, dim3(1), dim3(256), 0, s, sg.mode, (const int *)lo.nlev, (const int *)lo.lev_pbeg,
+               (const uint32_t *)sl.flag_scan, (int)ndense, lev_sbeg);
     tprep.stop();
     // (the field is first read and written by the pass kernels below)
     if (ctx->field_wait) cudaStreamWaitEvent(s, (cudaEvent_t)ctx->field_wait, 0);
