@@ -330,6 +330,8 @@ __device__ __forceinline__ int block_scan_chunked(int n, F f, O out) {
     return s_carry;
 }
 
+constexpr int kLevSweeps = 64;  // parallel relaxation sweeps before the ordered sweep
+
 __global__ void __launch_bounds__(1024) k_levels(CaseTab ct, int P, int order, int KW,
                                                  const double *__restrict__ Xr,
                                                  const double *__restrict__ rho,
@@ -358,10 +360,54 @@ __global__ void __launch_bounds__(1024) k_levels(CaseTab ct, int P, int order, i
         }
     __threadfence();  // the zeroed counters reach L2 before the atomics below
     __syncthreads();
-    // ---- sweep, one thread per case
-    const int ncases = ct.arr ? ct.ncases : 1;
     int mymax = 0;
-    for (int c = threadIdx.x; c < ncases; c += blockDim.x) {
+    // ---- parallel levels: lev(p) = 1 + max lev(q) over conflicting q < p (0
+    // without), the longest path to p in the conflict DAG, relaxed for all
+    // particles at once until nothing changes.  Values only grow and never
+    // pass the fixed point, so reading a neighbour's value mid-sweep is
+    // harmless; a conflict chain of length c takes c + 1 sweeps.  Full
+    // conflict lists, or chains longer than kLevSweeps, fall back to the
+    // sweep in particle order below (which recomputes every level).
+    __shared__ int s_flag;
+    bool levels_done = false;
+    if (order == IB_ORDER_SEQUENTIAL) {
+        volatile int *vlev = lev;
+        if (threadIdx.x == 0) s_flag = 0;
+        __syncthreads();
+        for (int p = threadIdx.x; p < P; p += blockDim.x) {
+            if ((nbr_on ? s_cnt[p] : nbr_cnt[p]) < 0) s_flag = 1;
+            vlev[p] = 0;
+        }
+        __syncthreads();
+        const bool any_full = s_flag != 0;
+        __syncthreads();
+        for (int it = 0; !any_full && it < kLevSweeps; ++it) {
+            if (threadIdx.x == 0) s_flag = 0;
+            __syncthreads();
+            for (int p = threadIdx.x; p < P; p += blockDim.x) {
+                const int cn = nbr_on ? s_cnt[p] : nbr_cnt[p];
+                int best = 0;
+                for (int k = 0; k < cn; ++k)
+                    best = max(best, vlev[nbr_on ? s_nbr[p * kMaxNbr + k] : nbr[(size_t)p * kMaxNbr + k]] + 1);
+                if (best != vlev[p]) {
+                    vlev[p] = best;
+                    s_flag = 1;
+                }
+            }
+            __syncthreads();
+            const bool changed = s_flag != 0;
+            __syncthreads();
+            if (!changed) {
+                levels_done = true;
+                break;
+            }
+        }
+        if (levels_done)
+            for (int p = threadIdx.x; p < P; p += blockDim.x) mymax = max(mymax, vlev[p] + 1);
+    }
+    // ---- sweep in particle order, one thread per case
+    const int ncases = ct.arr ? ct.ncases : 1;
+    for (int c = threadIdx.x; !levels_done && c < ncases; c += blockDim.x) {
         const DevCase cd = ct.get(c);
         for (int p = cd.p0; p < cd.p1; ++p) {
             int best = 0;
