@@ -57,7 +57,7 @@ constexpr int kVolAx = kVolMaxBox + 1;
 // two node planes of (max(-phi, 0), max(phi, 0)) pairs + per-axis tables
 // (node squares, cell offsets, cell squares) + per-row grid offsets
 constexpr size_t kVolSmem = 2 * kVolAx * kVolAx * sizeof(double2) + 9 * kVolAx * sizeof(double) +
-                            kVolAx * sizeof(long long) + 3 * kVolAx * sizeof(float2);
+                            kVolAx * sizeof(long long) + 6 * kVolAx * sizeof(float2) + 3 * kVolAx * sizeof(float);
 
 // Double-float accumulation: a sum kept as the unevaluated pair hi + lo of two
 // floats -- Knuth's TwoSum for the addition error and the fused multiply-add
@@ -93,6 +93,29 @@ __device__ __forceinline__ void df_warp_sum(DF &a) {
 __device__ __forceinline__ float2 df_split(double x) {
     const float h = (float)x;
     return make_float2(h, (float)(x - (double)h));
+}
+// a + b, both double-float, renormalised (TwoSum on the high parts)
+__device__ __forceinline__ DF df_sum(DF a, DF b) {
+    const float s = a.hi + b.hi;
+    const float bb = s - a.hi;
+    const float e = (a.hi - (s - bb)) + (b.hi - bb);
+    const float l = e + (a.lo + b.lo);
+    const float h = s + l;
+    return DF{h, l - (h - s)};
+}
+// phi = sqrt(x2) * iR - 1 in double-float, x2 > 0: the square root by one
+// Newton step from the FP32 reciprocal square root (Heron's iteration; the
+// start's relative error below 2^-22 leaves about 2^-45), then the product
+// with 1/R and the subtraction.
+__device__ __forceinline__ DF df_phi(DF x2, float2 iR) {
+    const float rs = rsqrtf(x2.hi);
+    const float r = x2.hi * rs;
+    const float p = r * r;
+    const float pe = fmaf(r, r, -p);
+    const float corr = (((x2.hi - p) - pe) + x2.lo) * (0.5f * rs);
+    const float q = r * iR.x;
+    const float qe = fmaf(r, iR.x, -q) + fmaf(r, iR.y, corr * iR.x);
+    return df_sum(DF{q, qe}, DF{-1.0f, 0.0f});
 }
 
 // |x| from x^2 to within a few units of FP64 rounding: an FP32 square root
@@ -264,6 +287,8 @@ __global__ void __launch_bounds__(kVolThreads, 3) k_volume(CaseTab ct, int P, in
             double *tb = (double *)(phi2 + 2 * kVolAx * kVolAx);
             long long *row_off = (long long *)(tb + 9 * kVolAx);
             float2 *tbf = (float2 *)(row_off + kVolAx);  // cell offsets as float pairs
+            float2 *tsq = tbf + 3 * kVolAx;               // node offset squares as float pairs
+            float *tcf = (float *)(tsq + 3 * kVolAx);     // cell offset squares in FP32
             for (int a = 0; a < 3; ++a)
                 for (int i = threadIdx.x; i <= dims[a]; i += blockDim.x) {
                     const double xn = g.org[a] + (double)(lo[a] + i) * h - c[a];
@@ -271,8 +296,17 @@ __global__ void __launch_bounds__(kVolThreads, 3) k_volume(CaseTab ct, int P, in
                     tb[a * kVolAx + i] = xn * xn;
                     tb[(3 + a) * kVolAx + i] = xc;
                     tb[(6 + a) * kVolAx + i] = xc * xc;
-                    if (sizeof(T) == 4) tbf[a * kVolAx + i] = df_split(xc);
+                    if (sizeof(T) == 4) {
+                        tbf[a * kVolAx + i] = df_split(xc);
+                        tsq[a * kVolAx + i] = df_split(xn * xn);
+                        tcf[a * kVolAx + i] = (float)(xc * xc);
+                    }
                 }
+            const float2 iRf = df_split(iR);
+            // FP32 centre tests with a relative margin far above their rounding;
+            // cells in the margin take the corner formula, exact for them too
+            const float rout2f = (float)rout2 * (1.0f + 1e-5f);
+            const float rin2f = rin2 > 0 ? (float)rin2 * (1.0f - 1e-5f) : -1.0f;
             for (int j = threadIdx.x; j < dims[1]; j += blockDim.x)
                 row_off[j] = (long long)wrap_int(lo[1] + j, g.n[1]) * g.n[0];
             __syncthreads();
@@ -328,6 +362,17 @@ __global__ void __launch_bounds__(kVolThreads, 3) k_volume(CaseTab ct, int P, in
                     const int i = k < r_nc[0][j] ? r_na[j] + k : r_nb[j] + (k - r_nc[0][j]);
                     // every listed node gets its level set value (nodes slightly
                     // outside the shell too: the values stay exact)
+                    if constexpr (sizeof(T) == 4) {
+                        // FP32 fields: double-float level set, stored as
+                        // (max(-phi, 0), max(phi, 0)) float pairs
+                        const DF x2 = df_sum(DF{tsq[i].x, tsq[i].y},
+                                             df_sum(DF{tsq[kVolAx + j].x, tsq[kVolAx + j].y},
+                                                    DF{tsq[2 * kVolAx + kn].x, tsq[2 * kVolAx + kn].y}));
+                        const DF ph = x2.hi > 0.0f ? df_phi(x2, iRf) : DF{-1.0f, 0.0f};
+                        ((float4 *)buf)[j * nx + i] = ph.hi < 0.0f ? make_float4(-ph.hi, -ph.lo, 0.f, 0.f)
+                                                                   : make_float4(0.f, 0.f, ph.hi, ph.lo);
+                        continue;
+                    }
                     const double ph = fma(norm_from_square(tb[i] + tb[kVolAx + j] + zz), iR, -1.0);
                     buf[j * nx + i] = make_double2(fmax(-ph, 0.0), fmax(ph, 0.0));
                 }
@@ -340,7 +385,7 @@ __global__ void __launch_bounds__(kVolThreads, 3) k_volume(CaseTab ct, int P, in
             long long nint_cells = 0;
             // FP32 fields: double-float sums of w and of ry w2, rz w1, rz w0,
             // rx w2, rx w1, ry w0 (no FP64 work per cell but alpha's)
-            DF W[3] = {}, Pm[6] = {};
+            DF W[3] = {}, Pm[6] = {}, V = {};
             for (int kz = z0; kz < z1; ++kz) {
                 node_plane(kz + 1, phi2 + ((kz + 1) & 1) * plane);
                 // cell rows of plane kz: interior range and the boundary ranges around it
@@ -373,6 +418,7 @@ __global__ void __launch_bounds__(kVolThreads, 3) k_volume(CaseTab ct, int P, in
                 __syncthreads();
                 const double2 *b0 = phi2 + (kz & 1) * plane, *b1 = phi2 + ((kz + 1) & 1) * plane;
                 const float2 fz = sizeof(T) == 4 ? tbf[2 * kVolAx + kz] : make_float2(0.f, 0.f);
+                const float rz2f = sizeof(T) == 4 ? tcf[2 * kVolAx + kz] : 0.f;
                 const long long plane_off = (long long)wrap_int(lo[2] + kz, g.n[2]) * g.n[1] * g.n[0];
                 double s0 = 0, s1 = 0, s2 = 0;  // plane sums of alpha u
                 // interior cells: alpha = 1
@@ -412,6 +458,61 @@ __global__ void __launch_bounds__(kVolThreads, 3) k_volume(CaseTab ct, int P, in
                     const int j = find_row(p_bnd, dims[1], q);
                     const int k = q - p_bnd[j];
                     const int i = k < r_ca[j] ? r_ia[j] + k : r_ic[j] + c_int[j] + (k - r_ca[j]);
+                    if constexpr (sizeof(T) == 4) {
+                        // FP32 fields: the same cell in double-float, no FP64
+                        const float d2f = tcf[i] + tcf[kVolAx + j] + rz2f;
+                        if (d2f > rout2f) continue;
+                        float2 a2 = make_float2(1.f, 0.f);
+                        if (!(d2f < rin2f)) {
+                            const int qn = j * nx + i;
+                            const float4 *f0 = (const float4 *)b0, *f1 = (const float4 *)b1;
+                            const float4 cn[8] = {f0[qn], f0[qn + 1], f0[qn + nx], f0[qn + nx + 1],
+                                                  f1[qn], f1[qn + 1], f1[qn + nx], f1[qn + nx + 1]};
+                            DF num = {0.f, 0.f}, neg = {0.f, 0.f};
+#pragma unroll
+                            for (int m = 0; m < 8; ++m) {
+                                df_add2(num, cn[m].x, cn[m].y);
+                                df_add2(neg, cn[m].z, cn[m].w);
+                            }
+                            num = df_sum(num, DF{0.f, 0.f});
+                            neg = df_sum(neg, DF{0.f, 0.f});
+                            if (num.hi == 0.0f && neg.hi > 0.0f) continue;  // alpha = 0
+                            const DF den = df_sum(num, neg);
+                            if (den.hi == 0.0f) {
+                                a2 = make_float2(0.5f, 0.f);
+                            } else if (neg.hi != 0.0f) {
+                                if (den.hi < 1e-30f) {
+                                    a2 = df_split(((double)num.hi + num.lo) / ((double)den.hi + den.lo));
+                                } else {
+                                    // num / den: a quotient and one remainder correction
+                                    const float rd = __frcp_rn(den.hi);
+                                    const float q1 = num.hi * rd;
+                                    const float pr = q1 * den.hi;
+                                    const float pe = fmaf(q1, den.hi, -pr);
+                                    const float rr = ((num.hi - pr) - pe) + fmaf(-q1, den.lo, num.lo);
+                                    a2 = make_float2(q1, rr * rd);
+                                }
+                            }
+                        }
+                        const long long cc = plane_off + row_off[j] + wrap_add(lo0w, i, g.n[0]);
+                        df_add2(V, a2.x, a2.y);
+                        const float2 fx = tbf[i], fy = tbf[kVolAx + j];
+                        const float v[3] = {u[cc], u[N + cc], u[2 * N + cc]};
+                        float wh[3], wl[3];
+#pragma unroll
+                        for (int q3 = 0; q3 < 3; ++q3) {
+                            wh[q3] = a2.x * v[q3];
+                            wl[q3] = fmaf(a2.x, v[q3], -wh[q3]) + a2.y * v[q3];
+                            df_add2(W[q3], wh[q3], wl[q3]);
+                        }
+                        df_add_prod(Pm[0], fy.x, fy.y, wh[2], wl[2]);
+                        df_add_prod(Pm[1], fz.x, fz.y, wh[1], wl[1]);
+                        df_add_prod(Pm[2], fz.x, fz.y, wh[0], wl[0]);
+                        df_add_prod(Pm[3], fx.x, fx.y, wh[2], wl[2]);
+                        df_add_prod(Pm[4], fx.x, fx.y, wh[1], wl[1]);
+                        df_add_prod(Pm[5], fy.x, fy.y, wh[0], wl[0]);
+                        continue;
+                    }
                     // exact centre test: beyond R + 0.8661 h every corner is outside
                     // (alpha = 0), within R - 0.8661 h every corner is inside
                     // (alpha = 1); only cells in between read their corners,
@@ -430,26 +531,6 @@ __global__ void __launch_bounds__(kVolThreads, 3) k_volume(CaseTab ct, int P, in
                         al = den == 0.0 ? 0.5 : (neg == 0.0 ? 1.0 : (den > 1e-30 ? num * recip_refined(den) : num / den));
                     }
                     const long long cc = plane_off + row_off[j] + wrap_add(lo0w, i, g.n[0]);
-                    if constexpr (sizeof(T) == 4) {
-                        svol += al;
-                        const float2 fx = tbf[i], fy = tbf[kVolAx + j];
-                        const float2 a2 = al == 1.0 ? make_float2(1.f, 0.f) : df_split(al);
-                        const float v[3] = {u[cc], u[N + cc], u[2 * N + cc]};
-                        float wh[3], wl[3];
-#pragma unroll
-                        for (int q = 0; q < 3; ++q) {
-                            wh[q] = a2.x * v[q];
-                            wl[q] = fmaf(a2.x, v[q], -wh[q]) + a2.y * v[q];
-                            df_add2(W[q], wh[q], wl[q]);
-                        }
-                        df_add_prod(Pm[0], fy.x, fy.y, wh[2], wl[2]);
-                        df_add_prod(Pm[1], fz.x, fz.y, wh[1], wl[1]);
-                        df_add_prod(Pm[2], fz.x, fz.y, wh[0], wl[0]);
-                        df_add_prod(Pm[3], fx.x, fx.y, wh[2], wl[2]);
-                        df_add_prod(Pm[4], fx.x, fx.y, wh[1], wl[1]);
-                        df_add_prod(Pm[5], fy.x, fy.y, wh[0], wl[0]);
-                        continue;
-                    }
                     const double rx = tb[3 * kVolAx + i], ry = tb[4 * kVolAx + j];
                     const double w0 = al * (double)u[cc], w1 = al * (double)u[N + cc], w2 = al * (double)u[2 * N + cc];
                     s0 += w0;
@@ -482,7 +563,9 @@ __global__ void __launch_bounds__(kVolThreads, 3) k_volume(CaseTab ct, int P, in
                 for (int q = 0; q < 3; ++q) df_warp_sum(W[q]);
 #pragma unroll
                 for (int q = 0; q < 6; ++q) df_warp_sum(Pm[q]);
+                df_warp_sum(V);
                 if ((threadIdx.x & 31) == 0) {
+                    acc[6] += (double)V.hi + (double)V.lo;
                     double pm[6];
 #pragma unroll
                     for (int q = 0; q < 6; ++q) pm[q] = (double)Pm[q].hi + (double)Pm[q].lo;
