@@ -318,27 +318,47 @@ __global__ void __launch_bounds__(kVolThreads, 3) k_volume(CaseTab ct, int P, in
             // index is an exact member (range_in: |x_i| < w); empty when
             // first > last.  Exact FP64 tests decide the cells in the margin.
             constexpr float kEps = 1e-3f;
-            auto range_out = [&](double base, float w, int n, int &first, int &last) {
-                first = max(0, (int)ceilf((-w - (float)base) * fih - kEps));
-                last = min(n - 1, (int)floorf((w - (float)base) * fih + kEps));
+            auto range_out = [&](float base, float w, int n, int &first, int &last) {
+                first = max(0, (int)ceilf((-w - base) * fih - kEps));
+                last = min(n - 1, (int)floorf((w - base) * fih + kEps));
             };
-            auto range_in = [&](double base, float w, int n, int &first, int &last) {
-                first = max(0, (int)floorf((-w - (float)base) * fih + kEps) + 1);
-                last = min(n - 1, (int)ceilf((w - (float)base) * fih - kEps) - 1);
+            auto range_in = [&](float base, float w, int n, int &first, int &last) {
+                first = max(0, (int)floorf((-w - base) * fih + kEps) + 1);
+                last = min(n - 1, (int)ceilf((w - base) * fih - kEps) - 1);
             };
+            const float xbf = (float)(g.org[0] + (double)lo[0] * h - c[0]);            // x of node 0
+            const float xcbf = (float)(g.org[0] + ((double)lo[0] + 0.5) * h - c[0]);   // x of cell 0
+            // FP32 fields: the per-row ranges from FP32 squares, the shell and
+            // the cell bounds widened by a relative 1e-5 (the rows and cells
+            // that matter lie 0.01 h inside the node shell and 8e-5 h inside
+            // the cell bounds, far beyond the FP32 error of the squares)
+            const float sh2f = (float)sh2 * (1.0f + 1e-5f), sl2f = (float)sl2 * (1.0f - 1e-5f);
             auto node_plane = [&](int kn, double2 *buf) {
                 const double zz = tb[2 * kVolAx + kn];
                 const int rows = dims[1] + 1;
-                const double xb = g.org[0] + (double)lo[0] * h - c[0];  // x of node 0
                 for (int j = threadIdx.x; j < rows; j += blockDim.x) {
-                    const double dyz = tb[kVolAx + j] + zz;
+                    bool in_shell, beyond_sl;
+                    float wo, wi;
+                    if constexpr (sizeof(T) == 4) {
+                        const float dyz = tsq[kVolAx + j].x + tsq[2 * kVolAx + kn].x;
+                        in_shell = dyz < sh2f;
+                        beyond_sl = sl2f > dyz;
+                        wo = sqrtf(fmaxf(sh2f - dyz, 0.f));
+                        wi = sqrtf(fmaxf(sl2f - dyz, 0.f));
+                    } else {
+                        const double dyz = tb[kVolAx + j] + zz;
+                        in_shell = dyz < sh2;
+                        beyond_sl = sl2 > dyz;
+                        wo = in_shell ? sqrtf((float)(sh2 - dyz)) : 0.f;
+                        wi = beyond_sl ? sqrtf((float)(sl2 - dyz)) : 0.f;
+                    }
                     int a0 = 0, n0 = 0, a1 = 0, n1 = 0;
-                    if (dyz < sh2) {
+                    if (in_shell) {
                         // nodes of the shell sl <= |x| <= sh: the outer range minus
                         // the nodes surely inside sl
                         int f, l, fi = 1, li = 0;
-                        range_out(xb, sqrtf((float)(sh2 - dyz)), nx, f, l);
-                        if (sl2 > dyz) range_in(xb, sqrtf((float)(sl2 - dyz)), nx, fi, li);
+                        range_out(xbf, wo, nx, f, l);
+                        if (beyond_sl) range_in(xbf, wi, nx, fi, li);
                         if (li >= fi && l >= f) {
                             a0 = f;
                             n0 = max(0, min(l, fi - 1) - f + 1);
@@ -390,13 +410,26 @@ __global__ void __launch_bounds__(kVolThreads, 3) k_volume(CaseTab ct, int P, in
                 node_plane(kz + 1, phi2 + ((kz + 1) & 1) * plane);
                 // cell rows of plane kz: interior range and the boundary ranges around it
                 const double rz = tb[5 * kVolAx + kz], rz2 = tb[8 * kVolAx + kz];
-                const double xcb = g.org[0] + ((double)lo[0] + 0.5) * h - c[0];  // x of cell 0
                 for (int j = threadIdx.x; j < dims[1]; j += blockDim.x) {
-                    const double ryz2 = tb[7 * kVolAx + j] + rz2;
+                    bool in_out, in_in;
+                    float wo, wi;
+                    if constexpr (sizeof(T) == 4) {
+                        const float ryz2 = tcf[kVolAx + j] + tcf[2 * kVolAx + kz];
+                        in_out = ryz2 <= rout2f;
+                        in_in = ryz2 < rin2f;
+                        wo = sqrtf(fmaxf(rout2f - ryz2, 0.f));
+                        wi = sqrtf(fmaxf(rin2f - ryz2, 0.f));
+                    } else {
+                        const double ryz2 = tb[7 * kVolAx + j] + rz2;
+                        in_out = ryz2 <= rout2;
+                        in_in = ryz2 < rin2;
+                        wo = in_out ? sqrtf((float)(rout2 - ryz2)) : 0.f;
+                        wi = in_in ? sqrtf((float)(rin2 - ryz2)) : 0.f;
+                    }
                     int ia = 0, ib = -1, ja = 0, jb = -1;
-                    if (ryz2 <= rout2) {
-                        range_out(xcb, sqrtf((float)(rout2 - ryz2)), dims[0], ia, ib);
-                        if (ryz2 < rin2) range_in(xcb, sqrtf((float)(rin2 - ryz2)), dims[0], ja, jb);
+                    if (in_out) {
+                        range_out(xcbf, wo, dims[0], ia, ib);
+                        if (in_in) range_in(xcbf, wi, dims[0], ja, jb);
                         ja = max(ja, ia);  // interior within the outer range
                         jb = min(jb, ib);
                     }
