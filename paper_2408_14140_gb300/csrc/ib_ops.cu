@@ -611,6 +611,32 @@ __global__ void k_level_slots(int mode, const int *__restrict__ nlev_p, const in
     }
 }
 
+// Per wavefront, its tiles in decreasing number of band cells (a counting
+// sort; equal sizes in any order).  The wavefront gather takes its tiles in
+// this order, so when a wavefront has more tiles than resident CTAs the
+// second round gets the smallest ones.  Only the launch order changes: every
+// tile's sums are the same whichever CTA computes them.
+__global__ void __launch_bounds__(1024) k_level_tile_order(const int *__restrict__ nlev_p,
+                                                           const int *__restrict__ lev_sbeg,
+                                                           const int *__restrict__ nband, int *__restrict__ tperm) {
+    grid_dep_wait();
+    __shared__ int s_hist[kTileCells + 1];
+    const int nl = *nlev_p;
+    for (int L = 0; L < nl; ++L) {
+        const int s0 = lev_sbeg[L], s1 = lev_sbeg[L + 1];
+        for (int k = threadIdx.x; k <= kTileCells; k += blockDim.x) s_hist[k] = 0;
+        __syncthreads();
+        for (int t = s0 + threadIdx.x; t < s1; t += blockDim.x)
+            atomicAdd(&s_hist[kTileCells - min(max(nband[t], 0), kTileCells)], 1);
+        __syncthreads();
+        block_scan_chunked(kTileCells + 1, [&](int k) { return s_hist[k]; }, [&](int k, int pre) { s_hist[k] = pre; });
+        __syncthreads();
+        for (int t = s0 + threadIdx.x; t < s1; t += blockDim.x)
+            tperm[s0 + atomicAdd(&s_hist[kTileCells - min(max(nband[t], 0), kTileCells)], 1)] = t;
+        __syncthreads();
+    }
+}
+
 // Level-major marker list: the markers of the particle of rank r follow
 // those of the particles of lower rank, each particle's in index order (the
 // Fibonacci lattice index already walks the sphere band by band in z; a
@@ -1003,6 +1029,7 @@ struct PassArgs {
     const int *mperm;
     const int *lev_mbeg;
     const int *lev_sbeg;
+    const int *tperm;  // per wavefront, its tiles largest first (wavefront gather order)
     const int *nlev;
     int Ns;
     int L0;  // first wavefront the persistent kernel processes
@@ -1244,8 +1271,8 @@ __global__ void __launch_bounds__(kGatherThreads, sizeof(T) == 4 ? 5 : 4) k_gath
         return;
     }
     // (the wait inside returns at once after the first tile)
-    for (int cs = s0 + blockIdx.x; cs < s1; cs += gridDim.x)
-        gather_tile_level<T, Kernel<KER>::W>(a.ct, cs, a.sl, a.ms.wts, a.ms.A, a.inv_dt, sw, sA, sp);
+    for (int k = s0 + blockIdx.x; k < s1; k += gridDim.x)
+        gather_tile_level<T, Kernel<KER>::W>(a.ct, a.tperm[k], a.sl, a.ms.wts, a.ms.A, a.inv_dt, sw, sA, sp);
 }
 
 template <typename T, int KER>
@@ -1479,6 +1506,9 @@ static int run_mdf(ib_ctx *ctx, Arena &ar, const CaseTab &ct, const ib_particles
     SlotScratch sc;
     int rc = slots_alloc<KW>(ar, M, (int)ndense, sg.mode, sl, sc, s, true, resident);
     if (rc) return rc;
+    int *tperm = ar.take<int>(sc.ncompact_cap);
+    if (!ar.ok())
+        return oom_error(ar.used, ar.cap);
     PhaseTimer tprep(ctx, IB_PHASE_MDF_PREP, s);
     cudaMemsetAsync(bar.count, 0, 2 * sizeof(unsigned int), s);
     cudaMemsetAsync(prep_ps.lo, 0x7f, sizeof(long long) * 3 * P, s);
@@ -1547,6 +1577,8 @@ static int run_mdf(ib_ctx *ctx, Arena &ar, const CaseTab &ct, const ib_particles
     }
     launch_pdl(k_level_slots, dim3(1), dim3(256), 0, s, sg.mode, (const int *)lo.nlev, (const int *)lo.lev_pbeg,
                (const uint32_t *)sl.flag_scan, (int)ndense, lev_sbeg);
+    launch_pdl(k_level_tile_order, dim3(1), dim3(1024), 0, s, (const int *)lo.nlev, (const int *)lev_sbeg,
+               (const int *)sl.nband, tperm);
     tprep.stop();
     // (the field is first read and written by the pass kernels below)
     if (ctx->field_wait) cudaStreamWaitEvent(s, (cudaEvent_t)ctx->field_wait, 0);
@@ -1560,6 +1592,7 @@ static int run_mdf(ib_ctx *ctx, Arena &ar, const CaseTab &ct, const ib_particles
     a.mperm = mperm;
     a.lev_mbeg = lo.lev_mbeg;
     a.lev_sbeg = lev_sbeg;
+    a.tperm = tperm;
     a.nlev = lo.nlev;
     a.Ns = Ns;
     a.dt = dt;
