@@ -616,13 +616,13 @@ __global__ void k_level_slots(int mode, const int *__restrict__ nlev_p, const in
 // this order, so when a wavefront has more tiles than resident CTAs the
 // second round gets the smallest ones.  Only the launch order changes: every
 // tile's sums are the same whichever CTA computes them.
-__global__ void __launch_bounds__(1024) k_level_tile_order(const int *__restrict__ nlev_p,
+__global__ void __launch_bounds__(512) k_level_tile_order(const int *__restrict__ nlev_p,
                                                            const int *__restrict__ lev_sbeg,
                                                            const int *__restrict__ nband, int *__restrict__ tperm) {
     grid_dep_wait();
     __shared__ int s_hist[kTileCells + 1];
     const int nl = *nlev_p;
-    for (int L = 0; L < nl; ++L) {
+    for (int L = blockIdx.x; L < nl; L += gridDim.x) {  // one CTA per wavefront
         const int s0 = lev_sbeg[L], s1 = lev_sbeg[L + 1];
         for (int k = threadIdx.x; k <= kTileCells; k += blockDim.x) s_hist[k] = 0;
         __syncthreads();
@@ -1577,8 +1577,8 @@ static int run_mdf(ib_ctx *ctx, Arena &ar, const CaseTab &ct, const ib_particles
     }
     launch_pdl(k_level_slots, dim3(1), dim3(256), 0, s, sg.mode, (const int *)lo.nlev, (const int *)lo.lev_pbeg,
                (const uint32_t *)sl.flag_scan, (int)ndense, lev_sbeg);
-    launch_pdl(k_level_tile_order, dim3(1), dim3(1024), 0, s, (const int *)lo.nlev, (const int *)lev_sbeg,
-               (const int *)sl.nband, tperm);
+    launch_pdl(k_level_tile_order, dim3(P < 64 ? P : 64), dim3(512), 0, s, (const int *)lo.nlev,
+               (const int *)lev_sbeg, (const int *)sl.nband, tperm);
     tprep.stop();
     // (the field is first read and written by the pass kernels below)
     if (ctx->field_wait) cudaStreamWaitEvent(s, (cudaEvent_t)ctx->field_wait, 0);

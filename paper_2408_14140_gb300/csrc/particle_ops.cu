@@ -254,31 +254,62 @@ __global__ void __launch_bounds__(kVolThreads, 3) k_volume(CaseTab ct, int P, in
     const DevCase &cd = ct.of_particle(p);
     const DevGrid g = cd.g;
     const T *__restrict__ u = (const T *)cd.u;
-    const double c[3] = {Xr[3 * p], Xr[3 * p + 1], Xr[3 * p + 2]};
-    const double Rp = radius[p];
-    double acc[7] = {0, 0, 0, 0, 0, 0, 0};
-    bool ok = finite3(c) && isfinite(Rp) && Rp > 0.0;
-    if (!ok && threadIdx.x == 0 && split == 0) raise_status(st, IB_ERR_NONFINITE, p);
-    int lo[3] = {0, 0, 0}, dims[3] = {0, 0, 0};
-    if (ok) {
-        for (int a = 0; a < 3; ++a) {
-            long long l = (long long)floor((c[a] - Rp - g.org[a]) * g.inv_h) - 1;
-            long long hgh = (long long)floor((c[a] + Rp - g.org[a]) * g.inv_h) + 1;
-            lo[a] = (int)l;
-            dims[a] = (int)(hgh - l + 1);
-            if (dims[a] > g.n[a] || l < INT_MIN / 2 || l > INT_MAX / 2) ok = false;
+    // the particle's scalars, formed once by thread 0 (FP64 is scarce here:
+    // 256 threads each forming them cost more than a slab's cells)
+    __shared__ double s_c[3], s_d[6];
+    __shared__ float s_f[4];  // x of node 0 and of cell 0, 1/R as a float pair
+    __shared__ int s_box[7];
+    if (threadIdx.x == 0) {
+        const double cc[3] = {Xr[3 * p], Xr[3 * p + 1], Xr[3 * p + 2]};
+        const double R0 = radius[p];
+        bool okk = finite3(cc) && isfinite(R0) && R0 > 0.0;
+        if (!okk && split == 0) raise_status(st, IB_ERR_NONFINITE, p);
+        int lo0[3] = {0, 0, 0}, dm0[3] = {0, 0, 0};
+        if (okk) {
+            for (int a = 0; a < 3; ++a) {
+                long long l = (long long)floor((cc[a] - R0 - g.org[a]) * g.inv_h) - 1;
+                long long hgh = (long long)floor((cc[a] + R0 - g.org[a]) * g.inv_h) + 1;
+                lo0[a] = (int)l;
+                dm0[a] = (int)(hgh - l + 1);
+                if (dm0[a] > g.n[a] || l < INT_MIN / 2 || l > INT_MAX / 2) okk = false;
+            }
+            if (!okk && split == 0) raise_status(st, IB_ERR_UNSUPPORTED, p);
         }
-        if (!ok && threadIdx.x == 0 && split == 0) raise_status(st, IB_ERR_UNSUPPORTED, p);
+        for (int a = 0; a < 3; ++a) {
+            s_c[a] = cc[a];
+            s_box[a] = lo0[a];
+            s_box[3 + a] = dm0[a];
+        }
+        s_box[6] = okk;
+        if (okk) {
+            const double hh = g.h;
+            const double rin = R0 - 0.8661 * hh, rout = R0 + 0.8661 * hh;
+            const double sl = fmax(0.0, R0 - 1.75 * hh), sh = R0 + 1.75 * hh;
+            s_d[0] = R0;
+            s_d[1] = 1.0 / R0;
+            s_d[2] = rin > 0 ? rin * rin : -1.0;
+            s_d[3] = rout * rout;
+            s_d[4] = sl * sl;
+            s_d[5] = sh * sh;
+            s_f[0] = (float)(g.org[0] + (double)lo0[0] * hh - cc[0]);
+            s_f[1] = (float)(g.org[0] + ((double)lo0[0] + 0.5) * hh - cc[0]);
+            const float2 ir = df_split(s_d[1]);
+            s_f[2] = ir.x;
+            s_f[3] = ir.y;
+        }
     }
+    __syncthreads();
+    const double c[3] = {s_c[0], s_c[1], s_c[2]};
+    double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+    const bool ok = s_box[6] != 0;
+    const int lo[3] = {s_box[0], s_box[1], s_box[2]}, dims[3] = {s_box[3], s_box[4], s_box[5]};
     const int t = (dims[2] + nsplit - 1) / nsplit;
     const int z0 = split * t, z1 = min(dims[2], z0 + t);
     if (ok && z0 < z1) {
         const long long N = (long long)g.n[0] * g.n[1] * g.n[2];
-        const double h = g.h, iR = 1.0 / Rp;
-        const double rin = Rp - 0.8661 * h, rout = Rp + 0.8661 * h;
-        const double rin2 = rin > 0 ? rin * rin : -1.0, rout2 = rout * rout;
-        const double sl = fmax(0.0, Rp - 1.75 * h), sh = Rp + 1.75 * h;
-        const double sl2 = sl * sl, sh2 = sh * sh;
+        const double h = g.h, iR = s_d[1];
+        const double rin2 = s_d[2], rout2 = s_d[3];
+        const double sl2 = s_d[4], sh2 = s_d[5];
         const int lo0w = wrap_int(lo[0], g.n[0]);
         const bool tab = dims[0] <= kVolMaxBox && dims[1] <= kVolMaxBox && dims[2] <= kVolMaxBox;
         if (tab) {
@@ -302,7 +333,7 @@ __global__ void __launch_bounds__(kVolThreads, 3) k_volume(CaseTab ct, int P, in
                         tcf[a * kVolAx + i] = (float)(xc * xc);
                     }
                 }
-            const float2 iRf = df_split(iR);
+            const float2 iRf = make_float2(s_f[2], s_f[3]);
             // FP32 centre tests with a relative margin far above their rounding;
             // cells in the margin take the corner formula, exact for them too
             const float rout2f = (float)rout2 * (1.0f + 1e-5f);
@@ -326,8 +357,7 @@ __global__ void __launch_bounds__(kVolThreads, 3) k_volume(CaseTab ct, int P, in
                 first = max(0, (int)floorf((-w - base) * fih + kEps) + 1);
                 last = min(n - 1, (int)ceilf((w - base) * fih - kEps) - 1);
             };
-            const float xbf = (float)(g.org[0] + (double)lo[0] * h - c[0]);            // x of node 0
-            const float xcbf = (float)(g.org[0] + ((double)lo[0] + 0.5) * h - c[0]);   // x of cell 0
+            const float xbf = s_f[0], xcbf = s_f[1];  // x of node 0 and of cell 0
             // FP32 fields: the per-row ranges from FP32 squares, the shell and
             // the cell bounds widened by a relative 1e-5 (the rows and cells
             // that matter lie 0.01 h inside the node shell and 8e-5 h inside
