@@ -327,11 +327,9 @@ __global__ void __launch_bounds__(kVolThreads, 3) k_volume(CaseTab ct, int P, in
                     tb[a * kVolAx + i] = xn * xn;
                     tb[(3 + a) * kVolAx + i] = xc;
                     tb[(6 + a) * kVolAx + i] = xc * xc;
-                    if (sizeof(T) == 4) {
-                        tbf[a * kVolAx + i] = df_split(xc);
-                        tsq[a * kVolAx + i] = df_split(xn * xn);
-                        tcf[a * kVolAx + i] = (float)(xc * xc);
-                    }
+                    tbf[a * kVolAx + i] = df_split(xc);
+                    tsq[a * kVolAx + i] = df_split(xn * xn);
+                    tcf[a * kVolAx + i] = (float)(xc * xc);
                 }
             const float2 iRf = make_float2(s_f[2], s_f[3]);
             // FP32 centre tests with a relative margin far above their rounding;
@@ -369,7 +367,7 @@ __global__ void __launch_bounds__(kVolThreads, 3) k_volume(CaseTab ct, int P, in
                 for (int j = threadIdx.x; j < rows; j += blockDim.x) {
                     bool in_shell, beyond_sl;
                     float wo, wi;
-                    if constexpr (sizeof(T) == 4) {
+                    if constexpr (true) {
                         const float dyz = tsq[kVolAx + j].x + tsq[2 * kVolAx + kn].x;
                         in_shell = dyz < sh2f;
                         beyond_sl = sl2f > dyz;
@@ -412,8 +410,8 @@ __global__ void __launch_bounds__(kVolThreads, 3) k_volume(CaseTab ct, int P, in
                     const int i = k < r_nc[0][j] ? r_na[j] + k : r_nb[j] + (k - r_nc[0][j]);
                     // every listed node gets its level set value (nodes slightly
                     // outside the shell too: the values stay exact)
-                    if constexpr (sizeof(T) == 4) {
-                        // FP32 fields: double-float level set, stored as
+                    if constexpr (true) {
+                        // double-float level set, stored as
                         // (max(-phi, 0), max(phi, 0)) float pairs
                         const DF x2 = df_sum(DF{tsq[i].x, tsq[i].y},
                                              df_sum(DF{tsq[kVolAx + j].x, tsq[kVolAx + j].y},
@@ -443,7 +441,7 @@ __global__ void __launch_bounds__(kVolThreads, 3) k_volume(CaseTab ct, int P, in
                 for (int j = threadIdx.x; j < dims[1]; j += blockDim.x) {
                     bool in_out, in_in;
                     float wo, wi;
-                    if constexpr (sizeof(T) == 4) {
+                    if constexpr (true) {
                         const float ryz2 = tcf[kVolAx + j] + tcf[2 * kVolAx + kz];
                         in_out = ryz2 <= rout2f;
                         in_in = ryz2 < rin2f;
@@ -481,7 +479,7 @@ __global__ void __launch_bounds__(kVolThreads, 3) k_volume(CaseTab ct, int P, in
                 __syncthreads();
                 const double2 *b0 = phi2 + (kz & 1) * plane, *b1 = phi2 + ((kz + 1) & 1) * plane;
                 const float2 fz = sizeof(T) == 4 ? tbf[2 * kVolAx + kz] : make_float2(0.f, 0.f);
-                const float rz2f = sizeof(T) == 4 ? tcf[2 * kVolAx + kz] : 0.f;
+                const float rz2f = tcf[2 * kVolAx + kz];
                 const long long plane_off = (long long)wrap_int(lo[2] + kz, g.n[2]) * g.n[1] * g.n[0];
                 double s0 = 0, s1 = 0, s2 = 0;  // plane sums of alpha u
                 // interior cells: alpha = 1
@@ -521,8 +519,8 @@ __global__ void __launch_bounds__(kVolThreads, 3) k_volume(CaseTab ct, int P, in
                     const int j = find_row(p_bnd, dims[1], q);
                     const int k = q - p_bnd[j];
                     const int i = k < r_ca[j] ? r_ia[j] + k : r_ic[j] + c_int[j] + (k - r_ca[j]);
-                    if constexpr (sizeof(T) == 4) {
-                        // FP32 fields: the same cell in double-float, no FP64
+                    {
+                        // the cell's alpha in double-float (both field precisions)
                         const float d2f = tcf[i] + tcf[kVolAx + j] + rz2f;
                         if (d2f > rout2f) continue;
                         float2 a2 = make_float2(1.f, 0.f);
@@ -558,9 +556,25 @@ __global__ void __launch_bounds__(kVolThreads, 3) k_volume(CaseTab ct, int P, in
                             }
                         }
                         const long long cc = plane_off + row_off[j] + wrap_add(lo0w, i, g.n[0]);
+                        if constexpr (sizeof(T) == 8) {
+                            // FP64 fields: the sums in FP64
+                            const double al = (double)a2.x + (double)a2.y;
+                            const double rx = tb[3 * kVolAx + i], ry = tb[4 * kVolAx + j];
+                            const double w0 = al * (double)u[cc], w1 = al * (double)u[N + cc],
+                                         w2 = al * (double)u[2 * N + cc];
+                            s0 += w0;
+                            s1 += w1;
+                            s2 += w2;
+                            sA = fma(ry, w2, sA);
+                            sB = fma(rx, w2, sB);
+                            sC = fma(rx, w1, sC);
+                            sD = fma(ry, w0, sD);
+                            svol += al;
+                            continue;
+                        }
                         df_add2(V, a2.x, a2.y);
                         const float2 fx = tbf[i], fy = tbf[kVolAx + j];
-                        const float v[3] = {u[cc], u[N + cc], u[2 * N + cc]};
+                        const float v[3] = {(float)u[cc], (float)u[N + cc], (float)u[2 * N + cc]};
                         float wh[3], wl[3];
 #pragma unroll
                         for (int q3 = 0; q3 < 3; ++q3) {
