@@ -283,14 +283,15 @@ class Runner:
 
 
 def launches_per_step(Ns, levels):
-    """Library kernels per step on this workload (P * 512 = 32768 dense tiles,
-    so each scan is three kernels): volume 1 x 2 calls; multidirect forcing:
-    prep, conflicts, levels, marker order, tile count, scan (3), flags, scan
-    (3), compact, fill, sort, per-cell lists, level ranges (17), one
-    interpolation and one gather kernel per wavefront and pass, the
-    persistent remainder kernel (1); force/torque 1; collision +
-    Newton-Euler 2."""
-    return 2 + 17 + 2 * Ns * levels + 1 + 1 + 2
+    """Library kernels per step on this workload (P * 512 = 32768 dense tiles
+    and ~1e6 candidate slots, so each scan is three kernels): volume 1 x 2
+    calls; multidirect forcing: prep, conflicts, levels, marker order, tile
+    count, scan (3), flags, scan (3), compact, fill, scan (3), sort, per-cell
+    lists, level ranges, tile order (21), one interpolation and one gather
+    kernel per wavefront and pass, the persistent remainder kernel (1);
+    force/torque 1; collision + Newton-Euler 2.  (The ncu launch list shows
+    77 kernels between consecutive steps for Ns = 5 and 5 wavefronts.)"""
+    return 2 + 21 + 2 * Ns * levels + 1 + 1 + 2
 
 
 def time_steps(runner, steps, warmup, flush, use_graph):

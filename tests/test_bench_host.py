@@ -56,4 +56,4 @@ def test_workload_bookkeeping():
     assert len(lb) == bench.wavefront_levels(case)
     assert sum(m for _, m in lb) == case.M
     assert sum(b for b, _ in lb) >= bench.band_cells(case)
-    assert bench.launches_per_step(5, 5) == 73
+    assert bench.launches_per_step(5, 5) == 77
