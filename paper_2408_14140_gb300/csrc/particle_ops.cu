@@ -907,6 +907,7 @@ __global__ void k_collide_forces(CollideArgs a, double *__restrict__ Fc) {
 }
 
 __global__ void k_newton_euler(CollideArgs a, const double *__restrict__ Fc, DevStatus *st) {
+    grid_dep_wait();  // a programmatic dependent of the collision forces
     int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= a.P) return;
     const DevCase &cd = a.ct.of_particle(p);
@@ -1173,7 +1174,7 @@ static int run_collide(ib_ctx *ctx, Arena &ar, const CaseTab &ct, ib_particles *
     int nb = (parts->P + 127) / 128;
     PhaseTimer tm(ctx, IB_PHASE_COLLIDE, s);
     k_collide_forces<<<(parts->P + 3) / 4, 128, 0, s>>>(a, Fc);
-    k_newton_euler<<<nb, 128, 0, s>>>(a, Fc, ctx->status);
+    launch_pdl(k_newton_euler, dim3(nb), dim3(128), 0, s, a, (const double *)Fc, ctx->status);
     return check_launch("particle_collide_update");
 }
 
