@@ -1270,9 +1270,20 @@ __global__ void __launch_bounds__(kGatherThreads, sizeof(T) == 4 ? 5 : 4) k_gath
         grid_dep_wait();
         return;
     }
+    // Tiles come largest first.  FP64 sums are bound by FP64 issue, so their
+    // rounds alternate direction (boustrophedon): the CTA with the largest tile
+    // of one round takes the smallest of the next (measured 4 % faster per
+    // step).  FP32 tiles are latency-bound and finish sooner in plain
+    // grid-stride order (measured 0.5 %).  Either way, once a round's index
+    // passes the end, every later round's does too.
     // (the wait inside returns at once after the first tile)
-    for (int k = s0 + blockIdx.x; k < s1; k += gridDim.x)
-        gather_tile_level<T, Kernel<KER>::W>(a.ct, a.tperm[k], a.sl, a.ms.wts, a.ms.A, a.inv_dt, sw, sA, sp);
+    constexpr bool kSnake = sizeof(T) == 8;
+    const int G = gridDim.x, i = blockIdx.x, nt = s1 - s0;
+    for (int r = 0;; ++r) {
+        const int j = (kSnake && (r & 1)) ? (r + 1) * G - 1 - i : r * G + i;
+        if (j >= nt) break;
+        gather_tile_level<T, Kernel<KER>::W>(a.ct, a.tperm[s0 + j], a.sl, a.ms.wts, a.ms.A, a.inv_dt, sw, sA, sp);
+    }
 }
 
 template <typename T, int KER>
