@@ -357,14 +357,16 @@ def kernel_timing(runner, steps, flush):
     return out
 
 
-def e2e_steps(runner, steps, partner=None):
+def e2e_steps(runner, steps, partners=()):
     """Same step through the public API with host buffers: every step copies
     its inputs from pinned host memory to the device, runs, and reads its
-    results back.  With a partner replica the steps are pipelined over the
-    two replicas: step k+1's inputs upload (one copy stream) while step k
-    computes and step k-1's results download (another copy stream)."""
+    results back.  With partner replicas the steps are pipelined over the
+    replicas in turn: step k+1's inputs upload (one copy stream) while step k
+    computes and step k-1's results download (another copy stream).  A
+    replica's next upload waits for its previous download, so with three
+    replicas that wait no longer gates the next step's upload."""
     torch = runner.torch
-    reps = [runner] + ([partner] if partner is not None else [])
+    reps = [runner] + list(partners)
 
     def dev_in(r):
         return [r.u, r.parts["Xr"], r.parts["Ur"], r.parts["Wr"], r.parts["radius"], r.parts["rho_p"],
@@ -380,7 +382,7 @@ def e2e_steps(runner, steps, partner=None):
     s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()
     s_c = torch.cuda.current_stream()
     freed = [None] * len(reps)  # replica k's previous results downloaded
-    for r in reps[1:]:  # warm-up of the partner (its first call sizes its launches)
+    for r in reps[1:]:  # warm-up of the partners (a first call sizes its launches)
         for _ in range(2):
             r.step()
     torch.cuda.synchronize()
@@ -630,9 +632,10 @@ def run_gpu(args):
         kt = kernel_timing(r, max(3, min(args.steps, 10)), flush)
         e2e = None
         if not args.no_e2e:
-            partner = Runner(case, prec, device)  # second replica: uploads overlap compute
-            e2e = e2e_steps(r, max(4, min(args.steps, 12)), partner)
-            del partner
+            # two more replicas: uploads and downloads overlap compute
+            partners = [Runner(case, prec, device) for _ in range(2)]
+            e2e = e2e_steps(r, max(6, min(args.steps, 30)), partners)
+            del partners
         results[prec] = dict(ms=ms, t=t_rank, graphed=graphed, clocks=clocks, kt=kt, e2e=e2e,
                              runner=r)
         del r
@@ -703,7 +706,8 @@ def run_gpu(args):
     if f32["e2e"]:
         dt, bi, bo = f32["e2e"]
         line["e2e"] = {"value": world * M * Ns / dt, "unit": "marker-updates/s",
-                       "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo}
+                       "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo,
+                       "pipeline": "3 device replicas in turn, one copy stream per direction"}
     if f64["e2e"]:
         dt, bi, bo = f64["e2e"]
         line["fp64"]["e2e"] = {"value": world * M * Ns / dt, "h2d_bytes_per_step": bi,
