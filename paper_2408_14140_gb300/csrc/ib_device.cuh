@@ -435,7 +435,7 @@ struct ResidentArgs {
     const double *dV;       // [M]
     MarkerState<T> ms;
     Slots sl;               // particle-local tiles, compact and sorted
-    const int *mperm;       // markers level-major, spatially sorted per particle
+    const int *mperm;       // markers level-major, each particle's in index order
     const int *mbase;       // [P] first position of a particle's markers in mperm
     const int *moff;        // [P+1]
     const int *by_rank;     // [P] particle of each rank (level-major order)

@@ -652,8 +652,9 @@ __global__ void k_marker_order(int P, const int *__restrict__ moff, const int *_
 
 // ---------------------------------------------------------------------------
 // per-slot sort by (row, marker) and row starts.  Tiles with at most
-// kWarpSort candidates are sorted by one warp each (bitonic network in a
-// warp-private shared-memory region); larger tiles by a whole CTA.
+// kWarpSort candidates are sorted by one warp each (bitonic network in
+// registers, the sorted keys then kept in a warp-private shared-memory
+// region); larger tiles by a whole CTA (bitonic network in shared memory).
 // ---------------------------------------------------------------------------
 constexpr int kWarpSort = 256;
 
@@ -732,6 +733,55 @@ __device__ __forceinline__ void slot_emit(const DevGrid &g, const uint64_t *anch
     }
 }
 
+// Sorts 32 R keys held by one warp, element e = 32 r + lane in x[r], with a
+// bitonic network in registers: partners in other lanes come by shuffle,
+// partners in the same lane are compared directly.
+template <int R>
+__device__ __forceinline__ void warp_bitonic(unsigned long long (&x)[R], int lane) {
+#pragma unroll
+    for (int k = 2; k <= 32 * R; k <<= 1)
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            if (j >= 32) {
+                const int jr = j >> 5;
+#pragma unroll
+                for (int r = 0; r < R; ++r)
+                    if ((r & jr) == 0) {
+                        const bool asc = ((32 * r + lane) & k) == 0;
+                        const unsigned long long a = x[r], b = x[r | jr];
+                        const bool sw = (a > b) == asc;
+                        x[r] = sw ? b : a;
+                        x[r | jr] = sw ? a : b;
+                    }
+            } else {
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const unsigned long long y = __shfl_xor_sync(0xffffffffu, x[r], j);
+                    // the lower index of a pair keeps the minimum in an
+                    // ascending block, the maximum in a descending one
+                    const bool take_min = ((lane & j) == 0) == (((32 * r + lane) & k) == 0);
+                    x[r] = take_min ? (y < x[r] ? y : x[r]) : (y > x[r] ? y : x[r]);
+                }
+            }
+        }
+}
+
+// One warp: keys of a tile with nc <= 32 R candidates into wk[0, 32 R), sorted.
+template <int R>
+__device__ __forceinline__ void warp_sort_keys(const DevGrid &g, const uint64_t *anchor, const uint32_t *cand,
+                                               int nc, const int lo[3], unsigned long long *wk, int lane) {
+    unsigned long long x[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int e = 32 * r + lane;
+        x[r] = e < nc ? slot_key(g, anchor, cand[e], lo) : ~0ull;
+    }
+    warp_bitonic<R>(x, lane);
+#pragma unroll
+    for (int r = 0; r < R; ++r) wk[32 * r + lane] = x[r];
+    __syncwarp();
+}
+
 __global__ void __launch_bounds__(kBlock) k_slot_sort(
     CaseTab ct, int mode, int ncompact_cap, const int *__restrict__ ncompact_p, SlotGeom sg,
     const uint32_t *__restrict__ dense_of, const uint32_t *__restrict__ start,
@@ -750,24 +800,10 @@ __global__ void __launch_bounds__(kBlock) k_slot_sort(
         int lo[3], dim[3], lev;
         const int cse = slot_geometry(ct, mode, sg, sl, level, d, b, lo, dim, lev);
         const DevGrid &g = ct.get(cse).g;
-        int np2 = 1;
-        while (np2 < nc) np2 <<= 1;
-        for (int i = lane; i < np2; i += 32) wk[i] = i < nc ? slot_key(g, anchor, sl.cand[b + i], lo) : ~0ull;
-        __syncwarp();
-        for (int k = 2; k <= np2; k <<= 1)
-            for (int j = k >> 1; j > 0; j >>= 1) {
-                for (int i = lane; i < np2; i += 32) {
-                    const int ixj = i ^ j;
-                    if (ixj > i) {
-                        const unsigned long long x = wk[i], y = wk[ixj];
-                        if ((x > y) == ((i & k) == 0)) {
-                            wk[i] = y;
-                            wk[ixj] = x;
-                        }
-                    }
-                }
-                __syncwarp();
-            }
+        static_assert(kWarpSort == 256, "warp sorts cover 64, 128 or 256 keys");
+        if (nc <= 64) warp_sort_keys<2>(g, anchor, sl.cand + b, nc, lo, wk, lane);
+        else if (nc <= 128) warp_sort_keys<4>(g, anchor, sl.cand + b, nc, lo, wk, lane);
+        else warp_sort_keys<8>(g, anchor, sl.cand + b, nc, lo, wk, lane);
         slot_emit(g, anchor, wk, nc, b, cs, lo, sl, lane, 32);
         if (lane == 0) {
             sl.geo_lo[cs] = make_int4(lo[0], lo[1], lo[2], lev);
@@ -777,56 +813,72 @@ __global__ void __launch_bounds__(kBlock) k_slot_sort(
         __syncwarp();
     }
     __syncthreads();
-    // ---- phase 2: one CTA per large tile
-    for (int cs = blockIdx.x; cs < ncompact; cs += gridDim.x) {
-        const uint32_t d = dense_of[cs];
-        const uint32_t b = start[d];
-        const int nc = (int)(start[d + 1] - b);
-        if (nc <= kWarpSort) continue;
-        int lo[3], dim[3], lev;
-        const int cse = slot_geometry(ct, mode, sg, sl, level, d, b, lo, dim, lev);
-        const DevGrid &g = ct.get(cse).g;
-        if (nc > kMaxCand) {
-            // report, and leave an empty tile (no bins, no cells)
-            if (sl.bins) {
-                uint16_t *bs = sl.bins + (size_t)cs * kBins;
-                for (int r = threadIdx.x; r < kBins; r += blockDim.x) bs[r] = 0;
+    // ---- phase 2: one CTA per large tile.  The CTA's tiles (cs = blockIdx.x
+    // mod gridDim.x) are screened blockDim.x at a time, one load per thread,
+    // and only the large ones are walked.
+    __shared__ int s_big[kBlock];
+    __shared__ int s_nbig;
+    for (long long c0 = blockIdx.x; c0 < ncompact; c0 += (long long)gridDim.x * blockDim.x) {
+        if (threadIdx.x == 0) s_nbig = 0;
+        __syncthreads();
+        const long long ct_cs = c0 + (long long)threadIdx.x * gridDim.x;
+        if (ct_cs < ncompact) {
+            const uint32_t d = dense_of[ct_cs];
+            if ((int)(start[d + 1] - start[d]) > kWarpSort) s_big[atomicAdd(&s_nbig, 1)] = (int)ct_cs;
+        }
+        __syncthreads();
+        const int nbig = s_nbig;
+        for (int q = 0; q < nbig; ++q) {
+            const int cs = s_big[q];
+            const uint32_t d = dense_of[cs];
+            const uint32_t b = start[d];
+            const int nc = (int)(start[d + 1] - b);
+            int lo[3], dim[3], lev;
+            const int cse = slot_geometry(ct, mode, sg, sl, level, d, b, lo, dim, lev);
+            const DevGrid &g = ct.get(cse).g;
+            if (nc > kMaxCand) {
+                // report, and leave an empty tile (no bins, no cells)
+                if (sl.bins) {
+                    uint16_t *bs = sl.bins + (size_t)cs * kBins;
+                    for (int r = threadIdx.x; r < kBins; r += blockDim.x) bs[r] = 0;
+                }
+                if (threadIdx.x == 0) {
+                    raise_status(st, IB_ERR_UNSUPPORTED, nc);
+                    sl.geo_lo[cs] = make_int4(lo[0], lo[1], lo[2], lev);
+                    sl.geo_dim[cs] = make_int4(0, 0, 0, (int)b);
+                    sl.geo_case[cs] = cse;
+                }
+                __syncthreads();
+                continue;
             }
+            int np2 = 1;
+            while (np2 < nc) np2 <<= 1;
+            for (int i = threadIdx.x; i < np2; i += blockDim.x)
+                keys[i] = i < nc ? slot_key(g, anchor, sl.cand[b + i], lo) : ~0ull;
+            __syncthreads();
+            for (int k = 2; k <= np2; k <<= 1)
+                for (int j = k >> 1; j > 0; j >>= 1) {
+                    for (int i = threadIdx.x; i < np2; i += blockDim.x) {
+                        const int ixj = i ^ j;
+                        if (ixj > i) {
+                            const unsigned long long x = keys[i], y = keys[ixj];
+                            if ((x > y) == ((i & k) == 0)) {
+                                keys[i] = y;
+                                keys[ixj] = x;
+                            }
+                        }
+                    }
+                    __syncthreads();
+                }
+            slot_emit(g, anchor, keys, nc, b, cs, lo, sl, threadIdx.x, blockDim.x);
             if (threadIdx.x == 0) {
-                raise_status(st, IB_ERR_UNSUPPORTED, nc);
                 sl.geo_lo[cs] = make_int4(lo[0], lo[1], lo[2], lev);
-                sl.geo_dim[cs] = make_int4(0, 0, 0, (int)b);
+                sl.geo_dim[cs] = make_int4(dim[0], dim[1], dim[2], (int)b);
                 sl.geo_case[cs] = cse;
             }
             __syncthreads();
-            continue;
         }
-        int np2 = 1;
-        while (np2 < nc) np2 <<= 1;
-        for (int i = threadIdx.x; i < np2; i += blockDim.x)
-            keys[i] = i < nc ? slot_key(g, anchor, sl.cand[b + i], lo) : ~0ull;
-        __syncthreads();
-        for (int k = 2; k <= np2; k <<= 1)
-            for (int j = k >> 1; j > 0; j >>= 1) {
-                for (int i = threadIdx.x; i < np2; i += blockDim.x) {
-                    const int ixj = i ^ j;
-                    if (ixj > i) {
-                        const unsigned long long x = keys[i], y = keys[ixj];
-                        if ((x > y) == ((i & k) == 0)) {
-                            keys[i] = y;
-                            keys[ixj] = x;
-                        }
-                    }
-                }
-                __syncthreads();
-            }
-        slot_emit(g, anchor, keys, nc, b, cs, lo, sl, threadIdx.x, blockDim.x);
-        if (threadIdx.x == 0) {
-            sl.geo_lo[cs] = make_int4(lo[0], lo[1], lo[2], lev);
-            sl.geo_dim[cs] = make_int4(dim[0], dim[1], dim[2], (int)b);
-            sl.geo_case[cs] = cse;
-        }
-        __syncthreads();
+        __syncthreads();  // s_big and s_nbig are reused by the next screen
     }
 }
 
@@ -1424,9 +1476,12 @@ static int slots_build(ib_ctx *ctx, const CaseTab &ct, int M, int ndense, SlotGe
                sl.cursor, sl.cand, sl.pcnt);
     if (with_pairs) exclusive_scan(sl.pcnt, sl.poff, (int)sc.cand_cap, sc.cscratch, s);
     ncompact_dev = (int *)(sl.flag_scan + ndense);
-    launch_pdl(k_slot_sort, dim3(ctx->sm_count * 4), dim3(kBlock), 0, s, ct, sg.mode, sc.ncompact_cap,
-               (const int *)ncompact_dev, sg, (const uint32_t *)sl.dense_of, (const uint32_t *)sl.start, anchor,
-               level, sl, ctx->status);
+    // one resident wave (a second wave would only repeat the screening)
+    int sper = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&sper, k_slot_sort, kBlock, 0);
+    launch_pdl(k_slot_sort, dim3(ctx->sm_count * (sper > 0 ? sper : 1)), dim3(kBlock), 0, s, ct, sg.mode,
+               sc.ncompact_cap, (const int *)ncompact_dev, sg, (const uint32_t *)sl.dense_of,
+               (const uint32_t *)sl.start, anchor, level, sl, ctx->status);
     if (with_pairs)
         launch_pdl(k_tile_pairs<KW>, dim3(ctx->sm_count * 8), dim3(kPairThreads), 0, s, ct, sc.ncompact_cap,
                    (const int *)ncompact_dev, sl, anchor);
