@@ -889,17 +889,18 @@ __global__ void __launch_bounds__(kBlock) k_slot_sort(
 // order and a bin's candidates in index order -- in ascending candidate
 // index, the order the tile's candidates are sorted in -- so listing every
 // cell's candidates in ascending index reproduces its summation order.
-// The (candidate, stencil cell) pairs are enumerated candidate-major and
-// scattered by a stable counting sort on the cell: each warp counts its
-// contiguous segment of the enumeration, a scan over (cell, warp) gives every
-// warp its base in every cell's list, and each warp then places its pairs in
-// enumeration order (lanes with the same cell ranked by lane).
+// The (candidate, stencil cell) pairs are scattered by a stable counting sort
+// on the cell: each warp counts the pairs of a contiguous range of candidates
+// (one candidate per step, one lane per stencil offset, so the cells of a
+// step are distinct), a scan over (cell, warp) gives every warp its base in
+// every cell's list, and each warp then places its pairs candidate by
+// candidate.
 // ---------------------------------------------------------------------------
 constexpr int kPairThreads = 256;
 constexpr int kPairWarps = kPairThreads / 32;
 
 template <int KW>
-__global__ void __launch_bounds__(kPairThreads) k_tile_pairs(CaseTab ct, int ncompact_cap,
+__global__ void __launch_bounds__(kPairThreads, 5) k_tile_pairs(CaseTab ct, int ncompact_cap,
                                                              const int *__restrict__ ncompact_p, Slots sl,
                                                              const uint64_t *__restrict__ anchor) {
     grid_dep_wait();
@@ -909,7 +910,15 @@ __global__ void __launch_bounds__(kPairThreads) k_tile_pairs(CaseTab ct, int nco
     __shared__ int s_wp[kPairWarps], s_wb[kPairWarps];
     const int ncompact = min(*ncompact_p, ncompact_cap);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const unsigned lt_mask = (1u << lane) - 1u;
+    // this lane's stencil offsets k = lane + 32 q
+    // (ox | oy << 2 | oz << 4, or ~0u past the stencil)
+    constexpr int kSub = (KW3 + 31) / 32;
+    unsigned kcode[kSub];
+#pragma unroll
+    for (int q = 0; q < kSub; ++q) {
+        const int k = lane + 32 * q;
+        kcode[q] = k < KW3 ? (unsigned)((k % KW) | (((k / KW) % KW) << 2) | ((k / (KW * KW)) << 4)) : ~0u;
+    }
     for (int cs = blockIdx.x; cs < ncompact; cs += gridDim.x) {
         const int4 lo = sl.geo_lo[cs], dim = sl.geo_dim[cs];
         const DevGrid g = ct.get(sl.geo_case[cs]).g;
@@ -932,23 +941,27 @@ __global__ void __launch_bounds__(kPairThreads) k_tile_pairs(CaseTab ct, int nco
         }
         for (int c = tid; c < kPairWarps * kTileCells; c += blockDim.x) (&s_cnt[0][0])[c] = 0;
         __syncthreads();
-        // pair e = i * KW3 + k: candidate i, stencil offset k; cell or -1
-        auto cell_of = [&](int e, unsigned &code) {
-            const int i = e / KW3, k = e - i * KW3;
-            const int ox = k % KW, oy = (k / KW) % KW, oz = k / (KW * KW);
-            const unsigned pk = s_anc[i];
-            const int x = (int)(pk & 15) - 3 + ox, y = (int)((pk >> 4) & 15) - 3 + oy, z = (int)(pk >> 8) - 3 + oz;
-            code = (unsigned)i | ((unsigned)(ox | (oy << 2) | (oz << 4)) << 16);
-            return (x >= 0 && x < dim.x && y >= 0 && y < dim.y && z >= 0 && z < dim.z) ? (z * kTile + y) * kTile + x
-                                                                                      : -1;
+        // Each warp walks a contiguous range of candidates, one candidate per
+        // step, lane l taking the stencil offsets k = l + 32 q: the cells of
+        // one step are distinct, so counts and list slots need no ranking.
+        const int seg = (nc + kPairWarps - 1) / kPairWarps;
+        const int i0 = min(nc, warp * seg), i1 = min(nc, i0 + seg);
+        // cell of candidate i's stencil offset (lane, q), or -1
+        auto cell_of = [&](unsigned pk, int q) {
+            const unsigned o = kcode[q];
+            const int x = (int)(pk & 15) - 3 + (int)(o & 3), y = (int)((pk >> 4) & 15) - 3 + (int)((o >> 2) & 3),
+                      z = (int)(pk >> 8) - 3 + (int)((o >> 4) & 3);
+            return (o != ~0u && x >= 0 && x < dim.x && y >= 0 && y < dim.y && z >= 0 && z < dim.z)
+                       ? (z * kTile + y) * kTile + x
+                       : -1;
         };
-        const int ne = nc * KW3;
-        const int seg = (ne + kPairWarps - 1) / kPairWarps;
-        const int e0 = min(ne, warp * seg), e1 = min(ne, e0 + seg);
-        for (int e = e0 + lane; e < e1; e += 32) {
-            unsigned code;
-            const int c = cell_of(e, code);
-            if (c >= 0) atomicAdd(&s_cnt[warp][c], 1u);
+        for (int i = i0; i < i1; ++i) {
+            const unsigned pk = s_anc[i];
+#pragma unroll
+            for (int q = 0; q < kSub; ++q) {
+                const int c = cell_of(pk, q);
+                if (c >= 0) atomicAdd(&s_cnt[warp][c], 1u);
+            }
         }
         __syncthreads();
         // (cell, warp) scan: thread t owns cells 2t and 2t + 1
@@ -982,18 +995,15 @@ __global__ void __launch_bounds__(kPairThreads) k_tile_pairs(CaseTab ct, int nco
 #pragma unroll
             for (int w = 0; w < kPairWarps; ++w) s_cnt[w][2 * tid + h] = (unsigned)(cbase[h] + pre[h][w]);
         __syncthreads();
-        // stable placement of this warp's segment
-        for (int eb = e0; eb < e1; eb += 32) {
-            const int e = eb + lane;
-            unsigned code = 0;
-            const int c = e < e1 ? cell_of(e, code) : -1;
-            const unsigned peers = __match_any_sync(0xffffffffu, c);
-            if (c >= 0) {
-                const unsigned base = s_cnt[warp][c];
-                pairs[base + __popc(peers & lt_mask)] = code;
+        // placement in candidate order: a cell's list ascends in candidate
+        // index (one step's cells are distinct; the warp barrier orders steps)
+        for (int i = i0; i < i1; ++i) {
+            const unsigned pk = s_anc[i];
+#pragma unroll
+            for (int q = 0; q < kSub; ++q) {
+                const int c = cell_of(pk, q);
+                if (c >= 0) pairs[atomicAdd(&s_cnt[warp][c], 1u)] = (unsigned)i | (kcode[q] << 16);
             }
-            __syncwarp();
-            if (c >= 0 && (peers & lt_mask) == 0) s_cnt[warp][c] += __popc(peers);
             __syncwarp();
         }
         __syncthreads();
