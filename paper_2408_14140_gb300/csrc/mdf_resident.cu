@@ -171,7 +171,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_mdf_resident(ResidentArgs<T> a) {
             while (chunk_begin(o, nt, C) > k) --o;
             s_map[lt] = (o << 4) | (k - chunk_begin(o, nt, C));
         }
-        cl.sync();  // every CTA's capacity verdict is set
+        cl.sync();  // every CTA's capacity decision is set
         bool fast = true;
         for (int q = 0; q < C; ++q) fast = fast && *cl.map_shared_rank(&s_fits, q);
 
