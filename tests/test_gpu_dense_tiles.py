@@ -46,7 +46,7 @@ def nerr(g, o):
 def test_case_has_large_tiles():
     c = dense_case()
     X = c.R + c.Xr[0]
-    first = np.floor(X / c.h - 0.5).astype(int) - 1  # first stencil cell (three-point kernel)
+    first = np.floor(X / c.h).astype(int) - 1  # first stencil cell: round(X/h - 1/2) - 1
     touches = np.all((first + 2 >= 8) & (first <= 15), axis=1)  # grid tile (1, 1, 1)
     assert touches.sum() > 256
 
