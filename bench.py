@@ -163,8 +163,12 @@ class ClockSampler:
         self.index = index
         self.proc = None
         self.lines = []
+        self.skip = 0
 
     def start(self):
+        """Starts sampling and returns once the first sample is in (at most
+        3 s), so that the timed region that follows is sampled from its
+        start; samples taken before start() returns are left out."""
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
@@ -174,6 +178,12 @@ class ClockSampler:
             self.th.start()
         except Exception:
             self.proc = None
+            return
+        for _ in range(60):
+            if self.lines or self.proc.poll() is not None:
+                break
+            time.sleep(0.05)
+        self.skip = len(self.lines)
 
     def _read(self):
         for line in self.proc.stdout:
@@ -189,7 +199,7 @@ class ClockSampler:
             self.proc.kill()
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        for ln in self.lines[self.skip:]:
             f = [x.strip() for x in ln.split(",")]
             if len(f) < 9:
                 continue

@@ -1,5 +1,6 @@
 """Host-side logic of bench.py: replica timing over ranks (gloo, two CPU
-processes), the whole-job value, and the workload bookkeeping."""
+processes), the whole-job value, the workload bookkeeping, and the clock
+sampler (against a stand-in nvidia-smi)."""
 import os
 import socket
 import sys
@@ -57,3 +58,38 @@ def test_workload_bookkeeping():
     assert sum(m for _, m in lb) == case.M
     assert sum(b for b, _ in lb) >= bench.band_cells(case)
     assert bench.launches_per_step(5, 5) == 77
+
+
+def _fake_smi(tmp_path, reasons):
+    """A stand-in nvidia-smi printing one CSV sample every 20 ms."""
+    f = tmp_path / "nvidia-smi"
+    f.write_text("#!/bin/sh\nwhile true; do echo \"0, 1980, 2070, 900.0, x, %s\"; sleep 0.02; done\n"
+                 % ", ".join(reasons))
+    f.chmod(0o755)
+    return str(tmp_path)
+
+
+def test_clock_sampler_reads_samples_and_reasons(tmp_path, monkeypatch):
+    sys.path.insert(0, ROOT)
+    import time
+
+    import bench
+    d = _fake_smi(tmp_path, ["Not Active", "Active", "Not Active", "Active"])
+    monkeypatch.setenv("PATH", d + os.pathsep + os.environ["PATH"])
+    c = bench.ClockSampler(0)
+    c.start()
+    assert c.skip >= 1  # returned after the first sample, which is left out
+    time.sleep(0.2)
+    out = c.stop()
+    assert out["sm_mhz"] == 1980.0 and out["sm_max_mhz"] == 2070.0
+    assert out["reasons"] == ["hw_thermal_slowdown", "sw_power_cap"]
+    assert out["samples"] >= 3
+
+
+def test_clock_sampler_without_nvidia_smi(tmp_path, monkeypatch):
+    sys.path.insert(0, ROOT)
+    import bench
+    monkeypatch.setenv("PATH", str(tmp_path))
+    c = bench.ClockSampler(0)
+    c.start()
+    assert c.stop() == {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
