@@ -408,6 +408,25 @@ def test_force_torque_hand_values():
     assert np.array_equal(Tib[1], [0, 0, 0])
 
 
+def test_force_torque_reference_shift_and_segments():
+    """Moving the torque's reference point by c changes T_ib by c x F_ib
+    (T' = -rho_f sum (R + c) x F dV = T_ib + c x F_ib), particle by particle;
+    the particles' forces add up to -rho_f sum F dV over all markers."""
+    rng = np.random.default_rng(12)
+    moff = [0, 7, 7, 20]  # the middle particle has no markers
+    M = moff[-1]
+    R, F = rng.normal(size=(M, 3)), rng.normal(size=(M, 3))
+    dV = rng.uniform(0.5, 2.0, M)
+    c = np.array([[0.3, -1.2, 2.0], [5.0, 5.0, 5.0], [-0.7, 0.4, 0.9]])
+    shift = np.repeat(c, np.diff(moff), axis=0)
+    Fib, Tib = oracle.force_torque(moff, R, dV, F, 0.8)
+    Fs, Ts = oracle.force_torque(moff, R + shift, dV, F, 0.8)
+    np.testing.assert_allclose(Fs, Fib, rtol=0, atol=1e-14)
+    np.testing.assert_allclose(Ts, Tib + np.cross(c, Fib), rtol=1e-13, atol=1e-13)
+    assert np.array_equal(Fib[1], [0, 0, 0]) and np.array_equal(Tib[1], [0, 0, 0])
+    np.testing.assert_allclose(Fib.sum(axis=0), -0.8 * (F * dV[:, None]).sum(axis=0), rtol=1e-13)
+
+
 # -------------------------------------------------- collision + Newton-Euler
 PHYS0 = (1.0, 0.0, 0.0, -9.81, 9.81, 1e-4, 0.02)
 
