@@ -187,6 +187,17 @@ GBIB_API int ib_ctx_set_volume_split(ib_ctx *ctx, int ctas_per_particle);
  * wait becomes a graph dependency).  The context does not own the event.    */
 GBIB_API int ib_ctx_set_field_wait(ib_ctx *ctx, void *event);
 
+/* ---- self-test of the failure path (no paper counterpart) ----------------
+ * Enqueues on `stream` a one-thread kernel that waits on a device word that
+ * nothing ever sets and gives up after `cycles` SM clock cycles, raising
+ * IB_ERR_TIMEOUT in the context's device status the way every bounded wait
+ * of the library does.  The next ib_ctx_status(ctx, stream) returns
+ * IB_ERR_TIMEOUT and clears the status; the context stays usable.  Nothing
+ * faults and nothing hangs: the wait ends after `cycles` (1e6 cycles is about
+ * half a millisecond at 2 GHz).  IB_ERR_INVALID for a NULL ctx or `cycles`
+ * outside [1, 4e9]; IB_ERR_CUDA if the launch fails.                        */
+GBIB_API int ib_selftest_wait_timeout(ib_ctx *ctx, long long cycles, void *stream);
+
 /* ---- velocity interpolation J: Eq. (u), Eq. (vi), Algorithm 1 -----------
  * U[l] = sum_ijk u(x_ijk) delta_h(x_ijk - X[l]) h^3 for l < M, where
  * delta_h(x) = h^-3 prod_a phi(x_a / h) (Sec. 2).  X[M][3] are absolute

@@ -44,7 +44,7 @@ PHASES = {"mdf_prep": 0, "mdf_passes": 1, "spread": 2, "interp": 3, "volume": 4,
 EXPORTS = ["ib_ctx_create", "ib_ctx_reserve", "ib_ctx_destroy", "ib_ctx_status",
            "ib_last_error", "ib_workspace_needed", "ib_ctx_sm_count",
            "ib_ctx_set_timing", "ib_ctx_read_timing", "ib_ctx_set_pass_kernels", "ib_ctx_set_volume_split",
-           "ib_ctx_set_field_wait",
+           "ib_ctx_set_field_wait", "ib_selftest_wait_timeout",
            "ib_interpolate", "ib_spread", "ib_multidirect_forcing",
            "particle_volume_integrals", "particle_force_torque",
            "particle_collide_update", "particle_volume_integrals_static",
@@ -109,6 +109,7 @@ def load(path: str = LIB_PATH):
         "ib_ctx_set_pass_kernels": (i, [p, i]),
         "ib_ctx_set_volume_split": (i, [p, i]),
         "ib_ctx_set_field_wait": (i, [p, p]),
+        "ib_selftest_wait_timeout": (i, [p, ctypes.c_longlong, p]),
         "ib_interpolate": (i, [p, p, p, i, p, i, p, p]),
         "ib_spread": (i, [p, p, i, p, p, p, i, p, p]),
         "ib_multidirect_forcing": (i, [p, p, p, p, p, i, d, i, i, p, p, p]),
@@ -230,6 +231,11 @@ class Context:
         self._field_wait = event
         handle = None if event is None else ctypes.c_void_p(event.cuda_event)
         self._check(self.lib.ib_ctx_set_field_wait(self.handle, handle))
+
+    def selftest_wait_timeout(self, cycles: int = 1_000_000, stream=None):
+        """Enqueue a bounded wait that runs out (a device word nothing sets):
+        the next :meth:`status` raises IB_ERR_TIMEOUT and clears it."""
+        self._check(self.lib.ib_selftest_wait_timeout(self.handle, int(cycles), _stream(stream)))
 
     def set_volume_split(self, ctas_per_particle: int):
         """CTAs per particle of the volume integrals, 0 = automatic (see gbib.h)."""

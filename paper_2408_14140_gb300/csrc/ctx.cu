@@ -171,6 +171,23 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *t
     return r;
 }
 
+// A device word that nothing ever writes, and a bounded wait on it: the
+// self-test of the failure path (ib_selftest_wait_timeout).  The wait has
+// the shape of the library's others: poll, give up after a clock64 budget,
+// raise IB_ERR_TIMEOUT in the context's status latch, return.
+__device__ unsigned int g_never_set = 0u;
+
+__global__ void k_selftest_wait(long long cycles, DevStatus *st) {
+    if (threadIdx.x != 0) return;
+    const long long t0 = clock64();
+    while (*(volatile unsigned int *)&g_never_set == 0u) {
+        if (clock64() - t0 > cycles) {
+            raise_status(st, IB_ERR_TIMEOUT, -1);
+            return;
+        }
+    }
+}
+
 // (the scan kernels are launched as programmatic dependents: they wait for
 // their predecessor before touching memory)
 __global__ void k_scan_totals(const uint32_t *in, int n, uint32_t *totals) {
@@ -372,6 +389,14 @@ int ib_ctx_set_field_wait(ib_ctx *c, void *event) {
     if (!c) return set_error(IB_ERR_INVALID, "ctx is NULL");
     c->field_wait = event;
     return IB_OK;
+}
+
+int ib_selftest_wait_timeout(ib_ctx *c, long long cycles, void *stream) {
+    if (!c) return set_error(IB_ERR_INVALID, "ctx is NULL");
+    if (cycles < 1 || cycles > 4000000000LL)
+        return set_error(IB_ERR_INVALID, "self-test wait of %lld cycles outside [1, 4e9]", cycles);
+    k_selftest_wait<<<1, 32, 0, (cudaStream_t)stream>>>(cycles, c->status);
+    return check_launch("self-test wait");
 }
 
 int ib_ctx_set_volume_split(ib_ctx *c, int ctas_per_particle) {
