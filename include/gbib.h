@@ -256,7 +256,7 @@ GBIB_API int particle_volume_integrals_ellipsoid(ib_ctx *ctx, const ib_grid *gri
                                                  double *Iu, double *Irxu, double *vol,
                                                  void *stream);
 
-/* ---- drag diagnostic: Sec. 4.2, Eq. (FD) ----------------------------------
+/* ---- drag diagnostic: Sec. 4.3 (flow past a fixed sphere), Eq. (FD) -------
  * F_D[P][3] = -rho_f sum_l F_l dV_l + rho_f d/dt int_Vp u dV, with the first
  * term given as F_ib (particle_force_torque) and the time derivative as
  * (Iu_new - Iu_old) / dt of the PVF integrals.  FP64, overwritten.          */
@@ -317,8 +317,10 @@ GBIB_API int ib_batch_collide_update(ib_ctx *ctx, int ncases, const ib_case *cas
  * being captured (where cudaMalloc is not allowed), latency-critical loops
  * that must not take cudaMalloc's implicit device synchronisation, and hosts
  * whose device memory is all owned by another allocator.  It computes the
- * same Iu, Irxu, vol as particle_volume_integrals (same kernel, same
- * summation order) but takes no context: its per-particle partial sums live
+ * same Iu, Irxu, vol as particle_volume_integrals with the same kernel, its
+ * slab split fixed at 8 CTAs per particle: the sums agree with a context call
+ * to rounding, and bitwise with one whose ib_ctx_set_volume_split is 8.  It
+ * takes no context: its per-particle partial sums live
  * in a fixed array inside the library, sized for IB_STATIC_VOLUME_MAX_P
  * particles (896 KiB of device memory, held on every device that loads the
  * library until the process exits).

@@ -141,7 +141,7 @@ def test_full_step_dense_cluster_384(api):
     assert nerr(I0[0], a0[0]) <= 1e-12 and nerr(I0[1], a0[1]) <= 1e-12 and nerr(I0[2], a0[2]) <= 1e-12
     assert nerr(I1[0], a1[0]) <= 2e-5 and nerr(I1[2], a1[2]) <= 1e-12
     assert nerr(Fib, fo) <= 2e-5 and nerr(Tib, to) <= 2e-5
-    assert nerr(Fc, Fco) <= 1e-9
+    assert nerr(Fc, Fco) <= 1e-12
     # X^{n+1} = X^n + dt/2 (U^{n+1} + U^n): an FP32-level error in U^{n+1} moves
     # X by at most dt/2 times that error
     tol_x = 2e-5 * 0.5 * case.dt * np.max(np.abs(U)) / np.max(np.abs(X)) + 1e-14

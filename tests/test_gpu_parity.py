@@ -90,8 +90,12 @@ def test_spread(api, ctx, prec, kernel):
                   torch.tensor(dV, device="cuda"), h, org, kernel)
     ctx.status()
     assert nerr(fg, ref) <= TOL[prec]
-    # the spread part alone, against its own scale
-    assert nerr(fg.double().cpu().numpy() - f0in, ref - f0in) <= TOL[prec] * 4
+    # the spread part alone, against its own scale: f is stored in the grid
+    # precision, so the difference carries the result's error (bounded by the
+    # gate times max|f|), rescaled from max|f| to max|spread part|
+    part = ref - f0in
+    tol_part = TOL[prec] * np.max(np.abs(ref)) / np.max(np.abs(part))
+    assert nerr(fg.double().cpu().numpy() - f0in, part) <= tol_part
 
 
 def test_spread_deterministic(api, ctx):
@@ -130,7 +134,7 @@ def test_mdf_single_sphere(api, ctx, prec):
                                     case.dt, want_f=True)
     assert nerr(u, un) <= TOL[prec]
     assert nerr(F, Fo) <= TOL[prec]
-    assert nerr(f, fo) <= TOL[prec] * 10
+    assert nerr(f, fo) <= TOL[prec]
 
 
 @pytest.mark.parametrize("prec", [0, 1])
@@ -145,7 +149,7 @@ def test_mdf_cluster(api, ctx, prec, kernel, order):
                                     case.dt, kernel, order, want_f=True)
     assert nerr(u, un) <= TOL[prec]
     assert nerr(F, Fo) <= TOL[prec]
-    assert nerr(f, fo) <= TOL[prec] * 10
+    assert nerr(f, fo) <= TOL[prec]
 
 
 def test_mdf_particle_across_seam(api, ctx):

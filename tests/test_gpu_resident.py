@@ -95,5 +95,5 @@ def test_resident_equals_wavefront_and_oracle(api, form, name, prec, kernel):
     u, F, f = ref
     assert nerr(u, un) <= TOL[prec]
     assert nerr(F, Fo) <= TOL[prec]
-    assert nerr(f, fo) <= TOL[prec] * 10
+    assert nerr(f, fo) <= TOL[prec]
     ctx.close()

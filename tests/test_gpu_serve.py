@@ -66,7 +66,7 @@ def test_served_request_matches_oracle_steps(served):
             a1 = oracle.volume_integrals(c.n, c.h, c.org, un, X, c.radius)
             X, U, W, _ = oracle.collide_update(X, U, W, c.radius, c.rho_p, c.n, c.h, phys, cfg.dt, fo, to,
                                                a1[0], a0[0], a1[1], a0[1])
-        tol = 1e-10 if prec == api.IB_F64 else 2e-5
+        tol = 1e-12 if prec == api.IB_F64 else 2e-5
         for k, o in (("Ur", U), ("Wr", W)):
             g = r.host[k].numpy()
             assert np.max(np.abs(g - o)) / np.max(np.abs(o)) <= tol, (prec, k)

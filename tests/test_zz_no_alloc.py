@@ -60,6 +60,16 @@ def test_static_matches_context_version_twice(api, prec):
         torch.cuda.synchronize()
         for a, b in zip(out, ref):
             assert nerr(a, b) <= 1e-12
+        # the static call's slab split is fixed at 8 CTAs per particle: a
+        # context call with the same split runs the same sums bit for bit
+        ctx.set_volume_split(8)
+        ref8 = ctx.particle_volume_integrals(u, case.h, parts)
+        ctx.set_volume_split(0)
+        out8 = tuple(torch.full_like(t, float("nan")) for t in ref)
+        assert static_call(api, u, case.h, parts, out8) == api.IB_OK
+        torch.cuda.synchronize()
+        for a, b in zip(out8, ref8):
+            assert torch.equal(a, b)
     ctx.close()
 
 
