@@ -158,7 +158,9 @@ GBIB_API int ib_ctx_read_timing(ib_ctx *ctx, int phase, double *ms_total,
  *   runs all Ns passes of one particle (barriers over the group's CTAs only),
  *   and particles start as soon as the earlier particles they conflict with
  *   are done.
- * The simultaneous order always runs the wavefront form (one wavefront).
+ * The simultaneous order always runs the wavefront form (one wavefront),
+ * and so do FP64 fields, whose pass sums run in double-float arithmetic on
+ * the FP32 pipes (RESIDENT and GROUPS serve FP32 fields).
  * Returns IB_ERR_INVALID for any other value.                             */
 #define IB_PASSES_AUTO 0
 #define IB_PASSES_WAVEFRONT 1

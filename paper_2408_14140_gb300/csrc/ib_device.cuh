@@ -3,9 +3,47 @@
 // one marker's interpolation and one cell's deterministic gather.
 #pragma once
 
+#include "df.cuh"
 #include "gbib_internal.cuh"
 
 namespace gbib {
+
+// Storage of the per-marker kernel weights and spread sources of a pass:
+// the field type for FP32 fields; a double-float pair (hi, lo) for FP64
+// fields, whose pass sums run on the FP32 pipes (df.cuh).  Both are the size
+// of the field type.
+template <typename T> struct PassStore { using type = T; };
+template <> struct PassStore<double> { using type = float2; };
+template <typename T> using PS = typename PassStore<T>::type;
+
+__device__ __forceinline__ float to_store(float v) { return v; }
+__device__ __forceinline__ float2 to_store(double v) { return df_split(v); }
+
+// Product of a pair's three axis weights (w[0..3] x, w[4..7] y, w[8..11] z).
+__device__ __forceinline__ float pair_weight(const float *w, int ox, int oy, int oz) {
+    return w[ox] * w[4 + oy] * w[8 + oz];
+}
+__device__ __forceinline__ float2 pair_weight(const float2 *w, int ox, int oy, int oz) {
+    return df_mul(df_mul(w[ox], w[4 + oy]), w[8 + oz]);
+}
+
+__device__ __forceinline__ float pair_weight3(float wx, float wy, float wz) { return wx * wy * wz; }
+__device__ __forceinline__ float2 pair_weight3(float2 wx, float2 wy, float2 wz) {
+    return df_mul(df_mul(wx, wy), wz);
+}
+
+// Running sum of weight x source products of one cell or marker component.
+template <typename T> struct SumAcc;
+template <> struct SumAcc<float> {
+    float v = 0.0f;
+    __device__ __forceinline__ void add(float w, float a) { v += w * a; }
+    __device__ __forceinline__ float value() const { return v; }
+};
+template <> struct SumAcc<double> {
+    DFAcc v;
+    __device__ __forceinline__ void add(float2 w, float2 a) { v.add_prod(w, a); }
+    __device__ __forceinline__ double value() const { return v.value(); }
+};
 
 constexpr int kBlock = 512;          // threads per CTA (one per tile cell)
 constexpr int kLocalTiles = 8;       // local tiles per axis of a particle box
@@ -34,8 +72,8 @@ constexpr int kBins = kRows * kBinsPerRow + 1;
 template <typename T>
 struct MarkerState {
     uint64_t *anchor;  // [M] wrapped first stencil cell
-    T *wts;            // [M][12] per-axis weights (x 0..3, y 4..7, z 8..11)
-    T *A;              // [M][4] spread source of the current pass
+    PS<T> *wts;        // [M][12] per-axis weights (x 0..3, y 4..7, z 8..11)
+    PS<T> *A;          // [M][4] spread source of the current pass
     double *Ud;        // [M][3] desired velocity
     // FP32 fields only: [M][8] the desired velocity as float pairs, hi
     // (0..2) + lo (4..6), and dV / h^3 (3)
@@ -45,7 +83,8 @@ struct MarkerState {
 // One marker's update in one pass of Algorithm 1, given its interpolated
 // velocity U: with the velocity error e = U^d - U, the force F += e / dt
 // and the spread source A = e dV / h^3 (the field correction is S A).
-// FP64 fields: all in FP64.  FP32 fields: U^d is held as an unevaluated float
+// FP64 fields: all in FP64, the source stored as a float pair.  FP32 fields:
+// U^d is held as an unevaluated float
 // pair hi + lo and e = (hi - U) + lo is formed in FP32, which is within a unit
 // roundoff of e (the precision of the interpolated U itself); only the force
 // sum stays in FP64.  GB300 runs FP64 at a small fraction of its FP32 rate,
@@ -76,7 +115,7 @@ struct PassMarker {
     __device__ __forceinline__ static double force(double F, T e, double inv_dt) {
         return fma((double)e, inv_dt, F);
     }
-    __device__ __forceinline__ T source(T e) const { return e * q; }
+    __device__ __forceinline__ PS<T> source(T e) const { return to_store(e * q); }
 };
 
 // Slot (spreading tile) records.
@@ -124,11 +163,13 @@ __device__ __forceinline__ T ld(const T *p) {
 }
 
 // ALL: every tap's loads issued at once (the z loop unrolled too); the sums
-// are the same, in the same order.
+// are the same, in the same order.  FP64 fields: every tap value is split
+// into a float pair and the products and their sum run in double-float
+// arithmetic (df.cuh), in the same tap order (z, y, x).
 template <typename T, int KW, bool COH = false, bool ALL = false>
 __device__ __forceinline__ void interp_marker(const T *__restrict__ u, const DevGrid &g,
                                               long long N, uint64_t anc,
-                                              const T *__restrict__ w, T out[3]) {
+                                              const PS<T> *__restrict__ w, T out[3]) {
     int ix[KW], iy[KW], iz[KW];
     int ax = anchor_x(anc), ay = anchor_y(anc), az = anchor_z(anc);
 #pragma unroll
@@ -137,32 +178,63 @@ __device__ __forceinline__ void interp_marker(const T *__restrict__ u, const Dev
         iy[k] = wrap_add(ay, k, g.n[1]);
         iz[k] = wrap_add(az, k, g.n[2]);
     }
-    T a0 = 0, a1 = 0, a2 = 0;
-    auto plane = [&](int kz) {
+    if constexpr (sizeof(T) == 8) {
+        SumAcc<double> a0, a1, a2;
+        auto plane = [&](int kz) {
 #pragma unroll
-        for (int ky = 0; ky < KW; ++ky) {
-            long long row = ((long long)iz[kz] * g.n[1] + iy[ky]) * g.n[0];
-            T wyz = w[8 + kz] * w[4 + ky];
+            for (int ky = 0; ky < KW; ++ky) {
+                long long row = ((long long)iz[kz] * g.n[1] + iy[ky]) * g.n[0];
+                const float2 wyz = df_mul(w[8 + kz], w[4 + ky]);
+                double v[KW][3];
 #pragma unroll
-            for (int kx = 0; kx < KW; ++kx) {
-                long long c = row + ix[kx];
-                T wt = wyz * w[kx];
-                a0 += wt * ld<COH>(u + c);
-                a1 += wt * ld<COH>(u + N + c);
-                a2 += wt * ld<COH>(u + 2 * N + c);
+                for (int kx = 0; kx < KW; ++kx) {
+                    long long c = row + ix[kx];
+                    v[kx][0] = ld<COH>(u + c);
+                    v[kx][1] = ld<COH>(u + N + c);
+                    v[kx][2] = ld<COH>(u + 2 * N + c);
+                }
+#pragma unroll
+                for (int kx = 0; kx < KW; ++kx) {
+                    const float2 wt = df_mul(wyz, w[kx]);
+                    a0.add(wt, df_split(v[kx][0]));
+                    a1.add(wt, df_split(v[kx][1]));
+                    a2.add(wt, df_split(v[kx][2]));
+                }
             }
-        }
-    };
-    if (ALL) {
-#pragma unroll
-        for (int kz = 0; kz < KW; ++kz) plane(kz);
-    } else {
+        };
 #pragma unroll 1
         for (int kz = 0; kz < KW; ++kz) plane(kz);
+        out[0] = a0.value();
+        out[1] = a1.value();
+        out[2] = a2.value();
+    } else {
+        T a0 = 0, a1 = 0, a2 = 0;
+        auto plane = [&](int kz) {
+#pragma unroll
+            for (int ky = 0; ky < KW; ++ky) {
+                long long row = ((long long)iz[kz] * g.n[1] + iy[ky]) * g.n[0];
+                T wyz = w[8 + kz] * w[4 + ky];
+#pragma unroll
+                for (int kx = 0; kx < KW; ++kx) {
+                    long long c = row + ix[kx];
+                    T wt = wyz * w[kx];
+                    a0 += wt * ld<COH>(u + c);
+                    a1 += wt * ld<COH>(u + N + c);
+                    a2 += wt * ld<COH>(u + 2 * N + c);
+                }
+            }
+        };
+        if (ALL) {
+#pragma unroll
+            for (int kz = 0; kz < KW; ++kz) plane(kz);
+        } else {
+#pragma unroll 1
+            for (int kz = 0; kz < KW; ++kz) plane(kz);
+        }
+        out[0] = a0;
+        out[1] = a1;
+        out[2] = a2;
     }
-    out[0] = a0;
-    out[1] = a1;
-    out[2] = a2;
 }
 
 template <typename T, int KW, bool STAGED, bool COH>
@@ -228,8 +300,9 @@ constexpr size_t tile_stage_bytes() {
 // this kernel (plain loads after an acquire) rather than by an earlier one.
 // Ends with a CTA barrier.
 template <typename T, int KW, bool COH>
-__device__ __forceinline__ void gather_tile_lists(const CaseTab &ct, int cs, const Slots &sl, const T *wts,
-                                                  const T *A_src, double inv_dt, T *sw, T *sA) {
+__device__ __forceinline__ void gather_tile_lists(const CaseTab &ct, int cs, const Slots &sl, const PS<T> *wts,
+                                                  const PS<T> *A_src, double inv_dt, PS<T> *sw, PS<T> *sA) {
+    using S = PS<T>;
     const DevCase cd = ct.get(sl.geo_case[cs]);
     const DevGrid &g = cd.g;
     const long long N = (long long)g.n[0] * g.n[1] * g.n[2];
@@ -272,7 +345,7 @@ __device__ __forceinline__ void gather_tile_lists(const CaseTab &ct, int cs, con
         const uint32_t m0 = threadIdx.x < nc ? cand[threadIdx.x] : 0u;
         for (int i = threadIdx.x; i < nc; i += blockDim.x) {
             const uint32_t m = i == (int)threadIdx.x ? m0 : cand[i];
-            const T *wm = wts + 12 * (size_t)m;
+            const S *wm = wts + 12 * (size_t)m;
 #pragma unroll
             for (int q = 0; q < 3; ++q)
 #pragma unroll
@@ -290,7 +363,7 @@ __device__ __forceinline__ void gather_tile_lists(const CaseTab &ct, int cs, con
         const int2 e = first ? e0 : band[q];
         const int cnt = e.x >> 16;
         const uint32_t *pr = pairs + e.y;
-        T acc0 = 0, acc1 = 0, acc2 = 0;
+        SumAcc<T> acc0, acc1, acc2;
         for (int k0 = 0; k0 < cnt; k0 += kPB) {
             uint32_t pk[kPB];
 #pragma unroll
@@ -301,33 +374,34 @@ __device__ __forceinline__ void gather_tile_lists(const CaseTab &ct, int cs, con
                 if (k0 + j >= cnt) break;
                 const int i = pk[j] & 0xffff, ox = (pk[j] >> 16) & 3, oy = (pk[j] >> 18) & 3,
                           oz = (pk[j] >> 20) & 3;
-                T wt, a0, a1, a2;
+                S wt, a0, a1, a2;
                 if (staged) {
-                    const T *w = sw + 12 * i;
-                    const T *Ai = sA + 4 * i;
-                    wt = w[ox] * w[4 + oy] * w[8 + oz];
+                    const S *w = sw + 12 * i;
+                    const S *Ai = sA + 4 * i;
+                    wt = pair_weight(w, ox, oy, oz);
                     a0 = Ai[0], a1 = Ai[1], a2 = Ai[2];
                 } else {
                     const size_t m = cand[i];
-                    const T *w = wts + 12 * m;
-                    const T *Ai = A_src + 4 * m;
-                    wt = __ldg(w + ox) * __ldg(w + 4 + oy) * __ldg(w + 8 + oz);
+                    const S *w = wts + 12 * m;
+                    const S *Ai = A_src + 4 * m;
+                    wt = pair_weight3(__ldg(w + ox), __ldg(w + 4 + oy), __ldg(w + 8 + oz));
                     a0 = ld<COH>(Ai), a1 = ld<COH>(Ai + 1), a2 = ld<COH>(Ai + 2);
                 }
-                acc0 += wt * a0;
-                acc1 += wt * a1;
-                acc2 += wt * a2;
+                acc0.add(wt, a0);
+                acc1.add(wt, a1);
+                acc2.add(wt, a2);
             }
         }
         const long long c = first ? c0 : cell_index(e.x & 0xffff);
         const T u0 = first ? v0[0] : u[c], u1 = first ? v0[1] : u[N + c], u2 = first ? v0[2] : u[2 * N + c];
-        u[c] = u0 + acc0;
-        u[N + c] = u1 + acc1;
-        u[2 * N + c] = u2 + acc2;
+        const T s0 = acc0.value(), s1 = acc1.value(), s2 = acc2.value();
+        u[c] = u0 + s0;
+        u[N + c] = u1 + s1;
+        u[2 * N + c] = u2 + s2;
         if (f_out) {
-            f_out[c] += (T)(acc0 * inv_dt);
-            f_out[N + c] += (T)(acc1 * inv_dt);
-            f_out[2 * N + c] += (T)(acc2 * inv_dt);
+            f_out[c] += (T)(s0 * inv_dt);
+            f_out[N + c] += (T)(s1 * inv_dt);
+            f_out[2 * N + c] += (T)(s2 * inv_dt);
         }
     }
     __syncthreads();

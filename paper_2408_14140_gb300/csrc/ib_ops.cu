@@ -59,8 +59,11 @@ __global__ void __launch_bounds__(256) k_interpolate(DevGrid g, const T *__restr
         T w[12];
         long long first[3];
         uint64_t anc = marker_weights<T, KER>(g, x, w, first);
+        PS<T> ws[12];
+#pragma unroll
+        for (int k = 0; k < 12; ++k) ws[k] = to_store(w[k]);
         T o[3];
-        interp_marker<T, KW>(u, g, N, anc, w, o);
+        interp_marker<T, KW>(u, g, N, anc, ws, o);
         U[3 * l] = (double)o[0];
         U[3 * l + 1] = (double)o[1];
         U[3 * l + 2] = (double)o[2];
@@ -92,12 +95,12 @@ __global__ void k_prep_spread(DevGrid g, int M, const double *__restrict__ X,
         long long first[3];
         ms.anchor[l] = marker_weights<T, KER>(g, x, w, first);
 #pragma unroll
-        for (int k = 0; k < 12; ++k) ms.wts[12 * l + k] = w[k];
+        for (int k = 0; k < 12; ++k) ms.wts[12 * l + k] = to_store(w[k]);
         double q = dv * g.inv_h3;
-        ms.A[4 * l + 0] = (T)(f[0] * q);
-        ms.A[4 * l + 1] = (T)(f[1] * q);
-        ms.A[4 * l + 2] = (T)(f[2] * q);
-        ms.A[4 * l + 3] = T(0);
+        ms.A[4 * l + 0] = to_store((T)(f[0] * q));
+        ms.A[4 * l + 1] = to_store((T)(f[1] * q));
+        ms.A[4 * l + 2] = to_store((T)(f[2] * q));
+        ms.A[4 * l + 3] = to_store(T(0));
     }
 }
 
@@ -157,7 +160,7 @@ __global__ void __launch_bounds__(256) k_prep_particles(
         long long first[3];
         ms.anchor[l] = marker_weights<T, KER>(g, x, w, first);
 #pragma unroll
-        for (int k = 0; k < 12; ++k) ms.wts[12 * l + k] = w[k];
+        for (int k = 0; k < 12; ++k) ms.wts[12 * l + k] = to_store(w[k]);
         const double ud[3] = {uc[0] + (wc[1] * r[2] - wc[2] * r[1]), uc[1] + (wc[2] * r[0] - wc[0] * r[2]),
                               uc[2] + (wc[0] * r[1] - wc[1] * r[0])};
 #pragma unroll
@@ -1022,10 +1025,10 @@ __global__ void __launch_bounds__(kPairThreads, 5) k_tile_pairs(CaseTab ct, int 
 // holds the field spread into, its f slot is null.
 template <typename T, int KER>
 __global__ void __launch_bounds__(256) k_spread_gather(CaseTab ct, const int *__restrict__ ncompact_p, Slots sl,
-                                                       const T *__restrict__ wts, const T *__restrict__ A) {
+                                                       const PS<T> *__restrict__ wts, const PS<T> *__restrict__ A) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T *sw = (T *)smem_raw;
-    T *sA = sw + (size_t)TileStage<T>::N * 12;
+    PS<T> *sw = (PS<T> *)smem_raw;
+    PS<T> *sA = sw + (size_t)TileStage<T>::N * 12;
     const int nc = *ncompact_p;
     for (int cs = blockIdx.x; cs < nc; cs += gridDim.x)
         gather_tile_lists<T, Kernel<KER>::W, false>(ct, cs, sl, wts, A, 0.0, sw, sA);
@@ -1129,7 +1132,7 @@ __global__ void __launch_bounds__(kInterpThreads) k_interp_level(PassArgs<T> a, 
     // one marker's data but the field (loaded before the wait for the first)
     int l = 0;
     uint64_t anc = 0;
-    T w[12];
+    PS<T> w[12];
     PassMarker<T> pm;
     double F[3];
     auto load = [&]() {
@@ -1180,9 +1183,10 @@ constexpr size_t level_stage_bytes() {
 }
 
 template <typename T, int KW>
-__device__ __forceinline__ void gather_tile_level(const CaseTab &ct, int cs, const Slots &sl, const T *wts,
-                                                  const T *A_src, double inv_dt, T *sw, T *sA,
+__device__ __forceinline__ void gather_tile_level(const CaseTab &ct, int cs, const Slots &sl, const PS<T> *wts,
+                                                  const PS<T> *A_src, double inv_dt, PS<T> *sw, PS<T> *sA,
                                                   uint32_t *sp) {
+    using S = PS<T>;
     const DevCase cd = ct.get(sl.geo_case[cs]);
     const DevGrid &g = cd.g;
     const long long N = (long long)g.n[0] * g.n[1] * g.n[2];
@@ -1227,7 +1231,7 @@ __device__ __forceinline__ void gather_tile_level(const CaseTab &ct, int cs, con
     if (staged)
         for (int i = threadIdx.x; i < nc; i += blockDim.x) {
             const uint32_t m = i == (int)threadIdx.x ? m0 : cand[i];
-            const T *wm = wts + 12 * (size_t)m;
+            const S *wm = wts + 12 * (size_t)m;
 #pragma unroll
             for (int q = 0; q < 3; ++q)
 #pragma unroll
@@ -1242,9 +1246,13 @@ __device__ __forceinline__ void gather_tile_level(const CaseTab &ct, int cs, con
             for (int q = 0; q < 3; ++q) sA[4 * i + q] = A_src[4 * (size_t)m + q];
         }
     __syncthreads();
-    auto cell_sum = [&](int2 ee, T acc[3]) {
+    auto cell_sum = [&](int2 ee, T out[3]) {
         const int cnt = ee.x >> 16;
-        acc[0] = acc[1] = acc[2] = T(0);
+        SumAcc<T> acc[3];
+        auto done = [&]() {
+#pragma unroll
+            for (int q = 0; q < 3; ++q) out[q] = acc[q].value();
+        };
         if (staged && pstaged) {
             // batches of kSB pairs: every shared-memory load of a batch is
             // issued before its sums, which are added in list order
@@ -1253,46 +1261,48 @@ __device__ __forceinline__ void gather_tile_level(const CaseTab &ct, int cs, con
                 uint32_t pk[kSB];
 #pragma unroll
                 for (int j = 0; j < kSB; ++j) pk[j] = k0 + j < cnt ? sp[ee.y + k0 + j] : 0u;
-                T wt[kSB], a[kSB][3];
+                S wt[kSB], a[kSB][3];
 #pragma unroll
                 for (int j = 0; j < kSB; ++j) {
                     const int i = pk[j] & 0xffff, ox = (pk[j] >> 16) & 3, oy = (pk[j] >> 18) & 3,
                               oz = (pk[j] >> 20) & 3;
-                    const T *w = sw + 12 * i;
-                    const T *Ai = sA + 4 * i;
-                    wt[j] = w[ox] * w[4 + oy] * w[8 + oz];
+                    const S *w = sw + 12 * i;
+                    const S *Ai = sA + 4 * i;
+                    wt[j] = pair_weight(w, ox, oy, oz);
                     a[j][0] = Ai[0], a[j][1] = Ai[1], a[j][2] = Ai[2];
                 }
 #pragma unroll
                 for (int j = 0; j < kSB; ++j)
                     if (k0 + j < cnt) {
-                        acc[0] += wt[j] * a[j][0];
-                        acc[1] += wt[j] * a[j][1];
-                        acc[2] += wt[j] * a[j][2];
+                        acc[0].add(wt[j], a[j][0]);
+                        acc[1].add(wt[j], a[j][1]);
+                        acc[2].add(wt[j], a[j][2]);
                     }
             }
+            done();
             return;
         }
         for (int k = 0; k < cnt; ++k) {
             const uint32_t pk = pstaged ? sp[ee.y + k] : __ldg(pairs + ee.y + k);
             const int i = pk & 0xffff, ox = (pk >> 16) & 3, oy = (pk >> 18) & 3, oz = (pk >> 20) & 3;
-            T wt, a0, a1, a2;
+            S wt, a0, a1, a2;
             if (staged) {
-                const T *w = sw + 12 * i;
-                const T *Ai = sA + 4 * i;
-                wt = w[ox] * w[4 + oy] * w[8 + oz];
+                const S *w = sw + 12 * i;
+                const S *Ai = sA + 4 * i;
+                wt = pair_weight(w, ox, oy, oz);
                 a0 = Ai[0], a1 = Ai[1], a2 = Ai[2];
             } else {
                 const size_t m = cand[i];
-                const T *w = wts + 12 * m;
-                const T *Ai = A_src + 4 * m;
-                wt = __ldg(w + ox) * __ldg(w + 4 + oy) * __ldg(w + 8 + oz);
+                const S *w = wts + 12 * m;
+                const S *Ai = A_src + 4 * m;
+                wt = pair_weight3(__ldg(w + ox), __ldg(w + 4 + oy), __ldg(w + 8 + oz));
                 a0 = Ai[0], a1 = Ai[1], a2 = Ai[2];
             }
-            acc[0] += wt * a0;
-            acc[1] += wt * a1;
-            acc[2] += wt * a2;
+            acc[0].add(wt, a0);
+            acc[1].add(wt, a1);
+            acc[2].add(wt, a2);
         }
+        done();
     };
     auto update = [&](long long cc, const T vv[3], const T acc[3]) {
 #pragma unroll
@@ -1323,8 +1333,8 @@ __device__ __forceinline__ void gather_tile_level(const CaseTab &ct, int cs, con
 template <typename T, int KER>
 __global__ void __launch_bounds__(kGatherThreads, sizeof(T) == 4 ? 5 : 4) k_gather_level(PassArgs<T> a, int L) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T *sw = (T *)smem_raw;                          // [N][12]
-    T *sA = sw + (size_t)TileStage<T>::N * 12;      // [N][4]
+    PS<T> *sw = (PS<T> *)smem_raw;                      // [N][12]
+    PS<T> *sA = sw + (size_t)TileStage<T>::N * 12;      // [N][4]
     uint32_t *sp = (uint32_t *)(sA + (size_t)TileStage<T>::N * 4);  // [kLevPairs]
     const int nl = *a.nlev;
     const int s0 = L < nl ? a.lev_sbeg[L] : 0, s1 = L < nl ? a.lev_sbeg[L + 1] : 0;
@@ -1352,8 +1362,8 @@ template <typename T, int KER>
 __global__ void __launch_bounds__(256) k_mdf_passes(PassArgs<T> a) {
     constexpr int KW = Kernel<KER>::W;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T *sw = (T *)smem_raw;                      // [N][12]
-    T *sA = sw + (size_t)TileStage<T>::N * 12;  // [N][4]
+    PS<T> *sw = (PS<T> *)smem_raw;                      // [N][12]
+    PS<T> *sA = sw + (size_t)TileStage<T>::N * 12;      // [N][4]
     const int nl = *a.nlev;
     const double inv_dt = a.inv_dt;
     const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1407,8 +1417,8 @@ static int grid_blocks(long long work, int threads, int sm) {
 template <typename T>
 static bool take_markers(Arena &ar, int M, MarkerState<T> &ms) {
     ms.anchor = ar.take<uint64_t>(M > 0 ? M : 1);
-    ms.wts = ar.take<T>((size_t)12 * (M > 0 ? M : 1));
-    ms.A = ar.take<T>((size_t)4 * (M > 0 ? M : 1));
+    ms.wts = ar.take<PS<T>>((size_t)12 * (M > 0 ? M : 1));
+    ms.A = ar.take<PS<T>>((size_t)4 * (M > 0 ? M : 1));
     ms.Ud = ar.take<double>((size_t)3 * (M > 0 ? M : 1));
     ms.Ud32 = sizeof(T) == 4 ? ar.take<float>((size_t)8 * (M > 0 ? M : 1)) : nullptr;
     return ar.ok();
@@ -1577,7 +1587,10 @@ static int run_mdf(ib_ctx *ctx, Arena &ar, const CaseTab &ct, const ib_particles
     if (ndense > (1LL << 30)) return set_error(IB_ERR_UNSUPPORTED, "too many tiles");
     if (!ar.ok())
         return oom_error(ar.used, ar.cap);
-    const bool resident = order == IB_ORDER_SEQUENTIAL && ctx->pass_kernels == IB_PASSES_RESIDENT;
+    // the particle-resident and particle-group forms serve FP32 fields; FP64
+    // fields always run the wavefront form (double-float pass sums)
+    const int pass_kernels = sizeof(T) == 4 ? ctx->pass_kernels : IB_PASSES_WAVEFRONT;
+    const bool resident = order == IB_ORDER_SEQUENTIAL && pass_kernels == IB_PASSES_RESIDENT;
     Slots sl;
     SlotScratch sc;
     int rc = slots_alloc<KW>(ar, M, (int)ndense, sg.mode, sl, sc, s, true, resident);
@@ -1610,9 +1623,10 @@ static int run_mdf(ib_ctx *ctx, Arena &ar, const CaseTab &ct, const ib_particles
     int *ncompact = nullptr;
     rc = slots_build<KW>(ctx, ct, M, (int)ndense, sg, ms.anchor, lo.level, sl, sc, ncompact, s, true);
     if (rc) return rc;
+    if constexpr (sizeof(T) == 4) {
     if (order == IB_ORDER_SEQUENTIAL &&
-        (ctx->pass_kernels == IB_PASSES_RESIDENT || ctx->pass_kernels == IB_PASSES_GROUPS)) {
-        const bool groups = ctx->pass_kernels == IB_PASSES_GROUPS;
+        (pass_kernels == IB_PASSES_RESIDENT || pass_kernels == IB_PASSES_GROUPS)) {
+        const bool groups = pass_kernels == IB_PASSES_GROUPS;
         const int ngroups = groups ? mdf_groups_count<T, KER>(ctx) : 0;
         if (groups && ngroups < 1) return set_error(IB_ERR_CUDA, "group kernel: no resident group");
         unsigned int *gwords = groups ? ar.take<unsigned int>((size_t)4 * ngroups) : nullptr;
@@ -1650,6 +1664,7 @@ static int run_mdf(ib_ctx *ctx, Arena &ar, const CaseTab &ct, const ib_particles
         if (rc) return rc;
         tpass.stop();
         return check_launch("ib_multidirect_forcing");
+    }
     }
     launch_pdl(k_level_slots, dim3(1), dim3(256), 0, s, sg.mode, (const int *)lo.nlev, (const int *)lo.lev_pbeg,
                (const uint32_t *)sl.flag_scan, (int)ndense, lev_sbeg);

@@ -204,8 +204,6 @@ int launch_mdf_groups(ib_ctx *ctx, const ResidentArgs<T> &a, cudaStream_t s) {
     template int mdf_groups_count<T, K>(ib_ctx *);
 GBIB_GROUPS_INST(float, IB_DELTA_ROMA3)
 GBIB_GROUPS_INST(float, IB_DELTA_PESKIN4)
-GBIB_GROUPS_INST(double, IB_DELTA_ROMA3)
-GBIB_GROUPS_INST(double, IB_DELTA_PESKIN4)
 #undef GBIB_GROUPS_INST
 
 }  // namespace gbib

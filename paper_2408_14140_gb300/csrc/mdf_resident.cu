@@ -365,7 +365,5 @@ int launch_mdf_resident(ib_ctx *ctx, const ResidentArgs<T> &a, cudaStream_t s) {
 
 template int launch_mdf_resident<float, IB_DELTA_ROMA3>(ib_ctx *, const ResidentArgs<float> &, cudaStream_t);
 template int launch_mdf_resident<float, IB_DELTA_PESKIN4>(ib_ctx *, const ResidentArgs<float> &, cudaStream_t);
-template int launch_mdf_resident<double, IB_DELTA_ROMA3>(ib_ctx *, const ResidentArgs<double> &, cudaStream_t);
-template int launch_mdf_resident<double, IB_DELTA_PESKIN4>(ib_ctx *, const ResidentArgs<double> &, cudaStream_t);
 
 }  // namespace gbib
