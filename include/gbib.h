@@ -27,7 +27,9 @@
  *    bytes needed.  Calls on one context must not overlap on the GPU (they
  *    share its workspace): use one context per concurrent stream.
  *  * Results are deterministic: the same inputs give bitwise identical
- *    outputs run to run (fixed summation orders, no floating-point atomics).
+ *    outputs run to run (fixed summation orders, no floating-point atomics),
+ *    unless a context selects the atomic spreading form
+ *    (ib_ctx_set_spread_mode).
  */
 #ifndef GBIB_H
 #define GBIB_H
@@ -167,6 +169,23 @@ GBIB_API int ib_ctx_read_timing(ib_ctx *ctx, int phase, double *ms_total,
 #define IB_PASSES_RESIDENT 2
 #define IB_PASSES_GROUPS 3
 GBIB_API int ib_ctx_set_pass_kernels(ib_ctx *ctx, int which);
+
+/* ---- spreading form (Eq. f, Eq. fs; Algorithm 1's spreading step) ------
+ * GATHER (the default): every cell sums the contributions of the markers
+ *   whose stencils cover it in a fixed order, from per-tile marker lists
+ *   built once per call: bitwise reproducible.
+ * ATOMIC: every marker adds its KW^3 contributions to the cells with atomic
+ *   additions, combined first across the lanes of a warp that target the
+ *   same cell (one addition per distinct cell and warp).  No tile lists are
+ *   built, so a forcing call's preparation is shorter.  The sums agree with
+ *   the gather to rounding, but the order of the additions varies, so
+ *   results are not bitwise reproducible run to run.
+ * Applies to ib_spread and to every multidirect-forcing call on the context
+ * (in the sequential order with the wavefront form; the resident and group
+ * forms always gather).  IB_ERR_INVALID for any other value.                */
+#define IB_SPREAD_GATHER 0
+#define IB_SPREAD_ATOMIC 1
+GBIB_API int ib_ctx_set_spread_mode(ib_ctx *ctx, int mode);
 
 /* ---- CTAs per particle of the volume integrals (tuning knob) -----------
  * Each particle's box is cut into this many slabs of cell planes, one CTA
@@ -312,6 +331,40 @@ GBIB_API int ib_batch_collide_update(ib_ctx *ctx, int ncases, const ib_case *cas
                                      const double *Irxu_old, double *Fc_out,
                                      void *stream);
 /* (particle_force_torque works on any flat particle set, batched or not.) */
+
+/* ---- prepared batches: the case table uploaded once --------------------
+ * ib_batch_table_create validates `cases` as the ib_batch_* calls do (and
+ * phys, when given: eps_c, d_c > 0 per case) and copies the case table into
+ * device memory that the returned table owns.  It allocates (cudaMalloc) and
+ * waits for its copies, so create tables before any stream capture.  The
+ * table keeps the cases' field pointers: it serves calls on exactly those
+ * fields and particle ranges (P particles) until ib_batch_table_destroy.
+ * The ib_batch_table_* calls compute what the ib_batch_* calls of the same
+ * name compute (same kernels: bitwise equal) but upload nothing and never
+ * wait on the host, so they can be captured into a CUDA graph, provided the
+ * context's workspace already fits the call (make one call outside capture
+ * first; a capture that meets IB_ERR_OOM cannot grow it).  phys may be NULL
+ * when the table is not used for ib_batch_table_collide_update (which then
+ * returns IB_ERR_INVALID).  Errors: IB_ERR_INVALID for bad cases, a NULL
+ * table, a table of another device or a call whose P differs; IB_ERR_OOM /
+ * IB_ERR_CUDA when the device copy cannot be made.  Destroy waits for the
+ * device before freeing.                                                      */
+typedef struct ib_batch_table ib_batch_table;
+GBIB_API int ib_batch_table_create(ib_ctx *ctx, int ncases, const ib_case *cases, int P,
+                                   const ib_phys *phys, ib_batch_table **table);
+GBIB_API int ib_batch_table_destroy(ib_batch_table *table);
+GBIB_API int ib_batch_table_multidirect_forcing(ib_ctx *ctx, const ib_batch_table *table,
+                                                const ib_particles *parts, const ib_markers *marks,
+                                                int Ns, double dt, int delta, int order,
+                                                double *F_out, void *stream);
+GBIB_API int ib_batch_table_volume_integrals(ib_ctx *ctx, const ib_batch_table *table,
+                                             const ib_particles *parts, double *Iu, double *Irxu,
+                                             double *vol, void *stream);
+GBIB_API int ib_batch_table_collide_update(ib_ctx *ctx, const ib_batch_table *table,
+                                           ib_particles *parts, double dt, const double *F_ib,
+                                           const double *T_ib, const double *Iu_new,
+                                           const double *Iu_old, const double *Irxu_new,
+                                           const double *Irxu_old, double *Fc_out, void *stream);
 
 /* ---- allocation-free volume integrals ----------------------------------
  * The paper has no counterpart to this entry point; it exists for callers

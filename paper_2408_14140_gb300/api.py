@@ -38,6 +38,8 @@ SEQUENTIAL = 0
 SIMULTANEOUS = 1
 PASSES = {"auto": 0, "wavefront": 1, "resident": 2, "groups": 3}
 
+SPREAD_MODES = {"gather": 0, "atomic": 1}
+
 PHASES = {"mdf_prep": 0, "mdf_passes": 1, "spread": 2, "interp": 3, "volume": 4,
           "force": 5, "collide": 6, "mdf_interp": 7, "mdf_gather": 8}
 
@@ -49,7 +51,9 @@ EXPORTS = ["ib_ctx_create", "ib_ctx_reserve", "ib_ctx_destroy", "ib_ctx_status",
            "particle_volume_integrals", "particle_force_torque",
            "particle_collide_update", "particle_volume_integrals_static",
            "ib_batch_multidirect_forcing", "ib_batch_volume_integrals", "ib_batch_collide_update",
-           "particle_volume_integrals_ellipsoid", "particle_drag_force"]
+           "particle_volume_integrals_ellipsoid", "particle_drag_force",
+           "ib_batch_table_create", "ib_batch_table_destroy", "ib_batch_table_multidirect_forcing",
+           "ib_batch_table_volume_integrals", "ib_batch_table_collide_update", "ib_ctx_set_spread_mode"]
 
 
 class IBError(RuntimeError):
@@ -122,6 +126,12 @@ def load(path: str = LIB_PATH):
         "particle_drag_force": (i, [p, i, p, p, p, d, d, p, p]),
         "ib_batch_volume_integrals": (i, [p, i, p, p, p, p, p, p]),
         "ib_batch_collide_update": (i, [p, i, p, p, p, d, p, p, p, p, p, p, p, p]),
+        "ib_ctx_set_spread_mode": (i, [p, i]),
+        "ib_batch_table_create": (i, [p, i, p, i, p, ctypes.POINTER(p)]),
+        "ib_batch_table_destroy": (i, [p]),
+        "ib_batch_table_multidirect_forcing": (i, [p, p, p, p, i, d, i, i, p, p]),
+        "ib_batch_table_volume_integrals": (i, [p, p, p, p, p, p, p]),
+        "ib_batch_table_collide_update": (i, [p, p, p, d, p, p, p, p, p, p, p, p]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -223,6 +233,11 @@ class Context:
         "resident" or "groups" (see gbib.h; every choice gives bitwise the
         same result)."""
         self._check(self.lib.ib_ctx_set_pass_kernels(self.handle, PASSES[which]))
+
+    def set_spread_mode(self, mode: str):
+        """Spreading form: "gather" (deterministic, the default) or "atomic"
+        (warp-aggregated atomic additions; see gbib.h)."""
+        self._check(self.lib.ib_ctx_set_spread_mode(self.handle, SPREAD_MODES[mode]))
 
     def set_field_wait(self, event):
         """Make the forcing calls on this context wait for a torch.cuda.Event
@@ -492,6 +507,89 @@ class Context:
                    ph, float(dt), _ptr(F_ib), _ptr(T_ib), _ptr(Iu_new), _ptr(Iu_old),
                    _ptr(Irxu_new), _ptr(Irxu_old), _ptr(Fc_out), _stream(stream))
         return Fc_out
+
+    def ib_batch_table_multidirect_forcing(self, table, parts, marks, Ns, dt, delta=ROMA3,
+                                           order=SEQUENTIAL, F_out=None, stream=None):
+        """Algorithm 1 on every case of a prepared batch (see :class:`BatchTable`)."""
+        ps = self.particles_struct(parts["Xr"], parts["Ur"], parts["Wr"], parts["radius"],
+                                   parts["rho_p"], parts["moff"])
+        ms = self.markers_struct(marks["R"], marks["dV"])
+        if F_out is None:
+            F_out = torch.empty((ms.M, 3), dtype=torch.float64, device=parts["Xr"].device)
+        _need(F_out, "F_out", torch.float64, (ms.M, 3))
+        self._call(self.lib.ib_batch_table_multidirect_forcing, self.handle, table.handle, ctypes.byref(ps),
+                   ctypes.byref(ms), int(Ns), float(dt), int(delta), int(order), _ptr(F_out), _stream(stream))
+        return F_out
+
+    def ib_batch_table_volume_integrals(self, table, parts, out=None, stream=None):
+        """(Iu, Irxu, vol) of every particle of a prepared batch."""
+        ps = self.particles_struct(parts["Xr"], parts["Ur"], parts["Wr"], parts["radius"],
+                                   parts["rho_p"], parts["moff"])
+        P, dev = ps.P, parts["Xr"].device
+        if out is None:
+            out = (torch.empty((P, 3), dtype=torch.float64, device=dev),
+                   torch.empty((P, 3), dtype=torch.float64, device=dev),
+                   torch.empty((P,), dtype=torch.float64, device=dev))
+        Iu, Irxu, vol = out
+        _need(Iu, "Iu", torch.float64, (P, 3))
+        _need(Irxu, "Irxu", torch.float64, (P, 3))
+        _need(vol, "vol", torch.float64, (P,))
+        self._call(self.lib.ib_batch_table_volume_integrals, self.handle, table.handle, ctypes.byref(ps),
+                   _ptr(Iu), _ptr(Irxu), _ptr(vol), _stream(stream))
+        return Iu, Irxu, vol
+
+    def ib_batch_table_collide_update(self, table, parts, dt, F_ib, T_ib, Iu_new, Iu_old, Irxu_new,
+                                      Irxu_old, Fc_out=None, stream=None):
+        """Collision within each case + Newton-Euler on a prepared batch."""
+        ps = self.particles_struct(parts["Xr"], parts["Ur"], parts["Wr"], parts["radius"],
+                                   parts["rho_p"], parts["moff"])
+        P = ps.P
+        for t, nm in ((F_ib, "F_ib"), (T_ib, "T_ib"), (Iu_new, "Iu_new"), (Iu_old, "Iu_old"),
+                      (Irxu_new, "Irxu_new"), (Irxu_old, "Irxu_old")):
+            _need(t, nm, torch.float64, (P, 3))
+        if Fc_out is not None:
+            _need(Fc_out, "Fc_out", torch.float64, (P, 3))
+        self._call(self.lib.ib_batch_table_collide_update, self.handle, table.handle, ctypes.byref(ps),
+                   float(dt), _ptr(F_ib), _ptr(T_ib), _ptr(Iu_new), _ptr(Iu_old), _ptr(Irxu_new),
+                   _ptr(Irxu_old), _ptr(Fc_out), _stream(stream))
+        return Fc_out
+
+
+class BatchTable:
+    """A batch's case table uploaded once (``ib_batch_table_create``): the
+    ``ib_batch_table_*`` calls that take it stage nothing on the host, so they
+    can be captured into a CUDA graph.  It serves exactly the given fields
+    and particle ranges; ``fields`` are kept referenced while it lives.
+    ``phys`` (one tuple per case, or one for all) is needed only by the
+    collision update."""
+
+    def __init__(self, ctx, fields, hs, ranges, P, phys=None, origins=None, f_outs=None):
+        self.lib = ctx.lib
+        self._keep = (list(fields), list(f_outs) if f_outs is not None else None)
+        cases = case_array(fields, hs, ranges, origins, f_outs)
+        ph = None
+        if phys is not None:
+            per_case = phys if len(phys) == len(cases) and not isinstance(phys[0], (int, float)) else \
+                [phys] * len(cases)
+            ph = (Phys * len(cases))(*[_phys_struct(x) for x in per_case])
+        h = ctypes.c_void_p()
+        rc = self.lib.ib_batch_table_create(ctx.handle, len(cases), cases, int(P), ph, ctypes.byref(h))
+        if rc != IB_OK:
+            raise IBError(rc, self.lib.ib_last_error().decode())
+        self.handle = h
+        self.P = int(P)
+        self.ncases = len(cases)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.ib_batch_table_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def _phys_struct(phys):

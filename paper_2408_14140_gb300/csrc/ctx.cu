@@ -4,6 +4,8 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <new>
+
 #include "gbib_internal.cuh"
 
 namespace gbib {
@@ -88,12 +90,12 @@ __global__ void k_case_of_particle(const DevCase *cases, int ncases, int *pcase)
         for (int p = cases[c].p0 + threadIdx.x; p < cases[c].p1; p += blockDim.x) pcase[p] = c;
 }
 
-int build_case_table(ib_ctx *ctx, Arena &ar, int ncases, const ib_case *cases, int P, int need_prec,
-                     CaseTab &ct, cudaStream_t s, const ib_phys *phys) {
+int fill_case_table(int ncases, const ib_case *cases, int P, int need_prec, const ib_phys *phys,
+                    std::vector<DevCase> &h, unsigned long long &toff) {
     if (ncases < 1 || !cases) return set_error(IB_ERR_INVALID, "batch needs ncases >= 1 and a case array");
     int prec = cases[0].grid.prec;
-    std::vector<DevCase> h(ncases);
-    unsigned long long toff = 0;
+    h.assign(ncases, DevCase{});
+    toff = 0;
     for (int c = 0; c < ncases; ++c) {
         int rc = validate_grid(&cases[c].grid, need_prec);
         if (rc) return set_error(rc, "case %d: %s", c, ib_last_error());
@@ -108,6 +110,15 @@ int build_case_table(ib_ctx *ctx, Arena &ar, int ncases, const ib_case *cases, i
         if (toff > (1ull << 30)) return set_error(IB_ERR_UNSUPPORTED, "batch has too many grid tiles");
     }
     if (cases[ncases - 1].p_end != P) return set_error(IB_ERR_INVALID, "case ranges must end at P = %d", P);
+    return IB_OK;
+}
+
+int build_case_table(ib_ctx *ctx, Arena &ar, int ncases, const ib_case *cases, int P, int need_prec,
+                     CaseTab &ct, cudaStream_t s, const ib_phys *phys) {
+    std::vector<DevCase> h;
+    unsigned long long toff = 0;
+    int rc = fill_case_table(ncases, cases, P, need_prec, phys, h, toff);
+    if (rc) return rc;
     DevCase *d = ar.take<DevCase>(ncases);
     int *pcase = ar.take<int>(P > 0 ? P : 1);
     if (!ar.ok()) return oom_error(ar.used, ar.cap);
@@ -138,6 +149,79 @@ int build_case_table(ib_ctx *ctx, Arena &ar, int ncases, const ib_case *cases, i
     ct.one = h[0];
     return check_launch("case table");
 }
+
+int table_cases(const ib_batch_table *t, int P, CaseTab &ct) {
+    if (!t) return set_error(IB_ERR_INVALID, "table is NULL");
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev != t->device)
+        return set_error(IB_ERR_INVALID, "table belongs to device %d, current device is %d", t->device, dev);
+    if (P != t->P) return set_error(IB_ERR_INVALID, "table has P = %d particles, the call %d", t->P, P);
+    ct = t->ct;
+    return IB_OK;
+}
+
+}  // namespace gbib
+
+extern "C" int ib_batch_table_create(ib_ctx *ctx, int ncases, const ib_case *cases, int P, const ib_phys *phys,
+                                     ib_batch_table **out) {
+    using namespace gbib;
+    if (!ctx || !out) return set_error(IB_ERR_INVALID, "ctx or out is NULL");
+    *out = nullptr;
+    if (P < 0) return set_error(IB_ERR_INVALID, "P must be >= 0");
+    for (int c = 0; c < ncases && cases; ++c) {
+        if (!cases[c].u) return set_error(IB_ERR_INVALID, "case %d: NULL field", c);
+        if (phys && (!(phys[c].eps_c > 0.0) || !(phys[c].d_c > 0.0)))
+            return set_error(IB_ERR_INVALID, "case %d: eps_c and d_c must be > 0", c);
+    }
+    std::vector<DevCase> h;
+    unsigned long long toff = 0;
+    int rc = fill_case_table(ncases, cases, P, 1, phys, h, toff);
+    if (rc) return rc;
+    std::vector<int> pcase(P > 0 ? P : 1, 0);
+    for (int c = 0; c < ncases; ++c)
+        for (int p = cases[c].p_begin; p < cases[c].p_end; ++p) pcase[p] = c;
+    const size_t cbytes = ((sizeof(DevCase) * ncases + 255) / 256) * 256;
+    const size_t pbytes = sizeof(int) * pcase.size();
+    ib_batch_table *t = new (std::nothrow) ib_batch_table();
+    if (!t) return set_error(IB_ERR_OOM, "table");
+    if (cudaGetDevice(&t->device) != cudaSuccess || cudaMalloc(&t->mem, cbytes + pbytes) != cudaSuccess) {
+        delete t;
+        return set_error(IB_ERR_OOM, "case table: %s", cudaGetErrorString(cudaGetLastError()));
+    }
+    DevCase *d = (DevCase *)t->mem;
+    int *dp = (int *)((char *)t->mem + cbytes);
+    if (cudaMemcpy(d, h.data(), sizeof(DevCase) * ncases, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(dp, pcase.data(), pbytes, cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaFree(t->mem);
+        delete t;
+        return set_error(IB_ERR_CUDA, "case table upload: %s", cudaGetErrorString(cudaGetLastError()));
+    }
+    t->P = P;
+    t->ncases = ncases;
+    t->prec = cases[0].grid.prec;
+    t->has_phys = phys != nullptr;
+    t->ct.arr = d;
+    t->ct.pcase = dp;
+    t->ct.ncases = ncases;
+    t->ct.ntiles = (long long)toff;
+    t->ct.one = h[0];
+    *out = t;
+    return IB_OK;
+}
+
+extern "C" int ib_batch_table_destroy(ib_batch_table *t) {
+    if (!t) return IB_OK;
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (cur != t->device) cudaSetDevice(t->device);
+    cudaDeviceSynchronize();
+    cudaFree(t->mem);
+    if (cur >= 0 && cur != t->device) cudaSetDevice(cur);
+    delete t;
+    return IB_OK;
+}
+
+namespace gbib {
 
 // ---- exclusive scan ------------------------------------------------------
 // Three stages: per-block totals, a scan of the totals in one block, then a
@@ -343,6 +427,7 @@ int ib_ctx_create(ib_ctx **ctx, size_t workspace_bytes) {
     *c->h_nlev = 0;
     c->pass_kernels = IB_PASSES_AUTO;
     c->vol_split = 0;  // automatic
+    c->spread_mode = IB_SPREAD_GATHER;
     c->field_wait = nullptr;
     for (int k = 0; k < ib_ctx::kStageSlots; ++k) {
         c->stage_ptr[k] = nullptr;
@@ -397,6 +482,13 @@ int ib_selftest_wait_timeout(ib_ctx *c, long long cycles, void *stream) {
         return set_error(IB_ERR_INVALID, "self-test wait of %lld cycles outside [1, 4e9]", cycles);
     k_selftest_wait<<<1, 32, 0, (cudaStream_t)stream>>>(cycles, c->status);
     return check_launch("self-test wait");
+}
+
+int ib_ctx_set_spread_mode(ib_ctx *c, int mode) {
+    if (!c) return set_error(IB_ERR_INVALID, "ctx is NULL");
+    if (mode != IB_SPREAD_GATHER && mode != IB_SPREAD_ATOMIC) return set_error(IB_ERR_INVALID, "spread mode %d", mode);
+    c->spread_mode = mode;
+    return IB_OK;
 }
 
 int ib_ctx_set_volume_split(ib_ctx *c, int ctas_per_particle) {

@@ -151,6 +151,7 @@ struct ib_ctx {
     int nlev_hint;
     int pass_kernels;    // IB_PASSES_* of the sequential order
     int vol_split;       // CTAs per particle of the volume integrals (0: one resident wave)
+    int spread_mode;     // IB_SPREAD_GATHER (deterministic) or IB_SPREAD_ATOMIC
     void *field_wait;    // cudaEvent_t waited on before the forcing passes (nullable)
     // pinned staging ring for the case tables of batch calls: a slot is
     // reused only after the copy that last read it has run (its event)
@@ -159,6 +160,16 @@ struct ib_ctx {
     size_t stage_cap[kStageSlots];
     cudaEvent_t stage_ev[kStageSlots];
     int stage_next;
+};
+
+// A batch's case table uploaded once (ib_batch_table_create): device memory
+// owned by the table, so calls that take it stage nothing on the host.
+struct ib_batch_table {
+    int device;
+    int P, ncases, prec;
+    int has_phys;        // physical parameters given (needed by the collision update)
+    void *mem;           // device: DevCase[ncases], then int pcase[P]
+    gbib::CaseTab ct;
 };
 
 namespace gbib {
@@ -195,6 +206,12 @@ CaseTab single_case(const ib_grid *g, void *u, void *f, int P);
 // when the cases are invalid or the workspace is short.
 int build_case_table(ib_ctx *ctx, struct Arena &ar, int ncases, const ib_case *cases, int P, int need_prec,
                      CaseTab &ct, cudaStream_t s, const ib_phys *phys = nullptr);
+// Host side of a case table: validates the cases (grids, ranges partitioning
+// [0, P), one precision when need_prec) and fills h and the global tile count.
+int fill_case_table(int ncases, const ib_case *cases, int P, int need_prec, const ib_phys *phys,
+                    std::vector<DevCase> &h, unsigned long long &ntiles);
+// The table's CaseTab after checking it against the call (device, P).
+int table_cases(const ib_batch_table *t, int P, CaseTab &ct);
 
 // Records a CUDA event pair around a scope when the context times phases.
 // Programmatic dependent launch (sm_90 and later).  A kernel launched with

@@ -237,6 +237,60 @@ __device__ __forceinline__ void interp_marker(const T *__restrict__ u, const Dev
     }
 }
 
+// Atomic spreading of one marker: u += w_c A at its KW^3 stencil cells (and
+// f_out += w_c A / dt when given), combined first across the lanes of the warp
+// that target the same cell, so each distinct cell takes one atomic addition
+// per warp and component.  Every lane of the warp must call it together
+// (lanes with valid = false take part in the matching only).  FP64 fields:
+// the products run in double-float and each contribution is rounded to
+// double once before the lane sums.
+template <typename T, int KW>
+__device__ __forceinline__ void scatter_marker(T *u, T *f_out, const DevGrid &g, long long N, uint64_t anc,
+                                               const PS<T> *w, const PS<T> *A, bool valid, double inv_dt) {
+    const int lane = threadIdx.x & 31;
+    int ix[KW], iy[KW], iz[KW];
+    const int ax = anchor_x(anc), ay = anchor_y(anc), az = anchor_z(anc);
+#pragma unroll
+    for (int k = 0; k < KW; ++k) {
+        ix[k] = wrap_add(ax, k, g.n[0]);
+        iy[k] = wrap_add(ay, k, g.n[1]);
+        iz[k] = wrap_add(az, k, g.n[2]);
+    }
+#pragma unroll 1
+    for (int kz = 0; kz < KW; ++kz)
+#pragma unroll
+        for (int ky = 0; ky < KW; ++ky)
+#pragma unroll
+            for (int kx = 0; kx < KW; ++kx) {
+                const long long c = ((long long)iz[kz] * g.n[1] + iy[ky]) * g.n[0] + ix[kx];
+                T v[3];
+                if constexpr (sizeof(T) == 8) {
+                    const float2 wt = pair_weight(w, kx, ky, kz);
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) v[q] = valid ? df_to_double(df_mul(wt, A[q])) : 0.0;
+                } else {
+                    const T wt = pair_weight(w, kx, ky, kz);
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) v[q] = valid ? wt * A[q] : T(0);
+                }
+                const unsigned long long key = valid ? (unsigned long long)c : ~0ull - (unsigned)lane;
+                const unsigned grp = __match_any_sync(0xffffffffu, key);
+                T sum[3] = {T(0), T(0), T(0)};
+                for (unsigned m = grp; m; m &= m - 1) {
+                    const int src = __ffs(m) - 1;
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) sum[q] += __shfl_sync(grp, v[q], src);
+                }
+                if (valid && lane == __ffs(grp) - 1) {
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) atomicAdd(u + q * N + c, sum[q]);
+                    if (f_out)
+#pragma unroll
+                        for (int q = 0; q < 3; ++q) atomicAdd(f_out + q * N + c, (T)(sum[q] * inv_dt));
+                }
+            }
+}
+
 template <typename T, int KW, bool STAGED, bool COH>
 __device__ __forceinline__ bool gather_cell(int tx, int ty, int tz, const uint16_t *bins, const uint32_t *cand,
                                             const T *w_src, const T *A_src, T acc[3]) {

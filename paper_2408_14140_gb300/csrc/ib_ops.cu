@@ -1034,6 +1034,45 @@ __global__ void __launch_bounds__(256) k_spread_gather(CaseTab ct, const int *__
         gather_tile_lists<T, Kernel<KER>::W, false>(ct, cs, sl, wts, A, 0.0, sw, sA);
 }
 
+// Spreading (ib_spread) with warp-aggregated atomics: one lane per marker,
+// weights formed on the fly, no binning.
+template <typename T, int KER>
+__global__ void __launch_bounds__(256) k_spread_atomic(DevGrid g, int M, const double *__restrict__ X,
+                                                       const double *__restrict__ F, const double *__restrict__ dV,
+                                                       T *__restrict__ f, DevStatus *st) {
+    constexpr int KW = Kernel<KER>::W;
+    const long long N = (long long)g.n[0] * g.n[1] * g.n[2];
+    const int lane = threadIdx.x & 31;
+    const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
+    // warp-uniform loop: every lane takes part in the matching
+    for (long long base = ((long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32; base < M;
+         base += nwarps * 32) {
+        const long long l = base + lane;
+        bool valid = l < M;
+        double x[3] = {0, 0, 0}, fv[3] = {0, 0, 0}, dv = 0.0;
+        if (valid) {
+            x[0] = X[3 * l], x[1] = X[3 * l + 1], x[2] = X[3 * l + 2];
+            fv[0] = F[3 * l], fv[1] = F[3 * l + 1], fv[2] = F[3 * l + 2];
+            dv = dV[l];
+            if (!(finite3(x) && finite3(fv) && isfinite(dv))) {
+                raise_status(st, IB_ERR_NONFINITE, (int)l);
+                valid = false;
+            }
+        }
+        if (!valid) x[0] = g.org[0], x[1] = g.org[1], x[2] = g.org[2];
+        T w[12];
+        long long first[3];
+        const uint64_t anc = marker_weights<T, KER>(g, x, w, first);
+        PS<T> ws[12], A[3];
+#pragma unroll
+        for (int k = 0; k < 12; ++k) ws[k] = to_store(w[k]);
+        const double q = dv * g.inv_h3;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) A[c] = to_store((T)(fv[c] * q));
+        scatter_marker<T, KW>(f, (T *)nullptr, g, N, anc, ws, A, valid, 0.0);
+    }
+}
+
 // ---------------------------------------------------------------------------
 // grid barrier with a bounded wait
 // ---------------------------------------------------------------------------
@@ -1098,6 +1137,7 @@ struct PassArgs {
     const int *nlev;
     int Ns;
     int L0;  // first wavefront the persistent kernel processes
+    int atomic;  // spread with warp-aggregated atomics instead of the tile gather
     double dt, inv_dt;  // inv_dt = 1 / dt, formed on the host
     Barrier bar;
     DevStatus *st;
@@ -1358,6 +1398,39 @@ __global__ void __launch_bounds__(kGatherThreads, sizeof(T) == 4 ? 5 : 4) k_gath
     }
 }
 
+// The atomic form of a wavefront's spreading (ib_ctx_set_spread_mode):
+// every marker of the wavefront adds S A to the field with warp-aggregated
+// atomics.  Its position data are loaded before the wait; the sources after.
+template <typename T, int KER>
+__global__ void __launch_bounds__(256) k_scatter_level(PassArgs<T> a, int L) {
+    constexpr int KW = Kernel<KER>::W;
+    const int nl = *a.nlev;
+    const int m0 = L < nl ? a.lev_mbeg[L] : 0, m1 = L < nl ? a.lev_mbeg[L + 1] : 0;
+    const int lane = threadIdx.x & 31;
+    const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
+    bool waited = false;
+    for (long long base = m0 + ((long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32; base < m1;
+         base += nwarps * 32) {
+        const long long i = base + lane;
+        const bool valid = i < m1;
+        const int l = valid ? a.mperm[i] : a.mperm[m0];
+        const uint64_t anc = a.ms.anchor[l];
+        PS<T> w[12], A[3];
+#pragma unroll
+        for (int k = 0; k < 12; ++k) w[k] = __ldg(a.ms.wts + 12 * (size_t)l + k);
+        const DevCase cd = a.ct.of_particle(a.part_of[l]);
+        if (!waited) {
+            grid_dep_wait();
+            waited = true;
+        }
+#pragma unroll
+        for (int c = 0; c < 3; ++c) A[c] = a.ms.A[4 * (size_t)l + c];
+        const long long N = (long long)cd.g.n[0] * cd.g.n[1] * cd.g.n[2];
+        scatter_marker<T, KW>((T *)cd.u, (T *)cd.f, cd.g, N, anc, w, A, valid, a.inv_dt);
+    }
+    if (!waited) grid_dep_wait();
+}
+
 template <typename T, int KER>
 __global__ void __launch_bounds__(256) k_mdf_passes(PassArgs<T> a) {
     constexpr int KW = Kernel<KER>::W;
@@ -1390,9 +1463,29 @@ __global__ void __launch_bounds__(256) k_mdf_passes(PassArgs<T> a) {
                 }
             }
             if (!grid_sync(a.bar, a.st)) return;
-            // gather phase over the wavefront's tiles (their per-cell lists)
-            for (int cs = s0 + blockIdx.x; cs < s1; cs += gridDim.x)
-                gather_tile_lists<T, KW, true>(a.ct, cs, a.sl, a.ms.wts, a.ms.A, inv_dt, sw, sA);
+            if (a.atomic) {
+                // atomic spreading of the wavefront's markers (warp-uniform loop)
+                const int lane = threadIdx.x & 31;
+                const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
+                for (long long base = m0 + ((long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32;
+                     base < m1; base += nwarps * 32) {
+                    const long long i = base + lane;
+                    const bool valid = i < m1;
+                    const int l = valid ? a.mperm[i] : a.mperm[m0];
+                    const DevCase cd = a.ct.of_particle(a.part_of[l]);
+                    const long long N = (long long)cd.g.n[0] * cd.g.n[1] * cd.g.n[2];
+                    PS<T> w[12], A[3];
+#pragma unroll
+                    for (int k = 0; k < 12; ++k) w[k] = a.ms.wts[12 * (size_t)l + k];
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) A[c] = a.ms.A[4 * (size_t)l + c];
+                    scatter_marker<T, KW>((T *)cd.u, (T *)cd.f, cd.g, N, a.ms.anchor[l], w, A, valid, inv_dt);
+                }
+            } else {
+                // gather phase over the wavefront's tiles (their per-cell lists)
+                for (int cs = s0 + blockIdx.x; cs < s1; cs += gridDim.x)
+                    gather_tile_lists<T, KW, true>(a.ct, cs, a.sl, a.ms.wts, a.ms.A, inv_dt, sw, sA);
+            }
             if (!grid_sync(a.bar, a.st)) return;
         }
     }
@@ -1521,6 +1614,13 @@ template <typename T, int KER>
 static int run_spread(ib_ctx *ctx, const ib_grid *grid, int M, const double *X, const double *F,
                       const double *dV, void *f, cudaStream_t s) {
     constexpr int KW = Kernel<KER>::W;
+    if (ctx->spread_mode == IB_SPREAD_ATOMIC) {
+        PhaseTimer tm(ctx, IB_PHASE_SPREAD, s);
+        const DevGrid g = make_dev_grid(grid);
+        k_spread_atomic<T, KER><<<grid_blocks(M, 256, ctx->sm_count), 256, 0, s>>>(g, M, X, F, dV, (T *)f,
+                                                                                 ctx->status);
+        return check_launch("ib_spread");
+    }
     Arena ar(ctx);
     MarkerState<T> ms;
     take_markers<T>(ar, M, ms);
@@ -1591,11 +1691,19 @@ static int run_mdf(ib_ctx *ctx, Arena &ar, const CaseTab &ct, const ib_particles
     // fields always run the wavefront form (double-float pass sums)
     const int pass_kernels = sizeof(T) == 4 ? ctx->pass_kernels : IB_PASSES_WAVEFRONT;
     const bool resident = order == IB_ORDER_SEQUENTIAL && pass_kernels == IB_PASSES_RESIDENT;
-    Slots sl;
-    SlotScratch sc;
-    int rc = slots_alloc<KW>(ar, M, (int)ndense, sg.mode, sl, sc, s, true, resident);
-    if (rc) return rc;
-    int *tperm = ar.take<int>(sc.ncompact_cap);
+    // atomic spreading (wavefront form): no tile lists at all
+    const bool wavefront = order == IB_ORDER_SIMULTANEOUS || pass_kernels == IB_PASSES_AUTO ||
+                           pass_kernels == IB_PASSES_WAVEFRONT;
+    const bool atomic = wavefront && ctx->spread_mode == IB_SPREAD_ATOMIC;
+    Slots sl{};
+    SlotScratch sc{};
+    int rc = IB_OK;
+    int *tperm = nullptr;
+    if (!atomic) {
+        rc = slots_alloc<KW>(ar, M, (int)ndense, sg.mode, sl, sc, s, true, resident);
+        if (rc) return rc;
+        tperm = ar.take<int>(sc.ncompact_cap);
+    }
     if (!ar.ok())
         return oom_error(ar.used, ar.cap);
     PhaseTimer tprep(ctx, IB_PHASE_MDF_PREP, s);
@@ -1621,8 +1729,10 @@ static int run_mdf(ib_ctx *ctx, Arena &ar, const CaseTab &ct, const ib_particles
     sg.box_lo = box_lo;
     sg.box_dim = box_dim;
     int *ncompact = nullptr;
-    rc = slots_build<KW>(ctx, ct, M, (int)ndense, sg, ms.anchor, lo.level, sl, sc, ncompact, s, true);
-    if (rc) return rc;
+    if (!atomic) {
+        rc = slots_build<KW>(ctx, ct, M, (int)ndense, sg, ms.anchor, lo.level, sl, sc, ncompact, s, true);
+        if (rc) return rc;
+    }
     if constexpr (sizeof(T) == 4) {
     if (order == IB_ORDER_SEQUENTIAL &&
         (pass_kernels == IB_PASSES_RESIDENT || pass_kernels == IB_PASSES_GROUPS)) {
@@ -1666,10 +1776,12 @@ static int run_mdf(ib_ctx *ctx, Arena &ar, const CaseTab &ct, const ib_particles
         return check_launch("ib_multidirect_forcing");
     }
     }
-    launch_pdl(k_level_slots, dim3(1), dim3(256), 0, s, sg.mode, (const int *)lo.nlev, (const int *)lo.lev_pbeg,
-               (const uint32_t *)sl.flag_scan, (int)ndense, lev_sbeg);
-    launch_pdl(k_level_tile_order, dim3(P < 64 ? P : 64), dim3(512), 0, s, (const int *)lo.nlev,
-               (const int *)lev_sbeg, (const int *)sl.nband, tperm);
+    if (!atomic) {
+        launch_pdl(k_level_slots, dim3(1), dim3(256), 0, s, sg.mode, (const int *)lo.nlev,
+                   (const int *)lo.lev_pbeg, (const uint32_t *)sl.flag_scan, (int)ndense, lev_sbeg);
+        launch_pdl(k_level_tile_order, dim3(P < 64 ? P : 64), dim3(512), 0, s, (const int *)lo.nlev,
+                   (const int *)lev_sbeg, (const int *)sl.nband, tperm);
+    }
     tprep.stop();
     // (the field is first read and written by the pass kernels below)
     if (ctx->field_wait) cudaStreamWaitEvent(s, (cudaEvent_t)ctx->field_wait, 0);
@@ -1690,6 +1802,7 @@ static int run_mdf(ib_ctx *ctx, Arena &ar, const CaseTab &ct, const ib_particles
     a.inv_dt = 1.0 / dt;
     a.bar = bar;
     a.st = ctx->status;
+    a.atomic = atomic ? 1 : 0;
     // wavefronts enqueued as separate kernels: the count the last call on this
     // context copied to a pinned host word (read without synchronising: an
     // aligned 4-byte word is either the old or the new count; a short count
@@ -1722,6 +1835,11 @@ static int run_mdf(ib_ctx *ctx, Arena &ar, const CaseTab &ct, const ib_particles
         cg.blockDim = dim3(kGatherThreads);
         cg.dynamicSmemBytes = gsm;
         cg.numAttrs = 1;
+        // the atomic form: one lane per marker of the largest wavefront at most
+        cudaLaunchConfig_t cs = ci;
+        cs.gridDim = dim3(grid_blocks(M, 256, ctx->sm_count));
+        cs.blockDim = dim3(256);
+        cs.numAttrs = 1;
         for (int L = 0; L < Lenq; ++L)
             for (int m = 0; m < Ns; ++m) {
                 {
@@ -1730,7 +1848,10 @@ static int run_mdf(ib_ctx *ctx, Arena &ar, const CaseTab &ct, const ib_particles
                     cudaLaunchKernelEx(&ci, k_interp_level<T, KER>, a, L);
                 }
                 PhaseTimer tg(ctx, IB_PHASE_MDF_GATHER, s);
-                cudaLaunchKernelEx(&cg, k_gather_level<T, KER>, a, L);
+                if (atomic)
+                    cudaLaunchKernelEx(&cs, k_scatter_level<T, KER>, a, L);
+                else
+                    cudaLaunchKernelEx(&cg, k_gather_level<T, KER>, a, L);
             }
     }
     int per_sm = 0;
@@ -1813,6 +1934,19 @@ int ib_multidirect_forcing(ib_ctx *ctx, const ib_grid *grid, void *u, const ib_p
     const CaseTab ct = single_case(grid, u, f_out, parts->P);
     Arena ar(ctx);
     return DISPATCH(grid->prec, delta, run_mdf, ctx, ar, ct, parts, marks, Ns, dt, order, F_out,
+                    (cudaStream_t)stream);
+}
+
+int ib_batch_table_multidirect_forcing(ib_ctx *ctx, const ib_batch_table *table, const ib_particles *parts,
+                                       const ib_markers *marks, int Ns, double dt, int delta, int order,
+                                       double *F_out, void *stream) {
+    int rc = check_mdf_args(ctx, parts, marks, Ns, dt, delta, order, F_out);
+    if (rc) return rc == 1 ? IB_OK : rc;
+    CaseTab ct;
+    rc = table_cases(table, parts->P, ct);
+    if (rc) return rc;
+    Arena ar(ctx);
+    return DISPATCH(table->prec, delta, run_mdf, ctx, ar, ct, parts, marks, Ns, dt, order, F_out,
                     (cudaStream_t)stream);
 }
 

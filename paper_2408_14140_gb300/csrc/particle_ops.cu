@@ -1193,6 +1193,37 @@ int particle_collide_update(ib_ctx *ctx, ib_particles *parts, const ib_grid *gri
                        (cudaStream_t)stream);
 }
 
+int ib_batch_table_volume_integrals(ib_ctx *ctx, const ib_batch_table *table, const ib_particles *parts,
+                                    double *Iu, double *Irxu, double *vol, void *stream) {
+    if (!ctx) return set_error(IB_ERR_INVALID, "ctx is NULL");
+    if (!parts || parts->P < 0) return set_error(IB_ERR_INVALID, "bad particles");
+    CaseTab ct;
+    int rc = table_cases(table, parts->P, ct);
+    if (rc) return rc;
+    if (parts->P == 0) return IB_OK;
+    if (!parts->Xr || !parts->radius || !Iu || !Irxu || !vol) return set_error(IB_ERR_INVALID, "NULL array");
+    if ((long long)parts->P * kVolMaxSplit > (1LL << 31) - 1) return set_error(IB_ERR_UNSUPPORTED, "too many particles");
+    Arena ar(ctx);
+    if (table->prec == IB_F64) return run_volume<double>(ctx, ar, ct, parts, Iu, Irxu, vol, (cudaStream_t)stream);
+    return run_volume<float>(ctx, ar, ct, parts, Iu, Irxu, vol, (cudaStream_t)stream);
+}
+
+int ib_batch_table_collide_update(ib_ctx *ctx, const ib_batch_table *table, ib_particles *parts, double dt,
+                                  const double *F_ib, const double *T_ib, const double *Iu_new,
+                                  const double *Iu_old, const double *Irxu_new, const double *Irxu_old,
+                                  double *Fc_out, void *stream) {
+    if (table && !table->has_phys) return set_error(IB_ERR_INVALID, "the table was created without physical parameters");
+    const ib_phys *ph = table ? &table->ct.one.phys : nullptr;
+    int rc = check_collide_args(ctx, parts, ph, dt, F_ib, T_ib, Iu_new, Iu_old, Irxu_new, Irxu_old);
+    if (rc) return rc == 1 ? IB_OK : rc;
+    CaseTab ct;
+    rc = table_cases(table, parts->P, ct);
+    if (rc) return rc;
+    Arena ar(ctx);
+    return run_collide(ctx, ar, ct, parts, dt, F_ib, T_ib, Iu_new, Iu_old, Irxu_new, Irxu_old, Fc_out,
+                       (cudaStream_t)stream);
+}
+
 int ib_batch_collide_update(ib_ctx *ctx, int ncases, const ib_case *cases, ib_particles *parts,
                             const ib_phys *phys, double dt, const double *F_ib, const double *T_ib,
                             const double *Iu_new, const double *Iu_old, const double *Irxu_new,
