@@ -192,7 +192,10 @@ GBIB_API int ib_ctx_set_spread_mode(ib_ctx *ctx, int mode);
  * each (1 <= n <= 32), or 0 (the default): as many as fill one resident wave
  * of the device for the call's particle count (at least 1, at most 32).
  * Results do not depend on it beyond the rounding of the partial sums'
- * grouping.  IB_ERR_INVALID outside [0, 32].                              */
+ * grouping.  The automatic choice depends on the call's particle count, so
+ * a case's integrals computed inside a batch agree with the same case alone
+ * only to rounding; a fixed split makes them bitwise equal.
+ * IB_ERR_INVALID outside [0, 32].                                          */
 GBIB_API int ib_ctx_set_volume_split(ib_ctx *ctx, int ctas_per_particle);
 
 /* ---- overlap: a dependency before the field is written ------------------
@@ -336,7 +339,9 @@ GBIB_API int ib_batch_collide_update(ib_ctx *ctx, int ncases, const ib_case *cas
  * ib_batch_table_create validates `cases` as the ib_batch_* calls do (and
  * phys, when given: eps_c, d_c > 0 per case) and copies the case table into
  * device memory that the returned table owns.  It allocates (cudaMalloc) and
- * waits for its copies, so create tables before any stream capture.  The
+ * waits for its copies (made on a private non-blocking stream, so they wait
+ * for no work the caller has queued), so create tables before any stream
+ * capture.  The
  * table keeps the cases' field pointers: it serves calls on exactly those
  * fields and particle ranges (P particles) until ib_batch_table_destroy.
  * The ib_batch_table_* calls compute what the ib_batch_* calls of the same
@@ -347,8 +352,8 @@ GBIB_API int ib_batch_collide_update(ib_ctx *ctx, int ncases, const ib_case *cas
  * when the table is not used for ib_batch_table_collide_update (which then
  * returns IB_ERR_INVALID).  Errors: IB_ERR_INVALID for bad cases, a NULL
  * table, a table of another device or a call whose P differs; IB_ERR_OOM /
- * IB_ERR_CUDA when the device copy cannot be made.  Destroy waits for the
- * device before freeing.                                                      */
+ * IB_ERR_CUDA when the device copy cannot be made.  Destroy frees the device
+ * memory once the work already queued on the device has finished.            */
 typedef struct ib_batch_table ib_batch_table;
 GBIB_API int ib_batch_table_create(ib_ctx *ctx, int ncases, const ib_case *cases, int P,
                                    const ib_phys *phys, ib_batch_table **table);

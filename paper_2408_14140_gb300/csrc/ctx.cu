@@ -190,11 +190,18 @@ extern "C" int ib_batch_table_create(ib_ctx *ctx, int ncases, const ib_case *cas
     }
     DevCase *d = (DevCase *)t->mem;
     int *dp = (int *)((char *)t->mem + cbytes);
-    if (cudaMemcpy(d, h.data(), sizeof(DevCase) * ncases, cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(dp, pcase.data(), pbytes, cudaMemcpyHostToDevice) != cudaSuccess) {
+    // upload on a private non-blocking stream: the copy waits for nothing the
+    // caller has queued (not even on the legacy default stream)
+    cudaStream_t us = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&us, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d, h.data(), sizeof(DevCase) * ncases, cudaMemcpyHostToDevice, us);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dp, pcase.data(), pbytes, cudaMemcpyHostToDevice, us);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(us);
+    if (us) cudaStreamDestroy(us);
+    if (e != cudaSuccess) {
         cudaFree(t->mem);
         delete t;
-        return set_error(IB_ERR_CUDA, "case table upload: %s", cudaGetErrorString(cudaGetLastError()));
+        return set_error(IB_ERR_CUDA, "case table upload: %s", cudaGetErrorString(e));
     }
     t->P = P;
     t->ncases = ncases;
@@ -214,8 +221,7 @@ extern "C" int ib_batch_table_destroy(ib_batch_table *t) {
     int cur = -1;
     cudaGetDevice(&cur);
     if (cur != t->device) cudaSetDevice(t->device);
-    cudaDeviceSynchronize();
-    cudaFree(t->mem);
+    cudaFree(t->mem);  // (cudaFree waits for the device's queued work first)
     if (cur >= 0 && cur != t->device) cudaSetDevice(cur);
     delete t;
     return IB_OK;

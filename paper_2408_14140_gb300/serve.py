@@ -12,10 +12,15 @@ Sec. 3.1 (Step 2) on a prescribed flow:
     collision forces (Eq. DKT_model) + Newton-Euler update (Eq. pr2)
 
 The server keeps every admitted request's field, background flow, particle
-state and markers resident on the device.  Waiting requests are admitted
-first come, first served, while the device-memory budget and the slot count
-allow; each loop iteration advances every active request by one time step
-through one sequence of batch launches, so requests that arrived at
+state and markers resident on the device.  Requests wait in one queue per
+field precision and are admitted first come, first served within it, while
+the shared device-memory budget and the precision's slot count allow (a
+blocked head of one precision does not hold back the other).  Each loop
+iteration advances every active request by one time step through one
+sequence of batch launches per precision -- the batch's case table uploaded
+once per change of its active set, the precisions on separate streams so
+their steps overlap on the device, and a step replayed from a CUDA graph
+while the active set stays the same -- so requests that arrived at
 different times share the same kernels.  A request that has run all its
 steps has its particle state copied to pinned host memory; its latency runs
 from its arrival to that copy's completion.
@@ -49,7 +54,11 @@ class ServeConfig:
     U0: float = 1.0                # Taylor-Green amplitude
     fp64_fraction: float = 0.0     # share of requests served with FP64 fields
     budget_bytes: int = 32 << 30   # device memory for resident requests
-    max_active: int = 64
+    max_active: int = 64           # active requests per field precision
+    graph_after: int = 2           # replay a group's step from a CUDA graph once its
+                                   # active set has not changed for this many steps (0: never)
+    volume_split: int = 8          # CTAs per particle of the volume integrals: fixed, so a
+                                   # request's sums do not depend on which requests share its batch
     seed: int = 0
 
 
@@ -122,17 +131,26 @@ def admit_count(waiting_bytes, used: int, budget: int, n_active: int, max_active
 
 
 class Group:
-    """Active requests of one field precision and their flat batch arrays."""
+    """Active requests of one field precision: their flat batch arrays, the
+    batch's case table on the device, and the group's own stream, so that the
+    two precisions' steps overlap on the device."""
 
-    def __init__(self, prec: int, ctx: api.Context):
+    def __init__(self, prec: int, ctx: api.Context, device):
         self.prec = prec
         self.ctx = ctx
+        self.stream = torch.cuda.Stream(device=device)
         self.active: list[Request] = []
         self.dirty = True
+        self.table = None
+        self.graph = None
+        self.stable = 0          # steps since the active set last changed
+        self.graph_steps = 0     # steps replayed from a graph
+        self.eager_steps = 0
 
     def rebuild(self, device):
         """Lay the active requests out as one flat particle/marker set; the
-        requests' particle tensors become views of the flat arrays."""
+        requests' particle tensors become views of the flat arrays; upload the
+        batch's case table once."""
         reqs = self.active
         self.parts, self.marks, self.ranges, _ = api.pack_batch([r.parts for r in reqs],
                                                                 [r.marks for r in reqs])
@@ -140,9 +158,9 @@ class Group:
             for k in ("Xr", "Ur", "Wr"):
                 r.parts[k] = self.parts[k][p0:p1]
         self.fields = [r.u for r in reqs]
-        self.hs = [r.case.h for r in reqs]
-        self.shapes = [r.case.n for r in reqs]
-        self.phys = [r.case.phys() for r in reqs]
+        self.bgs = [r.u_bg for r in reqs]
+        hs = [r.case.h for r in reqs]
+        phys = [r.case.phys() for r in reqs]
         P, M = self.parts["Xr"].shape[0], self.marks["R"].shape[0]
         f64 = dict(dtype=torch.float64, device=device)
         self.F = torch.empty((M, 3), **f64)
@@ -151,36 +169,64 @@ class Group:
         self.Fc = torch.empty((P, 3), **f64)
         self.I_old = (torch.empty((P, 3), **f64), torch.empty((P, 3), **f64), torch.empty((P,), **f64))
         self.I_new = (torch.empty((P, 3), **f64), torch.empty((P, 3), **f64), torch.empty((P,), **f64))
+        if self.table is not None:
+            self.table.close()
+        self.table = api.BatchTable(self.ctx, self.fields, hs, self.ranges, P, phys=phys)
+        self.graph = None
+        self.stable = 0
         self.dirty = False
+
+    def launch(self, cfg: ServeConfig):
+        """One time step of every active request (enqueued on the current stream)."""
+        torch._foreach_copy_(self.fields, self.bgs)
+        c, t = self.ctx, self.table
+        c.ib_batch_table_volume_integrals(t, self.parts, out=self.I_old)
+        c.ib_batch_table_multidirect_forcing(t, self.parts, self.marks, cfg.Ns, cfg.dt, F_out=self.F)
+        c.particle_force_torque(self.parts, self.marks, self.F, 1.0, out=(self.Fib, self.Tib))
+        c.ib_batch_table_volume_integrals(t, self.parts, out=self.I_new)
+        c.ib_batch_table_collide_update(t, self.parts, cfg.dt, self.Fib, self.Tib, self.I_new[0], self.I_old[0],
+                                        self.I_new[1], self.I_old[1], Fc_out=self.Fc)
 
     def step(self, cfg: ServeConfig, device):
         if not self.active:
             return
-        if self.dirty:
-            self.rebuild(device)
-        for r in self.active:
-            r.u.copy_(r.u_bg)
-        c = self.ctx
-        c.ib_batch_volume_integrals(self.fields, self.hs, self.parts, self.ranges, out=self.I_old)
-        c.ib_batch_multidirect_forcing(self.fields, self.hs, self.parts, self.marks, self.ranges, cfg.Ns,
-                                       cfg.dt, F_out=self.F)
-        c.particle_force_torque(self.parts, self.marks, self.F, 1.0, out=(self.Fib, self.Tib))
-        c.ib_batch_volume_integrals(self.fields, self.hs, self.parts, self.ranges, out=self.I_new)
-        c.ib_batch_collide_update(self.parts, self.shapes, self.hs, self.ranges, self.phys, cfg.dt, self.Fib,
-                                  self.Tib, self.I_new[0], self.I_old[0], self.I_new[1], self.I_old[1],
-                                  Fc_out=self.Fc)
+        # every device operation of the group (its allocations included) runs
+        # on the group's stream, so it is ordered after the group's last step
+        with torch.cuda.stream(self.stream):
+            if self.dirty:
+                self.rebuild(device)
+            if self.graph is not None:
+                self.graph.replay()
+                self.graph_steps += 1
+            else:
+                self.launch(cfg)
+                self.eager_steps += 1
+                self.stable += 1
+                if cfg.graph_after and self.stable >= cfg.graph_after:
+                    # the step's launch sequence, captured once for the steps
+                    # that follow while the active set stays the same (the
+                    # eager steps have sized the workspace)
+                    g = torch.cuda.CUDAGraph()
+                    with torch.cuda.graph(g, stream=self.stream):
+                        self.launch(cfg)
+                    self.graph = g
+                    # capture records the work without running it: this step ran eagerly
         for r in self.active:
             r.steps_done += 1
 
 
 class Server:
-    """Admission by device-memory budget, one batch step per iteration."""
+    """Admission by device-memory budget, one batch step per group and
+    iteration.  Each field precision has its own FIFO queue, slot count and
+    stream; the device-memory budget is shared."""
 
     def __init__(self, cfg: ServeConfig, device="cuda"):
         self.cfg = cfg
         self.device = device
-        self.groups = {p: Group(p, api.Context()) for p in (api.IB_F32, api.IB_F64)}
-        self.waiting: list[Request] = []
+        self.groups = {p: Group(p, api.Context(), device) for p in (api.IB_F32, api.IB_F64)}
+        for g in self.groups.values():
+            g.ctx.set_volume_split(cfg.volume_split)
+        self.waiting = {p: [] for p in self.groups}
         self.finishing: list[Request] = []
         self.used = 0
         self.active_peak = 0
@@ -188,15 +234,19 @@ class Server:
     def n_active(self):
         return sum(len(g.active) for g in self.groups.values())
 
+    def n_waiting(self):
+        return sum(len(q) for q in self.waiting.values())
+
     def admit(self, r: Request):
         c = r.case
         dt = api.field_dtype(r.prec)
-        r.u_bg = synth.taylor_green_torch(c.n, self.cfg.U0, c.h, device=self.device, dtype=dt)
-        r.u = torch.empty_like(r.u_bg)
-        _, r.parts, r.marks = api.device_case(c.__class__(**{**c.__dict__, "u": np.zeros((3, 1, 1, 1))}),
-                                              r.prec, self.device)
-        self.used += r.bytes
         g = self.groups[r.prec]
+        with torch.cuda.stream(g.stream):  # the request's memory belongs to its group's stream
+            r.u_bg = synth.taylor_green_torch(c.n, self.cfg.U0, c.h, device=self.device, dtype=dt)
+            r.u = torch.empty_like(r.u_bg)
+            _, r.parts, r.marks = api.device_case(c.__class__(**{**c.__dict__, "u": np.zeros((3, 1, 1, 1))}),
+                                                  r.prec, self.device)
+        self.used += r.bytes
         g.active.append(r)
         g.dirty = True
 
@@ -206,10 +256,11 @@ class Server:
         g.dirty = True
         r.host = {k: torch.empty(r.parts[k].shape, dtype=torch.float64, pin_memory=True)
                   for k in ("Xr", "Ur", "Wr")}
-        for k, t in r.host.items():
-            t.copy_(r.parts[k], non_blocking=True)
-        r.event = torch.cuda.Event()
-        r.event.record()
+        with torch.cuda.stream(g.stream):
+            for k, t in r.host.items():
+                t.copy_(r.parts[k], non_blocking=True)
+            r.event = torch.cuda.Event()
+            r.event.record(g.stream)
         r.u = r.u_bg = None
         self.finishing.append(r)
 
@@ -233,15 +284,17 @@ class Server:
         pending = list(trace)
         t0 = time.perf_counter()
         now = lambda: time.perf_counter() - t0
-        inflight: list[torch.cuda.Event] = []
-        while pending or self.waiting or self.n_active() or self.finishing:
+        inflight: list[list[torch.cuda.Event]] = []
+        while pending or self.n_waiting() or self.n_active() or self.finishing:
             tnow = now()
             while pending and pending[0].arrival <= tnow:
-                self.waiting.append(pending.pop(0))
-            k = admit_count([r.bytes for r in self.waiting], self.used, cfg.budget_bytes, self.n_active(),
-                            cfg.max_active)
-            for _ in range(k):
-                self.admit(self.waiting.pop(0))
+                r = pending.pop(0)
+                self.waiting[r.prec].append(r)
+            for p, q in self.waiting.items():
+                k = admit_count([r.bytes for r in q], self.used, cfg.budget_bytes, len(self.groups[p].active),
+                                cfg.max_active)
+                for _ in range(k):
+                    self.admit(q.pop(0))
             self.active_peak = max(self.active_peak, self.n_active())
             if self.n_active():
                 for g in self.groups.values():
@@ -249,14 +302,19 @@ class Server:
                 for g in self.groups.values():
                     for r in [r for r in g.active if r.steps_done >= cfg.steps]:
                         self.retire(r)
-                ev = torch.cuda.Event()
-                ev.record()
-                inflight.append(ev)
+                evs = []
+                for g in self.groups.values():
+                    ev = torch.cuda.Event()
+                    ev.record(g.stream)
+                    evs.append(ev)
+                inflight.append(evs)
                 # keep the host at most two steps ahead of the device
                 if sync_every_step:
-                    ev.synchronize()
+                    for ev in evs:
+                        ev.synchronize()
                 elif len(inflight) > 2:
-                    inflight.pop(0).synchronize()
+                    for ev in inflight.pop(0):
+                        ev.synchronize()
             else:
                 self.poll(now)
                 if not self.finishing:
@@ -264,12 +322,21 @@ class Server:
                     time.sleep(max(0.0, min(nxt - now(), 0.002)))
                 continue
             self.poll(now)
+        torch.cuda.synchronize()
         for g in self.groups.values():
             g.ctx.status()
         return trace
 
+    def stats(self):
+        return {"graph_steps": sum(g.graph_steps for g in self.groups.values()),
+                "eager_steps": sum(g.eager_steps for g in self.groups.values())}
+
     def close(self):
+        torch.cuda.synchronize()
         for g in self.groups.values():
+            if g.table is not None:
+                g.table.close()
+            g.graph = None
             g.ctx.close()
 
 
@@ -282,6 +349,7 @@ def serve_alone(cfg: ServeConfig, r: Request, device="cuda"):
     g = srv.groups[r.prec]
     for _ in range(cfg.steps):
         g.step(cfg, device)
+    g.stream.synchronize()
     out = {k: r.parts[k].cpu() for k in ("Xr", "Ur", "Wr")}
     for gg in srv.groups.values():
         gg.ctx.status()
