@@ -198,6 +198,16 @@ GBIB_API int ib_ctx_set_spread_mode(ib_ctx *ctx, int mode);
  * IB_ERR_INVALID outside [0, 32].                                          */
 GBIB_API int ib_ctx_set_volume_split(ib_ctx *ctx, int ctas_per_particle);
 
+/* ---- wavefront gather layout (tuning knobs) ------------------------------
+ * ctas_per_sm: resident gather CTAs per SM (0, the default: as many as fit;
+ * 1..32 caps it).  stage: the candidates of a tile that a gather CTA stages
+ * in shared memory (0, the default: the largest capacity, 256 for FP32 and
+ * 192 for FP64 fields; else a multiple of 32 in [32, 256], capped at the
+ * largest); a tile with more candidates reads them from memory, and a smaller
+ * capacity lets more CTAs share an SM.  Neither changes a result: every cell
+ * adds the same values in the same order.  IB_ERR_INVALID otherwise.       */
+GBIB_API int ib_ctx_set_gather(ib_ctx *ctx, int ctas_per_sm, int stage);
+
 /* ---- overlap: a dependency before the field is written ------------------
  * `event` is a cudaEvent_t (or NULL, the default, for none).  Every
  * multidirect-forcing call on this context (single or batched) makes its

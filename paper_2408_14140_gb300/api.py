@@ -53,7 +53,8 @@ EXPORTS = ["ib_ctx_create", "ib_ctx_reserve", "ib_ctx_destroy", "ib_ctx_status",
            "ib_batch_multidirect_forcing", "ib_batch_volume_integrals", "ib_batch_collide_update",
            "particle_volume_integrals_ellipsoid", "particle_drag_force",
            "ib_batch_table_create", "ib_batch_table_destroy", "ib_batch_table_multidirect_forcing",
-           "ib_batch_table_volume_integrals", "ib_batch_table_collide_update", "ib_ctx_set_spread_mode"]
+           "ib_batch_table_volume_integrals", "ib_batch_table_collide_update", "ib_ctx_set_spread_mode",
+           "ib_ctx_set_gather"]
 
 
 class IBError(RuntimeError):
@@ -127,6 +128,7 @@ def load(path: str = LIB_PATH):
         "ib_batch_volume_integrals": (i, [p, i, p, p, p, p, p, p]),
         "ib_batch_collide_update": (i, [p, i, p, p, p, d, p, p, p, p, p, p, p, p]),
         "ib_ctx_set_spread_mode": (i, [p, i]),
+        "ib_ctx_set_gather": (i, [p, i, i]),
         "ib_batch_table_create": (i, [p, i, p, i, p, ctypes.POINTER(p)]),
         "ib_batch_table_destroy": (i, [p]),
         "ib_batch_table_multidirect_forcing": (i, [p, p, p, p, i, d, i, i, p, p]),
@@ -238,6 +240,11 @@ class Context:
         """Spreading form: "gather" (deterministic, the default) or "atomic"
         (warp-aggregated atomic additions; see gbib.h)."""
         self._check(self.lib.ib_ctx_set_spread_mode(self.handle, SPREAD_MODES[mode]))
+
+    def set_gather(self, ctas_per_sm: int = 0, stage: int = 0):
+        """Wavefront gather layout: resident CTAs per SM and staged candidates
+        per tile (0: the defaults; see gbib.h).  Results do not change."""
+        self._check(self.lib.ib_ctx_set_gather(self.handle, int(ctas_per_sm), int(stage)))
 
     def set_field_wait(self, event):
         """Make the forcing calls on this context wait for a torch.cuda.Event

@@ -434,6 +434,8 @@ int ib_ctx_create(ib_ctx **ctx, size_t workspace_bytes) {
     c->pass_kernels = IB_PASSES_AUTO;
     c->vol_split = 0;  // automatic
     c->spread_mode = IB_SPREAD_GATHER;
+    c->gather_ctas = 0;
+    c->gather_stage = 0;
     c->field_wait = nullptr;
     for (int k = 0; k < ib_ctx::kStageSlots; ++k) {
         c->stage_ptr[k] = nullptr;
@@ -494,6 +496,16 @@ int ib_ctx_set_spread_mode(ib_ctx *c, int mode) {
     if (!c) return set_error(IB_ERR_INVALID, "ctx is NULL");
     if (mode != IB_SPREAD_GATHER && mode != IB_SPREAD_ATOMIC) return set_error(IB_ERR_INVALID, "spread mode %d", mode);
     c->spread_mode = mode;
+    return IB_OK;
+}
+
+int ib_ctx_set_gather(ib_ctx *c, int ctas_per_sm, int stage) {
+    if (!c) return set_error(IB_ERR_INVALID, "ctx is NULL");
+    if (ctas_per_sm < 0 || ctas_per_sm > 32) return set_error(IB_ERR_INVALID, "gather CTAs per SM %d", ctas_per_sm);
+    if (stage != 0 && (stage < 32 || stage > 256 || stage % 32))
+        return set_error(IB_ERR_INVALID, "gather staging %d: 0 or a multiple of 32 in [32, 256]", stage);
+    c->gather_ctas = ctas_per_sm;
+    c->gather_stage = stage;
     return IB_OK;
 }
 

@@ -152,6 +152,8 @@ struct ib_ctx {
     int pass_kernels;    // IB_PASSES_* of the sequential order
     int vol_split;       // CTAs per particle of the volume integrals (0: one resident wave)
     int spread_mode;     // IB_SPREAD_GATHER (deterministic) or IB_SPREAD_ATOMIC
+    int gather_ctas;     // wavefront gather CTAs per SM (0: as many as fit)
+    int gather_stage;    // candidates a gather CTA stages (0: the largest capacity)
     void *field_wait;    // cudaEvent_t waited on before the forcing passes (nullable)
     // pinned staging ring for the case tables of batch calls: a slot is
     // reused only after the copy that last read it has run (its event)

@@ -1138,6 +1138,7 @@ struct PassArgs {
     int Ns;
     int L0;  // first wavefront the persistent kernel processes
     int atomic;  // spread with warp-aggregated atomics instead of the tile gather
+    int stage;   // candidates a gather CTA stages in shared memory (larger tiles read memory)
     double dt, inv_dt;  // inv_dt = 1 / dt, formed on the host
     Barrier bar;
     DevStatus *st;
@@ -1222,10 +1223,16 @@ constexpr size_t level_stage_bytes() {
     return tile_stage_bytes<T>() + (size_t)kLevPairs * sizeof(uint32_t);
 }
 
+// The same for a staging capacity of `stage` candidates (ib_ctx_set_gather).
+template <typename T>
+size_t level_stage_bytes(int stage) {
+    return (size_t)stage * 16 * sizeof(T) + (size_t)kLevPairs * sizeof(uint32_t);
+}
+
 template <typename T, int KW>
 __device__ __forceinline__ void gather_tile_level(const CaseTab &ct, int cs, const Slots &sl, const PS<T> *wts,
                                                   const PS<T> *A_src, double inv_dt, PS<T> *sw, PS<T> *sA,
-                                                  uint32_t *sp) {
+                                                  uint32_t *sp, int stage) {
     using S = PS<T>;
     const DevCase cd = ct.get(sl.geo_case[cs]);
     const DevGrid &g = cd.g;
@@ -1241,7 +1248,7 @@ __device__ __forceinline__ void gather_tile_level(const CaseTab &ct, int cs, con
     const int np = (int)(sl.poff[dim.w + nc] - pb);
     const int2 *band = sl.band + pb;
     const uint32_t *pairs = sl.pairs + pb;
-    const bool staged = nc <= TileStage<T>::N, pstaged = np <= kLevPairs;
+    const bool staged = nc <= stage, pstaged = np <= kLevPairs;
     auto cell_index = [&](int cell) {
         const int tx = cell & 7, ty = (cell >> 3) & 7, tz = cell >> 6;
         return ((long long)wrap_add(lo.z, tz, g.n[2]) * g.n[1] + wrap_add(lo.y, ty, g.n[1])) * g.n[0] +
@@ -1373,9 +1380,10 @@ __device__ __forceinline__ void gather_tile_level(const CaseTab &ct, int cs, con
 template <typename T, int KER>
 __global__ void __launch_bounds__(kGatherThreads, sizeof(T) == 4 ? 5 : 4) k_gather_level(PassArgs<T> a, int L) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    PS<T> *sw = (PS<T> *)smem_raw;                      // [N][12]
-    PS<T> *sA = sw + (size_t)TileStage<T>::N * 12;      // [N][4]
-    uint32_t *sp = (uint32_t *)(sA + (size_t)TileStage<T>::N * 4);  // [kLevPairs]
+    const int stage = a.stage;                           // staged candidates per tile
+    PS<T> *sw = (PS<T> *)smem_raw;                      // [stage][12]
+    PS<T> *sA = sw + (size_t)stage * 12;                // [stage][4]
+    uint32_t *sp = (uint32_t *)(sA + (size_t)stage * 4);  // [kLevPairs]
     const int nl = *a.nlev;
     const int s0 = L < nl ? a.lev_sbeg[L] : 0, s1 = L < nl ? a.lev_sbeg[L + 1] : 0;
     if (s0 + (int)blockIdx.x >= s1) {
@@ -1394,7 +1402,8 @@ __global__ void __launch_bounds__(kGatherThreads, sizeof(T) == 4 ? 5 : 4) k_gath
     for (int r = 0;; ++r) {
         const int j = (kSnake && (r & 1)) ? (r + 1) * G - 1 - i : r * G + i;
         if (j >= nt) break;
-        gather_tile_level<T, Kernel<KER>::W>(a.ct, a.tperm[s0 + j], a.sl, a.ms.wts, a.ms.A, a.inv_dt, sw, sA, sp);
+        gather_tile_level<T, Kernel<KER>::W>(a.ct, a.tperm[s0 + j], a.sl, a.ms.wts, a.ms.A, a.inv_dt, sw, sA, sp,
+                                             stage);
     }
 }
 
@@ -1803,6 +1812,9 @@ static int run_mdf(ib_ctx *ctx, Arena &ar, const CaseTab &ct, const ib_particles
     a.bar = bar;
     a.st = ctx->status;
     a.atomic = atomic ? 1 : 0;
+    // staging capacity of the wavefront gather (a layout choice: the sums
+    // are the same staged or not)
+    a.stage = ctx->gather_stage > 0 && ctx->gather_stage < TileStage<T>::N ? ctx->gather_stage : TileStage<T>::N;
     // wavefronts enqueued as separate kernels: the count the last call on this
     // context copied to a pinned host word (read without synchronising: an
     // aligned 4-byte word is either the old or the new count; a short count
@@ -1814,12 +1826,14 @@ static int run_mdf(ib_ctx *ctx, Arena &ar, const CaseTab &ct, const ib_particles
     PhaseTimer tpass(ctx, IB_PHASE_MDF_PASSES, s);
     {
         const int gi = grid_blocks(M, kInterpThreads, ctx->sm_count);
-        const size_t gsm = level_stage_bytes<T>();
+        const size_t gsm = level_stage_bytes<T>(a.stage);
         cudaFuncSetAttribute(k_gather_level<T, KER>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsm);
         // one resident wave of gather CTAs (grid-stride over the wavefront's tiles)
         int gper = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&gper, k_gather_level<T, KER>, kGatherThreads, gsm);
-        const int gg = ctx->sm_count * (gper > 0 ? gper : 1);
+        if (gper < 1) gper = 1;
+        if (ctx->gather_ctas > 0 && ctx->gather_ctas < gper) gper = ctx->gather_ctas;
+        const int gg = ctx->sm_count * gper;
         // every level kernel after the first is a programmatic dependent of
         // the one before it (see k_interp_level)
         cudaLaunchAttribute pdl[1];

@@ -223,8 +223,13 @@ def test_autotune_on_a_batch_keeps_results(api):
     assert torch.equal(outs["wavefront"][1], outs["groups"][1])
     autotune_key[0] = "tuned"
     res = autotune.tune([ctx], step, warmup=1, reps=2, steps_per_rep=1)
+    step()  # once more with the tuned choice set
     ctx.status()
-    assert res["choice"]["pass_kernels"] in ("wavefront", "groups")
-    assert res["choice"]["volume_split"] in (0, 4, 8, 16)
-    assert len(res["table"]) == 8 and all(ms > 0 for _, ms in res["table"])
+    for k, v in res["choice"].items():
+        assert v in autotune.SPACE[k]
+    assert len(res["table"]) >= 1 + sum(len(v) - 1 for v in autotune.SPACE.values())
+    assert all(ms > 0 for _, ms in res["table"])
+    for a, b in zip(outs["tuned"][0], outs["wavefront"][0]):
+        assert torch.equal(a, b)
+    assert torch.equal(outs["tuned"][1], outs["wavefront"][1])
     ctx.close()
