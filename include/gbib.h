@@ -409,6 +409,35 @@ GBIB_API int particle_volume_integrals_static(const ib_grid *grid, const void *u
                                               double *Iu, double *Irxu,
                                               double *vol, void *stream);
 
+/* ---- the fluid step around the forcing, one periodic level --------------
+ * Sec. 3.1 on a uniform periodic grid: velocity at cell centres
+ * ([3][n2][n1][n0], grid precision), pressure at nodes ([n2][n1][n0], grid
+ * precision; node (i, j, k) is the lower corner of cell (i, j, k)).  The
+ * gradient of a nodal field at a cell centre averages the four node
+ * differences across the cell; the divergence of a cell field at a node is
+ * its negative adjoint.  The implicit solves are exact in Fourier space, so
+ * every n[a] must be a power of two in [16, 1024] (else IB_ERR_UNSUPPORTED).
+ * Workspace: two complex grid fields (predictor), one (projection).
+ *
+ * fluid_predictor -- Step 1, Eq. (31): writes u_star = u~*,n+1 from
+ *   (I - nu dt/2 L) u~* = u^n + dt (-div(u u)^{n+1/2} - grad p^{n-1/2} / rho_f
+ *                                   + (nu/2) L u^n + g),   nu = mu / rho_f,
+ *   L the 7-point cell Laplacian, div(u u)^{n+1/2} a second-order Godunov edge
+ *   extrapolation (monotonized-central limited slopes, upwinded by the Burgers
+ *   Riemann solution of the normal states).  u (u^n), p (p^{n-1/2}) are read;
+ *   g[3] is a host array.  u_star must not alias u.
+ * level_projection -- Step 3, Eqs. (ns_lp1)-(ns_lp3): with V = u / dt +
+ *   grad p / rho_f, solves div((1/rho_f) grad p') = div V (exactly, the
+ *   divergence-free part's null modes set to 0) and writes
+ *   u = dt (V - grad p' / rho_f) (divergence-free to rounding) and p = p'
+ *   (p^{n+1/2}), both in place.
+ * IB_ERR_INVALID for NULL arrays or rho_f <= 0, mu < 0, dt <= 0, non-finite g. */
+GBIB_API int fluid_predictor(ib_ctx *ctx, const ib_grid *grid, const void *u, const void *p,
+                             double rho_f, double mu, const double *g, double dt, void *u_star,
+                             void *stream);
+GBIB_API int level_projection(ib_ctx *ctx, const ib_grid *grid, void *u, void *p, double rho_f,
+                              double dt, void *stream);
+
 /* ---- marker force and torque (Eqs. particle1, particle2, first terms) ---
  * F_ib[p] = -rho_f sum_l F[l] dV[l],  T_ib[p] = -rho_f sum_l R[l] x F[l] dV[l]
  * over the markers of particle p; FP64, overwritten.                      */

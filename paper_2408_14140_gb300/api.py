@@ -54,7 +54,7 @@ EXPORTS = ["ib_ctx_create", "ib_ctx_reserve", "ib_ctx_destroy", "ib_ctx_status",
            "particle_volume_integrals_ellipsoid", "particle_drag_force",
            "ib_batch_table_create", "ib_batch_table_destroy", "ib_batch_table_multidirect_forcing",
            "ib_batch_table_volume_integrals", "ib_batch_table_collide_update", "ib_ctx_set_spread_mode",
-           "ib_ctx_set_gather"]
+           "ib_ctx_set_gather", "fluid_predictor", "level_projection"]
 
 
 class IBError(RuntimeError):
@@ -129,6 +129,8 @@ def load(path: str = LIB_PATH):
         "ib_batch_collide_update": (i, [p, i, p, p, p, d, p, p, p, p, p, p, p, p]),
         "ib_ctx_set_spread_mode": (i, [p, i]),
         "ib_ctx_set_gather": (i, [p, i, i]),
+        "fluid_predictor": (i, [p, p, p, p, d, d, ctypes.POINTER(d), d, p, p]),
+        "level_projection": (i, [p, p, p, p, d, d, p]),
         "ib_batch_table_create": (i, [p, i, p, i, p, ctypes.POINTER(p)]),
         "ib_batch_table_destroy": (i, [p]),
         "ib_batch_table_multidirect_forcing": (i, [p, p, p, p, i, d, i, i, p, p]),
@@ -245,6 +247,33 @@ class Context:
         """Wavefront gather layout: resident CTAs per SM and staged candidates
         per tile (0: the defaults; see gbib.h).  Results do not change."""
         self._check(self.lib.ib_ctx_set_gather(self.handle, int(ctas_per_sm), int(stage)))
+
+    def fluid_predictor(self, u, p, h, rho_f, mu, g, dt, u_star=None, origin=(0.0, 0.0, 0.0), stream=None):
+        """Step 1 (Eq. 31): u~* from u^n [3, n2, n1, n0] and p^{n-1/2} [n2, n1, n0]
+        (nodes) on a periodic power-of-two grid; returns u_star."""
+        prec = IB_F64 if u.dtype == torch.float64 else IB_F32
+        n = (u.shape[3], u.shape[2], u.shape[1])
+        _need(u, "u", u.dtype, (3, n[2], n[1], n[0]))
+        _need(p, "p", u.dtype, (n[2], n[1], n[0]))
+        if u_star is None:
+            u_star = torch.empty_like(u)
+        _need(u_star, "u_star", u.dtype, tuple(u.shape))
+        gr = make_grid(n, h, origin, prec)
+        gv = (ctypes.c_double * 3)(*[float(x) for x in g])
+        self._call(self.lib.fluid_predictor, self.handle, ctypes.byref(gr), _ptr(u), _ptr(p), float(rho_f),
+                   float(mu), gv, float(dt), _ptr(u_star), _stream(stream))
+        return u_star
+
+    def level_projection(self, u, p, h, rho_f, dt, origin=(0.0, 0.0, 0.0), stream=None):
+        """Step 3 (Eqs. ns_lp1-3) in place: u* -> u^{n+1}, p^{n-1/2} -> p^{n+1/2}."""
+        prec = IB_F64 if u.dtype == torch.float64 else IB_F32
+        n = (u.shape[3], u.shape[2], u.shape[1])
+        _need(u, "u", u.dtype, (3, n[2], n[1], n[0]))
+        _need(p, "p", u.dtype, (n[2], n[1], n[0]))
+        gr = make_grid(n, h, origin, prec)
+        self._call(self.lib.level_projection, self.handle, ctypes.byref(gr), _ptr(u), _ptr(p), float(rho_f),
+                   float(dt), _stream(stream))
+        return u, p
 
     def set_field_wait(self, event):
         """Make the forcing calls on this context wait for a torch.cuda.Event
