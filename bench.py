@@ -862,6 +862,8 @@ def run_gpu(args):
             del rv
     if world == 1 and not args.no_dense:
         line["dense"] = run_dense(args, device, flush, hbm, hbm_src)
+    if world == 1 and not args.no_single_level:
+        line["single_level_step"] = run_single_level(args, device, flush, hbm)
     if world == 1 and not args.no_batched:
         line["batched"] = run_batched(args, device, hbm)
     if world == 1 and not args.no_serve:
@@ -886,6 +888,60 @@ def run_gpu(args):
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
+
+
+class LevelRunner(Runner):
+    """The whole single-level step of Sec. 3.1 on the bench workload: the
+    momentum predictor (Step 1), the hot path (Step 2 with the volume
+    integrals, reductions and particle update) and the level projection
+    (Step 3), one after another on the same field."""
+
+    def __init__(self, case, prec, device):
+        super().__init__(case, prec, device)
+        torch = self.torch
+        n = case.n
+        self.p = torch.zeros((n[2], n[1], n[0]), dtype=self.u.dtype, device=device)
+        self.u_star = torch.empty_like(self.u)
+        self.mu = 1e-3
+
+    def step(self):
+        c, ctx, torch = self.case, self.ctx, self.torch
+        ctx.fluid_predictor(self.u, self.p, c.h, c.rho_f, self.mu, (0.0, 0.0, 0.0), c.dt, u_star=self.u_star)
+        self.u, self.u_star = self.u_star, self.u
+        super().step()
+        ctx.level_projection(self.u, self.p, c.h, c.rho_f, c.dt)
+
+
+def run_single_level(args, device, flush, hbm):
+    """NEXT row: the full single-level step on the 256^3 / 64 x D24 workload,
+    FP32 and FP64 fields, CUDA-graph replayed.  Compulsory bytes of the fluid
+    calls: the predictor reads u (3 s N) and p (s N) and writes u* (3 s N);
+    the projection reads and writes u and p (8 s N); the FFT passes between
+    are the solver's own traffic."""
+    from paper_2408_14140_gb300 import api
+    case = make_case(seed=0)
+    N = int(np.prod(case.n))
+    out = {"workload": WORKLOAD_NAME + "+predictor+projection", "grid": list(case.n),
+           "l2": "flushed (512 MiB write) between timed steps"}
+    for prec, name in ((api.IB_F32, "fp32"), (api.IB_F64, "fp64")):
+        r = LevelRunner(case, prec, device)
+        ms, graphed, _ = time_steps(r, max(3, min(args.steps // 4, 10)), args.warmup, flush, not args.no_graph)
+        kt = kernel_timing(r, 3, flush)
+        s = 8 if prec == api.IB_F64 else 4
+        step_s = sum(ms) / 1000.0 / len(ms)
+        o = {"ms_per_step": step_s * 1000.0, "value": case.M * case.Ns / step_s, "unit": "marker-updates/s",
+             "steps": len(ms), "launch": "cuda-graph replay" if graphed else "eager",
+             "phases_us": {k: round(v[0] / v[1] * 1000.0, 2) for k, v in kt.items()}}
+        for ph, nbytes in (("fluid_predictor", 7 * s * N), ("fluid_projection", 8 * s * N)):
+            if ph in kt:
+                dur = kt[ph][0] / kt[ph][1] / 1000.0
+                o[ph] = {"algorithmic_bytes": nbytes, "duration_us": dur * 1e6,
+                         "achieved_gbs": nbytes / dur / 1e9, "frac_of_peak": nbytes / dur / 1e9 / hbm}
+        out[name] = o
+        r.ctx.close()
+        r.ctx_v.close()
+        del r
+    return out
 
 
 def run_dense(args, device, flush, hbm, hbm_src):
@@ -970,6 +1026,7 @@ def main():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-dense", action="store_true")
+    ap.add_argument("--no-single-level", action="store_true")
     ap.add_argument("--no-replays", action="store_true")
     ap.add_argument("--serve-rate", type=float, default=200.0)
     ap.add_argument("--serve-seconds", type=float, default=2.0)

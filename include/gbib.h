@@ -142,7 +142,9 @@ GBIB_API int ib_ctx_sm_count(const ib_ctx *ctx);
 #define IB_PHASE_COLLIDE 6     /* particle_collide_update                   */
 #define IB_PHASE_MDF_INTERP 7  /* each wavefront-pass interpolation kernel  */
 #define IB_PHASE_MDF_GATHER 8  /* each wavefront-pass gather kernel         */
-#define IB_PHASE_COUNT 9
+#define IB_PHASE_FLUID_PREDICTOR 9   /* fluid_predictor                   */
+#define IB_PHASE_FLUID_PROJECTION 10 /* level_projection                  */
+#define IB_PHASE_COUNT 11
 GBIB_API int ib_ctx_set_timing(ib_ctx *ctx, int enable);
 GBIB_API int ib_ctx_read_timing(ib_ctx *ctx, int phase, double *ms_total,
                                 int *launches);

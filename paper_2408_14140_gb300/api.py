@@ -41,7 +41,8 @@ PASSES = {"auto": 0, "wavefront": 1, "resident": 2, "groups": 3}
 SPREAD_MODES = {"gather": 0, "atomic": 1}
 
 PHASES = {"mdf_prep": 0, "mdf_passes": 1, "spread": 2, "interp": 3, "volume": 4,
-          "force": 5, "collide": 6, "mdf_interp": 7, "mdf_gather": 8}
+          "force": 5, "collide": 6, "mdf_interp": 7, "mdf_gather": 8, "fluid_predictor": 9,
+          "fluid_projection": 10}
 
 EXPORTS = ["ib_ctx_create", "ib_ctx_reserve", "ib_ctx_destroy", "ib_ctx_status",
            "ib_last_error", "ib_workspace_needed", "ib_ctx_sm_count",

@@ -395,6 +395,7 @@ static int run_predictor(ib_ctx *ctx, const ib_grid *grid, const void *u, const 
     if (!ar.ok()) return oom_error(ar.used, ar.cap);
     const int nb = elem_blocks(N, ctx->sm_count);
     const double nu = mu / rho_f;
+    PhaseTimer tm(ctx, IB_PHASE_FLUID_PREDICTOR, s);
     k_predictor_rhs<T><<<nb, 256, 0, s>>>(dg, (const T *)u, (const T *)p, rho_f, nu, g[0], g[1], g[2], dt, c0, c1);
     for (C *c : {c0, c1}) {
         int rc = fft3<T>(ctx, c, grid->n, 0, s);
@@ -417,6 +418,7 @@ static int run_projection(ib_ctx *ctx, const ib_grid *grid, void *u, void *p, do
     C *c = ar.take<C>(N);
     if (!ar.ok()) return oom_error(ar.used, ar.cap);
     const int nb = elem_blocks(N, ctx->sm_count);
+    PhaseTimer tm(ctx, IB_PHASE_FLUID_PROJECTION, s);
     k_projection_div<T><<<nb, 256, 0, s>>>(dg, (const T *)u, (const T *)p, rho_f, dt, c);
     int rc = fft3<T>(ctx, c, grid->n, 0, s);
     if (rc) return rc;
