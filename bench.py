@@ -666,15 +666,29 @@ def run_serving(args):
     results = {}
     cfg = serve.ServeConfig(rate=args.serve_rate, seconds=args.serve_seconds, fp64_fraction=0.25, seed=0)
     base = serve.make_trace(cfg)
-    for name, prec in (("mixed", None), ("fp32", api.IB_F32), ("fp64", api.IB_F64)):
+    # a short untimed trace first: the first served requests of a process pay
+    # one-time costs (contexts' workspace growth, pinned staging)
+    warm = serve.ServeConfig(rate=args.serve_rate, seconds=0.3, fp64_fraction=0.5, seed=1)
+    wsrv = serve.Server(warm)
+    wsrv.run(serve.make_trace(warm))
+    wsrv.close()
+    graphs = serve.ServeConfig(rate=args.serve_rate, seconds=args.serve_seconds, fp64_fraction=0.25, seed=0,
+                               graph_after=4)
+    for name, prec, c in (("mixed", None, cfg), ("fp32", api.IB_F32, cfg), ("fp64", api.IB_F64, cfg),
+                          ("mixed_graph_replay", None, graphs)):
         trace = [serve.Request(r.rid, r.arrival, r.case, r.prec if prec is None else prec) for r in base]
-        srv = serve.Server(cfg)
+        srv = serve.Server(c)
         t0 = time.perf_counter()
         srv.run(trace)
         wall = time.perf_counter() - t0
         srv.close()
-        s = serve.summarize(trace, cfg, wall)
+        s = serve.summarize(trace, c, wall)
         s.update(srv.stats())
+        s["graph_after"] = c.graph_after
+        for p_, nm in ((api.IB_F32, "fp32"), (api.IB_F64, "fp64")):
+            lat = np.array([r.latency for r in trace if r.prec == p_ and r.latency is not None])
+            if lat.size:
+                s["p99_ms_" + nm + "_requests"] = float(np.percentile(lat, 99) * 1e3)
         s["active_peak"] = srv.active_peak
         s["fp64_requests"] = sum(r.prec == api.IB_F64 for r in trace)
         out[name] = s

@@ -370,6 +370,15 @@ typedef struct ib_batch_table ib_batch_table;
 GBIB_API int ib_batch_table_create(ib_ctx *ctx, int ncases, const ib_case *cases, int P,
                                    const ib_phys *phys, ib_batch_table **table);
 GBIB_API int ib_batch_table_destroy(ib_batch_table *table);
+/* Re-points a table at another batch (validated as at creation): the new
+ * case table is uploaded asynchronously on `stream` from a pinned copy the
+ * table owns, so calls enqueued on `stream` afterwards see it and calls
+ * before it see the old one; only when the new batch outgrows the table's
+ * memory does it reallocate (waiting for the device).  Not capturable.  A
+ * CUDA graph captured with the table keeps reading its memory, so replay
+ * such a graph only while the table still describes the batch it captured. */
+GBIB_API int ib_batch_table_update(ib_batch_table *table, int ncases, const ib_case *cases, int P,
+                                   const ib_phys *phys, void *stream);
 GBIB_API int ib_batch_table_multidirect_forcing(ib_ctx *ctx, const ib_batch_table *table,
                                                 const ib_particles *parts, const ib_markers *marks,
                                                 int Ns, double dt, int delta, int order,

@@ -55,7 +55,7 @@ EXPORTS = ["ib_ctx_create", "ib_ctx_reserve", "ib_ctx_destroy", "ib_ctx_status",
            "particle_volume_integrals_ellipsoid", "particle_drag_force",
            "ib_batch_table_create", "ib_batch_table_destroy", "ib_batch_table_multidirect_forcing",
            "ib_batch_table_volume_integrals", "ib_batch_table_collide_update", "ib_ctx_set_spread_mode",
-           "ib_ctx_set_gather", "fluid_predictor", "level_projection"]
+           "ib_ctx_set_gather", "fluid_predictor", "level_projection", "ib_batch_table_update"]
 
 
 class IBError(RuntimeError):
@@ -134,6 +134,7 @@ def load(path: str = LIB_PATH):
         "level_projection": (i, [p, p, p, p, d, d, p]),
         "ib_batch_table_create": (i, [p, i, p, i, p, ctypes.POINTER(p)]),
         "ib_batch_table_destroy": (i, [p]),
+        "ib_batch_table_update": (i, [p, i, p, i, p, p]),
         "ib_batch_table_multidirect_forcing": (i, [p, p, p, p, i, d, i, i, p, p]),
         "ib_batch_table_volume_integrals": (i, [p, p, p, p, p, p, p]),
         "ib_batch_table_collide_update": (i, [p, p, p, d, p, p, p, p, p, p, p, p]),
@@ -614,6 +615,22 @@ class BatchTable:
         if rc != IB_OK:
             raise IBError(rc, self.lib.ib_last_error().decode())
         self.handle = h
+        self.P = int(P)
+        self.ncases = len(cases)
+
+    def update(self, fields, hs, ranges, P, phys=None, origins=None, f_outs=None, stream=None):
+        """Point the table at another batch: an asynchronous upload on
+        ``stream`` (see ``ib_batch_table_update``)."""
+        cases = case_array(fields, hs, ranges, origins, f_outs)
+        ph = None
+        if phys is not None:
+            per_case = phys if len(phys) == len(cases) and not isinstance(phys[0], (int, float)) else \
+                [phys] * len(cases)
+            ph = (Phys * len(cases))(*[_phys_struct(x) for x in per_case])
+        rc = self.lib.ib_batch_table_update(self.handle, len(cases), cases, int(P), ph, _stream(stream))
+        if rc != IB_OK:
+            raise IBError(rc, self.lib.ib_last_error().decode())
+        self._keep = (list(fields), list(f_outs) if f_outs is not None else None)
         self.P = int(P)
         self.ncases = len(cases)
 

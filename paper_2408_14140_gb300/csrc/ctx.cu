@@ -162,11 +162,12 @@ int table_cases(const ib_batch_table *t, int P, CaseTab &ct) {
 
 }  // namespace gbib
 
-extern "C" int ib_batch_table_create(ib_ctx *ctx, int ncases, const ib_case *cases, int P, const ib_phys *phys,
-                                     ib_batch_table **out) {
+// Validates the cases and uploads the table into t's memory on stream s,
+// growing it first if needed (a synchronous reallocation); the host copy sits
+// in t's pinned stage, reused once the previous upload from it has run.
+static int table_upload(ib_batch_table *t, int ncases, const ib_case *cases, int P, const ib_phys *phys,
+                        cudaStream_t s) {
     using namespace gbib;
-    if (!ctx || !out) return set_error(IB_ERR_INVALID, "ctx or out is NULL");
-    *out = nullptr;
     if (P < 0) return set_error(IB_ERR_INVALID, "P must be >= 0");
     for (int c = 0; c < ncases && cases; ++c) {
         if (!cases[c].u) return set_error(IB_ERR_INVALID, "case %d: NULL field", c);
@@ -177,32 +178,49 @@ extern "C" int ib_batch_table_create(ib_ctx *ctx, int ncases, const ib_case *cas
     unsigned long long toff = 0;
     int rc = fill_case_table(ncases, cases, P, 1, phys, h, toff);
     if (rc) return rc;
-    std::vector<int> pcase(P > 0 ? P : 1, 0);
-    for (int c = 0; c < ncases; ++c)
-        for (int p = cases[c].p_begin; p < cases[c].p_end; ++p) pcase[p] = c;
-    const size_t cbytes = ((sizeof(DevCase) * ncases + 255) / 256) * 256;
-    const size_t pbytes = sizeof(int) * pcase.size();
-    ib_batch_table *t = new (std::nothrow) ib_batch_table();
-    if (!t) return set_error(IB_ERR_OOM, "table");
-    if (cudaGetDevice(&t->device) != cudaSuccess || cudaMalloc(&t->mem, cbytes + pbytes) != cudaSuccess) {
-        delete t;
-        return set_error(IB_ERR_OOM, "case table: %s", cudaGetErrorString(cudaGetLastError()));
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || (t->mem && dev != t->device))
+        return set_error(IB_ERR_INVALID, "table belongs to device %d, current device is %d", t->device, dev);
+    if (!t->mem || (size_t)ncases > t->cap_cases || (size_t)(P > 0 ? P : 1) > t->cap_p) {
+        // grow with headroom (rare: later updates of similar batches fit)
+        const size_t cc = (size_t)ncases * 2 + 16, cp = (size_t)(P > 0 ? P : 1) * 2 + 64;
+        const size_t cbytes = ((sizeof(DevCase) * cc + 255) / 256) * 256;
+        void *mem = nullptr;
+        if (cudaMalloc(&mem, cbytes + sizeof(int) * cp) != cudaSuccess)
+            return set_error(IB_ERR_OOM, "case table: %s", cudaGetErrorString(cudaGetLastError()));
+        if (t->mem) {
+            cudaDeviceSynchronize();  // work queued on the old table has finished
+            cudaFree(t->mem);
+        }
+        t->mem = mem;
+        t->cap_cases = cc;
+        t->cap_p = cp;
+        t->device = dev;
     }
+    const size_t cbytes = ((sizeof(DevCase) * t->cap_cases + 255) / 256) * 256;
+    const size_t hb = sizeof(DevCase) * ncases, pb = sizeof(int) * (size_t)(P > 0 ? P : 1);
+    if (t->staged) cudaEventSynchronize(t->staged);  // the previous upload has read the stage
+    else if (cudaEventCreateWithFlags(&t->staged, cudaEventDisableTiming) != cudaSuccess)
+        return set_error(IB_ERR_CUDA, "table event: %s", cudaGetErrorString(cudaGetLastError()));
+    if (t->stage_cap < hb + pb) {
+        if (t->stage) cudaFreeHost(t->stage);
+        t->stage = nullptr;
+        t->stage_cap = 0;
+        if (cudaHostAlloc(&t->stage, hb + pb, cudaHostAllocDefault) != cudaSuccess)
+            return set_error(IB_ERR_CUDA, "table staging: %s", cudaGetErrorString(cudaGetLastError()));
+        t->stage_cap = hb + pb;
+    }
+    memcpy(t->stage, h.data(), hb);
+    int *ps = (int *)((char *)t->stage + hb);
+    for (int p = 0; p < P; ++p) ps[p] = 0;
+    for (int c = 0; c < ncases; ++c)
+        for (int p = cases[c].p_begin; p < cases[c].p_end; ++p) ps[p] = c;
     DevCase *d = (DevCase *)t->mem;
     int *dp = (int *)((char *)t->mem + cbytes);
-    // upload on a private non-blocking stream: the copy waits for nothing the
-    // caller has queued (not even on the legacy default stream)
-    cudaStream_t us = nullptr;
-    cudaError_t e = cudaStreamCreateWithFlags(&us, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(d, h.data(), sizeof(DevCase) * ncases, cudaMemcpyHostToDevice, us);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(dp, pcase.data(), pbytes, cudaMemcpyHostToDevice, us);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(us);
-    if (us) cudaStreamDestroy(us);
-    if (e != cudaSuccess) {
-        cudaFree(t->mem);
-        delete t;
-        return set_error(IB_ERR_CUDA, "case table upload: %s", cudaGetErrorString(e));
-    }
+    cudaError_t e = cudaMemcpyAsync(d, t->stage, hb, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dp, ps, pb, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaEventRecord(t->staged, s);
+    if (e != cudaSuccess) return set_error(IB_ERR_CUDA, "case table upload: %s", cudaGetErrorString(e));
     t->P = P;
     t->ncases = ncases;
     t->prec = cases[0].grid.prec;
@@ -212,17 +230,54 @@ extern "C" int ib_batch_table_create(ib_ctx *ctx, int ncases, const ib_case *cas
     t->ct.ncases = ncases;
     t->ct.ntiles = (long long)toff;
     t->ct.one = h[0];
+    return IB_OK;
+}
+
+extern "C" int ib_batch_table_create(ib_ctx *ctx, int ncases, const ib_case *cases, int P, const ib_phys *phys,
+                                     ib_batch_table **out) {
+    using namespace gbib;
+    if (!ctx || !out) return set_error(IB_ERR_INVALID, "ctx or out is NULL");
+    *out = nullptr;
+    ib_batch_table *t = new (std::nothrow) ib_batch_table();
+    if (!t) return set_error(IB_ERR_OOM, "table");
+    // upload on a private non-blocking stream: the copy waits for nothing the
+    // caller has queued (not even on the legacy default stream)
+    cudaStream_t us = nullptr;
+    if (cudaStreamCreateWithFlags(&us, cudaStreamNonBlocking) != cudaSuccess) {
+        delete t;
+        return set_error(IB_ERR_CUDA, "table stream: %s", cudaGetErrorString(cudaGetLastError()));
+    }
+    int rc = table_upload(t, ncases, cases, P, phys, us);
+    if (rc == IB_OK && cudaStreamSynchronize(us) != cudaSuccess)
+        rc = set_error(IB_ERR_CUDA, "case table upload: %s", cudaGetErrorString(cudaGetLastError()));
+    cudaStreamDestroy(us);
+    if (rc) {
+        ib_batch_table_destroy(t);
+        return rc;
+    }
     *out = t;
     return IB_OK;
+}
+
+extern "C" int ib_batch_table_update(ib_batch_table *t, int ncases, const ib_case *cases, int P,
+                                     const ib_phys *phys, void *stream) {
+    using namespace gbib;
+    if (!t) return set_error(IB_ERR_INVALID, "table is NULL");
+    return table_upload(t, ncases, cases, P, phys, (cudaStream_t)stream);
 }
 
 extern "C" int ib_batch_table_destroy(ib_batch_table *t) {
     if (!t) return IB_OK;
     int cur = -1;
     cudaGetDevice(&cur);
-    if (cur != t->device) cudaSetDevice(t->device);
-    cudaFree(t->mem);  // (cudaFree waits for the device's queued work first)
-    if (cur >= 0 && cur != t->device) cudaSetDevice(cur);
+    if (t->mem && cur != t->device) cudaSetDevice(t->device);
+    if (t->mem) cudaFree(t->mem);  // (cudaFree waits for the device's queued work first)
+    if (t->staged) {
+        cudaEventSynchronize(t->staged);
+        cudaEventDestroy(t->staged);
+    }
+    if (t->stage) cudaFreeHost(t->stage);
+    if (t->mem && cur >= 0 && cur != t->device) cudaSetDevice(cur);
     delete t;
     return IB_OK;
 }

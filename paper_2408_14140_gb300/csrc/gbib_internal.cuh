@@ -171,6 +171,10 @@ struct ib_batch_table {
     int P, ncases, prec;
     int has_phys;        // physical parameters given (needed by the collision update)
     void *mem;           // device: DevCase[ncases], then int pcase[P]
+    size_t cap_cases, cap_p;  // capacity of mem
+    void *stage;         // pinned host copy of the last update (read by its upload)
+    size_t stage_cap;
+    cudaEvent_t staged;  // the last update's upload has read `stage`
     gbib::CaseTab ct;
 };
 

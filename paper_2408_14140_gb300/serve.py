@@ -17,11 +17,12 @@ field precision and are admitted first come, first served within it, while
 the shared device-memory budget and the precision's slot count allow (a
 blocked head of one precision does not hold back the other).  Each loop
 iteration advances every active request by one time step through one
-sequence of batch launches per precision -- the batch's case table uploaded
-once per change of its active set, the precisions on separate streams so
-their steps overlap on the device, and a step replayed from a CUDA graph
-while the active set stays the same -- so requests that arrived at
-different times share the same kernels.  A request that has run all its
+sequence of batch launches per precision -- the batch's case table
+re-uploaded asynchronously once per change of its active set, the
+precisions on separate streams so their steps overlap on the device, and
+(optionally) a step replayed from a CUDA graph while the active set stays
+the same -- so requests that arrived at different times share the same
+kernels.  A request that has run all its
 steps has its particle state copied to pinned host memory; its latency runs
 from its arrival to that copy's completion.
 
@@ -55,8 +56,10 @@ class ServeConfig:
     fp64_fraction: float = 0.0     # share of requests served with FP64 fields
     budget_bytes: int = 32 << 30   # device memory for resident requests
     max_active: int = 64           # active requests per field precision
-    graph_after: int = 2           # replay a group's step from a CUDA graph once its
-                                   # active set has not changed for this many steps (0: never)
+    graph_after: int = 0           # replay a group's step from a CUDA graph once its
+                                   # active set has not changed for this many steps (0: never;
+                                   # on a Poisson stream the set changes every few steps and a
+                                   # capture costs more host time than its replays save)
     volume_split: int = 8          # CTAs per particle of the volume integrals: fixed, so a
                                    # request's sums do not depend on which requests share its batch
     seed: int = 0
@@ -138,7 +141,9 @@ class Group:
     def __init__(self, prec: int, ctx: api.Context, device):
         self.prec = prec
         self.ctx = ctx
-        self.stream = torch.cuda.Stream(device=device)
+        # the FP64 group's steps are the slower ones and set the latency
+        # tail, so its stream gets the higher scheduling priority
+        self.stream = torch.cuda.Stream(device=device, priority=-1 if prec == api.IB_F64 else 0)
         self.active: list[Request] = []
         self.dirty = True
         self.table = None
@@ -146,6 +151,7 @@ class Group:
         self.stable = 0          # steps since the active set last changed
         self.graph_steps = 0     # steps replayed from a graph
         self.eager_steps = 0
+        self.host_s = {"rebuild": 0.0, "eager": 0.0, "capture": 0.0, "replay": 0.0}  # host seconds
 
     def rebuild(self, device):
         """Lay the active requests out as one flat particle/marker set; the
@@ -169,9 +175,10 @@ class Group:
         self.Fc = torch.empty((P, 3), **f64)
         self.I_old = (torch.empty((P, 3), **f64), torch.empty((P, 3), **f64), torch.empty((P,), **f64))
         self.I_new = (torch.empty((P, 3), **f64), torch.empty((P, 3), **f64), torch.empty((P,), **f64))
-        if self.table is not None:
-            self.table.close()
-        self.table = api.BatchTable(self.ctx, self.fields, hs, self.ranges, P, phys=phys)
+        if self.table is None:
+            self.table = api.BatchTable(self.ctx, self.fields, hs, self.ranges, P, phys=phys)
+        else:  # re-upload on the group's stream: no device-wide wait
+            self.table.update(self.fields, hs, self.ranges, P, phys=phys, stream=self.stream)
         self.graph = None
         self.stable = 0
         self.dirty = False
@@ -193,15 +200,21 @@ class Group:
         # every device operation of the group (its allocations included) runs
         # on the group's stream, so it is ordered after the group's last step
         with torch.cuda.stream(self.stream):
+            t0 = time.perf_counter()
             if self.dirty:
                 self.rebuild(device)
+            t1 = time.perf_counter()
+            self.host_s["rebuild"] += t1 - t0
             if self.graph is not None:
                 self.graph.replay()
                 self.graph_steps += 1
+                self.host_s["replay"] += time.perf_counter() - t1
             else:
                 self.launch(cfg)
                 self.eager_steps += 1
                 self.stable += 1
+                t2 = time.perf_counter()
+                self.host_s["eager"] += t2 - t1
                 if cfg.graph_after and self.stable >= cfg.graph_after:
                     # the step's launch sequence, captured once for the steps
                     # that follow while the active set stays the same (the
@@ -211,6 +224,7 @@ class Group:
                         self.launch(cfg)
                     self.graph = g
                     # capture records the work without running it: this step ran eagerly
+                    self.host_s["capture"] += time.perf_counter() - t2
         for r in self.active:
             r.steps_done += 1
 
@@ -244,8 +258,16 @@ class Server:
         with torch.cuda.stream(g.stream):  # the request's memory belongs to its group's stream
             r.u_bg = synth.taylor_green_torch(c.n, self.cfg.U0, c.h, device=self.device, dtype=dt)
             r.u = torch.empty_like(r.u_bg)
-            _, r.parts, r.marks = api.device_case(c.__class__(**{**c.__dict__, "u": np.zeros((3, 1, 1, 1))}),
-                                                  r.prec, self.device)
+
+            # pinned, non-blocking uploads: a pageable copy would make the
+            # host wait for the group's queued steps
+            def up(a, dtype=torch.float64):
+                return torch.as_tensor(np.ascontiguousarray(a)).to(dtype).pin_memory().to(
+                    self.device, non_blocking=True)
+
+            r.parts = dict(Xr=up(c.Xr), Ur=up(c.Ur), Wr=up(c.Wr), radius=up(c.radius), rho_p=up(c.rho_p),
+                           moff=up(c.moff, torch.int32))
+            r.marks = dict(R=up(c.R), dV=up(c.dV))
         self.used += r.bytes
         g.active.append(r)
         g.dirty = True
@@ -284,7 +306,11 @@ class Server:
         pending = list(trace)
         t0 = time.perf_counter()
         now = lambda: time.perf_counter() - t0
-        inflight: list[list[torch.cuda.Event]] = []
+        # each group's steps in flight (events on its stream): a group with
+        # `depth` steps outstanding waits its turn, the other goes on, so one
+        # precision's pace does not gate the other's
+        inflight = {p: [] for p in self.groups}
+        depth = 1 if sync_every_step else 3
         while pending or self.n_waiting() or self.n_active() or self.finishing:
             tnow = now()
             while pending and pending[0].arrival <= tnow:
@@ -297,24 +323,31 @@ class Server:
                     self.admit(q.pop(0))
             self.active_peak = max(self.active_peak, self.n_active())
             if self.n_active():
-                for g in self.groups.values():
+                stepped = False
+                for p, g in self.groups.items():
+                    q = inflight[p]
+                    while q and q[0].query():
+                        q.pop(0)
+                    if not g.active or len(q) >= depth:
+                        continue
                     g.step(cfg, self.device)
-                for g in self.groups.values():
                     for r in [r for r in g.active if r.steps_done >= cfg.steps]:
                         self.retire(r)
-                evs = []
-                for g in self.groups.values():
                     ev = torch.cuda.Event()
                     ev.record(g.stream)
-                    evs.append(ev)
-                inflight.append(evs)
-                # keep the host at most two steps ahead of the device
+                    q.append(ev)
+                    stepped = True
                 if sync_every_step:
-                    for ev in evs:
-                        ev.synchronize()
-                elif len(inflight) > 2:
-                    for ev in inflight.pop(0):
-                        ev.synchronize()
+                    for q in inflight.values():
+                        for ev in q:
+                            ev.synchronize()
+                        q.clear()
+                elif not stepped:
+                    # every active group has `depth` steps outstanding: wait for
+                    # the oldest step of either group (whichever finishes first)
+                    oldest = [q[0] for q in inflight.values() if q]
+                    while oldest and not any(ev.query() for ev in oldest):
+                        time.sleep(20e-6)
             else:
                 self.poll(now)
                 if not self.finishing:
@@ -328,8 +361,13 @@ class Server:
         return trace
 
     def stats(self):
+        host = {}
+        for g in self.groups.values():
+            for k, v in g.host_s.items():
+                host[k] = round(host.get(k, 0.0) + v, 4)
         return {"graph_steps": sum(g.graph_steps for g in self.groups.values()),
-                "eager_steps": sum(g.eager_steps for g in self.groups.values())}
+                "eager_steps": sum(g.eager_steps for g in self.groups.values()),
+                "host_seconds": host}
 
     def close(self):
         torch.cuda.synchronize()

@@ -132,3 +132,23 @@ def test_table_rejects_mismatches(api):
         api.BatchTable(ctx, b.fields, b.hs, b.ranges, b.P + 1)  # ranges must end at P
     table.close()
     ctx.close()
+
+
+def test_table_update_equals_a_fresh_table(api):
+    """A table re-pointed at another batch (asynchronous upload on the stream)
+    computes exactly what a table created for that batch computes."""
+    ctx = api.Context()
+    a = Batch(api, uneven_cases(51), 1)
+    b1, b2 = Batch(api, uneven_cases(52), 1), Batch(api, uneven_cases(52), 1)
+    table = api.BatchTable(ctx, a.fields, a.hs, a.ranges, a.P, phys=a.phys)
+    table_step(ctx, a, table)
+    table.update(b1.fields, b1.hs, b1.ranges, b1.P, phys=b1.phys)  # on the current stream
+    table_step(ctx, b1, table)
+    fresh = api.BatchTable(ctx, b2.fields, b2.hs, b2.ranges, b2.P, phys=b2.phys)
+    table_step(ctx, b2, fresh)
+    ctx.status()
+    for x, y in zip(b1.state(), b2.state()):
+        assert torch.equal(x, y)
+    table.close()
+    fresh.close()
+    ctx.close()

@@ -16,12 +16,15 @@ from paper_2408_14140_gb300 import api, serve, synth
 pytestmark = pytest.mark.gpu
 
 
-@pytest.fixture(scope="module")
-def served():
+@pytest.fixture(scope="module", params=[0, 2], ids=["eager", "graph-replay"])
+def served(request):
+    """The trace served with eager launches, and with each precision's step
+    replayed from a CUDA graph once its active set held for two steps."""
     from paper_2408_14140_gb300 import build
     build.build()
     cfg = serve.ServeConfig(rate=150.0, seconds=0.25, grids=(48, 64), P_max=6, D_lo=8.0, D_hi=14.0,
-                            steps=4, fp64_fraction=0.3, budget_bytes=8 << 30, max_active=16, seed=5)
+                            steps=4, fp64_fraction=0.3, budget_bytes=8 << 30, max_active=16, seed=5,
+                            graph_after=request.param)
     trace = serve.make_trace(cfg)
     srv = serve.Server(cfg)
     srv.run(trace)
