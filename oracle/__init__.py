@@ -10,9 +10,16 @@ The arithmetic lives in ``ib_oracle.c`` (plain C, FP64, compiled with
 module only builds it with gcc and marshals numpy arrays through ctypes.
 Every function cites the passage of the paper it follows in the C source.
 
+The fluid step around the forcing (Sec. 3.1 Steps 1 and 3, one periodic
+level) is in ``fluid.py``, in numpy, with numpy's FFT as its only library
+step.
+
 Parity status: every function is pinned by ``tests/test_oracle_pins.py``
 against values the paper prints (PVF tables, Sec. 4.1), closed forms and
-brute force; see the test module for which pin covers which function.
+brute force, and the fluid step by ``tests/test_oracle_fluid.py`` (closed-form
+gradient and solves, adjointness, divergence-free and idempotent projection,
+Taylor-Green convergence); see the test modules for which pin covers which
+function.
 """
 from __future__ import annotations
 
