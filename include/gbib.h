@@ -150,7 +150,7 @@ GBIB_API int ib_ctx_read_timing(ib_ctx *ctx, int phase, double *ms_total,
                                 int *launches);
 
 /* ---- kernels of the sequential-order passes ----------------------------
- * Both forms compute bitwise the same result (same summation orders).
+ * Every form computes bitwise the same result (same summation orders).
  * WAVEFRONT (the default, AUTO): per wavefront of non-conflicting particles
  *   and per pass, an interpolation kernel and a gather kernel through global
  *   memory (a persistent cooperative kernel takes the wavefronts beyond the

@@ -902,10 +902,12 @@ __global__ void __launch_bounds__(kBlock) k_slot_sort(
 constexpr int kPairThreads = 256;
 constexpr int kPairWarps = kPairThreads / 32;
 
-template <int KW>
+template <typename T, int KW>
 __global__ void __launch_bounds__(kPairThreads, 5) k_tile_pairs(CaseTab ct, int ncompact_cap,
                                                              const int *__restrict__ ncompact_p, Slots sl,
-                                                             const uint64_t *__restrict__ anchor) {
+                                                             const uint64_t *__restrict__ anchor,
+                                                             const PS<T> *__restrict__ wts) {
+    PS<T> *const pwts = (PS<T> *)sl.pw;
     grid_dep_wait();
     constexpr int KW3 = KW * KW * KW;
     __shared__ unsigned int s_anc[kMaxCand];                // (x + 3) | (y + 3) << 4 | (z + 3) << 8
@@ -931,6 +933,7 @@ __global__ void __launch_bounds__(kPairThreads, 5) k_tile_pairs(CaseTab ct, int 
         if (nc > kMaxCand) nc = 0;  // left empty by the sort (status raised there)
         int2 *band = sl.band + sl.poff[b];
         uint32_t *pairs = sl.pairs + sl.poff[b];
+        PS<T> *pw = pwts ? pwts + sl.poff[b] : nullptr;
         for (int i = tid; i < nc; i += blockDim.x) {
             const uint64_t an = anchor[sl.cand[b + i]];
             int d[3] = {anchor_x(an) - lo.x + 3, anchor_y(an) - lo.y + 3, anchor_z(an) - lo.z + 3};
@@ -1002,10 +1005,15 @@ __global__ void __launch_bounds__(kPairThreads, 5) k_tile_pairs(CaseTab ct, int 
         // index (one step's cells are distinct; the warp barrier orders steps)
         for (int i = i0; i < i1; ++i) {
             const unsigned pk = s_anc[i];
+            const PS<T> *w = wts + 12 * (size_t)sl.cand[b + i];
 #pragma unroll
             for (int q = 0; q < kSub; ++q) {
                 const int c = cell_of(pk, q);
-                if (c >= 0) pairs[atomicAdd(&s_cnt[warp][c], 1u)] = (unsigned)i | (kcode[q] << 16);
+                if (c >= 0) {
+                    const unsigned pos = atomicAdd(&s_cnt[warp][c], 1u);
+                    pairs[pos] = (unsigned)i | (kcode[q] << 16);
+                    if (pw) pw[pos] = pair_weight(w, kcode[q] & 3, (kcode[q] >> 2) & 3, (kcode[q] >> 4) & 3);
+                }
             }
             __syncwarp();
         }
@@ -1207,32 +1215,118 @@ __global__ void __launch_bounds__(kInterpThreads) k_interp_level(PassArgs<T> a, 
     }
 }
 
+// FP64 fields: one thread per marker component, three per marker.  Each sums
+// its component's taps in the order of interp_marker (planes z, rows y,
+// columns x; the same double-float products and additions), so the result
+// is bitwise the one-thread form's; three times the threads hide the latency
+// of the double-float chains and of the field loads.
+constexpr bool kInterpSplit = true;  // FP64 level interpolation by component
+constexpr bool kInterpSplitAll = true;  // every tap of a component in flight at once
+
+template <int KW, bool ALL>
+__device__ __forceinline__ double interp_component(const double *__restrict__ uc, const DevGrid &g, uint64_t anc,
+                                                   const float2 *w) {
+    int ix[KW], iy[KW], iz[KW];
+    const int ax = anchor_x(anc), ay = anchor_y(anc), az = anchor_z(anc);
+#pragma unroll
+    for (int k = 0; k < KW; ++k) {
+        ix[k] = wrap_add(ax, k, g.n[0]);
+        iy[k] = wrap_add(ay, k, g.n[1]);
+        iz[k] = wrap_add(az, k, g.n[2]);
+    }
+    SumAcc<double> acc;
+    auto plane = [&](int kz) {
+        double v[KW][KW];
+#pragma unroll
+        for (int ky = 0; ky < KW; ++ky) {
+            const long long row = ((long long)iz[kz] * g.n[1] + iy[ky]) * g.n[0];
+#pragma unroll
+            for (int kx = 0; kx < KW; ++kx) v[ky][kx] = uc[row + ix[kx]];
+        }
+#pragma unroll
+        for (int ky = 0; ky < KW; ++ky) {
+            const float2 wyz = df_mul(w[8 + kz], w[4 + ky]);
+#pragma unroll
+            for (int kx = 0; kx < KW; ++kx) acc.add(df_mul(wyz, w[kx]), df_split(v[ky][kx]));
+        }
+    };
+    if (ALL) {
+#pragma unroll
+        for (int kz = 0; kz < KW; ++kz) plane(kz);
+    } else {
+#pragma unroll 1
+        for (int kz = 0; kz < KW; ++kz) plane(kz);
+    }
+    return acc.value();
+}
+
+template <typename T, int KER>
+__global__ void __launch_bounds__(kInterpThreads) k_interp_level_c3(PassArgs<T> a, int L) {
+    static_assert(sizeof(T) == 8, "component split serves FP64 fields");
+    constexpr int KW = Kernel<KER>::W;
+    const int nl = *a.nlev;
+    const int m0 = L < nl ? a.lev_mbeg[L] : 0, m1 = L < nl ? a.lev_mbeg[L + 1] : 0;
+    const int n3 = 3 * (m1 - m0);
+    const int stride = gridDim.x * blockDim.x;
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    // one item's data but the field (loaded before the wait for the first)
+    int l = 0, c = 0;
+    uint64_t anc = 0;
+    float2 w[12];
+    double ud = 0.0, q = 0.0, F = 0.0;
+    auto load = [&]() {
+        l = a.mperm[m0 + t / 3];
+        c = t % 3;
+        anc = a.ms.anchor[l];
+#pragma unroll
+        for (int k = 0; k < 12; ++k) w[k] = __ldg(a.ms.wts + 12 * (size_t)l + k);
+        ud = __ldg(a.ms.Ud + 3 * l + c);
+        q = a.dV[l] * a.ct.of_particle(a.part_of[l]).g.inv_h3;
+        F = a.F[3 * l + c];
+    };
+    if (t < n3) load();
+    grid_dep_wait();
+    grid_dep_launch();
+    for (bool first = true; t < n3; t += stride, first = false) {
+        if (!first) load();
+        const DevCase cd = a.ct.of_particle(a.part_of[l]);
+        const DevGrid &g = cd.g;
+        const long long N = (long long)g.n[0] * g.n[1] * g.n[2];
+        const double U = interp_component<KW, kInterpSplitAll>((const double *)cd.u + c * N, g, anc, w);
+        const double e = ud - U;
+        a.F[3 * l + c] = fma(e, a.inv_dt, F);
+        a.ms.A[4 * l + c] = to_store(e * q);
+    }
+}
+
 // The wavefront gather, one CTA per tile (grid-stride), many CTAs per SM,
 // over the tiles' per-cell lists (sums bitwise those of the bin walk).
 //
 // Before the wait (nothing here is written by the interpolation): the tile's
-// candidate weights and its pairs are staged in shared memory, and each
-// thread loads the list heads and field values of its (at most two) band
-// cells.  After the wait only the spread sources are loaded; the sums then
-// run from shared memory and registers.  Each cell's pairs are added in list
-// order, as in gather_tile_lists.
+// pair words and pair weights (the weight products, formed once per call by
+// k_tile_pairs) are staged in shared memory, and each thread loads the list
+// heads and field values of its (at most two) band cells.  After the wait
+// only the spread sources are loaded; the sums then run from shared memory
+// and registers.  Each cell's pairs are added in list order with the same
+// weight products as gather_tile_lists forms on the fly, so the sums are
+// bitwise the same.
 constexpr int kLevPairs = 3072;  // pairs staged per tile (more: read from memory)
 
-template <typename T>
-constexpr size_t level_stage_bytes() {
-    return tile_stage_bytes<T>() + (size_t)kLevPairs * sizeof(uint32_t);
-}
-
-// The same for a staging capacity of `stage` candidates (ib_ctx_set_gather).
+// Shared memory of a level gather CTA staging `stage` candidates: their
+// spread sources, then the tile's pair words and pair weights.
 template <typename T>
 size_t level_stage_bytes(int stage) {
-    return (size_t)stage * 16 * sizeof(T) + (size_t)kLevPairs * sizeof(uint32_t);
+    return (size_t)stage * 4 * sizeof(PS<T>) + (size_t)kLevPairs * (sizeof(uint32_t) + sizeof(PS<T>));
 }
 
-template <typename T, int KW>
-__device__ __forceinline__ void gather_tile_level(const CaseTab &ct, int cs, const Slots &sl, const PS<T> *wts,
-                                                  const PS<T> *A_src, double inv_dt, PS<T> *sw, PS<T> *sA,
-                                                  uint32_t *sp, int stage) {
+// `wait` runs between the staging of what the interpolation does not write
+// and the loads of the spread sources; false (a wait that gave up) leaves the
+// tile untouched, CTA-uniformly.  Each pair's weight product comes from the
+// per-pair weights k_tile_pairs formed (the value pair_weight gives).
+template <typename T, int KW, class Wait>
+__device__ __forceinline__ bool gather_tile_level(const CaseTab &ct, int cs, const Slots &sl, const PS<T> *A_src,
+                                                  double inv_dt, PS<T> *sA, uint32_t *sp, PS<T> *spw, int stage,
+                                                  Wait wait) {
     using S = PS<T>;
     const DevCase cd = ct.get(sl.geo_case[cs]);
     const DevGrid &g = cd.g;
@@ -1248,6 +1342,7 @@ __device__ __forceinline__ void gather_tile_level(const CaseTab &ct, int cs, con
     const int np = (int)(sl.poff[dim.w + nc] - pb);
     const int2 *band = sl.band + pb;
     const uint32_t *pairs = sl.pairs + pb;
+    const S *pwg = (const S *)sl.pw + pb;
     const bool staged = nc <= stage, pstaged = np <= kLevPairs;
     auto cell_index = [&](int cell) {
         const int tx = cell & 7, ty = (cell >> 3) & 7, tz = cell >> 6;
@@ -1273,19 +1368,13 @@ __device__ __forceinline__ void gather_tile_level(const CaseTab &ct, int cs, con
         }
     }
     if (pstaged)
-        for (int k = threadIdx.x; k < np; k += blockDim.x) sp[k] = __ldg(pairs + k);
-    const uint32_t m0 = (staged && (int)threadIdx.x < nc) ? cand[threadIdx.x] : 0u;
-    if (staged)
-        for (int i = threadIdx.x; i < nc; i += blockDim.x) {
-            const uint32_t m = i == (int)threadIdx.x ? m0 : cand[i];
-            const S *wm = wts + 12 * (size_t)m;
-#pragma unroll
-            for (int q = 0; q < 3; ++q)
-#pragma unroll
-                for (int jj = 0; jj < KW; ++jj) sw[12 * i + 4 * q + jj] = __ldg(wm + 4 * q + jj);
+        for (int k = threadIdx.x; k < np; k += blockDim.x) {
+            sp[k] = __ldg(pairs + k);
+            spw[k] = __ldg(pwg + k);
         }
+    const uint32_t m0 = (staged && (int)threadIdx.x < nc) ? cand[threadIdx.x] : 0u;
     // ---- the interpolation's sources
-    grid_dep_wait();
+    if (!wait()) return false;
     if (staged)
         for (int i = threadIdx.x; i < nc; i += blockDim.x) {
             const uint32_t m = i == (int)threadIdx.x ? m0 : cand[i];
@@ -1306,16 +1395,16 @@ __device__ __forceinline__ void gather_tile_level(const CaseTab &ct, int cs, con
             constexpr int kSB = 4;
             for (int k0 = 0; k0 < cnt; k0 += kSB) {
                 uint32_t pk[kSB];
-#pragma unroll
-                for (int j = 0; j < kSB; ++j) pk[j] = k0 + j < cnt ? sp[ee.y + k0 + j] : 0u;
                 S wt[kSB], a[kSB][3];
 #pragma unroll
                 for (int j = 0; j < kSB; ++j) {
-                    const int i = pk[j] & 0xffff, ox = (pk[j] >> 16) & 3, oy = (pk[j] >> 18) & 3,
-                              oz = (pk[j] >> 20) & 3;
-                    const S *w = sw + 12 * i;
-                    const S *Ai = sA + 4 * i;
-                    wt[j] = pair_weight(w, ox, oy, oz);
+                    const bool in = k0 + j < cnt;
+                    pk[j] = in ? sp[ee.y + k0 + j] : 0u;
+                    wt[j] = in ? spw[ee.y + k0 + j] : S();
+                }
+#pragma unroll
+                for (int j = 0; j < kSB; ++j) {
+                    const S *Ai = sA + 4 * (pk[j] & 0xffff);
                     a[j][0] = Ai[0], a[j][1] = Ai[1], a[j][2] = Ai[2];
                 }
 #pragma unroll
@@ -1331,18 +1420,14 @@ __device__ __forceinline__ void gather_tile_level(const CaseTab &ct, int cs, con
         }
         for (int k = 0; k < cnt; ++k) {
             const uint32_t pk = pstaged ? sp[ee.y + k] : __ldg(pairs + ee.y + k);
-            const int i = pk & 0xffff, ox = (pk >> 16) & 3, oy = (pk >> 18) & 3, oz = (pk >> 20) & 3;
-            S wt, a0, a1, a2;
+            const S wt = pstaged ? spw[ee.y + k] : __ldg(pwg + ee.y + k);
+            const int i = pk & 0xffff;
+            S a0, a1, a2;
             if (staged) {
-                const S *w = sw + 12 * i;
                 const S *Ai = sA + 4 * i;
-                wt = pair_weight(w, ox, oy, oz);
                 a0 = Ai[0], a1 = Ai[1], a2 = Ai[2];
             } else {
-                const size_t m = cand[i];
-                const S *w = wts + 12 * m;
-                const S *Ai = A_src + 4 * m;
-                wt = pair_weight3(__ldg(w + ox), __ldg(w + 4 + oy), __ldg(w + 8 + oz));
+                const S *Ai = A_src + 4 * (size_t)cand[i];
                 a0 = Ai[0], a1 = Ai[1], a2 = Ai[2];
             }
             acc[0].add(wt, a0);
@@ -1375,15 +1460,16 @@ __device__ __forceinline__ void gather_tile_level(const CaseTab &ct, int cs, con
         update(cc, vv, acc);
     }
     __syncthreads();
+    return true;
 }
 
 template <typename T, int KER>
 __global__ void __launch_bounds__(kGatherThreads, sizeof(T) == 4 ? 5 : 4) k_gather_level(PassArgs<T> a, int L) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int stage = a.stage;                           // staged candidates per tile
-    PS<T> *sw = (PS<T> *)smem_raw;                      // [stage][12]
-    PS<T> *sA = sw + (size_t)stage * 12;                // [stage][4]
-    uint32_t *sp = (uint32_t *)(sA + (size_t)stage * 4);  // [kLevPairs]
+    const int stage = a.stage;                             // staged candidates per tile
+    PS<T> *sA = (PS<T> *)smem_raw;                         // [stage][4]
+    uint32_t *sp = (uint32_t *)(sA + (size_t)stage * 4);   // [kLevPairs]
+    PS<T> *spw = (PS<T> *)(sp + kLevPairs);                // [kLevPairs]
     const int nl = *a.nlev;
     const int s0 = L < nl ? a.lev_sbeg[L] : 0, s1 = L < nl ? a.lev_sbeg[L + 1] : 0;
     if (s0 + (int)blockIdx.x >= s1) {
@@ -1402,8 +1488,11 @@ __global__ void __launch_bounds__(kGatherThreads, sizeof(T) == 4 ? 5 : 4) k_gath
     for (int r = 0;; ++r) {
         const int j = (kSnake && (r & 1)) ? (r + 1) * G - 1 - i : r * G + i;
         if (j >= nt) break;
-        gather_tile_level<T, Kernel<KER>::W>(a.ct, a.tperm[s0 + j], a.sl, a.ms.wts, a.ms.A, a.inv_dt, sw, sA, sp,
-                                             stage);
+        gather_tile_level<T, Kernel<KER>::W>(a.ct, a.tperm[s0 + j], a.sl, a.ms.A, a.inv_dt, sA, sp, spw, stage,
+                                             [] {
+                                                 grid_dep_wait();
+                                                 return true;
+                                             });
     }
 }
 
@@ -1537,7 +1626,7 @@ struct SlotScratch {
 };
 
 // Workspace of the slot lists, and the zeroing they need.
-template <int KW>
+template <typename T, int KW>
 static int slots_alloc(Arena &ar, int M, int ndense, int mode, Slots &sl, SlotScratch &sc, cudaStream_t s,
                        bool with_pairs, bool with_bins) {
     const size_t per = mode == 0 ? 27 : 8;
@@ -1566,12 +1655,14 @@ static int slots_alloc(Arena &ar, int M, int ndense, int mode, Slots &sl, SlotSc
         sl.poff = ar.take<uint32_t>(sc.cand_cap + 1);
         sl.band = ar.take<int2>((size_t)KW3 * M);
         sl.pairs = ar.take<uint32_t>((size_t)KW3 * M);
+        sl.pw = ar.take<PS<T>>((size_t)KW3 * M);
         sl.nband = ar.take<int>(ncap);
     } else {
         sl.pcnt = sl.poff = nullptr;
         sl.band = nullptr;
         sl.pairs = nullptr;
         sl.nband = nullptr;
+        sl.pw = nullptr;
     }
     if (!ar.ok())
         return oom_error(ar.used, ar.cap);
@@ -1582,10 +1673,10 @@ static int slots_alloc(Arena &ar, int M, int ndense, int mode, Slots &sl, SlotSc
 }
 
 // The kernel chain: count, scan, compact, fill, scan, sort, per-cell lists.
-template <int KW>
+template <typename T, int KW>
 static int slots_build(ib_ctx *ctx, const CaseTab &ct, int M, int ndense, SlotGeom sg, const uint64_t *anchor,
-                       const int *level, Slots &sl, const SlotScratch &sc, int *&ncompact_dev, cudaStream_t s,
-                       bool with_pairs) {
+                       const PS<T> *wts, const int *level, Slots &sl, const SlotScratch &sc, int *&ncompact_dev,
+                       cudaStream_t s, bool with_pairs) {
     const int nb = grid_blocks(M, 256, ctx->sm_count);
     launch_pdl(k_slot_count<KW>, dim3(nb), dim3(256), 0, s, ct, M, sg, anchor, sl.count);
     exclusive_scan(sl.count, sl.start, ndense, sc.scratch, s);
@@ -1605,8 +1696,8 @@ static int slots_build(ib_ctx *ctx, const CaseTab &ct, int M, int ndense, SlotGe
                sc.ncompact_cap, (const int *)ncompact_dev, sg, (const uint32_t *)sl.dense_of,
                (const uint32_t *)sl.start, anchor, level, sl, ctx->status);
     if (with_pairs)
-        launch_pdl(k_tile_pairs<KW>, dim3(ctx->sm_count * 8), dim3(kPairThreads), 0, s, ct, sc.ncompact_cap,
-                   (const int *)ncompact_dev, sl, anchor);
+        launch_pdl(k_tile_pairs<T, KW>, dim3(ctx->sm_count * 8), dim3(kPairThreads), 0, s, ct, sc.ncompact_cap,
+                   (const int *)ncompact_dev, sl, anchor, wts);
     return check_launch("slot lists");
 }
 
@@ -1645,11 +1736,12 @@ static int run_spread(ib_ctx *ctx, const ib_grid *grid, int M, const double *X, 
     Slots sl;
     SlotScratch sc;
     int *ncompact = nullptr;
-    int rc = slots_alloc<KW>(ar, M, (int)ndense, sg.mode, sl, sc, s, true, false);
+    int rc = slots_alloc<T, KW>(ar, M, (int)ndense, sg.mode, sl, sc, s, true, false);
     if (rc) return rc;
     PhaseTimer tm(ctx, IB_PHASE_SPREAD, s);
     k_prep_spread<T, KER><<<nb, 256, 0, s>>>(g, M, X, F, dV, ms, ctx->status);
-    rc = slots_build<KW>(ctx, ct, M, (int)ndense, sg, ms.anchor, nullptr, sl, sc, ncompact, s, true);
+    rc = slots_build<T, KW>(ctx, ct, M, (int)ndense, sg, ms.anchor, (const PS<T> *)ms.wts, nullptr, sl, sc, ncompact, s,
+                            true);
     if (rc) return rc;
     cudaFuncSetAttribute(k_spread_gather<T, KER>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)tile_stage_bytes<T>());
@@ -1709,7 +1801,7 @@ static int run_mdf(ib_ctx *ctx, Arena &ar, const CaseTab &ct, const ib_particles
     int rc = IB_OK;
     int *tperm = nullptr;
     if (!atomic) {
-        rc = slots_alloc<KW>(ar, M, (int)ndense, sg.mode, sl, sc, s, true, resident);
+        rc = slots_alloc<T, KW>(ar, M, (int)ndense, sg.mode, sl, sc, s, true, resident);
         if (rc) return rc;
         tperm = ar.take<int>(sc.ncompact_cap);
     }
@@ -1739,7 +1831,8 @@ static int run_mdf(ib_ctx *ctx, Arena &ar, const CaseTab &ct, const ib_particles
     sg.box_dim = box_dim;
     int *ncompact = nullptr;
     if (!atomic) {
-        rc = slots_build<KW>(ctx, ct, M, (int)ndense, sg, ms.anchor, lo.level, sl, sc, ncompact, s, true);
+        rc = slots_build<T, KW>(ctx, ct, M, (int)ndense, sg, ms.anchor, (const PS<T> *)ms.wts, lo.level, sl, sc,
+                                ncompact, s, true);
         if (rc) return rc;
     }
     if constexpr (sizeof(T) == 4) {
@@ -1844,6 +1937,8 @@ static int run_mdf(ib_ctx *ctx, Arena &ar, const CaseTab &ct, const ib_particles
         ci.blockDim = dim3(kInterpThreads);
         ci.stream = s;
         ci.attrs = pdl;
+        cudaLaunchConfig_t ci3 = ci;
+        ci3.gridDim = dim3(grid_blocks(3LL * M, kInterpThreads, ctx->sm_count));
         cg = ci;
         cg.gridDim = dim3(gg);
         cg.blockDim = dim3(kGatherThreads);
@@ -1858,8 +1953,11 @@ static int run_mdf(ib_ctx *ctx, Arena &ar, const CaseTab &ct, const ib_particles
             for (int m = 0; m < Ns; ++m) {
                 {
                     PhaseTimer ti(ctx, IB_PHASE_MDF_INTERP, s);
-                    ci.numAttrs = (L > 0 || m > 0) ? 1 : 0;
-                    cudaLaunchKernelEx(&ci, k_interp_level<T, KER>, a, L);
+                    ci.numAttrs = ci3.numAttrs = (L > 0 || m > 0) ? 1 : 0;
+                    if constexpr (sizeof(T) == 8 && kInterpSplit)
+                        cudaLaunchKernelEx(&ci3, k_interp_level_c3<T, KER>, a, L);
+                    else
+                        cudaLaunchKernelEx(&ci, k_interp_level<T, KER>, a, L);
                 }
                 PhaseTimer tg(ctx, IB_PHASE_MDF_GATHER, s);
                 if (atomic)
