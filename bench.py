@@ -293,6 +293,8 @@ class Runner:
         main = torch.cuda.current_stream()
         self.side.wait_stream(main)
         with torch.cuda.stream(self.side):
+            # two CTAs per particle: the preparation's kernels keep most SMs
+            self.ctx_v.set_volume_split(2)
             self.ctx_v.particle_volume_integrals(self.u, c.h, self.parts, out=self.I0)
             self.ev_v.record(self.side)
         ctx.ib_multidirect_forcing(self.u, c.h, self.parts, self.marks, c.Ns, c.dt, F_out=self.F,
@@ -301,6 +303,7 @@ class Runner:
         # force and torque sums (forces only)
         self.side.wait_stream(main)
         with torch.cuda.stream(self.side):
+            self.ctx_v.set_volume_split(0)
             self.ctx_v.particle_volume_integrals(self.u, c.h, self.parts, out=self.I1)
         ctx.particle_force_torque(self.parts, self.marks, self.F, c.rho_f, out=(self.Fib, self.Tib))
         main.wait_stream(self.side)
@@ -309,15 +312,14 @@ class Runner:
 
 
 def launches_per_step(Ns, levels):
-    """Library kernels per step on this workload (P * 512 = 32768 dense tiles
-    and ~1e6 candidate slots, so each scan is three kernels): volume 1 x 2
-    calls; multidirect forcing: prep, conflicts, levels, marker order, tile
-    count, scan (3), flags, scan (3), compact, fill, scan (3), sort, per-cell
-    lists, level ranges, tile order (21), one interpolation and one gather
-    kernel per wavefront and pass, the persistent remainder kernel (1);
-    force/torque 1; collision + Newton-Euler 2.  (The ncu launch list shows
-    77 kernels between consecutive steps for Ns = 5 and 5 wavefronts.)"""
-    return 2 + 21 + 2 * Ns * levels + 1 + 1 + 2
+    """Library kernels per step on this workload: volume 1 x 2 calls;
+    multidirect forcing: prep, conflicts, levels, marker order, tile count,
+    slot scan (counts, flags and compaction in one single-pass scan), fill,
+    pair-count scan, sort, per-cell lists, level ranges, tile order (12), one
+    interpolation and one gather kernel per wavefront and pass, the
+    persistent remainder kernel (1); force/torque 1; collision + Newton-Euler
+    2."""
+    return 2 + 12 + 2 * Ns * levels + 1 + 1 + 2
 
 
 def capture(runner):

@@ -284,38 +284,6 @@ extern "C" int ib_batch_table_destroy(ib_batch_table *t) {
 
 namespace gbib {
 
-// ---- exclusive scan ------------------------------------------------------
-// Three stages: per-block totals, a scan of the totals in one block, then a
-// per-block scan that adds the block's offset.  1024 elements per block.
-constexpr int kScanBlock = 1024;
-
-__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *total) {
-    __shared__ uint32_t warp_sums[32];
-    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    uint32_t x = v;
-    for (int o = 1; o < 32; o <<= 1) {
-        uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
-    }
-    if (lane == 31) warp_sums[wid] = x;
-    __syncthreads();
-    if (wid == 0) {
-        int nw = blockDim.x >> 5;
-        uint32_t s = lane < nw ? warp_sums[lane] : 0;
-        for (int o = 1; o < 32; o <<= 1) {
-            uint32_t y = __shfl_up_sync(0xffffffffu, s, o);
-            if (lane >= o) s += y;
-        }
-        warp_sums[lane] = s;
-    }
-    __syncthreads();
-    uint32_t base = wid ? warp_sums[wid - 1] : 0;
-    if (total) *total = warp_sums[(blockDim.x >> 5) - 1];
-    uint32_t r = base + x - v;
-    __syncthreads();
-    return r;
-}
-
 // A device word that nothing ever writes, and a bounded wait on it: the
 // self-test of the failure path (ib_selftest_wait_timeout).  The wait has
 // the shape of the library's others: poll, give up after a clock64 budget,
@@ -331,45 +299,6 @@ __global__ void k_selftest_wait(long long cycles, DevStatus *st) {
             return;
         }
     }
-}
-
-// (the scan kernels are launched as programmatic dependents: they wait for
-// their predecessor before touching memory)
-__global__ void k_scan_totals(const uint32_t *in, int n, uint32_t *totals) {
-    grid_dep_wait();
-    int i = blockIdx.x * kScanBlock + threadIdx.x;
-    uint32_t v = i < n ? in[i] : 0;
-    uint32_t tot;
-    block_exclusive_scan(v, &tot);
-    if (threadIdx.x == 0) totals[blockIdx.x] = tot;
-}
-
-__global__ void k_scan_top(uint32_t *totals, int nb) {
-    // nb <= kScanBlock * kScanBlock: each thread folds a strided chunk.
-    __shared__ uint32_t carry;
-    grid_dep_wait();
-    if (threadIdx.x == 0) carry = 0;
-    __syncthreads();
-    for (int base = 0; base < nb; base += kScanBlock) {
-        int i = base + threadIdx.x;
-        uint32_t v = i < nb ? totals[i] : 0;
-        uint32_t tot;
-        uint32_t ex = block_exclusive_scan(v, &tot);
-        if (i < nb) totals[i] = carry + ex;
-        __syncthreads();
-        if (threadIdx.x == 0) carry += tot;
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) totals[nb] = carry;
-}
-
-__global__ void k_scan_apply(const uint32_t *in, uint32_t *out, int n, const uint32_t *totals) {
-    grid_dep_wait();
-    int i = blockIdx.x * kScanBlock + threadIdx.x;
-    uint32_t v = i < n ? in[i] : 0;
-    uint32_t ex = block_exclusive_scan(v, nullptr);
-    if (i < n) out[i] = totals[blockIdx.x] + ex;
-    if (blockIdx.x == 0 && threadIdx.x == 0) out[n] = totals[gridDim.x];
 }
 
 static cudaEvent_t take_event(ib_ctx *c) {
@@ -403,46 +332,6 @@ void PhaseTimer::stop() {
         if (b) ctx->pool.push_back(b);
     }
     ctx = nullptr;
-}
-
-// Small arrays: one CTA, each thread scans kScanItems consecutive elements
-// (few, so that a warp's loads stay within a few cache lines; larger arrays
-// take the three-kernel path, whose loads are fully coalesced).
-constexpr int kScanItems = 4;
-
-__global__ void __launch_bounds__(kScanBlock) k_scan_single(const uint32_t *in, uint32_t *out, int n) {
-    grid_dep_wait();
-    const int base = threadIdx.x * kScanItems;
-    uint32_t v[kScanItems];
-    uint32_t sum = 0;
-#pragma unroll
-    for (int k = 0; k < kScanItems; ++k) {
-        v[k] = base + k < n ? in[base + k] : 0u;
-        sum += v[k];
-    }
-    uint32_t tot;
-    uint32_t run = block_exclusive_scan(sum, &tot);
-#pragma unroll
-    for (int k = 0; k < kScanItems; ++k) {
-        if (base + k < n) out[base + k] = run;
-        run += v[k];
-    }
-    if (threadIdx.x == 0) out[n] = tot;
-}
-
-size_t scan_workspace(int n) { return (size_t)(n + kScanBlock - 1) / kScanBlock + 2; }
-
-void exclusive_scan(const uint32_t *in, uint32_t *out, int n, uint32_t *scratch,
-                    cudaStream_t s) {
-    if (n <= kScanBlock * kScanItems) {
-        launch_pdl(k_scan_single, dim3(1), dim3(kScanBlock), 0, s, in, out, n);
-        return;
-    }
-    int nb = (n + kScanBlock - 1) / kScanBlock;
-    if (nb == 0) nb = 1;
-    launch_pdl(k_scan_totals, dim3(nb), dim3(kScanBlock), 0, s, in, n, scratch);
-    launch_pdl(k_scan_top, dim3(1), dim3(kScanBlock), 0, s, scratch, nb);
-    launch_pdl(k_scan_apply, dim3(nb), dim3(kScanBlock), 0, s, in, out, n, (const uint32_t *)scratch);
 }
 
 }  // namespace gbib

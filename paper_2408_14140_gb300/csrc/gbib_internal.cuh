@@ -263,10 +263,4 @@ struct PhaseTimer {
     ~PhaseTimer() { stop(); }
 };
 
-// Exclusive scan of n uint32 counts into out[0..n] (out[n] = total).
-// Needs scan_workspace(n) uint32 of scratch.
-size_t scan_workspace(int n);
-void exclusive_scan(const uint32_t *in, uint32_t *out, int n, uint32_t *scratch,
-                    cudaStream_t s);
-
 }  // namespace gbib

@@ -585,21 +585,180 @@ __global__ void k_slot_fill(CaseTab ct, int M, SlotGeom sg, const uint64_t *__re
         });
 }
 
-__global__ void k_flags(const uint32_t *__restrict__ count, uint32_t *__restrict__ flags, int n) {
-    grid_dep_wait();
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-        flags[i] = count[i] ? 1u : 0u;
+// ---------------------------------------------------------------------------
+// single-pass exclusive scans (decoupled look-back, Merrill & Garland 2016):
+// each CTA takes the next tile of kLbTile elements from a ticket counter,
+// publishes its tile sum, then -- walking back over the tiles before it
+// until one has published its inclusive prefix -- its own inclusive prefix,
+// and scans the tile from that base.  A tile waits only for tiles taken
+// earlier by CTAs already running, so every wait ends; each is bounded all
+// the same (IB_ERR_TIMEOUT).  Tile words pack a 2-bit state (0 none,
+// 1 tile sum, 2 inclusive prefix) above a 62-bit value; the words and the
+// ticket are zeroed before the call's kernel chain.
+// ---------------------------------------------------------------------------
+constexpr int kLbThreads = 256, kLbItems = 8, kLbTile = kLbThreads * kLbItems;
+constexpr unsigned long long kLbVal = (1ull << 62) - 1;
+
+__device__ __forceinline__ unsigned long long ld_acquire64(const unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release64(unsigned long long *p, unsigned long long v) {
+    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
-__global__ void k_compact(const uint32_t *__restrict__ count, const uint32_t *__restrict__ fscan,
-                          uint32_t *__restrict__ dense_of, int n) {
-    grid_dep_wait();
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-        if (count[i]) dense_of[fscan[i]] = (uint32_t)i;
+// Exclusive scan of one value per thread over the CTA (64-bit, fixed order).
+__device__ __forceinline__ unsigned long long lb_block_scan(unsigned long long v, unsigned long long *total) {
+    __shared__ unsigned long long s_w[kLbThreads / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned long long x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s_w[warp] = x;
+    __syncthreads();
+    unsigned long long wbase = 0, tot = 0;
+#pragma unroll
+    for (int w = 0; w < kLbThreads / 32; ++w) {
+        if (w < warp) wbase += s_w[w];
+        tot += s_w[w];
+    }
+    *total = tot;
+    return wbase + x - v;
 }
 
-// Per-level ranges of the compact slot list (dense slots of the
-// particle-local mode are level-major: rank * 512 + local tile).
+// The tile's exclusive base: warp 0 publishes the tile sum, then reads the
+// words of the 32 tiles before it at once (lane l: tile - 1 - l), waiting for
+// each to be published, and adds the sums up to the nearest inclusive prefix;
+// without one it moves 32 tiles further back.  Positions before tile 0 count
+// as an inclusive prefix of 0.  Every thread gets the base.  false: a wait
+// gave up.
+__device__ __forceinline__ bool lb_tile_base(int tile, unsigned long long tot, unsigned long long *tstat,
+                                             DevStatus *st, unsigned long long &base) {
+    __shared__ unsigned long long s_base;
+    __shared__ int s_ok;
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        unsigned long long pre = 0;
+        bool ok = true;
+        if (tile > 0) {
+            if (lane == 0) st_release64(tstat + tile, (1ull << 62) | tot);
+            for (int hi = tile - 1;; hi -= 32) {
+                const int j = hi - lane;
+                unsigned long long w = j >= 0 ? ld_acquire64(tstat + j) : (2ull << 62);
+                if ((w >> 62) == 0) {
+                    const long long t0 = clock64();
+                    do {
+                        if (clock64() - t0 > kSpinCycles) {
+                            raise_status(st, IB_ERR_TIMEOUT, -2);
+                            w = 2ull << 62;  // give up: stop here
+                            ok = false;
+                            break;
+                        }
+                        w = ld_acquire64(tstat + j);
+                    } while ((w >> 62) == 0);
+                }
+                __syncwarp();
+                const unsigned incl = __ballot_sync(0xffffffffu, (w >> 62) == 2);
+                const int first = incl ? __ffs(incl) - 1 : 31;
+                unsigned long long v = (lane <= first && j >= 0) ? (w & kLbVal) : 0ull;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                pre += v;
+                if (incl) break;
+            }
+            ok = __all_sync(0xffffffffu, ok);
+        }
+        if (lane == 0) {
+            st_release64(tstat + tile, (2ull << 62) | ((pre + tot) & kLbVal));
+            s_base = pre;
+            s_ok = ok ? 1 : 0;
+        }
+    }
+    __syncthreads();
+    base = s_base;
+    return s_ok != 0;
+}
+
+// The dense slots: start = exclusive scan of the counts, flag_scan =
+// exclusive scan of (count > 0), and dense_of[flag_scan[i]] = i for every
+// non-empty slot i -- one pass over the counts (the two sums packed in one
+// 64-bit word: counts below, flags from bit 32).
+__global__ void __launch_bounds__(kLbThreads) k_slot_scan(const uint32_t *__restrict__ count, int n,
+                                                          uint32_t *__restrict__ start,
+                                                          uint32_t *__restrict__ flag_scan,
+                                                          uint32_t *__restrict__ dense_of,
+                                                          unsigned long long *tstat, unsigned int *ticket,
+                                                          DevStatus *st) {
+    __shared__ int s_tile;
+    grid_dep_wait();
+    if (threadIdx.x == 0) s_tile = (int)atomicAdd(ticket, 1u);
+    __syncthreads();
+    const int tile = s_tile;
+    const int i0 = tile * kLbTile + threadIdx.x * kLbItems;
+    uint32_t c[kLbItems];
+    unsigned long long sum = 0;
+#pragma unroll
+    for (int k = 0; k < kLbItems; ++k) {
+        c[k] = i0 + k < n ? count[i0 + k] : 0u;
+        sum += (unsigned long long)c[k] | ((unsigned long long)(c[k] != 0u) << 32);
+    }
+    unsigned long long tot, base;
+    const unsigned long long ex = lb_block_scan(sum, &tot);
+    if (!lb_tile_base(tile, tot, tstat, st, base)) return;
+    unsigned long long run = base + ex;
+#pragma unroll
+    for (int k = 0; k < kLbItems; ++k) {
+        const int i = i0 + k;
+        if (i < n) {
+            start[i] = (uint32_t)run;
+            flag_scan[i] = (uint32_t)(run >> 32);
+            if (c[k]) dense_of[run >> 32] = (uint32_t)i;
+        }
+        run += (unsigned long long)c[k] | ((unsigned long long)(c[k] != 0u) << 32);
+    }
+    if (i0 <= n && n < i0 + kLbItems) {  // the thread holding position n writes the totals
+        start[n] = (uint32_t)run;
+        flag_scan[n] = (uint32_t)(run >> 32);
+    }
+}
+
+// out = exclusive scan of in[0, n'), n' = min(n, *n_dev); out[n'] = total.
+// Tiles past n' return at once.
+__global__ void __launch_bounds__(kLbThreads) k_scan_lb(const uint32_t *__restrict__ in, int n,
+                                                        const uint32_t *__restrict__ n_dev,
+                                                        uint32_t *__restrict__ out, unsigned long long *tstat,
+                                                        unsigned int *ticket, DevStatus *st) {
+    __shared__ int s_tile;
+    grid_dep_wait();
+    const int nn = min(n, (int)*n_dev);
+    if (threadIdx.x == 0) s_tile = (int)atomicAdd(ticket, 1u);
+    __syncthreads();
+    const int tile = s_tile;
+    if (tile * kLbTile > nn) return;  // no element, and not the tile of the total either
+    const int i0 = tile * kLbTile + threadIdx.x * kLbItems;
+    uint32_t v[kLbItems];
+    unsigned long long sum = 0;
+#pragma unroll
+    for (int k = 0; k < kLbItems; ++k) {
+        v[k] = i0 + k < nn ? in[i0 + k] : 0u;
+        sum += v[k];
+    }
+    unsigned long long tot, base;
+    const unsigned long long ex = lb_block_scan(sum, &tot);
+    if (!lb_tile_base(tile, tot, tstat, st, base)) return;
+    unsigned long long run = base + ex;
+#pragma unroll
+    for (int k = 0; k < kLbItems; ++k) {
+        if (i0 + k < nn) out[i0 + k] = (uint32_t)run;
+        run += v[k];
+    }
+    if (i0 <= nn && nn < i0 + kLbItems) out[nn] = (uint32_t)run;
+}
+
 __global__ void k_level_slots(int mode, const int *__restrict__ nlev_p, const int *__restrict__ lev_pbeg,
                               const uint32_t *__restrict__ fscan, int ndense, int *__restrict__ lev_sbeg) {
     grid_dep_wait();
@@ -1005,19 +1164,24 @@ __global__ void __launch_bounds__(kPairThreads, 5) k_tile_pairs(CaseTab ct, int 
         // index (one step's cells are distinct; the warp barrier orders steps)
         for (int i = i0; i < i1; ++i) {
             const unsigned pk = s_anc[i];
-            const PS<T> *w = wts + 12 * (size_t)sl.cand[b + i];
 #pragma unroll
             for (int q = 0; q < kSub; ++q) {
                 const int c = cell_of(pk, q);
-                if (c >= 0) {
-                    const unsigned pos = atomicAdd(&s_cnt[warp][c], 1u);
-                    pairs[pos] = (unsigned)i | (kcode[q] << 16);
-                    if (pw) pw[pos] = pair_weight(w, kcode[q] & 3, (kcode[q] >> 2) & 3, (kcode[q] >> 4) & 3);
-                }
+                if (c >= 0) pairs[atomicAdd(&s_cnt[warp][c], 1u)] = (unsigned)i | (kcode[q] << 16);
             }
             __syncwarp();
         }
         __syncthreads();
+        // every pair's weight product, one pair per thread (the pair words
+        // written above are visible to the whole CTA after the barrier)
+        if (pw) {
+            const int np = (int)(sl.poff[b + nc] - sl.poff[b]);
+            for (int k = tid; k < np; k += blockDim.x) {
+                const unsigned pk = pairs[k];
+                const PS<T> *w = wts + 12 * (size_t)sl.cand[b + (pk & 0xffff)];
+                pw[k] = pair_weight(w, (pk >> 16) & 3, (pk >> 18) & 3, (pk >> 20) & 3);
+            }
+        }
     }
 }
 
@@ -1622,7 +1786,9 @@ static bool take_markers(Arena &ar, int M, MarkerState<T> &ms) {
 struct SlotScratch {
     size_t cand_cap;
     int ncompact_cap;
-    uint32_t *flags, *scratch, *cscratch;
+    int lb_tiles[2];              // look-back tiles of the slot scan and of the pair-count scan
+    unsigned long long *lb_stat;  // [lb_tiles[0] + lb_tiles[1]] tile words
+    unsigned int *lb_ticket;      // [2]
 };
 
 // Workspace of the slot lists, and the zeroing they need.
@@ -1638,9 +1804,10 @@ static int slots_alloc(Arena &ar, int M, int ndense, int mode, Slots &sl, SlotSc
     sl.start = ar.take<uint32_t>(ndense + 1);
     sl.cursor = ar.take<uint32_t>(ndense);
     sl.flag_scan = ar.take<uint32_t>(ndense + 1);
-    sc.flags = ar.take<uint32_t>(ndense);
-    sc.scratch = ar.take<uint32_t>(scan_workspace(ndense));
-    sc.cscratch = with_pairs ? ar.take<uint32_t>(scan_workspace((int)sc.cand_cap)) : nullptr;
+    sc.lb_tiles[0] = ndense / kLbTile + 1;
+    sc.lb_tiles[1] = with_pairs ? (int)(sc.cand_cap / kLbTile) + 1 : 0;
+    sc.lb_stat = ar.take<unsigned long long>((size_t)sc.lb_tiles[0] + sc.lb_tiles[1]);
+    sc.lb_ticket = ar.take<unsigned int>(2);
     sl.dense_of = ar.take<uint32_t>(ncap);
     sl.cand = ar.take<uint32_t>(sc.cand_cap);
     // bin tables: only the particle-resident form walks them
@@ -1668,7 +1835,8 @@ static int slots_alloc(Arena &ar, int M, int ndense, int mode, Slots &sl, SlotSc
         return oom_error(ar.used, ar.cap);
     cudaMemsetAsync(sl.count, 0, sizeof(uint32_t) * ndense, s);
     cudaMemsetAsync(sl.cursor, 0, sizeof(uint32_t) * ndense, s);
-    if (with_pairs) cudaMemsetAsync(sl.pcnt, 0, sizeof(uint32_t) * sc.cand_cap, s);
+    cudaMemsetAsync(sc.lb_stat, 0, sizeof(unsigned long long) * (sc.lb_tiles[0] + sc.lb_tiles[1]), s);
+    cudaMemsetAsync(sc.lb_ticket, 0, 2 * sizeof(unsigned int), s);
     return IB_OK;
 }
 
@@ -1679,15 +1847,15 @@ static int slots_build(ib_ctx *ctx, const CaseTab &ct, int M, int ndense, SlotGe
                        cudaStream_t s, bool with_pairs) {
     const int nb = grid_blocks(M, 256, ctx->sm_count);
     launch_pdl(k_slot_count<KW>, dim3(nb), dim3(256), 0, s, ct, M, sg, anchor, sl.count);
-    exclusive_scan(sl.count, sl.start, ndense, sc.scratch, s);
-    const int nbd = grid_blocks(ndense, 256, ctx->sm_count);
-    launch_pdl(k_flags, dim3(nbd), dim3(256), 0, s, (const uint32_t *)sl.count, sc.flags, ndense);
-    exclusive_scan(sc.flags, sl.flag_scan, ndense, sc.scratch, s);
-    launch_pdl(k_compact, dim3(nbd), dim3(256), 0, s, (const uint32_t *)sl.count, (const uint32_t *)sl.flag_scan,
-               sl.dense_of, ndense);
+    launch_pdl(k_slot_scan, dim3(sc.lb_tiles[0]), dim3(kLbThreads), 0, s, (const uint32_t *)sl.count, ndense,
+               sl.start, sl.flag_scan, sl.dense_of, sc.lb_stat, sc.lb_ticket, ctx->status);
     launch_pdl(k_slot_fill<KW>, dim3(nb), dim3(256), 0, s, ct, M, sg, anchor, (const uint32_t *)sl.start,
                sl.cursor, sl.cand, sl.pcnt);
-    if (with_pairs) exclusive_scan(sl.pcnt, sl.poff, (int)sc.cand_cap, sc.cscratch, s);
+    // the pair counts of the filled candidate positions [0, start[ndense])
+    if (with_pairs)
+        launch_pdl(k_scan_lb, dim3(sc.lb_tiles[1]), dim3(kLbThreads), 0, s, (const uint32_t *)sl.pcnt,
+                   (int)sc.cand_cap, (const uint32_t *)(sl.start + ndense), sl.poff, sc.lb_stat + sc.lb_tiles[0],
+                   sc.lb_ticket + 1, ctx->status);
     ncompact_dev = (int *)(sl.flag_scan + ndense);
     // one resident wave (a second wave would only repeat the screening)
     int sper = 0;
@@ -1695,9 +1863,13 @@ static int slots_build(ib_ctx *ctx, const CaseTab &ct, int M, int ndense, SlotGe
     launch_pdl(k_slot_sort, dim3(ctx->sm_count * (sper > 0 ? sper : 1)), dim3(kBlock), 0, s, ct, sg.mode,
                sc.ncompact_cap, (const int *)ncompact_dev, sg, (const uint32_t *)sl.dense_of,
                (const uint32_t *)sl.start, anchor, level, sl, ctx->status);
-    if (with_pairs)
-        launch_pdl(k_tile_pairs<T, KW>, dim3(ctx->sm_count * 8), dim3(kPairThreads), 0, s, ct, sc.ncompact_cap,
-                   (const int *)ncompact_dev, sl, anchor, wts);
+    if (with_pairs) {
+        // one resident wave
+        int pper = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pper, k_tile_pairs<T, KW>, kPairThreads, 0);
+        launch_pdl(k_tile_pairs<T, KW>, dim3(ctx->sm_count * (pper > 0 ? pper : 1)), dim3(kPairThreads), 0, s, ct,
+                   sc.ncompact_cap, (const int *)ncompact_dev, sl, anchor, wts);
+    }
     return check_launch("slot lists");
 }
 
