@@ -375,6 +375,16 @@ int ib_ctx_create(ib_ctx **ctx, size_t workspace_bytes) {
         return set_error(IB_ERR_CUDA, "context host word allocation failed");
     }
     *c->h_nlev = 0;
+    if (cudaStreamCreateWithFlags(&c->fork_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->fork_ev[0], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->fork_ev[1], cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFreeHost(c->h_nlev);
+        cudaFree(c->status);
+        cudaFree(c->ws);
+        delete c;
+        return set_error(IB_ERR_CUDA, "context stream/event creation failed");
+    }
     c->pass_kernels = IB_PASSES_AUTO;
     c->vol_split = 0;  // automatic
     c->spread_mode = IB_SPREAD_GATHER;
@@ -492,6 +502,9 @@ int ib_ctx_destroy(ib_ctx *c) {
         }
     for (auto e : c->pool) cudaEventDestroy(e);
     cudaFreeHost(c->h_nlev);
+    cudaStreamDestroy(c->fork_stream);
+    cudaEventDestroy(c->fork_ev[0]);
+    cudaEventDestroy(c->fork_ev[1]);
     for (int k = 0; k < ib_ctx::kStageSlots; ++k) {
         if (c->stage_ptr[k]) cudaFreeHost(c->stage_ptr[k]);
         if (c->stage_ev[k]) cudaEventDestroy(c->stage_ev[k]);

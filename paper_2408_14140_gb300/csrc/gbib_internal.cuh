@@ -155,6 +155,10 @@ struct ib_ctx {
     int gather_ctas;     // wavefront gather CTAs per SM (0: as many as fit)
     int gather_stage;    // candidates a gather CTA stages (0: the largest capacity)
     void *field_wait;    // cudaEvent_t waited on before the forcing passes (nullable)
+    // a second stream and two events: the first interpolation of a forcing
+    // call runs on it beside the slot-list kernels (fork and join)
+    cudaStream_t fork_stream;
+    cudaEvent_t fork_ev[2];
     // pinned staging ring for the case tables of batch calls: a slot is
     // reused only after the copy that last read it has run (its event)
     static constexpr int kStageSlots = 4;

@@ -1979,6 +1979,58 @@ static int run_mdf(ib_ctx *ctx, Arena &ar, const CaseTab &ct, const ib_particles
     }
     if (!ar.ok())
         return oom_error(ar.used, ar.cap);
+    PassArgs<T> a;
+    a.ct = ct;
+    a.part_of = part_of;
+    a.F = F_out;
+    a.dV = mk->dV;
+    a.ms = ms;
+    a.sl = sl;
+    a.mperm = mperm;
+    a.lev_mbeg = lo.lev_mbeg;
+    a.lev_sbeg = lev_sbeg;
+    a.tperm = tperm;
+    a.nlev = lo.nlev;
+    a.Ns = Ns;
+    a.dt = dt;
+    a.inv_dt = 1.0 / dt;
+    a.bar = bar;
+    a.st = ctx->status;
+    a.atomic = atomic ? 1 : 0;
+    // staging capacity of the wavefront gather (a layout choice: the sums
+    // are the same staged or not)
+    a.stage = ctx->gather_stage > 0 && ctx->gather_stage < TileStage<T>::N ? ctx->gather_stage : TileStage<T>::N;
+    // wavefronts enqueued as separate kernels: the count the last call on this
+    // context copied to a pinned host word (read without synchronising: an
+    // aligned 4-byte word is either the old or the new count; a short count
+    // only leaves more wavefronts to the persistent kernel)
+    ctx->nlev_hint = *(volatile int *)ctx->h_nlev;
+    const int Lenq = ctx->nlev_hint < P ? ctx->nlev_hint : P;
+    a.L0 = Lenq;
+    // the level kernels' launch shapes; the first interpolation runs on the
+    // context's second stream beside the slot-list kernels (it reads only the
+    // field and the prepared markers), and the first gather joins it
+    const bool level_path = !(sizeof(T) == 4 && order == IB_ORDER_SEQUENTIAL &&
+                              (pass_kernels == IB_PASSES_RESIDENT || pass_kernels == IB_PASSES_GROUPS));
+    const bool fork = level_path && Lenq >= 1;
+    cudaLaunchAttribute pdl[1];
+    pdl[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    pdl[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t ci = {};
+    ci.gridDim = dim3(sizeof(T) == 8 && kInterpSplit ? grid_blocks(3LL * M, kInterpThreads, ctx->sm_count)
+                                                     : grid_blocks(M, kInterpThreads, ctx->sm_count));
+    ci.blockDim = dim3(kInterpThreads);
+    ci.stream = s;
+    ci.attrs = pdl;
+    auto launch_interp = [&](int L, cudaStream_t st, bool dep) {
+        ci.stream = st;
+        ci.numAttrs = dep ? 1 : 0;
+        if constexpr (sizeof(T) == 8 && kInterpSplit)
+            cudaLaunchKernelEx(&ci, k_interp_level_c3<T, KER>, a, L);
+        else
+            cudaLaunchKernelEx(&ci, k_interp_level<T, KER>, a, L);
+        ci.stream = s;
+    };
     PhaseTimer tprep(ctx, IB_PHASE_MDF_PREP, s);
     cudaMemsetAsync(bar.count, 0, 2 * sizeof(unsigned int), s);
     cudaMemsetAsync(prep_ps.lo, 0x7f, sizeof(long long) * 3 * P, s);
@@ -1997,6 +2049,13 @@ static int run_mdf(ib_ctx *ctx, Arena &ar, const CaseTab &ct, const ib_particles
                lev_work, lev_cur);
     launch_pdl(k_marker_order, dim3(P < ctx->sm_count * 4 ? P : ctx->sm_count * 4), dim3(256), 0, s, P,
                (const int *)pp->marker_offset, (const int *)lo.mbase, mperm);
+    if (fork) {
+        cudaEventRecord(ctx->fork_ev[0], s);
+        cudaStreamWaitEvent(ctx->fork_stream, ctx->fork_ev[0], 0);
+        if (ctx->field_wait) cudaStreamWaitEvent(ctx->fork_stream, (cudaEvent_t)ctx->field_wait, 0);
+        launch_interp(0, ctx->fork_stream, false);
+        cudaEventRecord(ctx->fork_ev[1], ctx->fork_stream);
+    }
     sg.part_of = part_of;
     sg.rank = lo.rank;
     sg.box_lo = box_lo;
@@ -2006,6 +2065,7 @@ static int run_mdf(ib_ctx *ctx, Arena &ar, const CaseTab &ct, const ib_particles
         rc = slots_build<T, KW>(ctx, ct, M, (int)ndense, sg, ms.anchor, (const PS<T> *)ms.wts, lo.level, sl, sc,
                                 ncompact, s, true);
         if (rc) return rc;
+        a.sl = sl;
     }
     if constexpr (sizeof(T) == 4) {
     if (order == IB_ORDER_SEQUENTIAL &&
@@ -2059,38 +2119,9 @@ static int run_mdf(ib_ctx *ctx, Arena &ar, const CaseTab &ct, const ib_particles
     tprep.stop();
     // (the field is first read and written by the pass kernels below)
     if (ctx->field_wait) cudaStreamWaitEvent(s, (cudaEvent_t)ctx->field_wait, 0);
-    PassArgs<T> a;
-    a.ct = ct;
-    a.part_of = part_of;
-    a.F = F_out;
-    a.dV = mk->dV;
-    a.ms = ms;
-    a.sl = sl;
-    a.mperm = mperm;
-    a.lev_mbeg = lo.lev_mbeg;
-    a.lev_sbeg = lev_sbeg;
-    a.tperm = tperm;
-    a.nlev = lo.nlev;
-    a.Ns = Ns;
-    a.dt = dt;
-    a.inv_dt = 1.0 / dt;
-    a.bar = bar;
-    a.st = ctx->status;
-    a.atomic = atomic ? 1 : 0;
-    // staging capacity of the wavefront gather (a layout choice: the sums
-    // are the same staged or not)
-    a.stage = ctx->gather_stage > 0 && ctx->gather_stage < TileStage<T>::N ? ctx->gather_stage : TileStage<T>::N;
-    // wavefronts enqueued as separate kernels: the count the last call on this
-    // context copied to a pinned host word (read without synchronising: an
-    // aligned 4-byte word is either the old or the new count; a short count
-    // only leaves more wavefronts to the persistent kernel)
-    ctx->nlev_hint = *(volatile int *)ctx->h_nlev;
-    const int Lenq = ctx->nlev_hint < P ? ctx->nlev_hint : P;
-    a.L0 = Lenq;
     // one timed phase: the wavefront kernels and the persistent remainder
     PhaseTimer tpass(ctx, IB_PHASE_MDF_PASSES, s);
     {
-        const int gi = grid_blocks(M, kInterpThreads, ctx->sm_count);
         const size_t gsm = level_stage_bytes<T>(a.stage);
         cudaFuncSetAttribute(k_gather_level<T, KER>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsm);
         // one resident wave of gather CTAs (grid-stride over the wavefront's tiles)
@@ -2098,40 +2129,30 @@ static int run_mdf(ib_ctx *ctx, Arena &ar, const CaseTab &ct, const ib_particles
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&gper, k_gather_level<T, KER>, kGatherThreads, gsm);
         if (gper < 1) gper = 1;
         if (ctx->gather_ctas > 0 && ctx->gather_ctas < gper) gper = ctx->gather_ctas;
-        const int gg = ctx->sm_count * gper;
         // every level kernel after the first is a programmatic dependent of
-        // the one before it (see k_interp_level)
-        cudaLaunchAttribute pdl[1];
-        pdl[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-        pdl[0].val.programmaticStreamSerializationAllowed = 1;
-        cudaLaunchConfig_t ci = {}, cg = {};
-        ci.gridDim = dim3(gi);
-        ci.blockDim = dim3(kInterpThreads);
-        ci.stream = s;
-        ci.attrs = pdl;
-        cudaLaunchConfig_t ci3 = ci;
-        ci3.gridDim = dim3(grid_blocks(3LL * M, kInterpThreads, ctx->sm_count));
-        cg = ci;
-        cg.gridDim = dim3(gg);
+        // the one before it (see k_interp_level); the first gather instead
+        // waits for the interpolation on the second stream
+        cudaLaunchConfig_t cg = {};
+        cg.gridDim = dim3(ctx->sm_count * gper);
         cg.blockDim = dim3(kGatherThreads);
         cg.dynamicSmemBytes = gsm;
-        cg.numAttrs = 1;
+        cg.stream = s;
+        cg.attrs = pdl;
         // the atomic form: one lane per marker of the largest wavefront at most
-        cudaLaunchConfig_t cs = ci;
+        cudaLaunchConfig_t cs = cg;
         cs.gridDim = dim3(grid_blocks(M, 256, ctx->sm_count));
         cs.blockDim = dim3(256);
-        cs.numAttrs = 1;
+        cs.dynamicSmemBytes = 0;
+        if (fork) cudaStreamWaitEvent(s, ctx->fork_ev[1], 0);
         for (int L = 0; L < Lenq; ++L)
             for (int m = 0; m < Ns; ++m) {
-                {
+                const bool first = L == 0 && m == 0;
+                if (!first || !fork) {
                     PhaseTimer ti(ctx, IB_PHASE_MDF_INTERP, s);
-                    ci.numAttrs = ci3.numAttrs = (L > 0 || m > 0) ? 1 : 0;
-                    if constexpr (sizeof(T) == 8 && kInterpSplit)
-                        cudaLaunchKernelEx(&ci3, k_interp_level_c3<T, KER>, a, L);
-                    else
-                        cudaLaunchKernelEx(&ci, k_interp_level<T, KER>, a, L);
+                    launch_interp(L, s, !first);
                 }
                 PhaseTimer tg(ctx, IB_PHASE_MDF_GATHER, s);
+                cg.numAttrs = cs.numAttrs = first && fork ? 0 : 1;
                 if (atomic)
                     cudaLaunchKernelEx(&cs, k_scatter_level<T, KER>, a, L);
                 else
