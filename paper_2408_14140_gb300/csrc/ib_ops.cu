@@ -1069,7 +1069,10 @@ __global__ void __launch_bounds__(kPairThreads, 5) k_tile_pairs(CaseTab ct, int 
     PS<T> *const pwts = (PS<T> *)sl.pw;
     grid_dep_wait();
     constexpr int KW3 = KW * KW * KW;
-    __shared__ unsigned int s_anc[kMaxCand];                // (x + 3) | (y + 3) << 4 | (z + 3) << 8
+    // per candidate: the in-tile stencil offsets per axis (bits 0-3 x, 4-7 y,
+    // 8-11 z) and its first stencil cell relative to the tile, x + 8 y + 64 z
+    // + 256, from bit 12
+    __shared__ unsigned int s_anc[kMaxCand];
     __shared__ unsigned int s_cnt[kPairWarps][kTileCells];  // counts, then list cursors
     __shared__ int s_wp[kPairWarps], s_wb[kPairWarps];
     const int ncompact = min(*ncompact_p, ncompact_cap);
@@ -1078,10 +1081,12 @@ __global__ void __launch_bounds__(kPairThreads, 5) k_tile_pairs(CaseTab ct, int 
     // (ox | oy << 2 | oz << 4, or ~0u past the stencil)
     constexpr int kSub = (KW3 + 31) / 32;
     unsigned kcode[kSub];
+    int koff[kSub];  // the offset's cell step x + 8 y + 64 z
 #pragma unroll
     for (int q = 0; q < kSub; ++q) {
         const int k = lane + 32 * q;
         kcode[q] = k < KW3 ? (unsigned)((k % KW) | (((k / KW) % KW) << 2) | ((k / (KW * KW)) << 4)) : ~0u;
+        koff[q] = (k % KW) + kTile * ((k / KW) % KW) + kTile * kTile * (k / (KW * KW));
     }
     for (int cs = blockIdx.x; cs < ncompact; cs += gridDim.x) {
         const int4 lo = sl.geo_lo[cs], dim = sl.geo_dim[cs];
@@ -1096,13 +1101,19 @@ __global__ void __launch_bounds__(kPairThreads, 5) k_tile_pairs(CaseTab ct, int 
         for (int i = tid; i < nc; i += blockDim.x) {
             const uint64_t an = anchor[sl.cand[b + i]];
             int d[3] = {anchor_x(an) - lo.x + 3, anchor_y(an) - lo.y + 3, anchor_z(an) - lo.z + 3};
+            const int dm[3] = {dim.x, dim.y, dim.z};
+            unsigned code = 0;
 #pragma unroll
             for (int q = 0; q < 3; ++q) {
                 if (d[q] < 0) d[q] += g.n[q];
                 if (d[q] >= g.n[q]) d[q] -= g.n[q];
-                d[q] = min(d[q], 15);  // a candidate's anchor lies within [-3, 8) of the tile
+                d[q] = min(d[q], 15) - 3;  // a candidate's anchor lies within [-3, 8) of the tile
+                unsigned mq = 0;
+#pragma unroll
+                for (int k = 0; k < KW; ++k) mq |= (d[q] + k >= 0 && d[q] + k < dm[q]) ? 1u << k : 0u;
+                code |= mq << (4 * q);
             }
-            s_anc[i] = (unsigned)d[0] | ((unsigned)d[1] << 4) | ((unsigned)d[2] << 8);
+            s_anc[i] = code | (unsigned)(d[0] + kTile * d[1] + kTile * kTile * d[2] + 256) << 12;
         }
         for (int c = tid; c < kPairWarps * kTileCells; c += blockDim.x) (&s_cnt[0][0])[c] = 0;
         __syncthreads();
@@ -1114,11 +1125,8 @@ __global__ void __launch_bounds__(kPairThreads, 5) k_tile_pairs(CaseTab ct, int 
         // cell of candidate i's stencil offset (lane, q), or -1
         auto cell_of = [&](unsigned pk, int q) {
             const unsigned o = kcode[q];
-            const int x = (int)(pk & 15) - 3 + (int)(o & 3), y = (int)((pk >> 4) & 15) - 3 + (int)((o >> 2) & 3),
-                      z = (int)(pk >> 8) - 3 + (int)((o >> 4) & 3);
-            return (o != ~0u && x >= 0 && x < dim.x && y >= 0 && y < dim.y && z >= 0 && z < dim.z)
-                       ? (z * kTile + y) * kTile + x
-                       : -1;
+            const unsigned in = (pk >> (o & 3)) & (pk >> (4 + ((o >> 2) & 3))) & (pk >> (8 + ((o >> 4) & 3)));
+            return (o != ~0u && (in & 1u)) ? (int)(pk >> 12) - 256 + koff[q] : -1;
         };
         for (int i = i0; i < i1; ++i) {
             const unsigned pk = s_anc[i];
