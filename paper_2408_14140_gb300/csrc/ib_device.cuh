@@ -144,6 +144,9 @@ struct Slots {
     int2 *band;
     uint32_t *pairs;
     int *nband;        // [ncompact_max] band cells of the tile
+    // [ncompact_max] the tile's list record {first pair poff[b], pairs,
+    // band cells, candidates}, one load for the wavefront gather
+    int4 *tinfo;
     // [KW^3 M] per pair, its weight product pair_weight(w, ox, oy, oz) in the
     // pass-sum type PS<T> (parallel to pairs; nullable)
     void *pw;

@@ -1162,7 +1162,11 @@ __global__ void __launch_bounds__(kPairThreads, 5) k_tile_pairs(CaseTab ct, int 
         const int cbase[2] = {cp0, cp0 + tot[0]};
         if (tot[0] > 0) band[cb0] = make_int2((2 * tid) | (tot[0] << 16), cbase[0]);
         if (tot[1] > 0) band[cb0 + (tot[0] > 0)] = make_int2((2 * tid + 1) | (tot[1] << 16), cbase[1]);
-        if (tid == blockDim.x - 1) sl.nband[cs] = cb0 + (tot[0] > 0) + (tot[1] > 0);
+        if (tid == blockDim.x - 1) {
+            const int nbd = cb0 + (tot[0] > 0) + (tot[1] > 0);
+            sl.nband[cs] = nbd;
+            sl.tinfo[cs] = make_int4((int)sl.poff[b], (int)(sl.poff[b + nc] - sl.poff[b]), nbd, nc);
+        }
 #pragma unroll
         for (int h = 0; h < 2; ++h)
 #pragma unroll
@@ -1500,18 +1504,17 @@ __device__ __forceinline__ bool gather_tile_level(const CaseTab &ct, int cs, con
                                                   double inv_dt, PS<T> *sA, uint32_t *sp, PS<T> *spw, int stage,
                                                   Wait wait) {
     using S = PS<T>;
+    // the tile's record, geometry and case: independent loads
+    const int4 ti = sl.tinfo[cs];
+    const int4 lo = sl.geo_lo[cs], dim = sl.geo_dim[cs];
     const DevCase cd = ct.get(sl.geo_case[cs]);
     const DevGrid &g = cd.g;
     const long long N = (long long)g.n[0] * g.n[1] * g.n[2];
     T *const u = (T *)cd.u;
     T *const f_out = (T *)cd.f;
-    const int4 lo = sl.geo_lo[cs], dim = sl.geo_dim[cs];
-    const uint32_t d = sl.dense_of[cs];
-    const int nc = (int)(sl.start[d + 1] - sl.start[d]);
-    const int nb = sl.nband[cs];
+    const uint32_t pb = (uint32_t)ti.x;
+    const int np = ti.y, nb = ti.z, nc = ti.w;
     const uint32_t *cand = sl.cand + dim.w;
-    const uint32_t pb = sl.poff[dim.w];
-    const int np = (int)(sl.poff[dim.w + nc] - pb);
     const int2 *band = sl.band + pb;
     const uint32_t *pairs = sl.pairs + pb;
     const S *pwg = (const S *)sl.pw + pb;
@@ -1832,11 +1835,13 @@ static int slots_alloc(Arena &ar, int M, int ndense, int mode, Slots &sl, SlotSc
         sl.pairs = ar.take<uint32_t>((size_t)KW3 * M);
         sl.pw = ar.take<PS<T>>((size_t)KW3 * M);
         sl.nband = ar.take<int>(ncap);
+        sl.tinfo = ar.take<int4>(ncap);
     } else {
         sl.pcnt = sl.poff = nullptr;
         sl.band = nullptr;
         sl.pairs = nullptr;
         sl.nband = nullptr;
+        sl.tinfo = nullptr;
         sl.pw = nullptr;
     }
     if (!ar.ok())
