@@ -259,6 +259,9 @@ class Runner:
         # the step's first volume integrals run on a side stream (own context)
         # while the forcing call prepares; its passes wait for them
         self.ctx_v = api.Context()
+        # the volume integrals after the forcing reuse the cells and alpha the
+        # ones before it kept (the particles do not move in between)
+        self.plan = api.PvfPlan(self.ctx_v, case.P, int(2 * np.max(case.radius) / case.h + 4) ** 3)
         self.side = torch.cuda.Stream(device=device)
         self.ev_v = torch.cuda.Event()
         self.ctx.set_field_wait(self.ev_v)
@@ -295,7 +298,7 @@ class Runner:
         with torch.cuda.stream(self.side):
             # two CTAs per particle: the preparation's kernels keep most SMs
             self.ctx_v.set_volume_split(2)
-            self.ctx_v.particle_volume_integrals(self.u, c.h, self.parts, out=self.I0)
+            self.ctx_v.particle_volume_integrals_keep(self.u, c.h, self.parts, self.plan, out=self.I0)
             self.ev_v.record(self.side)
         ctx.ib_multidirect_forcing(self.u, c.h, self.parts, self.marks, c.Ns, c.dt, F_out=self.F,
                                    delta=self.delta, order=self.order)
@@ -303,8 +306,7 @@ class Runner:
         # force and torque sums (forces only)
         self.side.wait_stream(main)
         with torch.cuda.stream(self.side):
-            self.ctx_v.set_volume_split(0)
-            self.ctx_v.particle_volume_integrals(self.u, c.h, self.parts, out=self.I1)
+            self.ctx_v.particle_volume_integrals_plan(self.u, c.h, self.parts, self.plan, out=self.I1)
         ctx.particle_force_torque(self.parts, self.marks, self.F, c.rho_f, out=(self.Fib, self.Tib))
         main.wait_stream(self.side)
         ctx.particle_collide_update(self.parts, c.n, c.h, c.phys(), c.dt, self.Fib, self.Tib,

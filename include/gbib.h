@@ -278,6 +278,34 @@ GBIB_API int particle_volume_integrals(ib_ctx *ctx, const ib_grid *grid, const v
                               const ib_particles *parts, double *Iu,
                               double *Irxu, double *vol, void *stream);
 
+/* ---- volume integrals twice at the same particle positions --------------
+ * The step integrates the PVF of each particle over the field before and
+ * after the forcing (Eqs. particle1/particle2, Sec. 3.2.2) with the particles
+ * where they are: the cells and their volume fractions alpha are the same.
+ * particle_volume_integrals_keep computes what particle_volume_integrals
+ * computes and keeps in `plan` the cells each CTA visited, plane by plane, with
+ * the boundary cells' alpha; particle_volume_integrals_plan then integrates
+ * another field u (same grid, same particles) from the kept cells, without
+ * evaluating a level set, with the context's split (ib_ctx_set_volume_split)
+ * whatever the keeping call's was: bitwise the sums particle_volume_integrals
+ * gives on that field with that split.  A plan holds up to P particles
+ * whose stencil boxes have at most max_box_cells cells (at most 40 cells per
+ * axis); a larger box raises IB_ERR_UNSUPPORTED in the context status.  The
+ * plan call checks the grid (IB_ERR_INVALID) and, on the device, that every
+ * particle's X_r and radius equal the kept ones (IB_ERR_INVALID in the status;
+ * that particle's integrals are then 0).  The plan is device memory owned by
+ * the caller: create it once (not under stream capture), destroy it after its
+ * last call has run.                                                       */
+typedef struct ib_pvf_plan ib_pvf_plan;
+GBIB_API int ib_pvf_plan_create(ib_ctx *ctx, int P, int max_box_cells, ib_pvf_plan **plan);
+GBIB_API int ib_pvf_plan_destroy(ib_pvf_plan *plan);
+GBIB_API int particle_volume_integrals_keep(ib_ctx *ctx, const ib_grid *grid, const void *u,
+                                            const ib_particles *parts, ib_pvf_plan *plan, double *Iu,
+                                            double *Irxu, double *vol, void *stream);
+GBIB_API int particle_volume_integrals_plan(ib_ctx *ctx, const ib_grid *grid, const void *u,
+                                            const ib_particles *parts, const ib_pvf_plan *plan,
+                                            double *Iu, double *Irxu, double *vol, void *stream);
+
 /* ---- PVF volume integrals of ellipsoids: Sec. 4.1, Eq. (level-set
  * function of spheroidal geometries) -----------------------------------
  * As particle_volume_integrals, for P axis-aligned ellipsoids centred at

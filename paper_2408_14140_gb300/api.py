@@ -55,7 +55,9 @@ EXPORTS = ["ib_ctx_create", "ib_ctx_reserve", "ib_ctx_destroy", "ib_ctx_status",
            "particle_volume_integrals_ellipsoid", "particle_drag_force",
            "ib_batch_table_create", "ib_batch_table_destroy", "ib_batch_table_multidirect_forcing",
            "ib_batch_table_volume_integrals", "ib_batch_table_collide_update", "ib_ctx_set_spread_mode",
-           "ib_ctx_set_gather", "fluid_predictor", "level_projection", "ib_batch_table_update"]
+           "ib_ctx_set_gather", "fluid_predictor", "level_projection", "ib_batch_table_update",
+           "ib_pvf_plan_create", "ib_pvf_plan_destroy", "particle_volume_integrals_keep",
+           "particle_volume_integrals_plan"]
 
 
 class IBError(RuntimeError):
@@ -138,6 +140,10 @@ def load(path: str = LIB_PATH):
         "ib_batch_table_multidirect_forcing": (i, [p, p, p, p, i, d, i, i, p, p]),
         "ib_batch_table_volume_integrals": (i, [p, p, p, p, p, p, p]),
         "ib_batch_table_collide_update": (i, [p, p, p, d, p, p, p, p, p, p, p, p]),
+        "ib_pvf_plan_create": (i, [p, i, i, ctypes.POINTER(p)]),
+        "ib_pvf_plan_destroy": (i, [p]),
+        "particle_volume_integrals_keep": (i, [p, p, p, p, p, p, p, p, p]),
+        "particle_volume_integrals_plan": (i, [p, p, p, p, p, p, p, p, p]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -408,6 +414,35 @@ class Context:
                    ctypes.byref(ps), _ptr(Iu), _ptr(Irxu), _ptr(vol), _stream(stream))
         return Iu, Irxu, vol
 
+    def _volume_call(self, fn, u, h, parts, plan, origin, out, stream):
+        n = (u.shape[3], u.shape[2], u.shape[1])
+        _need(u, "u", u.dtype, (3, n[2], n[1], n[0]))
+        ps = self.particles_struct(parts["Xr"], parts["Ur"], parts["Wr"], parts["radius"],
+                                   parts["rho_p"], parts["moff"])
+        P = ps.P
+        if out is None:
+            out = (torch.empty((P, 3), dtype=torch.float64, device=u.device),
+                   torch.empty((P, 3), dtype=torch.float64, device=u.device),
+                   torch.empty((P,), dtype=torch.float64, device=u.device))
+        Iu, Irxu, vol = out
+        _need(Iu, "Iu", torch.float64, (P, 3))
+        _need(Irxu, "Irxu", torch.float64, (P, 3))
+        _need(vol, "vol", torch.float64, (P,))
+        g = self._grid_of(u, n, h, origin)
+        self._call(fn, self.handle, ctypes.byref(g), _ptr(u), ctypes.byref(ps), plan.handle, _ptr(Iu), _ptr(Irxu),
+                   _ptr(vol), _stream(stream))
+        return Iu, Irxu, vol
+
+    def particle_volume_integrals_keep(self, u, h, parts, plan, origin=(0.0, 0.0, 0.0), out=None, stream=None):
+        """particle_volume_integrals, keeping the visited cells and their alpha
+        in ``plan`` (a :class:`PvfPlan`)."""
+        return self._volume_call(self.lib.particle_volume_integrals_keep, u, h, parts, plan, origin, out, stream)
+
+    def particle_volume_integrals_plan(self, u, h, parts, plan, origin=(0.0, 0.0, 0.0), out=None, stream=None):
+        """The volume integrals of another field at the particle positions the
+        plan was kept for, from the kept cells and alpha."""
+        return self._volume_call(self.lib.particle_volume_integrals_plan, u, h, parts, plan, origin, out, stream)
+
     def particle_volume_integrals_ellipsoid(self, u, h, Xr, axes, origin=(0.0, 0.0, 0.0), out=None,
                                             stream=None):
         """(Iu[P,3], Irxu[P,3], vol[P]) through the PVF of axis-aligned
@@ -591,6 +626,31 @@ class Context:
                    float(dt), _ptr(F_ib), _ptr(T_ib), _ptr(Iu_new), _ptr(Iu_old), _ptr(Irxu_new),
                    _ptr(Irxu_old), _ptr(Fc_out), _stream(stream))
         return Fc_out
+
+
+class PvfPlan:
+    """Device lists of a kept volume plan (``ib_pvf_plan_create``): up to P
+    particles whose stencil boxes have at most ``max_box_cells`` cells."""
+
+    def __init__(self, ctx, P, max_box_cells):
+        self.lib = ctx.lib
+        h = ctypes.c_void_p()
+        rc = self.lib.ib_pvf_plan_create(ctx.handle, int(P), int(max_box_cells), ctypes.byref(h))
+        if rc != IB_OK:
+            raise IBError(rc, self.lib.ib_last_error().decode())
+        self.handle = h
+        self.P = int(P)
+
+    def close(self):
+        if self.handle:
+            self.lib.ib_pvf_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class BatchTable:

@@ -8,6 +8,7 @@
 // then a fixed shuffle tree), so results are bitwise reproducible.
 #include <climits>
 #include <mutex>
+#include <new>
 
 #include "gbib_internal.cuh"
 
@@ -236,13 +237,31 @@ __device__ void volume_finish(double acc[7], double h, int p, int split, int nsp
 //   * boundary cells (the rest within R + 0.8661 h): alpha from the corners.
 // Per-row index ranges come from FP32 square roots widened by a cell; every
 // node and boundary cell is still tested exactly in FP64.
-template <typename T>
+// A kept volume plan (particle_volume_integrals_keep / _plan): per particle,
+// the cells each CTA visits plane by plane in its visiting order -- interior
+// cells (alpha = 1) and boundary cells with their alpha, or a skip mark --
+// so that a second call at the same particle positions repeats the same sums
+// from another field without evaluating a level set.  Capacity `cap` entries
+// per particle and list; a CTA's slab starts at dims0 dims1 z0.
+struct PvfPlanDev {
+    int cap;
+    int4 *hdr;        // [P][kVolAx] per plane: interior and boundary counts, first entries
+    unsigned *ient;   // [P][cap] interior cell i | j << 16
+    unsigned *bent;   // [P][cap] boundary cell i | j << 16, or kPvfSkip
+    float2 *balpha;   // [P][cap] boundary alpha as a float pair
+    double *pos;      // [P][4] X_r and R the plan was kept for
+};
+constexpr unsigned kPvfSkip = 0x80000000u;
+
+// MODE 0: plain; 1: also keep the plan; 2: the sums from a kept plan.
+template <typename T, int MODE = 0>
 __global__ void __launch_bounds__(kVolThreads, 3) k_volume(CaseTab ct, int P, int nsplit,
                                                         const double *__restrict__ Xr,
                                                         const double *__restrict__ radius,
                                                         double *__restrict__ partial,
                                                         unsigned int *__restrict__ done, double *Iu,
-                                                        double *Irxu, double *vol, DevStatus *st) {
+                                                        double *Irxu, double *vol, DevStatus *st,
+                                                        PvfPlanDev pl = PvfPlanDev{}) {
     extern __shared__ __align__(16) double s_vol[];
     // per-row work lists (rows <= kVolAx)
     __shared__ int r_na[kVolAx], r_nb[kVolAx], r_nc[2][kVolAx], r_ca[kVolAx], r_cb[kVolAx];
@@ -279,6 +298,25 @@ __global__ void __launch_bounds__(kVolThreads, 3) k_volume(CaseTab ct, int P, in
             s_c[a] = cc[a];
             s_box[a] = lo0[a];
             s_box[3 + a] = dm0[a];
+        }
+        if constexpr (MODE != 0) {
+            const bool tabbed = dm0[0] <= kVolMaxBox && dm0[1] <= kVolMaxBox && dm0[2] <= kVolMaxBox;
+            if (okk && (!tabbed || (long long)dm0[0] * dm0[1] * dm0[2] > pl.cap)) {
+                if (split == 0) raise_status(st, IB_ERR_UNSUPPORTED, p);
+                okk = false;
+            }
+            if constexpr (MODE == 1) {
+                if (split == 0) {
+                    pl.pos[4 * p] = cc[0], pl.pos[4 * p + 1] = cc[1], pl.pos[4 * p + 2] = cc[2];
+                    pl.pos[4 * p + 3] = R0;
+                }
+            } else {
+                const double *q = pl.pos + 4 * p;
+                if (okk && !(q[0] == cc[0] && q[1] == cc[1] && q[2] == cc[2] && q[3] == R0)) {
+                    if (split == 0) raise_status(st, IB_ERR_INVALID, p);  // not the plan's particle
+                    okk = false;
+                }
+            }
         }
         s_box[6] = okk;
         if (okk) {
@@ -425,7 +463,9 @@ __global__ void __launch_bounds__(kVolThreads, 3) k_volume(CaseTab ct, int P, in
                     buf[j * nx + i] = make_double2(fmax(-ph, 0.0), fmax(ph, 0.0));
                 }
             };
-            node_plane(z0, phi2 + (z0 & 1) * plane);
+            if (MODE != 2) node_plane(z0, phi2 + (z0 & 1) * plane);
+            // the CTA's entries in the plan: from dims0 dims1 z0 on, plane by plane
+            long long pi = (long long)p * pl.cap + (long long)dims[0] * dims[1] * z0, pb = pi;
             // per-thread sums.  r x u is split so that rz (constant over a cell
             // plane) multiplies plane sums once per plane:
             //   (ry w2 - rz w1, rz w0 - rx w2, rx w1 - ry w0), w = alpha u
@@ -435,10 +475,10 @@ __global__ void __launch_bounds__(kVolThreads, 3) k_volume(CaseTab ct, int P, in
             // rx w2, rx w1, ry w0 (no FP64 work per cell but alpha's)
             DF W[3] = {}, Pm[6] = {}, V = {};
             for (int kz = z0; kz < z1; ++kz) {
-                node_plane(kz + 1, phi2 + ((kz + 1) & 1) * plane);
+                if (MODE != 2) node_plane(kz + 1, phi2 + ((kz + 1) & 1) * plane);
                 // cell rows of plane kz: interior range and the boundary ranges around it
                 const double rz = tb[5 * kVolAx + kz], rz2 = tb[8 * kVolAx + kz];
-                for (int j = threadIdx.x; j < dims[1]; j += blockDim.x) {
+                for (int j = threadIdx.x; MODE != 2 && j < dims[1]; j += blockDim.x) {
                     bool in_out, in_in;
                     float wo, wi;
                     if constexpr (true) {
@@ -473,20 +513,42 @@ __global__ void __launch_bounds__(kVolThreads, 3) k_volume(CaseTab ct, int P, in
                     r_cb[j] = jb >= ja ? max(0, ib - jb) : 0;      // right boundary [jb+1, ib]
                     c_bnd[j] = r_ca[j] + r_cb[j];
                 }
-                __syncthreads();
-                warp0_scan(c_int, p_int, dims[1]);
-                warp0_scan(c_bnd, p_bnd, dims[1]);
-                __syncthreads();
+                int nint, nbnd;
+                if constexpr (MODE == 2) {
+                    // the plane's lists, wherever the keeping call's CTA put them
+                    const int4 hc = pl.hdr[p * kVolAx + kz];
+                    nint = hc.x;
+                    nbnd = hc.y;
+                    pi = (long long)p * pl.cap + hc.z;
+                    pb = (long long)p * pl.cap + hc.w;
+                } else {
+                    __syncthreads();
+                    warp0_scan(c_int, p_int, dims[1]);
+                    warp0_scan(c_bnd, p_bnd, dims[1]);
+                    __syncthreads();
+                    nint = p_int[dims[1]];
+                    nbnd = p_bnd[dims[1]];
+                    if (MODE == 1 && threadIdx.x == 0)
+                        pl.hdr[p * kVolAx + kz] =
+                            make_int4(nint, nbnd, (int)(pi - (long long)p * pl.cap), (int)(pb - (long long)p * pl.cap));
+                }
                 const double2 *b0 = phi2 + (kz & 1) * plane, *b1 = phi2 + ((kz + 1) & 1) * plane;
                 const float2 fz = sizeof(T) == 4 ? tbf[2 * kVolAx + kz] : make_float2(0.f, 0.f);
                 const float rz2f = tcf[2 * kVolAx + kz];
                 const long long plane_off = (long long)wrap_int(lo[2] + kz, g.n[2]) * g.n[1] * g.n[0];
                 double s0 = 0, s1 = 0, s2 = 0;  // plane sums of alpha u
                 // interior cells: alpha = 1
-                const int nint = p_int[dims[1]];
                 for (int q = threadIdx.x; q < nint; q += blockDim.x) {
-                    const int j = find_row(p_int, dims[1], q);
-                    const int i = r_ic[j] + (q - p_int[j]);
+                    int i, j;
+                    if constexpr (MODE == 2) {
+                        const unsigned e = pl.ient[pi + q];
+                        i = (int)(e & 0xffffu);
+                        j = (int)(e >> 16);
+                    } else {
+                        j = find_row(p_int, dims[1], q);
+                        i = r_ic[j] + (q - p_int[j]);
+                        if (MODE == 1) pl.ient[pi + q] = (unsigned)i | ((unsigned)j << 16);
+                    }
                     const long long cc = plane_off + row_off[j] + wrap_add(lo0w, i, g.n[0]);
                     if constexpr (sizeof(T) == 4) {
                         const float2 fx = tbf[i], fy = tbf[kVolAx + j];
@@ -514,17 +576,26 @@ __global__ void __launch_bounds__(kVolThreads, 3) k_volume(CaseTab ct, int P, in
                 }
                 nint_cells += (nint + (int)blockDim.x - 1 - (int)threadIdx.x) / (int)blockDim.x;
                 // boundary cells: alpha = sum of max(-phi, 0) / sum |phi| over the corners
-                const int nbnd = p_bnd[dims[1]];
                 for (int q = threadIdx.x; q < nbnd; q += blockDim.x) {
-                    const int j = find_row(p_bnd, dims[1], q);
-                    const int k = q - p_bnd[j];
-                    const int i = k < r_ca[j] ? r_ia[j] + k : r_ic[j] + c_int[j] + (k - r_ca[j]);
+                    int i, j;
+                    float2 a2 = make_float2(1.f, 0.f);
+                    if constexpr (MODE == 2) {
+                        const unsigned e = pl.bent[pb + q];
+                        if (e == kPvfSkip) continue;
+                        i = (int)(e & 0xffffu);
+                        j = (int)(e >> 16);
+                        a2 = pl.balpha[pb + q];
+                    } else {
+                        j = find_row(p_bnd, dims[1], q);
+                        const int k = q - p_bnd[j];
+                        i = k < r_ca[j] ? r_ia[j] + k : r_ic[j] + c_int[j] + (k - r_ca[j]);
+                        if (MODE == 1) pl.bent[pb + q] = kPvfSkip;  // until the cell counts
+                    }
                     {
                         // the cell's alpha in double-float (both field precisions)
                         const float d2f = tcf[i] + tcf[kVolAx + j] + rz2f;
-                        if (d2f > rout2f) continue;
-                        float2 a2 = make_float2(1.f, 0.f);
-                        if (!(d2f < rin2f)) {
+                        if (MODE != 2 && d2f > rout2f) continue;
+                        if (MODE != 2 && !(d2f < rin2f)) {
                             const int qn = j * nx + i;
                             const float4 *f0 = (const float4 *)b0, *f1 = (const float4 *)b1;
                             const float4 cn[8] = {f0[qn], f0[qn + 1], f0[qn + nx], f0[qn + nx + 1],
@@ -554,6 +625,10 @@ __global__ void __launch_bounds__(kVolThreads, 3) k_volume(CaseTab ct, int P, in
                                     a2 = make_float2(q1, rr * rd);
                                 }
                             }
+                        }
+                        if constexpr (MODE == 1) {
+                            pl.bent[pb + q] = (unsigned)i | ((unsigned)j << 16);
+                            pl.balpha[pb + q] = a2;
                         }
                         const long long cc = plane_off + row_off[j] + wrap_add(lo0w, i, g.n[0]);
                         if constexpr (sizeof(T) == 8) {
@@ -626,7 +701,9 @@ __global__ void __launch_bounds__(kVolThreads, 3) k_volume(CaseTab ct, int P, in
                     acc[3] = fma(-rz, s1, acc[3]);
                     acc[4] = fma(rz, s0, acc[4]);
                 }
-                __syncthreads();
+                pi += nint;
+                pb += nbnd;
+                if (MODE != 2) __syncthreads();
             }
             if constexpr (sizeof(T) == 8) {
                 acc[3] += sA;
@@ -1017,11 +1094,128 @@ static int run_volume_static(const CaseTab &ct, const ib_particles *pp, double *
     return check_launch("particle_volume_integrals_static");
 }
 
+template <typename T, int MODE>
+static int run_volume_plan(ib_ctx *ctx, Arena &ar, const CaseTab &ct, const ib_particles *pp, int nsplit,
+                           const PvfPlanDev &pl, double *Iu, double *Irxu, double *vol, cudaStream_t s) {
+    cudaFuncSetAttribute(k_volume<T, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kVolSmem);
+    double *partial = ar.take<double>((size_t)pp->P * nsplit * 7);
+    unsigned int *done = ar.take<unsigned int>(pp->P);
+    if (!ar.ok())
+        return oom_error(ar.used, ar.cap);
+    PhaseTimer tm(ctx, IB_PHASE_VOLUME, s);
+    cudaMemsetAsync(done, 0, sizeof(unsigned int) * pp->P, s);
+    k_volume<T, MODE><<<pp->P * nsplit, kVolThreads, kVolSmem, s>>>(ct, pp->P, nsplit, pp->Xr, pp->radius, partial,
+                                                                    done, Iu, Irxu, vol, ctx->status, pl);
+    return check_launch(MODE == 1 ? "particle_volume_integrals_keep" : "particle_volume_integrals_plan");
+}
+
 }  // namespace gbib
 
 using namespace gbib;
 
+// The kept volume plan: device lists and the call it was kept for.
+struct ib_pvf_plan {
+    int device;
+    int P, cap;
+    int nsplit;     // CTAs per particle of the keeping call (0: not kept yet)
+    ib_grid grid;   // the keeping call's grid
+    void *mem;
+    PvfPlanDev dev;
+};
+
+static bool same_grid(const ib_grid &a, const ib_grid &b) {
+    return a.n[0] == b.n[0] && a.n[1] == b.n[1] && a.n[2] == b.n[2] && a.h == b.h && a.origin[0] == b.origin[0] &&
+           a.origin[1] == b.origin[1] && a.origin[2] == b.origin[2] && a.prec == b.prec;
+}
+
 extern "C" {
+
+int ib_pvf_plan_create(ib_ctx *ctx, int P, int max_box_cells, ib_pvf_plan **plan) {
+    if (!ctx || !plan) return set_error(IB_ERR_INVALID, "NULL argument");
+    *plan = nullptr;
+    if (P < 1 || max_box_cells < 1 || max_box_cells > kVolMaxBox * kVolMaxBox * kVolMaxBox)
+        return set_error(IB_ERR_INVALID, "bad plan size (P %d, max_box_cells %d)", P, max_box_cells);
+    const size_t cap = (size_t)max_box_cells;
+    auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
+    const size_t b_hdr = up(sizeof(int4) * (size_t)P * kVolAx), b_ient = up(sizeof(unsigned) * P * cap),
+                 b_bent = b_ient, b_alpha = up(sizeof(float2) * P * cap), b_pos = up(sizeof(double) * 4 * (size_t)P);
+    ib_pvf_plan *pl = new (std::nothrow) ib_pvf_plan();
+    if (!pl) return set_error(IB_ERR_OOM, "plan object");
+    pl->device = ctx->device;
+    pl->P = P;
+    pl->cap = max_box_cells;
+    pl->nsplit = 0;
+    if (cudaMalloc(&pl->mem, b_hdr + b_ient + b_bent + b_alpha + b_pos) != cudaSuccess) {
+        cudaGetLastError();
+        delete pl;
+        return set_error(IB_ERR_OOM, "plan of %zu bytes", b_hdr + b_ient + b_bent + b_alpha + b_pos);
+    }
+    char *m = (char *)pl->mem;
+    pl->dev.cap = max_box_cells;
+    pl->dev.hdr = (int4 *)m;
+    pl->dev.ient = (unsigned *)(m + b_hdr);
+    pl->dev.bent = (unsigned *)(m + b_hdr + b_ient);
+    pl->dev.balpha = (float2 *)(m + b_hdr + b_ient + b_bent);
+    pl->dev.pos = (double *)(m + b_hdr + b_ient + b_bent + b_alpha);
+    *plan = pl;
+    return IB_OK;
+}
+
+int ib_pvf_plan_destroy(ib_pvf_plan *plan) {
+    if (!plan) return IB_OK;
+    cudaDeviceSynchronize();
+    cudaFree(plan->mem);
+    delete plan;
+    return IB_OK;
+}
+
+int particle_volume_integrals_keep(ib_ctx *ctx, const ib_grid *grid, const void *u, const ib_particles *parts,
+                                   ib_pvf_plan *plan, double *Iu, double *Irxu, double *vol, void *stream) {
+    if (!ctx || !plan) return set_error(IB_ERR_INVALID, "NULL argument");
+    int rc = validate_grid(grid, 1);
+    if (rc) return rc;
+    if (!parts || parts->P < 0) return set_error(IB_ERR_INVALID, "bad particles");
+    if (parts->P != plan->P) return set_error(IB_ERR_INVALID, "plan made for %d particles, not %d", plan->P, parts->P);
+    if (!u || !parts->Xr || !parts->radius) return set_error(IB_ERR_INVALID, "NULL array");
+    const CaseTab ct = single_case(grid, (void *)u, nullptr, parts->P);
+    Arena ar(ctx);
+    int nsplit;
+    if (grid->prec == IB_F64) {
+        cudaFuncSetAttribute(k_volume<double, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kVolSmem);
+        nsplit = volume_split(ctx, (const void *)k_volume<double, 1>, kVolSmem, parts->P);
+    } else {
+        cudaFuncSetAttribute(k_volume<float, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kVolSmem);
+        nsplit = volume_split(ctx, (const void *)k_volume<float, 1>, kVolSmem, parts->P);
+    }
+    plan->nsplit = nsplit;
+    plan->grid = *grid;
+    if (grid->prec == IB_F64)
+        return run_volume_plan<double, 1>(ctx, ar, ct, parts, nsplit, plan->dev, Iu, Irxu, vol, (cudaStream_t)stream);
+    return run_volume_plan<float, 1>(ctx, ar, ct, parts, nsplit, plan->dev, Iu, Irxu, vol, (cudaStream_t)stream);
+}
+
+int particle_volume_integrals_plan(ib_ctx *ctx, const ib_grid *grid, const void *u, const ib_particles *parts,
+                                   const ib_pvf_plan *plan, double *Iu, double *Irxu, double *vol, void *stream) {
+    if (!ctx || !plan) return set_error(IB_ERR_INVALID, "NULL argument");
+    int rc = validate_grid(grid, 1);
+    if (rc) return rc;
+    if (!parts || parts->P != plan->P) return set_error(IB_ERR_INVALID, "plan made for %d particles", plan->P);
+    if (plan->nsplit < 1) return set_error(IB_ERR_INVALID, "plan not kept yet");
+    if (!same_grid(*grid, plan->grid)) return set_error(IB_ERR_INVALID, "grid differs from the plan's");
+    if (!u || !parts->Xr || !parts->radius) return set_error(IB_ERR_INVALID, "NULL array");
+    const CaseTab ct = single_case(grid, (void *)u, nullptr, parts->P);
+    Arena ar(ctx);
+    // any split: the plan holds each plane's lists
+    int nsplit;
+    if (grid->prec == IB_F64) {
+        cudaFuncSetAttribute(k_volume<double, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kVolSmem);
+        nsplit = volume_split(ctx, (const void *)k_volume<double, 2>, kVolSmem, parts->P);
+        return run_volume_plan<double, 2>(ctx, ar, ct, parts, nsplit, plan->dev, Iu, Irxu, vol, (cudaStream_t)stream);
+    }
+    cudaFuncSetAttribute(k_volume<float, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kVolSmem);
+    nsplit = volume_split(ctx, (const void *)k_volume<float, 2>, kVolSmem, parts->P);
+    return run_volume_plan<float, 2>(ctx, ar, ct, parts, nsplit, plan->dev, Iu, Irxu, vol, (cudaStream_t)stream);
+}
 
 int particle_volume_integrals(ib_ctx *ctx, const ib_grid *grid, const void *u, const ib_particles *parts,
                               double *Iu, double *Irxu, double *vol, void *stream) {
