@@ -10,6 +10,7 @@
 #include <mutex>
 #include <new>
 
+#include "df.cuh"
 #include "gbib_internal.cuh"
 
 namespace gbib {
@@ -64,7 +65,8 @@ constexpr size_t kVolSmem = 2 * kVolAx * kVolAx * sizeof(double2) + 9 * kVolAx *
 // floats -- Knuth's TwoSum for the addition error and the fused multiply-add
 // for the exact product error (Dekker 1971) -- about 44 significant bits on
 // the FP32 pipes, which run 64 times faster than FP64 on GB300.  Used for the
-// field sums of FP32 fields; the level set and alpha stay FP64.
+// level set, alpha and the field sums of both field precisions; the per-CTA
+// tables and the CTA reduction stay FP64.
 struct DF {
     float hi, lo;
 };
@@ -91,10 +93,14 @@ __device__ __forceinline__ void df_warp_sum(DF &a) {
         df_add2(a, bh, bl + lo);
     }
 }
-__device__ __forceinline__ float2 df_split(double x) {
+__device__ __forceinline__ float2 df_split_rn(double x) {
     const float h = (float)x;
     return make_float2(h, (float)(x - (double)h));
 }
+// A field value as a float pair: an FP32 value exactly (lo = 0), an FP64 value
+// split on the integer pipe (within 2^-47 of the double; no FP64 operation)
+__device__ __forceinline__ float2 field_pair(float x) { return make_float2(x, 0.0f); }
+__device__ __forceinline__ float2 field_pair(double x) { return df_split(x); }
 // a + b, both double-float, renormalised (TwoSum on the high parts)
 __device__ __forceinline__ DF df_sum(DF a, DF b) {
     const float s = a.hi + b.hi;
@@ -331,7 +337,7 @@ __global__ void __launch_bounds__(kVolThreads, 3) k_volume(CaseTab ct, int P, in
             s_d[5] = sh * sh;
             s_f[0] = (float)(g.org[0] + (double)lo0[0] * hh - cc[0]);
             s_f[1] = (float)(g.org[0] + ((double)lo0[0] + 0.5) * hh - cc[0]);
-            const float2 ir = df_split(s_d[1]);
+            const float2 ir = df_split_rn(s_d[1]);
             s_f[2] = ir.x;
             s_f[3] = ir.y;
         }
@@ -365,8 +371,8 @@ __global__ void __launch_bounds__(kVolThreads, 3) k_volume(CaseTab ct, int P, in
                     tb[a * kVolAx + i] = xn * xn;
                     tb[(3 + a) * kVolAx + i] = xc;
                     tb[(6 + a) * kVolAx + i] = xc * xc;
-                    tbf[a * kVolAx + i] = df_split(xc);
-                    tsq[a * kVolAx + i] = df_split(xn * xn);
+                    tbf[a * kVolAx + i] = df_split_rn(xc);
+                    tsq[a * kVolAx + i] = df_split_rn(xn * xn);
                     tcf[a * kVolAx + i] = (float)(xc * xc);
                 }
             const float2 iRf = make_float2(s_f[2], s_f[3]);
@@ -400,23 +406,16 @@ __global__ void __launch_bounds__(kVolThreads, 3) k_volume(CaseTab ct, int P, in
             // the cell bounds, far beyond the FP32 error of the squares)
             const float sh2f = (float)sh2 * (1.0f + 1e-5f), sl2f = (float)sl2 * (1.0f - 1e-5f);
             auto node_plane = [&](int kn, double2 *buf) {
-                const double zz = tb[2 * kVolAx + kn];
                 const int rows = dims[1] + 1;
                 for (int j = threadIdx.x; j < rows; j += blockDim.x) {
                     bool in_shell, beyond_sl;
                     float wo, wi;
-                    if constexpr (true) {
+                    {
                         const float dyz = tsq[kVolAx + j].x + tsq[2 * kVolAx + kn].x;
                         in_shell = dyz < sh2f;
                         beyond_sl = sl2f > dyz;
                         wo = sqrtf(fmaxf(sh2f - dyz, 0.f));
                         wi = sqrtf(fmaxf(sl2f - dyz, 0.f));
-                    } else {
-                        const double dyz = tb[kVolAx + j] + zz;
-                        in_shell = dyz < sh2;
-                        beyond_sl = sl2 > dyz;
-                        wo = in_shell ? sqrtf((float)(sh2 - dyz)) : 0.f;
-                        wi = beyond_sl ? sqrtf((float)(sl2 - dyz)) : 0.f;
                     }
                     int a0 = 0, n0 = 0, a1 = 0, n1 = 0;
                     if (in_shell) {
@@ -448,7 +447,7 @@ __global__ void __launch_bounds__(kVolThreads, 3) k_volume(CaseTab ct, int P, in
                     const int i = k < r_nc[0][j] ? r_na[j] + k : r_nb[j] + (k - r_nc[0][j]);
                     // every listed node gets its level set value (nodes slightly
                     // outside the shell too: the values stay exact)
-                    if constexpr (true) {
+                    {
                         // double-float level set, stored as
                         // (max(-phi, 0), max(phi, 0)) float pairs
                         const DF x2 = df_sum(DF{tsq[i].x, tsq[i].y},
@@ -457,42 +456,30 @@ __global__ void __launch_bounds__(kVolThreads, 3) k_volume(CaseTab ct, int P, in
                         const DF ph = x2.hi > 0.0f ? df_phi(x2, iRf) : DF{-1.0f, 0.0f};
                         ((float4 *)buf)[j * nx + i] = ph.hi < 0.0f ? make_float4(-ph.hi, -ph.lo, 0.f, 0.f)
                                                                    : make_float4(0.f, 0.f, ph.hi, ph.lo);
-                        continue;
                     }
-                    const double ph = fma(norm_from_square(tb[i] + tb[kVolAx + j] + zz), iR, -1.0);
-                    buf[j * nx + i] = make_double2(fmax(-ph, 0.0), fmax(ph, 0.0));
                 }
             };
             if (MODE != 2) node_plane(z0, phi2 + (z0 & 1) * plane);
             // the CTA's entries in the plan: from dims0 dims1 z0 on, plane by plane
             long long pi = (long long)p * pl.cap + (long long)dims[0] * dims[1] * z0, pb = pi;
-            // per-thread sums.  r x u is split so that rz (constant over a cell
-            // plane) multiplies plane sums once per plane:
-            //   (ry w2 - rz w1, rz w0 - rx w2, rx w1 - ry w0), w = alpha u
-            double sA = 0, sB = 0, sC = 0, sD = 0, svol = 0;
+            // per-thread double-float sums of w = alpha u, of the six products
+            // ry w2, rz w1, rz w0, rx w2, rx w1, ry w0 (r x w = (ry w2 - rz w1,
+            // rz w0 - rx w2, rx w1 - ry w0)) and of the boundary cells' alpha;
+            // no FP64 operation per cell in either field precision
             long long nint_cells = 0;
-            // FP32 fields: double-float sums of w and of ry w2, rz w1, rz w0,
-            // rx w2, rx w1, ry w0 (no FP64 work per cell but alpha's)
             DF W[3] = {}, Pm[6] = {}, V = {};
             for (int kz = z0; kz < z1; ++kz) {
                 if (MODE != 2) node_plane(kz + 1, phi2 + ((kz + 1) & 1) * plane);
                 // cell rows of plane kz: interior range and the boundary ranges around it
-                const double rz = tb[5 * kVolAx + kz], rz2 = tb[8 * kVolAx + kz];
                 for (int j = threadIdx.x; MODE != 2 && j < dims[1]; j += blockDim.x) {
                     bool in_out, in_in;
                     float wo, wi;
-                    if constexpr (true) {
+                    {
                         const float ryz2 = tcf[kVolAx + j] + tcf[2 * kVolAx + kz];
                         in_out = ryz2 <= rout2f;
                         in_in = ryz2 < rin2f;
                         wo = sqrtf(fmaxf(rout2f - ryz2, 0.f));
                         wi = sqrtf(fmaxf(rin2f - ryz2, 0.f));
-                    } else {
-                        const double ryz2 = tb[7 * kVolAx + j] + rz2;
-                        in_out = ryz2 <= rout2;
-                        in_in = ryz2 < rin2;
-                        wo = in_out ? sqrtf((float)(rout2 - ryz2)) : 0.f;
-                        wi = in_in ? sqrtf((float)(rin2 - ryz2)) : 0.f;
                     }
                     int ia = 0, ib = -1, ja = 0, jb = -1;
                     if (in_out) {
@@ -533,10 +520,9 @@ __global__ void __launch_bounds__(kVolThreads, 3) k_volume(CaseTab ct, int P, in
                             make_int4(nint, nbnd, (int)(pi - (long long)p * pl.cap), (int)(pb - (long long)p * pl.cap));
                 }
                 const double2 *b0 = phi2 + (kz & 1) * plane, *b1 = phi2 + ((kz + 1) & 1) * plane;
-                const float2 fz = sizeof(T) == 4 ? tbf[2 * kVolAx + kz] : make_float2(0.f, 0.f);
+                const float2 fz = tbf[2 * kVolAx + kz];
                 const float rz2f = tcf[2 * kVolAx + kz];
                 const long long plane_off = (long long)wrap_int(lo[2] + kz, g.n[2]) * g.n[1] * g.n[0];
-                double s0 = 0, s1 = 0, s2 = 0;  // plane sums of alpha u
                 // interior cells: alpha = 1
                 for (int q = threadIdx.x; q < nint; q += blockDim.x) {
                     int i, j;
@@ -550,29 +536,17 @@ __global__ void __launch_bounds__(kVolThreads, 3) k_volume(CaseTab ct, int P, in
                         if (MODE == 1) pl.ient[pi + q] = (unsigned)i | ((unsigned)j << 16);
                     }
                     const long long cc = plane_off + row_off[j] + wrap_add(lo0w, i, g.n[0]);
-                    if constexpr (sizeof(T) == 4) {
-                        const float2 fx = tbf[i], fy = tbf[kVolAx + j];
-                        const float v0 = u[cc], v1 = u[N + cc], v2 = u[2 * N + cc];
-                        df_add2(W[0], v0, 0.f);
-                        df_add2(W[1], v1, 0.f);
-                        df_add2(W[2], v2, 0.f);
-                        df_add_prod(Pm[0], fy.x, fy.y, v2, 0.f);
-                        df_add_prod(Pm[1], fz.x, fz.y, v1, 0.f);
-                        df_add_prod(Pm[2], fz.x, fz.y, v0, 0.f);
-                        df_add_prod(Pm[3], fx.x, fx.y, v2, 0.f);
-                        df_add_prod(Pm[4], fx.x, fx.y, v1, 0.f);
-                        df_add_prod(Pm[5], fy.x, fy.y, v0, 0.f);
-                        continue;
-                    }
-                    const double rx = tb[3 * kVolAx + i], ry = tb[4 * kVolAx + j];
-                    const double u0 = (double)u[cc], u1 = (double)u[N + cc], u2 = (double)u[2 * N + cc];
-                    s0 += u0;
-                    s1 += u1;
-                    s2 += u2;
-                    sA = fma(ry, u2, sA);
-                    sB = fma(rx, u2, sB);
-                    sC = fma(rx, u1, sC);
-                    sD = fma(ry, u0, sD);
+                    const float2 fx = tbf[i], fy = tbf[kVolAx + j];
+                    const float2 v0 = field_pair(u[cc]), v1 = field_pair(u[N + cc]), v2 = field_pair(u[2 * N + cc]);
+                    df_add2(W[0], v0.x, v0.y);
+                    df_add2(W[1], v1.x, v1.y);
+                    df_add2(W[2], v2.x, v2.y);
+                    df_add_prod(Pm[0], fy.x, fy.y, v2.x, v2.y);
+                    df_add_prod(Pm[1], fz.x, fz.y, v1.x, v1.y);
+                    df_add_prod(Pm[2], fz.x, fz.y, v0.x, v0.y);
+                    df_add_prod(Pm[3], fx.x, fx.y, v2.x, v2.y);
+                    df_add_prod(Pm[4], fx.x, fx.y, v1.x, v1.y);
+                    df_add_prod(Pm[5], fy.x, fy.y, v0.x, v0.y);
                 }
                 nint_cells += (nint + (int)blockDim.x - 1 - (int)threadIdx.x) / (int)blockDim.x;
                 // boundary cells: alpha = sum of max(-phi, 0) / sum |phi| over the corners
@@ -614,7 +588,7 @@ __global__ void __launch_bounds__(kVolThreads, 3) k_volume(CaseTab ct, int P, in
                                 a2 = make_float2(0.5f, 0.f);
                             } else if (neg.hi != 0.0f) {
                                 if (den.hi < 1e-30f) {
-                                    a2 = df_split(((double)num.hi + num.lo) / ((double)den.hi + den.lo));
+                                    a2 = df_split_rn(((double)num.hi + num.lo) / ((double)den.hi + den.lo));
                                 } else {
                                     // num / den: a quotient and one remainder correction
                                     const float rd = __frcp_rn(den.hi);
@@ -631,30 +605,16 @@ __global__ void __launch_bounds__(kVolThreads, 3) k_volume(CaseTab ct, int P, in
                             pl.balpha[pb + q] = a2;
                         }
                         const long long cc = plane_off + row_off[j] + wrap_add(lo0w, i, g.n[0]);
-                        if constexpr (sizeof(T) == 8) {
-                            // FP64 fields: the sums in FP64
-                            const double al = (double)a2.x + (double)a2.y;
-                            const double rx = tb[3 * kVolAx + i], ry = tb[4 * kVolAx + j];
-                            const double w0 = al * (double)u[cc], w1 = al * (double)u[N + cc],
-                                         w2 = al * (double)u[2 * N + cc];
-                            s0 += w0;
-                            s1 += w1;
-                            s2 += w2;
-                            sA = fma(ry, w2, sA);
-                            sB = fma(rx, w2, sB);
-                            sC = fma(rx, w1, sC);
-                            sD = fma(ry, w0, sD);
-                            svol += al;
-                            continue;
-                        }
                         df_add2(V, a2.x, a2.y);
                         const float2 fx = tbf[i], fy = tbf[kVolAx + j];
-                        const float v[3] = {(float)u[cc], (float)u[N + cc], (float)u[2 * N + cc]};
+                        const float2 v[3] = {field_pair(u[cc]), field_pair(u[N + cc]), field_pair(u[2 * N + cc])};
                         float wh[3], wl[3];
 #pragma unroll
                         for (int q3 = 0; q3 < 3; ++q3) {
-                            wh[q3] = a2.x * v[q3];
-                            wl[q3] = fmaf(a2.x, v[q3], -wh[q3]) + a2.y * v[q3];
+                            // alpha u with the product's rounding error and the cross terms
+                            wh[q3] = a2.x * v[q3].x;
+                            wl[q3] = fmaf(a2.x, v[q3].x, -wh[q3]) + a2.y * v[q3].x;
+                            if constexpr (sizeof(T) == 8) wl[q3] = fmaf(a2.x, v[q3].y, wl[q3]);
                             df_add2(W[q3], wh[q3], wl[q3]);
                         }
                         df_add_prod(Pm[0], fy.x, fy.y, wh[2], wl[2]);
@@ -663,72 +623,29 @@ __global__ void __launch_bounds__(kVolThreads, 3) k_volume(CaseTab ct, int P, in
                         df_add_prod(Pm[3], fx.x, fx.y, wh[2], wl[2]);
                         df_add_prod(Pm[4], fx.x, fx.y, wh[1], wl[1]);
                         df_add_prod(Pm[5], fy.x, fy.y, wh[0], wl[0]);
-                        continue;
                     }
-                    // exact centre test: beyond R + 0.8661 h every corner is outside
-                    // (alpha = 0), within R - 0.8661 h every corner is inside
-                    // (alpha = 1); only cells in between read their corners,
-                    // all of which lie in the evaluated node shell
-                    const double d2 = tb[6 * kVolAx + i] + tb[7 * kVolAx + j] + rz2;
-                    if (d2 > rout2) continue;
-                    double al = 1.0;
-                    if (!(d2 < rin2)) {
-                        const int qn = j * nx + i;
-                        const double2 c0 = b0[qn], c1 = b0[qn + 1], c2 = b0[qn + nx], c3 = b0[qn + nx + 1];
-                        const double2 c4 = b1[qn], c5 = b1[qn + 1], c6 = b1[qn + nx], c7 = b1[qn + nx + 1];
-                        const double num = ((c0.x + c1.x) + (c2.x + c3.x)) + ((c4.x + c5.x) + (c6.x + c7.x));
-                        const double neg = ((c0.y + c1.y) + (c2.y + c3.y)) + ((c4.y + c5.y) + (c6.y + c7.y));
-                        if (num == 0.0 && neg > 0.0) continue;  // alpha = 0
-                        const double den = num + neg;
-                        al = den == 0.0 ? 0.5 : (neg == 0.0 ? 1.0 : (den > 1e-30 ? num * recip_refined(den) : num / den));
-                    }
-                    const long long cc = plane_off + row_off[j] + wrap_add(lo0w, i, g.n[0]);
-                    const double rx = tb[3 * kVolAx + i], ry = tb[4 * kVolAx + j];
-                    const double w0 = al * (double)u[cc], w1 = al * (double)u[N + cc], w2 = al * (double)u[2 * N + cc];
-                    s0 += w0;
-                    s1 += w1;
-                    s2 += w2;
-                    sA = fma(ry, w2, sA);
-                    sB = fma(rx, w2, sB);
-                    sC = fma(rx, w1, sC);
-                    sD = fma(ry, w0, sD);
-                    svol += al;
-                }
-                if constexpr (sizeof(T) == 8) {
-                    acc[0] += s0;
-                    acc[1] += s1;
-                    acc[2] += s2;
-                    acc[3] = fma(-rz, s1, acc[3]);
-                    acc[4] = fma(rz, s0, acc[4]);
                 }
                 pi += nint;
                 pb += nbnd;
                 if (MODE != 2) __syncthreads();
             }
-            if constexpr (sizeof(T) == 8) {
-                acc[3] += sA;
-                acc[4] -= sB;
-                acc[5] += sC - sD;
-            }
-            acc[6] += svol + (double)nint_cells;
-            if constexpr (sizeof(T) == 4) {
-                // warp sums in double-float, then FP64 in lane 0 only
+            acc[6] += (double)nint_cells;
+            // warp sums in double-float, then FP64 in lane 0 only
 #pragma unroll
-                for (int q = 0; q < 3; ++q) df_warp_sum(W[q]);
+            for (int q = 0; q < 3; ++q) df_warp_sum(W[q]);
 #pragma unroll
-                for (int q = 0; q < 6; ++q) df_warp_sum(Pm[q]);
-                df_warp_sum(V);
-                if ((threadIdx.x & 31) == 0) {
-                    acc[6] += (double)V.hi + (double)V.lo;
-                    double pm[6];
+            for (int q = 0; q < 6; ++q) df_warp_sum(Pm[q]);
+            df_warp_sum(V);
+            if ((threadIdx.x & 31) == 0) {
+                acc[6] += (double)V.hi + (double)V.lo;
+                double pm[6];
 #pragma unroll
-                    for (int q = 0; q < 6; ++q) pm[q] = (double)Pm[q].hi + (double)Pm[q].lo;
+                for (int q = 0; q < 6; ++q) pm[q] = (double)Pm[q].hi + (double)Pm[q].lo;
 #pragma unroll
-                    for (int q = 0; q < 3; ++q) acc[q] = (double)W[q].hi + (double)W[q].lo;
-                    acc[3] = pm[0] - pm[1];
-                    acc[4] = pm[2] - pm[3];
-                    acc[5] = pm[4] - pm[5];
-                }
+                for (int q = 0; q < 3; ++q) acc[q] = (double)W[q].hi + (double)W[q].lo;
+                acc[3] = pm[0] - pm[1];
+                acc[4] = pm[2] - pm[3];
+                acc[5] = pm[4] - pm[5];
             }
         } else {
             // boxes wider than kVolMaxBox: every cell of the slab, corners evaluated directly
