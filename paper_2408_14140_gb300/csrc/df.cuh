@@ -88,6 +88,32 @@ __device__ __forceinline__ float2 df_mul(float2 a, float2 b) {
     return df_fast_two_sum(p, e);
 }
 
+// a + b of two pairs: TwoSum of the high parts, the low parts added to its
+// error, renormalised.
+__device__ __forceinline__ float2 df_add(float2 a, float2 b) {
+    const float s = __fadd_rn(a.x, b.x);
+    const float bb = __fsub_rn(s, a.x);
+    const float e = __fadd_rn(__fsub_rn(a.x, __fsub_rn(s, bb)), __fsub_rn(b.x, bb));
+    return df_fast_two_sum(s, __fadd_rn(e, __fadd_rn(a.y, b.y)));
+}
+
+__device__ __forceinline__ float2 df_neg(float2 a) { return make_float2(-a.x, -a.y); }
+
+// a * k for a power of two k: exact.
+__device__ __forceinline__ float2 df_scale(float2 a, float k) { return make_float2(__fmul_rn(a.x, k), __fmul_rn(a.y, k)); }
+
+// Square root of a pair a > 0 (a.x a normal float): one Newton (Heron) step
+// q = q0 + (a - q0^2) / (2 q0) from the FP32 root q0, the residual from the
+// exact FMA square (a.x - q0^2 is exact: q0^2 is within a factor 2 of a.x).
+// The start's relative error below 2^-24 leaves about 2^-47.
+__device__ __forceinline__ float2 df_sqrt(float2 a) {
+    const float q0 = __fsqrt_rn(a.x);
+    const float p = __fmul_rn(q0, q0);
+    const float pe = __fmaf_rn(q0, q0, -p);
+    const float res = __fadd_rn(__fsub_rn(__fsub_rn(a.x, p), pe), a.y);
+    return df_fast_two_sum(q0, __fmul_rn(res, __fdiv_rn(0.5f, q0)));
+}
+
 // Running sum of pair products, renormalised after every term.
 struct DFAcc {
     float hi, lo;

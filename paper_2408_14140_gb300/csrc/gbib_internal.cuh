@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "df.cuh"
 #include "gbib.h"
 
 namespace gbib {
@@ -102,31 +103,75 @@ template <> struct Kernel<IB_DELTA_PESKIN4> { static constexpr int W = 4; };
 // they are ((3 - 2r - q)/8, (3 - 2r + q)/8, (1 + 2r + q)/8, (1 + 2r - q)/8),
 // q = sqrt(1 + 4r - 4r^2).  These are the piecewise kernels of Roma et al.
 // (1999) and Peskin (2002) evaluated at the W offsets of the stencil.
-template <int KER, typename T>
-__device__ __forceinline__ long long axis_weights(double s, T w[4]) {
+// s, the stencil cell and r are FP64 (r = s - b is exact); the weights are
+// FP32 for FP32 fields.
+template <int KER>
+__device__ __forceinline__ long long axis_weights(double s, float w[4]) {
     if (KER == IB_DELTA_ROMA3) {
         double b = floor(s + 0.5);
-        T r = (T)(s - b);
-        T q = sqrt(T(1) - T(3) * r * r);
-        w[0] = (T(2) - T(3) * r - q) * T(1.0 / 6.0);
-        w[1] = (T(1) + q) * T(1.0 / 3.0);
-        w[2] = (T(2) + T(3) * r - q) * T(1.0 / 6.0);
-        w[3] = T(0);
+        float r = (float)(s - b);
+        float q = sqrtf(1.0f - 3.0f * r * r);
+        w[0] = (2.0f - 3.0f * r - q) * (float)(1.0 / 6.0);
+        w[1] = (1.0f + q) * (float)(1.0 / 3.0);
+        w[2] = (2.0f + 3.0f * r - q) * (float)(1.0 / 6.0);
+        w[3] = 0.0f;
         return (long long)b - 1;
     } else {
         double b = floor(s);
-        T r = (T)(s - b);
-        T q = sqrt(T(1) + T(4) * r - T(4) * r * r);
-        w[0] = (T(3) - T(2) * r - q) * T(0.125);
-        w[1] = (T(3) - T(2) * r + q) * T(0.125);
-        w[2] = (T(1) + T(2) * r + q) * T(0.125);
-        w[3] = (T(1) + T(2) * r - q) * T(0.125);
+        float r = (float)(s - b);
+        float q = sqrtf(1.0f + 4.0f * r - 4.0f * r * r);
+        w[0] = (3.0f - 2.0f * r - q) * 0.125f;
+        w[1] = (3.0f - 2.0f * r + q) * 0.125f;
+        w[2] = (1.0f + 2.0f * r + q) * 0.125f;
+        w[3] = (1.0f + 2.0f * r - q) * 0.125f;
         return (long long)b - 1;
     }
 }
 
+// The same weights for FP64 fields as double-float pairs (hi, lo), the form
+// the pass kernels read (df.cuh), evaluated on the FP32 pipes: r split on the
+// integer pipe, the products from the FMA remainder, the sums by TwoSum, the
+// root by one Newton (Heron) step from the FP32 root, and the divisions by 3
+// and 6 as products with the pairs of 1/3 and 1/6 (the divisions by 8 and
+// the factors 2 and 4 are exact).  Each weight is within a few 2^-47 of the
+// FP64 formula, which keeps only the first stencil cell's FP64 arithmetic.
+template <int KER>
+__device__ __forceinline__ long long axis_weights(double s, float2 w[4]) {
+    if (KER == IB_DELTA_ROMA3) {
+        const double b = floor(s + 0.5);
+        const float2 r = df_split(s - b);
+        const float2 r3 = df_mul(r, make_float2(3.0f, 0.0f));
+        const float2 q = df_sqrt(df_add(make_float2(1.0f, 0.0f), df_neg(df_mul(r3, r))));
+        constexpr float k6 = (float)(1.0 / 6.0), k3 = (float)(1.0 / 3.0);
+        const float2 c6 = make_float2(k6, (float)(1.0 / 6.0 - (double)k6));
+        const float2 c3 = make_float2(k3, (float)(1.0 / 3.0 - (double)k3));
+        w[0] = df_mul(df_add(df_add(make_float2(2.0f, 0.0f), df_neg(r3)), df_neg(q)), c6);
+        w[1] = df_mul(df_add(make_float2(1.0f, 0.0f), q), c3);
+        w[2] = df_mul(df_add(df_add(make_float2(2.0f, 0.0f), r3), df_neg(q)), c6);
+        w[3] = make_float2(0.0f, 0.0f);
+        return (long long)b - 1;
+    } else {
+        const double b = floor(s);
+        const float2 r = df_split(s - b);
+        const float2 r2 = df_scale(r, 2.0f);
+        // 1 + 4r - 4r^2 = 1 + 2 (2r) - (2r)^2
+        const float2 q = df_sqrt(df_add(df_add(make_float2(1.0f, 0.0f), df_scale(r2, 2.0f)), df_neg(df_mul(r2, r2))));
+        const float2 a = df_add(make_float2(3.0f, 0.0f), df_neg(r2)), c = df_add(make_float2(1.0f, 0.0f), r2);
+        w[0] = df_scale(df_add(a, df_neg(q)), 0.125f);
+        w[1] = df_scale(df_add(a, q), 0.125f);
+        w[2] = df_scale(df_add(c, q), 0.125f);
+        w[3] = df_scale(df_add(c, df_neg(q)), 0.125f);
+        return (long long)b - 1;
+    }
+}
+
+// x is finite: its exponent field is not all ones (an integer test, no FP64
+// operation)
+__device__ __forceinline__ bool finite_bits(double x) {
+    return ((unsigned)((unsigned long long)__double_as_longlong(x) >> 52) & 0x7ffu) != 0x7ffu;
+}
 __device__ __forceinline__ bool finite3(const double *v) {
-    return isfinite(v[0]) && isfinite(v[1]) && isfinite(v[2]);
+    return finite_bits(v[0]) && finite_bits(v[1]) && finite_bits(v[2]);
 }
 
 }  // namespace gbib

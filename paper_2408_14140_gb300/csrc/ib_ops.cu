@@ -27,14 +27,16 @@
 
 namespace gbib {
 
+// A marker's wrapped anchor and its per-axis weights in the pass storage
+// form (FP32, or double-float pairs for FP64 fields).
 template <typename T, int KER>
 __device__ __forceinline__ uint64_t marker_weights(const DevGrid &g, const double X[3],
-                                                   T w[12], long long first[3]) {
+                                                   PS<T> w[12], long long first[3]) {
     int a[3];
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
         double s = (X[d] - g.org[d]) * g.inv_h - 0.5;
-        first[d] = axis_weights<KER, T>(s, w + 4 * d);
+        first[d] = axis_weights<KER>(s, w + 4 * d);
         a[d] = wrap_int(first[d], g.n[d]);
     }
     return pack_anchor(a[0], a[1], a[2]);
@@ -56,12 +58,9 @@ __global__ void __launch_bounds__(256) k_interpolate(DevGrid g, const T *__restr
             U[3 * l] = U[3 * l + 1] = U[3 * l + 2] = 0.0;
             continue;
         }
-        T w[12];
-        long long first[3];
-        uint64_t anc = marker_weights<T, KER>(g, x, w, first);
         PS<T> ws[12];
-#pragma unroll
-        for (int k = 0; k < 12; ++k) ws[k] = to_store(w[k]);
+        long long first[3];
+        uint64_t anc = marker_weights<T, KER>(g, x, ws, first);
         T o[3];
         interp_marker<T, KW>(u, g, N, anc, ws, o);
         U[3 * l] = (double)o[0];
@@ -91,11 +90,11 @@ __global__ void k_prep_spread(DevGrid g, int M, const double *__restrict__ X,
             f[0] = f[1] = f[2] = 0.0;
             dv = 0.0;
         }
-        T w[12];
+        PS<T> w[12];
         long long first[3];
         ms.anchor[l] = marker_weights<T, KER>(g, x, w, first);
 #pragma unroll
-        for (int k = 0; k < 12; ++k) ms.wts[12 * l + k] = to_store(w[k]);
+        for (int k = 0; k < 12; ++k) ms.wts[12 * l + k] = w[k];
         double q = dv * g.inv_h3;
         ms.A[4 * l + 0] = to_store((T)(f[0] * q));
         ms.A[4 * l + 1] = to_store((T)(f[1] * q));
@@ -150,17 +149,17 @@ __global__ void __launch_bounds__(256) k_prep_particles(
     for (int l = l0 + threadIdx.x; l < l1; l += blockDim.x) {
         double r[3] = {R[3 * l], R[3 * l + 1], R[3 * l + 2]};
         double dv = dV[l];
-        if (!pok || !finite3(r) || !isfinite(dv)) {
+        if (!pok || !finite3(r) || !finite_bits(dv)) {
             raise_status(st, IB_ERR_NONFINITE, l);
             r[0] = r[1] = r[2] = 0.0;
         }
         double x[3] = {xc[0] + r[0], xc[1] + r[1], xc[2] + r[2]};
         if (!pok) x[0] = g.org[0], x[1] = g.org[1], x[2] = g.org[2];
-        T w[12];
+        PS<T> w[12];
         long long first[3];
         ms.anchor[l] = marker_weights<T, KER>(g, x, w, first);
 #pragma unroll
-        for (int k = 0; k < 12; ++k) ms.wts[12 * l + k] = to_store(w[k]);
+        for (int k = 0; k < 12; ++k) ms.wts[12 * l + k] = w[k];
         const double ud[3] = {uc[0] + (wc[1] * r[2] - wc[2] * r[1]), uc[1] + (wc[2] * r[0] - wc[0] * r[2]),
                               uc[2] + (wc[0] * r[1] - wc[1] * r[0])};
 #pragma unroll
@@ -1244,12 +1243,9 @@ __global__ void __launch_bounds__(256) k_spread_atomic(DevGrid g, int M, const d
             }
         }
         if (!valid) x[0] = g.org[0], x[1] = g.org[1], x[2] = g.org[2];
-        T w[12];
-        long long first[3];
-        const uint64_t anc = marker_weights<T, KER>(g, x, w, first);
         PS<T> ws[12], A[3];
-#pragma unroll
-        for (int k = 0; k < 12; ++k) ws[k] = to_store(w[k]);
+        long long first[3];
+        const uint64_t anc = marker_weights<T, KER>(g, x, ws, first);
         const double q = dv * g.inv_h3;
 #pragma unroll
         for (int c = 0; c < 3; ++c) A[c] = to_store((T)(fv[c] * q));
