@@ -540,9 +540,10 @@ __device__ __forceinline__ void for_marker_slots(const CaseTab &ct, const SlotGe
         int p = sg.part_of[l];
         int4 blo = sg.box_lo[p];
         // relative first cell: (anchor - box_lo) mod n, < box dims
-        long long rx = wrap_diff(anchor_x(anc), wrap_int(blo.x, g.n[0]), g.n[0]);
-        long long ry = wrap_diff(anchor_y(anc), wrap_int(blo.y, g.n[1]), g.n[1]);
-        long long rz = wrap_diff(anchor_z(anc), wrap_int(blo.z, g.n[2]), g.n[2]);
+        // box_lo is wrapped by the preparation kernel: [0, n)
+        long long rx = wrap_diff(anchor_x(anc), blo.x, g.n[0]);
+        long long ry = wrap_diff(anchor_y(anc), blo.y, g.n[1]);
+        long long rz = wrap_diff(anchor_z(anc), blo.z, g.n[2]);
         nx = axis_tiles_local<KW>(rx, tx, cx);
         ny = axis_tiles_local<KW>(ry, ty, cy);
         nz = axis_tiles_local<KW>(rz, tz, cz);
@@ -863,12 +864,19 @@ __device__ __forceinline__ int slot_geometry(const CaseTab &ct, int mode, const 
     }
 }
 
+// v mod n for v in [-n, 2n)
+__device__ __forceinline__ int wrap_once(int v, int n) {
+    v += v < 0 ? n : 0;
+    return v >= n ? v - n : v;
+}
+
 __device__ __forceinline__ unsigned long long slot_key(const DevGrid &g, const uint64_t *anchor, uint32_t m,
                                                        const int lo[3]) {
     const uint64_t anc = anchor[m];
-    const int rz = wrap_int((long long)anchor_z(anc) - lo[2] + 3, g.n[2]);
-    const int ry = wrap_int((long long)anchor_y(anc) - lo[1] + 3, g.n[1]);
-    const int v = wrap_int((long long)anchor_x(anc) - lo[0] + 3, g.n[0]);
+    // anchor and lo lie in [0, n): one conditional add or subtract wraps
+    const int rz = wrap_once(anchor_z(anc) - lo[2] + 3, g.n[2]);
+    const int ry = wrap_once(anchor_y(anc) - lo[1] + 3, g.n[1]);
+    const int v = wrap_once(anchor_x(anc) - lo[0] + 3, g.n[0]);
     const int bin = (rz < kRow && ry < kRow && v < kRow) ? (rz * kRow + ry) * kBinsPerRow + v
                                                          : kBins - 1;  // never read
     return ((unsigned long long)bin << 32) | m;
@@ -1059,6 +1067,7 @@ __global__ void __launch_bounds__(kBlock) k_slot_sort(
 // ---------------------------------------------------------------------------
 constexpr int kPairThreads = 256;
 constexpr int kPairWarps = kPairThreads / 32;
+static_assert(kTileCells == 2 * kPairThreads, "each thread of k_tile_pairs owns two cells");
 
 template <typename T, int KW>
 __global__ void __launch_bounds__(kPairThreads, 5) k_tile_pairs(CaseTab ct, int ncompact_cap,
@@ -1072,7 +1081,7 @@ __global__ void __launch_bounds__(kPairThreads, 5) k_tile_pairs(CaseTab ct, int 
     // 8-11 z) and its first stencil cell relative to the tile, x + 8 y + 64 z
     // + 256, from bit 12
     __shared__ unsigned int s_anc[kMaxCand];
-    __shared__ unsigned int s_cnt[kPairWarps][kTileCells];  // counts, then list cursors
+    __shared__ __align__(16) unsigned int s_cnt[kPairWarps][kTileCells];  // counts, then list cursors
     __shared__ int s_wp[kPairWarps], s_wb[kPairWarps];
     const int ncompact = min(*ncompact_p, ncompact_cap);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -1114,7 +1123,8 @@ __global__ void __launch_bounds__(kPairThreads, 5) k_tile_pairs(CaseTab ct, int 
             }
             s_anc[i] = code | (unsigned)(d[0] + kTile * d[1] + kTile * kTile * d[2] + 256) << 12;
         }
-        for (int c = tid; c < kPairWarps * kTileCells; c += blockDim.x) (&s_cnt[0][0])[c] = 0;
+        for (int c = tid; c < kPairWarps * kTileCells / 4; c += blockDim.x)
+            ((uint4 *)&s_cnt[0][0])[c] = make_uint4(0u, 0u, 0u, 0u);
         __syncthreads();
         // Each warp walks a contiguous range of candidates, one candidate per
         // step, lane l taking the stencil offsets k = l + 32 q: the cells of
@@ -1137,16 +1147,14 @@ __global__ void __launch_bounds__(kPairThreads, 5) k_tile_pairs(CaseTab ct, int 
         }
         __syncthreads();
         // (cell, warp) scan: thread t owns cells 2t and 2t + 1
-        int tot[2], pre[2][kPairWarps];
+        int tot[2] = {0, 0}, pre[2][kPairWarps];
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            int acc = 0;
-#pragma unroll
-            for (int w = 0; w < kPairWarps; ++w) {
-                pre[h][w] = acc;
-                acc += (int)s_cnt[w][2 * tid + h];
-            }
-            tot[h] = acc;
+        for (int w = 0; w < kPairWarps; ++w) {
+            const uint2 cw = ((const uint2 *)s_cnt[w])[tid];
+            pre[0][w] = tot[0];
+            pre[1][w] = tot[1];
+            tot[0] += (int)cw.x;
+            tot[1] += (int)cw.y;
         }
         int pv = tot[0] + tot[1], bv = (tot[0] > 0) + (tot[1] > 0);
         for (int o = 1; o < 32; o <<= 1) {
@@ -1167,9 +1175,8 @@ __global__ void __launch_bounds__(kPairThreads, 5) k_tile_pairs(CaseTab ct, int 
             sl.tinfo[cs] = make_int4((int)sl.poff[b], (int)(sl.poff[b + nc] - sl.poff[b]), nbd, nc);
         }
 #pragma unroll
-        for (int h = 0; h < 2; ++h)
-#pragma unroll
-            for (int w = 0; w < kPairWarps; ++w) s_cnt[w][2 * tid + h] = (unsigned)(cbase[h] + pre[h][w]);
+        for (int w = 0; w < kPairWarps; ++w)
+            ((uint2 *)s_cnt[w])[tid] = make_uint2((unsigned)(cbase[0] + pre[0][w]), (unsigned)(cbase[1] + pre[1][w]));
         __syncthreads();
         // placement in candidate order: a cell's list ascends in candidate
         // index (one step's cells are distinct; the warp barrier orders steps)
@@ -1184,13 +1191,36 @@ __global__ void __launch_bounds__(kPairThreads, 5) k_tile_pairs(CaseTab ct, int 
         }
         __syncthreads();
         // every pair's weight product, one pair per thread (the pair words
-        // written above are visible to the whole CTA after the barrier)
+        // written above are visible to the whole CTA after the barrier), kPwU
+        // pairs per thread at a time: the pair words, then the candidates'
+        // marker indices, then their axis weights are each loaded together,
+        // three dependent rounds of loads instead of three per pair
         if (pw) {
             const int np = (int)(sl.poff[b + nc] - sl.poff[b]);
-            for (int k = tid; k < np; k += blockDim.x) {
-                const unsigned pk = pairs[k];
-                const PS<T> *w = wts + 12 * (size_t)sl.cand[b + (pk & 0xffff)];
-                pw[k] = pair_weight(w, (pk >> 16) & 3, (pk >> 18) & 3, (pk >> 20) & 3);
+            constexpr int kPwU = 4;
+            for (int k0 = tid; k0 < np; k0 += kPwU * kPairThreads) {
+                unsigned pk[kPwU];
+                uint32_t mk[kPwU];
+#pragma unroll
+                for (int u = 0; u < kPwU; ++u) {
+                    const int k = k0 + u * kPairThreads;
+                    pk[u] = k < np ? pairs[k] : 0u;
+                }
+#pragma unroll
+                for (int u = 0; u < kPwU; ++u) mk[u] = k0 + u * kPairThreads < np ? sl.cand[b + (pk[u] & 0xffff)] : 0u;
+                PS<T> wx[kPwU], wy[kPwU], wz[kPwU];
+#pragma unroll
+                for (int u = 0; u < kPwU; ++u) {
+                    const PS<T> *w = wts + 12 * (size_t)mk[u];
+                    wx[u] = w[(pk[u] >> 16) & 3];
+                    wy[u] = w[4 + ((pk[u] >> 18) & 3)];
+                    wz[u] = w[8 + ((pk[u] >> 20) & 3)];
+                }
+#pragma unroll
+                for (int u = 0; u < kPwU; ++u) {
+                    const int k = k0 + u * kPairThreads;
+                    if (k < np) pw[k] = pair_weight3(wx[u], wy[u], wz[u]);
+                }
             }
         }
     }
