@@ -315,13 +315,13 @@ class Runner:
 
 def launches_per_step(Ns, levels):
     """Library kernels per step on this workload: volume 1 x 2 calls;
-    multidirect forcing: prep, conflicts, levels, marker order, tile count,
-    slot scan (counts, flags and compaction in one single-pass scan), fill,
-    pair-count scan, sort, per-cell lists, level ranges, tile order (12), one
-    interpolation and one gather kernel per wavefront and pass, the
-    persistent remainder kernel (1); force/torque 1; collision + Newton-Euler
-    2."""
-    return 2 + 12 + 2 * Ns * levels + 1 + 1 + 2
+    multidirect forcing: prep, marker radii, conflicts, levels, marker order,
+    tile count, slot scan (counts, flags and compaction in one single-pass
+    scan), fill, pair-count scan, sort, per-cell lists, level ranges, tile
+    order (13), one interpolation and one gather kernel per wavefront and
+    pass, the persistent remainder kernel (1); force/torque 1; collision +
+    Newton-Euler 2."""
+    return 2 + 13 + 2 * Ns * levels + 1 + 1 + 2
 
 
 def capture(runner):

@@ -377,7 +377,9 @@ int ib_ctx_create(ib_ctx **ctx, size_t workspace_bytes) {
     *c->h_nlev = 0;
     if (cudaStreamCreateWithFlags(&c->fork_stream, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->fork_ev[0], cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&c->fork_ev[1], cudaEventDisableTiming) != cudaSuccess) {
+        cudaEventCreateWithFlags(&c->fork_ev[1], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->fork_ev[2], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->fork_ev[3], cudaEventDisableTiming) != cudaSuccess) {
         cudaGetLastError();
         cudaFreeHost(c->h_nlev);
         cudaFree(c->status);
@@ -503,8 +505,7 @@ int ib_ctx_destroy(ib_ctx *c) {
     for (auto e : c->pool) cudaEventDestroy(e);
     cudaFreeHost(c->h_nlev);
     cudaStreamDestroy(c->fork_stream);
-    cudaEventDestroy(c->fork_ev[0]);
-    cudaEventDestroy(c->fork_ev[1]);
+    for (auto e : c->fork_ev) cudaEventDestroy(e);
     for (int k = 0; k < ib_ctx::kStageSlots; ++k) {
         if (c->stage_ptr[k]) cudaFreeHost(c->stage_ptr[k]);
         if (c->stage_ev[k]) cudaEventDestroy(c->stage_ev[k]);

@@ -203,7 +203,7 @@ struct ib_ctx {
     // a second stream and two events: the first interpolation of a forcing
     // call runs on it beside the slot-list kernels (fork and join)
     cudaStream_t fork_stream;
-    cudaEvent_t fork_ev[2];
+    cudaEvent_t fork_ev[4];  // call start, first interpolation, preparation, levels
     // pinned staging ring for the case tables of batch calls: a slot is
     // reused only after the copy that last read it has run (its event)
     static constexpr int kStageSlots = 4;
@@ -286,9 +286,11 @@ __device__ __forceinline__ void grid_dep_launch() { asm volatile("griddepcontrol
 
 // Host side: launch with programmatic stream serialization.  The kernel must
 // call grid_dep_wait() before it touches memory its predecessor may write.
+// With pdl false it is an ordinary launch (after a wait on another stream's
+// event, where the kernel's predecessor is not only the one in its stream).
 template <typename... KArgs, typename... Args>
-inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
-                              Args &&...args) {
+inline cudaError_t launch_dep(bool pdl, void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                              cudaStream_t s, Args &&...args) {
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     at[0].val.programmaticStreamSerializationAllowed = 1;
@@ -298,8 +300,13 @@ inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, siz
     cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
     cfg.attrs = at;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = pdl ? 1 : 0;
     return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
+}
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              Args &&...args) {
+    return launch_dep(true, kern, grid, block, smem, s, std::forward<Args>(args)...);
 }
 
 struct PhaseTimer {

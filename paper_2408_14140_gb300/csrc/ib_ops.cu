@@ -103,15 +103,42 @@ __global__ void k_prep_spread(DevGrid g, int M, const double *__restrict__ X,
     }
 }
 
-// Per particle (one CTA): marker positions, desired velocities, anchors,
-// weights; the particle's marker radius and its unwrapped stencil box.
-// Scratch of the cross-CTA reductions of k_prep_particles: per particle the
-// stencil box bounds (lo starts at a huge value, hi at a very negative one:
-// memset 0x7f / 0x80 bytes), the squared marker radius (0) and a completion
-// count (0).
+// The marker radius of each particle, rho_p = max_l |R_l| (one CTA per
+// particle; a marker with a non-finite input, or any marker of a particle
+// with a non-finite state, counts as R_l = 0, as in the marker preparation,
+// which reports it).  It reads only the call's inputs, so the conflict lists
+// and the wavefront levels, which need rho, run on the context's second
+// stream beside the marker preparation.
+__global__ void __launch_bounds__(256) k_marker_radius(int P, const double *__restrict__ Xr,
+                                                       const double *__restrict__ Ur,
+                                                       const double *__restrict__ Wr,
+                                                       const int *__restrict__ moff, const double *__restrict__ R,
+                                                       const double *__restrict__ dV, double *__restrict__ rho) {
+    __shared__ double s_max[8];
+    const int p = blockIdx.x;
+    if (p >= P) return;
+    const bool pok = finite3(Xr + 3 * p) && finite3(Ur + 3 * p) && finite3(Wr + 3 * p);
+    double rmax = 0.0;  // squared; the root is taken once below
+    for (int l = moff[p] + threadIdx.x; l < moff[p + 1]; l += blockDim.x) {
+        const double r[3] = {R[3 * l], R[3 * l + 1], R[3 * l + 2]};
+        if (pok && finite3(r) && finite_bits(dV[l])) rmax = fmax(rmax, r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+    }
+    for (int o = 16; o > 0; o >>= 1) rmax = fmax(rmax, __shfl_down_sync(0xffffffffu, rmax, o));
+    if ((threadIdx.x & 31) == 0) s_max[threadIdx.x >> 5] = rmax;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) rmax = fmax(rmax, s_max[w]);
+        rho[p] = sqrt(rmax);
+    }
+}
+
+// Per particle (kPrepSplit CTAs): marker positions, desired velocities,
+// anchors, weights, and the particle's unwrapped stencil box.  Scratch of the
+// cross-CTA reductions: per particle the stencil box bounds (lo starts at a
+// huge value, hi at a very negative one: memset 0x7f / 0x80 bytes) and a
+// completion count (0).
 struct PrepScratch {
     long long *lo, *hi;          // [P][3]
-    unsigned long long *rho2;    // [P] bit pattern of a non-negative double
     unsigned int *done;          // [P]
 };
 constexpr int kPrepSplit = 4;    // CTAs per particle
@@ -121,11 +148,10 @@ __global__ void __launch_bounds__(256) k_prep_particles(
     CaseTab ct, int P, const double *__restrict__ Xr, const double *__restrict__ Ur,
     const double *__restrict__ Wr, const int *__restrict__ moff, const double *__restrict__ R,
     const double *__restrict__ dV, MarkerState<T> ms, double *__restrict__ F,
-    double *__restrict__ rho, int4 *__restrict__ box_lo, int4 *__restrict__ box_dim,
+    int4 *__restrict__ box_lo, int4 *__restrict__ box_dim,
     int *__restrict__ part_of, PrepScratch ps, DevStatus *st) {
     constexpr int KW = Kernel<KER>::W;
     __shared__ long long s_lo[3], s_hi[3];
-    __shared__ double s_rho;
     __shared__ int s_last;
     const int p = blockIdx.x / kPrepSplit, part = blockIdx.x % kPrepSplit;
     if (p >= P) return;
@@ -134,7 +160,6 @@ __global__ void __launch_bounds__(256) k_prep_particles(
         s_lo[threadIdx.x] = LLONG_MAX;
         s_hi[threadIdx.x] = LLONG_MIN;
     }
-    if (threadIdx.x == 0) s_rho = 0.0;
     __syncthreads();
     double xc[3] = {Xr[3 * p], Xr[3 * p + 1], Xr[3 * p + 2]};
     double uc[3] = {Ur[3 * p], Ur[3 * p + 1], Ur[3 * p + 2]};
@@ -145,7 +170,6 @@ __global__ void __launch_bounds__(256) k_prep_particles(
     const int nm = m1 - m0;
     const int l0 = m0 + (int)((long long)part * nm / kPrepSplit), l1 = m0 + (int)((long long)(part + 1) * nm / kPrepSplit);
     long long lo[3] = {LLONG_MAX, LLONG_MAX, LLONG_MAX}, hi[3] = {LLONG_MIN, LLONG_MIN, LLONG_MIN};
-    double rmax = 0.0;
     for (int l = l0 + threadIdx.x; l < l1; l += blockDim.x) {
         double r[3] = {R[3 * l], R[3 * l + 1], R[3 * l + 2]};
         double dv = dV[l];
@@ -180,15 +204,12 @@ __global__ void __launch_bounds__(256) k_prep_particles(
             lo[d] = min(lo[d], first[d]);
             hi[d] = max(hi[d], first[d] + KW - 1);
         }
-        rmax = fmax(rmax, r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);  // squared; root taken once below
     }
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
         atomicMin(&s_lo[d], lo[d]);
         atomicMax(&s_hi[d], hi[d]);
     }
-    // rmax >= 0: the bit pattern orders like the value
-    atomicMax((unsigned long long *)&s_rho, (unsigned long long)__double_as_longlong(rmax));
     __syncthreads();
     // combine the particle's CTAs; the last one to finish writes the results
     if (threadIdx.x == 0) {
@@ -196,7 +217,6 @@ __global__ void __launch_bounds__(256) k_prep_particles(
             atomicMin(&ps.lo[3 * p + d], s_lo[d]);
             atomicMax(&ps.hi[3 * p + d], s_hi[d]);
         }
-        atomicMax(&ps.rho2[p], (unsigned long long)__double_as_longlong(s_rho));
         __threadfence();
         s_last = atomicAdd(&ps.done[p], 1u) == kPrepSplit - 1;
         __threadfence();
@@ -208,7 +228,6 @@ __global__ void __launch_bounds__(256) k_prep_particles(
             blo[d] = atomicAdd((unsigned long long *)&ps.lo[3 * p + d], 0ull);
             bhi[d] = atomicAdd((unsigned long long *)&ps.hi[3 * p + d], 0ull);
         }
-        rho[p] = sqrt(__longlong_as_double((long long)atomicAdd(&ps.rho2[p], 0ull)));
         if (m1 > m0) {
             int dims[3];
             for (int d = 0; d < 3; ++d) dims[d] = (int)(bhi[d] - blo[d] + 1);
@@ -333,8 +352,11 @@ __device__ __forceinline__ int block_scan_chunked(int n, F f, O out) {
 }
 
 constexpr int kLevSweeps = 64;  // parallel relaxation sweeps before the ordered sweep
+// threads of the one k_levels CTA: 512 (24k registers) fit on an SM beside a
+// marker-preparation CTA, so the levels need not wait for that kernel's tail
+constexpr int kLevThreads = 512;
 
-__global__ void __launch_bounds__(1024) k_levels(CaseTab ct, int P, int order, int KW,
+__global__ void __launch_bounds__(kLevThreads) k_levels(CaseTab ct, int P, int order, int KW,
                                                  const double *__restrict__ Xr,
                                                  const double *__restrict__ rho,
                                                  const int *__restrict__ moff,
@@ -1958,9 +1980,9 @@ static int slots_alloc(Arena &ar, int M, int ndense, int mode, Slots &sl, SlotSc
 template <typename T, int KW>
 static int slots_build(ib_ctx *ctx, const CaseTab &ct, int M, int ndense, SlotGeom sg, const uint64_t *anchor,
                        const PS<T> *wts, const int *level, Slots &sl, const SlotScratch &sc, int *&ncompact_dev,
-                       cudaStream_t s, bool with_pairs) {
+                       cudaStream_t s, bool with_pairs, bool pdl_first = true) {
     const int nb = grid_blocks(M, 256, ctx->sm_count);
-    launch_pdl(k_slot_count<KW>, dim3(nb), dim3(256), 0, s, ct, M, sg, anchor, sl.count);
+    launch_dep(pdl_first, k_slot_count<KW>, dim3(nb), dim3(256), 0, s, ct, M, sg, anchor, sl.count);
     launch_pdl(k_slot_scan, dim3(sc.lb_tiles[0]), dim3(kLbThreads), 0, s, (const uint32_t *)sl.count, ndense,
                sl.start, sl.flag_scan, sl.dense_of, sc.lb_stat, sc.lb_ticket, ctx->status);
     launch_pdl(k_slot_fill<KW>, dim3(nb), dim3(256), 0, s, ct, M, sg, anchor, (const uint32_t *)sl.start,
@@ -2049,7 +2071,6 @@ static int run_mdf(ib_ctx *ctx, Arena &ar, const CaseTab &ct, const ib_particles
     PrepScratch prep_ps;
     prep_ps.lo = ar.take<long long>((size_t)3 * P);
     prep_ps.hi = ar.take<long long>((size_t)3 * P);
-    prep_ps.rho2 = ar.take<unsigned long long>(P);
     prep_ps.done = ar.take<unsigned int>(P);
     LevelOut lo;
     lo.level = ar.take<int>(P);
@@ -2146,30 +2167,41 @@ static int run_mdf(ib_ctx *ctx, Arena &ar, const CaseTab &ct, const ib_particles
         ci.stream = s;
     };
     PhaseTimer tprep(ctx, IB_PHASE_MDF_PREP, s);
+    // the marker radii, conflict lists, levels and level-major marker order
+    // on the second stream, beside the marker preparation (after everything
+    // already enqueued on the call's stream, whose earlier work may still use
+    // this workspace)
+    cudaStream_t fs = ctx->fork_stream;
+    cudaEventRecord(ctx->fork_ev[0], s);
+    cudaStreamWaitEvent(fs, ctx->fork_ev[0], 0);
+    k_marker_radius<<<P, 256, 0, fs>>>(P, pp->Xr, pp->Ur, pp->Wr, pp->marker_offset, mk->R, mk->dV, rho);
+    if (order == IB_ORDER_SEQUENTIAL)
+        launch_pdl(k_conflicts, dim3(grid_blocks(32 * P, 256, ctx->sm_count)), dim3(256), 0, fs, ct, P, KW,
+                   (const double *)pp->Xr, (const double *)rho, nbr_cnt, nbr);
+    cudaFuncSetAttribute(k_levels, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLevSmem);
+    launch_pdl(k_levels, dim3(1), dim3(kLevThreads), kLevSmem, fs, ct, P, order, KW, (const double *)pp->Xr,
+               (const double *)rho, (const int *)pp->marker_offset, (const int *)nbr_cnt, (const int *)nbr, lo,
+               lev_work, lev_cur);
+    launch_pdl(k_marker_order, dim3(P < ctx->sm_count * 4 ? P : ctx->sm_count * 4), dim3(256), 0, fs, P,
+               (const int *)pp->marker_offset, (const int *)lo.mbase, mperm);
+    cudaEventRecord(ctx->fork_ev[3], fs);
     cudaMemsetAsync(bar.count, 0, 2 * sizeof(unsigned int), s);
     cudaMemsetAsync(prep_ps.lo, 0x7f, sizeof(long long) * 3 * P, s);
     cudaMemsetAsync(prep_ps.hi, 0x80, sizeof(long long) * 3 * P, s);
-    cudaMemsetAsync(prep_ps.rho2, 0, sizeof(unsigned long long) * P, s);
     cudaMemsetAsync(prep_ps.done, 0, sizeof(unsigned int) * P, s);
     k_prep_particles<T, KER><<<P * kPrepSplit, 256, 0, s>>>(ct, P, pp->Xr, pp->Ur, pp->Wr, pp->marker_offset, mk->R,
-                                                 mk->dV, ms, F_out, rho, box_lo, box_dim, part_of, prep_ps,
+                                                 mk->dV, ms, F_out, box_lo, box_dim, part_of, prep_ps,
                                                  ctx->status);
-    if (order == IB_ORDER_SEQUENTIAL)
-        launch_pdl(k_conflicts, dim3(grid_blocks(32 * P, 256, ctx->sm_count)), dim3(256), 0, s, ct, P, KW,
-                   (const double *)pp->Xr, (const double *)rho, nbr_cnt, nbr);
-    cudaFuncSetAttribute(k_levels, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLevSmem);
-    launch_pdl(k_levels, dim3(1), dim3(1024), kLevSmem, s, ct, P, order, KW, (const double *)pp->Xr,
-               (const double *)rho, (const int *)pp->marker_offset, (const int *)nbr_cnt, (const int *)nbr, lo,
-               lev_work, lev_cur);
-    launch_pdl(k_marker_order, dim3(P < ctx->sm_count * 4 ? P : ctx->sm_count * 4), dim3(256), 0, s, P,
-               (const int *)pp->marker_offset, (const int *)lo.mbase, mperm);
+    // the first interpolation (second stream) needs the prepared markers and
+    // the marker order; the slot lists (this stream) need the levels' ranks
+    cudaEventRecord(ctx->fork_ev[2], s);
     if (fork) {
-        cudaEventRecord(ctx->fork_ev[0], s);
-        cudaStreamWaitEvent(ctx->fork_stream, ctx->fork_ev[0], 0);
-        if (ctx->field_wait) cudaStreamWaitEvent(ctx->fork_stream, (cudaEvent_t)ctx->field_wait, 0);
-        launch_interp(0, ctx->fork_stream, false);
-        cudaEventRecord(ctx->fork_ev[1], ctx->fork_stream);
+        cudaStreamWaitEvent(fs, ctx->fork_ev[2], 0);
+        if (ctx->field_wait) cudaStreamWaitEvent(fs, (cudaEvent_t)ctx->field_wait, 0);
+        launch_interp(0, fs, false);
+        cudaEventRecord(ctx->fork_ev[1], fs);
     }
+    cudaStreamWaitEvent(s, ctx->fork_ev[3], 0);
     sg.part_of = part_of;
     sg.rank = lo.rank;
     sg.box_lo = box_lo;
@@ -2177,7 +2209,7 @@ static int run_mdf(ib_ctx *ctx, Arena &ar, const CaseTab &ct, const ib_particles
     int *ncompact = nullptr;
     if (!atomic) {
         rc = slots_build<T, KW>(ctx, ct, M, (int)ndense, sg, ms.anchor, (const PS<T> *)ms.wts, lo.level, sl, sc,
-                                ncompact, s, true);
+                                ncompact, s, true, false);
         if (rc) return rc;
         a.sl = sl;
     }

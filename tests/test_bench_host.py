@@ -57,7 +57,7 @@ def test_workload_bookkeeping():
     assert len(lb) == bench.wavefront_levels(case)
     assert sum(m for _, m in lb) == case.M
     assert sum(b for b, _ in lb) >= bench.band_cells(case)
-    assert bench.launches_per_step(5, 5) == 68
+    assert bench.launches_per_step(5, 5) == 69
 
 
 def _fake_smi(tmp_path, reasons):
