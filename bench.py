@@ -306,6 +306,8 @@ class Runner:
         # force and torque sums (forces only)
         self.side.wait_stream(main)
         with torch.cuda.stream(self.side):
+            # the plan's cells over a full wave of CTAs (automatic split)
+            self.ctx_v.set_volume_split(0)
             self.ctx_v.particle_volume_integrals_plan(self.u, c.h, self.parts, self.plan, out=self.I1)
         ctx.particle_force_torque(self.parts, self.marks, self.F, c.rho_f, out=(self.Fib, self.Tib))
         main.wait_stream(self.side)

@@ -283,12 +283,15 @@ GBIB_API int particle_volume_integrals(ib_ctx *ctx, const ib_grid *grid, const v
  * after the forcing (Eqs. particle1/particle2, Sec. 3.2.2) with the particles
  * where they are: the cells and their volume fractions alpha are the same.
  * particle_volume_integrals_keep computes what particle_volume_integrals
- * computes and keeps in `plan` the cells each CTA visited, plane by plane, with
- * the boundary cells' alpha; particle_volume_integrals_plan then integrates
- * another field u (same grid, same particles) from the kept cells, without
- * evaluating a level set, with the context's split (ib_ctx_set_volume_split)
- * whatever the keeping call's was: bitwise the sums particle_volume_integrals
- * gives on that field with that split.  A plan holds up to P particles
+ * computes (bitwise) and keeps in `plan` the cells each CTA visited, plane by
+ * plane, with the boundary cells' alpha; particle_volume_integrals_plan then
+ * integrates another field u (same grid, same particles) over the kept cells
+ * with the kept alpha and the same per-cell arithmetic, without evaluating a
+ * level set: each particle's kept cells are one list spread evenly over the
+ * context's split of CTAs per particle (ib_ctx_set_volume_split; automatic:
+ * one resident wave), so its sums agree with particle_volume_integrals on
+ * that field to rounding (another summation order; deterministic for a given
+ * split).  A plan holds up to P particles
  * whose stencil boxes have at most max_box_cells cells (at most 40 cells per
  * axis); a larger box raises IB_ERR_UNSUPPORTED in the context status.  The
  * plan call checks the grid (IB_ERR_INVALID) and, on the device, that every

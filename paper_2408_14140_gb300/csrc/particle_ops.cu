@@ -17,27 +17,30 @@ namespace gbib {
 
 constexpr double kPi = 3.14159265358979323846;
 
-// Fixed-order block sum of NV doubles; result valid in thread 0.
-template <int NV>
+// Fixed-order sum of NV doubles over a CTA of NT threads (NT / 32 >= NV
+// warps); result valid in thread 0.  The values go through shared memory and
+// warp k sums quantity k (each lane NT / 32 entries, then a shuffle tree):
+// NV (NT / 32 + 5) FP64 warp instructions, against NV * 5 per warp for a
+// shuffle tree in every warp -- FP64 issue is scarce on this part.
+template <int NV, int NT>
 __device__ __forceinline__ void block_sum(double v[NV]) {
-    __shared__ double red[32][NV];
-    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    static_assert(NT / 32 >= NV, "one warp per quantity");
+    __shared__ double red[NV][NT];
 #pragma unroll
-    for (int k = 0; k < NV; ++k)
-        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
-    if (lane == 0)
-#pragma unroll
-        for (int k = 0; k < NV; ++k) red[wid][k] = v[k];
+    for (int k = 0; k < NV; ++k) red[k][threadIdx.x] = v[k];
     __syncthreads();
-    if (wid == 0) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (wid < NV) {
+        double x = 0.0;
 #pragma unroll
-        for (int k = 0; k < NV; ++k) {
-            double x = lane < nw ? red[lane][k] : 0.0;
-            for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
-            v[k] = x;
-        }
+        for (int m = 0; m < NT / 32; ++m) x += red[wid][lane + 32 * m];
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+        if (lane == 0) red[wid][0] = x;
     }
     __syncthreads();
+    if (threadIdx.x == 0)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) v[k] = red[k][0];
 }
 
 // ---------------------------------------------------------------------------
@@ -56,10 +59,11 @@ constexpr int kVolMaxSplit = 32;
 constexpr int kVolThreads = 256;   // 8 warps
 constexpr int kVolMaxBox = 40;     // cells per axis of one particle's box (tabulated path)
 constexpr int kVolAx = kVolMaxBox + 1;
-// two node planes of (max(-phi, 0), max(phi, 0)) pairs + per-axis tables
-// (node squares, cell offsets, cell squares) + per-row grid offsets
-constexpr size_t kVolSmem = 2 * kVolAx * kVolAx * sizeof(double2) + 9 * kVolAx * sizeof(double) +
-                            kVolAx * sizeof(long long) + 6 * kVolAx * sizeof(float2) + 3 * kVolAx * sizeof(float);
+// two node planes of (max(-phi, 0), max(phi, 0)) pairs + per-row grid
+// offsets + per-axis tables (cell offsets and node squares as float pairs,
+// cell squares in FP32)
+constexpr size_t kVolSmem = 2 * kVolAx * kVolAx * sizeof(double2) + kVolAx * sizeof(long long) +
+                            6 * kVolAx * sizeof(float2) + 3 * kVolAx * sizeof(float);
 
 // Double-float accumulation: a sum kept as the unevaluated pair hi + lo of two
 // floats -- Knuth's TwoSum for the addition error and the fused multiply-add
@@ -246,9 +250,11 @@ __device__ void volume_finish(double acc[7], double h, int p, int split, int nsp
 // A kept volume plan (particle_volume_integrals_keep / _plan): per particle,
 // the cells each CTA visits plane by plane in its visiting order -- interior
 // cells (alpha = 1) and boundary cells with their alpha, or a skip mark --
-// so that a second call at the same particle positions repeats the same sums
-// from another field without evaluating a level set.  Capacity `cap` entries
-// per particle and list; a CTA's slab starts at dims0 dims1 z0.
+// so that a second call at the same particle positions sums another field
+// over the same cells with the same alpha without evaluating a level set.
+// Capacity `cap` entries per particle and list; a keeping CTA's slab starts
+// at dims0 dims1 z0, and each plane's header gives its lists' counts and
+// first entries.
 struct PvfPlanDev {
     int cap;
     int4 *hdr;        // [P][kVolAx] per plane: interior and boundary counts, first entries
@@ -259,7 +265,7 @@ struct PvfPlanDev {
 };
 constexpr unsigned kPvfSkip = 0x80000000u;
 
-// MODE 0: plain; 1: also keep the plan; 2: the sums from a kept plan.
+// MODE 0: plain; 1: also keep the plan (k_volume_plan sums from it).
 template <typename T, int MODE = 0>
 __global__ void __launch_bounds__(kVolThreads, 3) k_volume(CaseTab ct, int P, int nsplit,
                                                         const double *__restrict__ Xr,
@@ -311,17 +317,9 @@ __global__ void __launch_bounds__(kVolThreads, 3) k_volume(CaseTab ct, int P, in
                 if (split == 0) raise_status(st, IB_ERR_UNSUPPORTED, p);
                 okk = false;
             }
-            if constexpr (MODE == 1) {
-                if (split == 0) {
-                    pl.pos[4 * p] = cc[0], pl.pos[4 * p + 1] = cc[1], pl.pos[4 * p + 2] = cc[2];
-                    pl.pos[4 * p + 3] = R0;
-                }
-            } else {
-                const double *q = pl.pos + 4 * p;
-                if (okk && !(q[0] == cc[0] && q[1] == cc[1] && q[2] == cc[2] && q[3] == R0)) {
-                    if (split == 0) raise_status(st, IB_ERR_INVALID, p);  // not the plan's particle
-                    okk = false;
-                }
+            if (split == 0) {
+                pl.pos[4 * p] = cc[0], pl.pos[4 * p + 1] = cc[1], pl.pos[4 * p + 2] = cc[2];
+                pl.pos[4 * p + 3] = R0;
             }
         }
         s_box[6] = okk;
@@ -359,18 +357,14 @@ __global__ void __launch_bounds__(kVolThreads, 3) k_volume(CaseTab ct, int P, in
         if (tab) {
             const int nx = dims[0] + 1, plane = nx * (dims[1] + 1);
             double2 *phi2 = (double2 *)s_vol;  // node planes: (max(-phi, 0), max(phi, 0))
-            double *tb = (double *)(phi2 + 2 * kVolAx * kVolAx);
-            long long *row_off = (long long *)(tb + 9 * kVolAx);
+            long long *row_off = (long long *)(phi2 + 2 * kVolAx * kVolAx);
             float2 *tbf = (float2 *)(row_off + kVolAx);  // cell offsets as float pairs
             float2 *tsq = tbf + 3 * kVolAx;               // node offset squares as float pairs
             float *tcf = (float *)(tsq + 3 * kVolAx);     // cell offset squares in FP32
             for (int a = 0; a < 3; ++a)
                 for (int i = threadIdx.x; i <= dims[a]; i += blockDim.x) {
-                    const double xn = g.org[a] + (double)(lo[a] + i) * h - c[a];
                     const double xc = g.org[a] + ((double)(lo[a] + i) + 0.5) * h - c[a];
-                    tb[a * kVolAx + i] = xn * xn;
-                    tb[(3 + a) * kVolAx + i] = xc;
-                    tb[(6 + a) * kVolAx + i] = xc * xc;
+                    const double xn = g.org[a] + (double)(lo[a] + i) * h - c[a];
                     tbf[a * kVolAx + i] = df_split_rn(xc);
                     tsq[a * kVolAx + i] = df_split_rn(xn * xn);
                     tcf[a * kVolAx + i] = (float)(xc * xc);
@@ -459,7 +453,7 @@ __global__ void __launch_bounds__(kVolThreads, 3) k_volume(CaseTab ct, int P, in
                     }
                 }
             };
-            if (MODE != 2) node_plane(z0, phi2 + (z0 & 1) * plane);
+            node_plane(z0, phi2 + (z0 & 1) * plane);
             // the CTA's entries in the plan: from dims0 dims1 z0 on, plane by plane
             long long pi = (long long)p * pl.cap + (long long)dims[0] * dims[1] * z0, pb = pi;
             // per-thread double-float sums of w = alpha u, of the six products
@@ -469,9 +463,9 @@ __global__ void __launch_bounds__(kVolThreads, 3) k_volume(CaseTab ct, int P, in
             long long nint_cells = 0;
             DF W[3] = {}, Pm[6] = {}, V = {};
             for (int kz = z0; kz < z1; ++kz) {
-                if (MODE != 2) node_plane(kz + 1, phi2 + ((kz + 1) & 1) * plane);
+                node_plane(kz + 1, phi2 + ((kz + 1) & 1) * plane);
                 // cell rows of plane kz: interior range and the boundary ranges around it
-                for (int j = threadIdx.x; MODE != 2 && j < dims[1]; j += blockDim.x) {
+                for (int j = threadIdx.x; j < dims[1]; j += blockDim.x) {
                     bool in_out, in_in;
                     float wo, wi;
                     {
@@ -500,41 +494,23 @@ __global__ void __launch_bounds__(kVolThreads, 3) k_volume(CaseTab ct, int P, in
                     r_cb[j] = jb >= ja ? max(0, ib - jb) : 0;      // right boundary [jb+1, ib]
                     c_bnd[j] = r_ca[j] + r_cb[j];
                 }
-                int nint, nbnd;
-                if constexpr (MODE == 2) {
-                    // the plane's lists, wherever the keeping call's CTA put them
-                    const int4 hc = pl.hdr[p * kVolAx + kz];
-                    nint = hc.x;
-                    nbnd = hc.y;
-                    pi = (long long)p * pl.cap + hc.z;
-                    pb = (long long)p * pl.cap + hc.w;
-                } else {
-                    __syncthreads();
-                    warp0_scan(c_int, p_int, dims[1]);
-                    warp0_scan(c_bnd, p_bnd, dims[1]);
-                    __syncthreads();
-                    nint = p_int[dims[1]];
-                    nbnd = p_bnd[dims[1]];
-                    if (MODE == 1 && threadIdx.x == 0)
-                        pl.hdr[p * kVolAx + kz] =
-                            make_int4(nint, nbnd, (int)(pi - (long long)p * pl.cap), (int)(pb - (long long)p * pl.cap));
-                }
+                __syncthreads();
+                warp0_scan(c_int, p_int, dims[1]);
+                warp0_scan(c_bnd, p_bnd, dims[1]);
+                __syncthreads();
+                const int nint = p_int[dims[1]], nbnd = p_bnd[dims[1]];
+                if (MODE == 1 && threadIdx.x == 0)
+                    pl.hdr[p * kVolAx + kz] =
+                        make_int4(nint, nbnd, (int)(pi - (long long)p * pl.cap), (int)(pb - (long long)p * pl.cap));
                 const double2 *b0 = phi2 + (kz & 1) * plane, *b1 = phi2 + ((kz + 1) & 1) * plane;
                 const float2 fz = tbf[2 * kVolAx + kz];
                 const float rz2f = tcf[2 * kVolAx + kz];
                 const long long plane_off = (long long)wrap_int(lo[2] + kz, g.n[2]) * g.n[1] * g.n[0];
                 // interior cells: alpha = 1
                 for (int q = threadIdx.x; q < nint; q += blockDim.x) {
-                    int i, j;
-                    if constexpr (MODE == 2) {
-                        const unsigned e = pl.ient[pi + q];
-                        i = (int)(e & 0xffffu);
-                        j = (int)(e >> 16);
-                    } else {
-                        j = find_row(p_int, dims[1], q);
-                        i = r_ic[j] + (q - p_int[j]);
-                        if (MODE == 1) pl.ient[pi + q] = (unsigned)i | ((unsigned)j << 16);
-                    }
+                    const int j = find_row(p_int, dims[1], q);
+                    const int i = r_ic[j] + (q - p_int[j]);
+                    if (MODE == 1) pl.ient[pi + q] = (unsigned)i | ((unsigned)j << 16);
                     const long long cc = plane_off + row_off[j] + wrap_add(lo0w, i, g.n[0]);
                     const float2 fx = tbf[i], fy = tbf[kVolAx + j];
                     const float2 v0 = field_pair(u[cc]), v1 = field_pair(u[N + cc]), v2 = field_pair(u[2 * N + cc]);
@@ -551,25 +527,16 @@ __global__ void __launch_bounds__(kVolThreads, 3) k_volume(CaseTab ct, int P, in
                 nint_cells += (nint + (int)blockDim.x - 1 - (int)threadIdx.x) / (int)blockDim.x;
                 // boundary cells: alpha = sum of max(-phi, 0) / sum |phi| over the corners
                 for (int q = threadIdx.x; q < nbnd; q += blockDim.x) {
-                    int i, j;
                     float2 a2 = make_float2(1.f, 0.f);
-                    if constexpr (MODE == 2) {
-                        const unsigned e = pl.bent[pb + q];
-                        if (e == kPvfSkip) continue;
-                        i = (int)(e & 0xffffu);
-                        j = (int)(e >> 16);
-                        a2 = pl.balpha[pb + q];
-                    } else {
-                        j = find_row(p_bnd, dims[1], q);
-                        const int k = q - p_bnd[j];
-                        i = k < r_ca[j] ? r_ia[j] + k : r_ic[j] + c_int[j] + (k - r_ca[j]);
-                        if (MODE == 1) pl.bent[pb + q] = kPvfSkip;  // until the cell counts
-                    }
+                    const int j = find_row(p_bnd, dims[1], q);
+                    const int k = q - p_bnd[j];
+                    const int i = k < r_ca[j] ? r_ia[j] + k : r_ic[j] + c_int[j] + (k - r_ca[j]);
+                    if (MODE == 1) pl.bent[pb + q] = kPvfSkip;  // until the cell counts
                     {
                         // the cell's alpha in double-float (both field precisions)
                         const float d2f = tcf[i] + tcf[kVolAx + j] + rz2f;
-                        if (MODE != 2 && d2f > rout2f) continue;
-                        if (MODE != 2 && !(d2f < rin2f)) {
+                        if (d2f > rout2f) continue;
+                        if (!(d2f < rin2f)) {
                             const int qn = j * nx + i;
                             const float4 *f0 = (const float4 *)b0, *f1 = (const float4 *)b1;
                             const float4 cn[8] = {f0[qn], f0[qn + 1], f0[qn + nx], f0[qn + nx + 1],
@@ -627,7 +594,7 @@ __global__ void __launch_bounds__(kVolThreads, 3) k_volume(CaseTab ct, int P, in
                 }
                 pi += nint;
                 pb += nbnd;
-                if (MODE != 2) __syncthreads();
+                __syncthreads();
             }
             acc[6] += (double)nint_cells;
             // warp sums in double-float, then FP64 in lane 0 only
@@ -686,6 +653,205 @@ __global__ void __launch_bounds__(kVolThreads, 3) k_volume(CaseTab ct, int P, in
                 }
             }
         }
+    }
+    volume_finish(acc, g.h, p, split, nsplit, partial, done, Iu, Irxu, vol, s_vol);
+}
+
+// ---------------------------------------------------------------------------
+// Volume integrals from a kept plan.  The particle's kept cells -- interior
+// cells, and boundary cells with their double-float alpha -- are read as one
+// list per particle (the planes' lists in plane order), split evenly over
+// nsplit CTAs, each taking a contiguous range.  A thread sums its cells in
+// double-float exactly as k_volume does per cell, kPlanUnroll cells at a
+// time with their list entries and field values loaded together, so no chain
+// of dependent loads runs plane by plane; then warp sums in double-float and
+// the CTA and particle sums of volume_finish.  The same cells, alpha and
+// per-cell arithmetic as k_volume, in another summation order.
+// ---------------------------------------------------------------------------
+constexpr int kPlanUnroll = 4;
+constexpr size_t kPlanSmem = 7 * kVolThreads * sizeof(double);  // volume_finish's CTA sum
+
+template <typename T>
+__global__ void __launch_bounds__(kVolThreads, 2) k_volume_plan(CaseTab ct, int P, int nsplit,
+                                                              const double *__restrict__ Xr,
+                                                              const double *__restrict__ radius,
+                                                              double *__restrict__ partial,
+                                                              unsigned int *__restrict__ done, double *Iu,
+                                                              double *Irxu, double *vol, DevStatus *st,
+                                                              PvfPlanDev pl) {
+    extern __shared__ __align__(16) double s_vol[];
+    __shared__ float2 tbf[3 * kVolAx];  // cell-centre offsets from X_r as float pairs
+    __shared__ long long row_off[kVolAx], plane_off[kVolAx];
+    __shared__ int c_int[kVolAx], c_bnd[kVolAx], b_int[kVolAx], b_bnd[kVolAx];
+    __shared__ int p_int[kVolAx + 1], p_bnd[kVolAx + 1];
+    __shared__ double s_c[3];
+    __shared__ int s_box[7];
+    const int p = blockIdx.x / nsplit, split = blockIdx.x % nsplit;
+    if (p >= P) return;
+    const DevCase &cd = ct.of_particle(p);
+    const DevGrid g = cd.g;
+    const T *__restrict__ u = (const T *)cd.u;
+    if (threadIdx.x == 0) {
+        // the particle's box as the keeping call formed it, once the plan is
+        // known to be this particle's
+        const double cc[3] = {Xr[3 * p], Xr[3 * p + 1], Xr[3 * p + 2]};
+        const double R0 = radius[p];
+        const double *q = pl.pos + 4 * p;
+        bool okk = q[0] == cc[0] && q[1] == cc[1] && q[2] == cc[2] && q[3] == R0;
+        if (!okk && split == 0) raise_status(st, IB_ERR_INVALID, p);  // not the plan's particle
+        int lo0[3] = {0, 0, 0}, dm0[3] = {0, 0, 0};
+        okk = okk && finite3(cc) && isfinite(R0) && R0 > 0.0;
+        if (okk)
+            for (int a = 0; a < 3; ++a) {
+                const long long l = (long long)floor((cc[a] - R0 - g.org[a]) * g.inv_h) - 1;
+                const long long hgh = (long long)floor((cc[a] + R0 - g.org[a]) * g.inv_h) + 1;
+                lo0[a] = (int)l;
+                dm0[a] = (int)(hgh - l + 1);
+                // the keeping call kept only boxes of the tabulated size
+                if (dm0[a] > g.n[a] || dm0[a] > kVolMaxBox || l < INT_MIN / 2 || l > INT_MAX / 2) okk = false;
+            }
+        if (okk && (long long)dm0[0] * dm0[1] * dm0[2] > pl.cap) okk = false;  // not kept (reported then)
+        for (int a = 0; a < 3; ++a) {
+            s_c[a] = cc[a];
+            s_box[a] = lo0[a];
+            s_box[3 + a] = dm0[a];
+        }
+        s_box[6] = okk;
+    }
+    __syncthreads();
+    const bool ok = s_box[6] != 0;
+    const int lo[3] = {s_box[0], s_box[1], s_box[2]}, dims[3] = {s_box[3], s_box[4], s_box[5]};
+    const long long N = (long long)g.n[0] * g.n[1] * g.n[2];
+    if (ok) {
+        const double h = g.h;
+        for (int a = 0; a < 3; ++a)
+            for (int i = threadIdx.x; i <= dims[a]; i += blockDim.x)
+                tbf[a * kVolAx + i] = df_split_rn(g.org[a] + ((double)(lo[a] + i) + 0.5) * h - s_c[a]);
+        for (int j = threadIdx.x; j < dims[1]; j += blockDim.x)
+            row_off[j] = (long long)wrap_int(lo[1] + j, g.n[1]) * g.n[0];
+        for (int k = threadIdx.x; k < dims[2]; k += blockDim.x) {
+            plane_off[k] = (long long)wrap_int(lo[2] + k, g.n[2]) * g.n[1] * g.n[0];
+            const int4 hc = pl.hdr[p * kVolAx + k];
+            c_int[k] = hc.x;
+            c_bnd[k] = hc.y;
+            b_int[k] = hc.z;
+            b_bnd[k] = hc.w;
+        }
+    }
+    __syncthreads();
+    if (ok) {
+        warp0_scan(c_int, p_int, dims[2]);
+        warp0_scan(c_bnd, p_bnd, dims[2]);
+    }
+    __syncthreads();
+    DF W[3] = {}, Pm[6] = {}, V = {};
+    long long nint_cells = 0;
+    if (ok) {
+        const int lo0w = wrap_int(lo[0], g.n[0]);
+        const long long base = (long long)p * pl.cap;
+        const int NI = p_int[dims[2]], NB = p_bnd[dims[2]];
+        // interior cells: alpha = 1
+        const int i0 = (int)((long long)NI * split / nsplit), i1 = (int)((long long)NI * (split + 1) / nsplit);
+        for (int e0 = i0 + threadIdx.x; e0 < i1; e0 += kPlanUnroll * blockDim.x) {
+            long long cc[kPlanUnroll];
+            int kz[kPlanUnroll];
+            unsigned ent[kPlanUnroll];
+#pragma unroll
+            for (int t = 0; t < kPlanUnroll; ++t) {
+                const int e = e0 + t * blockDim.x;
+                kz[t] = e < i1 ? find_row(p_int, dims[2], e) : 0;
+                ent[t] = e < i1 ? pl.ient[base + b_int[kz[t]] + (e - p_int[kz[t]])] : 0u;
+            }
+            float2 v[kPlanUnroll][3];
+#pragma unroll
+            for (int t = 0; t < kPlanUnroll; ++t) {
+                const int i = (int)(ent[t] & 0xffffu), j = (int)(ent[t] >> 16);
+                cc[t] = plane_off[kz[t]] + row_off[j] + wrap_add(lo0w, i, g.n[0]);
+                if (e0 + t * (int)blockDim.x < i1)
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) v[t][c] = field_pair(u[c * N + cc[t]]);
+            }
+#pragma unroll
+            for (int t = 0; t < kPlanUnroll; ++t) {
+                if (e0 + t * (int)blockDim.x >= i1) break;
+                const int i = (int)(ent[t] & 0xffffu), j = (int)(ent[t] >> 16);
+                const float2 fx = tbf[i], fy = tbf[kVolAx + j], fz = tbf[2 * kVolAx + kz[t]];
+                df_add2(W[0], v[t][0].x, v[t][0].y);
+                df_add2(W[1], v[t][1].x, v[t][1].y);
+                df_add2(W[2], v[t][2].x, v[t][2].y);
+                df_add_prod(Pm[0], fy.x, fy.y, v[t][2].x, v[t][2].y);
+                df_add_prod(Pm[1], fz.x, fz.y, v[t][1].x, v[t][1].y);
+                df_add_prod(Pm[2], fz.x, fz.y, v[t][0].x, v[t][0].y);
+                df_add_prod(Pm[3], fx.x, fx.y, v[t][2].x, v[t][2].y);
+                df_add_prod(Pm[4], fx.x, fx.y, v[t][1].x, v[t][1].y);
+                df_add_prod(Pm[5], fy.x, fy.y, v[t][0].x, v[t][0].y);
+                ++nint_cells;
+            }
+        }
+        // boundary cells: the kept alpha (entries of cells with alpha = 0 are marked)
+        const int j0 = (int)((long long)NB * split / nsplit), j1 = (int)((long long)NB * (split + 1) / nsplit);
+        for (int e0 = j0 + threadIdx.x; e0 < j1; e0 += kPlanUnroll * blockDim.x) {
+            int kz[kPlanUnroll];
+            unsigned ent[kPlanUnroll];
+            float2 al[kPlanUnroll];
+#pragma unroll
+            for (int t = 0; t < kPlanUnroll; ++t) {
+                const int e = e0 + t * blockDim.x;
+                kz[t] = e < j1 ? find_row(p_bnd, dims[2], e) : 0;
+                const long long at = base + b_bnd[kz[t]] + (e - p_bnd[kz[t]]);
+                ent[t] = e < j1 ? pl.bent[at] : kPvfSkip;
+                al[t] = e < j1 ? pl.balpha[at] : make_float2(0.f, 0.f);
+            }
+            float2 v[kPlanUnroll][3];
+#pragma unroll
+            for (int t = 0; t < kPlanUnroll; ++t) {
+                if (ent[t] == kPvfSkip) continue;
+                const int i = (int)(ent[t] & 0xffffu), j = (int)(ent[t] >> 16);
+                const long long cc = plane_off[kz[t]] + row_off[j] + wrap_add(lo0w, i, g.n[0]);
+#pragma unroll
+                for (int c = 0; c < 3; ++c) v[t][c] = field_pair(u[c * N + cc]);
+            }
+#pragma unroll
+            for (int t = 0; t < kPlanUnroll; ++t) {
+                if (ent[t] == kPvfSkip) continue;
+                const float2 a2 = al[t];
+                const int i = (int)(ent[t] & 0xffffu), j = (int)(ent[t] >> 16);
+                df_add2(V, a2.x, a2.y);
+                const float2 fx = tbf[i], fy = tbf[kVolAx + j], fz = tbf[2 * kVolAx + kz[t]];
+                float wh[3], wl[3];
+#pragma unroll
+                for (int q3 = 0; q3 < 3; ++q3) {
+                    wh[q3] = a2.x * v[t][q3].x;
+                    wl[q3] = fmaf(a2.x, v[t][q3].x, -wh[q3]) + a2.y * v[t][q3].x;
+                    if constexpr (sizeof(T) == 8) wl[q3] = fmaf(a2.x, v[t][q3].y, wl[q3]);
+                    df_add2(W[q3], wh[q3], wl[q3]);
+                }
+                df_add_prod(Pm[0], fy.x, fy.y, wh[2], wl[2]);
+                df_add_prod(Pm[1], fz.x, fz.y, wh[1], wl[1]);
+                df_add_prod(Pm[2], fz.x, fz.y, wh[0], wl[0]);
+                df_add_prod(Pm[3], fx.x, fx.y, wh[2], wl[2]);
+                df_add_prod(Pm[4], fx.x, fx.y, wh[1], wl[1]);
+                df_add_prod(Pm[5], fy.x, fy.y, wh[0], wl[0]);
+            }
+        }
+    }
+    double acc[7] = {0, 0, 0, 0, 0, 0, (double)nint_cells};
+    // warp sums in double-float, then FP64 in lane 0 only
+#pragma unroll
+    for (int q = 0; q < 3; ++q) df_warp_sum(W[q]);
+#pragma unroll
+    for (int q = 0; q < 6; ++q) df_warp_sum(Pm[q]);
+    df_warp_sum(V);
+    if ((threadIdx.x & 31) == 0) {
+        acc[6] += (double)V.hi + (double)V.lo;
+        double pm[6];
+#pragma unroll
+        for (int q = 0; q < 6; ++q) pm[q] = (double)Pm[q].hi + (double)Pm[q].lo;
+#pragma unroll
+        for (int q = 0; q < 3; ++q) acc[q] = (double)W[q].hi + (double)W[q].lo;
+        acc[3] = pm[0] - pm[1];
+        acc[4] = pm[2] - pm[3];
+        acc[5] = pm[4] - pm[5];
     }
     volume_finish(acc, g.h, p, split, nsplit, partial, done, Iu, Irxu, vol, s_vol);
 }
@@ -815,17 +981,29 @@ __global__ void k_drag(int P, const double *__restrict__ Fib, const double *__re
 }
 
 // ---------------------------------------------------------------------------
-// force and torque: one CTA per particle
+// force and torque (Sec. 3.2.2): nsplit CTAs per particle, each summing a
+// contiguous range of the particle's markers in FP64; with nsplit > 1 the
+// particle's last CTA adds the CTAs' partial sums in CTA order (deterministic).
+// FP64 issue (two operations per clock per SM) bounds these sums, so each
+// particle's markers are spread over kFtSplit CTAs.  The split is a constant:
+// a particle's sums do not depend on the other particles of the call (a
+// request served alone equals the same request in a batch, bit for bit).
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_force_torque(int P, const int *__restrict__ moff,
-                                                      const double *__restrict__ R,
-                                                      const double *__restrict__ dV,
-                                                      const double *__restrict__ F, double rho_f,
-                                                      double *__restrict__ Fib, double *__restrict__ Tib) {
-    int p = blockIdx.x;
+constexpr int kFtThreads = 256;
+constexpr int kFtSplit = 4;
+__global__ void __launch_bounds__(kFtThreads) k_force_torque(int P, int nsplit, const int *__restrict__ moff,
+                                                             const double *__restrict__ R,
+                                                             const double *__restrict__ dV,
+                                                             const double *__restrict__ F, double rho_f,
+                                                             double *__restrict__ partial,
+                                                             unsigned int *__restrict__ done,
+                                                             double *__restrict__ Fib, double *__restrict__ Tib) {
+    const int p = blockIdx.x / nsplit, part = blockIdx.x % nsplit;
     if (p >= P) return;
+    const int m0 = moff[p], nm = moff[p + 1] - m0;
+    const int l0 = m0 + (int)((long long)part * nm / nsplit), l1 = m0 + (int)((long long)(part + 1) * nm / nsplit);
     double acc[6] = {0, 0, 0, 0, 0, 0};
-    for (int l = moff[p] + threadIdx.x; l < moff[p + 1]; l += blockDim.x) {
+    for (int l = l0 + threadIdx.x; l < l1; l += blockDim.x) {
         double gx = F[3 * l] * dV[l], gy = F[3 * l + 1] * dV[l], gz = F[3 * l + 2] * dV[l];
         double rx = R[3 * l], ry = R[3 * l + 1], rz = R[3 * l + 2];
         acc[0] += gx;
@@ -835,12 +1013,24 @@ __global__ void __launch_bounds__(256) k_force_torque(int P, const int *__restri
         acc[4] += rz * gx - rx * gz;
         acc[5] += rx * gy - ry * gx;
     }
-    block_sum<6>(acc);
-    if (threadIdx.x == 0)
-        for (int a = 0; a < 3; ++a) {
-            Fib[3 * p + a] = -rho_f * acc[a];
-            Tib[3 * p + a] = -rho_f * acc[3 + a];
-        }
+    block_sum<6, kFtThreads>(acc);
+    if (threadIdx.x != 0) return;
+    if (nsplit > 1) {
+        // the particle's last CTA adds the partial sums in CTA order
+        double *dst = partial + ((size_t)p * nsplit + part) * 6;
+        for (int a = 0; a < 6; ++a) dst[a] = acc[a];
+        __threadfence();  // release: partials before the count
+        const bool last = atomicAdd(done + p, 1u) == (unsigned int)nsplit - 1;
+        __threadfence();  // acquire: the count before the other partials
+        if (!last) return;
+        for (int a = 0; a < 6; ++a) acc[a] = 0.0;
+        for (int k = 0; k < nsplit; ++k)
+            for (int a = 0; a < 6; ++a) acc[a] += __ldcg(partial + ((size_t)p * nsplit + k) * 6 + a);
+    }
+    for (int a = 0; a < 3; ++a) {
+        Fib[3 * p + a] = -rho_f * acc[a];
+        Tib[3 * p + a] = -rho_f * acc[3 + a];
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -851,7 +1041,7 @@ struct CollideArgs {
     CaseTab ct;  // pairs are taken within a case, in the case's periodic box
     double *Xr, *Ur, *Wr;
     const double *radius, *rho_p;
-    double dt;
+    double dt, inv_dt;  // inv_dt = 1 / dt, formed on the host
     const double *Fib, *Tib, *Iu_new, *Iu_old, *Ir_new, *Ir_old;
     double *Fc_out;
     double *Xnew;  // [P][3] scratch: positions are read by every thread
@@ -910,14 +1100,18 @@ __global__ void k_newton_euler(CollideArgs a, const double *__restrict__ Fc, Dev
     double V = 4.0 / 3.0 * kPi * Rp * Rp * Rp;
     double m = a.rho_p[p] * V;
     double I = 0.4 * m * Rp * Rp;
+    // FP64 divisions are long instruction sequences on a part with two FP64
+    // operations per clock per SM: 1/dt comes from the host, dt/m and dt/I
+    // are formed once
+    const double dtm = a.dt / m, dtI = a.dt / I;
     bool ok = true;
     for (int k = 0; k < 3; ++k) {
         double Un = a.Ur[3 * p + k];
-        double rhs = a.Fib[3 * p + k] + ph.rho_f * (a.Iu_new[3 * p + k] - a.Iu_old[3 * p + k]) / a.dt +
+        double rhs = a.Fib[3 * p + k] + ph.rho_f * (a.Iu_new[3 * p + k] - a.Iu_old[3 * p + k]) * a.inv_dt +
                      (a.rho_p[p] - ph.rho_f) * V * ph.g[k] + Fc[3 * p + k];
-        double Unew = Un + a.dt / m * rhs;
-        double trq = a.Tib[3 * p + k] + ph.rho_f * (a.Ir_new[3 * p + k] - a.Ir_old[3 * p + k]) / a.dt;
-        double Wnew = a.Wr[3 * p + k] + a.dt / I * trq;
+        double Unew = Un + dtm * rhs;
+        double trq = a.Tib[3 * p + k] + ph.rho_f * (a.Ir_new[3 * p + k] - a.Ir_old[3 * p + k]) * a.inv_dt;
+        double Wnew = a.Wr[3 * p + k] + dtI * trq;
         double Xnew = a.Xr[3 * p + k] + 0.5 * a.dt * (Unew + Un);
         ok = ok && isfinite(Unew) && isfinite(Wnew) && isfinite(Xnew);
         a.Ur[3 * p + k] = Unew;
@@ -1023,7 +1217,22 @@ static int run_volume_plan(ib_ctx *ctx, Arena &ar, const CaseTab &ct, const ib_p
     cudaMemsetAsync(done, 0, sizeof(unsigned int) * pp->P, s);
     k_volume<T, MODE><<<pp->P * nsplit, kVolThreads, kVolSmem, s>>>(ct, pp->P, nsplit, pp->Xr, pp->radius, partial,
                                                                     done, Iu, Irxu, vol, ctx->status, pl);
-    return check_launch(MODE == 1 ? "particle_volume_integrals_keep" : "particle_volume_integrals_plan");
+    return check_launch("particle_volume_integrals_keep");
+}
+
+template <typename T>
+static int run_plan_sums(ib_ctx *ctx, Arena &ar, const CaseTab &ct, const ib_particles *pp, const PvfPlanDev &pl,
+                         double *Iu, double *Irxu, double *vol, cudaStream_t s) {
+    const int nsplit = volume_split(ctx, (const void *)k_volume_plan<T>, kPlanSmem, pp->P);
+    double *partial = ar.take<double>((size_t)pp->P * nsplit * 7);
+    unsigned int *done = ar.take<unsigned int>(pp->P);
+    if (!ar.ok())
+        return oom_error(ar.used, ar.cap);
+    PhaseTimer tm(ctx, IB_PHASE_VOLUME, s);
+    cudaMemsetAsync(done, 0, sizeof(unsigned int) * pp->P, s);
+    k_volume_plan<T><<<pp->P * nsplit, kVolThreads, kPlanSmem, s>>>(ct, pp->P, nsplit, pp->Xr, pp->radius, partial,
+                                                                    done, Iu, Irxu, vol, ctx->status, pl);
+    return check_launch("particle_volume_integrals_plan");
 }
 
 }  // namespace gbib
@@ -1122,16 +1331,10 @@ int particle_volume_integrals_plan(ib_ctx *ctx, const ib_grid *grid, const void 
     if (!u || !parts->Xr || !parts->radius) return set_error(IB_ERR_INVALID, "NULL array");
     const CaseTab ct = single_case(grid, (void *)u, nullptr, parts->P);
     Arena ar(ctx);
-    // any split: the plan holds each plane's lists
-    int nsplit;
-    if (grid->prec == IB_F64) {
-        cudaFuncSetAttribute(k_volume<double, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kVolSmem);
-        nsplit = volume_split(ctx, (const void *)k_volume<double, 2>, kVolSmem, parts->P);
-        return run_volume_plan<double, 2>(ctx, ar, ct, parts, nsplit, plan->dev, Iu, Irxu, vol, (cudaStream_t)stream);
-    }
-    cudaFuncSetAttribute(k_volume<float, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kVolSmem);
-    nsplit = volume_split(ctx, (const void *)k_volume<float, 2>, kVolSmem, parts->P);
-    return run_volume_plan<float, 2>(ctx, ar, ct, parts, nsplit, plan->dev, Iu, Irxu, vol, (cudaStream_t)stream);
+    // any split: the plan holds each particle's cells
+    if (grid->prec == IB_F64)
+        return run_plan_sums<double>(ctx, ar, ct, parts, plan->dev, Iu, Irxu, vol, (cudaStream_t)stream);
+    return run_plan_sums<float>(ctx, ar, ct, parts, plan->dev, Iu, Irxu, vol, (cudaStream_t)stream);
 }
 
 int particle_volume_integrals(ib_ctx *ctx, const ib_grid *grid, const void *u, const ib_particles *parts,
@@ -1237,9 +1440,17 @@ int particle_force_torque(ib_ctx *ctx, const ib_particles *parts, const ib_marke
     if (parts->P == 0) return IB_OK;
     if (!parts->marker_offset || !F_ib || !T_ib || (marks->M > 0 && (!marks->R || !marks->dV || !F)))
         return set_error(IB_ERR_INVALID, "NULL array");
-    PhaseTimer tm(ctx, IB_PHASE_FORCE, (cudaStream_t)stream);
-    k_force_torque<<<parts->P, 256, 0, (cudaStream_t)stream>>>(parts->P, parts->marker_offset, marks->R,
-                                                              marks->dV, F, rho_f, F_ib, T_ib);
+    const int P = parts->P, nsplit = kFtSplit;
+    cudaStream_t s = (cudaStream_t)stream;
+    Arena ar(ctx);
+    double *partial = nsplit > 1 ? ar.take<double>((size_t)P * nsplit * 6) : nullptr;
+    unsigned int *done = nsplit > 1 ? ar.take<unsigned int>(P) : nullptr;
+    if (!ar.ok())
+        return oom_error(ar.used, ar.cap);
+    PhaseTimer tm(ctx, IB_PHASE_FORCE, s);
+    if (done) cudaMemsetAsync(done, 0, sizeof(unsigned int) * P, s);
+    k_force_torque<<<P * nsplit, kFtThreads, 0, s>>>(P, nsplit, parts->marker_offset, marks->R, marks->dV, F, rho_f,
+                                                   partial, done, F_ib, T_ib);
     return check_launch("particle_force_torque");
 }
 
@@ -1274,6 +1485,7 @@ static int run_collide(ib_ctx *ctx, Arena &ar, const CaseTab &ct, ib_particles *
     a.radius = parts->radius;
     a.rho_p = parts->rho_p;
     a.dt = dt;
+    a.inv_dt = 1.0 / dt;
     a.Fib = F_ib;
     a.Tib = T_ib;
     a.Iu_new = Iu_new;
@@ -1282,10 +1494,11 @@ static int run_collide(ib_ctx *ctx, Arena &ar, const CaseTab &ct, ib_particles *
     a.Ir_old = Irxu_old;
     a.Fc_out = Fc_out;
     a.Xnew = nullptr;
-    int nb = (parts->P + 127) / 128;
+    // one warp per CTA: both kernels are FP64-issue bound (two operations per
+    // clock per SM), so the particles' warps are spread over as many SMs
     PhaseTimer tm(ctx, IB_PHASE_COLLIDE, s);
-    k_collide_forces<<<(parts->P + 3) / 4, 128, 0, s>>>(a, Fc);
-    launch_pdl(k_newton_euler, dim3(nb), dim3(128), 0, s, a, (const double *)Fc, ctx->status);
+    k_collide_forces<<<parts->P, 32, 0, s>>>(a, Fc);
+    launch_pdl(k_newton_euler, dim3((parts->P + 31) / 32), dim3(32), 0, s, a, (const double *)Fc, ctx->status);
     return check_launch("particle_collide_update");
 }
 
