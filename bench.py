@@ -263,6 +263,11 @@ class Runner:
         # ones before it kept (the particles do not move in between)
         self.plan = api.PvfPlan(self.ctx_v, case.P, int(2 * np.max(case.radius) / case.h + 4) ** 3)
         self.side = torch.cuda.Stream(device=device)
+        # CTAs per particle of the first volume integrals, which run beside
+        # the forcing's preparation kernels and take SMs from them (measured
+        # best: 2 for FP32 fields, 3 for FP64 fields, whose preparation is
+        # longer)
+        self.v0_split = 3 if prec == api.IB_F64 else 2
         self.ev_v = torch.cuda.Event()
         self.ctx.set_field_wait(self.ev_v)
         dt = api.field_dtype(prec)
@@ -296,8 +301,8 @@ class Runner:
         main = torch.cuda.current_stream()
         self.side.wait_stream(main)
         with torch.cuda.stream(self.side):
-            # two CTAs per particle: the preparation's kernels keep most SMs
-            self.ctx_v.set_volume_split(2)
+            # a few CTAs per particle: the preparation's kernels keep most SMs
+            self.ctx_v.set_volume_split(self.v0_split)
             self.ctx_v.particle_volume_integrals_keep(self.u, c.h, self.parts, self.plan, out=self.I0)
             self.ev_v.record(self.side)
         ctx.ib_multidirect_forcing(self.u, c.h, self.parts, self.marks, c.Ns, c.dt, F_out=self.F,

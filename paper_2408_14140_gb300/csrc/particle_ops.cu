@@ -691,6 +691,15 @@ __global__ void __launch_bounds__(kVolThreads, 2) k_volume_plan(CaseTab ct, int 
     const DevCase &cd = ct.of_particle(p);
     const DevGrid g = cd.g;
     const T *__restrict__ u = (const T *)cd.u;
+    // the plan's plane headers, loaded beside the particle's scalars (every
+    // particle has kVolAx header slots; only the box's planes are read)
+    for (int k = threadIdx.x; k < kVolAx; k += blockDim.x) {
+        const int4 hc = pl.hdr[p * kVolAx + k];
+        c_int[k] = hc.x;
+        c_bnd[k] = hc.y;
+        b_int[k] = hc.z;
+        b_bnd[k] = hc.w;
+    }
     if (threadIdx.x == 0) {
         // the particle's box as the keeping call formed it, once the plan is
         // known to be this particle's
@@ -729,14 +738,8 @@ __global__ void __launch_bounds__(kVolThreads, 2) k_volume_plan(CaseTab ct, int 
                 tbf[a * kVolAx + i] = df_split_rn(g.org[a] + ((double)(lo[a] + i) + 0.5) * h - s_c[a]);
         for (int j = threadIdx.x; j < dims[1]; j += blockDim.x)
             row_off[j] = (long long)wrap_int(lo[1] + j, g.n[1]) * g.n[0];
-        for (int k = threadIdx.x; k < dims[2]; k += blockDim.x) {
+        for (int k = threadIdx.x; k < dims[2]; k += blockDim.x)
             plane_off[k] = (long long)wrap_int(lo[2] + k, g.n[2]) * g.n[1] * g.n[0];
-            const int4 hc = pl.hdr[p * kVolAx + k];
-            c_int[k] = hc.x;
-            c_bnd[k] = hc.y;
-            b_int[k] = hc.z;
-            b_bnd[k] = hc.w;
-        }
     }
     __syncthreads();
     if (ok) {
