@@ -108,27 +108,36 @@ __global__ void k_prep_spread(DevGrid g, int M, const double *__restrict__ X,
 // with a non-finite state, counts as R_l = 0, as in the marker preparation,
 // which reports it).  It reads only the call's inputs, so the conflict lists
 // and the wavefront levels, which need rho, run on the context's second
-// stream beside the marker preparation.
+// stream beside the marker preparation.  rho only widens the FP32 conflict
+// test (whose margin is h/16), so it is formed in FP32 from the components'
+// leading 24 bits (split on the integer pipe, each at most |R_l|) and then
+// enlarged by a relative 2^-18, which keeps it an upper bound of max |R_l|
+// above the FP32 roundings; no FP64 operation runs per marker.
 __global__ void __launch_bounds__(256) k_marker_radius(int P, const double *__restrict__ Xr,
                                                        const double *__restrict__ Ur,
                                                        const double *__restrict__ Wr,
                                                        const int *__restrict__ moff, const double *__restrict__ R,
                                                        const double *__restrict__ dV, double *__restrict__ rho) {
-    __shared__ double s_max[8];
+    __shared__ float s_max[8];
     const int p = blockIdx.x;
     if (p >= P) return;
     const bool pok = finite3(Xr + 3 * p) && finite3(Ur + 3 * p) && finite3(Wr + 3 * p);
-    double rmax = 0.0;  // squared; the root is taken once below
-    for (int l = moff[p] + threadIdx.x; l < moff[p + 1]; l += blockDim.x) {
+    float rmax = 0.0f;  // squared; the root is taken once below
+    const int m1 = moff[p + 1];
+#pragma unroll 4
+    for (int l = moff[p] + threadIdx.x; l < m1; l += blockDim.x) {
         const double r[3] = {R[3 * l], R[3 * l + 1], R[3 * l + 2]};
-        if (pok && finite3(r) && finite_bits(dV[l])) rmax = fmax(rmax, r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+        if (pok && finite3(r) && finite_bits(dV[l])) {
+            const float x = df_split(r[0]).x, y = df_split(r[1]).x, z = df_split(r[2]).x;
+            rmax = fmaxf(rmax, fmaf(z, z, fmaf(y, y, x * x)));
+        }
     }
-    for (int o = 16; o > 0; o >>= 1) rmax = fmax(rmax, __shfl_down_sync(0xffffffffu, rmax, o));
+    for (int o = 16; o > 0; o >>= 1) rmax = fmaxf(rmax, __shfl_down_sync(0xffffffffu, rmax, o));
     if ((threadIdx.x & 31) == 0) s_max[threadIdx.x >> 5] = rmax;
     __syncthreads();
     if (threadIdx.x == 0) {
-        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) rmax = fmax(rmax, s_max[w]);
-        rho[p] = sqrt(rmax);
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) rmax = fmaxf(rmax, s_max[w]);
+        rho[p] = (double)sqrtf(rmax) * (1.0 + 0x1p-18);
     }
 }
 

@@ -665,11 +665,12 @@ __global__ void __launch_bounds__(kVolThreads, 3) k_volume(CaseTab ct, int P, in
 // double-float exactly as k_volume does per cell, kPlanUnroll cells at a
 // time with their list entries and field values loaded together, so no chain
 // of dependent loads runs plane by plane; then warp sums in double-float and
-// the CTA and particle sums of volume_finish.  The same cells, alpha and
-// per-cell arithmetic as k_volume, in another summation order.
+// the CTA's warp sums and the particle's CTA sums in FP64, in order.  The same
+// cells, alpha and per-cell arithmetic as k_volume, in another summation
+// order.
 // ---------------------------------------------------------------------------
 constexpr int kPlanUnroll = 4;
-constexpr size_t kPlanSmem = 7 * kVolThreads * sizeof(double);  // volume_finish's CTA sum
+constexpr size_t kPlanSmem = 7 * (kVolThreads / 32) * sizeof(double);  // the warps' sums
 
 template <typename T>
 __global__ void __launch_bounds__(kVolThreads, 2) k_volume_plan(CaseTab ct, int P, int nsplit,
@@ -838,25 +839,59 @@ __global__ void __launch_bounds__(kVolThreads, 2) k_volume_plan(CaseTab ct, int 
             }
         }
     }
-    double acc[7] = {0, 0, 0, 0, 0, 0, (double)nint_cells};
-    // warp sums in double-float, then FP64 in lane 0 only
+    // warp sums (double-float; the interior count exactly), then the CTA's
+    // eight warp sums and the particle's nsplit CTA sums in FP64, in order
+    // (the few FP64 operations left: FP64 issue is scarce on this part)
 #pragma unroll
     for (int q = 0; q < 3; ++q) df_warp_sum(W[q]);
 #pragma unroll
     for (int q = 0; q < 6; ++q) df_warp_sum(Pm[q]);
     df_warp_sum(V);
-    if ((threadIdx.x & 31) == 0) {
-        acc[6] += (double)V.hi + (double)V.lo;
+    const unsigned ncell = __reduce_add_sync(0xffffffffu, (unsigned)nint_cells);
+    double *s_w = s_vol;  // [warps][7]
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) {
         double pm[6];
 #pragma unroll
         for (int q = 0; q < 6; ++q) pm[q] = (double)Pm[q].hi + (double)Pm[q].lo;
 #pragma unroll
-        for (int q = 0; q < 3; ++q) acc[q] = (double)W[q].hi + (double)W[q].lo;
-        acc[3] = pm[0] - pm[1];
-        acc[4] = pm[2] - pm[3];
-        acc[5] = pm[4] - pm[5];
+        for (int q = 0; q < 3; ++q) s_w[wid * 7 + q] = (double)W[q].hi + (double)W[q].lo;
+        s_w[wid * 7 + 3] = pm[0] - pm[1];
+        s_w[wid * 7 + 4] = pm[2] - pm[3];
+        s_w[wid * 7 + 5] = pm[4] - pm[5];
+        s_w[wid * 7 + 6] = (double)ncell + ((double)V.hi + (double)V.lo);
     }
-    volume_finish(acc, g.h, p, split, nsplit, partial, done, Iu, Irxu, vol, s_vol);
+    __syncthreads();
+    __shared__ int s_last;
+    if (threadIdx.x < 7) {
+        const int k = threadIdx.x;
+        double x = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) x += s_w[w * 7 + k];
+        const double h3 = g.h * g.h * g.h;
+        partial[((size_t)p * nsplit + split) * 7 + k] = x * h3;
+        __threadfence();  // release: partials before the count
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        s_last = atomicAdd(done + p, 1u) == (unsigned int)nsplit - 1;
+        __threadfence();  // acquire: the count before the other partials
+    }
+    __syncthreads();
+    if (s_last && threadIdx.x < 7) {
+        // the particle's last CTA adds the CTA sums in CTA order
+        const int k = threadIdx.x;
+        double x = 0.0;
+        for (int sp = 0; sp < nsplit; ++sp) x += __ldcg(partial + ((size_t)p * nsplit + sp) * 7 + k);
+        if (k < 3) {
+            if (Iu) Iu[3 * p + k] = x;
+        } else if (k < 6) {
+            if (Irxu) Irxu[3 * p + k - 3] = x;
+        } else if (vol) {
+            vol[p] = x;
+        }
+        if (k == 0) done[p] = 0;  // ready for the next call
+    }
 }
 
 // ---------------------------------------------------------------------------
