@@ -756,6 +756,8 @@ __global__ void __launch_bounds__(kVolThreads, 2) k_volume_plan(CaseTab ct, int 
         const int NI = p_int[dims[2]], NB = p_bnd[dims[2]];
         // interior cells: alpha = 1
         const int i0 = (int)((long long)NI * split / nsplit), i1 = (int)((long long)NI * (split + 1) / nsplit);
+        // a thread's entries ascend, so its plane only moves forward
+        int kzc = i0 + (int)threadIdx.x < i1 ? find_row(p_int, dims[2], i0 + threadIdx.x) : 0;
         for (int e0 = i0 + threadIdx.x; e0 < i1; e0 += kPlanUnroll * blockDim.x) {
             long long cc[kPlanUnroll];
             int kz[kPlanUnroll];
@@ -763,8 +765,10 @@ __global__ void __launch_bounds__(kVolThreads, 2) k_volume_plan(CaseTab ct, int 
 #pragma unroll
             for (int t = 0; t < kPlanUnroll; ++t) {
                 const int e = e0 + t * blockDim.x;
-                kz[t] = e < i1 ? find_row(p_int, dims[2], e) : 0;
-                ent[t] = e < i1 ? pl.ient[base + b_int[kz[t]] + (e - p_int[kz[t]])] : 0u;
+                if (e < i1)
+                    while (p_int[kzc + 1] <= e) ++kzc;
+                kz[t] = kzc;
+                ent[t] = e < i1 ? pl.ient[base + b_int[kzc] + (e - p_int[kzc])] : 0u;
             }
             float2 v[kPlanUnroll][3];
 #pragma unroll
@@ -794,6 +798,7 @@ __global__ void __launch_bounds__(kVolThreads, 2) k_volume_plan(CaseTab ct, int 
         }
         // boundary cells: the kept alpha (entries of cells with alpha = 0 are marked)
         const int j0 = (int)((long long)NB * split / nsplit), j1 = (int)((long long)NB * (split + 1) / nsplit);
+        int kzb = j0 + (int)threadIdx.x < j1 ? find_row(p_bnd, dims[2], j0 + threadIdx.x) : 0;
         for (int e0 = j0 + threadIdx.x; e0 < j1; e0 += kPlanUnroll * blockDim.x) {
             int kz[kPlanUnroll];
             unsigned ent[kPlanUnroll];
@@ -801,7 +806,9 @@ __global__ void __launch_bounds__(kVolThreads, 2) k_volume_plan(CaseTab ct, int 
 #pragma unroll
             for (int t = 0; t < kPlanUnroll; ++t) {
                 const int e = e0 + t * blockDim.x;
-                kz[t] = e < j1 ? find_row(p_bnd, dims[2], e) : 0;
+                if (e < j1)
+                    while (p_bnd[kzb + 1] <= e) ++kzb;
+                kz[t] = kzb;
                 const long long at = base + b_bnd[kz[t]] + (e - p_bnd[kz[t]]);
                 ent[t] = e < j1 ? pl.bent[at] : kPvfSkip;
                 al[t] = e < j1 ? pl.balpha[at] : make_float2(0.f, 0.f);
