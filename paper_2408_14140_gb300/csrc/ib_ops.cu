@@ -113,12 +113,13 @@ __global__ void k_prep_spread(DevGrid g, int M, const double *__restrict__ X,
 // leading 24 bits (split on the integer pipe, each at most |R_l|) and then
 // enlarged by a relative 2^-18, which keeps it an upper bound of max |R_l|
 // above the FP32 roundings; no FP64 operation runs per marker.
-__global__ void __launch_bounds__(256) k_marker_radius(int P, const double *__restrict__ Xr,
+constexpr int kRadiusThreads = 1024;  // a particle's ~2k markers: two loads in flight per thread
+__global__ void __launch_bounds__(kRadiusThreads) k_marker_radius(int P, const double *__restrict__ Xr,
                                                        const double *__restrict__ Ur,
                                                        const double *__restrict__ Wr,
                                                        const int *__restrict__ moff, const double *__restrict__ R,
                                                        const double *__restrict__ dV, double *__restrict__ rho) {
-    __shared__ float s_max[8];
+    __shared__ float s_max[kRadiusThreads / 32];
     const int p = blockIdx.x;
     if (p >= P) return;
     const bool pok = finite3(Xr + 3 * p) && finite3(Ur + 3 * p) && finite3(Wr + 3 * p);
@@ -2183,7 +2184,7 @@ static int run_mdf(ib_ctx *ctx, Arena &ar, const CaseTab &ct, const ib_particles
     cudaStream_t fs = ctx->fork_stream;
     cudaEventRecord(ctx->fork_ev[0], s);
     cudaStreamWaitEvent(fs, ctx->fork_ev[0], 0);
-    k_marker_radius<<<P, 256, 0, fs>>>(P, pp->Xr, pp->Ur, pp->Wr, pp->marker_offset, mk->R, mk->dV, rho);
+    k_marker_radius<<<P, kRadiusThreads, 0, fs>>>(P, pp->Xr, pp->Ur, pp->Wr, pp->marker_offset, mk->R, mk->dV, rho);
     if (order == IB_ORDER_SEQUENTIAL)
         launch_pdl(k_conflicts, dim3(grid_blocks(32 * P, 256, ctx->sm_count)), dim3(256), 0, fs, ct, P, KW,
                    (const double *)pp->Xr, (const double *)rho, nbr_cnt, nbr);

@@ -670,7 +670,7 @@ __global__ void __launch_bounds__(kVolThreads, 3) k_volume(CaseTab ct, int P, in
 // order.
 // ---------------------------------------------------------------------------
 constexpr int kPlanUnroll = 4;
-constexpr size_t kPlanSmem = 7 * (kVolThreads / 32) * sizeof(double);  // the warps' sums
+constexpr size_t kPlanSmem = 10 * (kVolThreads / 32) * sizeof(float2);  // the warps' sums
 
 template <typename T>
 __global__ void __launch_bounds__(kVolThreads, 2) k_volume_plan(CaseTab ct, int P, int nsplit,
@@ -846,39 +846,53 @@ __global__ void __launch_bounds__(kVolThreads, 2) k_volume_plan(CaseTab ct, int 
             }
         }
     }
-    // warp sums (double-float; the interior count exactly), then the CTA's
-    // eight warp sums and the particle's nsplit CTA sums in FP64, in order
-    // (the few FP64 operations left: FP64 issue is scarce on this part)
+    // warp sums (double-float; the interior count exactly), the CTA's eight
+    // warp sums in double-float too, one conversion to FP64 per quantity, and
+    // the particle's nsplit CTA sums in FP64, in order (FP64 issue is scarce
+    // on this part: no FP64 operation per warp)
 #pragma unroll
     for (int q = 0; q < 3; ++q) df_warp_sum(W[q]);
 #pragma unroll
     for (int q = 0; q < 6; ++q) df_warp_sum(Pm[q]);
     df_warp_sum(V);
     const unsigned ncell = __reduce_add_sync(0xffffffffu, (unsigned)nint_cells);
-    double *s_w = s_vol;  // [warps][7]
+    float2 *s_w = (float2 *)s_vol;  // [warps][10] double-float warp sums
+    __shared__ unsigned s_ncell[kVolThreads / 32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     if (lane == 0) {
-        double pm[6];
 #pragma unroll
-        for (int q = 0; q < 6; ++q) pm[q] = (double)Pm[q].hi + (double)Pm[q].lo;
+        for (int q = 0; q < 3; ++q) s_w[wid * 10 + q] = make_float2(W[q].hi, W[q].lo);
 #pragma unroll
-        for (int q = 0; q < 3; ++q) s_w[wid * 7 + q] = (double)W[q].hi + (double)W[q].lo;
-        s_w[wid * 7 + 3] = pm[0] - pm[1];
-        s_w[wid * 7 + 4] = pm[2] - pm[3];
-        s_w[wid * 7 + 5] = pm[4] - pm[5];
-        s_w[wid * 7 + 6] = (double)ncell + ((double)V.hi + (double)V.lo);
+        for (int q = 0; q < 6; ++q) s_w[wid * 10 + 3 + q] = make_float2(Pm[q].hi, Pm[q].lo);
+        s_w[wid * 10 + 9] = make_float2(V.hi, V.lo);
+        s_ncell[wid] = ncell;
     }
     __syncthreads();
-    __shared__ int s_last;
+    __shared__ double s_q[10];
+    if (threadIdx.x < 10) {
+        const int k = threadIdx.x;
+        DF x = {0.f, 0.f};
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) x = df_sum(x, DF{s_w[w * 10 + k].x, s_w[w * 10 + k].y});
+        s_q[k] = df_to_double(make_float2(x.hi, x.lo));
+    }
+    __syncthreads();
     if (threadIdx.x < 7) {
         const int k = threadIdx.x;
-        double x = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) x += s_w[w * 7 + k];
+        double x;
+        if (k < 3) {
+            x = s_q[k];
+        } else if (k < 6) {
+            x = s_q[3 + 2 * (k - 3)] - s_q[4 + 2 * (k - 3)];  // (ry w2 - rz w1, rz w0 - rx w2, rx w1 - ry w0)
+        } else {
+            unsigned n = 0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) n += s_ncell[w];
+            x = (double)n + s_q[9];
+        }
         const double h3 = g.h * g.h * g.h;
         partial[((size_t)p * nsplit + split) * 7 + k] = x * h3;
         __threadfence();  // release: partials before the count
     }
-    __syncthreads();
+    __shared__ int s_last;
     if (threadIdx.x == 0) {
         __threadfence();
         s_last = atomicAdd(done + p, 1u) == (unsigned int)nsplit - 1;
