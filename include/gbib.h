@@ -482,7 +482,11 @@ GBIB_API int level_projection(ib_ctx *ctx, const ib_grid *grid, void *u, void *p
 
 /* ---- marker force and torque (Eqs. particle1, particle2, first terms) ---
  * F_ib[p] = -rho_f sum_l F[l] dV[l],  T_ib[p] = -rho_f sum_l R[l] x F[l] dV[l]
- * over the markers of particle p; FP64, overwritten.                      */
+ * over the markers of particle p; FP64, overwritten.  Each particle's
+ * markers are summed in a fixed number of contiguous ranges whose sums are
+ * added in order, so the result is deterministic and does not depend on the
+ * other particles of the call.  Scratch comes from the context workspace
+ * (IB_ERR_OOM when it is short).                                           */
 GBIB_API int particle_force_torque(ib_ctx *ctx, const ib_particles *parts,
                           const ib_markers *marks, const double *F,
                           double rho_f, double *F_ib, double *T_ib,
