@@ -4,8 +4,11 @@
 //   * marker force and torque (first terms of Eqs. particle1/particle2),
 //   * repulsive-potential collision (Eq. DKT_model) + Newton-Euler update
 //     (Eqs. particle1, particle2) + centroid update (Eq. pr2).
-// All sums are FP64 and run in a fixed order (per-thread strided partials,
-// then a fixed shuffle tree), so results are bitwise reproducible.
+// All sums run in a fixed order (per-thread partials, then fixed warp, CTA
+// and cross-CTA orders), so results are bitwise reproducible.  The volume
+// integrals' per-cell sums are double-float (FP32 pipes, about 44 significant
+// bits) in both field precisions; the force, torque, collision and update
+// arithmetic is FP64.
 #include <climits>
 #include <mutex>
 #include <new>
